@@ -1,0 +1,310 @@
+#!/usr/bin/env python
+"""Throughput of one forward + gradient evaluation (fwd+grad slice-steps/s) on a GB300.
+
+Workload (default): transmon (4 levels) x cavity (10 levels), d = 40, N = 2000 slices, dt = 1 ns,
+two transmon drives, |g,0> -> |g,1> state transfer with a forbidden-level penalty at every slice,
+FP32 products, sqrt(N) checkpointing.  A "step" is one full evaluation: norm bound and (p, n),
+all slice exponentials, the forward propagation with per-slice costs, the backward costate
+sweep with recomputation from checkpoints, the exact adjoint of every truncated exponential
+and the gradient reduction.  Metric: N x trajectories / seconds per evaluation.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun every rank evaluates its own replica (the path has no data exchange); the
+value is the sum over ranks of slice-steps divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+grad slice-steps/s"
+UNIT = "slice-steps/s"
+# FP32 FMA peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (max SM clock)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="transmon_cavity")
+    ap.add_argument("--precision", default=None)
+    ap.add_argument("--ckpt-stride", type=int, default=0)
+    ap.add_argument("--cpu-sample", type=int, default=0, help="slices in the oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def make_problem(name):
+    import synthetic as sy
+    return sy.WORKLOADS[name]()
+
+
+def config_of(prob, precision, stride, extra=None):
+    cfg = {"workload": prob.name, "d": prob.d, "N": prob.N, "M": prob.M, "S": prob.S, "E": prob.E,
+           "precision": precision, "ckpt_stride": stride,
+           "l2": "flushed before every timed step (256 MiB write outside the step's events)"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == len(self.FIELDS):
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = sorted(float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit())
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[4 + i].lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------------ oracle (CPU) timing
+def oracle_sample_time(workload, nslices, repeats=1):
+    """Times the CPU FP64 oracle on the first `nslices` slices of the workload in a child
+    process limited to one BLAS thread.  Returns (seconds per evaluation, slices)."""
+    code = f"""
+import os, sys, time
+sys.path.insert(0, {ROOT!r})
+import synthetic as sy
+from oracle import qoc_oracle as orc
+p = sy.WORKLOADS[{workload!r}](N={nslices})
+orc.cost_and_grad(p, p.u)
+ts = []
+for _ in range({repeats}):
+    t0 = time.perf_counter(); orc.cost_and_grad(p, p.u); ts.append(time.perf_counter() - t0)
+print(sum(ts) / len(ts))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr)
+    return float(r.stdout.strip().split()[-1]), nslices
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    prob = make_problem(args.workload)
+    nsl = args.cpu_sample or max(20, prob.N // 20)
+    import synthetic as sy
+    from oracle import qoc_oracle as orc
+    sample = sy.WORKLOADS[args.workload](N=nsl)
+    for _ in range(args.warmup):
+        orc.cost_and_grad(sample, sample.u)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        orc.cost_and_grad(sample, sample.u)
+        ts.append(time.perf_counter() - t0)
+    t = sum(ts) / len(ts)
+    value = nsl * sample.E / t
+    desc = (f"CPU FP64 oracle (eigendecomposition exponentials, explicit adjoint) on the first {nsl} of "
+            f"{prob.N} slices, steps={args.steps}, numpy BLAS default threads")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(prob, "fp64-oracle", 0, {"sample_slices": nsl}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def expm_flops_per_slice(d, p, n):
+    """Algorithmic flops of one slice exponential: p - 1 Horner and n squaring complex d x d
+    products at 8 d^3 real flops each."""
+    return (p - 1 + n) * 8.0 * d ** 3
+
+
+def ours_arm(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_1612_04929_gb300 import Context, build as qbuild
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        qbuild.build()
+    if world > 1:
+        dist.barrier()
+    prob = make_problem(args.workload)
+    precision = args.precision or prob.precision
+    stream = torch.cuda.Stream()          # every kernel of the step and every event on one stream
+    torch.cuda.set_stream(stream)
+    ctx = Context(precision, device=local, stream=stream.cuda_stream, ckpt_stride=args.ckpt_stride, profile=True)
+    ctx.set_problem(prob)
+    u = torch.tensor(prob.u, dtype=torch.float64, device="cuda")
+    grad = torch.empty_like(u)
+    out = torch.empty(6, dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def step():
+        ctx.evaluate_device(u.data_ptr(), grad.data_ptr(), out.data_ptr())
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    ctx.sync()
+    info = ctx.info()
+    K = args.steps
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ctx.reset_profile()
+    with ClockSampler(local) as clk:
+        for k in range(K):
+            flush.zero_()
+            starts[k].record(stream)
+            step()
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / K
+    prof = ctx.profile()
+    ctx.sync()
+    t_max = ms
+    if world > 1:
+        tt = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    units = prob.N * prob.E
+    value = units * world / (t_max / 1e3)
+
+    # dominant kernel and its roofline (algorithmic flops / measured launch time)
+    d, p, n = prob.d, info["p"], info["n"]
+    per_slice = {"expm_fwd": expm_flops_per_slice(d, p, n),
+                 "expm_fwd (recompute)": expm_flops_per_slice(d, p, n),
+                 "expm_adj": 3 * expm_flops_per_slice(d, p, n) + 8.0 * d * d * prob.S}
+    top = max(prof.items(), key=lambda kv: kv[1][1])
+    top_name, (top_launches, top_ms) = top
+    slices_per_eval = prob.N * prob.E
+    roof = None
+    if top_name in per_slice:
+        evals = K
+        flops = per_slice[top_name] * slices_per_eval * evals
+        if top_name == "expm_fwd":   # forward launches of every segment (+ recomputes counted apart)
+            pass
+        achieved = flops / (top_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS if precision != "fp64" else None,
+                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS if precision != "fp64" else None,
+                "traffic": None, "kernel": top_name, "launches": top_launches,
+                "avg_launch_ms": top_ms / top_launches,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"}
+    kernels = {k: {"launches": v[0], "ms_per_step": v[1] / K} for k, v in prof.items()}
+
+    # end to end through the host API with pinned buffers
+    uh = torch.tensor(prob.u, dtype=torch.float64).pin_memory()
+    gh = torch.empty_like(uh).pin_memory()
+    ctx.evaluate_host_ptr(uh.data_ptr(), gh.data_ptr())
+    e2e_t = []
+    for k in range(max(1, min(K, 5))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.evaluate_host_ptr(uh.data_ptr(), gh.data_ptr())
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_value = units * world / (sum(e2e_t) / len(e2e_t))
+    mn_bytes = prob.M * prob.N * 8
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        nsl = args.cpu_sample or max(20, prob.N // 10)
+        try:
+            t, nsl = oracle_sample_time(args.workload, nsl)
+            cpu = {"value": nsl * prob.E / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"first {nsl} of {prob.N} slices of the same workload, FP64 oracle, 1 BLAS thread, "
+                             f"{t:.2f} s per evaluation"}
+        except Exception as exc:   # keep the GPU line even if the CPU leg fails
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {exc}"}
+
+    # error of this evaluation against the oracle is checked by the tests; report the cost here
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+                "warmup": max(args.warmup, 3), "ms_per_step": t_max, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": {"fp64": "f64", "fp32": "f32", "tf32": "tf32x3", "bf16": "bf16x3"}[precision],
+                "data": "synthetic (seeded transmon-cavity system, random controls)",
+                "config": config_of(prob, precision, info["ckpt_stride"],
+                                    {"p": p, "n": n, "wave_slices": info["wave_slices"], "n_waves": info["n_waves"]}),
+                "roofline": roof, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": mn_bytes,
+                        "d2h_bytes_per_step": mn_bytes + 6 * 8 + 32},
+                "gpu_launches": info["launches_per_eval"] * K,
+                "clocks": clk.summary(), "kernels": kernels,
+                "cost": float(out[0].item())}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        ours_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,182 @@
+/*
+ * qoc.h -- C ABI of the GB300 forward + gradient evaluation of a piecewise-constant
+ * quantum-control cost (Leung, Abdelhafez, Koch, Schuster, arXiv:1612.04929).
+ *
+ * One evaluation computes, for controls u[k][j] (k = 1..M controls, j = 1..N slices):
+ *   H_j   = H_0 + sum_k u[k][j] H_k (+ delta_e H_det per ensemble member)        Sec. II, Eq. 1
+ *   U_j   = exp(-i H_j dt) by a truncated Taylor series of order p after scaling
+ *           by 2^-n, then n squarings, with one global (p, n) per evaluation       Sec. III, Eqs. 3, 9, 10
+ *   Psi_j = U_j Psi_{j-1} for a d x S block of columns (S = d, Psi_0 = I: gates)  Sec. II, Eqs. 2, 4
+ *   C     = a_fid C_fid + a_amp C3 + a_var C4 + a_forbid C5 + a_time C67          Sec. II, Table I
+ *   dC/du by a backward (adjoint) sweep that differentiates the truncated series
+ *   exactly                                                                       Sec. II.B, Appendix A
+ * The cost terms (Table I, with column weights w_s, W = sum_s w_s):
+ *   O_j   = sum_s w_s <PsiT^s(j)|Psi_j^s> / W
+ *   C_fid = 1 - |O_N|^2                          (C1 gate, C2 state, C2-Sigma subspace)
+ *   C3    = sum_{k,j} u[k][j]^2
+ *   C4    = sum_k sum_{j=2..N} (u[k][j] - u[k][j-1])^2
+ *   C5    = sum_{j=1..N} sum_s w_s sum_{f in F} |Psi_j[f][s]|^2   (forbidden basis states F)
+ *   C67   = 1 - (1/N) sum_{j=1..N} |O_j|^2        (C6 gate / C7 state; PsiT(j) may vary with j)
+ * State-dependent terms are averaged over ensemble members.
+ *
+ * Conventions for every entry point:
+ *   - Complex arrays are complex128 interleaved (re, im) and row-major: a d x d matrix A has
+ *     A[a][b] at doubles [2*(a*d + b)], [2*(a*d + b) + 1]; a d x S block likewise with S columns.
+ *   - Host input arrays are copied before the call returns; the library never keeps caller
+ *     pointers.  Output arrays are owned by the caller.
+ *   - Every call returns a qoc_status; no C++ exception crosses this boundary.  On an error the
+ *     context keeps its previous valid state and qoc_last_error() describes the failure.
+ *   - A context owns all of its device memory and runs on one CUDA stream; use one context per
+ *     host thread.
+ */
+#ifndef QOC_H
+#define QOC_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qoc_ctx qoc_ctx;
+
+typedef enum qoc_status {
+    QOC_OK = 0,
+    QOC_ERR_ARG = 1,            /* NULL pointer where one is required, or an invalid option */
+    QOC_ERR_SHAPE = 2,          /* d, M, N, S, E, or an index out of range */
+    QOC_ERR_NOT_HERMITIAN = 3,  /* H_0, H_k or H_det deviates from Hermitian by > 1e-12 max|H| */
+    QOC_ERR_NONFINITE = 4,      /* NaN or Inf in an input */
+    QOC_ERR_STATE = 5,          /* call order: set_system before set_targets before evaluate */
+    QOC_ERR_OOM = 6,            /* device allocation failed */
+    QOC_ERR_CUDA = 7,           /* a CUDA runtime call or kernel launch failed */
+    QOC_ERR_TIMEOUT = 8,        /* a bounded device wait ran out (kernel returned early) */
+    QOC_ERR_UNSUPPORTED = 9,    /* size / precision combination this build does not provide */
+    QOC_ERR_RANGE = 10          /* the (p, n) heuristic needs p above its maximum (huge |H dt|) */
+} qoc_status;
+
+/* Arithmetic of the Taylor, squaring and propagation products.  Reductions of overlaps,
+ * traces, costs and gradient sums are FP64 in every mode; so is the norm bound that picks n. */
+typedef enum qoc_precision {
+    QOC_PREC_FP64 = 0,          /* plain FP64 form: parity anchor */
+    QOC_PREC_FP32 = 1,          /* FP32 propagation, costates and adjoint; slice exponentials in
+                                   split hi+lo FP32 (see qoc_options.plain_fp32_exp) */
+    QOC_PREC_TF32_SPLIT = 2,    /* large d: TF32 tensor-core products, hi+lo split, FP32 accum */
+    QOC_PREC_BF16_SPLIT = 3     /* large d: BF16 tensor-core products, hi+lo split, FP32 accum */
+} qoc_precision;
+
+typedef struct qoc_options {
+    int precision;        /* qoc_precision */
+    double tol;           /* bound on the Taylor remainder per slice after squaring; <= 0: default
+                             (1e-15 FP64, 1e-8 otherwise) */
+    double theta_max;     /* n is the least n >= 0 with theta / 2^n <= theta_max; <= 0: default
+                             (0.25 FP64, 1.0 otherwise) */
+    int ckpt_stride;      /* slices between stored checkpoints of the propagated block Psi
+                             (0: ceil(sqrt(N))).  The backward sweep regenerates Psi_j and U_j
+                             between checkpoints instead of storing all N of them. */
+    int device;           /* CUDA device ordinal */
+    void* stream;         /* cudaStream_t to run on (cudaStreamLegacy = (void*)1 selects the legacy
+                             default stream); NULL: the context creates its own stream */
+    int p_override;       /* >= 1 forces the Taylor order p (diagnostics); <= 0: heuristic */
+    int n_override;       /* >= 0 forces the squaring count n (diagnostics); < 0: heuristic */
+    int profile;          /* != 0: bracket every kernel launch with CUDA events (qoc_get_profile) */
+    int wave_slices;      /* slices whose propagators are held at once (one parallel launch),
+                             rounded up to a multiple of ckpt_stride; 0: twice the SM count.
+                             Device memory is O(wave d^2 + N / ckpt_stride d S). */
+    int plain_fp32_exp;   /* FP32 form only.  0 (default): the slice exponentials (forward and
+                             recomputation) use split hi+lo FP32 arithmetic from an FP64 H_j, which
+                             keeps the coherent rounding of H_j dt out of long evolutions;
+                             != 0: plain FP32 exponentials (faster, diagnostics) */
+} qoc_options;
+
+/* Information about the last evaluation (reading it synchronises the context stream). */
+typedef struct qoc_info {
+    int p, n;             /* Taylor order and squaring count used */
+    double theta;         /* dt * max_j ||H_j||_1 bound that picked n (FP64) */
+    int ckpt_stride;      /* slices per checkpoint segment */
+    int wave_slices;      /* slices per parallel launch (multiple of ckpt_stride) */
+    int n_waves;          /* number of waves */
+    int launches_per_eval;/* kernels launched by one evaluation */
+    int kernel_path;      /* 0: fused per-slice kernels (small d); 1: batched tiled GEMM (large d) */
+    long long device_bytes; /* device memory held by the context */
+} qoc_info;
+
+/* Per-kernel timings gathered while qoc_options.profile is set: for each kernel class the number
+ * of launches and the summed CUDA-event duration (ms) on the context stream. */
+#define QOC_PROFILE_SLOTS 16
+typedef struct qoc_profile {
+    int count;                           /* classes filled */
+    char name[QOC_PROFILE_SLOTS][32];
+    long long launches[QOC_PROFILE_SLOTS];
+    double total_ms[QOC_PROFILE_SLOTS];
+} qoc_profile;
+
+/* Fills *opt with the defaults (FP64, heuristic p and n, sqrt(N) checkpoints, device 0, own
+ * stream). */
+void qoc_default_options(qoc_options* opt);
+
+/* Creates a context on opt->device (opt may be NULL for the defaults).  *out receives the
+ * context, or NULL on failure.  Errors: QOC_ERR_ARG (out NULL, bad precision), QOC_ERR_CUDA. */
+qoc_status qoc_create(qoc_ctx** out, const qoc_options* opt);
+
+/* Releases every device buffer and the stream the context created.  NULL is a no-op. */
+void qoc_destroy(qoc_ctx* ctx);
+
+/* Text of the last error of this context (never NULL; "" after a successful call).  The pointer
+ * stays valid until the next call on the same context. */
+const char* qoc_last_error(const qoc_ctx* ctx);
+
+/* Static name of a status code. */
+const char* qoc_status_string(qoc_status s);
+
+/* The system of Eq. 1.  H0: d x d complex; Hk: M consecutive d x d complex matrices (may be
+ * NULL when M = 0); dt > 0; N >= 1 slices; 1 <= d <= 512; 0 <= M <= 64.
+ * Checks Hermiticity (QOC_ERR_NOT_HERMITIAN) and finiteness (QOC_ERR_NONFINITE).  Resets the
+ * targets and the ensemble (a later evaluate needs qoc_set_targets again). */
+qoc_status qoc_set_system(qoc_ctx* ctx, int d, int M, const double* H0, const double* Hk,
+                          double dt, int N);
+
+/* Initial columns and costs (Table I).  psi0, psiT: d x S complex (1 <= S <= d); forbidden: nF
+ * basis indices in [0, d) (may be NULL when nF = 0); col_weight: S non-negative weights with a
+ * positive sum (NULL: all 1); psiT_path: N consecutive d x S targets for the per-slice time cost
+ * C67 (NULL: psiT at every slice); alpha: 5 weights [fid, C3 amplitude, C4 variation,
+ * C5 forbidden, C67 time].  Requires qoc_set_system (else QOC_ERR_STATE). */
+qoc_status qoc_set_targets(qoc_ctx* ctx, int S, const double* psi0, const double* psiT, int nF,
+                           const int* forbidden, const double* col_weight,
+                           const double* psiT_path, const double* alpha);
+
+/* Detuning ensemble for robust control: member e propagates H_j + delta[e] Hdet; the
+ * state-dependent cost terms and their gradients are averaged over the E members.  E >= 1;
+ * delta: E doubles; Hdet: d x d complex Hermitian (may be NULL when every delta is 0).
+ * Requires qoc_set_system. */
+qoc_status qoc_set_ensemble(qoc_ctx* ctx, int E, const double* delta, const double* Hdet);
+
+/* One forward + gradient evaluation from host memory.  u: M x N doubles (row k holds control k
+ * over the N slices); *cost receives C; grad (M x N doubles) receives dC/du; terms (5 doubles,
+ * may be NULL) receives the unweighted [C_fid, C3, C4, C5, C67].  Copies u to the device, runs,
+ * copies the results back and synchronises the stream.  Requires set_system and set_targets. */
+qoc_status qoc_evaluate_cost_and_grad(qoc_ctx* ctx, const double* u, double* cost, double* grad,
+                                      double* terms);
+
+/* The same evaluation on device memory, asynchronous on the context stream: u_dev (M x N
+ * doubles), grad_dev (M x N doubles) and out_dev (6 doubles: C then the 5 terms) are device
+ * pointers owned by the caller.  Returns after enqueueing; errors raised inside kernels are
+ * reported by the next synchronising call (qoc_sync, qoc_get_info or a host evaluation). */
+qoc_status qoc_evaluate_device(qoc_ctx* ctx, const double* u_dev, double* grad_dev,
+                               double* out_dev);
+
+/* Waits for the context stream and reports a device-side error of earlier evaluations. */
+qoc_status qoc_sync(qoc_ctx* ctx);
+
+/* Fills *info (synchronises). */
+qoc_status qoc_get_info(qoc_ctx* ctx, qoc_info* info);
+
+/* Synchronises and returns the per-kernel timings accumulated since the last reset (all zero
+ * when the context was created without qoc_options.profile). */
+qoc_status qoc_get_profile(qoc_ctx* ctx, qoc_profile* out);
+
+/* Clears the accumulated per-kernel timings. */
+qoc_status qoc_reset_profile(qoc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QOC_H */

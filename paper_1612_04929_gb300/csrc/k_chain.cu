@@ -1,0 +1,337 @@
+// Kernels around the slice exponentials and the serial sweeps (k_serial.cu):
+//  * k_norms / k_theta  : FP64 induced 1-norms of H_0, H_k, H_det and the global bound
+//                         theta = dt max_j (||H_0||_1 + |delta|max ||H_det||_1 + sum_k |u_kj| ||H_k||_1)
+//                         that picks one (p, n) for all slices (Sec. III).
+//  * k_slice_costs      : per-slice overlaps O_j and forbidden occupations (Table I C5, C6/C7).
+//  * k_sources          : dC/dPsi_j of every state-dependent cost term (Appendix A, the source
+//                         terms that Algorithm 3 adds at every slice; the fidelity term at j = N).
+//  * k_finalize         : FP64 cost reduction (Table I weighted sum), the C3/C4 gradient terms
+//                         and the ensemble sum of the per-slice gradients.
+#include <math.h>
+
+#include "qoc_device.cuh"
+#include "qoc_internal.h"
+
+namespace qoc {
+
+// ------------------------------------------------------------------------------------------
+// norms and (p, n)
+// ------------------------------------------------------------------------------------------
+__global__ void k_norms(const double2* __restrict__ mats, int d, double* __restrict__ norms) {
+    __shared__ double red[32];
+    const double2* A = mats + (size_t)blockIdx.x * d * d;
+    double best = 0.0;
+    for (int b = threadIdx.x; b < d; b += blockDim.x) {
+        double s = 0.0;
+        for (int a = 0; a < d; ++a) {
+            const double2 z = A[(size_t)a * d + b];
+            s += hypot(z.x, z.y);
+        }
+        best = fmax(best, s);
+    }
+    for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+        norms[blockIdx.x] = m;
+    }
+}
+
+cudaError_t launch_norms(const double2* mats, int count, int d, double* norms, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    k_norms<<<count, 256, 0, st>>>(mats, d, norms);
+    return cudaGetLastError();
+}
+
+__global__ void k_theta(const double* __restrict__ u, int M, int N, const double* __restrict__ norms,
+                        const double* __restrict__ delta, int E, double dt, double theta_max, double tol,
+                        int p_override, int n_override, DevParams* __restrict__ prm) {
+    __shared__ double red[32];
+    double best = 0.0;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        double s = 0.0;
+        for (int k = 0; k < M; ++k) s += fabs(u[(size_t)k * N + j]) * norms[1 + k];
+        best = fmax(best, s);
+    }
+    for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) best = fmax(best, red[w]);
+    double dmax = 0.0;
+    if (delta)
+        for (int e = 0; e < E; ++e) dmax = fmax(dmax, fabs(delta[e]));
+    const double theta = dt * (norms[0] + dmax * norms[M + 1] + best);
+    int n = 0;
+    while (ldexp(theta, -n) > theta_max && n < 1000) ++n;
+    if (n_override >= 0) n = n_override;
+    const double ts = ldexp(theta, -n);
+    int p = 1;
+    double fact = 2.0;   // (p + 1)!
+    int err = 0;
+    for (;;) {
+        const double rem = ldexp(1.0, n) * pow(ts, (double)(p + 1)) / fact / (1.0 - ts / (p + 2));
+        if (rem <= tol) break;
+        if (p >= kPMax) { err |= kErrRange; break; }
+        ++p;
+        fact *= (double)(p + 1);
+    }
+    if (p_override >= 1) { p = p_override; err &= ~kErrRange; }
+    prm->theta = theta;
+    prm->p = p;
+    prm->n = n;
+    prm->s = ldexp(dt, -n);
+    prm->err = err;
+}
+
+cudaError_t launch_theta(const double* u, int M, int N, const double* norms, const double* delta, int E,
+                         double dt, double theta_max, double tol, int p_override, int n_override,
+                         DevParams* prm, cudaStream_t st) {
+    k_theta<<<1, 1024, 0, st>>>(u, M, N, norms, delta, E, dt, theta_max, tol, p_override, n_override, prm);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// conversions
+// ------------------------------------------------------------------------------------------
+template <typename R>
+__global__ void k_convert(const double2* __restrict__ src, C_t<R>* __restrict__ dst, size_t count) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+        const double2 z = src[i];
+        C_t<R> o;
+        o.x = (R)z.x;
+        o.y = (R)z.y;
+        dst[i] = o;
+    }
+}
+
+template <typename R>
+cudaError_t launch_convert(const double2* src, C_t<R>* dst, size_t count, cudaStream_t st) {
+    if (count == 0) return cudaSuccess;
+    const int blocks = (int)((count + 255) / 256 < 4096 ? (count + 255) / 256 : 4096);
+    k_convert<R><<<blocks, 256, 0, st>>>(src, dst, count);
+    return cudaGetLastError();
+}
+
+// row-major d x S (FP64) -> `copies` panel-layout blocks d x Spad (R), zero padding
+template <typename R>
+__global__ void k_to_panels(const double2* __restrict__ src, C_t<R>* __restrict__ dst, int d, int S, int ncb,
+                            int cb, int pstride, size_t dst_stride, size_t src_stride) {
+    const size_t per = (size_t)ncb * pstride;
+    C_t<R>* out = dst + blockIdx.y * dst_stride;
+    src += blockIdx.y * src_stride;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < per; i += (size_t)gridDim.x * blockDim.x) {
+        const int kb = (int)(i / pstride);
+        const int rem = (int)(i - (size_t)kb * pstride);
+        const int a = rem / cb, s = kb * cb + rem % cb;
+        C_t<R> o;
+        o.x = 0;
+        o.y = 0;
+        if (rem < d * cb && s < S) {
+            const double2 z = src[(size_t)a * S + s];
+            o.x = (R)z.x;
+            o.y = (R)z.y;
+        }
+        out[i] = o;
+    }
+}
+
+template <typename R>
+cudaError_t launch_to_panels(const double2* src, C_t<R>* dst, int d, int S, StateView<R> sv, int copies,
+                             size_t dst_stride, size_t src_stride, cudaStream_t st) {
+    const size_t per = sv.slice();
+    const int blocks = (int)((per + 255) / 256 < 1024 ? (per + 255) / 256 : 1024);
+    k_to_panels<R><<<dim3(blocks, copies), 256, 0, st>>>(src, dst, d, S, sv.ncb, sv.cb, sv.pstride, dst_stride,
+                                                         src_stride);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// per-slice costs and sources
+// ------------------------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(256)
+k_slice_costs(int d, StateView<R> sv, int j0, int N, const C_t<R>* __restrict__ states, int wmax, CostView<R> cv,
+              double2* __restrict__ Oj, double* __restrict__ C5j, double2* __restrict__ Ofin) {
+    using C = C_t<R>;
+    __shared__ double red[32];
+    const int jl = blockIdx.x, e = blockIdx.y, j = j0 + jl, cb = sv.cb, ps = sv.pstride;
+    const size_t slice = sv.slice();
+    const C* psi = states + ((size_t)e * (wmax + 1) + jl + 1) * slice;
+    const C* T = cv.path ? cv.path + (size_t)j * slice : cv.psiT;
+    const bool last = (j == N - 1);
+    double ore = 0, oim = 0, c5 = 0, fre = 0, fim = 0;
+    for (size_t i = threadIdx.x; i < slice; i += blockDim.x) {
+        const int kb = (int)(i / ps);
+        const int rem = (int)(i - (size_t)kb * ps);
+        if (rem >= d * cb) continue;
+        const int a = rem / cb, s = kb * cb + rem % cb;
+        const double w = cv.w[s];
+        if (w == 0.0) continue;
+        const C z = psi[i], t = T[i];
+        ore += w * ((double)t.x * z.x + (double)t.y * z.y);
+        oim += w * ((double)t.x * z.y - (double)t.y * z.x);
+        if (cv.fmask[a]) c5 += w * ((double)z.x * z.x + (double)z.y * z.y);
+        if (last) {
+            const C f = cv.psiT[i];
+            fre += w * ((double)f.x * z.x + (double)f.y * z.y);
+            fim += w * ((double)f.x * z.y - (double)f.y * z.x);
+        }
+    }
+    ore = block_sum(ore, red);
+    oim = block_sum(oim, red);
+    c5 = block_sum(c5, red);
+    if (last) {
+        fre = block_sum(fre, red);
+        fim = block_sum(fim, red);
+    }
+    if (threadIdx.x == 0) {
+        Oj[(size_t)e * N + j] = make_double2(ore / cv.Wsum, oim / cv.Wsum);
+        C5j[(size_t)e * N + j] = c5;
+        if (last) Ofin[e] = make_double2(fre / cv.Wsum, fim / cv.Wsum);
+    }
+}
+
+template <typename R>
+cudaError_t launch_slice_costs(int d, StateView<R> sv, int j0, int wlen, int N, int E, const C_t<R>* states, int wmax,
+                               const CostView<R>& cv, double2* Oj, double* C5j, double2* Ofin, cudaStream_t st) {
+    k_slice_costs<R><<<dim3(wlen, E), 256, 0, st>>>(d, sv, j0, N, states, wmax, cv, Oj, C5j, Ofin);
+    return cudaGetLastError();
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256)
+k_sources(int d, StateView<R> sv, int j0, int N, int E, const C_t<R>* __restrict__ states, int wmax, CostView<R> cv,
+          const double2* __restrict__ Oj, const double2* __restrict__ Ofin, C_t<R>* __restrict__ src) {
+    using C = C_t<R>;
+    const int jl = blockIdx.x, e = blockIdx.y, j = j0 + jl, cb = sv.cb, ps = sv.pstride;
+    const size_t slice = sv.slice();
+    const C* psi = states + ((size_t)e * (wmax + 1) + jl + 1) * slice;
+    const C* T = cv.path ? cv.path + (size_t)j * slice : cv.psiT;
+    C* out = src + ((size_t)e * wmax + jl) * slice;
+    const double invE = 1.0 / E;
+    const double2 o = Oj[(size_t)e * N + j];
+    const bool last = (j == N - 1);
+    const double2 of = last ? Ofin[e] : make_double2(0.0, 0.0);
+    // coefficient of T:  -(2 a67 / N) O_j w / W ;  of psiT at j = N: -2 a_fid O_N w / W
+    const double ct = -2.0 * cv.alpha[4] / N * invE / cv.Wsum;
+    const double cf = -2.0 * cv.alpha[0] * invE / cv.Wsum;
+    const double c5 = 2.0 * cv.alpha[3] * invE;
+    for (size_t i = threadIdx.x; i < slice; i += blockDim.x) {
+        const int kb = (int)(i / ps);
+        const int rem = (int)(i - (size_t)kb * ps);
+        const bool valid = rem < d * cb;
+        const int a = rem / cb, s = kb * cb + rem % cb;
+        const double w = valid ? cv.w[s] : 0.0;
+        double vx = 0.0, vy = 0.0;
+        if (w != 0.0) {
+            const C t = T[i];
+            vx = ct * w * (o.x * t.x - o.y * t.y);
+            vy = ct * w * (o.x * t.y + o.y * t.x);
+            if (cv.fmask[a]) {
+                const C z = psi[i];
+                vx += c5 * w * z.x;
+                vy += c5 * w * z.y;
+            }
+            if (last) {
+                const C f = cv.psiT[i];
+                vx += cf * w * (of.x * f.x - of.y * f.y);
+                vy += cf * w * (of.x * f.y + of.y * f.x);
+            }
+        }
+        C r;
+        r.x = (R)vx;
+        r.y = (R)vy;
+        out[i] = r;
+    }
+}
+
+template <typename R>
+cudaError_t launch_sources(int d, StateView<R> sv, int j0, int wlen, int N, int E, const C_t<R>* states, int wmax,
+                           const CostView<R>& cv, const double2* Oj, const double2* Ofin, C_t<R>* src,
+                           cudaStream_t st) {
+    k_sources<R><<<dim3(wlen, E), 256, 0, st>>>(d, sv, j0, N, E, states, wmax, cv, Oj, Ofin, src);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// final FP64 reduction
+// ------------------------------------------------------------------------------------------
+struct Alpha5 { double a[5]; };
+
+__global__ void __launch_bounds__(1024)
+k_finalize(int E, int M, int N, const double* __restrict__ u, Alpha5 al, const double2* __restrict__ Oj,
+           const double* __restrict__ C5j, const double2* __restrict__ Ofin, const double* __restrict__ gpart,
+           double* __restrict__ grad, double* __restrict__ out) {
+    __shared__ double red[32];
+    const int tid = threadIdx.x;
+    double c3 = 0, c4 = 0, c5 = 0, t67 = 0;
+    for (int i = tid; i < M * N; i += blockDim.x) {
+        const int k = i / N, j = i - k * N;
+        const double x = u[i];
+        c3 += x * x;
+        if (j > 0) {
+            const double dx = x - u[i - 1];
+            c4 += dx * dx;
+        }
+        double g = 0.0;
+        for (int e = 0; e < E; ++e) g += gpart[((size_t)e * M + k) * N + j];
+        g += al.a[1] * 2.0 * x;
+        double gv = 0.0;
+        if (j > 0) gv += 2.0 * (x - u[i - 1]);
+        if (j < N - 1) gv -= 2.0 * (u[i + 1] - x);
+        g += al.a[2] * gv;
+        grad[i] = g;
+    }
+    for (int i = tid; i < E * N; i += blockDim.x) {
+        c5 += C5j[i];
+        const double2 o = Oj[i];
+        t67 += o.x * o.x + o.y * o.y;
+    }
+    c3 = block_sum(c3, red);
+    c4 = block_sum(c4, red);
+    c5 = block_sum(c5, red);
+    t67 = block_sum(t67, red);
+    if (tid == 0) {
+        double fid = 0.0;
+        for (int e = 0; e < E; ++e) fid += 1.0 - (Ofin[e].x * Ofin[e].x + Ofin[e].y * Ofin[e].y);
+        fid /= E;
+        c5 /= E;
+        const double c67 = 1.0 - t67 / ((double)N * E);
+        out[1] = fid;
+        out[2] = c3;
+        out[3] = c4;
+        out[4] = c5;
+        out[5] = c67;
+        out[0] = al.a[0] * fid + al.a[1] * c3 + al.a[2] * c4 + al.a[3] * c5 + al.a[4] * c67;
+    }
+}
+
+cudaError_t launch_finalize(int E, int M, int N, const double* u, const double* alpha, const double2* Oj,
+                            const double* C5j, const double2* Ofin, const double* gpart, double* grad, double* out,
+                            cudaStream_t st) {
+    Alpha5 al;
+    for (int i = 0; i < 5; ++i) al.a[i] = alpha[i];
+    k_finalize<<<1, 1024, 0, st>>>(E, M, N, u, al, Oj, C5j, Ofin, gpart, grad, out);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// instantiations
+// ------------------------------------------------------------------------------------------
+#define QOC_INST(R)                                                                                              \
+    template cudaError_t launch_convert<R>(const double2*, C_t<R>*, size_t, cudaStream_t);                       \
+    template cudaError_t launch_to_panels<R>(const double2*, C_t<R>*, int, int, StateView<R>, int, size_t,       \
+                                             size_t, cudaStream_t);                                              \
+    template cudaError_t launch_slice_costs<R>(int, StateView<R>, int, int, int, int, const C_t<R>*, int,        \
+                                               const CostView<R>&, double2*, double*, double2*, cudaStream_t);   \
+    template cudaError_t launch_sources<R>(int, StateView<R>, int, int, int, int, const C_t<R>*, int,            \
+                                           const CostView<R>&, const double2*, const double2*, C_t<R>*,          \
+                                           cudaStream_t);                                                        \
+
+QOC_INST(float)
+QOC_INST(double)
+
+}  // namespace qoc

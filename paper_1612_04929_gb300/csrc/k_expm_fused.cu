@@ -1,0 +1,372 @@
+// Fused per-slice kernels for small and medium Hilbert dimension d (d <= 64 in FP32, d <= 48 in
+// FP64): one CTA owns one slice (and one ensemble member) and keeps every matrix of that slice
+// in shared memory.
+//
+//  k_expm_fwd : X_j = -i s H_j (s = dt / 2^n; Eq. 1 assembly fused), Horner evaluation of the
+//               order-p Taylor polynomial T_j = I + X(I + X/2(... (I + X/p))) (Eq. 10), then n
+//               squarings U_j = T_j^(2^n) (Eq. 9).  Writes U_j.
+//  k_expm_adj : exact adjoint of that same polynomial map X -> f(X).  For a polynomial f with
+//               real coefficients the adjoint of its Frechet derivative is L_f(X^dag, .), and
+//               L_f(A, E) is the (1,2) block of f([[A, E], [0, A]]).  So Xbar_j is obtained by
+//               running the same Horner + squaring recursion on the block-upper-triangular
+//               matrix [[X^dag, Ubar], [0, X^dag]] with Ubar_j = G_j Psi_{j-1}^dag (G_j the
+//               costate, Appendix A), then dC/du_{k,j} = Re tr(Xbar^dag (-i s H_k)) (Eq. A3).
+//               This differentiates the truncated series exactly (not the first-order Eq. 11)
+//               without storing the p + n intermediate matrices.
+//
+// Thread layout: 256 threads as a 16 x 16 grid; thread (ty, tx) owns the MT x MT outputs
+// (ty + 16 a, tx + 16 b).  Matrices sit in shared memory padded to D = 16 MT rows with a
+// leading dimension of D + 1 complex elements (breaks bank conflicts between the two rows a
+// warp reads); padding rows and columns are kept at zero.
+#include "qoc_device.cuh"
+#include "qoc_internal.h"
+
+namespace qoc {
+
+template <typename C, int MT>
+__device__ __forceinline__ void mm_acc(C (&acc)[MT][MT], const C* __restrict__ A,
+                                       const C* __restrict__ B, int kd, int LD, int ty, int tx) {
+#pragma unroll 2
+    for (int k = 0; k < kd; ++k) {
+        C a[MT], b[MT];
+#pragma unroll
+        for (int i = 0; i < MT; ++i) a[i] = A[(ty + 16 * i) * LD + k];
+#pragma unroll
+        for (int i = 0; i < MT; ++i) b[i] = B[k * LD + tx + 16 * i];
+#pragma unroll
+        for (int i = 0; i < MT; ++i)
+#pragma unroll
+            for (int jj = 0; jj < MT; ++jj) cfma(acc[i][jj], a[i], b[jj]);
+    }
+}
+
+// acc11 += A11 B11 ;  acc12 += A11 B12 + A12 B11   (block-upper-triangular product)
+template <typename C, int MT>
+__device__ __forceinline__ void mm_block(C (&acc11)[MT][MT], C (&acc12)[MT][MT],
+                                         const C* __restrict__ A11, const C* __restrict__ A12,
+                                         const C* __restrict__ B11, const C* __restrict__ B12,
+                                         int kd, int LD, int ty, int tx) {
+#pragma unroll 1
+    for (int k = 0; k < kd; ++k) {
+        C a1[MT], a2[MT], b1[MT], b2[MT];
+#pragma unroll
+        for (int i = 0; i < MT; ++i) {
+            a1[i] = A11[(ty + 16 * i) * LD + k];
+            a2[i] = A12[(ty + 16 * i) * LD + k];
+        }
+#pragma unroll
+        for (int i = 0; i < MT; ++i) {
+            b1[i] = B11[k * LD + tx + 16 * i];
+            b2[i] = B12[k * LD + tx + 16 * i];
+        }
+#pragma unroll
+        for (int i = 0; i < MT; ++i)
+#pragma unroll
+            for (int jj = 0; jj < MT; ++jj) {
+                cfma(acc11[i][jj], a1[i], b1[jj]);
+                cfma(acc12[i][jj], a1[i], b2[jj]);
+                cfma(acc12[i][jj], a2[i], b1[jj]);
+            }
+    }
+}
+
+template <typename C, int MT>
+__device__ __forceinline__ void zero_acc(C (&acc)[MT][MT]) {
+#pragma unroll
+    for (int i = 0; i < MT; ++i)
+#pragma unroll
+        for (int jj = 0; jj < MT; ++jj) acc[i][jj] = czero<C>();
+}
+
+// out = diag * I + scale * acc on the d x d block, zero in the padding.
+template <typename C, typename R, int MT>
+__device__ __forceinline__ void store_acc(C* __restrict__ out, const C (&acc)[MT][MT], R scale,
+                                          R diag, int d, int LD, int ty, int tx) {
+#pragma unroll
+    for (int i = 0; i < MT; ++i)
+#pragma unroll
+        for (int jj = 0; jj < MT; ++jj) {
+            const int r = ty + 16 * i, c = tx + 16 * jj;
+            C v = czero<C>();
+            if (r < d && c < d) {
+                v.x = acc[i][jj].x * scale + (r == c ? diag : R(0));
+                v.y = acc[i][jj].y * scale;
+            }
+            out[r * LD + c] = v;
+        }
+}
+
+// Assemble H_j (+ delta_e Hdet) and write X = -i s H into padded shared memory (rows/cols >= d
+// zero).  us: the M control values of this slice (shared).
+template <typename C, typename R>
+__device__ __forceinline__ void assemble_X(C* __restrict__ X, int d, int D, int LD, int M,
+                                           const C* __restrict__ H0, const C* __restrict__ Hk,
+                                           const C* __restrict__ Hdet, R de, const R* us, R s) {
+    const size_t dd = (size_t)d * d;
+    for (int idx = threadIdx.x; idx < D * D; idx += blockDim.x) {
+        const int a = idx / D, b = idx - a * D;
+        C x = czero<C>();
+        if (a < d && b < d) {
+            const int o = a * d + b;
+            C h = H0[o];
+            for (int k = 0; k < M; ++k) {
+                const C hk = Hk[k * dd + o];
+                h.x = fma(us[k], hk.x, h.x);
+                h.y = fma(us[k], hk.y, h.y);
+            }
+            if (Hdet) {
+                const C hd = Hdet[o];
+                h.x = fma(de, hd.x, h.x);
+                h.y = fma(de, hd.y, h.y);
+            }
+            x.x = s * h.y;      // -i s (hr + i hi) = s hi - i s hr
+            x.y = -s * h.x;
+        }
+        X[a * LD + b] = x;
+    }
+}
+
+template <typename R, int MT>
+__global__ void __launch_bounds__(256)
+k_expm_fwd(const DevParams* __restrict__ prm, SysView<R> sys, int j0, C_t<R>* __restrict__ Ubuf,
+           long long ustride, int wmax) {
+    using C = C_t<R>;
+    constexpr int D = 16 * MT, LD = D + 1, SZ = D * LD;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ R us[kMaxControls];
+    C* X = reinterpret_cast<C*>(smraw);
+    C* Za = X + SZ;
+    C* Zb = Za + SZ;
+    const int jl = blockIdx.x, e = blockIdx.y, j = j0 + jl;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int d = sys.d, p = prm->p, n = prm->n;
+    const R s = (R)prm->s;
+    for (int k = tid; k < sys.M; k += blockDim.x) us[k] = (R)sys.u[(size_t)k * sys.N + j];
+    __syncthreads();
+    const R de = sys.delta ? (R)sys.delta[e] : R(0);
+    assemble_X<C, R>(X, d, D, LD, sys.M, sys.H0, sys.Hk, sys.Hdet, de, us, s);
+    __syncthreads();
+    {   // Z = I + X / p
+        const R ip = R(1) / R(p);
+        for (int idx = tid; idx < D * D; idx += blockDim.x) {
+            const int a = idx / D, b = idx - a * D;
+            C x = X[a * LD + b];
+            C z;
+            z.x = x.x * ip + ((a == b && a < d) ? R(1) : R(0));
+            z.y = x.y * ip;
+            Za[a * LD + b] = z;
+        }
+    }
+    __syncthreads();
+    C* zin = Za;
+    C* zout = Zb;
+    for (int i = p - 1; i >= 1; --i) {          // Horner: Z <- I + X Z / i
+        C acc[MT][MT];
+        zero_acc<C, MT>(acc);
+        mm_acc<C, MT>(acc, X, zin, d, LD, ty, tx);
+        store_acc<C, R, MT>(zout, acc, R(1) / R(i), R(1), d, LD, ty, tx);
+        __syncthreads();
+        C* t = zin; zin = zout; zout = t;
+    }
+    for (int m = 0; m < n; ++m) {               // squaring: Z <- Z Z
+        C acc[MT][MT];
+        zero_acc<C, MT>(acc);
+        mm_acc<C, MT>(acc, zin, zin, d, LD, ty, tx);
+        store_acc<C, R, MT>(zout, acc, R(1), R(0), d, LD, ty, tx);
+        __syncthreads();
+        C* t = zin; zin = zout; zout = t;
+    }
+    C* U = Ubuf + ((size_t)e * wmax + jl) * ustride;
+    for (int idx = tid; idx < d * d; idx += blockDim.x) {
+        const int a = idx / d, b = idx - a * d;
+        U[idx] = zin[a * LD + b];
+    }
+}
+
+template <typename R, int MT>
+__global__ void __launch_bounds__(256)
+k_expm_adj(const DevParams* __restrict__ prm, SysView<R> sys, StateView<R> st, int j0,
+           const C_t<R>* __restrict__ states, const C_t<R>* __restrict__ Gbuf, int wmax,
+           double* __restrict__ gpart) {
+    using C = C_t<R>;
+    constexpr int D = 16 * MT, LD = D + 1, SZ = D * LD;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ R us[kMaxControls];
+    __shared__ double red[32];
+    C* XH = reinterpret_cast<C*>(smraw);
+    C* Ub = XH + SZ;
+    C* Z11a = Ub + SZ;
+    C* Z12a = Z11a + SZ;
+    C* Z11b = Z12a + SZ;
+    C* Z12b = Z11b + SZ;
+    const int jl = blockIdx.x, e = blockIdx.y, j = j0 + jl;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int d = sys.d, p = prm->p, n = prm->n, Sp = st.Spad, cb = st.cb, ps = st.pstride;
+    const R s = (R)prm->s;
+    for (int k = tid; k < sys.M; k += blockDim.x) us[k] = (R)sys.u[(size_t)k * sys.N + j];
+    __syncthreads();
+    const R de = sys.delta ? (R)sys.delta[e] : R(0);
+    // X into Z11a, then XH = X^dag
+    assemble_X<C, R>(Z11a, d, D, LD, sys.M, sys.H0, sys.Hk, sys.Hdet, de, us, s);
+    // stage G_j (Z11b) and Psi_{j-1} (Z12b) as d x Sp row-major from the column-panel layout
+    const size_t slice = st.slice();
+    const C* Gj = Gbuf + ((size_t)e * wmax + jl) * slice;
+    const C* Pj = states + ((size_t)e * (wmax + 1) + jl) * slice;
+    for (int idx = tid; idx < d * Sp; idx += blockDim.x) {
+        const int a = idx / Sp, sc = idx - a * Sp;
+        const size_t off = (size_t)(sc / cb) * ps + (size_t)a * cb + (sc % cb);
+        Z11b[idx] = Gj[off];
+        Z12b[idx] = Pj[off];
+    }
+    __syncthreads();
+    for (int idx = tid; idx < D * D; idx += blockDim.x) {
+        const int a = idx / D, b = idx - a * D;
+        C x = Z11a[b * LD + a];
+        x.y = -x.y;
+        XH[a * LD + b] = x;
+    }
+    {   // Ubar = G Psi^dag
+        C acc[MT][MT];
+        zero_acc<C, MT>(acc);
+        for (int sc = 0; sc < Sp; ++sc) {
+            C g[MT], q[MT];
+#pragma unroll
+            for (int i = 0; i < MT; ++i) {
+                const int r = ty + 16 * i, c = tx + 16 * i;
+                g[i] = (r < d) ? Z11b[r * Sp + sc] : czero<C>();
+                q[i] = (c < d) ? Z12b[c * Sp + sc] : czero<C>();
+            }
+#pragma unroll
+            for (int i = 0; i < MT; ++i)
+#pragma unroll
+                for (int jj = 0; jj < MT; ++jj) cfma_bcj(acc[i][jj], g[i], q[jj]);
+        }
+        store_acc<C, R, MT>(Ub, acc, R(1), R(0), d, LD, ty, tx);
+    }
+    __syncthreads();
+    {   // Horner start: Z11 = I + XH / p, Z12 = Ubar / p
+        const R ip = R(1) / R(p);
+        for (int idx = tid; idx < D * D; idx += blockDim.x) {
+            const int a = idx / D, b = idx - a * D;
+            C x = XH[a * LD + b], u = Ub[a * LD + b];
+            C z1, z2;
+            z1.x = x.x * ip + ((a == b && a < d) ? R(1) : R(0));
+            z1.y = x.y * ip;
+            z2.x = u.x * ip;
+            z2.y = u.y * ip;
+            Z11a[a * LD + b] = z1;
+            Z12a[a * LD + b] = z2;
+        }
+    }
+    __syncthreads();
+    C *z11 = Z11a, *z12 = Z12a, *o11 = Z11b, *o12 = Z12b;
+    for (int i = p - 1; i >= 1; --i) {
+        C a11[MT][MT], a12[MT][MT];
+        zero_acc<C, MT>(a11);
+        zero_acc<C, MT>(a12);
+        mm_block<C, MT>(a11, a12, XH, Ub, z11, z12, d, LD, ty, tx);
+        const R ri = R(1) / R(i);
+        store_acc<C, R, MT>(o11, a11, ri, R(1), d, LD, ty, tx);
+        store_acc<C, R, MT>(o12, a12, ri, R(0), d, LD, ty, tx);
+        __syncthreads();
+        C* t = z11; z11 = o11; o11 = t;
+        t = z12; z12 = o12; o12 = t;
+    }
+    for (int m = 0; m < n; ++m) {
+        C a11[MT][MT], a12[MT][MT];
+        zero_acc<C, MT>(a11);
+        zero_acc<C, MT>(a12);
+        mm_block<C, MT>(a11, a12, z11, z12, z11, z12, d, LD, ty, tx);
+        store_acc<C, R, MT>(o11, a11, R(1), R(0), d, LD, ty, tx);
+        store_acc<C, R, MT>(o12, a12, R(1), R(0), d, LD, ty, tx);
+        __syncthreads();
+        C* t = z11; z11 = o11; o11 = t;
+        t = z12; z12 = o12; o12 = t;
+    }
+    // dC/du_{k,j} = Re tr(Xbar^dag (-i s H_k)) = s sum_ab (Xbar_re Hk_im - Xbar_im Hk_re)
+    const size_t dd = (size_t)d * d;
+    for (int k = 0; k < sys.M; ++k) {
+        double v = 0.0;
+        for (int idx = tid; idx < d * d; idx += blockDim.x) {
+            const int a = idx / d, b = idx - a * d;
+            const C xb = z12[a * LD + b];
+            const C hk = sys.Hk[k * dd + idx];
+            v += (double)xb.x * (double)hk.y - (double)xb.y * (double)hk.x;
+        }
+        v = block_sum(v, red);
+        if (tid == 0) gpart[((size_t)e * sys.M + k) * sys.N + j] = prm->s * v;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// launchers
+// ------------------------------------------------------------------------------------------
+template <typename R>
+static size_t fused_smem(int MT, int nmat) {
+    const int D = 16 * MT;
+    return (size_t)nmat * D * (D + 1) * sizeof(C_t<R>);
+}
+
+template <typename R>
+int fused_max_d() {
+    for (int MT = 5; MT >= 1; --MT)
+        if (fused_smem<R>(MT, 6) <= kMaxDynSmem) return 16 * MT;
+    return 0;
+}
+
+template <typename R, int MT>
+static cudaError_t launch_fwd_mt(const DevParams* prm, const SysView<R>& sys, int j0, int wlen, int E,
+                                 C_t<R>* Ubuf, long long ustride, int wmax, cudaStream_t st) {
+    const size_t smem = fused_smem<R>(MT, 3);
+    cudaError_t err = cudaFuncSetAttribute(k_expm_fwd<R, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    k_expm_fwd<R, MT><<<dim3(wlen, E), 256, smem, st>>>(prm, sys, j0, Ubuf, ustride, wmax);
+    return cudaGetLastError();
+}
+
+template <typename R, int MT>
+static cudaError_t launch_adj_mt(const DevParams* prm, const SysView<R>& sys, const StateView<R>& sv, int j0,
+                                 int wlen, int E, const C_t<R>* states, const C_t<R>* Gbuf, int wmax,
+                                 double* gpart, cudaStream_t st) {
+    const size_t smem = fused_smem<R>(MT, 6);
+    cudaError_t err = cudaFuncSetAttribute(k_expm_adj<R, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    k_expm_adj<R, MT><<<dim3(wlen, E), 256, smem, st>>>(prm, sys, sv, j0, states, Gbuf, wmax, gpart);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_expm_fwd_fused(const DevParams* prm, const SysView<R>& sys, int j0, int wlen, int E,
+                                  C_t<R>* Ubuf, long long ustride, int wmax, cudaStream_t st) {
+    const int MT = (sys.d + 15) / 16;
+    switch (MT) {
+        case 1: return launch_fwd_mt<R, 1>(prm, sys, j0, wlen, E, Ubuf, ustride, wmax, st);
+        case 2: return launch_fwd_mt<R, 2>(prm, sys, j0, wlen, E, Ubuf, ustride, wmax, st);
+        case 3: return launch_fwd_mt<R, 3>(prm, sys, j0, wlen, E, Ubuf, ustride, wmax, st);
+        case 4: if (sizeof(R) == 4) return launch_fwd_mt<R, 4>(prm, sys, j0, wlen, E, Ubuf, ustride, wmax, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename R>
+cudaError_t launch_expm_adj_fused(const DevParams* prm, const SysView<R>& sys, const StateView<R>& sv, int j0,
+                                  int wlen, int E, const C_t<R>* states, const C_t<R>* Gbuf, int wmax,
+                                  double* gpart, cudaStream_t st) {
+    const int MT = (sys.d + 15) / 16;
+    switch (MT) {
+        case 1: return launch_adj_mt<R, 1>(prm, sys, sv, j0, wlen, E, states, Gbuf, wmax, gpart, st);
+        case 2: return launch_adj_mt<R, 2>(prm, sys, sv, j0, wlen, E, states, Gbuf, wmax, gpart, st);
+        case 3: return launch_adj_mt<R, 3>(prm, sys, sv, j0, wlen, E, states, Gbuf, wmax, gpart, st);
+        case 4: if (sizeof(R) == 4) return launch_adj_mt<R, 4>(prm, sys, sv, j0, wlen, E, states, Gbuf, wmax, gpart, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template int fused_max_d<float>();
+template int fused_max_d<double>();
+template cudaError_t launch_expm_fwd_fused<float>(const DevParams*, const SysView<float>&, int, int, int, float2*, long long, int, cudaStream_t);
+template cudaError_t launch_expm_fwd_fused<double>(const DevParams*, const SysView<double>&, int, int, int, double2*, long long, int, cudaStream_t);
+template cudaError_t launch_expm_adj_fused<float>(const DevParams*, const SysView<float>&, const StateView<float>&, int, int, int, const float2*, const float2*, int, double*, cudaStream_t);
+template cudaError_t launch_expm_adj_fused<double>(const DevParams*, const SysView<double>&, const StateView<double>&, int, int, int, const double2*, const double2*, int, double*, cudaStream_t);
+
+}  // namespace qoc

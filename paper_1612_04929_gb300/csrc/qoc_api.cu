@@ -1,0 +1,721 @@
+// C ABI of the quantum-control cost + gradient evaluation (declared in include/qoc.h).
+//
+// One evaluation runs, on the context stream:
+//   k_theta                      FP64 norm bound -> one global (p, n)               (Sec. III)
+//   per wave w = 0 .. nw-1 (forward; a wave is a multiple of the checkpoint stride):
+//     expm_fwd (all slices of w) U_j = [Taylor_p(-i s H_j)]^(2^n)                 (Eqs. 1, 9, 10)
+//     chain_fwd                  Psi_j = U_j Psi_{j-1}; checkpoint every stride     (Eqs. 2, 4)
+//     slice_costs                O_j, forbidden occupation per slice                (Table I)
+//   per wave w = nw-1 .. 0 (backward):
+//     [expm_fwd + chain replay]  recompute U_j, regenerate Psi_j from the checkpoints, one
+//                                segment per CTA (skipped for the wave still resident from the
+//                                forward sweep)
+//     sources                    dC/dPsi_j of every cost term                       (App. A)
+//     costate                    G_{j-1} = U_j^dag G_j + src_{j-1}                  (Alg. 1-3)
+//     expm_adj                   exact adjoint of the truncated series, dC/du_{k,j}  (Eq. A3)
+//   finalize                     FP64 costs, C3/C4 gradients, ensemble sum          (Table I)
+// Only the checkpoints (one d x S block per stride c) and one wave (W slices) of propagators,
+// states and costates live at a time: device memory is O(N/c d S + W d^2), independent of N
+// apart from the checkpoints.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/qoc.h"
+#include "qoc_internal.h"
+
+using namespace qoc;
+
+namespace {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    cudaError_t alloc(size_t n) {
+        release();
+        if (n == 0) return cudaSuccess;
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return e;
+        }
+        bytes = n;
+        return cudaSuccess;
+    }
+    template <typename T> T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+struct Fail {
+    qoc_status st;
+};
+
+// CUDA-event brackets around kernel launches, harvested when the stream is synchronised.
+struct Profiler {
+    struct Pending { int cls; cudaEvent_t a, b; };
+    std::vector<std::string> names;
+    std::vector<long long> launches;
+    std::vector<double> ms;
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> pool;
+    cudaEvent_t get() {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    int cls(const char* name) {
+        for (size_t i = 0; i < names.size(); ++i)
+            if (names[i] == name) return (int)i;
+        names.push_back(name);
+        launches.push_back(0);
+        ms.push_back(0.0);
+        return (int)names.size() - 1;
+    }
+    void harvest() {   // stream already synchronised
+        for (auto& p : pending) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) {
+                launches[p.cls] += 1;
+                ms[p.cls] += t;
+            }
+            pool.push_back(p.a);
+            pool.push_back(p.b);
+        }
+        pending.clear();
+    }
+    void reset() {
+        for (auto& v : launches) v = 0;
+        for (auto& v : ms) v = 0.0;
+    }
+    ~Profiler() {
+        for (auto& p : pending) { pool.push_back(p.a); pool.push_back(p.b); }
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
+}  // namespace
+
+struct qoc_ctx {
+    qoc_options opt{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+
+    // problem (host FP64 copies; the device copies are made by the planner)
+    bool has_sys = false, has_tgt = false;
+    int d = 0, M = 0, N = 0, S = 0, nF = 0, E = 1;
+    double dt = 0.0;
+    std::vector<double> H0, Hk, Hdet, delta, psi0, psiT, path, w;
+    std::vector<int> forb;
+    double alpha[5] = {0, 0, 0, 0, 0};
+    double Wsum = 0.0;
+
+    // plan
+    bool planned = false;
+    int W = 0, nw = 0, seg = 0, nseg_total = 0, path_kind = 0;
+    int Spad = 0, cb = 0, ncb = 0, pstride = 0;
+    long long ustride = 0;
+    int launches = 0;
+
+    Profiler prof;
+
+    DevBuf H64, HR, dDelta, norms, psiTR, pathR, fmask, colw, ckpt, Ubuf, states, Gbuf, src, carry, Oj, C5j, Ofin,
+        gpart, prm, u_h, grad_h, out_h;
+
+    size_t device_bytes() const {
+        const DevBuf* all[] = {&H64, &HR, &dDelta, &norms, &psiTR, &pathR, &fmask, &colw, &ckpt, &Ubuf, &states,
+                               &Gbuf, &src, &carry, &Oj, &C5j, &Ofin, &gpart, &prm, &u_h, &grad_h, &out_h};
+        size_t s = 0;
+        for (auto* b : all) s += b->bytes;
+        return s;
+    }
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+qoc_status set_err(qoc_ctx* c, qoc_status st, const std::string& msg) {
+    if (c) c->err = msg;
+    return st;
+}
+
+void check_cuda(qoc_ctx* c, cudaError_t e, const char* what) {
+    if (e != cudaSuccess) {
+        c->err = std::string(what) + ": " + cudaGetErrorString(e);
+        throw Fail{e == cudaErrorMemoryAllocation ? QOC_ERR_OOM : QOC_ERR_CUDA};
+    }
+}
+
+bool all_finite(const double* x, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(x[i])) return false;
+    return true;
+}
+
+// max |H_ab - conj(H_ba)| <= 1e-12 * max(1, max |H|)
+bool hermitian(const double* H, int d) {
+    double mx = 0.0, dev = 0.0;
+    for (int a = 0; a < d; ++a)
+        for (int b = 0; b < d; ++b) {
+            const double* x = H + 2 * ((size_t)a * d + b);
+            const double* y = H + 2 * ((size_t)b * d + a);
+            mx = std::max(mx, std::hypot(x[0], x[1]));
+            dev = std::max(dev, std::hypot(x[0] - y[0], x[1] + y[1]));
+        }
+    return dev <= 1e-12 * std::max(1.0, mx);
+}
+
+bool is_fp64(const qoc_ctx* c) { return c->opt.precision == QOC_PREC_FP64; }
+
+template <typename R>
+bool split_exp(const qoc_ctx* c) {
+    return sizeof(R) == 4 && c->opt.plain_fp32_exp == 0;
+}
+
+template <typename R>
+void plan_impl(qoc_ctx* c) {
+    using C = C_t<R>;
+    const int d = c->d, S = c->S, N = c->N, E = c->E, M = c->M;
+    const size_t cs = sizeof(C);
+    const int dmax = split_exp<R>(c) ? std::min(fused_max_d<R>(), split_max_d()) : fused_max_d<R>();
+    c->path_kind = (d <= dmax) ? 0 : 1;
+    if (c->path_kind != 0) {
+        c->err = "d = " + std::to_string(d) + " exceeds the fused per-slice kernels of this precision";
+        throw Fail{QOC_ERR_UNSUPPORTED};
+    }
+    c->cb = std::min(S, 8);
+    c->ncb = (S + c->cb - 1) / c->cb;
+    c->Spad = c->ncb * c->cb;
+    const int align_elems = (int)(16 / cs) > 0 ? (int)(16 / cs) : 1;
+    c->pstride = ((d * c->cb + align_elems - 1) / align_elems) * align_elems;
+    const size_t slice = (size_t)c->ncb * c->pstride;
+    // checkpoint stride (sqrt N by default) and wave: the slices of one parallel launch, a
+    // multiple of the stride large enough to fill the GPU (independent of N)
+    int seg = c->opt.ckpt_stride > 0 ? c->opt.ckpt_stride : (int)std::ceil(std::sqrt((double)N));
+    seg = std::max(1, std::min(seg, N));
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->opt.device);
+    int want = c->opt.wave_slices > 0 ? c->opt.wave_slices : std::max(seg, 2 * std::max(sms, 1));
+    int W = ((want + seg - 1) / seg) * seg;
+    W = std::min(W, ((N + seg - 1) / seg) * seg);
+    c->seg = seg;
+    c->W = W;
+    c->nw = (N + W - 1) / W;
+    c->nseg_total = (N + seg - 1) / seg;
+    const long long ue = 256 / (long long)cs;
+    c->ustride = (((long long)d * d + ue - 1) / ue) * ue;
+    const int nseg_total = c->nseg_total;
+
+    StateView<R> sv{c->Spad, c->cb, c->ncb, c->pstride};
+    cudaStream_t st = c->stream;
+    auto A = [&](DevBuf& b, size_t bytes, const char* what) { check_cuda(c, b.alloc(bytes), what); };
+
+    // system in the compute precision (H0, Hk, Hdet consecutive)
+    const size_t dd = (size_t)d * d;
+    A(c->HR, (M + 2) * dd * cs, "alloc H");
+    check_cuda(c, launch_convert<R>(c->H64.as<double2>(), c->HR.as<C>(), (M + 2) * dd, st), "convert H");
+    // costs
+    std::vector<int> mask(d, 0);
+    for (int f : c->forb) mask[f] = 1;
+    A(c->fmask, d * sizeof(int), "alloc mask");
+    check_cuda(c, cudaMemcpyAsync(c->fmask.p, mask.data(), d * sizeof(int), cudaMemcpyHostToDevice, st), "copy mask");
+    std::vector<double> wpad(c->Spad, 0.0);
+    for (int s = 0; s < S; ++s) wpad[s] = c->w[s];
+    A(c->colw, c->Spad * sizeof(double), "alloc weights");
+    check_cuda(c, cudaMemcpyAsync(c->colw.p, wpad.data(), c->Spad * sizeof(double), cudaMemcpyHostToDevice, st),
+               "copy weights");
+    // targets and the initial block (checkpoint 0 of every member) through an FP64 staging buffer
+    DevBuf stage;
+    const size_t blk = (size_t)d * S * 2 * sizeof(double);
+    A(stage, std::max(blk, c->path.empty() ? blk : (size_t)N * blk), "alloc staging");
+    A(c->psiTR, slice * cs, "alloc target");
+    check_cuda(c, cudaMemcpyAsync(stage.p, c->psiT.data(), blk, cudaMemcpyHostToDevice, st), "copy target");
+    check_cuda(c, launch_to_panels<R>(stage.as<double2>(), c->psiTR.as<C>(), d, S, sv, 1, 0, 0, st), "target panels");
+    A(c->ckpt, (size_t)E * nseg_total * slice * sizeof(K_t<R>), "alloc checkpoints");
+    check_cuda(c, cudaStreamSynchronize(st), "sync");
+    check_cuda(c, cudaMemcpyAsync(stage.p, c->psi0.data(), blk, cudaMemcpyHostToDevice, st), "copy psi0");
+    check_cuda(c, launch_to_carry<R>(stage.as<double2>(), c->ckpt.as<K_t<R>>(), d, S, sv, E,
+                                     (size_t)nseg_total * slice, st),
+               "psi0 panels");
+    if (!c->path.empty()) {
+        check_cuda(c, cudaStreamSynchronize(st), "sync");
+        A(c->pathR, (size_t)N * slice * cs, "alloc path");
+        check_cuda(c, cudaMemcpyAsync(stage.p, c->path.data(), (size_t)N * blk, cudaMemcpyHostToDevice, st),
+                   "copy path");
+        check_cuda(c, launch_to_panels<R>(stage.as<double2>(), c->pathR.as<C>(), d, S, sv, N, slice, (size_t)d * S, st),
+                   "path panels");
+    } else {
+        c->pathR.release();
+    }
+    // per-segment work buffers
+    A(c->Ubuf, (size_t)E * W * c->ustride * cs, "alloc U");
+    A(c->states, (size_t)E * (W + 1) * slice * cs, "alloc states");
+    A(c->Gbuf, (size_t)E * W * slice * cs, "alloc costates");
+    A(c->src, (size_t)E * W * slice * cs, "alloc sources");
+    A(c->carry, (size_t)E * slice * sizeof(K_t<R>), "alloc carry");
+    A(c->Oj, (size_t)E * N * sizeof(double2), "alloc O");
+    A(c->C5j, (size_t)E * N * sizeof(double), "alloc C5");
+    A(c->Ofin, (size_t)E * sizeof(double2), "alloc Ofin");
+    A(c->gpart, (size_t)E * M * N * sizeof(double) + 8, "alloc gpart");
+    A(c->prm, sizeof(DevParams), "alloc params");
+    check_cuda(c, cudaMemsetAsync(c->prm.p, 0, sizeof(DevParams), st), "memset params");
+    A(c->u_h, (size_t)M * N * sizeof(double) + 8, "alloc u");
+    A(c->grad_h, (size_t)M * N * sizeof(double) + 8, "alloc grad");
+    A(c->out_h, 8 * sizeof(double), "alloc out");
+    check_cuda(c, cudaStreamSynchronize(st), "plan sync");
+    c->planned = true;
+}
+
+template <typename R>
+void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out) {
+    using C = C_t<R>;
+    const int d = c->d, N = c->N, E = c->E, M = c->M, W = c->W, nw = c->nw;
+    cudaStream_t st = c->stream;
+    StateView<R> sv{c->Spad, c->cb, c->ncb, c->pstride};
+    const size_t slice = sv.slice();
+    const size_t dd = (size_t)d * d;
+    C* HR = c->HR.as<C>();
+    SysView<R> sys{d, M, N, HR, HR + dd, c->Hdet.empty() ? nullptr : HR + (size_t)(M + 1) * dd,
+                   c->delta.empty() ? nullptr : c->dDelta.as<double>(), u};
+    CostView<R> cv{c->nF, c->fmask.as<int>(), c->colw.as<double>(), c->Wsum, c->psiTR.as<C>(),
+                   c->path.empty() ? nullptr : c->pathR.as<C>(), {c->alpha[0], c->alpha[1], c->alpha[2], c->alpha[3], c->alpha[4]}};
+    DevParams* prm = c->prm.as<DevParams>();
+    C* Ub = c->Ubuf.as<C>();
+    C* states = c->states.as<C>();
+    const int seg = c->seg;
+    ChainArgs<R> ch{d, sv, 0, seg, 0, E, c->ckpt.as<K_t<R>>(), (size_t)c->nseg_total * slice, 0, c->nseg_total,
+                    Ub, c->ustride, W, states};
+    int launches = 0;
+    const bool prof = c->opt.profile != 0;
+    cudaEvent_t ev0 = nullptr;
+    // B(name) opens an event bracket before a launch, L(...) closes it after the launch
+    auto B = [&](const char*) {
+        if (prof) {
+            ev0 = c->prof.get();
+            cudaEventRecord(ev0, st);
+        }
+    };
+    auto L = [&](cudaError_t e, const char* what) {
+        ++launches;
+        check_cuda(c, e, what);
+        if (prof) {
+            cudaEvent_t ev1 = c->prof.get();
+            cudaEventRecord(ev1, st);
+            c->prof.pending.push_back({c->prof.cls(what), ev0, ev1});
+        }
+    };
+    B(nullptr);
+    L(launch_theta(u, M, N, c->norms.as<double>(), c->delta.empty() ? nullptr : c->dDelta.as<double>(), E, c->dt,
+                   c->opt.theta_max, c->opt.tol, c->opt.p_override, c->opt.n_override, prm, st),
+      "theta");
+    // slice exponentials: split hi+lo FP32 for the FP32 form (unless disabled), else plain
+    const bool split = split_exp<R>(c);
+    auto expm_fwd = [&](int j0, int wlen) -> cudaError_t {
+        if constexpr (sizeof(R) == 4) {
+            if (split)
+                return launch_expm_fwd_split(prm, sys, c->H64.as<double2>(), j0, wlen, E, Ub, c->ustride, W, st);
+        }
+        return launch_expm_fwd_fused<R>(prm, sys, j0, wlen, E, Ub, c->ustride, W, st);
+    };
+    for (int w = 0; w < nw; ++w) {
+        const int j0 = w * W, wlen = std::min(W, N - j0);
+        B(nullptr);
+        L(expm_fwd(j0, wlen), "expm_fwd");
+        ch.wlen = wlen;
+        ch.seg0 = j0 / seg;
+        ch.mode = 0;
+        B(nullptr);
+        L(launch_chain<R>(ch, st), "chain_fwd");
+        B(nullptr);
+        L(launch_slice_costs<R>(d, sv, j0, wlen, N, E, states, W, cv, c->Oj.as<double2>(), c->C5j.as<double>(),
+                                c->Ofin.as<double2>(), st),
+          "slice_costs");
+    }
+    check_cuda(c, cudaMemsetAsync(c->carry.p, 0, c->carry.bytes, st), "memset carry");
+    for (int w = nw - 1; w >= 0; --w) {
+        const int j0 = w * W, wlen = std::min(W, N - j0);
+        if (w != nw - 1) {   // the last wave is still resident from the forward sweep
+            B(nullptr);
+            L(expm_fwd(j0, wlen), "expm_fwd (recompute)");
+            ch.wlen = wlen;
+            ch.seg0 = j0 / seg;
+            ch.mode = 1;
+            B(nullptr);
+            L(launch_chain<R>(ch, st), "chain (replay)");
+        }
+        B(nullptr);
+        L(launch_sources<R>(d, sv, j0, wlen, N, E, states, W, cv, c->Oj.as<double2>(), c->Ofin.as<double2>(),
+                            c->src.as<C>(), st),
+          "sources");
+        B(nullptr);
+        L(launch_costate<R>(d, sv, wlen, E, Ub, c->ustride, W, c->src.as<C>(), c->carry.as<K_t<R>>(),
+                            c->Gbuf.as<C>(), st),
+          "costate");
+        B(nullptr);
+        L(launch_expm_adj_fused<R>(prm, sys, sv, j0, wlen, E, states, c->Gbuf.as<C>(), W, c->gpart.as<double>(), st),
+          "expm_adj");
+    }
+    B(nullptr);
+    L(launch_finalize(E, M, N, u, c->alpha, c->Oj.as<double2>(), c->C5j.as<double>(), c->Ofin.as<double2>(),
+                      c->gpart.as<double>(), grad, out, st),
+      "finalize");
+    c->launches = launches;
+}
+
+void plan(qoc_ctx* c) {
+    if (is_fp64(c)) plan_impl<double>(c);
+    else plan_impl<float>(c);
+}
+
+void evaluate(qoc_ctx* c, const double* u, double* grad, double* out) {
+    if (!c->planned) plan(c);
+    if (is_fp64(c)) evaluate_impl<double>(c, u, grad, out);
+    else evaluate_impl<float>(c, u, grad, out);
+}
+
+qoc_status device_error(qoc_ctx* c) {
+    DevParams h{};
+    check_cuda(c, cudaMemcpyAsync(&h, c->prm.p, sizeof(DevParams), cudaMemcpyDeviceToHost, c->stream), "read params");
+    check_cuda(c, cudaStreamSynchronize(c->stream), "sync");
+    c->prof.harvest();
+    if (h.err & kErrTimeout) return set_err(c, QOC_ERR_TIMEOUT, "a bounded device wait ran out");
+    if (h.err & kErrRange)
+        return set_err(c, QOC_ERR_RANGE, "Taylor order above its maximum for theta = " + std::to_string(h.theta));
+    return QOC_OK;
+}
+
+#define QOC_GUARD_BEGIN try {
+#define QOC_GUARD_END                                               \
+    }                                                               \
+    catch (const Fail& f) { return f.st; }                          \
+    catch (const std::bad_alloc&) { return set_err(ctx, QOC_ERR_OOM, "host allocation failed"); } \
+    catch (...) { return set_err(ctx, QOC_ERR_CUDA, "unexpected exception"); }
+
+}  // namespace
+
+extern "C" {
+
+void qoc_default_options(qoc_options* opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->precision = QOC_PREC_FP64;
+    opt->tol = 0.0;
+    opt->theta_max = 0.0;
+    opt->ckpt_stride = 0;
+    opt->device = 0;
+    opt->stream = nullptr;
+    opt->p_override = 0;
+    opt->n_override = -1;
+    opt->wave_slices = 0;
+}
+
+const char* qoc_status_string(qoc_status s) {
+    switch (s) {
+        case QOC_OK: return "QOC_OK";
+        case QOC_ERR_ARG: return "QOC_ERR_ARG";
+        case QOC_ERR_SHAPE: return "QOC_ERR_SHAPE";
+        case QOC_ERR_NOT_HERMITIAN: return "QOC_ERR_NOT_HERMITIAN";
+        case QOC_ERR_NONFINITE: return "QOC_ERR_NONFINITE";
+        case QOC_ERR_STATE: return "QOC_ERR_STATE";
+        case QOC_ERR_OOM: return "QOC_ERR_OOM";
+        case QOC_ERR_CUDA: return "QOC_ERR_CUDA";
+        case QOC_ERR_TIMEOUT: return "QOC_ERR_TIMEOUT";
+        case QOC_ERR_UNSUPPORTED: return "QOC_ERR_UNSUPPORTED";
+        case QOC_ERR_RANGE: return "QOC_ERR_RANGE";
+    }
+    return "QOC_ERR_UNKNOWN";
+}
+
+qoc_status qoc_create(qoc_ctx** out, const qoc_options* opt) {
+    if (!out) return QOC_ERR_ARG;
+    *out = nullptr;
+    qoc_options o;
+    qoc_default_options(&o);
+    if (opt) o = *opt;
+    if (o.precision < QOC_PREC_FP64 || o.precision > QOC_PREC_BF16_SPLIT) return QOC_ERR_ARG;
+    if (!(o.tol >= 0.0) || !(o.theta_max >= 0.0) || o.ckpt_stride < 0 || o.wave_slices < 0) return QOC_ERR_ARG;
+    const bool f64 = o.precision == QOC_PREC_FP64;
+    if (o.tol == 0.0) o.tol = f64 ? 1e-15 : 1e-8;
+    if (o.theta_max == 0.0) o.theta_max = f64 ? 0.25 : 1.0;
+    qoc_ctx* ctx = new (std::nothrow) qoc_ctx;
+    if (!ctx) return QOC_ERR_OOM;
+    ctx->opt = o;
+    cudaError_t e = cudaSetDevice(o.device);
+    if (e == cudaSuccess) {
+        if (o.stream) {
+            ctx->stream = reinterpret_cast<cudaStream_t>(o.stream);
+        } else {
+            e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+            ctx->own_stream = (e == cudaSuccess);
+        }
+    }
+    if (e != cudaSuccess) {
+        delete ctx;
+        return QOC_ERR_CUDA;
+    }
+    *out = ctx;
+    return QOC_OK;
+}
+
+void qoc_destroy(qoc_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->opt.device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+const char* qoc_last_error(const qoc_ctx* ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
+
+qoc_status qoc_set_system(qoc_ctx* ctx, int d, int M, const double* H0, const double* Hk, double dt, int N) {
+    if (!ctx) return QOC_ERR_ARG;
+    ctx->err.clear();
+    if (!H0 || (M > 0 && !Hk)) return set_err(ctx, QOC_ERR_ARG, "H0 or Hk is NULL");
+    if (d < 1 || d > kMaxD) return set_err(ctx, QOC_ERR_SHAPE, "d must be in [1, 512]");
+    if (M < 0 || M > kMaxControls) return set_err(ctx, QOC_ERR_SHAPE, "M must be in [0, 64]");
+    if (N < 1) return set_err(ctx, QOC_ERR_SHAPE, "N must be >= 1");
+    if (!std::isfinite(dt) || dt <= 0.0) return set_err(ctx, QOC_ERR_ARG, "dt must be finite and > 0");
+    const size_t dd2 = (size_t)d * d * 2;
+    if (!all_finite(H0, dd2) || (M > 0 && !all_finite(Hk, M * dd2)))
+        return set_err(ctx, QOC_ERR_NONFINITE, "non-finite entry in H0 or Hk");
+    if (!hermitian(H0, d)) return set_err(ctx, QOC_ERR_NOT_HERMITIAN, "H0 is not Hermitian");
+    for (int k = 0; k < M; ++k)
+        if (!hermitian(Hk + k * dd2, d))
+            return set_err(ctx, QOC_ERR_NOT_HERMITIAN, "H_" + std::to_string(k + 1) + " is not Hermitian");
+    QOC_GUARD_BEGIN
+    check_cuda(ctx, cudaSetDevice(ctx->opt.device), "set device");
+    ctx->planned = false;
+    ctx->has_sys = ctx->has_tgt = false;
+    ctx->d = d;
+    ctx->M = M;
+    ctx->N = N;
+    ctx->dt = dt;
+    ctx->H0.assign(H0, H0 + dd2);
+    ctx->Hk.assign(Hk ? Hk : H0, Hk ? Hk + M * dd2 : H0);
+    ctx->Hdet.clear();
+    ctx->delta.clear();
+    ctx->E = 1;
+    // FP64 device copy [H0, H1..HM, Hdet] and the FP64 1-norms used by the (p, n) pick
+    check_cuda(ctx, ctx->H64.alloc((M + 2) * dd2 * sizeof(double)), "alloc H64");
+    check_cuda(ctx, cudaMemsetAsync(ctx->H64.p, 0, ctx->H64.bytes, ctx->stream), "memset H64");
+    check_cuda(ctx, cudaMemcpyAsync(ctx->H64.p, H0, dd2 * sizeof(double), cudaMemcpyHostToDevice, ctx->stream),
+               "copy H0");
+    if (M > 0)
+        check_cuda(ctx, cudaMemcpyAsync(ctx->H64.as<double>() + dd2, Hk, M * dd2 * sizeof(double),
+                                        cudaMemcpyHostToDevice, ctx->stream),
+                   "copy Hk");
+    check_cuda(ctx, ctx->norms.alloc((M + 2) * sizeof(double)), "alloc norms");
+    check_cuda(ctx, launch_norms(ctx->H64.as<double2>(), M + 2, d, ctx->norms.as<double>(), ctx->stream), "norms");
+    check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "sync");
+    ctx->has_sys = true;
+    return QOC_OK;
+    QOC_GUARD_END
+}
+
+qoc_status qoc_set_targets(qoc_ctx* ctx, int S, const double* psi0, const double* psiT, int nF, const int* forbidden,
+                           const double* col_weight, const double* psiT_path, const double* alpha) {
+    if (!ctx) return QOC_ERR_ARG;
+    ctx->err.clear();
+    if (!ctx->has_sys) return set_err(ctx, QOC_ERR_STATE, "qoc_set_system must come first");
+    const int d = ctx->d, N = ctx->N;
+    if (!psi0 || !psiT || !alpha || (nF > 0 && !forbidden)) return set_err(ctx, QOC_ERR_ARG, "NULL argument");
+    if (S < 1 || S > d) return set_err(ctx, QOC_ERR_SHAPE, "S must be in [1, d]");
+    if (nF < 0 || nF > d) return set_err(ctx, QOC_ERR_SHAPE, "nF must be in [0, d]");
+    for (int i = 0; i < nF; ++i)
+        if (forbidden[i] < 0 || forbidden[i] >= d) return set_err(ctx, QOC_ERR_SHAPE, "forbidden index out of range");
+    const size_t blk = (size_t)d * S * 2;
+    if (!all_finite(psi0, blk) || !all_finite(psiT, blk) || !all_finite(alpha, 5) ||
+        (psiT_path && !all_finite(psiT_path, (size_t)N * blk)))
+        return set_err(ctx, QOC_ERR_NONFINITE, "non-finite target, initial state or weight");
+    double wsum = 0.0;
+    std::vector<double> w(S, 1.0);
+    if (col_weight) {
+        for (int s = 0; s < S; ++s) {
+            if (!std::isfinite(col_weight[s]) || col_weight[s] < 0.0)
+                return set_err(ctx, QOC_ERR_ARG, "column weights must be finite and >= 0");
+            w[s] = col_weight[s];
+        }
+    }
+    for (double x : w) wsum += x;
+    if (!(wsum > 0.0)) return set_err(ctx, QOC_ERR_ARG, "column weights must have a positive sum");
+    ctx->planned = false;
+    ctx->S = S;
+    ctx->nF = nF;
+    ctx->psi0.assign(psi0, psi0 + blk);
+    ctx->psiT.assign(psiT, psiT + blk);
+    if (psiT_path) ctx->path.assign(psiT_path, psiT_path + (size_t)N * blk);
+    else ctx->path.clear();
+    ctx->forb.assign(forbidden ? forbidden : nullptr, forbidden ? forbidden + nF : nullptr);
+    ctx->w = w;
+    ctx->Wsum = wsum;
+    for (int i = 0; i < 5; ++i) ctx->alpha[i] = alpha[i];
+    ctx->has_tgt = true;
+    return QOC_OK;
+}
+
+qoc_status qoc_set_ensemble(qoc_ctx* ctx, int E, const double* delta, const double* Hdet) {
+    if (!ctx) return QOC_ERR_ARG;
+    ctx->err.clear();
+    if (!ctx->has_sys) return set_err(ctx, QOC_ERR_STATE, "qoc_set_system must come first");
+    if (E < 1 || E > 65535) return set_err(ctx, QOC_ERR_SHAPE, "E must be in [1, 65535]");
+    if (!delta) return set_err(ctx, QOC_ERR_ARG, "delta is NULL");
+    if (!all_finite(delta, E)) return set_err(ctx, QOC_ERR_NONFINITE, "non-finite detuning");
+    bool nonzero = false;
+    for (int e = 0; e < E; ++e) nonzero |= (delta[e] != 0.0);
+    const int d = ctx->d, M = ctx->M;
+    const size_t dd2 = (size_t)d * d * 2;
+    if (nonzero && !Hdet) return set_err(ctx, QOC_ERR_ARG, "Hdet is NULL while a detuning is non-zero");
+    if (Hdet) {
+        if (!all_finite(Hdet, dd2)) return set_err(ctx, QOC_ERR_NONFINITE, "non-finite entry in Hdet");
+        if (!hermitian(Hdet, d)) return set_err(ctx, QOC_ERR_NOT_HERMITIAN, "Hdet is not Hermitian");
+    }
+    QOC_GUARD_BEGIN
+    ctx->planned = false;
+    ctx->E = E;
+    ctx->delta.assign(delta, delta + E);
+    if (Hdet) ctx->Hdet.assign(Hdet, Hdet + dd2);
+    else ctx->Hdet.clear();
+    check_cuda(ctx, ctx->dDelta.alloc(E * sizeof(double)), "alloc delta");
+    check_cuda(ctx, cudaMemcpyAsync(ctx->dDelta.p, delta, E * sizeof(double), cudaMemcpyHostToDevice, ctx->stream),
+               "copy delta");
+    double* slot = ctx->H64.as<double>() + (size_t)(M + 1) * dd2;
+    if (Hdet) {
+        check_cuda(ctx, cudaMemcpyAsync(slot, Hdet, dd2 * sizeof(double), cudaMemcpyHostToDevice, ctx->stream),
+                   "copy Hdet");
+    } else {
+        check_cuda(ctx, cudaMemsetAsync(slot, 0, dd2 * sizeof(double), ctx->stream), "clear Hdet");
+    }
+    check_cuda(ctx, launch_norms(ctx->H64.as<double2>() + (size_t)(M + 1) * d * d, 1, d,
+                                 ctx->norms.as<double>() + M + 1, ctx->stream),
+               "Hdet norm");
+    check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "sync");
+    return QOC_OK;
+    QOC_GUARD_END
+}
+
+qoc_status qoc_evaluate_device(qoc_ctx* ctx, const double* u_dev, double* grad_dev, double* out_dev) {
+    if (!ctx) return QOC_ERR_ARG;
+    ctx->err.clear();
+    if (!ctx->has_sys || !ctx->has_tgt) return set_err(ctx, QOC_ERR_STATE, "set_system and set_targets must come first");
+    if (!u_dev || !grad_dev || !out_dev) return set_err(ctx, QOC_ERR_ARG, "NULL device pointer");
+    QOC_GUARD_BEGIN
+    check_cuda(ctx, cudaSetDevice(ctx->opt.device), "set device");
+    evaluate(ctx, u_dev, grad_dev, out_dev);
+    return QOC_OK;
+    QOC_GUARD_END
+}
+
+qoc_status qoc_evaluate_cost_and_grad(qoc_ctx* ctx, const double* u, double* cost, double* grad, double* terms) {
+    if (!ctx) return QOC_ERR_ARG;
+    ctx->err.clear();
+    if (!ctx->has_sys || !ctx->has_tgt) return set_err(ctx, QOC_ERR_STATE, "set_system and set_targets must come first");
+    if (!u || !cost || (!grad && ctx->M > 0)) return set_err(ctx, QOC_ERR_ARG, "NULL argument");
+    const size_t mn = (size_t)ctx->M * ctx->N;
+    if (!all_finite(u, mn)) return set_err(ctx, QOC_ERR_NONFINITE, "non-finite control");
+    QOC_GUARD_BEGIN
+    check_cuda(ctx, cudaSetDevice(ctx->opt.device), "set device");
+    if (!ctx->planned) plan(ctx);
+    cudaStream_t st = ctx->stream;
+    if (mn) check_cuda(ctx, cudaMemcpyAsync(ctx->u_h.p, u, mn * sizeof(double), cudaMemcpyHostToDevice, st), "copy u");
+    evaluate(ctx, ctx->u_h.as<double>(), ctx->grad_h.as<double>(), ctx->out_h.as<double>());
+    double out[6];
+    if (mn)
+        check_cuda(ctx, cudaMemcpyAsync(grad, ctx->grad_h.p, mn * sizeof(double), cudaMemcpyDeviceToHost, st),
+                   "copy grad");
+    check_cuda(ctx, cudaMemcpyAsync(out, ctx->out_h.p, 6 * sizeof(double), cudaMemcpyDeviceToHost, st), "copy cost");
+    qoc_status s = device_error(ctx);   // synchronises
+    if (s != QOC_OK) return s;
+    *cost = out[0];
+    if (terms)
+        for (int i = 0; i < 5; ++i) terms[i] = out[1 + i];
+    return QOC_OK;
+    QOC_GUARD_END
+}
+
+qoc_status qoc_sync(qoc_ctx* ctx) {
+    if (!ctx) return QOC_ERR_ARG;
+    ctx->err.clear();
+    QOC_GUARD_BEGIN
+    if (!ctx->planned) {
+        check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "sync");
+        return QOC_OK;
+    }
+    return device_error(ctx);
+    QOC_GUARD_END
+}
+
+qoc_status qoc_get_info(qoc_ctx* ctx, qoc_info* info) {
+    if (!ctx || !info) return QOC_ERR_ARG;
+    ctx->err.clear();
+    std::memset(info, 0, sizeof(*info));
+    QOC_GUARD_BEGIN
+    if (ctx->planned) {
+        DevParams h{};
+        check_cuda(ctx, cudaMemcpyAsync(&h, ctx->prm.p, sizeof(DevParams), cudaMemcpyDeviceToHost, ctx->stream),
+                   "read params");
+        check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "sync");
+        info->p = h.p;
+        info->n = h.n;
+        info->theta = h.theta;
+        ctx->prof.harvest();
+    }
+    info->ckpt_stride = ctx->seg;
+    info->wave_slices = ctx->W;
+    info->n_waves = ctx->nw;
+    info->launches_per_eval = ctx->launches;
+    info->kernel_path = ctx->path_kind;
+    info->device_bytes = (long long)ctx->device_bytes();
+    return QOC_OK;
+    QOC_GUARD_END
+}
+
+qoc_status qoc_get_profile(qoc_ctx* ctx, qoc_profile* out) {
+    if (!ctx || !out) return QOC_ERR_ARG;
+    ctx->err.clear();
+    std::memset(out, 0, sizeof(*out));
+    QOC_GUARD_BEGIN
+    check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "sync");
+    ctx->prof.harvest();
+    const int n = std::min((int)ctx->prof.names.size(), QOC_PROFILE_SLOTS);
+    out->count = n;
+    for (int i = 0; i < n; ++i) {
+        std::snprintf(out->name[i], sizeof(out->name[i]), "%s", ctx->prof.names[i].c_str());
+        out->launches[i] = ctx->prof.launches[i];
+        out->total_ms[i] = ctx->prof.ms[i];
+    }
+    return QOC_OK;
+    QOC_GUARD_END
+}
+
+qoc_status qoc_reset_profile(qoc_ctx* ctx) {
+    if (!ctx) return QOC_ERR_ARG;
+    ctx->err.clear();
+    QOC_GUARD_BEGIN
+    check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "sync");
+    ctx->prof.harvest();
+    ctx->prof.reset();
+    return QOC_OK;
+    QOC_GUARD_END
+}
+
+}  // extern "C"

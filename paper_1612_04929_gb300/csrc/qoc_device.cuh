@@ -1,0 +1,75 @@
+// Device-side helpers shared by the CUDA kernels of the quantum-control evaluation.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace qoc {
+
+template <typename R> struct Cplx;
+template <> struct Cplx<float> { using T = float2; };
+template <> struct Cplx<double> { using T = double2; };
+
+template <typename C> __device__ __forceinline__ C czero() { C z; z.x = 0; z.y = 0; return z; }
+template <typename C, typename R> __device__ __forceinline__ C cmk(R re, R im) { C z; z.x = re; z.y = im; return z; }
+
+// acc += a * b
+template <typename C> __device__ __forceinline__ void cfma(C& acc, const C a, const C b) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+}
+// acc += conj(a) * b
+template <typename C> __device__ __forceinline__ void cfma_cj(C& acc, const C a, const C b) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(-a.y, b.x, acc.y);
+}
+// acc += a * conj(b)
+template <typename C> __device__ __forceinline__ void cfma_bcj(C& acc, const C a, const C b) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(a.y, b.x, acc.y);
+    acc.y = fma(-a.x, b.y, acc.y);
+}
+
+// Per-evaluation scalars produced on the device by the norm kernel and read by every kernel.
+struct DevParams {
+    double theta;   // dt * max_j ||H_j||_1 bound (FP64)
+    double s;       // dt / 2^n
+    int p;          // Taylor order
+    int n;          // squaring count
+    int err;        // error bits (kErr*)
+    int pad;
+};
+
+enum : int { kErrRange = 1, kErrTimeout = 2 };
+
+// ------------------------------------------------------------------------------------------
+// cp.async (16-byte) helpers for the prefetch rings of the serial propagation kernels.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// FP64 block reduction (blockDim.x multiple of 32, <= 1024); result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* scratch /* >= 32 doubles */) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) scratch[w] = v;
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    v = (threadIdx.x < nw) ? scratch[threadIdx.x] : 0.0;
+    if (w == 0)
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace qoc

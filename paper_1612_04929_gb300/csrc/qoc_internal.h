@@ -1,0 +1,124 @@
+// Host/device interface between the C ABI layer and the CUDA kernels (internal, not installed).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "qoc_device.cuh"
+
+namespace qoc {
+
+template <typename R> using C_t = typename Cplx<R>::T;
+
+// Element of the block carried by the serial sweeps: FP64 complex in the FP64 form, an
+// unevaluated pair hi + lo of FP32 complex numbers (x, y = hi; z, w = lo) in the FP32 form.
+template <typename R> struct Carry;
+template <> struct Carry<float> { using T = float4; };
+template <> struct Carry<double> { using T = double2; };
+template <typename R> using K_t = typename Carry<R>::T;
+
+constexpr int kMaxControls = 64;
+constexpr int kMaxD = 512;
+constexpr int kPMax = 40;                 // largest Taylor order the heuristic may pick
+constexpr size_t kMaxDynSmem = 232448 - 2048;   // opt-in dynamic shared memory per CTA
+
+// The system (Eq. 1) in the compute precision R; u and delta stay FP64.
+template <typename R>
+struct SysView {
+    int d, M, N;
+    const C_t<R>* H0;     // d x d
+    const C_t<R>* Hk;     // M x d x d
+    const C_t<R>* Hdet;   // d x d or nullptr
+    const double* delta;  // E or nullptr
+    const double* u;      // M x N
+};
+
+// Column-panel layout of every d x S block on the device: the S columns are padded to
+// Spad = ncb * cb and stored as ncb contiguous d x cb panels, so a CTA that owns one panel
+// reads and writes contiguous memory.  Element (a, s) sits at (s / cb) * pstride + a * cb + s % cb;
+// pstride >= d * cb is rounded up to 16 bytes so that every panel can be copied by cp.async.
+// A block (one state, costate or source) occupies slice() = ncb * pstride elements.
+template <typename R>
+struct StateView {
+    int Spad, cb, ncb, pstride;
+    __host__ __device__ size_t slice() const { return (size_t)ncb * pstride; }
+};
+
+// Cost inputs (Table I).
+template <typename R>
+struct CostView {
+    int nF;
+    const int* fmask;       // d: 1 for forbidden basis states
+    const double* w;        // Spad column weights (0 on padding)
+    double Wsum;            // sum of weights
+    const C_t<R>* psiT;     // final target, panel layout d x Spad
+    const C_t<R>* path;     // N targets (panel layout) or nullptr
+    double alpha[5];        // [fid, C3, C4, C5, C67]
+};
+
+// ---- norms / (p, n) ----
+cudaError_t launch_norms(const double2* mats, int count, int d, double* norms, cudaStream_t st);
+cudaError_t launch_theta(const double* u, int M, int N, const double* norms, const double* delta, int E,
+                         double dt, double theta_max, double tol, int p_override, int n_override,
+                         DevParams* prm, cudaStream_t st);
+
+// ---- conversions ----
+template <typename R>
+cudaError_t launch_convert(const double2* src, C_t<R>* dst, size_t count, cudaStream_t st);
+template <typename R>
+cudaError_t launch_to_panels(const double2* src, C_t<R>* dst, int d, int S, StateView<R> sv,
+                             int copies, size_t dst_stride, size_t src_stride, cudaStream_t st);
+
+// ---- fused per-slice exponential kernels ----
+template <typename R> int fused_max_d();
+template <typename R>
+cudaError_t launch_expm_fwd_fused(const DevParams* prm, const SysView<R>& sys, int j0, int wlen, int E,
+                                  C_t<R>* Ubuf, long long ustride, int wmax, cudaStream_t st);
+template <typename R>
+cudaError_t launch_expm_adj_fused(const DevParams* prm, const SysView<R>& sys, const StateView<R>& sv, int j0,
+                                  int wlen, int E, const C_t<R>* states, const C_t<R>* Gbuf, int wmax,
+                                  double* gpart, cudaStream_t st);
+
+// ---- split hi+lo FP32 slice exponential (FP32 form) ----
+int split_max_d();
+cudaError_t launch_expm_fwd_split(const DevParams* prm, const SysView<float>& sys, const double2* H64, int j0, int wlen,
+                                  int E, float2* Ubuf, long long ustride, int wmax, cudaStream_t st);
+
+// ---- serial sweeps (k_serial.cu) ----
+// mode 0: forward propagation of one wave (grid z = 1) from checkpoint `seg0`, storing the
+//         states of the wave and the carried block every `seg` slices (checkpoints seg0 + 1, ..)
+// mode 1: regeneration of the wave's states, one CTA per checkpoint segment in parallel
+template <typename R>
+struct ChainArgs {
+    int d;
+    StateView<R> sv;
+    int wlen, seg, mode, E;
+    K_t<R>* ckpt;           // [E][nseg_total] carried blocks
+    size_t ck_estride;      // elements per member
+    int seg0, nseg_total;
+    const C_t<R>* Ubuf;
+    long long ustride;
+    int wmax;
+    C_t<R>* states;         // [E][wmax + 1] FP32/FP64 blocks of the wave
+};
+template <typename R> cudaError_t launch_chain(const ChainArgs<R>& a, cudaStream_t st);
+template <typename R>
+cudaError_t launch_costate(int d, StateView<R> sv, int wlen, int E, const C_t<R>* Ubuf, long long ustride, int wmax,
+                           const C_t<R>* src, K_t<R>* carry, C_t<R>* Gbuf, cudaStream_t st);
+template <typename R>
+cudaError_t launch_to_carry(const double2* src, K_t<R>* dst, int d, int S, StateView<R> sv, int copies,
+                            size_t dst_stride, cudaStream_t st);
+
+// ---- per-slice costs, sources, final reduction (k_chain.cu) ----
+template <typename R>
+cudaError_t launch_slice_costs(int d, StateView<R> sv, int j0, int wlen, int N, int E, const C_t<R>* states,
+                               int wmax, const CostView<R>& cv, double2* Oj, double* C5j, double2* Ofin,
+                               cudaStream_t st);
+template <typename R>
+cudaError_t launch_sources(int d, StateView<R> sv, int j0, int wlen, int N, int E, const C_t<R>* states,
+                           int wmax, const CostView<R>& cv, const double2* Oj, const double2* Ofin,
+                           C_t<R>* src, cudaStream_t st);
+cudaError_t launch_finalize(int E, int M, int N, const double* u, const double* alpha, const double2* Oj,
+                            const double* C5j, const double2* Ofin, const double* gpart, double* grad,
+                            double* out, cudaStream_t st);
+
+}  // namespace qoc

@@ -1,0 +1,225 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the CPU FP64 oracle on the same
+seeded inputs.
+
+Tolerances: the FP64 form matches the exact-exponential oracle to <= 1e-10 relative in cost
+and in ||g - g_ref|| / ||g_ref||; the FP32 form to <= 1e-5.  Against the truncated-series
+oracle at the same (p, n) the FP64 form agrees to ~1e-12 (arithmetic error only).  The integer
+decision (p, n) is taken in FP64 on both sides and must agree exactly."""
+import numpy as np
+import pytest
+
+import synthetic as sy
+from oracle import qoc_oracle as orc
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "fp32": 1e-5}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1612_04929_gb300 import build
+    build.build()
+
+
+def run(prob, precision, **opt):
+    from paper_1612_04929_gb300 import Context
+    with Context(precision, **opt) as c:
+        c.set_problem(prob)
+        cost, grad, terms = c.evaluate(prob.u)
+        info = c.info()
+    return cost, grad, terms, info
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+def check(prob, precision, tol=None, **opt):
+    tol = TOL[precision] if tol is None else tol
+    cost, grad, terms, info = run(prob, precision, **opt)
+    c_ref, g_ref, t_ref = orc.cost_and_grad(prob, prob.u)
+    assert abs(cost - c_ref) <= tol * max(abs(c_ref), 1e-12), (cost, c_ref)
+    assert np.max(np.abs(terms - t_ref) / np.maximum(np.abs(t_ref), 1.0)) <= tol, (terms, t_ref)
+    if prob.M:
+        assert rel(grad, g_ref) <= tol, rel(grad, g_ref)
+        floor = 1e-12 * np.max(np.abs(g_ref))
+        comp = np.abs(grad - g_ref) / np.maximum(np.abs(g_ref), floor)
+        # per component: relative to the component, with an absolute floor at tol*||g||_inf
+        assert np.all((comp <= 10 * tol) | (np.abs(grad - g_ref) <= tol * np.max(np.abs(g_ref))))
+    return cost, grad, terms, info
+
+
+CASES64 = [
+    dict(d=2, M=1, N=9, S=1, seed=101, nF=1),
+    dict(d=3, M=2, N=17, S=2, seed=102, nF=1, weights=True),
+    dict(d=4, M=3, N=33, S=4, seed=103, nF=2, path=True),
+    dict(d=5, M=2, N=20, S=1, seed=104, nF=1, E=3),
+    dict(d=7, M=4, N=41, S=3, seed=105, nF=2, path=True, E=2, weights=True),
+    dict(d=16, M=2, N=23, S=16, seed=106, nF=3),
+    dict(d=17, M=3, N=19, S=9, seed=107, nF=4, path=True),     # two column panels, ragged tail
+    dict(d=33, M=2, N=13, S=1, seed=108, nF=5),                 # 3 x 16 thread tile, ragged
+    dict(d=48, M=2, N=7, S=10, seed=109, nF=3, E=2),            # largest fused FP64 size
+]
+
+
+LAYOUTS = [dict(), dict(ckpt_stride=4, wave_slices=8), dict(ckpt_stride=3, wave_slices=3),
+           dict(ckpt_stride=1000)]
+
+
+@pytest.mark.parametrize("case", CASES64, ids=lambda c: f"d{c['d']}S{c['S']}N{c['N']}")
+@pytest.mark.parametrize("layout", LAYOUTS, ids=lambda l: "-".join(f"{k}{v}" for k, v in l.items()) or "auto")
+def test_fp64_matches_oracle(case, layout):
+    prob = sy.random_problem(**case, dt=0.2, u_scale=0.8)
+    check(prob, "fp64", **layout)
+
+
+@pytest.mark.parametrize("case", CASES64[:6], ids=lambda c: f"d{c['d']}S{c['S']}N{c['N']}")
+def test_fp64_pn_and_truncated_series(case):
+    prob = sy.random_problem(**case, dt=0.2, u_scale=0.8)
+    cost, grad, terms, info = run(prob, "fp64")
+    theta = orc.theta_bound(prob, prob.u)
+    assert info["theta"] == pytest.approx(theta, rel=1e-13)
+    assert (info["p"], info["n"]) == orc.pick_pn(theta, 0.25, 1e-15)
+    c_t, g_t, _ = orc.taylor_cost_and_grad(prob, prob.u, info["p"], info["n"])
+    assert abs(cost - c_t) <= 1e-12 * max(1.0, abs(c_t))
+    assert rel(grad, g_t) <= 1e-11
+
+
+def test_fp64_short_series_is_differentiated_exactly():
+    """A deliberately short series (p=3, n=1): the GPU gradient must be the exact derivative of
+    that truncated map (the truncated-series oracle), not the exact exponential's."""
+    prob = sy.random_problem(d=6, M=2, N=15, S=2, seed=110, nF=2, path=True, dt=0.2)
+    cost, grad, terms, info = run(prob, "fp64", p_override=3, n_override=1)
+    assert (info["p"], info["n"]) == (3, 1)
+    c_t, g_t, _ = orc.taylor_cost_and_grad(prob, prob.u, 3, 1)
+    assert abs(cost - c_t) <= 1e-12 * abs(c_t)
+    assert rel(grad, g_t) <= 1e-11
+    _, g_e, _ = orc.cost_and_grad(prob, prob.u)
+    assert rel(grad, g_e) > 1e-6
+
+
+CASES32 = [
+    dict(d=4, M=2, N=50, S=4, seed=201, nF=1),
+    dict(d=13, M=3, N=37, S=1, seed=202, nF=2, path=True),
+    dict(d=40, M=2, N=64, S=1, seed=203, nF=13),
+    dict(d=40, M=2, N=30, S=40, seed=204, nF=6, E=2),
+    dict(d=64, M=3, N=21, S=8, seed=205, nF=4, weights=True),   # largest fused FP32 size
+]
+
+
+@pytest.mark.parametrize("case", CASES32, ids=lambda c: f"d{c['d']}S{c['S']}N{c['N']}")
+@pytest.mark.parametrize("layout", LAYOUTS[:3], ids=lambda l: "-".join(f"{k}{v}" for k, v in l.items()) or "auto")
+def test_fp32_matches_oracle(case, layout):
+    prob = sy.random_problem(**case, dt=0.2, u_scale=0.8)
+    check(prob, "fp32", **layout)
+
+
+def test_plain_fp32_exponential_option_runs():
+    """The diagnostic plain-FP32 exponential is less accurate on long evolutions but must stay
+    close to the oracle and differ from the split default."""
+    prob = sy.transmon_cavity(N=400)
+    c1, g1, _, _ = run(prob, "fp32", plain_fp32_exp=True)
+    c2, g2, _, _ = run(prob, "fp32")
+    c_ref, g_ref, _ = orc.cost_and_grad(prob, prob.u)
+    assert abs(c1 - c_ref) <= 1e-4 * abs(c_ref) and rel(g1, g_ref) <= 1e-3
+    assert rel(g2, g_ref) <= 1e-5 and rel(g1, g2) > 0
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("fp32", 1e-7)])
+def test_checkpoint_layout_does_not_change_results(precision, tol):
+    """Checkpoint stride and wave size change only where partial sums are added (costate
+    carries between waves); the carried hi+lo recursion keeps that at rounding level."""
+    prob = sy.random_problem(d=9, M=2, N=50, S=3, seed=301, nF=2, path=True, E=2)
+    ref = run(prob, precision, ckpt_stride=1000)
+    for stride, wave in ((1, 1), (7, 14), (16, 16), (49, 0), (5, 45)):
+        out = run(prob, precision, ckpt_stride=stride, wave_slices=wave)
+        assert out[3]["ckpt_stride"] == stride
+        assert abs(out[0] - ref[0]) <= tol * abs(ref[0])
+        assert np.max(np.abs(out[1] - ref[1])) <= tol * np.max(np.abs(ref[1]))
+
+
+# ------------------------------------------------------------------ the workloads
+def test_cnot2q_fp64_full_size():
+    check(sy.cnot2q(), "fp64")
+
+
+def test_transmon_cavity_fp32_full_size():
+    prob = sy.transmon_cavity()
+    cost, grad, terms, info = check(prob, "fp32")
+    assert info["ckpt_stride"] == 45 and info["n_waves"] > 1     # sqrt(N) checkpoints, recomputation on
+
+
+def test_transmon_cavity_fp64_reduced_N():
+    check(sy.transmon_cavity(N=300), "fp64")
+
+
+# ------------------------------------------------------------------ edge cases
+def test_single_slice_and_single_level():
+    check(sy.random_problem(d=3, M=2, N=1, S=2, seed=401, nF=1), "fp64")
+    check(sy.random_problem(d=1, M=1, N=5, S=1, seed=402), "fp64")
+
+
+def test_no_controls():
+    prob = sy.random_problem(d=4, M=0, N=6, S=2, seed=403, nF=1)
+    cost, grad, terms, info = run(prob, "fp64")
+    c_ref, _, t_ref = orc.cost_and_grad(prob, prob.u)
+    assert grad.shape == (0, 6) and abs(cost - c_ref) <= 1e-10 * abs(c_ref)
+
+
+def test_zero_hamiltonian_identity_target():
+    d, N = 5, 8
+    z = np.zeros((d, d), np.complex128)
+    prob = sy.Problem("zero", z, np.stack([z]), 0.3, N, np.eye(d, dtype=np.complex128),
+                      np.eye(d, dtype=np.complex128), np.zeros(0, np.int32), np.ones(d),
+                      np.array([1.0, 0, 0, 0, 1.0]), np.zeros((1, N)))
+    cost, grad, terms, info = run(prob, "fp64")
+    assert abs(cost) < 1e-14 and info["n"] == 0
+
+
+# ------------------------------------------------------------------ error paths
+def test_error_statuses():
+    from paper_1612_04929_gb300 import Context, QocError
+    c = Context("fp64")
+    with pytest.raises(QocError) as e:
+        c.evaluate(np.zeros((1, 3)))
+    assert e.value.status == 5                                   # call order
+    H = np.array([[0, 1], [0, 0]], np.complex128)
+    with pytest.raises(QocError) as e:
+        c.set_system(H, None, 0.1, 3)
+    assert e.value.status == 3                                   # not Hermitian
+    with pytest.raises(QocError) as e:
+        c.set_system(np.eye(2) * np.nan, None, 0.1, 3)
+    assert e.value.status == 4
+    c.set_system(np.eye(2), sy.SX[None], 0.1, 3)
+    with pytest.raises(QocError) as e:
+        c.set_targets(np.eye(2), np.eye(2), forbidden=[5])
+    assert e.value.status == 2
+    c.set_targets(np.eye(2), np.eye(2))
+    with pytest.raises(QocError) as e:
+        c.evaluate(np.full((1, 3), np.inf))
+    assert e.value.status == 4
+    c.close()
+    big = Context("fp64")
+    big.set_system(np.eye(49), None, 0.1, 2)
+    big.set_targets(np.eye(49)[:, :1], np.eye(49)[:, :1])
+    with pytest.raises(QocError) as e:
+        big.evaluate(np.zeros((0, 2)))
+    assert e.value.status == 9                                   # beyond the fused FP64 sizes
+    big.close()
+
+
+# ------------------------------------------------------------------ torch autograd
+def test_autograd_function_matches_oracle():
+    import torch
+    from paper_1612_04929_gb300 import Context, cost as qcost
+    prob = sy.random_problem(d=6, M=2, N=25, S=2, seed=501, nF=2)
+    stream = torch.cuda.current_stream().cuda_stream
+    with Context("fp64", stream=stream) as c:
+        c.set_problem(prob)
+        u = torch.tensor(prob.u, dtype=torch.float64, device="cuda", requires_grad=True)
+        C, terms = qcost(c, u)
+        (3.0 * C).backward()
+        c_ref, g_ref, _ = orc.cost_and_grad(prob, prob.u)
+        assert abs(C.item() - c_ref) <= 1e-10 * abs(c_ref)
+        assert rel(u.grad.cpu().numpy(), 3.0 * g_ref) <= 1e-10
