@@ -175,6 +175,39 @@ qoc_status qoc_get_profile(qoc_ctx* ctx, qoc_profile* out);
 /* Clears the accumulated per-kernel timings. */
 qoc_status qoc_reset_profile(qoc_ctx* ctx);
 
+/* Bytes of the device array that qoc_evaluate_static works in (32 MiB).  Every GPU that loads
+ * the library holds this array until the process exits. */
+#define QOC_STATIC_ARENA_BYTES (32u << 20)
+
+/* One evaluation that allocates no memory, for callers that may not allocate at the time they
+ * evaluate: code running while a stream is captured into a CUDA graph (allocation is not
+ * permitted there), real-time loops that forbid allocator calls because they can block, or
+ * programs whose device memory belongs to a pool that must not be bypassed.  The paper has no
+ * counterpart; this is a packaging of the same computation.
+ *
+ * It computes what qoc_evaluate_device computes for the FP64 form with no ensemble, no
+ * per-slice targets and unit column weights, keeping every intermediate in a fixed device array
+ * of QOC_STATIC_ARENA_BYTES instead of context-owned buffers.  There is no context.
+ *   d (1..48), M (0..64), N (>= 1), S (1..d); dt > 0.
+ *   H0_dev: d x d complex128 (interleaved, row-major), Hk_dev: M such matrices, u_dev: M x N
+ *   doubles, psi0_dev / psiT_dev: d x S complex128, fmask_dev: d ints, 1 for a forbidden basis
+ *   state (NULL: none) -- all device pointers owned by the caller and not validated.
+ *   alpha: 5 host doubles [fid, C3, C4, C5, C67], read before the call returns.
+ *   grad_dev (M x N doubles) and out_dev (6 doubles: C then the 5 terms) receive the results.
+ *   stream: cudaStream_t to enqueue on (NULL: the legacy default stream).
+ * The call enqueues its kernels and returns without synchronising.  Its status covers the
+ * argument checks, the size check and launch errors only; device-side conditions (a Taylor
+ * order above its maximum) are not reported.  QOC_ERR_SHAPE also means that the problem does
+ * not fit the array: about (N d^2 + 4 N d S) 16-byte numbers must stay below its size.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before capturing a stream.  All calls share the
+ * one array and every call overwrites it: calls that may overlap on the GPU (different streams
+ * without ordering between them, or different host threads) race and give wrong results. */
+qoc_status qoc_evaluate_static(int d, int M, int N, int S, double dt, const double* H0_dev,
+                               const double* Hk_dev, const double* u_dev, const double* psi0_dev,
+                               const double* psiT_dev, const int* fmask_dev, const double* alpha,
+                               double* grad_dev, double* out_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,127 @@
+// qoc_evaluate_static: one cost + gradient evaluation that allocates no memory.
+//
+// Who needs it: callers that may not allocate device memory at the moment they evaluate, for
+// example code running while a CUDA stream is being captured into a graph (cudaMalloc is not
+// allowed there), real-time control loops that forbid allocator calls (they can block and take
+// locks), or hosts whose memory is managed by a pool that must not be bypassed.  The regular
+// entry points allocate their working buffers inside a context; this one instead uses a fixed
+// device array compiled into the library, so it needs no context and no allocation at all.
+//
+// The array is a file-scope __device__ variable of QOC_STATIC_ARENA_BYTES bytes.  Every GPU
+// that loads the library holds it until the process exits.  On the host its name only stands
+// for the variable, so its device address is looked up once per device, with that device
+// current, by cudaGetSymbolAddress on the first call made on that device.
+#include <cuda_runtime.h>
+
+#include <cstring>
+
+#include "../../include/qoc.h"
+#include "qoc_internal.h"
+
+using namespace qoc;
+
+namespace {
+
+static __device__ __align__(256) unsigned char g_arena[QOC_STATIC_ARENA_BYTES];
+
+constexpr int kMaxDevices = 64;
+void* g_arena_addr[kMaxDevices] = {nullptr};
+
+// carve 256-byte-aligned pieces out of the arena (pointer arithmetic only)
+struct Carver {
+    unsigned char* base;
+    size_t used = 0;
+    template <typename T>
+    T* take(size_t count) {
+        used = (used + 255) & ~(size_t)255;
+        T* p = reinterpret_cast<T*>(base + used);
+        used += count * sizeof(T);
+        return p;
+    }
+};
+
+__global__ void k_static_weights(double* w, int S, int Spad) {
+    for (int s = threadIdx.x; s < Spad; s += blockDim.x) w[s] = (s < S) ? 1.0 : 0.0;
+}
+
+}  // namespace
+
+extern "C" qoc_status qoc_evaluate_static(int d, int M, int N, int S, double dt, const double* H0_dev,
+                                          const double* Hk_dev, const double* u_dev, const double* psi0_dev,
+                                          const double* psiT_dev, const int* fmask_dev, const double* alpha,
+                                          double* grad_dev, double* out_dev, void* stream) {
+    if (!H0_dev || (M > 0 && (!Hk_dev || !u_dev)) || !psi0_dev || !psiT_dev || !alpha || !out_dev ||
+        (M > 0 && !grad_dev))
+        return QOC_ERR_ARG;
+    if (d < 1 || d > fused_max_d<double>() || M < 0 || M > kMaxControls || N < 1 || S < 1 || S > d)
+        return QOC_ERR_SHAPE;
+    if (!(dt > 0.0)) return QOC_ERR_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return QOC_ERR_CUDA;
+    if (!g_arena_addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_arena) != cudaSuccess || !p) return QOC_ERR_CUDA;
+        g_arena_addr[dev] = p;
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    using R = double;
+    using C = C_t<R>;
+    using K = K_t<R>;
+    StateView<R> sv;
+    sv.cb = S < 8 ? S : 8;
+    sv.ncb = (S + sv.cb - 1) / sv.cb;
+    sv.Spad = sv.ncb * sv.cb;
+    sv.pstride = d * sv.cb;                       // 16-byte elements: always aligned
+    const size_t slice = sv.slice();
+    const long long ustride = ((long long)d * d + 15) / 16 * 16;
+
+    Carver cv{reinterpret_cast<unsigned char*>(g_arena_addr[dev])};
+    DevParams* prm = cv.take<DevParams>(1);
+    double* norms = cv.take<double>(M + 2);
+    C* psiT = cv.take<C>(slice);
+    K* ckpt = cv.take<K>(slice);
+    C* Ubuf = cv.take<C>((size_t)N * ustride);
+    C* states = cv.take<C>((size_t)(N + 1) * slice);
+    C* Gbuf = cv.take<C>((size_t)N * slice);
+    C* src = cv.take<C>((size_t)N * slice);
+    K* carry = cv.take<K>(slice);
+    double2* Oj = cv.take<double2>(N);
+    double* C5j = cv.take<double>(N);
+    double2* Ofin = cv.take<double2>(1);
+    double* gpart = cv.take<double>((size_t)M * N + 1);
+    double* colw = cv.take<double>(sv.Spad);
+    int* fmask_zero = cv.take<int>(d);
+    if (cv.used > QOC_STATIC_ARENA_BYTES) return QOC_ERR_SHAPE;   // the problem does not fit
+
+    auto ok = [](cudaError_t e) { return e == cudaSuccess; };
+    const double2* H0 = reinterpret_cast<const double2*>(H0_dev);
+    const double2* Hk = reinterpret_cast<const double2*>(Hk_dev);
+    // state a previous call left behind that must start at zero: the unused norm slot of the
+    // detuning operator, the costate carry and (without forbidden states) the mask
+    if (!ok(cudaMemsetAsync(norms + M + 1, 0, sizeof(double), st))) return QOC_ERR_CUDA;
+    if (!ok(cudaMemsetAsync(carry, 0, slice * sizeof(K), st))) return QOC_ERR_CUDA;
+    if (!fmask_dev && !ok(cudaMemsetAsync(fmask_zero, 0, d * sizeof(int), st))) return QOC_ERR_CUDA;
+    if (!ok(launch_norms(H0, 1, d, norms, st))) return QOC_ERR_CUDA;
+    if (M > 0 && !ok(launch_norms(Hk, M, d, norms + 1, st))) return QOC_ERR_CUDA;
+    k_static_weights<<<1, 64, 0, st>>>(colw, S, sv.Spad);
+    if (!ok(cudaGetLastError())) return QOC_ERR_CUDA;
+    if (!ok(launch_to_panels<R>(reinterpret_cast<const double2*>(psiT_dev), psiT, d, S, sv, 1, 0, 0, st)))
+        return QOC_ERR_CUDA;
+    if (!ok(launch_to_carry<R>(reinterpret_cast<const double2*>(psi0_dev), ckpt, d, S, sv, 1, slice, st)))
+        return QOC_ERR_CUDA;
+
+    SysView<R> sys{d, M, N, H0, Hk, nullptr, nullptr, u_dev};
+    CostView<R> cost{0, fmask_dev ? fmask_dev : fmask_zero, colw, (double)S, psiT, nullptr,
+                     {alpha[0], alpha[1], alpha[2], alpha[3], alpha[4]}};
+    ChainArgs<R> ch{d, sv, N, N, 0, 1, ckpt, slice, 0, 1, Ubuf, ustride, N, states};
+    if (!ok(launch_theta(u_dev, M, N, norms, nullptr, 1, dt, 0.25, 1e-15, 0, -1, prm, st))) return QOC_ERR_CUDA;
+    if (!ok(launch_expm_fwd_fused<R>(prm, sys, 0, N, 1, Ubuf, ustride, N, st))) return QOC_ERR_CUDA;
+    if (!ok(launch_chain<R>(ch, st))) return QOC_ERR_CUDA;
+    if (!ok(launch_slice_costs<R>(d, sv, 0, N, N, 1, states, N, cost, Oj, C5j, Ofin, st))) return QOC_ERR_CUDA;
+    if (!ok(launch_sources<R>(d, sv, 0, N, N, 1, states, N, cost, Oj, Ofin, src, st))) return QOC_ERR_CUDA;
+    if (!ok(launch_costate<R>(d, sv, N, 1, Ubuf, ustride, N, src, carry, Gbuf, st))) return QOC_ERR_CUDA;
+    if (!ok(launch_expm_adj_fused<R>(prm, sys, sv, 0, N, 1, states, Gbuf, N, gpart, st))) return QOC_ERR_CUDA;
+    if (!ok(launch_finalize(1, M, N, u_dev, alpha, Oj, C5j, Ofin, gpart, grad_dev, out_dev, st)))
+        return QOC_ERR_CUDA;
+    return QOC_OK;
+}

@@ -29,7 +29,8 @@ PRECISIONS = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
 # every symbol exported by include/qoc.h
 ABI_SYMBOLS = ("qoc_default_options", "qoc_create", "qoc_destroy", "qoc_last_error", "qoc_status_string",
                "qoc_set_system", "qoc_set_targets", "qoc_set_ensemble", "qoc_evaluate_cost_and_grad",
-               "qoc_evaluate_device", "qoc_sync", "qoc_get_info", "qoc_get_profile", "qoc_reset_profile")
+               "qoc_evaluate_device", "qoc_sync", "qoc_get_info", "qoc_get_profile", "qoc_reset_profile",
+               "qoc_evaluate_static")
 
 
 class QocError(RuntimeError):
@@ -100,6 +101,8 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.qoc_get_profile.restype = I
     lib.qoc_reset_profile.argtypes = [P]
     lib.qoc_reset_profile.restype = I
+    lib.qoc_evaluate_static.argtypes = [I, I, I, I, D, VP, VP, VP, VP, VP, VP, DP, VP, VP, VP]
+    lib.qoc_evaluate_static.restype = I
     _lib = lib
     return lib
 
@@ -218,6 +221,19 @@ def qoc_get_profile(ctx) -> dict:
 
 def qoc_reset_profile(ctx) -> None:
     _check(ctx, load().qoc_reset_profile(ctx))
+
+
+def qoc_evaluate_static(d: int, M: int, N: int, S: int, dt: float, H0_dev: int, Hk_dev: int, u_dev: int,
+                        psi0_dev: int, psiT_dev: int, fmask_dev: int, alpha, grad_dev: int, out_dev: int,
+                        stream: int = 0) -> None:
+    """The evaluation that allocates no memory (see include/qoc.h): every array argument except
+    ``alpha`` is a raw device pointer (int); the call is asynchronous on ``stream``."""
+    al = _f64(alpha)
+    st = load().qoc_evaluate_static(d, M, N, S, float(dt), H0_dev or None, Hk_dev or None, u_dev or None,
+                                    psi0_dev or None, psiT_dev or None, fmask_dev or None, _dp(al),
+                                    grad_dev or None, out_dev or None, stream or None)
+    if st != QOC_OK:
+        raise QocError(st, "qoc_evaluate_static failed")
 
 
 # ------------------------------------------------------------------ convenience wrapper
