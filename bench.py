@@ -42,14 +42,15 @@ def parse():
     ap.add_argument("--workload", default="transmon_cavity")
     ap.add_argument("--precision", default=None)
     ap.add_argument("--ckpt-stride", type=int, default=0)
+    ap.add_argument("--N", type=int, default=0, help="override the slice count (profiling runs)")
     ap.add_argument("--cpu-sample", type=int, default=0, help="slices in the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
 
-def make_problem(name):
+def make_problem(name, N=0):
     import synthetic as sy
-    return sy.WORKLOADS[name]()
+    return sy.WORKLOADS[name](N=N) if N else sy.WORKLOADS[name]()
 
 
 def config_of(prob, precision, stride, extra=None):
@@ -185,7 +186,7 @@ def ours_arm(args):
         qbuild.build()
     if world > 1:
         dist.barrier()
-    prob = make_problem(args.workload)
+    prob = make_problem(args.workload, args.N)
     precision = args.precision or prob.precision
     stream = torch.cuda.Stream()          # every kernel of the step and every event on one stream
     torch.cuda.set_stream(stream)

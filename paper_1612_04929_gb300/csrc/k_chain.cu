@@ -79,6 +79,16 @@ __global__ void k_theta(const double* __restrict__ u, int M, int N, const double
         fact *= (double)(p + 1);
     }
     if (p_override >= 1) { p = p_override; err &= ~kErrRange; }
+    // A rounding error e made in Horner step i + 1 reaches T = Z_1 multiplied by at most
+    // ts^i / i! (the X / i' factors of steps i..1).  Steps i <= m need the hi+lo pair; beyond m
+    // the factor is below 2^-6 and plain FP32 is exact enough.
+    int m = 1;
+    double f = ts;
+    while (m < p && f > 0.015625) {
+        ++m;
+        f *= ts / m;
+    }
+    prm->m_split = m;
     prm->theta = theta;
     prm->p = p;
     prm->n = n;

@@ -7,7 +7,9 @@
 //   * X_j = -i s H_j is assembled in FP64 from FP64 copies of H_0, H_k, H_det and split,
 //   * each product uses an exact FP32 product (hi*hi and its FMA residual), the two cross
 //     terms hi*lo + lo*hi, and an error-free TwoSum accumulation of the high parts,
-//   * the Horner division by i and the identity shift are done in the same pair arithmetic.
+//   * the Horner division by i and the identity shift are done in the same pair arithmetic,
+//   * Horner steps i > m_split use plain FP32 on the hi parts: an error made there reaches T
+//     scaled by ts^m / m! < 2^-6 (m_split is picked with (p, n) from the FP64 norm bound).
 // Only the rounded U_j (the hi part) is stored: propagation, costates and the adjoint stay FP32.
 // The same kernel is used for the recomputation in the backward sweep, so the forward and
 // backward propagators are bitwise identical.
@@ -81,6 +83,30 @@ __device__ __forceinline__ void mm_df(float (&ar)[MT][MT][2], float (&ai)[MT][MT
                 df_mac(ai[i][j][0], ai[i][j][1], a[i].x, a[i].z, b[j].y, b[j].w);
                 df_mac(ai[i][j][0], ai[i][j][1], a[i].y, a[i].w, b[j].x, b[j].z);
             }
+    }
+}
+
+// plain FP32 product of the hi parts (the early Horner steps)
+template <int MT>
+__device__ __forceinline__ void mm_hi(float2 (&acc)[MT][MT], const float4* __restrict__ A, const float4* __restrict__ B,
+                                      int kd, int LD, int ty, int tx) {
+#pragma unroll 2
+    for (int k = 0; k < kd; ++k) {
+        float2 a[MT], b[MT];
+#pragma unroll
+        for (int i = 0; i < MT; ++i) {
+            const float4 v = A[(ty + 16 * i) * LD + k];
+            a[i] = make_float2(v.x, v.y);
+        }
+#pragma unroll
+        for (int i = 0; i < MT; ++i) {
+            const float4 v = B[k * LD + tx + 16 * i];
+            b[i] = make_float2(v.x, v.y);
+        }
+#pragma unroll
+        for (int i = 0; i < MT; ++i)
+#pragma unroll
+            for (int j = 0; j < MT; ++j) cfma(acc[i][j], a[i], b[j]);
     }
 }
 
@@ -172,11 +198,34 @@ k_expm_fwd_split(const DevParams* __restrict__ prm, SysView<float> sys, const do
     __syncthreads();
     float4* zin = Za;
     float4* zout = Zb;
+    const int m_split = prm->m_split;
     for (int i = p - 1; i >= 1; --i) {        // Horner: Z <- I + X Z / i
-        float ar[MT][MT][2], ai[MT][MT][2];
-        df_zero<MT>(ar, ai);
-        mm_df<MT>(ar, ai, X, zin, d, LD, ty, tx);
-        df_store<MT>(zout, ar, ai, i, true, d, LD, ty, tx);
+        if (i > m_split) {
+            float2 acc[MT][MT];
+#pragma unroll
+            for (int a = 0; a < MT; ++a)
+#pragma unroll
+                for (int b = 0; b < MT; ++b) acc[a][b] = make_float2(0.f, 0.f);
+            mm_hi<MT>(acc, X, zin, d, LD, ty, tx);
+            const float ri = 1.0f / (float)i;
+#pragma unroll
+            for (int a = 0; a < MT; ++a)
+#pragma unroll
+                for (int b = 0; b < MT; ++b) {
+                    const int r = ty + 16 * a, c = tx + 16 * b;
+                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (r < d && c < d) {
+                        v.x = fmaf(acc[a][b].x, ri, (r == c) ? 1.0f : 0.0f);
+                        v.y = acc[a][b].y * ri;
+                    }
+                    zout[r * LD + c] = v;
+                }
+        } else {
+            float ar[MT][MT][2], ai[MT][MT][2];
+            df_zero<MT>(ar, ai);
+            mm_df<MT>(ar, ai, X, zin, d, LD, ty, tx);
+            df_store<MT>(zout, ar, ai, i, true, d, LD, ty, tx);
+        }
         __syncthreads();
         float4* t = zin; zin = zout; zout = t;
     }

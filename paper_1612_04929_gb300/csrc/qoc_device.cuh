@@ -41,7 +41,7 @@ struct DevParams {
     int p;          // Taylor order
     int n;          // squaring count
     int err;        // error bits (kErr*)
-    int pad;
+    int m_split;    // Horner steps i <= m_split need hi+lo arithmetic in the split exponential
 };
 
 enum : int { kErrRange = 1, kErrTimeout = 2 };
