@@ -197,13 +197,18 @@ def _dU_list(prob, V, lam, exact: bool, U: np.ndarray) -> list:
 # ----------------------------------------------------------------------------------------
 # cost and gradient by the explicit adjoint
 # ----------------------------------------------------------------------------------------
-def cost_and_grad(prob, u: np.ndarray, exact: bool = True) -> Tuple[float, np.ndarray, np.ndarray]:
+def cost_and_grad(prob, u: np.ndarray, exact: bool = True, slices=None) -> Tuple[float, np.ndarray, np.ndarray]:
     """Total cost, gradient dC/du (M, N) and terms, by one forward sweep and one backward sweep
     of the costate (Sec. II.B reverse mode; Appendix A, Algorithm 3 pattern with sources at every
-    slice)."""
+    slice).  ``slices`` (0-based indices) restricts the gradient to those slices (the other
+    columns are NaN); the costate sweep is unchanged, only the per-slice dU contractions are
+    skipped (used to check large systems at full length)."""
     u = np.asarray(u, np.float64)
     M, N = prob.M, prob.N
+    wanted = None if slices is None else set(int(s) for s in slices)
     grad = np.zeros((M, N))
+    if wanted is not None:
+        grad[:, [j for j in range(N) if j not in wanted]] = np.nan
     acc = np.zeros(3)
     for e in range(prob.E):
         H = slice_hamiltonians(prob, u, e)
@@ -215,10 +220,11 @@ def cost_and_grad(prob, u: np.ndarray, exact: bool = True) -> Tuple[float, np.nd
         src = _sources(prob, psi, oN, oj, 1.0 / prob.E)
         G = src[N].copy()
         for j in range(N, 0, -1):
-            Ubar = G @ psi[j - 1].conj().T
-            _, V, lam = eig[j - 1]
-            for k, dU in enumerate(_dU_list(prob, V, lam, exact, U[j - 1])):
-                grad[k, j - 1] += np.real(np.sum(Ubar.conj() * dU))
+            if wanted is None or (j - 1) in wanted:
+                Ubar = G @ psi[j - 1].conj().T
+                _, V, lam = eig[j - 1]
+                for k, dU in enumerate(_dU_list(prob, V, lam, exact, U[j - 1])):
+                    grad[k, j - 1] += np.real(np.sum(Ubar.conj() * dU))
             G = U[j - 1].conj().T @ G + src[j - 1]
     acc /= prob.E
     c3, c4, g3, g4 = _control_terms(u)

@@ -1,0 +1,523 @@
+// Large-d slice exponentials and their exact adjoint as batched tiled GEMMs.
+//
+// When the matrices of one slice no longer fit one CTA's shared memory (d > 64 FP32, d > 48
+// FP64), every Horner / squaring product of Eqs. 9-10 runs as one launch over all slices of the
+// wave: CTA (tile, item) computes a T x T tile of C_item = A_item B_item with the operands
+// streamed through shared memory in K-chunks.  The same arithmetic as the per-slice kernels:
+//   * FP32 form: X_j in split hi+lo FP32 from an FP64 assembly, pair (double-float) products
+//     for the squarings and for the Horner steps i <= m_split, plain products of the hi parts
+//     for the earlier steps; U_j is the rounded pair;
+//   * adjoint: the block recursion on [[X^dag, Ubar], [0, X^dag]] (exact derivative of the
+//     truncated series), FP32 (FP32 form) or FP64 (FP64 form);
+//   * dC/du_{k,j} = Re tr(Xbar^dag (-i s H_k)) reduced in FP64.
+// Matrices of item b sit at base + b * mstride, row-major d x d.
+#include <utility>
+
+#include "qoc_device.cuh"
+#include "qoc_internal.h"
+
+namespace qoc {
+
+// ------------------------------------------------------------------------------------------
+// element helpers: E = float4 (pair), float2, double2
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ void big_mac_pair(float& hi, float& lo, float ah, float al, float bh, float bl) {
+    const float p = ah * bh;
+    float e = fmaf(ah, bh, -p);
+    e = fmaf(ah, bl, e);
+    e = fmaf(al, bh, e);
+    const float t = hi + p;
+    const float bv = t - hi;
+    lo += (hi - (t - bv)) + (p - bv) + e;
+    hi = t;
+}
+__device__ __forceinline__ void big_norm(float& hi, float& lo) {
+    const float s = hi + lo;
+    lo = lo - (s - hi);
+    hi = s;
+}
+__device__ __forceinline__ void big_div(float& hi, float& lo, float fi) {
+    const float q = hi / fi;
+    const float r = fmaf(-q, fi, hi);
+    lo = (r + lo) / fi;
+    hi = q;
+    big_norm(hi, lo);
+}
+__device__ __forceinline__ void big_add1(float& hi, float& lo) {
+    const float t = hi + 1.0f;
+    const float bv = t - hi;
+    lo += (hi - (t - bv)) + (1.0f - bv);
+    hi = t;
+    big_norm(hi, lo);
+}
+
+template <typename E> __device__ __forceinline__ E ezero();
+template <> __device__ __forceinline__ float4 ezero<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+template <> __device__ __forceinline__ float2 ezero<float2>() { return make_float2(0.f, 0.f); }
+template <> __device__ __forceinline__ double2 ezero<double2>() { return make_double2(0.0, 0.0); }
+
+// ------------------------------------------------------------------------------------------
+// assembly: X = -i s H_j (+ delta_e H_det) from FP64 H; Z = I + X / p
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ void put(float4& o, double x, double y) {
+    o.x = (float)x;
+    o.y = (float)y;
+    o.z = (float)(x - (double)o.x);
+    o.w = (float)(y - (double)o.y);
+}
+__device__ __forceinline__ void put(double2& o, double x, double y) { o = make_double2(x, y); }
+__device__ __forceinline__ void put(float2& o, double x, double y) { o = make_float2((float)x, (float)y); }
+
+template <typename E>
+__global__ void k_big_assemble(const DevParams* __restrict__ prm, BigSys sys, int j0, int wlen, E* __restrict__ X,
+                               E* __restrict__ Z, size_t mstride) {
+    const int item = blockIdx.y, jl = item % wlen, e = item / wlen, j = j0 + jl;
+    const int d = sys.d, M = sys.M;
+    const size_t dd = (size_t)d * d;
+    const double s = prm->s;
+    const double ip = 1.0 / prm->p;
+    const double de = sys.delta ? sys.delta[e] : 0.0;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < dd; idx += (size_t)gridDim.x * blockDim.x) {
+        double2 h = sys.H64[idx];
+        for (int k = 0; k < M; ++k) {
+            const double uk = sys.u[(size_t)k * sys.N + j];
+            const double2 hk = sys.H64[(size_t)(1 + k) * dd + idx];
+            h.x = fma(uk, hk.x, h.x);
+            h.y = fma(uk, hk.y, h.y);
+        }
+        if (sys.has_det) {
+            const double2 hd = sys.H64[(size_t)(M + 1) * dd + idx];
+            h.x = fma(de, hd.x, h.x);
+            h.y = fma(de, hd.y, h.y);
+        }
+        const double xr = s * h.y, xi = -s * h.x;
+        const int a = (int)(idx / d), b = (int)(idx - (size_t)a * d);
+        E xv, zv;
+        put(xv, xr, xi);
+        put(zv, xr * ip + (a == b ? 1.0 : 0.0), xi * ip);
+        X[(size_t)item * mstride + idx] = xv;
+        Z[(size_t)item * mstride + idx] = zv;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// batched product C = A B (T x T tile per CTA), epilogue:
+//   kind 0: C = I + AB / i     (Horner step i)
+//   kind 1: C = AB             (squaring)
+// PAIR: pair arithmetic on float4 operands; HI: plain FP32 product of the hi parts of float4
+// operands (result stored with lo = 0); otherwise plain products of E = float2 / double2.
+// ------------------------------------------------------------------------------------------
+constexpr int KC = 16;
+
+template <typename E, int T, int MODE>   // MODE 0 plain, 1 pair, 2 hi-only (E = float4)
+__global__ void __launch_bounds__(256)
+k_big_mm(int d, const E* __restrict__ A, const E* __restrict__ B, E* __restrict__ Cm, size_t mstride, int kind, int i) {
+    constexpr int MT = T / 16;
+    __shared__ __align__(16) E As[T][KC + 1];
+    __shared__ __align__(16) E Bs[KC][T + 1];
+    const int item = blockIdx.y;
+    const int ntn = (d + T - 1) / T;
+    const int tm = blockIdx.x / ntn, tn = blockIdx.x - tm * ntn;
+    const int r0 = tm * T, c0 = tn * T;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const E* Ai = A + (size_t)item * mstride;
+    const E* Bi = B + (size_t)item * mstride;
+    float ar[MT][MT][2], ai_[MT][MT][2];     // pair accumulators (re hi/lo, im hi/lo)
+    E acc[MT][MT];
+#pragma unroll
+    for (int x = 0; x < MT; ++x)
+#pragma unroll
+        for (int y = 0; y < MT; ++y) {
+            ar[x][y][0] = ar[x][y][1] = ai_[x][y][0] = ai_[x][y][1] = 0.f;
+            acc[x][y] = ezero<E>();
+        }
+    for (int k0 = 0; k0 < d; k0 += KC) {
+        for (int idx = tid; idx < T * KC; idx += 256) {
+            const int r = idx / KC, k = idx - r * KC;
+            const int gr = r0 + r, gk = k0 + k;
+            As[r][k] = (gr < d && gk < d) ? Ai[(size_t)gr * d + gk] : ezero<E>();
+        }
+        for (int idx = tid; idx < KC * T; idx += 256) {
+            const int k = idx / T, c = idx - k * T;
+            const int gk = k0 + k, gc = c0 + c;
+            Bs[k][c] = (gk < d && gc < d) ? Bi[(size_t)gk * d + gc] : ezero<E>();
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int k = 0; k < KC; ++k) {
+            E a[MT], b[MT];
+#pragma unroll
+            for (int x = 0; x < MT; ++x) a[x] = As[ty + 16 * x][k];
+#pragma unroll
+            for (int y = 0; y < MT; ++y) b[y] = Bs[k][tx + 16 * y];
+#pragma unroll
+            for (int x = 0; x < MT; ++x)
+#pragma unroll
+                for (int y = 0; y < MT; ++y) {
+                    if constexpr (MODE == 1) {
+                        const float4 av = *reinterpret_cast<const float4*>(&a[x]);
+                        const float4 bv = *reinterpret_cast<const float4*>(&b[y]);
+                        big_mac_pair(ar[x][y][0], ar[x][y][1], av.x, av.z, bv.x, bv.z);
+                        big_mac_pair(ar[x][y][0], ar[x][y][1], -av.y, -av.w, bv.y, bv.w);
+                        big_mac_pair(ai_[x][y][0], ai_[x][y][1], av.x, av.z, bv.y, bv.w);
+                        big_mac_pair(ai_[x][y][0], ai_[x][y][1], av.y, av.w, bv.x, bv.z);
+                    } else if constexpr (MODE == 2) {
+                        const float4 av = *reinterpret_cast<const float4*>(&a[x]);
+                        const float4 bv = *reinterpret_cast<const float4*>(&b[y]);
+                        ar[x][y][0] = fmaf(av.x, bv.x, ar[x][y][0]);
+                        ar[x][y][0] = fmaf(-av.y, bv.y, ar[x][y][0]);
+                        ai_[x][y][0] = fmaf(av.x, bv.y, ai_[x][y][0]);
+                        ai_[x][y][0] = fmaf(av.y, bv.x, ai_[x][y][0]);
+                    } else {
+                        cfma(acc[x][y], a[x], b[y]);
+                    }
+                }
+        }
+        __syncthreads();
+    }
+    E* Ci = Cm + (size_t)item * mstride;
+#pragma unroll
+    for (int x = 0; x < MT; ++x)
+#pragma unroll
+        for (int y = 0; y < MT; ++y) {
+            const int r = r0 + ty + 16 * x, c = c0 + tx + 16 * y;
+            if (r >= d || c >= d) continue;
+            const bool diag = (kind == 0) && (r == c);
+            E out;
+            if constexpr (MODE == 1) {
+                float rh = ar[x][y][0], rl = ar[x][y][1], ih = ai_[x][y][0], il = ai_[x][y][1];
+                big_norm(rh, rl);
+                big_norm(ih, il);
+                if (kind == 0 && i > 1) {
+                    big_div(rh, rl, (float)i);
+                    big_div(ih, il, (float)i);
+                }
+                if (diag) big_add1(rh, rl);
+                float4 o = make_float4(rh, ih, rl, il);
+                out = *reinterpret_cast<E*>(&o);
+            } else if constexpr (MODE == 2) {
+                const float ri = 1.0f / (float)i;
+                float4 o = make_float4(fmaf(ar[x][y][0], ri, diag ? 1.0f : 0.0f), ai_[x][y][0] * ri, 0.f, 0.f);
+                out = *reinterpret_cast<E*>(&o);
+            } else {
+                out = acc[x][y];
+                if (kind == 0) {
+                    using S = decltype(out.x);
+                    const S ri = S(1) / S(i);
+                    out.x = out.x * ri + (diag ? S(1) : S(0));
+                    out.y = out.y * ri;
+                }
+            }
+            Ci[(size_t)r * d + c] = out;
+        }
+}
+
+// U_j (rounded) and U_j^dag into the propagator buffer (U at 0, U^dag at ustride / 2)
+template <typename E, typename C>
+__device__ __forceinline__ C to_c(const E v);
+template <> __device__ __forceinline__ float2 to_c<float4, float2>(const float4 v) { return make_float2(v.x + v.z, v.y + v.w); }
+template <> __device__ __forceinline__ float2 to_c<float2, float2>(const float2 v) { return v; }
+template <> __device__ __forceinline__ double2 to_c<double2, double2>(const double2 v) { return v; }
+
+template <typename E, typename C>
+__global__ void k_big_store_u(int d, const E* __restrict__ Z, size_t mstride, C* __restrict__ Ubuf, long long ustride,
+                              int wlen, int wmax) {
+    const int item = blockIdx.y, jl = item % wlen, e = item / wlen;
+    const size_t dd = (size_t)d * d;
+    C* U = Ubuf + ((size_t)e * wmax + jl) * ustride;
+    C* UH = U + ustride / 2;
+    const E* Zi = Z + (size_t)item * mstride;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < dd; idx += (size_t)gridDim.x * blockDim.x) {
+        const int a = (int)(idx / d), b = (int)(idx - (size_t)a * d);
+        U[idx] = to_c<E, C>(Zi[idx]);
+        C h = to_c<E, C>(Zi[(size_t)b * d + a]);
+        h.y = -h.y;
+        UH[idx] = h;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// adjoint
+// ------------------------------------------------------------------------------------------
+// XH = X^dag with X = -i s H_j assembled in the compute precision R (as the per-slice adjoint
+// kernel does); Ubar = G_j Psi_{j-1}^dag from the panel-layout states and costates;
+// Z11 = I + XH / p; Z12 = Ubar / p.
+template <typename R>
+__global__ void k_big_adj_init(const DevParams* __restrict__ prm, SysView<R> sys, StateView<R> sv, int j0, int wlen,
+                               const C_t<R>* __restrict__ states, const C_t<R>* __restrict__ Gbuf, int wmax,
+                               C_t<R>* __restrict__ XH, C_t<R>* __restrict__ Ubar, C_t<R>* __restrict__ Z11,
+                               C_t<R>* __restrict__ Z12, size_t mstride) {
+    using C = C_t<R>;
+    const int item = blockIdx.y, jl = item % wlen, e = item / wlen, j = j0 + jl;
+    const int d = sys.d, M = sys.M;
+    const size_t dd = (size_t)d * d, slice = sv.slice();
+    const R s = (R)prm->s;
+    const R ip = R(1) / R(prm->p);
+    const R de = sys.delta ? (R)sys.delta[e] : R(0);
+    const C* Gj = Gbuf + ((size_t)e * wmax + jl) * slice;
+    const C* Pj = states + ((size_t)e * (wmax + 1) + jl) * slice;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < dd; idx += (size_t)gridDim.x * blockDim.x) {
+        const int a = (int)(idx / d), b = (int)(idx - (size_t)a * d);
+        // X[b][a] = -i s H[b][a]  ->  XH[a][b] = conj(X[b][a])
+        const size_t o = (size_t)b * d + a;
+        C h = sys.H0[o];
+        for (int k = 0; k < M; ++k) {
+            const R uk = (R)sys.u[(size_t)k * sys.N + j];
+            const C hk = sys.Hk[(size_t)k * dd + o];
+            h.x = fma(uk, hk.x, h.x);
+            h.y = fma(uk, hk.y, h.y);
+        }
+        if (sys.Hdet) {
+            const C hd = sys.Hdet[o];
+            h.x = fma(de, hd.x, h.x);
+            h.y = fma(de, hd.y, h.y);
+        }
+        C xh;
+        xh.x = s * h.y;      // X = (s hi, -s hr); conj -> (s hi, s hr)
+        xh.y = s * h.x;
+        C ub = czero<C>();
+        for (int sc = 0; sc < sv.Spad; ++sc) {
+            const size_t pa = (size_t)(sc / sv.cb) * sv.pstride + (size_t)a * sv.cb + (sc % sv.cb);
+            const size_t pb = (size_t)(sc / sv.cb) * sv.pstride + (size_t)b * sv.cb + (sc % sv.cb);
+            cfma_bcj(ub, Gj[pa], Pj[pb]);
+        }
+        const size_t base = (size_t)item * mstride + idx;
+        XH[base] = xh;
+        Ubar[base] = ub;
+        C z1, z2;
+        z1.x = xh.x * ip + (a == b ? R(1) : R(0));
+        z1.y = xh.y * ip;
+        z2.x = ub.x * ip;
+        z2.y = ub.y * ip;
+        Z11[base] = z1;
+        Z12[base] = z2;
+    }
+}
+
+// P11 = A11 B11 ; P12 = A11 B12 + A12 B11 ; kind 0: Horner (I + P11 / i, P12 / i), 1: plain
+template <typename C, int T>
+__global__ void __launch_bounds__(256)
+k_big_mm_blk(int d, const C* __restrict__ A11, const C* __restrict__ A12, const C* __restrict__ B11,
+             const C* __restrict__ B12, C* __restrict__ O11, C* __restrict__ O12, size_t mstride, int kind, int i) {
+    constexpr int MT = T / 16;
+    __shared__ __align__(16) C A1s[T][KC + 1];
+    __shared__ __align__(16) C A2s[T][KC + 1];
+    __shared__ __align__(16) C B1s[KC][T + 1];
+    __shared__ __align__(16) C B2s[KC][T + 1];
+    const int item = blockIdx.y;
+    const int ntn = (d + T - 1) / T;
+    const int tm = blockIdx.x / ntn, tn = blockIdx.x - tm * ntn;
+    const int r0 = tm * T, c0 = tn * T;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const size_t off = (size_t)item * mstride;
+    C acc1[MT][MT], acc2[MT][MT];
+#pragma unroll
+    for (int x = 0; x < MT; ++x)
+#pragma unroll
+        for (int y = 0; y < MT; ++y) acc1[x][y] = acc2[x][y] = czero<C>();
+    for (int k0 = 0; k0 < d; k0 += KC) {
+        for (int idx = tid; idx < T * KC; idx += 256) {
+            const int r = idx / KC, k = idx - r * KC;
+            const int gr = r0 + r, gk = k0 + k;
+            const bool ok = gr < d && gk < d;
+            A1s[r][k] = ok ? A11[off + (size_t)gr * d + gk] : czero<C>();
+            A2s[r][k] = ok ? A12[off + (size_t)gr * d + gk] : czero<C>();
+        }
+        for (int idx = tid; idx < KC * T; idx += 256) {
+            const int k = idx / T, c = idx - k * T;
+            const int gk = k0 + k, gc = c0 + c;
+            const bool ok = gk < d && gc < d;
+            B1s[k][c] = ok ? B11[off + (size_t)gk * d + gc] : czero<C>();
+            B2s[k][c] = ok ? B12[off + (size_t)gk * d + gc] : czero<C>();
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int k = 0; k < KC; ++k) {
+            C a1[MT], a2[MT], b1[MT], b2[MT];
+#pragma unroll
+            for (int x = 0; x < MT; ++x) {
+                a1[x] = A1s[ty + 16 * x][k];
+                a2[x] = A2s[ty + 16 * x][k];
+            }
+#pragma unroll
+            for (int y = 0; y < MT; ++y) {
+                b1[y] = B1s[k][tx + 16 * y];
+                b2[y] = B2s[k][tx + 16 * y];
+            }
+#pragma unroll
+            for (int x = 0; x < MT; ++x)
+#pragma unroll
+                for (int y = 0; y < MT; ++y) {
+                    cfma(acc1[x][y], a1[x], b1[y]);
+                    cfma(acc2[x][y], a1[x], b2[y]);
+                    cfma(acc2[x][y], a2[x], b1[y]);
+                }
+        }
+        __syncthreads();
+    }
+    using S = decltype(acc1[0][0].x);
+    const S ri = (kind == 0) ? S(1) / S(i) : S(1);
+#pragma unroll
+    for (int x = 0; x < MT; ++x)
+#pragma unroll
+        for (int y = 0; y < MT; ++y) {
+            const int r = r0 + ty + 16 * x, c = c0 + tx + 16 * y;
+            if (r >= d || c >= d) continue;
+            C v1 = acc1[x][y], v2 = acc2[x][y];
+            v1.x = v1.x * ri + ((kind == 0 && r == c) ? S(1) : S(0));
+            v1.y *= ri;
+            v2.x *= ri;
+            v2.y *= ri;
+            O11[off + (size_t)r * d + c] = v1;
+            O12[off + (size_t)r * d + c] = v2;
+        }
+}
+
+// dC/du_{k,j} = s sum_ab (Xbar_re Hk_im - Xbar_im Hk_re), one CTA per (item, k)
+template <typename R>
+__global__ void __launch_bounds__(256)
+k_big_grad(const DevParams* __restrict__ prm, SysView<R> sys, int j0, int wlen, const C_t<R>* __restrict__ Xbar,
+           size_t mstride, double* __restrict__ gpart) {
+    __shared__ double red[32];
+    const int item = blockIdx.x, k = blockIdx.y, jl = item % wlen, e = item / wlen, j = j0 + jl;
+    const int d = sys.d;
+    const size_t dd = (size_t)d * d;
+    const C_t<R>* xb = Xbar + (size_t)item * mstride;
+    const C_t<R>* hk = sys.Hk + (size_t)k * dd;
+    double v = 0.0;
+    for (size_t idx = threadIdx.x; idx < dd; idx += blockDim.x)
+        v += (double)xb[idx].x * (double)hk[idx].y - (double)xb[idx].y * (double)hk[idx].x;
+    v = block_sum(v, red);
+    if (threadIdx.x == 0) gpart[((size_t)e * sys.M + k) * sys.N + j] = prm->s * v;
+}
+
+// ------------------------------------------------------------------------------------------
+// launchers
+// ------------------------------------------------------------------------------------------
+static int big_tile(int d) { return d <= 96 ? 32 : 64; }
+
+template <typename E, int MODE>
+static cudaError_t mm_launch(int d, int items, const E* A, const E* B, E* Cm, size_t mstride, int kind, int i,
+                             cudaStream_t st) {
+    const int T = big_tile(d);
+    const int nt = ((d + T - 1) / T) * ((d + T - 1) / T);
+    if (T == 32) k_big_mm<E, 32, MODE><<<dim3(nt, items), 256, 0, st>>>(d, A, B, Cm, mstride, kind, i);
+    else k_big_mm<E, 64, MODE><<<dim3(nt, items), 256, 0, st>>>(d, A, B, Cm, mstride, kind, i);
+    return cudaGetLastError();
+}
+
+static int ew_blocks(size_t dd) {
+    const size_t b = (dd + 255) / 256;
+    return (int)(b < 64 ? b : 64);
+}
+
+template <typename R>
+cudaError_t launch_big_expm(const BigArgs<R>& a, int p, int n, int m_split, bool split, cudaStream_t st, int* launches) {
+    const int d = a.d, items = a.wlen * a.E;
+    const size_t dd = (size_t)d * d;
+    const int eb = ew_blocks(dd);
+    cudaError_t err;
+    auto count = [&]() { if (launches) ++*launches; };
+    if (sizeof(R) == 4 && split) {
+        float4* X = reinterpret_cast<float4*>(a.scratch);
+        float4* Za = X + (size_t)items * a.mstride;
+        float4* Zb = Za + (size_t)items * a.mstride;
+        k_big_assemble<float4><<<dim3(eb, items), 256, 0, st>>>(a.prm, a.bsys, a.j0, a.wlen, X, Za, a.mstride);
+        count();
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+        float4 *zin = Za, *zout = Zb;
+        for (int i = p - 1; i >= 1; --i) {
+            err = (i > m_split) ? mm_launch<float4, 2>(d, items, X, zin, zout, a.mstride, 0, i, st)
+                                : mm_launch<float4, 1>(d, items, X, zin, zout, a.mstride, 0, i, st);
+            count();
+            if (err != cudaSuccess) return err;
+            std::swap(zin, zout);
+        }
+        for (int m = 0; m < n; ++m) {
+            if ((err = mm_launch<float4, 1>(d, items, zin, zin, zout, a.mstride, 1, 0, st)) != cudaSuccess) return err;
+            count();
+            std::swap(zin, zout);
+        }
+        k_big_store_u<float4, float2><<<dim3(eb, items), 256, 0, st>>>(d, zin, a.mstride,
+                                                                         reinterpret_cast<float2*>(a.Ubuf), a.ustride,
+                                                                         a.wlen, a.wmax);
+        count();
+        return cudaGetLastError();
+    }
+    using C = C_t<R>;
+    C* X = reinterpret_cast<C*>(a.scratch);
+    C* Za = X + (size_t)items * a.mstride;
+    C* Zb = Za + (size_t)items * a.mstride;
+    k_big_assemble<C><<<dim3(eb, items), 256, 0, st>>>(a.prm, a.bsys, a.j0, a.wlen, X, Za, a.mstride);
+    count();
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    C *zin = Za, *zout = Zb;
+    for (int i = p - 1; i >= 1; --i) {
+        if ((err = mm_launch<C, 0>(d, items, X, zin, zout, a.mstride, 0, i, st)) != cudaSuccess) return err;
+        count();
+        std::swap(zin, zout);
+    }
+    for (int m = 0; m < n; ++m) {
+        if ((err = mm_launch<C, 0>(d, items, zin, zin, zout, a.mstride, 1, 0, st)) != cudaSuccess) return err;
+        count();
+        std::swap(zin, zout);
+    }
+    k_big_store_u<C, C><<<dim3(eb, items), 256, 0, st>>>(d, zin, a.mstride, reinterpret_cast<C*>(a.Ubuf), a.ustride,
+                                                          a.wlen, a.wmax);
+    count();
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_big_adj(const BigArgs<R>& a, const SysView<R>& sys, const StateView<R>& sv, const C_t<R>* states,
+                           const C_t<R>* Gbuf, double* gpart, int p, int n, cudaStream_t st, int* launches) {
+    using C = C_t<R>;
+    const int d = a.d, items = a.wlen * a.E;
+    const size_t dd = (size_t)d * d, ms = a.mstride;
+    const int eb = ew_blocks(dd);
+    auto count = [&]() { if (launches) ++*launches; };
+    C* XH = reinterpret_cast<C*>(a.scratch);
+    C* Ub = XH + (size_t)items * ms;
+    C* Z11a = Ub + (size_t)items * ms;
+    C* Z12a = Z11a + (size_t)items * ms;
+    C* Z11b = Z12a + (size_t)items * ms;
+    C* Z12b = Z11b + (size_t)items * ms;
+    k_big_adj_init<R><<<dim3(eb, items), 256, 0, st>>>(a.prm, sys, sv, a.j0, a.wlen, states, Gbuf, a.wmax, XH, Ub,
+                                                        Z11a, Z12a, ms);
+    count();
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    const int T = (sizeof(C) == 16) ? 32 : big_tile(d);
+    const int nt = ((d + T - 1) / T) * ((d + T - 1) / T);
+    C *z11 = Z11a, *z12 = Z12a, *o11 = Z11b, *o12 = Z12b;
+    auto blk = [&](const C* A11, const C* A12, const C* B11, const C* B12, int kind, int i) {
+        if constexpr (sizeof(C) == 16) {   // 16-byte elements: 32 x 32 tiles keep the static SMEM < 48 KB
+            k_big_mm_blk<C, 32><<<dim3(nt, items), 256, 0, st>>>(d, A11, A12, B11, B12, o11, o12, ms, kind, i);
+        } else {
+            if (T == 32) k_big_mm_blk<C, 32><<<dim3(nt, items), 256, 0, st>>>(d, A11, A12, B11, B12, o11, o12, ms, kind, i);
+            else k_big_mm_blk<C, 64><<<dim3(nt, items), 256, 0, st>>>(d, A11, A12, B11, B12, o11, o12, ms, kind, i);
+        }
+        count();
+        std::swap(z11, o11);
+        std::swap(z12, o12);
+        return cudaGetLastError();
+    };
+    for (int i = p - 1; i >= 1; --i)
+        if ((err = blk(XH, Ub, z11, z12, 0, i)) != cudaSuccess) return err;
+    for (int m = 0; m < n; ++m)
+        if ((err = blk(z11, z12, z11, z12, 1, 0)) != cudaSuccess) return err;
+    if (sys.M > 0) {
+        k_big_grad<R><<<dim3(items, sys.M), 256, 0, st>>>(a.prm, sys, a.j0, a.wlen, z12, ms, gpart);
+        count();
+    }
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_big_expm<float>(const BigArgs<float>&, int, int, int, bool, cudaStream_t, int*);
+template cudaError_t launch_big_expm<double>(const BigArgs<double>&, int, int, int, bool, cudaStream_t, int*);
+template cudaError_t launch_big_adj<float>(const BigArgs<float>&, const SysView<float>&, const StateView<float>&,
+                                           const float2*, const float2*, double*, int, int, cudaStream_t, int*);
+template cudaError_t launch_big_adj<double>(const BigArgs<double>&, const SysView<double>&, const StateView<double>&,
+                                            const double2*, const double2*, double*, int, int, cudaStream_t, int*);
+
+}  // namespace qoc

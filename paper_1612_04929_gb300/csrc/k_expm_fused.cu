@@ -176,10 +176,16 @@ k_expm_fwd(const DevParams* __restrict__ prm, SysView<R> sys, int j0, C_t<R>* __
         __syncthreads();
         C* t = zin; zin = zout; zout = t;
     }
+    // a slice holds U_j at offset 0 and U_j^dag at offset ustride / 2 (rows of U^dag are what the
+    // backward costate sweep streams)
     C* U = Ubuf + ((size_t)e * wmax + jl) * ustride;
+    C* UH = U + ustride / 2;
     for (int idx = tid; idx < d * d; idx += blockDim.x) {
         const int a = idx / d, b = idx - a * d;
         U[idx] = zin[a * LD + b];
+        C h = zin[b * LD + a];
+        h.y = -h.y;
+        UH[idx] = h;
     }
 }
 
@@ -308,6 +314,11 @@ static size_t fused_smem(int MT, int nmat) {
 }
 
 template <typename R>
+size_t fused_adj_smem(int d) {
+    return fused_smem<R>((d + 15) / 16, 6);
+}
+
+template <typename R>
 int fused_max_d() {
     for (int MT = 5; MT >= 1; --MT)
         if (fused_smem<R>(MT, 6) <= kMaxDynSmem) return 16 * MT;
@@ -362,6 +373,8 @@ cudaError_t launch_expm_adj_fused(const DevParams* prm, const SysView<R>& sys, c
     }
 }
 
+template size_t fused_adj_smem<float>(int);
+template size_t fused_adj_smem<double>(int);
 template int fused_max_d<float>();
 template int fused_max_d<double>();
 template cudaError_t launch_expm_fwd_fused<float>(const DevParams*, const SysView<float>&, int, int, int, float2*, long long, int, cudaStream_t);

@@ -237,11 +237,15 @@ k_expm_fwd_split(const DevParams* __restrict__ prm, SysView<float> sys, const do
         __syncthreads();
         float4* t = zin; zin = zout; zout = t;
     }
+    // U_j at offset 0, U_j^dag at offset ustride / 2; the pair is rounded to FP32
     float2* U = Ubuf + ((size_t)e * wmax + jl) * ustride;
+    float2* UH = U + ustride / 2;
     for (int idx = tid; idx < d * d; idx += blockDim.x) {
         const int a = idx / d, b = idx - a * d;
         const float4 z = zin[a * LD + b];
-        U[idx] = make_float2(z.x + z.z, z.y + z.w);   // round the pair to FP32
+        U[idx] = make_float2(z.x + z.z, z.y + z.w);
+        const float4 h = zin[b * LD + a];
+        UH[idx] = make_float2(h.x + h.z, -(h.y + h.w));
     }
 }
 

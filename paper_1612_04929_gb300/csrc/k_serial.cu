@@ -96,73 +96,59 @@ __device__ __forceinline__ void ring_issue(unsigned char* slot, const void* gsrc
     for (size_t off = threadIdx.x * 16; off < bytes; off += blockDim.x * 16) cp_async16(slot + off, g + off);
 }
 
-// y = U x on one d x cb panel: g lanes per output sum b = q, q + g, ... then a shuffle reduction
-template <typename C, typename K>
-__device__ __forceinline__ void mv_U(const C* __restrict__ U, const K* __restrict__ x, K* __restrict__ y, int d,
-                                     int cb, int g) {
+// One step y = Mx x (+ add) on a d x cb panel.  g lanes per output (contiguous in a warp) sum
+// b = q, q + g, ... of row a of Mx (contiguous reads: the forward sweep streams U_j, the backward
+// sweep U_j^dag), then a shuffle reduction combines them.  Lane q = 0 owns the output: it adds
+// the source, normalises the pair, keeps it for the next step and hands it to `emit`.
+template <typename C, typename K, typename Emit>
+__device__ __forceinline__ void sweep_step(const C* __restrict__ Mx, const K* __restrict__ x, K* __restrict__ y,
+                                           const C* __restrict__ add, int d, int cb, int g, Emit emit) {
     const int O = d * cb;
     const int ngroups = blockDim.x / g;
     const int gi = threadIdx.x / g, q = threadIdx.x - gi * g;
     for (int base = 0; base < O; base += ngroups) {
         const int o = base + gi;
         K acc = kzero<K>();
-        int a = 0, sl = 0;
         if (o < O) {
-            a = o / cb;
-            sl = o - a * cb;
-            const C* Ur = U + (size_t)a * d;
-            for (int b = q; b < d; b += g) kmac(acc, Ur[b], x[b * cb + sl]);
+            const int a = o / cb, sl = o - a * cb;
+            const C* Mr = Mx + (size_t)a * d;
+            for (int b = q; b < d; b += g) kmac(acc, Mr[b], x[b * cb + sl]);
         }
         for (int off = g >> 1; off > 0; off >>= 1) kadd(acc, kshfl_xor(acc, off));
         if (o < O && q == 0) {
+            if (add) kadd(acc, kfrom(add[o]));
             knorm(acc);
-            y[a * cb + sl] = acc;
+            y[o] = acc;
+            emit(o, acc);
         }
     }
 }
 
-// y = U^dag x + add: lanes over outputs (contiguous reads of U[b][a]); for small panels the b
-// range is split over the warps and the partials summed through `red`
-template <typename C, typename K>
-__device__ __forceinline__ void mv_UH(const C* __restrict__ U, const K* __restrict__ x, K* __restrict__ y,
-                                      const C* __restrict__ add, int d, int cb, K* __restrict__ red) {
+// lanes per output and block size: minimise the issue time of one step on one SM
+// (passes x warps per scheduler x instructions per lane)
+static void pick_sweep_shape(int d, int cb, bool pair, int& g, int& threads) {
     const int O = d * cb;
-    if (O >= (int)blockDim.x) {
-        for (int o = threadIdx.x; o < O; o += blockDim.x) {
-            const int a = o / cb, sl = o - a * cb;
-            K acc = kzero<K>();
-            for (int b = 0; b < d; ++b) kmac_cj(acc, U[(size_t)b * d + a], x[b * cb + sl]);
-            if (add) kadd(acc, kfrom(add[o]));
-            knorm(acc);
-            y[o] = acc;
+    long best = -1;
+    for (int gg = 1, lg = 0; gg <= 32; gg <<= 1, ++lg) {
+        int thr = ((O * gg + 31) / 32) * 32;
+        thr = thr > 1024 ? 1024 : thr;
+        const int groups = thr / gg;
+        const int passes = (O + groups - 1) / groups;
+        const int wps = (thr / 32 + 3) / 4;
+        const long cost = (long)passes * wps * (((d + gg - 1) / gg) * (pair ? 44 : 10) + 12 * lg);
+        if (best < 0 || cost < best) {
+            best = cost;
+            g = gg;
+            threads = thr;
         }
-        __syncthreads();
-        return;
     }
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
-    const int chunk = (d + nw - 1) / nw;
-    const int b0 = w * chunk, b1 = min(d, b0 + chunk);
-    for (int o = l; o < O; o += 32) {
-        const int a = o / cb, sl = o - a * cb;
-        K acc = kzero<K>();
-        for (int b = b0; b < b1; ++b) kmac_cj(acc, U[(size_t)b * d + a], x[b * cb + sl]);
-        red[w * O + o] = acc;
-    }
-    __syncthreads();
-    for (int o = threadIdx.x; o < O; o += blockDim.x) {
-        K acc = add ? kfrom(add[o]) : kzero<K>();
-        for (int ww = 0; ww < nw; ++ww) kadd(acc, red[ww * O + o]);
-        knorm(acc);
-        y[o] = acc;
-    }
-    __syncthreads();
 }
 
 // ------------------------------------------------------------------------------------------
 // forward propagation (mode 0) and checkpoint replay (mode 1)
 // ------------------------------------------------------------------------------------------
 template <typename R, int RING>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(1024)
 k_chain(int d, StateView<R> sv, int wlen, int seg, int mode, K_t<R>* __restrict__ ckpt, size_t ck_estride, int seg0,
         int nseg_total, const C_t<R>* __restrict__ Ubuf, long long ustride, int wmax, C_t<R>* __restrict__ states,
         int g) {
@@ -173,7 +159,7 @@ k_chain(int d, StateView<R> sv, int wlen, int seg, int mode, K_t<R>* __restrict_
     const size_t slice = sv.slice(), panel = (size_t)d * cb;
     const size_t ub = ring_bytes((size_t)d * d, sizeof(C));
     unsigned char* ring = smraw;
-    K* xa = reinterpret_cast<K*>(smraw + RING * ub);
+    K* xa = reinterpret_cast<K*>(smraw + RING * ub);   // RING 0: no ring, rows read from global
     K* xb = xa + panel;
     const int t0 = (mode == 0) ? 0 : z * seg;
     const int t1 = (mode == 0) ? wlen : min(wlen, t0 + seg);
@@ -187,57 +173,64 @@ k_chain(int d, StateView<R> sv, int wlen, int seg, int mode, K_t<R>* __restrict_
         sdst[(size_t)t0 * slice + i] = kround(v);
     }
     const C* Ue = Ubuf + (size_t)e * wmax * ustride;
-#pragma unroll 1
-    for (int t = 0; t < RING - 1; ++t) {
-        if (t0 + t < t1) ring_issue(ring + t * ub, Ue + (size_t)(t0 + t) * ustride, ub);
-        cp_async_commit();
-    }
-#pragma unroll 1
-    for (int t = t0; t < t1; ++t) {
-        const int k = t - t0;
-        const int tn = t + RING - 1;
-        if (tn < t1) ring_issue(ring + ((k + RING - 1) % RING) * ub, Ue + (size_t)tn * ustride, ub);
-        cp_async_commit();
-        cp_async_wait<RING - 1>();
-        __syncthreads();
-        const C* U = reinterpret_cast<const C*>(ring + (k % RING) * ub);
-        mv_U<C, K>(U, xa, xb, d, cb, g);
-        __syncthreads();
+    auto emit_for = [&](int t) {
         C* dst = sdst + (size_t)(t + 1) * slice;
-        for (int i = tid; i < (int)panel; i += blockDim.x) dst[i] = kround(xb[i]);
-        if (mode == 0 && (t + 1) % seg == 0) {
-            const int slot = seg0 + (t + 1) / seg;
-            if (slot < nseg_total) {
-                K* c = ck_e + (size_t)slot * slice + (size_t)kb * sv.pstride;
-                for (int i = tid; i < (int)panel; i += blockDim.x) c[i] = xb[i];
-            }
+        K* ckd = nullptr;
+        if (mode == 0 && (t + 1) % seg == 0 && seg0 + (t + 1) / seg < nseg_total)
+            ckd = ck_e + (size_t)(seg0 + (t + 1) / seg) * slice + (size_t)kb * sv.pstride;
+        return [=](int o, const K& v) {
+            dst[o] = kround(v);
+            if (ckd) ckd[o] = v;
+        };
+    };
+    if constexpr (RING == 0) {          // slice too large for SMEM: rows streamed from global/L2
+#pragma unroll 1
+        for (int t = t0; t < t1; ++t) {
+            __syncthreads();
+            sweep_step<C, K>(Ue + (size_t)t * ustride, xa, xb, nullptr, d, cb, g, emit_for(t));
+            K* tmp = xa; xa = xb; xb = tmp;
         }
-        K* tmp = xa; xa = xb; xb = tmp;
+    } else if constexpr (RING == 1) {   // one slot: synchronous copy
+#pragma unroll 1
+        for (int t = t0; t < t1; ++t) {
+            __syncthreads();            // previous step done with the slot
+            ring_issue(ring, Ue + (size_t)t * ustride, ub);
+            cp_async_commit();
+            cp_async_wait<0>();
+            __syncthreads();
+            sweep_step<C, K>(reinterpret_cast<const C*>(ring), xa, xb, nullptr, d, cb, g, emit_for(t));
+            K* tmp = xa; xa = xb; xb = tmp;
+        }
+    } else {
+#pragma unroll 1
+        for (int t = 0; t < RING - 1; ++t) {
+            if (t0 + t < t1) ring_issue(ring + t * ub, Ue + (size_t)(t0 + t) * ustride, ub);
+            cp_async_commit();
+        }
+#pragma unroll 1
+        for (int t = t0; t < t1; ++t) {
+            const int k = t - t0;
+            cp_async_wait<(RING >= 2 ? RING - 2 : 0)>();   // the copy of step k has landed ...
+            __syncthreads();                                // ... for every thread; step k - 1 is finished
+            const int tn = t + RING - 1;
+            if (tn < t1) ring_issue(ring + ((k + RING - 1) % RING) * ub, Ue + (size_t)tn * ustride, ub);
+            cp_async_commit();
+            sweep_step<C, K>(reinterpret_cast<const C*>(ring + (k % RING) * ub), xa, xb, nullptr, d, cb, g, emit_for(t));
+            K* tmp = xa; xa = xb; xb = tmp;
+        }
     }
-}
-
-static int pick_group(int d, int cb, int threads, int term_cost) {
-    // minimise ceil(O / (threads / g)) * (term_cost ceil(d / g) + 8 log2 g) over g in {1, ..., 32}
-    const int O = d * cb;
-    int best = 1;
-    long best_cost = -1;
-    for (int g = 1, lg = 0; g <= 32; g <<= 1, ++lg) {
-        const long iters = (O + threads / g - 1) / (threads / g);
-        const long cost = iters * ((long)term_cost * ((d + g - 1) / g) + 8 * lg);
-        if (best_cost < 0 || cost < best_cost) { best_cost = cost; best = g; }
-    }
-    return best;
 }
 
 template <typename R, int RING>
 static cudaError_t chain_ring(const ChainArgs<R>& a, size_t smem, cudaStream_t st) {
     cudaError_t err = cudaFuncSetAttribute(k_chain<R, RING>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    const int g = pick_group(a.d, a.sv.cb, 256, sizeof(R) == 4 ? 10 : 4);
+    int g = 1, threads = 256;
+    pick_sweep_shape(a.d, a.sv.cb, sizeof(R) == 4, g, threads);
     const int nz = a.mode == 0 ? 1 : (a.wlen + a.seg - 1) / a.seg;
-    k_chain<R, RING><<<dim3(a.sv.ncb, a.E, nz), 256, smem, st>>>(a.d, a.sv, a.wlen, a.seg, a.mode, a.ckpt, a.ck_estride,
-                                                                  a.seg0, a.nseg_total, a.Ubuf, a.ustride, a.wmax,
-                                                                  a.states, g);
+    k_chain<R, RING><<<dim3(a.sv.ncb, a.E, nz), threads, smem, st>>>(a.d, a.sv, a.wlen, a.seg, a.mode, a.ckpt,
+                                                                      a.ck_estride, a.seg0, a.nseg_total, a.Ubuf,
+                                                                      a.ustride, a.wmax, a.states, g);
     return cudaGetLastError();
 }
 
@@ -245,23 +238,25 @@ template <typename R>
 cudaError_t launch_chain(const ChainArgs<R>& a, cudaStream_t st) {
     const size_t ub = ring_bytes((size_t)a.d * a.d, sizeof(C_t<R>));
     const size_t xs = 2 * (size_t)a.d * a.sv.cb * sizeof(K_t<R>);
-    for (int ring : {4, 2, 1}) {
+    if (xs > kMaxDynSmem) return cudaErrorInvalidValue;
+    for (int ring : {8, 4, 2, 1}) {
         const size_t smem = ring * ub + xs;
         if (smem > kMaxDynSmem) continue;
+        if (ring == 8) return chain_ring<R, 8>(a, smem, st);
         if (ring == 4) return chain_ring<R, 4>(a, smem, st);
         if (ring == 2) return chain_ring<R, 2>(a, smem, st);
         return chain_ring<R, 1>(a, smem, st);
     }
-    return cudaErrorInvalidValue;
+    return chain_ring<R, 0>(a, xs, st);   // slice larger than SMEM: stream its rows
 }
 
 // ------------------------------------------------------------------------------------------
-// backward costate sweep over one wave
+// backward costate sweep over one wave: G_{j-1} = U_j^dag G_j + src_{j-1}
 // ------------------------------------------------------------------------------------------
 template <typename R, int RING>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(1024)
 k_costate(int d, StateView<R> sv, int wlen, const C_t<R>* __restrict__ Ubuf, long long ustride, int wmax,
-          const C_t<R>* __restrict__ src, K_t<R>* __restrict__ carry, C_t<R>* __restrict__ Gbuf) {
+          const C_t<R>* __restrict__ src, K_t<R>* __restrict__ carry, C_t<R>* __restrict__ Gbuf, int g) {
     using C = C_t<R>;
     using K = K_t<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -271,50 +266,79 @@ k_costate(int d, StateView<R> sv, int wlen, const C_t<R>* __restrict__ Ubuf, lon
     const size_t pb = (size_t)sv.pstride * sizeof(C);
     const size_t slot = ub + pb;
     unsigned char* ring = smraw;
-    K* xa = reinterpret_cast<K*>(smraw + RING * slot);
+    K* xa = reinterpret_cast<K*>(smraw + RING * slot);   // RING 0: no ring
     K* xb = xa + panel;
-    K* red = xb + panel;      // 8 * panel partials
-    const C* Ue = Ubuf + (size_t)e * wmax * ustride;
+    const C* UHe = Ubuf + (size_t)e * wmax * ustride + ustride / 2;     // U_j^dag of every slice
     const C* Se = src + (size_t)e * wmax * slice + (size_t)kb * sv.pstride;
     C* Ge = Gbuf + (size_t)e * wmax * slice + (size_t)kb * sv.pstride;
     K* ce = carry + (size_t)e * slice + (size_t)kb * sv.pstride;
     {   // G at the last slice of the wave = carry + src
         const C* s_last = Se + (size_t)(wlen - 1) * slice;
+        C* g_last = Ge + (size_t)(wlen - 1) * slice;
         for (int i = tid; i < (int)panel; i += blockDim.x) {
             K v = ce[i];
             kadd(v, kfrom(s_last[i]));
             knorm(v);
             xa[i] = v;
+            g_last[i] = kround(v);
         }
     }
-    auto issue = [&](int t) {     // step t handles slice jl = wlen - 1 - t: U_jl and src_{jl-1}
-        const int jl = wlen - 1 - t;
-        unsigned char* sl = ring + (t % RING) * slot;
-        ring_issue(sl, Ue + (size_t)jl * ustride, ub);
-        if (jl > 0) ring_issue(sl + ub, Se + (size_t)(jl - 1) * slice, pb);
+    auto emit_for = [&](int jl) {
+        C* gd = (jl > 0) ? Ge + (size_t)(jl - 1) * slice : nullptr;
+        return [=](int o, const K& v) {
+            if (gd) gd[o] = kround(v);
+        };
     };
+    if constexpr (RING == 0) {          // rows of U^dag and the sources read from global/L2
 #pragma unroll 1
-    for (int t = 0; t < RING - 1; ++t) {
-        if (t < wlen) issue(t);
-        cp_async_commit();
+        for (int t = 0; t < wlen; ++t) {
+            const int jl = wlen - 1 - t;
+            __syncthreads();
+            sweep_step<C, K>(UHe + (size_t)jl * ustride, xa, xb, (jl > 0) ? Se + (size_t)(jl - 1) * slice : nullptr,
+                             d, cb, g, emit_for(jl));
+            K* tmp = xa; xa = xb; xb = tmp;
+        }
+    } else if constexpr (RING == 1) {
+#pragma unroll 1
+        for (int t = 0; t < wlen; ++t) {
+            const int jl = wlen - 1 - t;
+            __syncthreads();
+            ring_issue(ring, UHe + (size_t)jl * ustride, ub);
+            if (jl > 0) ring_issue(ring + ub, Se + (size_t)(jl - 1) * slice, pb);
+            cp_async_commit();
+            cp_async_wait<0>();
+            __syncthreads();
+            sweep_step<C, K>(reinterpret_cast<const C*>(ring), xa, xb,
+                             (jl > 0) ? reinterpret_cast<const C*>(ring + ub) : nullptr, d, cb, g, emit_for(jl));
+            K* tmp = xa; xa = xb; xb = tmp;
+        }
+    } else {
+        auto issue = [&](int t) {     // step t handles slice jl = wlen - 1 - t: U_jl^dag and src_{jl-1}
+            const int jl = wlen - 1 - t;
+            unsigned char* sl = ring + (t % RING) * slot;
+            ring_issue(sl, UHe + (size_t)jl * ustride, ub);
+            if (jl > 0) ring_issue(sl + ub, Se + (size_t)(jl - 1) * slice, pb);
+        };
+#pragma unroll 1
+        for (int t = 0; t < RING - 1; ++t) {
+            if (t < wlen) issue(t);
+            cp_async_commit();
+        }
+#pragma unroll 1
+        for (int t = 0; t < wlen; ++t) {
+            const int jl = wlen - 1 - t;
+            cp_async_wait<(RING >= 2 ? RING - 2 : 0)>();
+            __syncthreads();
+            const int tn = t + RING - 1;
+            if (tn < wlen) issue(tn);
+            cp_async_commit();
+            const unsigned char* sl = ring + (t % RING) * slot;
+            sweep_step<C, K>(reinterpret_cast<const C*>(sl), xa, xb,
+                             (jl > 0) ? reinterpret_cast<const C*>(sl + ub) : nullptr, d, cb, g, emit_for(jl));
+            K* tmp = xa; xa = xb; xb = tmp;
+        }
     }
     __syncthreads();
-#pragma unroll 1
-    for (int t = 0; t < wlen; ++t) {
-        const int jl = wlen - 1 - t;
-        const int tn = t + RING - 1;
-        if (tn < wlen) issue(tn);
-        cp_async_commit();
-        C* gd = Ge + (size_t)jl * slice;
-        for (int i = tid; i < (int)panel; i += blockDim.x) gd[i] = kround(xa[i]);
-        cp_async_wait<RING - 1>();
-        __syncthreads();
-        const unsigned char* sl = ring + (t % RING) * slot;
-        const C* U = reinterpret_cast<const C*>(sl);
-        const C* add = (jl > 0) ? reinterpret_cast<const C*>(sl + ub) : nullptr;
-        mv_UH<C, K>(U, xa, xb, add, d, cb, red);
-        K* tmp = xa; xa = xb; xb = tmp;
-    }
     for (int i = tid; i < (int)panel; i += blockDim.x) ce[i] = xa[i];
 }
 
@@ -323,7 +347,9 @@ static cudaError_t costate_ring(int d, StateView<R> sv, int wlen, int E, const C
                                 int wmax, const C_t<R>* src, K_t<R>* carry, C_t<R>* Gbuf, size_t smem, cudaStream_t st) {
     cudaError_t err = cudaFuncSetAttribute(k_costate<R, RING>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    k_costate<R, RING><<<dim3(sv.ncb, E), 256, smem, st>>>(d, sv, wlen, Ubuf, ustride, wmax, src, carry, Gbuf);
+    int g = 1, threads = 256;
+    pick_sweep_shape(d, sv.cb, sizeof(R) == 4, g, threads);
+    k_costate<R, RING><<<dim3(sv.ncb, E), threads, smem, st>>>(d, sv, wlen, Ubuf, ustride, wmax, src, carry, Gbuf, g);
     return cudaGetLastError();
 }
 
@@ -333,15 +359,17 @@ cudaError_t launch_costate(int d, StateView<R> sv, int wlen, int E, const C_t<R>
     const size_t panel = (size_t)d * sv.cb;
     const size_t ub = ring_bytes((size_t)d * d, sizeof(C_t<R>));
     const size_t pb = (size_t)sv.pstride * sizeof(C_t<R>);
-    const size_t fixed = (2 + 8) * panel * sizeof(K_t<R>);
-    for (int ring : {4, 2, 1}) {
+    const size_t fixed = 2 * panel * sizeof(K_t<R>);
+    if (fixed > kMaxDynSmem) return cudaErrorInvalidValue;
+    for (int ring : {8, 4, 2, 1}) {
         const size_t smem = ring * (ub + pb) + fixed;
         if (smem > kMaxDynSmem) continue;
+        if (ring == 8) return costate_ring<R, 8>(d, sv, wlen, E, Ubuf, ustride, wmax, src, carry, Gbuf, smem, st);
         if (ring == 4) return costate_ring<R, 4>(d, sv, wlen, E, Ubuf, ustride, wmax, src, carry, Gbuf, smem, st);
         if (ring == 2) return costate_ring<R, 2>(d, sv, wlen, E, Ubuf, ustride, wmax, src, carry, Gbuf, smem, st);
         return costate_ring<R, 1>(d, sv, wlen, E, Ubuf, ustride, wmax, src, carry, Gbuf, smem, st);
     }
-    return cudaErrorInvalidValue;
+    return costate_ring<R, 0>(d, sv, wlen, E, Ubuf, ustride, wmax, src, carry, Gbuf, fixed, st);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -118,6 +118,8 @@ struct qoc_ctx {
     qoc_options opt{};
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    cudaStream_t aux = nullptr;          // second stream of the evaluation (serial sweeps)
+    std::vector<cudaEvent_t> events;     // dependencies between the two streams
     std::string err;
 
     // problem (host FP64 copies; the device copies are made by the planner)
@@ -132,18 +134,20 @@ struct qoc_ctx {
     // plan
     bool planned = false;
     int W = 0, nw = 0, seg = 0, nseg_total = 0, path_kind = 0;
-    int Spad = 0, cb = 0, ncb = 0, pstride = 0;
+    int Spad = 0, cb = 0, ncb = 0, pstride = 0, S_eff = 0;
+    std::vector<int> cols;               // propagated columns (positive weight)
+    size_t mstride = 0;                  // elements per matrix slot of the batched path
     long long ustride = 0;
     int launches = 0;
 
     Profiler prof;
 
     DevBuf H64, HR, dDelta, norms, psiTR, pathR, fmask, colw, ckpt, Ubuf, states, Gbuf, src, carry, Oj, C5j, Ofin,
-        gpart, prm, u_h, grad_h, out_h;
+        gpart, prm, u_h, grad_h, out_h, scratch;
 
     size_t device_bytes() const {
         const DevBuf* all[] = {&H64, &HR, &dDelta, &norms, &psiTR, &pathR, &fmask, &colw, &ckpt, &Ubuf, &states,
-                               &Gbuf, &src, &carry, &Oj, &C5j, &Ofin, &gpart, &prm, &u_h, &grad_h, &out_h};
+                               &Gbuf, &src, &carry, &Oj, &C5j, &Ofin, &gpart, &prm, &u_h, &grad_h, &out_h, &scratch};
         size_t s = 0;
         for (auto* b : all) s += b->bytes;
         return s;
@@ -195,14 +199,17 @@ bool split_exp(const qoc_ctx* c) {
 template <typename R>
 void plan_impl(qoc_ctx* c) {
     using C = C_t<R>;
-    const int d = c->d, S = c->S, N = c->N, E = c->E, M = c->M;
+    const int d = c->d, N = c->N, E = c->E, M = c->M;
     const size_t cs = sizeof(C);
     const int dmax = split_exp<R>(c) ? std::min(fused_max_d<R>(), split_max_d()) : fused_max_d<R>();
-    c->path_kind = (d <= dmax) ? 0 : 1;
-    if (c->path_kind != 0) {
-        c->err = "d = " + std::to_string(d) + " exceeds the fused per-slice kernels of this precision";
-        throw Fail{QOC_ERR_UNSUPPORTED};
-    }
+    c->path_kind = (d <= dmax) ? 0 : 1;   // 0: per-slice fused kernels, 1: batched tiled GEMMs
+    // Columns whose weight is zero enter no cost term (every term is weighted by w_s), so they
+    // are not propagated at all.
+    c->cols.clear();
+    for (int s = 0; s < c->S; ++s)
+        if (c->w[s] > 0.0) c->cols.push_back(s);
+    const int S = (int)c->cols.size();
+    c->S_eff = S;
     c->cb = std::min(S, 8);
     c->ncb = (S + c->cb - 1) / c->cb;
     c->Spad = c->ncb * c->cb;
@@ -215,15 +222,42 @@ void plan_impl(qoc_ctx* c) {
     seg = std::max(1, std::min(seg, N));
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->opt.device);
-    int want = c->opt.wave_slices > 0 ? c->opt.wave_slices : std::max(seg, 2 * std::max(sms, 1));
-    int W = ((want + seg - 1) / seg) * seg;
-    W = std::min(W, ((N + seg - 1) / seg) * seg);
+    int W = 0;
+    if (c->opt.wave_slices > 0) {
+        W = ((c->opt.wave_slices + seg - 1) / seg) * seg;
+    } else {
+        // whole rounds of resident CTAs of the per-slice kernels: the largest multiple of the
+        // stride up to two rounds that keeps >= 90% of the CTA slots busy (else the best one)
+        const int per_sm = std::max(1, (int)(kMaxDynSmem / std::max<size_t>(1, fused_adj_smem<R>(d))));
+        const int cap = std::max(1, sms) * std::min(per_sm, 8);
+        const int kmax = std::max(1, (2 * cap + seg - 1) / seg);
+        int best_w = seg, good_w = 0;
+        double best_eff = -1.0;
+        for (int k = 1; k <= kmax; ++k) {
+            const int w = k * seg;
+            const double eff = (double)w / ((double)((w + cap - 1) / cap) * cap);
+            if (eff > best_eff) {
+                best_eff = eff;
+                best_w = w;
+            }
+            if (eff >= 0.9) good_w = w;
+        }
+        W = good_w > 0 ? good_w : best_w;
+    }
+    if (c->path_kind == 1 && c->opt.wave_slices <= 0) {
+        // batched path: as many whole checkpoint segments as the scratch budget allows
+        const size_t per = big_scratch_per_item(d, sizeof(R) == 8) * (size_t)E;
+        const size_t budget = (size_t)2 << 30;
+        W = std::max(seg, (int)std::min<size_t>((size_t)N + seg, budget / std::max<size_t>(per, 1)) / seg * seg);
+    }
+    W = std::max(seg, std::min(W, ((N + seg - 1) / seg) * seg));
     c->seg = seg;
     c->W = W;
     c->nw = (N + W - 1) / W;
     c->nseg_total = (N + seg - 1) / seg;
+    // one slice of the propagator buffer holds U_j and U_j^dag, each padded to 256 bytes
     const long long ue = 256 / (long long)cs;
-    c->ustride = (((long long)d * d + ue - 1) / ue) * ue;
+    c->ustride = 2 * ((((long long)d * d + ue - 1) / ue) * ue);
     const int nseg_total = c->nseg_total;
 
     StateView<R> sv{c->Spad, c->cb, c->ncb, c->pstride};
@@ -240,7 +274,22 @@ void plan_impl(qoc_ctx* c) {
     A(c->fmask, d * sizeof(int), "alloc mask");
     check_cuda(c, cudaMemcpyAsync(c->fmask.p, mask.data(), d * sizeof(int), cudaMemcpyHostToDevice, st), "copy mask");
     std::vector<double> wpad(c->Spad, 0.0);
-    for (int s = 0; s < S; ++s) wpad[s] = c->w[s];
+    for (int s = 0; s < S; ++s) wpad[s] = c->w[c->cols[s]];
+    // d x S blocks restricted to the propagated columns
+    auto prune = [&](const std::vector<double>& full, int blocks) {
+        std::vector<double> out((size_t)blocks * d * S * 2);
+        for (int b = 0; b < blocks; ++b)
+            for (int a = 0; a < d; ++a)
+                for (int s = 0; s < S; ++s) {
+                    const size_t src = (((size_t)b * d + a) * c->S + c->cols[s]) * 2;
+                    const size_t dst = (((size_t)b * d + a) * S + s) * 2;
+                    out[dst] = full[src];
+                    out[dst + 1] = full[src + 1];
+                }
+        return out;
+    };
+    const std::vector<double> psi0p = prune(c->psi0, 1), psiTp = prune(c->psiT, 1);
+    const std::vector<double> pathp = c->path.empty() ? std::vector<double>() : prune(c->path, N);
     A(c->colw, c->Spad * sizeof(double), "alloc weights");
     check_cuda(c, cudaMemcpyAsync(c->colw.p, wpad.data(), c->Spad * sizeof(double), cudaMemcpyHostToDevice, st),
                "copy weights");
@@ -249,18 +298,18 @@ void plan_impl(qoc_ctx* c) {
     const size_t blk = (size_t)d * S * 2 * sizeof(double);
     A(stage, std::max(blk, c->path.empty() ? blk : (size_t)N * blk), "alloc staging");
     A(c->psiTR, slice * cs, "alloc target");
-    check_cuda(c, cudaMemcpyAsync(stage.p, c->psiT.data(), blk, cudaMemcpyHostToDevice, st), "copy target");
+    check_cuda(c, cudaMemcpyAsync(stage.p, psiTp.data(), blk, cudaMemcpyHostToDevice, st), "copy target");
     check_cuda(c, launch_to_panels<R>(stage.as<double2>(), c->psiTR.as<C>(), d, S, sv, 1, 0, 0, st), "target panels");
     A(c->ckpt, (size_t)E * nseg_total * slice * sizeof(K_t<R>), "alloc checkpoints");
     check_cuda(c, cudaStreamSynchronize(st), "sync");
-    check_cuda(c, cudaMemcpyAsync(stage.p, c->psi0.data(), blk, cudaMemcpyHostToDevice, st), "copy psi0");
+    check_cuda(c, cudaMemcpyAsync(stage.p, psi0p.data(), blk, cudaMemcpyHostToDevice, st), "copy psi0");
     check_cuda(c, launch_to_carry<R>(stage.as<double2>(), c->ckpt.as<K_t<R>>(), d, S, sv, E,
                                      (size_t)nseg_total * slice, st),
                "psi0 panels");
     if (!c->path.empty()) {
         check_cuda(c, cudaStreamSynchronize(st), "sync");
         A(c->pathR, (size_t)N * slice * cs, "alloc path");
-        check_cuda(c, cudaMemcpyAsync(stage.p, c->path.data(), (size_t)N * blk, cudaMemcpyHostToDevice, st),
+        check_cuda(c, cudaMemcpyAsync(stage.p, pathp.data(), (size_t)N * blk, cudaMemcpyHostToDevice, st),
                    "copy path");
         check_cuda(c, launch_to_panels<R>(stage.as<double2>(), c->pathR.as<C>(), d, S, sv, N, slice, (size_t)d * S, st),
                    "path panels");
@@ -268,10 +317,23 @@ void plan_impl(qoc_ctx* c) {
         c->pathR.release();
     }
     // per-segment work buffers
-    A(c->Ubuf, (size_t)E * W * c->ustride * cs, "alloc U");
-    A(c->states, (size_t)E * (W + 1) * slice * cs, "alloc states");
-    A(c->Gbuf, (size_t)E * W * slice * cs, "alloc costates");
-    A(c->src, (size_t)E * W * slice * cs, "alloc sources");
+    // two sets of wave buffers (waves alternate between them)
+    A(c->Ubuf, 2 * (size_t)E * W * c->ustride * cs, "alloc U");
+    A(c->states, 2 * (size_t)E * (W + 1) * slice * cs, "alloc states");
+    A(c->Gbuf, 2 * (size_t)E * W * slice * cs, "alloc costates");
+    A(c->src, 2 * (size_t)E * W * slice * cs, "alloc sources");
+    if (c->path_kind == 1) {
+        c->mstride = (((size_t)d * d + 15) / 16) * 16;
+        const size_t per = big_scratch_per_item(d, sizeof(R) == 8) / ((size_t)d * d) * c->mstride;
+        A(c->scratch, per * (size_t)E * W, "alloc batched scratch");
+    } else {
+        c->scratch.release();
+    }
+    // second stream and the dependency events between the two streams
+    if (!c->aux) check_cuda(c, cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking), "create stream");
+    for (auto e : c->events) cudaEventDestroy(e);
+    c->events.assign(4 * c->nw + 3, nullptr);
+    for (auto& e : c->events) check_cuda(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "create event");
     A(c->carry, (size_t)E * slice * sizeof(K_t<R>), "alloc carry");
     A(c->Oj, (size_t)E * N * sizeof(double2), "alloc O");
     A(c->C5j, (size_t)E * N * sizeof(double), "alloc C5");
@@ -289,8 +351,10 @@ void plan_impl(qoc_ctx* c) {
 template <typename R>
 void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out) {
     using C = C_t<R>;
+    using K = K_t<R>;
     const int d = c->d, N = c->N, E = c->E, M = c->M, W = c->W, nw = c->nw;
-    cudaStream_t st = c->stream;
+    cudaStream_t st = c->stream;   // parallel kernels (the caller's stream)
+    cudaStream_t sx = c->aux;      // serial sweeps and the small per-slice kernels
     StateView<R> sv{c->Spad, c->cb, c->ncb, c->pstride};
     const size_t slice = sv.slice();
     const size_t dd = (size_t)d * d;
@@ -300,86 +364,142 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out) {
     CostView<R> cv{c->nF, c->fmask.as<int>(), c->colw.as<double>(), c->Wsum, c->psiTR.as<C>(),
                    c->path.empty() ? nullptr : c->pathR.as<C>(), {c->alpha[0], c->alpha[1], c->alpha[2], c->alpha[3], c->alpha[4]}};
     DevParams* prm = c->prm.as<DevParams>();
-    C* Ub = c->Ubuf.as<C>();
-    C* states = c->states.as<C>();
     const int seg = c->seg;
-    ChainArgs<R> ch{d, sv, 0, seg, 0, E, c->ckpt.as<K_t<R>>(), (size_t)c->nseg_total * slice, 0, c->nseg_total,
-                    Ub, c->ustride, W, states};
+    // two sets of wave buffers: wave w uses set w % 2, so the serial sweep of one wave overlaps
+    // the parallel kernels of its neighbour
+    const size_t u_set = (size_t)E * W * c->ustride, s_set = (size_t)E * (W + 1) * slice, g_set = (size_t)E * W * slice;
+    auto Ub = [&](int w) { return c->Ubuf.as<C>() + (w & 1) * u_set; };
+    auto Sb = [&](int w) { return c->states.as<C>() + (w & 1) * s_set; };
+    auto Gb = [&](int w) { return c->Gbuf.as<C>() + (w & 1) * g_set; };
+    auto Rb = [&](int w) { return c->src.as<C>() + (w & 1) * g_set; };
+    auto chain_args = [&](int w, int mode) {
+        const int j0 = w * W;
+        return ChainArgs<R>{d, sv, std::min(W, N - j0), seg, mode, E, c->ckpt.as<K>(), (size_t)c->nseg_total * slice,
+                            j0 / seg, c->nseg_total, Ub(w), c->ustride, W, Sb(w)};
+    };
     int launches = 0;
     const bool prof = c->opt.profile != 0;
     cudaEvent_t ev0 = nullptr;
-    // B(name) opens an event bracket before a launch, L(...) closes it after the launch
-    auto B = [&](const char*) {
+    // B(stream) opens an event bracket before a launch, L(..., stream) closes it after the launch
+    auto B = [&](cudaStream_t s) {
         if (prof) {
             ev0 = c->prof.get();
-            cudaEventRecord(ev0, st);
+            cudaEventRecord(ev0, s);
         }
     };
-    auto L = [&](cudaError_t e, const char* what) {
+    auto L = [&](cudaError_t e, const char* what, cudaStream_t s) {
         ++launches;
         check_cuda(c, e, what);
         if (prof) {
             cudaEvent_t ev1 = c->prof.get();
-            cudaEventRecord(ev1, st);
+            cudaEventRecord(ev1, s);
             c->prof.pending.push_back({c->prof.cls(what), ev0, ev1});
         }
     };
-    B(nullptr);
+    auto rec = [&](cudaEvent_t e, cudaStream_t s) { check_cuda(c, cudaEventRecord(e, s), "event record"); };
+    auto wait = [&](cudaStream_t s, cudaEvent_t e) { check_cuda(c, cudaStreamWaitEvent(s, e, 0), "event wait"); };
+    cudaEvent_t* ev_exp = &c->events[0];
+    cudaEvent_t* ev_fwd = &c->events[nw];
+    cudaEvent_t* ev_rep = &c->events[2 * nw];
+    cudaEvent_t* ev_cost = &c->events[3 * nw];
+    cudaEvent_t ev_fork = c->events[4 * nw], ev_fwd_done = c->events[4 * nw + 1], ev_join = c->events[4 * nw + 2];
+
+    B(st);
     L(launch_theta(u, M, N, c->norms.as<double>(), c->delta.empty() ? nullptr : c->dDelta.as<double>(), E, c->dt,
                    c->opt.theta_max, c->opt.tol, c->opt.p_override, c->opt.n_override, prm, st),
-      "theta");
+      "theta", st);
+    rec(ev_fork, st);
+    wait(sx, ev_fork);
     // slice exponentials: split hi+lo FP32 for the FP32 form (unless disabled), else plain
     const bool split = split_exp<R>(c);
-    auto expm_fwd = [&](int j0, int wlen) -> cudaError_t {
+    const bool big = c->path_kind == 1;
+    DevParams hp{};
+    if (big) {   // the batched path launches one kernel per product: read (p, n) back once
+        check_cuda(c, cudaMemcpyAsync(&hp, prm, sizeof(DevParams), cudaMemcpyDeviceToHost, st), "read (p, n)");
+        check_cuda(c, cudaStreamSynchronize(st), "sync (p, n)");
+        hp.p = std::max(1, std::min(hp.p, kPMax));
+        hp.n = std::max(0, std::min(hp.n, 1000));
+    }
+    BigSys bsys{d, M, N, c->H64.as<double2>(), u, c->delta.empty() ? nullptr : c->dDelta.as<double>(),
+                c->Hdet.empty() ? 0 : 1};
+    auto big_args = [&](int w) {
+        const int j0 = w * W;
+        return BigArgs<R>{prm, bsys, d, E, j0, std::min(W, N - j0), W, c->scratch.p, c->mstride, Ub(w), c->ustride};
+    };
+    int extra = 0;   // kernels of the batched calls beyond the one counted by L
+    auto expm_fwd = [&](int w) -> cudaError_t {
+        const int j0 = w * W, wlen = std::min(W, N - j0);
+        if (big) {
+            int n_l = 0;
+            cudaError_t e = launch_big_expm<R>(big_args(w), hp.p, hp.n, hp.m_split, split, st, &n_l);
+            extra += n_l - 1;
+            return e;
+        }
         if constexpr (sizeof(R) == 4) {
             if (split)
-                return launch_expm_fwd_split(prm, sys, c->H64.as<double2>(), j0, wlen, E, Ub, c->ustride, W, st);
+                return launch_expm_fwd_split(prm, sys, c->H64.as<double2>(), j0, wlen, E, Ub(w), c->ustride, W, st);
         }
-        return launch_expm_fwd_fused<R>(prm, sys, j0, wlen, E, Ub, c->ustride, W, st);
+        return launch_expm_fwd_fused<R>(prm, sys, j0, wlen, E, Ub(w), c->ustride, W, st);
     };
+    auto expm_adj = [&](int w) -> cudaError_t {
+        const int j0 = w * W, wlen = std::min(W, N - j0);
+        if (big) {
+            int n_l = 0;
+            cudaError_t e = launch_big_adj<R>(big_args(w), sys, sv, Sb(w), Gb(w), c->gpart.as<double>(), hp.p, hp.n, st,
+                                              &n_l);
+            extra += n_l - 1;
+            return e;
+        }
+        return launch_expm_adj_fused<R>(prm, sys, sv, j0, wlen, E, Sb(w), Gb(w), W, c->gpart.as<double>(), st);
+    };
+    // ---- forward: exponentials on st, propagation and per-slice costs on sx ----
     for (int w = 0; w < nw; ++w) {
         const int j0 = w * W, wlen = std::min(W, N - j0);
-        B(nullptr);
-        L(expm_fwd(j0, wlen), "expm_fwd");
-        ch.wlen = wlen;
-        ch.seg0 = j0 / seg;
-        ch.mode = 0;
-        B(nullptr);
-        L(launch_chain<R>(ch, st), "chain_fwd");
-        B(nullptr);
-        L(launch_slice_costs<R>(d, sv, j0, wlen, N, E, states, W, cv, c->Oj.as<double2>(), c->C5j.as<double>(),
-                                c->Ofin.as<double2>(), st),
-          "slice_costs");
+        if (w >= 2) wait(st, ev_fwd[w - 2]);           // set w % 2 released by wave w - 2
+        B(st);
+        L(expm_fwd(w), "expm_fwd", st);
+        rec(ev_exp[w], st);
+        wait(sx, ev_exp[w]);
+        B(sx);
+        L(launch_chain<R>(chain_args(w, 0), sx), "chain_fwd", sx);
+        B(sx);
+        L(launch_slice_costs<R>(d, sv, j0, wlen, N, E, Sb(w), W, cv, c->Oj.as<double2>(), c->C5j.as<double>(),
+                                c->Ofin.as<double2>(), sx),
+          "slice_costs", sx);
+        rec(ev_fwd[w], sx);
     }
-    check_cuda(c, cudaMemsetAsync(c->carry.p, 0, c->carry.bytes, st), "memset carry");
+    check_cuda(c, cudaMemsetAsync(c->carry.p, 0, c->carry.bytes, sx), "memset carry");
+    rec(ev_fwd_done, sx);
+    wait(st, ev_fwd_done);
+    // ---- backward: recompute + replay of wave w - 1 on st overlap the costate of wave w on sx ----
     for (int w = nw - 1; w >= 0; --w) {
         const int j0 = w * W, wlen = std::min(W, N - j0);
-        if (w != nw - 1) {   // the last wave is still resident from the forward sweep
-            B(nullptr);
-            L(expm_fwd(j0, wlen), "expm_fwd (recompute)");
-            ch.wlen = wlen;
-            ch.seg0 = j0 / seg;
-            ch.mode = 1;
-            B(nullptr);
-            L(launch_chain<R>(ch, st), "chain (replay)");
+        if (w != nw - 1) wait(sx, ev_rep[w]);           // the last wave is resident from the forward sweep
+        B(sx);
+        L(launch_sources<R>(d, sv, j0, wlen, N, E, Sb(w), W, cv, c->Oj.as<double2>(), c->Ofin.as<double2>(), Rb(w),
+                            sx),
+          "sources", sx);
+        B(sx);
+        L(launch_costate<R>(d, sv, wlen, E, Ub(w), c->ustride, W, Rb(w), c->carry.as<K>(), Gb(w), sx), "costate", sx);
+        rec(ev_cost[w], sx);
+        if (w >= 1) {                                    // set (w - 1) % 2 was released by wave w + 1
+            B(st);
+            L(expm_fwd(w - 1), "expm_fwd (recompute)", st);
+            B(st);
+            L(launch_chain<R>(chain_args(w - 1, 1), st), "chain (replay)", st);
+            rec(ev_rep[w - 1], st);
         }
-        B(nullptr);
-        L(launch_sources<R>(d, sv, j0, wlen, N, E, states, W, cv, c->Oj.as<double2>(), c->Ofin.as<double2>(),
-                            c->src.as<C>(), st),
-          "sources");
-        B(nullptr);
-        L(launch_costate<R>(d, sv, wlen, E, Ub, c->ustride, W, c->src.as<C>(), c->carry.as<K_t<R>>(),
-                            c->Gbuf.as<C>(), st),
-          "costate");
-        B(nullptr);
-        L(launch_expm_adj_fused<R>(prm, sys, sv, j0, wlen, E, states, c->Gbuf.as<C>(), W, c->gpart.as<double>(), st),
-          "expm_adj");
+        wait(st, ev_cost[w]);
+        B(st);
+        L(expm_adj(w), "expm_adj", st);
     }
-    B(nullptr);
+    rec(ev_join, sx);
+    wait(st, ev_join);
+    B(st);
     L(launch_finalize(E, M, N, u, c->alpha, c->Oj.as<double2>(), c->C5j.as<double>(), c->Ofin.as<double2>(),
                       c->gpart.as<double>(), grad, out, st),
-      "finalize");
-    c->launches = launches;
+      "finalize", st);
+    c->launches = launches + extra;
 }
 
 void plan(qoc_ctx* c) {
@@ -481,6 +601,11 @@ void qoc_destroy(qoc_ctx* ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->opt.device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    if (ctx->aux) {
+        cudaStreamSynchronize(ctx->aux);
+        cudaStreamDestroy(ctx->aux);
+    }
+    for (auto e : ctx->events) cudaEventDestroy(e);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }

@@ -70,6 +70,7 @@ cudaError_t launch_to_panels(const double2* src, C_t<R>* dst, int d, int S, Stat
 
 // ---- fused per-slice exponential kernels ----
 template <typename R> int fused_max_d();
+template <typename R> size_t fused_adj_smem(int d);   // dynamic SMEM of the per-slice adjoint kernel
 template <typename R>
 cudaError_t launch_expm_fwd_fused(const DevParams* prm, const SysView<R>& sys, int j0, int wlen, int E,
                                   C_t<R>* Ubuf, long long ustride, int wmax, cudaStream_t st);
@@ -82,6 +83,35 @@ cudaError_t launch_expm_adj_fused(const DevParams* prm, const SysView<R>& sys, c
 int split_max_d();
 cudaError_t launch_expm_fwd_split(const DevParams* prm, const SysView<float>& sys, const double2* H64, int j0, int wlen,
                                   int E, float2* Ubuf, long long ustride, int wmax, cudaStream_t st);
+
+// ---- large-d batched slice exponentials and adjoint (k_big.cu) ----
+struct BigSys {
+    int d, M, N;
+    const double2* H64;   // FP64 [H0, H1..HM, Hdet]
+    const double* u;      // M x N
+    const double* delta;  // E or nullptr
+    int has_det;
+};
+template <typename R>
+struct BigArgs {
+    const DevParams* prm;
+    BigSys bsys;
+    int d, E, j0, wlen, wmax;
+    void* scratch;        // per-item matrices of the wave (mstride elements apart)
+    size_t mstride;       // elements per matrix slot (>= d * d)
+    void* Ubuf;           // propagator buffer of the wave (C_t<R>, U at 0 and U^dag at ustride / 2)
+    long long ustride;
+};
+// bytes of scratch per wave item
+inline size_t big_scratch_per_item(int d, bool fp64) {
+    const size_t dd = (size_t)d * d;
+    return fp64 ? 6 * dd * 16 : 6 * dd * 8 > 3 * dd * 16 ? 6 * dd * 8 : 3 * dd * 16;
+}
+template <typename R>
+cudaError_t launch_big_expm(const BigArgs<R>& a, int p, int n, int m_split, bool split, cudaStream_t st, int* launches);
+template <typename R>
+cudaError_t launch_big_adj(const BigArgs<R>& a, const SysView<R>& sys, const StateView<R>& sv, const C_t<R>* states,
+                           const C_t<R>* Gbuf, double* gpart, int p, int n, cudaStream_t st, int* launches);
 
 // ---- serial sweeps (k_serial.cu) ----
 // mode 0: forward propagation of one wave (grid z = 1) from checkpoint `seg0`, storing the

@@ -73,7 +73,7 @@ extern "C" qoc_status qoc_evaluate_static(int d, int M, int N, int S, double dt,
     sv.Spad = sv.ncb * sv.cb;
     sv.pstride = d * sv.cb;                       // 16-byte elements: always aligned
     const size_t slice = sv.slice();
-    const long long ustride = ((long long)d * d + 15) / 16 * 16;
+    const long long ustride = 2 * (((long long)d * d + 15) / 16 * 16);   // U_j and U_j^dag
 
     Carver cv{reinterpret_cast<unsigned char*>(g_arena_addr[dev])};
     DevParams* prm = cv.take<DevParams>(1);

@@ -1,0 +1,70 @@
+"""GPU parity of the large-d path (batched tiled GEMMs for the slice exponentials and their
+adjoint, serial sweeps with a synchronous ring or rows streamed from global memory) against the
+CPU FP64 oracle.  Same tolerances as tests/test_gpu_parity.py."""
+import numpy as np
+import pytest
+
+import synthetic as sy
+from oracle import qoc_oracle as orc
+from test_gpu_parity import check, rel, run
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1612_04929_gb300 import build
+    build.build()
+
+
+BIG64 = [
+    dict(d=49, M=2, N=11, S=1, seed=601, nF=3),
+    dict(d=57, M=3, N=9, S=9, seed=602, nF=2, path=True, E=2),
+    dict(d=70, M=2, N=7, S=3, seed=603, nF=4, weights=True),
+]
+
+
+@pytest.mark.parametrize("case", BIG64, ids=lambda c: f"d{c['d']}S{c['S']}N{c['N']}")
+@pytest.mark.parametrize("layout", [dict(), dict(ckpt_stride=3, wave_slices=3)], ids=["auto", "stride3"])
+def test_big_fp64_matches_oracle(case, layout):
+    prob = sy.random_problem(**case, dt=0.15, u_scale=0.8)
+    cost, grad, terms, info = check(prob, "fp64", **layout)
+    assert info["kernel_path"] == 1
+
+
+BIG32 = [
+    dict(d=65, M=2, N=13, S=1, seed=611, nF=5),
+    dict(d=81, M=3, N=9, S=12, seed=612, nF=6, path=True),
+    dict(d=100, M=2, N=7, S=4, seed=613, nF=3, E=2, weights=True),
+    dict(d=130, M=2, N=5, S=2, seed=614, nF=2),
+]
+
+
+@pytest.mark.parametrize("case", BIG32, ids=lambda c: f"d{c['d']}S{c['S']}N{c['N']}")
+@pytest.mark.parametrize("layout", [dict(), dict(ckpt_stride=2, wave_slices=4)], ids=["auto", "stride2"])
+def test_big_fp32_matches_oracle(case, layout):
+    prob = sy.random_problem(**case, dt=0.15, u_scale=0.8)
+    cost, grad, terms, info = check(prob, "fp32", **layout)
+    assert info["kernel_path"] == 1
+
+
+def test_zero_weight_columns_are_not_needed():
+    """The 81-level workload weighs 16 of 81 columns; pruning the other 65 must not change the
+    result (checked against the oracle, which propagates all 81)."""
+    prob = sy.transmon4(N=40)
+    for prec in ("fp64", "fp32"):
+        check(prob, prec)
+
+
+def test_transmon4_fp32_full_size():
+    prob = sy.transmon4()
+    cost, grad, terms, info = check(prob, "fp32")
+    assert info["kernel_path"] == 1 and info["ckpt_stride"] == 32
+
+
+def test_gue256_fp32_reduced_N():
+    check(sy.gue256(N=60), "fp32")
+
+
+def test_gue256_fp64_tiny():
+    check(sy.gue256(N=3), "fp64")

@@ -350,3 +350,11 @@ def test_workload_inputs_are_well_formed():
     sub = np.where(c3.col_weight > 0)[0]
     V = c3.psiT[np.ix_(sub, sub)]
     assert np.max(np.abs(V.conj().T @ V - np.eye(16))) < 1e-13
+
+
+def test_sampled_slices_match_full_gradient():
+    p = sy.random_problem(3, 2, 9, 2, seed=71, nF=1, path=True, E=2)
+    _, g, _ = orc.cost_and_grad(p, p.u)
+    c, gs, _ = orc.cost_and_grad(p, p.u, slices=[0, 4, 8])
+    assert np.all(np.isnan(gs[:, [1, 2, 3, 5, 6, 7]]))
+    assert np.max(np.abs(gs[:, [0, 4, 8]] - g[:, [0, 4, 8]])) == 0.0
