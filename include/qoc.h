@@ -162,6 +162,19 @@ qoc_status qoc_evaluate_cost_and_grad(qoc_ctx* ctx, const double* u, double* cos
 qoc_status qoc_evaluate_device(qoc_ctx* ctx, const double* u_dev, double* grad_dev,
                                double* out_dev);
 
+/* Batched evaluation of `count` independent problems (for example many control problems of
+ * uneven d, N, M and ensemble size): ctxs[i] is a context set up for problem i, and u_dev[i],
+ * grad_dev[i], out_dev[i] are its device buffers as in qoc_evaluate_device.  Every context's
+ * (p, n) is picked first (FP64, on the GPU); if some problem uses the large-d kernels, the call
+ * waits once to read those choices.  Then every evaluation is enqueued on its own context's
+ * streams, so the problems run concurrently on the GPU; all of them start after the work
+ * already enqueued on `stream` and the work enqueued on `stream` after this call waits for all
+ * of them (NULL: the legacy default stream).  Contexts created with their own streams
+ * (qoc_options.stream = NULL) run concurrently; a context may appear only once.  Errors of one
+ * context are reported through its qoc_last_error. */
+qoc_status qoc_evaluate_batch(int count, qoc_ctx* const* ctxs, const double* const* u_dev,
+                              double* const* grad_dev, double* const* out_dev, void* stream);
+
 /* Waits for the context stream and reports a device-side error of earlier evaluations. */
 qoc_status qoc_sync(qoc_ctx* ctx);
 

@@ -348,8 +348,10 @@ void plan_impl(qoc_ctx* c) {
     c->planned = true;
 }
 
+// known: (p, n) already picked on the device by an earlier launch_theta on c->stream and read
+// back (batched evaluation); nullptr: pick them here.
 template <typename R>
-void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out) {
+void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const DevParams* known = nullptr) {
     using C = C_t<R>;
     using K = K_t<R>;
     const int d = c->d, N = c->N, E = c->E, M = c->M, W = c->W, nw = c->nw;
@@ -404,10 +406,14 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out) {
     cudaEvent_t* ev_cost = &c->events[3 * nw];
     cudaEvent_t ev_fork = c->events[4 * nw], ev_fwd_done = c->events[4 * nw + 1], ev_join = c->events[4 * nw + 2];
 
-    B(st);
-    L(launch_theta(u, M, N, c->norms.as<double>(), c->delta.empty() ? nullptr : c->dDelta.as<double>(), E, c->dt,
-                   c->opt.theta_max, c->opt.tol, c->opt.p_override, c->opt.n_override, prm, st),
-      "theta", st);
+    if (!known) {
+        B(st);
+        L(launch_theta(u, M, N, c->norms.as<double>(), c->delta.empty() ? nullptr : c->dDelta.as<double>(), E, c->dt,
+                       c->opt.theta_max, c->opt.tol, c->opt.p_override, c->opt.n_override, prm, st),
+          "theta", st);
+    } else {
+        ++launches;
+    }
     rec(ev_fork, st);
     wait(sx, ev_fork);
     // slice exponentials: split hi+lo FP32 for the FP32 form (unless disabled), else plain
@@ -415,8 +421,12 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out) {
     const bool big = c->path_kind == 1;
     DevParams hp{};
     if (big) {   // the batched path launches one kernel per product: read (p, n) back once
-        check_cuda(c, cudaMemcpyAsync(&hp, prm, sizeof(DevParams), cudaMemcpyDeviceToHost, st), "read (p, n)");
-        check_cuda(c, cudaStreamSynchronize(st), "sync (p, n)");
+        if (known) {
+            hp = *known;
+        } else {
+            check_cuda(c, cudaMemcpyAsync(&hp, prm, sizeof(DevParams), cudaMemcpyDeviceToHost, st), "read (p, n)");
+            check_cuda(c, cudaStreamSynchronize(st), "sync (p, n)");
+        }
         hp.p = std::max(1, std::min(hp.p, kPMax));
         hp.n = std::max(0, std::min(hp.n, 1000));
     }
@@ -507,10 +517,10 @@ void plan(qoc_ctx* c) {
     else plan_impl<float>(c);
 }
 
-void evaluate(qoc_ctx* c, const double* u, double* grad, double* out) {
+void evaluate(qoc_ctx* c, const double* u, double* grad, double* out, const DevParams* known = nullptr) {
     if (!c->planned) plan(c);
-    if (is_fp64(c)) evaluate_impl<double>(c, u, grad, out);
-    else evaluate_impl<float>(c, u, grad, out);
+    if (is_fp64(c)) evaluate_impl<double>(c, u, grad, out, known);
+    else evaluate_impl<float>(c, u, grad, out, known);
 }
 
 qoc_status device_error(qoc_ctx* c) {
@@ -812,6 +822,78 @@ qoc_status qoc_get_info(qoc_ctx* ctx, qoc_info* info) {
     info->device_bytes = (long long)ctx->device_bytes();
     return QOC_OK;
     QOC_GUARD_END
+}
+
+qoc_status qoc_evaluate_batch(int count, qoc_ctx* const* ctxs, const double* const* u_dev, double* const* grad_dev,
+                              double* const* out_dev, void* stream) {
+    if (count < 0 || (count > 0 && (!ctxs || !u_dev || !grad_dev || !out_dev))) return QOC_ERR_ARG;
+    for (int i = 0; i < count; ++i) {
+        qoc_ctx* c = ctxs[i];
+        if (!c) return QOC_ERR_ARG;
+        c->err.clear();
+        if (!c->has_sys || !c->has_tgt) return set_err(c, QOC_ERR_STATE, "set_system and set_targets must come first");
+        if (!u_dev[i] || !grad_dev[i] || !out_dev[i]) return set_err(c, QOC_ERR_ARG, "NULL device pointer");
+        for (int k = 0; k < i; ++k)
+            if (ctxs[k] == c) return set_err(c, QOC_ERR_ARG, "a context appears twice in the batch");
+    }
+    cudaStream_t caller = reinterpret_cast<cudaStream_t>(stream);
+    qoc_ctx* cur = nullptr;
+    try {
+        std::vector<cudaEvent_t> evs;
+        auto fresh = [&](qoc_ctx* c) {
+            cudaEvent_t e = nullptr;
+            check_cuda(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "create event");
+            evs.push_back(e);
+            return e;
+        };
+        struct Guard {
+            std::vector<cudaEvent_t>& v;
+            ~Guard() { for (auto e : v) cudaEventDestroy(e); }
+        } guard{evs};
+        // 1) plan every context, fork its stream from the caller's stream, pick (p, n)
+        std::vector<DevParams> hp(count);
+        std::vector<char> need(count, 0);
+        bool any_big = false;
+        for (int i = 0; i < count; ++i) {
+            qoc_ctx* c = cur = ctxs[i];
+            check_cuda(c, cudaSetDevice(c->opt.device), "set device");
+            if (!c->planned) plan(c);
+            cudaEvent_t f = fresh(c);
+            check_cuda(c, cudaEventRecord(f, caller), "fork");
+            check_cuda(c, cudaStreamWaitEvent(c->stream, f, 0), "fork wait");
+            check_cuda(c, launch_theta(u_dev[i], c->M, c->N, c->norms.as<double>(),
+                                       c->delta.empty() ? nullptr : c->dDelta.as<double>(), c->E, c->dt,
+                                       c->opt.theta_max, c->opt.tol, c->opt.p_override, c->opt.n_override,
+                                       c->prm.as<DevParams>(), c->stream),
+                       "theta");
+            if (c->path_kind == 1) {
+                need[i] = 1;
+                any_big = true;
+                check_cuda(c, cudaMemcpyAsync(&hp[i], c->prm.p, sizeof(DevParams), cudaMemcpyDeviceToHost, c->stream),
+                           "read (p, n)");
+            }
+        }
+        // 2) one wait for the (p, n) of the batched-path problems
+        if (any_big)
+            for (int i = 0; i < count; ++i)
+                if (need[i]) check_cuda(cur = ctxs[i], cudaStreamSynchronize(ctxs[i]->stream), "sync (p, n)");
+        // 3) every evaluation on its own streams, 4) join into the caller's stream
+        for (int i = 0; i < count; ++i) {
+            qoc_ctx* c = cur = ctxs[i];
+            evaluate(c, u_dev[i], grad_dev[i], out_dev[i], &hp[i]);   // (p, n) launched above
+        }
+        for (int i = 0; i < count; ++i) {
+            qoc_ctx* c = cur = ctxs[i];
+            cudaEvent_t j = fresh(c);
+            check_cuda(c, cudaEventRecord(j, c->stream), "join");
+            check_cuda(c, cudaStreamWaitEvent(caller, j, 0), "join wait");
+        }
+        return QOC_OK;
+    } catch (const Fail& f) {
+        return f.st;
+    } catch (...) {
+        return set_err(cur, QOC_ERR_CUDA, "unexpected exception");
+    }
 }
 
 qoc_status qoc_get_profile(qoc_ctx* ctx, qoc_profile* out) {

@@ -30,7 +30,7 @@ PRECISIONS = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
 ABI_SYMBOLS = ("qoc_default_options", "qoc_create", "qoc_destroy", "qoc_last_error", "qoc_status_string",
                "qoc_set_system", "qoc_set_targets", "qoc_set_ensemble", "qoc_evaluate_cost_and_grad",
                "qoc_evaluate_device", "qoc_sync", "qoc_get_info", "qoc_get_profile", "qoc_reset_profile",
-               "qoc_evaluate_static")
+               "qoc_evaluate_static", "qoc_evaluate_batch")
 
 
 class QocError(RuntimeError):
@@ -103,6 +103,9 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.qoc_reset_profile.restype = I
     lib.qoc_evaluate_static.argtypes = [I, I, I, I, D, VP, VP, VP, VP, VP, VP, DP, VP, VP, VP]
     lib.qoc_evaluate_static.restype = I
+    PP = ct.POINTER(ct.c_void_p)
+    lib.qoc_evaluate_batch.argtypes = [I, PP, PP, PP, PP, VP]
+    lib.qoc_evaluate_batch.restype = I
     _lib = lib
     return lib
 
@@ -234,6 +237,18 @@ def qoc_evaluate_static(d: int, M: int, N: int, S: int, dt: float, H0_dev: int, 
                                     grad_dev or None, out_dev or None, stream or None)
     if st != QOC_OK:
         raise QocError(st, "qoc_evaluate_static failed")
+
+
+def qoc_evaluate_batch(ctxs, u_dev, grad_dev, out_dev, stream: int = 0) -> None:
+    """Batched evaluation (see include/qoc.h): ``ctxs`` are Context objects or raw handles, the
+    other lists raw device pointers (ints), one per problem."""
+    n = len(ctxs)
+    arr = lambda xs: (ct.c_void_p * n)(*[ct.c_void_p(int(x)) for x in xs])
+    handles = (ct.c_void_p * n)(*[(c.handle if isinstance(c, Context) else c) for c in ctxs])
+    st = load().qoc_evaluate_batch(n, handles, arr(u_dev), arr(grad_dev), arr(out_dev), stream or None)
+    if st != QOC_OK:
+        msgs = [load().qoc_last_error(c.handle if isinstance(c, Context) else c).decode() for c in ctxs]
+        raise QocError(st, "; ".join(m for m in msgs if m))
 
 
 # ------------------------------------------------------------------ convenience wrapper

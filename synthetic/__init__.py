@@ -269,6 +269,7 @@ def batch_problem(idx: int, ensemble: int = 1, seed_base: int = 5000,
 
 
 def batch_problems(count: int = 128, ensemble: int = 1, **kw) -> List[Problem]:
+    """The batched sweep: problems 0..count-1 (keyword arguments go to ``batch_problem``)."""
     return [batch_problem(i, ensemble=ensemble, **kw) for i in range(count)]
 
 

@@ -68,3 +68,15 @@ def test_gue256_fp32_reduced_N():
 
 def test_gue256_fp64_tiny():
     check(sy.gue256(N=3), "fp64")
+
+
+def test_gue256_fp32_full_size_sampled():
+    """Full length (N = 2000): the cost and the gradient at sampled slices against the oracle
+    (its costate sweep covers all slices; only the per-slice contractions are sampled)."""
+    prob = sy.gue256()
+    cost, grad, terms, info = run(prob, "fp32")
+    cols = [0, 1, 500, 999, 1500, 1998, 1999]
+    c_ref, g_ref, _ = orc.cost_and_grad(prob, prob.u, slices=cols)
+    assert abs(cost - c_ref) <= 1e-5 * abs(c_ref)
+    assert rel(grad[:, cols], g_ref[:, cols]) <= 1e-5
+    assert info["ckpt_stride"] == 45 and info["n_waves"] > 1
