@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--precision", default=None)
     ap.add_argument("--ckpt-stride", type=int, default=0)
     ap.add_argument("--N", type=int, default=0, help="override the slice count (profiling runs)")
+    ap.add_argument("--count", type=int, default=128, help="problems of the batched sweep (--workload batch)")
+    ap.add_argument("--ensemble", type=int, default=32, help="members per problem (--workload batch)")
+    ap.add_argument("--profile-batch", action="store_true", help="per-kernel event times (--workload batch)")
     ap.add_argument("--cpu-sample", type=int, default=0, help="slices in the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -303,10 +306,90 @@ def ours_arm(args):
         dist.destroy_process_group()
 
 
+def batch_arm(args):
+    """The batched sweep: `count` problems of uneven d in {4, 8, 16, 40, 81, 128}, N in
+    [200, 4000], M in [2, 8], each with an `ensemble`-member detuning ensemble, FP32 form,
+    evaluated by one qoc_evaluate_batch call per step; compared with evaluating the same
+    contexts one after another.  Metric: sum_i N_i E_i / seconds per step."""
+    import torch
+    import synthetic as sy
+    from paper_1612_04929_gb300 import Context, build as qbuild, qoc_evaluate_batch
+    qbuild.build()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    probs = sy.batch_problems(args.count, ensemble=args.ensemble)
+    ctxs = []
+    for p in probs:
+        c = Context("fp32", profile=args.profile_batch)
+        c.set_problem(p)
+        ctxs.append(c)
+    us = [torch.tensor(p.u, dtype=torch.float64, device="cuda") for p in probs]
+    gs = [torch.empty_like(u) for u in us]
+    outs = [torch.empty(6, dtype=torch.float64, device="cuda") for _ in probs]
+    ptr = lambda ts: [t.data_ptr() for t in ts]
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def batch():
+        qoc_evaluate_batch(ctxs, ptr(us), ptr(gs), ptr(outs), stream.cuda_stream)
+
+    def one_by_one():
+        for c, u, g, o in zip(ctxs, us, gs, outs):
+            c.evaluate_device(u.data_ptr(), g.data_ptr(), o.data_ptr())
+            c.sync()
+
+    for _ in range(max(args.warmup, 1)):
+        batch()
+    torch.cuda.synchronize()
+    K = args.steps
+    ts = []
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        for _ in range(K):
+            flush.zero_()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            e = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            batch()
+            e.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(e))
+    ms = sum(ts) / len(ts)
+    by_d = {}
+    if args.profile_batch:     # per-kernel event time summed over the contexts (overlapping)
+        for c, p in zip(ctxs, probs):
+            for k, (n_l, t) in c.profile().items():
+                key = f"d{p.d}:{k}"
+                by_d[key] = by_d.get(key, 0.0) + t / K
+        for c in ctxs:
+            c.reset_profile()
+    one_by_one()
+    t0 = time.perf_counter()
+    for _ in range(max(1, min(K, 2))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        one_by_one()
+    ms_seq = (time.perf_counter() - t0) * 1e3 / max(1, min(K, 2))
+    units = sum(p.N * p.E for p in probs)
+    line = {"metric": METRIC, "value": units / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": K,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded batched sweep)",
+            "config": {"workload": f"batch{args.count}_E{args.ensemble}", "problems": args.count,
+                       "members": args.ensemble, "slice_steps_per_step": units,
+                       "d_counts": {str(d): sum(1 for p in probs if p.d == d) for d in sorted({p.d for p in probs})}},
+            "one_by_one_ms_per_step": ms_seq, "batch_speedup_vs_one_by_one": ms_seq / ms,
+            "kernel_ms_by_d": {k: round(v, 3) for k, v in sorted(by_d.items(), key=lambda kv: -kv[1])[:16]},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    for c in ctxs:
+        c.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
+    elif args.workload.startswith("batch"):
+        batch_arm(args)
     else:
         ours_arm(args)
 

@@ -58,8 +58,10 @@ typedef enum qoc_precision {
     QOC_PREC_FP64 = 0,          /* plain FP64 form: parity anchor */
     QOC_PREC_FP32 = 1,          /* FP32 propagation, costates and adjoint; slice exponentials in
                                    split hi+lo FP32 (see qoc_options.plain_fp32_exp) */
-    QOC_PREC_TF32_SPLIT = 2,    /* large d: TF32 tensor-core products, hi+lo split, FP32 accum */
-    QOC_PREC_BF16_SPLIT = 3     /* large d: BF16 tensor-core products, hi+lo split, FP32 accum */
+    QOC_PREC_TF32_SPLIT = 2,    /* the FP32 form, with the products of the large-d adjoint (d > 64)
+                                   on tcgen05 tensor cores: TF32 hi + lo split, three MMAs per real
+                                   product, FP32 accumulation in tensor memory */
+    QOC_PREC_BF16_SPLIT = 3     /* reserved; qoc_create returns QOC_ERR_UNSUPPORTED */
 } qoc_precision;
 
 typedef struct qoc_options {

@@ -143,11 +143,12 @@ struct qoc_ctx {
     Profiler prof;
 
     DevBuf H64, HR, dDelta, norms, psiTR, pathR, fmask, colw, ckpt, Ubuf, states, Gbuf, src, carry, Oj, C5j, Ofin,
-        gpart, prm, u_h, grad_h, out_h, scratch;
+        gpart, prm, u_h, grad_h, out_h, scratch, tc_planes;
+    TcMaps tc_maps{};
 
     size_t device_bytes() const {
         const DevBuf* all[] = {&H64, &HR, &dDelta, &norms, &psiTR, &pathR, &fmask, &colw, &ckpt, &Ubuf, &states,
-                               &Gbuf, &src, &carry, &Oj, &C5j, &Ofin, &gpart, &prm, &u_h, &grad_h, &out_h, &scratch};
+                               &Gbuf, &src, &carry, &Oj, &C5j, &Ofin, &gpart, &prm, &u_h, &grad_h, &out_h, &scratch, &tc_planes};
         size_t s = 0;
         for (auto* b : all) s += b->bytes;
         return s;
@@ -191,6 +192,9 @@ bool hermitian(const double* H, int d) {
 
 bool is_fp64(const qoc_ctx* c) { return c->opt.precision == QOC_PREC_FP64; }
 
+// TF32_SPLIT: the FP32 form with the large-d adjoint products on tcgen05 (TF32 x3 split)
+bool use_tc(const qoc_ctx* c) { return c->opt.precision == QOC_PREC_TF32_SPLIT && c->path_kind == 1; }
+
 template <typename R>
 bool split_exp(const qoc_ctx* c) {
     return sizeof(R) == 4 && c->opt.plain_fp32_exp == 0;
@@ -210,7 +214,13 @@ void plan_impl(qoc_ctx* c) {
         if (c->w[s] > 0.0) c->cols.push_back(s);
     const int S = (int)c->cols.size();
     c->S_eff = S;
-    c->cb = std::min(S, 8);
+    // column panel width: one CTA of a serial sweep per panel and member; narrow panels spread
+    // a wide block over more SMs (about two sweep CTAs per SM), up to 8 columns per panel
+    int sms0 = 0;
+    cudaDeviceGetAttribute(&sms0, cudaDevAttrMultiProcessorCount, c->opt.device);
+    const long want_ctas = 2L * std::max(sms0, 1);
+    c->cb = (int)std::max(1L, std::min<long>(8, ((long)S * E + want_ctas - 1) / want_ctas));
+    c->cb = std::min(c->cb, S);
     c->ncb = (S + c->cb - 1) / c->cb;
     c->Spad = c->ncb * c->cb;
     const int align_elems = (int)(16 / cs) > 0 ? (int)(16 / cs) : 1;
@@ -246,7 +256,8 @@ void plan_impl(qoc_ctx* c) {
     }
     if (c->path_kind == 1 && c->opt.wave_slices <= 0) {
         // batched path: as many whole checkpoint segments as the scratch budget allows
-        const size_t per = big_scratch_per_item(d, sizeof(R) == 8) * (size_t)E;
+        size_t per = big_scratch_per_item(d, sizeof(R) == 8) * (size_t)E;
+        if (use_tc(c)) per += tc_scratch_floats(d, 1) * sizeof(float) * (size_t)E;
         const size_t budget = (size_t)2 << 30;
         W = std::max(seg, (int)std::min<size_t>((size_t)N + seg, budget / std::max<size_t>(per, 1)) / seg * seg);
     }
@@ -328,6 +339,13 @@ void plan_impl(qoc_ctx* c) {
         A(c->scratch, per * (size_t)E * W, "alloc batched scratch");
     } else {
         c->scratch.release();
+    }
+    if (use_tc(c)) {
+        A(c->tc_planes, tc_scratch_floats(d, E * W) * sizeof(float), "alloc tensor-core planes");
+        check_cuda(c, cudaMemsetAsync(c->tc_planes.p, 0, c->tc_planes.bytes, st), "clear planes");
+        check_cuda(c, tc_make_maps(c->tc_planes.as<float>(), d, E * W, &c->tc_maps), "tensor maps");
+    } else {
+        c->tc_planes.release();
     }
     // second stream and the dependency events between the two streams
     if (!c->aux) check_cuda(c, cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking), "create stream");
@@ -453,6 +471,16 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
     };
     auto expm_adj = [&](int w) -> cudaError_t {
         const int j0 = w * W, wlen = std::min(W, N - j0);
+        if constexpr (sizeof(R) == 4) {
+            if (big && use_tc(c)) {
+                int n_l = 0;
+                TcAdjArgs ta{prm, sys, sv, d, E, j0, wlen, W, hp.p, hp.n, Sb(w), Gb(w), c->tc_planes.as<float>(),
+                             c->tc_maps, c->gpart.as<double>()};
+                cudaError_t e = launch_tc_adj(ta, st, &n_l);
+                extra += n_l - 1;
+                return e;
+            }
+        }
         if (big) {
             int n_l = 0;
             cudaError_t e = launch_big_adj<R>(big_args(w), sys, sv, Sb(w), Gb(w), c->gpart.as<double>(), hp.p, hp.n, st,
@@ -583,6 +611,7 @@ qoc_status qoc_create(qoc_ctx** out, const qoc_options* opt) {
     qoc_default_options(&o);
     if (opt) o = *opt;
     if (o.precision < QOC_PREC_FP64 || o.precision > QOC_PREC_BF16_SPLIT) return QOC_ERR_ARG;
+    if (o.precision == QOC_PREC_BF16_SPLIT) return QOC_ERR_UNSUPPORTED;
     if (!(o.tol >= 0.0) || !(o.theta_max >= 0.0) || o.ckpt_stride < 0 || o.wave_slices < 0) return QOC_ERR_ARG;
     const bool f64 = o.precision == QOC_PREC_FP64;
     if (o.tol == 0.0) o.tol = f64 ? 1e-15 : 1e-8;

@@ -113,6 +113,37 @@ template <typename R>
 cudaError_t launch_big_adj(const BigArgs<R>& a, const SysView<R>& sys, const StateView<R>& sv, const C_t<R>* states,
                            const C_t<R>* Gbuf, double* gpart, int p, int n, cudaStream_t st, int* launches);
 
+// ---- tensor-core (tcgen05) adjoint products of the large-d path, TF32_SPLIT form (k_tc.cu) ----
+constexpr int kTcMats = 10;   // XH, Ubar, and two sets of Z11 / Z12 in row and column layouts
+constexpr int kTcSplit = 3;   // TF32 terms per real value (hi, mid, lo)
+inline int tc_ld(int d) { return (d + 3) / 4 * 4; }   // row stride (elements): 16-byte rows for TMA
+struct TcTerm { int a_mat, b_mat, acc; };
+struct TcStep {
+    int nterms;
+    TcTerm t[3];
+    int kind, i, nacc;            // kind 0: Horner step i, 1: squaring
+    int out0_row, out0_col, out1_row, out1_col;
+};
+struct TcMats { int xh, ub, z11_row, z11_col, z12_row, z12_col; };
+struct TcMaps {                   // two CUtensorMap (128 bytes, 64-byte aligned) over the planes
+    alignas(64) unsigned char a[128];
+    alignas(64) unsigned char b[128];
+};
+struct TcAdjArgs {
+    DevParams* prm;
+    SysView<float> sys;
+    StateView<float> sv;
+    int d, E, j0, wlen, wmax, p, n;
+    const float2* states;
+    const float2* Gbuf;
+    float* planes;
+    TcMaps maps;
+    double* gpart;
+};
+size_t tc_scratch_floats(int d, int items);
+cudaError_t tc_make_maps(float* planes, int d, int items, TcMaps* maps);
+cudaError_t launch_tc_adj(const TcAdjArgs& a, cudaStream_t st, int* launches);
+
 // ---- serial sweeps (k_serial.cu) ----
 // mode 0: forward propagation of one wave (grid z = 1) from checkpoint `seg0`, storing the
 //         states of the wave and the carried block every `seg` slices (checkpoints seg0 + 1, ..)
