@@ -80,13 +80,21 @@ typedef struct qoc_options {
     int n_override;       /* >= 0 forces the squaring count n (diagnostics); < 0: heuristic */
     int profile;          /* != 0: bracket every kernel launch with CUDA events (qoc_get_profile) */
     int wave_slices;      /* slices whose propagators are held at once (one parallel launch),
-                             rounded up to a multiple of ckpt_stride; 0: twice the SM count.
+                             rounded up to a multiple of ckpt_stride.  0: half the evolution when
+                             two waves fit 1/8 of the free device memory (clamped to 1..32 GiB),
+                             so that nothing is recomputed, else the largest wave that fits.
                              Device memory is O(wave d^2 + N / ckpt_stride d S). */
     int plain_fp32_exp;   /* FP32 form only.  0 (default): the slice exponentials (forward and
                              recomputation) use split hi+lo FP32 arithmetic from an FP64 H_j, which
                              keeps the coherent rounding of H_j dt out of long evolutions;
                              != 0: plain FP32 exponentials (faster, diagnostics) */
+    int sweep;            /* form of the two recursions Psi_j = U_j Psi_{j-1} and the costate:
+                             QOC_SWEEP_AUTO (0), QOC_SWEEP_SERIAL (1: one step per slice), or
+                             QOC_SWEEP_SCAN (2: products of the U_j over each checkpoint segment by
+                             a parallel tree, a scan over segments, then all segments in parallel) */
 } qoc_options;
+
+enum { QOC_SWEEP_AUTO = 0, QOC_SWEEP_SERIAL = 1, QOC_SWEEP_SCAN = 2 };
 
 /* Information about the last evaluation (reading it synchronises the context stream). */
 typedef struct qoc_info {

@@ -35,6 +35,19 @@ __device__ __forceinline__ void pair_mac(float& hi, float& lo, float a, float bh
     two_sum_acc(hi, lo, p);
 }
 
+// (hi, lo) += (ah + al)(bh + bl), dropping al * bl
+__device__ __forceinline__ void pair_mac2(float& hi, float& lo, float ah, float al, float bh, float bl) {
+    const float p = ah * bh;
+    lo += fmaf(ah, bh, -p) + fmaf(ah, bl, al * bh);
+    two_sum_acc(hi, lo, p);
+}
+// acc += u x    (u and x carried: segment products)
+__device__ __forceinline__ void kmac(float4& acc, const float4 u, const float4 x) {
+    pair_mac2(acc.x, acc.z, u.x, u.z, x.x, x.z);
+    pair_mac2(acc.x, acc.z, -u.y, -u.w, x.y, x.w);
+    pair_mac2(acc.y, acc.w, u.x, u.z, x.y, x.w);
+    pair_mac2(acc.y, acc.w, u.y, u.w, x.x, x.z);
+}
 // acc += u x    (u plain, x carried)
 __device__ __forceinline__ void kmac(float4& acc, const float2 u, const float4 x) {
     pair_mac(acc.x, acc.z, u.x, x.x, x.z);
@@ -74,6 +87,7 @@ __device__ __forceinline__ void knorm(double2&) {}
 __device__ __forceinline__ float2 kround(const float4 a) { return make_float2(a.x + a.z, a.y + a.w); }
 __device__ __forceinline__ double2 kround(const double2 a) { return a; }
 __device__ __forceinline__ float4 kfrom(const float2 a) { return make_float4(a.x, a.y, 0.f, 0.f); }
+__device__ __forceinline__ float4 kfrom(const float4 a) { return a; }
 __device__ __forceinline__ double2 kfrom(const double2 a) { return a; }
 template <typename K> __device__ __forceinline__ K kzero();
 template <> __device__ __forceinline__ float4 kzero<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
@@ -100,9 +114,9 @@ __device__ __forceinline__ void ring_issue(unsigned char* slot, const void* gsrc
 // b = q, q + g, ... of row a of Mx (contiguous reads: the forward sweep streams U_j, the backward
 // sweep U_j^dag), then a shuffle reduction combines them.  Lane q = 0 owns the output: it adds
 // the source, normalises the pair, keeps it for the next step and hands it to `emit`.
-template <typename C, typename K, typename Emit>
+template <typename C, typename K, typename S = C, typename Emit>
 __device__ __forceinline__ void sweep_step(const C* __restrict__ Mx, const K* __restrict__ x, K* __restrict__ y,
-                                           const C* __restrict__ add, int d, int cb, int g, Emit emit) {
+                                           const S* __restrict__ add, int d, int cb, int g, Emit emit) {
     const int O = d * cb;
     const int ngroups = blockDim.x / g;
     const int gi = threadIdx.x / g, q = threadIdx.x - gi * g;
@@ -147,17 +161,17 @@ static void pick_sweep_shape(int d, int cb, bool pair, int& g, int& threads) {
 // ------------------------------------------------------------------------------------------
 // forward propagation (mode 0) and checkpoint replay (mode 1)
 // ------------------------------------------------------------------------------------------
-template <typename R, int RING>
+template <typename R, int RING, typename Mt>
 __global__ void __launch_bounds__(1024)
 k_chain(int d, StateView<R> sv, int wlen, int seg, int mode, K_t<R>* __restrict__ ckpt, size_t ck_estride, int seg0,
-        int nseg_total, const C_t<R>* __restrict__ Ubuf, long long ustride, int wmax, C_t<R>* __restrict__ states,
+        int nseg_total, const Mt* __restrict__ Ubuf, long long ustride, int wmax, C_t<R>* __restrict__ states,
         int g) {
     using C = C_t<R>;
     using K = K_t<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int kb = blockIdx.x, e = blockIdx.y, z = blockIdx.z, tid = threadIdx.x, cb = sv.cb;
     const size_t slice = sv.slice(), panel = (size_t)d * cb;
-    const size_t ub = ring_bytes((size_t)d * d, sizeof(C));
+    const size_t ub = ring_bytes((size_t)d * d, sizeof(Mt));
     unsigned char* ring = smraw;
     K* xa = reinterpret_cast<K*>(smraw + RING * ub);   // RING 0: no ring, rows read from global
     K* xb = xa + panel;
@@ -172,7 +186,7 @@ k_chain(int d, StateView<R> sv, int wlen, int seg, int mode, K_t<R>* __restrict_
         xa[i] = v;
         sdst[(size_t)t0 * slice + i] = kround(v);
     }
-    const C* Ue = Ubuf + (size_t)e * wmax * ustride;
+    const Mt* Ue = Ubuf + (size_t)e * wmax * ustride;
     auto emit_for = [&](int t) {
         C* dst = sdst + (size_t)(t + 1) * slice;
         K* ckd = nullptr;
@@ -187,7 +201,7 @@ k_chain(int d, StateView<R> sv, int wlen, int seg, int mode, K_t<R>* __restrict_
 #pragma unroll 1
         for (int t = t0; t < t1; ++t) {
             __syncthreads();
-            sweep_step<C, K>(Ue + (size_t)t * ustride, xa, xb, nullptr, d, cb, g, emit_for(t));
+            sweep_step<Mt, K, C>(Ue + (size_t)t * ustride, xa, xb, nullptr, d, cb, g, emit_for(t));
             K* tmp = xa; xa = xb; xb = tmp;
         }
     } else if constexpr (RING == 1) {   // one slot: synchronous copy
@@ -198,7 +212,7 @@ k_chain(int d, StateView<R> sv, int wlen, int seg, int mode, K_t<R>* __restrict_
             cp_async_commit();
             cp_async_wait<0>();
             __syncthreads();
-            sweep_step<C, K>(reinterpret_cast<const C*>(ring), xa, xb, nullptr, d, cb, g, emit_for(t));
+            sweep_step<Mt, K, C>(reinterpret_cast<const Mt*>(ring), xa, xb, nullptr, d, cb, g, emit_for(t));
             K* tmp = xa; xa = xb; xb = tmp;
         }
     } else {
@@ -215,161 +229,199 @@ k_chain(int d, StateView<R> sv, int wlen, int seg, int mode, K_t<R>* __restrict_
             const int tn = t + RING - 1;
             if (tn < t1) ring_issue(ring + ((k + RING - 1) % RING) * ub, Ue + (size_t)tn * ustride, ub);
             cp_async_commit();
-            sweep_step<C, K>(reinterpret_cast<const C*>(ring + (k % RING) * ub), xa, xb, nullptr, d, cb, g, emit_for(t));
+            sweep_step<Mt, K, C>(reinterpret_cast<const Mt*>(ring + (k % RING) * ub), xa, xb, nullptr, d, cb, g, emit_for(t));
             K* tmp = xa; xa = xb; xb = tmp;
         }
     }
 }
 
-template <typename R, int RING>
-static cudaError_t chain_ring(const ChainArgs<R>& a, size_t smem, cudaStream_t st) {
-    cudaError_t err = cudaFuncSetAttribute(k_chain<R, RING>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <typename R, int RING, typename Mt>
+static cudaError_t chain_ring(const ChainArgs<R>& a, const Mt* U, size_t smem, cudaStream_t st) {
+    cudaError_t err =
+        cudaFuncSetAttribute(k_chain<R, RING, Mt>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     int g = 1, threads = 256;
     pick_sweep_shape(a.d, a.sv.cb, sizeof(R) == 4, g, threads);
     const int nz = a.mode == 0 ? 1 : (a.wlen + a.seg - 1) / a.seg;
-    k_chain<R, RING><<<dim3(a.sv.ncb, a.E, nz), threads, smem, st>>>(a.d, a.sv, a.wlen, a.seg, a.mode, a.ckpt,
-                                                                      a.ck_estride, a.seg0, a.nseg_total, a.Ubuf,
-                                                                      a.ustride, a.wmax, a.states, g);
+    k_chain<R, RING, Mt><<<dim3(a.sv.ncb, a.E, nz), threads, smem, st>>>(a.d, a.sv, a.wlen, a.seg, a.mode, a.ckpt,
+                                                                          a.ck_estride, a.seg0, a.nseg_total, U,
+                                                                          a.ustride, a.wmax, a.states, g);
     return cudaGetLastError();
 }
 
-template <typename R>
-cudaError_t launch_chain(const ChainArgs<R>& a, cudaStream_t st) {
-    const size_t ub = ring_bytes((size_t)a.d * a.d, sizeof(C_t<R>));
+template <typename R, typename Mt>
+static cudaError_t chain_dispatch(const ChainArgs<R>& a, const Mt* U, cudaStream_t st) {
+    const size_t ub = ring_bytes((size_t)a.d * a.d, sizeof(Mt));
     const size_t xs = 2 * (size_t)a.d * a.sv.cb * sizeof(K_t<R>);
     if (xs > kMaxDynSmem) return cudaErrorInvalidValue;
     for (int ring : {8, 4, 2, 1}) {
         const size_t smem = ring * ub + xs;
         if (smem > kMaxDynSmem) continue;
-        if (ring == 8) return chain_ring<R, 8>(a, smem, st);
-        if (ring == 4) return chain_ring<R, 4>(a, smem, st);
-        if (ring == 2) return chain_ring<R, 2>(a, smem, st);
-        return chain_ring<R, 1>(a, smem, st);
+        if (ring == 8) return chain_ring<R, 8, Mt>(a, U, smem, st);
+        if (ring == 4) return chain_ring<R, 4, Mt>(a, U, smem, st);
+        if (ring == 2) return chain_ring<R, 2, Mt>(a, U, smem, st);
+        return chain_ring<R, 1, Mt>(a, U, smem, st);
     }
-    return chain_ring<R, 0>(a, xs, st);   // slice larger than SMEM: stream its rows
+    return chain_ring<R, 0, Mt>(a, U, xs, st);   // slice larger than SMEM: stream its rows
+}
+
+template <typename R>
+cudaError_t launch_chain(const ChainArgs<R>& a, cudaStream_t st) {
+    if ((a.Ubuf != nullptr) == (a.Uk != nullptr)) return cudaErrorInvalidValue;
+    if (a.Uk) return chain_dispatch<R, K_t<R>>(a, a.Uk, st);
+    return chain_dispatch<R, C_t<R>>(a, a.Ubuf, st);
 }
 
 // ------------------------------------------------------------------------------------------
-// backward costate sweep over one wave: G_{j-1} = U_j^dag G_j + src_{j-1}
+// backward costate sweep: G_{j-1} = U_j^dag G_j + src_{j-1}, one CTA per (panel, member, segment)
 // ------------------------------------------------------------------------------------------
-template <typename R, int RING>
-__global__ void __launch_bounds__(1024)
-k_costate(int d, StateView<R> sv, int wlen, const C_t<R>* __restrict__ Ubuf, long long ustride, int wmax,
-          const C_t<R>* __restrict__ src, K_t<R>* __restrict__ carry, C_t<R>* __restrict__ Gbuf, int g) {
+// Segment z covers local slices a = z * seg .. b = min(wlen, a + seg) - 1.  With in-carry Y
+// (zero when a.cin is null) the CTA sets G_b = Y + src_b, runs G_{jl-1} = U_jl^dag G_jl + src_{jl-1}
+// down to jl = a + 1, and leaves out = U_a^dag G_a, the in-carry of the segment below; `out`
+// goes to a.cout.  A whole wave is one segment (seg = wlen) with the carry as in- and out-carry.
+template <typename R, int RING, typename S, typename Mt>
+__global__ void __launch_bounds__(1024) k_costate(CostateArgs<R> A, int g) {
     using C = C_t<R>;
     using K = K_t<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int kb = blockIdx.x, e = blockIdx.y, tid = threadIdx.x, cb = sv.cb;
-    const size_t slice = sv.slice(), panel = (size_t)d * cb;
-    const size_t ub = ring_bytes((size_t)d * d, sizeof(C));
-    const size_t pb = (size_t)sv.pstride * sizeof(C);
+    const int kb = blockIdx.x, e = blockIdx.y, z = blockIdx.z, tid = threadIdx.x;
+    const int d = A.d, cb = A.sv.cb;
+    const int a0 = z * A.seg;
+    if (a0 >= A.wlen) return;
+    const int b0 = min(A.wlen, a0 + A.seg) - 1;
+    const int n = b0 - a0 + 1;
+    const size_t slice = A.sv.slice(), panel = (size_t)d * cb, poff = (size_t)kb * A.sv.pstride;
+    const size_t ub = ring_bytes((size_t)d * d, sizeof(Mt));
+    const size_t pb = (size_t)A.sv.pstride * sizeof(S);
     const size_t slot = ub + pb;
     unsigned char* ring = smraw;
     K* xa = reinterpret_cast<K*>(smraw + RING * slot);   // RING 0: no ring
     K* xb = xa + panel;
-    const C* UHe = Ubuf + (size_t)e * wmax * ustride + ustride / 2;     // U_j^dag of every slice
-    const C* Se = src + (size_t)e * wmax * slice + (size_t)kb * sv.pstride;
-    C* Ge = Gbuf + (size_t)e * wmax * slice + (size_t)kb * sv.pstride;
-    K* ce = carry + (size_t)e * slice + (size_t)kb * sv.pstride;
-    {   // G at the last slice of the wave = carry + src
-        const C* s_last = Se + (size_t)(wlen - 1) * slice;
-        C* g_last = Ge + (size_t)(wlen - 1) * slice;
+    const Mt* UHe = reinterpret_cast<const Mt*>(A.Uk ? (const void*)A.Uk : (const void*)A.U) + e * A.u_es +
+                    A.ustride / 2;                        // U_j^dag of every slice
+    const S* Se = reinterpret_cast<const S*>(A.srck ? (const void*)A.srck : (const void*)A.src) + e * A.src_es + poff;
+    C* Ge = A.G ? A.G + e * A.g_es + poff : nullptr;
+    K* Gk = A.Gk ? A.Gk + e * A.g_es + poff : nullptr;
+    {   // G_b = Y + src_b
+        const K* ci = A.cin ? A.cin + e * A.cin_es + (size_t)z * slice + poff : nullptr;
+        const S* s_last = Se + (size_t)b0 * slice;
         for (int i = tid; i < (int)panel; i += blockDim.x) {
-            K v = ce[i];
+            K v = ci ? ci[i] : kzero<K>();
             kadd(v, kfrom(s_last[i]));
             knorm(v);
             xa[i] = v;
-            g_last[i] = kround(v);
+            if (Ge) Ge[(size_t)b0 * slice + i] = kround(v);
+            if (Gk) Gk[(size_t)b0 * slice + i] = v;
         }
     }
     auto emit_for = [&](int jl) {
-        C* gd = (jl > 0) ? Ge + (size_t)(jl - 1) * slice : nullptr;
+        C* gd = (Ge && jl > a0) ? Ge + (size_t)(jl - 1) * slice : nullptr;
+        K* gk = (Gk && jl > a0) ? Gk + (size_t)(jl - 1) * slice : nullptr;
         return [=](int o, const K& v) {
             if (gd) gd[o] = kround(v);
+            if (gk) gk[o] = v;
         };
     };
+    // step t handles slice jl = b0 - t: U_jl^dag and src_{jl-1} (none at the segment's first slice)
     if constexpr (RING == 0) {          // rows of U^dag and the sources read from global/L2
 #pragma unroll 1
-        for (int t = 0; t < wlen; ++t) {
-            const int jl = wlen - 1 - t;
+        for (int t = 0; t < n; ++t) {
+            const int jl = b0 - t;
             __syncthreads();
-            sweep_step<C, K>(UHe + (size_t)jl * ustride, xa, xb, (jl > 0) ? Se + (size_t)(jl - 1) * slice : nullptr,
-                             d, cb, g, emit_for(jl));
+            sweep_step<Mt, K, S>(UHe + (size_t)jl * A.ustride, xa, xb, (jl > a0) ? Se + (size_t)(jl - 1) * slice : nullptr,
+                                d, cb, g, emit_for(jl));
             K* tmp = xa; xa = xb; xb = tmp;
         }
     } else if constexpr (RING == 1) {
 #pragma unroll 1
-        for (int t = 0; t < wlen; ++t) {
-            const int jl = wlen - 1 - t;
+        for (int t = 0; t < n; ++t) {
+            const int jl = b0 - t;
             __syncthreads();
-            ring_issue(ring, UHe + (size_t)jl * ustride, ub);
-            if (jl > 0) ring_issue(ring + ub, Se + (size_t)(jl - 1) * slice, pb);
+            ring_issue(ring, UHe + (size_t)jl * A.ustride, ub);
+            if (jl > a0) ring_issue(ring + ub, Se + (size_t)(jl - 1) * slice, pb);
             cp_async_commit();
             cp_async_wait<0>();
             __syncthreads();
-            sweep_step<C, K>(reinterpret_cast<const C*>(ring), xa, xb,
-                             (jl > 0) ? reinterpret_cast<const C*>(ring + ub) : nullptr, d, cb, g, emit_for(jl));
+            sweep_step<Mt, K, S>(reinterpret_cast<const Mt*>(ring), xa, xb,
+                                (jl > a0) ? reinterpret_cast<const S*>(ring + ub) : nullptr, d, cb, g, emit_for(jl));
             K* tmp = xa; xa = xb; xb = tmp;
         }
     } else {
-        auto issue = [&](int t) {     // step t handles slice jl = wlen - 1 - t: U_jl^dag and src_{jl-1}
-            const int jl = wlen - 1 - t;
+        auto issue = [&](int t) {
+            const int jl = b0 - t;
             unsigned char* sl = ring + (t % RING) * slot;
-            ring_issue(sl, UHe + (size_t)jl * ustride, ub);
-            if (jl > 0) ring_issue(sl + ub, Se + (size_t)(jl - 1) * slice, pb);
+            ring_issue(sl, UHe + (size_t)jl * A.ustride, ub);
+            if (jl > a0) ring_issue(sl + ub, Se + (size_t)(jl - 1) * slice, pb);
         };
 #pragma unroll 1
         for (int t = 0; t < RING - 1; ++t) {
-            if (t < wlen) issue(t);
+            if (t < n) issue(t);
             cp_async_commit();
         }
 #pragma unroll 1
-        for (int t = 0; t < wlen; ++t) {
-            const int jl = wlen - 1 - t;
+        for (int t = 0; t < n; ++t) {
+            const int jl = b0 - t;
             cp_async_wait<(RING >= 2 ? RING - 2 : 0)>();
             __syncthreads();
             const int tn = t + RING - 1;
-            if (tn < wlen) issue(tn);
+            if (tn < n) issue(tn);
             cp_async_commit();
             const unsigned char* sl = ring + (t % RING) * slot;
-            sweep_step<C, K>(reinterpret_cast<const C*>(sl), xa, xb,
-                             (jl > 0) ? reinterpret_cast<const C*>(sl + ub) : nullptr, d, cb, g, emit_for(jl));
+            sweep_step<Mt, K, S>(reinterpret_cast<const Mt*>(sl), xa, xb,
+                                (jl > a0) ? reinterpret_cast<const S*>(sl + ub) : nullptr, d, cb, g, emit_for(jl));
             K* tmp = xa; xa = xb; xb = tmp;
         }
     }
     __syncthreads();
-    for (int i = tid; i < (int)panel; i += blockDim.x) ce[i] = xa[i];
+    if (A.cout) {
+        K* co = A.cout + e * A.cout_es + (size_t)z * slice + poff;
+        for (int i = tid; i < (int)panel; i += blockDim.x) co[i] = xa[i];
+    }
+    if (A.zero_next && z == gridDim.z - 1) {   // clear the slot after the last out-carry
+        K* co = A.cout + e * A.cout_es + (size_t)(z + 1) * slice + poff;
+        for (int i = tid; i < (int)panel; i += blockDim.x) co[i] = kzero<K>();
+    }
 }
 
-template <typename R, int RING>
-static cudaError_t costate_ring(int d, StateView<R> sv, int wlen, int E, const C_t<R>* Ubuf, long long ustride,
-                                int wmax, const C_t<R>* src, K_t<R>* carry, C_t<R>* Gbuf, size_t smem, cudaStream_t st) {
-    cudaError_t err = cudaFuncSetAttribute(k_costate<R, RING>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <typename R, int RING, typename S, typename Mt>
+static cudaError_t costate_ring(const CostateArgs<R>& a, size_t smem, cudaStream_t st) {
+    cudaError_t err =
+        cudaFuncSetAttribute(k_costate<R, RING, S, Mt>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     int g = 1, threads = 256;
-    pick_sweep_shape(d, sv.cb, sizeof(R) == 4, g, threads);
-    k_costate<R, RING><<<dim3(sv.ncb, E), threads, smem, st>>>(d, sv, wlen, Ubuf, ustride, wmax, src, carry, Gbuf, g);
+    pick_sweep_shape(a.d, a.sv.cb, sizeof(R) == 4, g, threads);
+    const int nz = (a.wlen + a.seg - 1) / a.seg;
+    k_costate<R, RING, S, Mt><<<dim3(a.sv.ncb, a.E, nz), threads, smem, st>>>(a, g);
     return cudaGetLastError();
 }
 
-template <typename R>
-cudaError_t launch_costate(int d, StateView<R> sv, int wlen, int E, const C_t<R>* Ubuf, long long ustride, int wmax,
-                           const C_t<R>* src, K_t<R>* carry, C_t<R>* Gbuf, cudaStream_t st) {
-    const size_t panel = (size_t)d * sv.cb;
-    const size_t ub = ring_bytes((size_t)d * d, sizeof(C_t<R>));
-    const size_t pb = (size_t)sv.pstride * sizeof(C_t<R>);
+template <typename R, typename S, typename Mt>
+static cudaError_t costate_dispatch(const CostateArgs<R>& a, cudaStream_t st) {
+    const size_t panel = (size_t)a.d * a.sv.cb;
+    const size_t ub = ring_bytes((size_t)a.d * a.d, sizeof(Mt));
+    const size_t pb = (size_t)a.sv.pstride * sizeof(S);
     const size_t fixed = 2 * panel * sizeof(K_t<R>);
     if (fixed > kMaxDynSmem) return cudaErrorInvalidValue;
     for (int ring : {8, 4, 2, 1}) {
         const size_t smem = ring * (ub + pb) + fixed;
         if (smem > kMaxDynSmem) continue;
-        if (ring == 8) return costate_ring<R, 8>(d, sv, wlen, E, Ubuf, ustride, wmax, src, carry, Gbuf, smem, st);
-        if (ring == 4) return costate_ring<R, 4>(d, sv, wlen, E, Ubuf, ustride, wmax, src, carry, Gbuf, smem, st);
-        if (ring == 2) return costate_ring<R, 2>(d, sv, wlen, E, Ubuf, ustride, wmax, src, carry, Gbuf, smem, st);
-        return costate_ring<R, 1>(d, sv, wlen, E, Ubuf, ustride, wmax, src, carry, Gbuf, smem, st);
+        if (ring == 8) return costate_ring<R, 8, S, Mt>(a, smem, st);
+        if (ring == 4) return costate_ring<R, 4, S, Mt>(a, smem, st);
+        if (ring == 2) return costate_ring<R, 2, S, Mt>(a, smem, st);
+        return costate_ring<R, 1, S, Mt>(a, smem, st);
     }
-    return costate_ring<R, 0>(d, sv, wlen, E, Ubuf, ustride, wmax, src, carry, Gbuf, fixed, st);
+    return costate_ring<R, 0, S, Mt>(a, fixed, st);
+}
+
+template <typename R>
+cudaError_t launch_costate(const CostateArgs<R>& a, cudaStream_t st) {
+    if (a.wlen <= 0 || a.seg <= 0 || (a.zero_next && !a.cout) || (a.src != nullptr) == (a.srck != nullptr))
+        return cudaErrorInvalidValue;
+    if ((a.U != nullptr) == (a.Uk != nullptr)) return cudaErrorInvalidValue;
+    // carried sources go with carried matrices (the scan over segments), plain with plain
+    if (a.srck && a.Uk) return costate_dispatch<R, K_t<R>, K_t<R>>(a, st);
+    if (a.src && a.U) return costate_dispatch<R, C_t<R>, C_t<R>>(a, st);
+    return cudaErrorInvalidValue;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -416,8 +468,7 @@ cudaError_t launch_to_carry(const double2* src, K_t<R>* dst, int d, int S, State
 
 #define QOC_SERIAL_INST(R)                                                                                        \
     template cudaError_t launch_chain<R>(const ChainArgs<R>&, cudaStream_t);                                      \
-    template cudaError_t launch_costate<R>(int, StateView<R>, int, int, const C_t<R>*, long long, int,           \
-                                           const C_t<R>*, K_t<R>*, C_t<R>*, cudaStream_t);                        \
+    template cudaError_t launch_costate<R>(const CostateArgs<R>&, cudaStream_t);                                \
     template cudaError_t launch_to_carry<R>(const double2*, K_t<R>*, int, int, StateView<R>, int, size_t,        \
                                             cudaStream_t);
 QOC_SERIAL_INST(float)

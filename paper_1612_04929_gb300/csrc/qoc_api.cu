@@ -135,6 +135,8 @@ struct qoc_ctx {
     bool planned = false;
     int W = 0, nw = 0, seg = 0, nseg_total = 0, path_kind = 0;
     int Spad = 0, cb = 0, ncb = 0, pstride = 0, S_eff = 0;
+    bool scan = false;                   // segmented-scan form of the two recursions
+    int nzmax = 0;                       // checkpoint segments per wave
     std::vector<int> cols;               // propagated columns (positive weight)
     size_t mstride = 0;                  // elements per matrix slot of the batched path
     long long ustride = 0;
@@ -144,11 +146,14 @@ struct qoc_ctx {
 
     DevBuf H64, HR, dDelta, norms, psiTR, pathR, fmask, colw, ckpt, Ubuf, states, Gbuf, src, carry, Oj, C5j, Ofin,
         gpart, prm, u_h, grad_h, out_h, scratch, tc_planes;
+    // segmented scan: segment products (two wave sets), tree levels, scan states, costate carries
+    DevBuf Pbuf, lv0, lv1, scanst, hbuf, Ybuf;
     TcMaps tc_maps{};
 
     size_t device_bytes() const {
         const DevBuf* all[] = {&H64, &HR, &dDelta, &norms, &psiTR, &pathR, &fmask, &colw, &ckpt, &Ubuf, &states,
-                               &Gbuf, &src, &carry, &Oj, &C5j, &Ofin, &gpart, &prm, &u_h, &grad_h, &out_h, &scratch, &tc_planes};
+                               &Gbuf, &src, &carry, &Oj, &C5j, &Ofin, &gpart, &prm, &u_h, &grad_h, &out_h, &scratch,
+                               &tc_planes, &Pbuf, &lv0, &lv1, &scanst, &hbuf, &Ybuf};
         size_t s = 0;
         for (auto* b : all) s += b->bytes;
         return s;
@@ -226,49 +231,41 @@ void plan_impl(qoc_ctx* c) {
     const int align_elems = (int)(16 / cs) > 0 ? (int)(16 / cs) : 1;
     c->pstride = ((d * c->cb + align_elems - 1) / align_elems) * align_elems;
     const size_t slice = (size_t)c->ncb * c->pstride;
-    // checkpoint stride (sqrt N by default) and wave: the slices of one parallel launch, a
-    // multiple of the stride large enough to fill the GPU (independent of N)
+    // checkpoint stride (sqrt N by default)
     int seg = c->opt.ckpt_stride > 0 ? c->opt.ckpt_stride : (int)std::ceil(std::sqrt((double)N));
     seg = std::max(1, std::min(seg, N));
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->opt.device);
+    // one slice of the propagator buffer holds U_j and U_j^dag, each padded to 256 bytes
+    const long long ue = 256 / (long long)cs;
+    c->ustride = 2 * ((((long long)d * d + ue - 1) / ue) * ue);
+    c->scan = c->opt.sweep == QOC_SWEEP_SCAN || (c->opt.sweep == QOC_SWEEP_AUTO && seg >= 4);
+    // Wave: the slices whose propagators are held at once (a multiple of the stride).  Two wave
+    // sets alternate, and after the forward pass they still hold the last two waves, so with at
+    // most two waves nothing is recomputed in the backward pass.  By default the wave is half the
+    // evolution when both sets fit a memory budget (1/8 of the free device memory, between 1 and
+    // 32 GiB), else the largest wave that fits.
     int W = 0;
     if (c->opt.wave_slices > 0) {
         W = ((c->opt.wave_slices + seg - 1) / seg) * seg;
     } else {
-        // whole rounds of resident CTAs of the per-slice kernels: the largest multiple of the
-        // stride up to two rounds that keeps >= 90% of the CTA slots busy (else the best one)
-        const int per_sm = std::max(1, (int)(kMaxDynSmem / std::max<size_t>(1, fused_adj_smem<R>(d))));
-        const int cap = std::max(1, sms) * std::min(per_sm, 8);
-        const int kmax = std::max(1, (2 * cap + seg - 1) / seg);
-        int best_w = seg, good_w = 0;
-        double best_eff = -1.0;
-        for (int k = 1; k <= kmax; ++k) {
-            const int w = k * seg;
-            const double eff = (double)w / ((double)((w + cap - 1) / cap) * cap);
-            if (eff > best_eff) {
-                best_eff = eff;
-                best_w = w;
-            }
-            if (eff >= 0.9) good_w = w;
-        }
-        W = good_w > 0 ? good_w : best_w;
-    }
-    if (c->path_kind == 1 && c->opt.wave_slices <= 0) {
-        // batched path: as many whole checkpoint segments as the scratch budget allows
-        size_t per = big_scratch_per_item(d, sizeof(R) == 8) * (size_t)E;
-        if (use_tc(c)) per += tc_scratch_floats(d, 1) * sizeof(float) * (size_t)E;
-        const size_t budget = (size_t)2 << 30;
-        W = std::max(seg, (int)std::min<size_t>((size_t)N + seg, budget / std::max<size_t>(per, 1)) / seg * seg);
+        const size_t dd0 = (size_t)d * d, ks = sizeof(K_t<R>);
+        size_t per = 2 * ((size_t)c->ustride * cs + 3 * slice * cs);          // U, states, G, sources
+        if (c->path_kind == 1) per += big_scratch_per_item(d, sizeof(R) == 8);
+        if (use_tc(c)) per += tc_scratch_floats(d, 1) * sizeof(float);
+        if (c->scan) per += dd0 * ks + (2 * (size_t)c->ustride * ks + seg - 1) / seg;
+        per *= (size_t)E;
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = (size_t)8 << 30;
+        const size_t budget = std::min<size_t>((size_t)32 << 30, std::max<size_t>((size_t)1 << 30, free_b / 8));
+        const long long w_mem = std::max<long long>(seg, (long long)(budget / std::max<size_t>(per, 1)) / seg * seg);
+        const long long w_half = (((long long)N + 1) / 2 + seg - 1) / seg * seg;
+        W = (int)std::min<long long>(w_half, w_mem);
     }
     W = std::max(seg, std::min(W, ((N + seg - 1) / seg) * seg));
     c->seg = seg;
     c->W = W;
     c->nw = (N + W - 1) / W;
     c->nseg_total = (N + seg - 1) / seg;
-    // one slice of the propagator buffer holds U_j and U_j^dag, each padded to 256 bytes
-    const long long ue = 256 / (long long)cs;
-    c->ustride = 2 * ((((long long)d * d + ue - 1) / ue) * ue);
+    c->nzmax = W / seg;
     const int nseg_total = c->nseg_total;
 
     StateView<R> sv{c->Spad, c->cb, c->ncb, c->pstride};
@@ -346,6 +343,18 @@ void plan_impl(qoc_ctx* c) {
         check_cuda(c, tc_make_maps(c->tc_planes.as<float>(), d, E * W, &c->tc_maps), "tensor maps");
     } else {
         c->tc_planes.release();
+    }
+    if (c->scan) {
+        const size_t nz = (size_t)c->nzmax, ks = sizeof(K_t<R>);
+        const size_t half = (size_t)((seg + 1) / 2);
+        A(c->Pbuf, 2 * (size_t)E * nz * c->ustride * ks, "alloc segment products");
+        A(c->lv0, (size_t)E * nz * half * dd * ks, "alloc tree level");
+        A(c->lv1, (size_t)E * nz * half * dd * ks, "alloc tree level");
+        A(c->scanst, (size_t)E * (nz + 1) * slice * cs, "alloc scan states");
+        A(c->hbuf, (size_t)E * (nz + 1) * slice * ks, "alloc segment costates");
+        A(c->Ybuf, 2 * (size_t)E * nz * slice * ks, "alloc segment carries");
+    } else {
+        for (DevBuf* b : {&c->Pbuf, &c->lv0, &c->lv1, &c->scanst, &c->hbuf, &c->Ybuf}) b->release();
     }
     // second stream and the dependency events between the two streams
     if (!c->aux) check_cuda(c, cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking), "create stream");
@@ -490,46 +499,178 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
         }
         return launch_expm_adj_fused<R>(prm, sys, sv, j0, wlen, E, Sb(w), Gb(w), W, c->gpart.as<double>(), st);
     };
-    // ---- forward: exponentials on st, propagation and per-slice costs on sx ----
-    for (int w = 0; w < nw; ++w) {
-        const int j0 = w * W, wlen = std::min(W, N - j0);
-        if (w >= 2) wait(st, ev_fwd[w - 2]);           // set w % 2 released by wave w - 2
-        B(st);
-        L(expm_fwd(w), "expm_fwd", st);
-        rec(ev_exp[w], st);
-        wait(sx, ev_exp[w]);
-        B(sx);
-        L(launch_chain<R>(chain_args(w, 0), sx), "chain_fwd", sx);
-        B(sx);
-        L(launch_slice_costs<R>(d, sv, j0, wlen, N, E, Sb(w), W, cv, c->Oj.as<double2>(), c->C5j.as<double>(),
-                                c->Ofin.as<double2>(), sx),
-          "slice_costs", sx);
-        rec(ev_fwd[w], sx);
-    }
-    check_cuda(c, cudaMemsetAsync(c->carry.p, 0, c->carry.bytes, sx), "memset carry");
-    rec(ev_fwd_done, sx);
-    wait(st, ev_fwd_done);
-    // ---- backward: recompute + replay of wave w - 1 on st overlap the costate of wave w on sx ----
-    for (int w = nw - 1; w >= 0; --w) {
-        const int j0 = w * W, wlen = std::min(W, N - j0);
-        if (w != nw - 1) wait(sx, ev_rep[w]);           // the last wave is resident from the forward sweep
-        B(sx);
-        L(launch_sources<R>(d, sv, j0, wlen, N, E, Sb(w), W, cv, c->Oj.as<double2>(), c->Ofin.as<double2>(), Rb(w),
-                            sx),
-          "sources", sx);
-        B(sx);
-        L(launch_costate<R>(d, sv, wlen, E, Ub(w), c->ustride, W, Rb(w), c->carry.as<K>(), Gb(w), sx), "costate", sx);
-        rec(ev_cost[w], sx);
-        if (w >= 1) {                                    // set (w - 1) % 2 was released by wave w + 1
+    const int nzmax = c->nzmax;
+    const size_t p_set = (size_t)E * nzmax * c->ustride;
+    auto Pb = [&](int w) { return c->Pbuf.as<K>() + (w & 1) * p_set; };
+    auto Yb = [&](int w) { return c->Ybuf.as<K>() + (w & 1) * (size_t)E * nzmax * slice; };
+    auto seg_products = [&](int w) -> cudaError_t {
+        const int j0 = w * W;
+        SegProdArgs<R> a{d, E, std::min(W, N - j0), seg, nzmax, Ub(w), c->ustride, W,
+                         c->lv0.as<K>(), c->lv1.as<K>(), dd, Pb(w)};
+        int n_l = 0;
+        cudaError_t e = launch_seg_products<R>(a, st, &n_l);
+        extra += n_l - 1;
+        return e;
+    };
+    auto costate_args = [&](int w) {
+        const int j0 = w * W;
+        CostateArgs<R> a{};
+        a.d = d;
+        a.sv = sv;
+        a.wlen = std::min(W, N - j0);
+        a.seg = seg;
+        a.E = E;
+        a.U = Ub(w);
+        a.ustride = c->ustride;
+        a.u_es = (size_t)W * c->ustride;
+        a.src = Rb(w);
+        a.src_es = (size_t)W * slice;
+        a.g_es = (size_t)W * slice;
+        return a;
+    };
+    if (!c->scan) {
+        // ---- forward: exponentials on st, propagation and per-slice costs on sx ----
+        for (int w = 0; w < nw; ++w) {
+            const int j0 = w * W, wlen = std::min(W, N - j0);
+            if (w >= 2) wait(st, ev_fwd[w - 2]);           // set w % 2 released by wave w - 2
             B(st);
-            L(expm_fwd(w - 1), "expm_fwd (recompute)", st);
-            B(st);
-            L(launch_chain<R>(chain_args(w - 1, 1), st), "chain (replay)", st);
-            rec(ev_rep[w - 1], st);
+            L(expm_fwd(w), "expm_fwd", st);
+            rec(ev_exp[w], st);
+            wait(sx, ev_exp[w]);
+            B(sx);
+            L(launch_chain<R>(chain_args(w, 0), sx), "chain_fwd", sx);
+            B(sx);
+            L(launch_slice_costs<R>(d, sv, j0, wlen, N, E, Sb(w), W, cv, c->Oj.as<double2>(), c->C5j.as<double>(),
+                                    c->Ofin.as<double2>(), sx),
+              "slice_costs", sx);
+            rec(ev_fwd[w], sx);
         }
-        wait(st, ev_cost[w]);
-        B(st);
-        L(expm_adj(w), "expm_adj", st);
+        check_cuda(c, cudaMemsetAsync(c->carry.p, 0, c->carry.bytes, sx), "memset carry");
+        rec(ev_fwd_done, sx);
+        wait(st, ev_fwd_done);
+        // ---- backward: recompute + replay of wave w - 1 on st overlap the costate of wave w on sx ----
+        for (int w = nw - 1; w >= 0; --w) {
+            const int j0 = w * W, wlen = std::min(W, N - j0);
+            if (w != nw - 1) wait(sx, ev_rep[w]);           // the last wave is resident from the forward sweep
+            B(sx);
+            L(launch_sources<R>(d, sv, j0, wlen, N, E, Sb(w), W, cv, c->Oj.as<double2>(), c->Ofin.as<double2>(), Rb(w),
+                                sx),
+              "sources", sx);
+            B(sx);
+            CostateArgs<R> ca = costate_args(w);
+            ca.seg = ca.wlen;                                // the whole wave as one segment
+            ca.G = Gb(w);
+            ca.cin = c->carry.as<K>();
+            ca.cin_es = slice;
+            ca.cout = c->carry.as<K>();
+            ca.cout_es = slice;
+            L(launch_costate<R>(ca, sx), "costate", sx);
+            rec(ev_cost[w], sx);
+            if (w >= 1) {                                    // set (w - 1) % 2 was released by wave w + 1
+                if (w - 1 != nw - 2) {                       // wave nw - 2 is still resident
+                    B(st);
+                    L(expm_fwd(w - 1), "expm_fwd (recompute)", st);
+                    B(st);
+                    L(launch_chain<R>(chain_args(w - 1, 1), st), "chain (replay)", st);
+                }
+                rec(ev_rep[w - 1], st);
+            }
+            wait(st, ev_cost[w]);
+            B(st);
+            L(expm_adj(w), "expm_adj", st);
+        }
+    } else {
+        // ---- forward: exponentials and segment products on st; the scan over segments
+        //      (checkpoints) on sx; replay of every segment and the per-slice costs on st ----
+        cudaEvent_t* ev_scan = ev_fwd;
+        auto replay_costs = [&](int w) {
+            const int j0 = w * W, wlen = std::min(W, N - j0);
+            wait(st, ev_scan[w]);
+            B(st);
+            L(launch_chain<R>(chain_args(w, 1), st), "chain (replay)", st);
+            B(st);
+            L(launch_slice_costs<R>(d, sv, j0, wlen, N, E, Sb(w), W, cv, c->Oj.as<double2>(), c->C5j.as<double>(),
+                                    c->Ofin.as<double2>(), st),
+              "slice_costs", st);
+        };
+        for (int w = 0; w < nw; ++w) {
+            const int j0 = w * W, wlen = std::min(W, N - j0);
+            const int nz = (wlen + seg - 1) / seg;
+            B(st);
+            L(expm_fwd(w), "expm_fwd", st);
+            B(st);
+            L(seg_products(w), "seg_products", st);
+            rec(ev_exp[w], st);
+            wait(sx, ev_exp[w]);
+            B(sx);
+            L(launch_chain<R>(ChainArgs<R>{d, sv, nz, 1, 0, E, c->ckpt.as<K>(), (size_t)c->nseg_total * slice, j0 / seg,
+                                           c->nseg_total, nullptr, c->ustride, nzmax, c->scanst.as<C>(), Pb(w)},
+                              sx),
+              "scan", sx);
+            rec(ev_scan[w], sx);
+            if (w >= 1) replay_costs(w - 1);
+        }
+        replay_costs(nw - 1);
+        rec(ev_fwd_done, st);
+        wait(sx, ev_fwd_done);
+        // ---- backward: per wave, the costate of every segment from a zero in-carry, the scan
+        //      Y_{z-1} = P_z^dag Y_z + h_z over segments, then every segment from its carry (sx);
+        //      recompute + replay of wave w - 1 and the adjoint of wave w on st ----
+        for (int w = nw - 1; w >= 0; --w) {
+            const int j0 = w * W, wlen = std::min(W, N - j0);
+            const int nz = (wlen + seg - 1) / seg;
+            if (w != nw - 1) wait(sx, ev_rep[w]);
+            B(sx);
+            L(launch_sources<R>(d, sv, j0, wlen, N, E, Sb(w), W, cv, c->Oj.as<double2>(), c->Ofin.as<double2>(), Rb(w),
+                                sx),
+              "sources", sx);
+            CostateArgs<R> loc = costate_args(w);
+            loc.cout = c->hbuf.as<K>();
+            loc.cout_es = (size_t)(nzmax + 1) * slice;
+            loc.zero_next = 1;
+            B(sx);
+            L(launch_costate<R>(loc, sx), "costate (segments)", sx);
+            CostateArgs<R> sc{};
+            sc.d = d;
+            sc.sv = sv;
+            sc.wlen = nz;
+            sc.seg = nz;
+            sc.E = E;
+            sc.Uk = Pb(w);
+            sc.ustride = c->ustride;
+            sc.u_es = (size_t)nzmax * c->ustride;
+            sc.srck = c->hbuf.as<K>() + slice;   // h_{z} is the source added after step z (slot nz is zero)
+            sc.src_es = (size_t)(nzmax + 1) * slice;
+            sc.Gk = Yb(w);
+            sc.g_es = (size_t)nzmax * slice;
+            sc.cin = (w == nw - 1) ? nullptr : Yb(w + 1);
+            sc.cin_es = (size_t)nzmax * slice;
+            B(sx);
+            L(launch_costate<R>(sc, sx), "costate (scan)", sx);
+            CostateArgs<R> fin = costate_args(w);
+            fin.G = Gb(w);
+            fin.cin = Yb(w);
+            fin.cin_es = (size_t)nzmax * slice;
+            fin.cout = Yb(w);   // out of segment z replaces its own in-carry; slot 0 feeds wave w - 1
+            fin.cout_es = (size_t)nzmax * slice;
+            B(sx);
+            L(launch_costate<R>(fin, sx), "costate (final)", sx);
+            rec(ev_cost[w], sx);
+            if (w >= 1) {
+                if (w - 1 != nw - 2) {   // the last two waves are still resident from the forward pass
+                    B(st);
+                    L(expm_fwd(w - 1), "expm_fwd (recompute)", st);
+                    B(st);
+                    L(seg_products(w - 1), "seg_products", st);
+                    B(st);
+                    L(launch_chain<R>(chain_args(w - 1, 1), st), "chain (replay)", st);
+                }
+                rec(ev_rep[w - 1], st);
+            }
+            wait(st, ev_cost[w]);
+            B(st);
+            L(expm_adj(w), "expm_adj", st);
+        }
     }
     rec(ev_join, sx);
     wait(st, ev_join);
@@ -612,7 +753,9 @@ qoc_status qoc_create(qoc_ctx** out, const qoc_options* opt) {
     if (opt) o = *opt;
     if (o.precision < QOC_PREC_FP64 || o.precision > QOC_PREC_BF16_SPLIT) return QOC_ERR_ARG;
     if (o.precision == QOC_PREC_BF16_SPLIT) return QOC_ERR_UNSUPPORTED;
-    if (!(o.tol >= 0.0) || !(o.theta_max >= 0.0) || o.ckpt_stride < 0 || o.wave_slices < 0) return QOC_ERR_ARG;
+    if (!(o.tol >= 0.0) || !(o.theta_max >= 0.0) || o.ckpt_stride < 0 || o.wave_slices < 0 || o.sweep < 0 ||
+        o.sweep > QOC_SWEEP_SCAN)
+        return QOC_ERR_ARG;
     const bool f64 = o.precision == QOC_PREC_FP64;
     if (o.tol == 0.0) o.tol = f64 ? 1e-15 : 1e-8;
     if (o.theta_max == 0.0) o.theta_max = f64 ? 0.25 : 1.0;

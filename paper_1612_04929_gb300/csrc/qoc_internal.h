@@ -156,15 +156,56 @@ struct ChainArgs {
     K_t<R>* ckpt;           // [E][nseg_total] carried blocks
     size_t ck_estride;      // elements per member
     int seg0, nseg_total;
-    const C_t<R>* Ubuf;
+    const C_t<R>* Ubuf;     // slice propagators, or ...
     long long ustride;
     int wmax;
     C_t<R>* states;         // [E][wmax + 1] FP32/FP64 blocks of the wave
+    const K_t<R>* Uk;       // ... carried segment products (exactly one of the two is set)
 };
 template <typename R> cudaError_t launch_chain(const ChainArgs<R>& a, cudaStream_t st);
+// Costate sweep G_{j-1} = U_j^dag G_j + src_{j-1}, split into segments of `seg` slices that run in
+// parallel (grid z): segment z (slices a..b) starts from G_b = Y_z + src_b with in-carry Y_z
+// (cin, or zero), writes G_b..G_a (rounded to G and/or carried to Gk) and leaves
+// U_a^dag G_a in cout.  Block (e, z) of cin / cout sits at base + e * es + z * slice.
 template <typename R>
-cudaError_t launch_costate(int d, StateView<R> sv, int wlen, int E, const C_t<R>* Ubuf, long long ustride, int wmax,
-                           const C_t<R>* src, K_t<R>* carry, C_t<R>* Gbuf, cudaStream_t st);
+struct CostateArgs {
+    int d;
+    StateView<R> sv;
+    int wlen, seg, E;
+    const C_t<R>* U;        // U_j at U + e * u_es + j * ustride, U_j^dag at + ustride / 2, or ...
+    const K_t<R>* Uk;       // ... carried segment products, same layout (exactly one is set)
+    long long ustride;
+    size_t u_es;
+    const C_t<R>* src;      // src_j at src + e * src_es + j * slice ...
+    const K_t<R>* srck;     // ... or carried sources (exactly one of the two is set)
+    size_t src_es;
+    C_t<R>* G;              // G_j (rounded) at G + e * g_es + j * slice, or nullptr
+    K_t<R>* Gk;             // G_j (carried), same layout, or nullptr
+    size_t g_es;
+    const K_t<R>* cin;      // in-carries or nullptr (zero)
+    size_t cin_es;
+    K_t<R>* cout;           // out-carries or nullptr
+    size_t cout_es;
+    int zero_next;          // also clear block (e, nz) of cout
+};
+template <typename R> cudaError_t launch_costate(const CostateArgs<R>& a, cudaStream_t st);
+
+// ---- segment products (k_scan.cu) ----
+// P_z = U_b ... U_a for every checkpoint segment z of a wave (a = z * seg, b = min(wlen, a + seg)
+// - 1) by a pairwise product tree in carried precision (log2(seg) batched launches), stored
+// carried with its adjoint: P_z at P + (e * nzmax + z) * ustride, P_z^dag at + ustride / 2.
+template <typename R>
+struct SegProdArgs {
+    int d, E, wlen, seg, nzmax;
+    const C_t<R>* U;        // U_j at U + (e * wmax + j) * ustride
+    long long ustride;
+    int wmax;
+    K_t<R>* lv0;            // two level buffers of E * nzmax * ceil(seg / 2) matrices of mstride
+    K_t<R>* lv1;
+    size_t mstride;
+    K_t<R>* P;
+};
+template <typename R> cudaError_t launch_seg_products(const SegProdArgs<R>& a, cudaStream_t st, int* launches);
 template <typename R>
 cudaError_t launch_to_carry(const double2* src, K_t<R>* dst, int d, int S, StateView<R> sv, int copies,
                             size_t dst_stride, cudaStream_t st);

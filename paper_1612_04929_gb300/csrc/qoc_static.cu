@@ -119,7 +119,17 @@ extern "C" qoc_status qoc_evaluate_static(int d, int M, int N, int S, double dt,
     if (!ok(launch_chain<R>(ch, st))) return QOC_ERR_CUDA;
     if (!ok(launch_slice_costs<R>(d, sv, 0, N, N, 1, states, N, cost, Oj, C5j, Ofin, st))) return QOC_ERR_CUDA;
     if (!ok(launch_sources<R>(d, sv, 0, N, N, 1, states, N, cost, Oj, Ofin, src, st))) return QOC_ERR_CUDA;
-    if (!ok(launch_costate<R>(d, sv, N, 1, Ubuf, ustride, N, src, carry, Gbuf, st))) return QOC_ERR_CUDA;
+    CostateArgs<R> co{};
+    co.d = d;
+    co.sv = sv;
+    co.wlen = co.seg = N;
+    co.E = 1;
+    co.U = Ubuf;
+    co.ustride = ustride;
+    co.src = src;
+    co.G = Gbuf;
+    co.cin = co.cout = carry;
+    if (!ok(launch_costate<R>(co, st))) return QOC_ERR_CUDA;
     if (!ok(launch_expm_adj_fused<R>(prm, sys, sv, 0, N, 1, states, Gbuf, N, gpart, st))) return QOC_ERR_CUDA;
     if (!ok(launch_finalize(1, M, N, u_dev, alpha, Oj, C5j, Ofin, gpart, grad_dev, out_dev, st)))
         return QOC_ERR_CUDA;

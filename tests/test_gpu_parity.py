@@ -142,6 +142,35 @@ def test_checkpoint_layout_does_not_change_results(precision, tol):
         assert np.max(np.abs(out[1] - ref[1])) <= tol * np.max(np.abs(ref[1]))
 
 
+SWEEP_CASES = [
+    ("fp64", dict(d=6, M=2, N=61, S=2, seed=311, nF=2, path=True, E=2), dict(ckpt_stride=5, wave_slices=15)),
+    ("fp64", dict(d=17, M=3, N=40, S=17, seed=312, nF=3), dict(ckpt_stride=8, wave_slices=16)),
+    ("fp32", dict(d=40, M=2, N=203, S=1, seed=313, nF=13), dict()),
+    ("fp32", dict(d=24, M=2, N=97, S=5, seed=314, nF=3, E=3, weights=True), dict(ckpt_stride=6, wave_slices=30)),
+    ("fp32", dict(d=40, M=2, N=45, S=40, seed=315, nF=4), dict(ckpt_stride=7, wave_slices=21)),
+]
+
+
+@pytest.mark.parametrize("precision,case,layout", SWEEP_CASES, ids=lambda x: str(x) if isinstance(x, str) else "")
+@pytest.mark.parametrize("sweep", ["serial", "scan"])
+def test_sweep_forms_match_oracle(precision, case, layout, sweep):
+    """Both forms of the recursions (one step per slice, or segment products + scan + parallel
+    segments) against the oracle, over several waves with ragged last waves and segments."""
+    prob = sy.random_problem(**case, dt=0.2, u_scale=0.8)
+    check(prob, precision, sweep=sweep, **layout)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-7)])
+def test_scan_agrees_with_serial_sweep(precision, tol):
+    """The segment products P_z are carried in the same extended precision as the propagated
+    block, so the two forms differ only in where that precision's roundings fall."""
+    prob = sy.random_problem(d=12, M=2, N=150, S=3, seed=316, nF=2, path=True, E=2)
+    a = run(prob, precision, sweep="serial", ckpt_stride=10, wave_slices=40)
+    b = run(prob, precision, sweep="scan", ckpt_stride=10, wave_slices=40)
+    assert abs(a[0] - b[0]) <= tol * abs(a[0])
+    assert np.max(np.abs(a[1] - b[1])) <= tol * np.max(np.abs(a[1]))
+
+
 # ------------------------------------------------------------------ the workloads
 def test_cnot2q_fp64_full_size():
     check(sy.cnot2q(), "fp64")
