@@ -69,7 +69,8 @@ typedef struct qoc_options {
     double tol;           /* bound on the Taylor remainder per slice after squaring; <= 0: default
                              (1e-15 FP64, 1e-8 otherwise) */
     double theta_max;     /* n is the least n >= 0 with theta / 2^n <= theta_max; <= 0: default
-                             (0.25 FP64, 1.0 otherwise) */
+                             (0.25 FP64; FP32 forms: 0.5 for d <= 68, the per-slice kernels, and
+                             1.0 for larger d) */
     int ckpt_stride;      /* slices between stored checkpoints of the propagated block Psi
                              (0: ceil(sqrt(N))).  The backward sweep regenerates Psi_j and U_j
                              between checkpoints instead of storing all N of them. */

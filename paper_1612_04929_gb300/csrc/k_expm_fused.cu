@@ -14,10 +14,10 @@
 //               This differentiates the truncated series exactly (not the first-order Eq. 11)
 //               without storing the p + n intermediate matrices.
 //
-// Thread layout: 256 threads as a 16 x 16 grid; thread (ty, tx) owns the MT x MT outputs
-// (ty + 16 a, tx + 16 b).  Matrices sit in shared memory padded to D = 16 MT rows with a
-// leading dimension of D + 1 complex elements (breaks bank conflicts between the two rows a
-// warp reads); padding rows and columns are kept at zero.
+// Thread layout: a G x G grid of threads (slice_tile); thread (ty, tx) owns the MT x MT outputs
+// (ty + G a, tx + G b).  Matrices sit in shared memory padded to D = G MT rows with a leading
+// dimension of D + 1 complex elements (breaks bank conflicts between the rows a warp reads);
+// padding rows and columns are kept at zero.
 #include "qoc_device.cuh"
 #include "qoc_internal.h"
 
@@ -25,14 +25,14 @@ namespace qoc {
 
 template <typename C, int MT>
 __device__ __forceinline__ void mm_acc(C (&acc)[MT][MT], const C* __restrict__ A,
-                                       const C* __restrict__ B, int kd, int LD, int ty, int tx) {
+                                       const C* __restrict__ B, int kd, int LD, int ty, int tx, int G) {
 #pragma unroll 2
     for (int k = 0; k < kd; ++k) {
         C a[MT], b[MT];
 #pragma unroll
-        for (int i = 0; i < MT; ++i) a[i] = A[(ty + 16 * i) * LD + k];
+        for (int i = 0; i < MT; ++i) a[i] = A[(ty + G * i) * LD + k];
 #pragma unroll
-        for (int i = 0; i < MT; ++i) b[i] = B[k * LD + tx + 16 * i];
+        for (int i = 0; i < MT; ++i) b[i] = B[k * LD + tx + G * i];
 #pragma unroll
         for (int i = 0; i < MT; ++i)
 #pragma unroll
@@ -45,19 +45,19 @@ template <typename C, int MT>
 __device__ __forceinline__ void mm_block(C (&acc11)[MT][MT], C (&acc12)[MT][MT],
                                          const C* __restrict__ A11, const C* __restrict__ A12,
                                          const C* __restrict__ B11, const C* __restrict__ B12,
-                                         int kd, int LD, int ty, int tx) {
+                                         int kd, int LD, int ty, int tx, int G) {
 #pragma unroll 1
     for (int k = 0; k < kd; ++k) {
         C a1[MT], a2[MT], b1[MT], b2[MT];
 #pragma unroll
         for (int i = 0; i < MT; ++i) {
-            a1[i] = A11[(ty + 16 * i) * LD + k];
-            a2[i] = A12[(ty + 16 * i) * LD + k];
+            a1[i] = A11[(ty + G * i) * LD + k];
+            a2[i] = A12[(ty + G * i) * LD + k];
         }
 #pragma unroll
         for (int i = 0; i < MT; ++i) {
-            b1[i] = B11[k * LD + tx + 16 * i];
-            b2[i] = B12[k * LD + tx + 16 * i];
+            b1[i] = B11[k * LD + tx + G * i];
+            b2[i] = B12[k * LD + tx + G * i];
         }
 #pragma unroll
         for (int i = 0; i < MT; ++i)
@@ -81,12 +81,12 @@ __device__ __forceinline__ void zero_acc(C (&acc)[MT][MT]) {
 // out = diag * I + scale * acc on the d x d block, zero in the padding.
 template <typename C, typename R, int MT>
 __device__ __forceinline__ void store_acc(C* __restrict__ out, const C (&acc)[MT][MT], R scale,
-                                          R diag, int d, int LD, int ty, int tx) {
+                                          R diag, int d, int LD, int ty, int tx, int G) {
 #pragma unroll
     for (int i = 0; i < MT; ++i)
 #pragma unroll
         for (int jj = 0; jj < MT; ++jj) {
-            const int r = ty + 16 * i, c = tx + 16 * jj;
+            const int r = ty + G * i, c = tx + G * jj;
             C v = czero<C>();
             if (r < d && c < d) {
                 v.x = acc[i][jj].x * scale + (r == c ? diag : R(0));
@@ -127,18 +127,19 @@ __device__ __forceinline__ void assemble_X(C* __restrict__ X, int d, int D, int 
 }
 
 template <typename R, int MT>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(512)
 k_expm_fwd(const DevParams* __restrict__ prm, SysView<R> sys, int j0, C_t<R>* __restrict__ Ubuf,
-           long long ustride, int wmax) {
+           long long ustride, int wmax, int G) {
     using C = C_t<R>;
-    constexpr int D = 16 * MT, LD = D + 1, SZ = D * LD;
+    const int D = G * MT, LD = D + 1, SZ = D * LD;
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ R us[kMaxControls];
     C* X = reinterpret_cast<C*>(smraw);
     C* Za = X + SZ;
     C* Zb = Za + SZ;
     const int jl = blockIdx.x, e = blockIdx.y, j = j0 + jl;
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int tid = threadIdx.x, tx = tid % G, ty = tid / G;
+    const bool act = tid < G * G;   // the block is rounded up to whole warps
     const int d = sys.d, p = prm->p, n = prm->n;
     const R s = (R)prm->s;
     for (int k = tid; k < sys.M; k += blockDim.x) us[k] = (R)sys.u[(size_t)k * sys.N + j];
@@ -161,18 +162,22 @@ k_expm_fwd(const DevParams* __restrict__ prm, SysView<R> sys, int j0, C_t<R>* __
     C* zin = Za;
     C* zout = Zb;
     for (int i = p - 1; i >= 1; --i) {          // Horner: Z <- I + X Z / i
-        C acc[MT][MT];
-        zero_acc<C, MT>(acc);
-        mm_acc<C, MT>(acc, X, zin, d, LD, ty, tx);
-        store_acc<C, R, MT>(zout, acc, R(1) / R(i), R(1), d, LD, ty, tx);
+        if (act) {
+            C acc[MT][MT];
+            zero_acc<C, MT>(acc);
+            mm_acc<C, MT>(acc, X, zin, d, LD, ty, tx, G);
+            store_acc<C, R, MT>(zout, acc, R(1) / R(i), R(1), d, LD, ty, tx, G);
+        }
         __syncthreads();
         C* t = zin; zin = zout; zout = t;
     }
     for (int m = 0; m < n; ++m) {               // squaring: Z <- Z Z
-        C acc[MT][MT];
-        zero_acc<C, MT>(acc);
-        mm_acc<C, MT>(acc, zin, zin, d, LD, ty, tx);
-        store_acc<C, R, MT>(zout, acc, R(1), R(0), d, LD, ty, tx);
+        if (act) {
+            C acc[MT][MT];
+            zero_acc<C, MT>(acc);
+            mm_acc<C, MT>(acc, zin, zin, d, LD, ty, tx, G);
+            store_acc<C, R, MT>(zout, acc, R(1), R(0), d, LD, ty, tx, G);
+        }
         __syncthreads();
         C* t = zin; zin = zout; zout = t;
     }
@@ -190,12 +195,12 @@ k_expm_fwd(const DevParams* __restrict__ prm, SysView<R> sys, int j0, C_t<R>* __
 }
 
 template <typename R, int MT>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(512)
 k_expm_adj(const DevParams* __restrict__ prm, SysView<R> sys, StateView<R> st, int j0,
            const C_t<R>* __restrict__ states, const C_t<R>* __restrict__ Gbuf, int wmax,
-           double* __restrict__ gpart) {
+           double* __restrict__ gpart, int G) {
     using C = C_t<R>;
-    constexpr int D = 16 * MT, LD = D + 1, SZ = D * LD;
+    const int D = G * MT, LD = D + 1, SZ = D * LD;
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ R us[kMaxControls];
     __shared__ double red[32];
@@ -206,7 +211,8 @@ k_expm_adj(const DevParams* __restrict__ prm, SysView<R> sys, StateView<R> st, i
     C* Z11b = Z12a + SZ;
     C* Z12b = Z11b + SZ;
     const int jl = blockIdx.x, e = blockIdx.y, j = j0 + jl;
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int tid = threadIdx.x, tx = tid % G, ty = tid / G;
+    const bool act = tid < G * G;   // the block is rounded up to whole warps
     const int d = sys.d, p = prm->p, n = prm->n, Sp = st.Spad, cb = st.cb, ps = st.pstride;
     const R s = (R)prm->s;
     for (int k = tid; k < sys.M; k += blockDim.x) us[k] = (R)sys.u[(size_t)k * sys.N + j];
@@ -231,14 +237,14 @@ k_expm_adj(const DevParams* __restrict__ prm, SysView<R> sys, StateView<R> st, i
         x.y = -x.y;
         XH[a * LD + b] = x;
     }
-    {   // Ubar = G Psi^dag
+    if (act) {   // Ubar = G Psi^dag
         C acc[MT][MT];
         zero_acc<C, MT>(acc);
         for (int sc = 0; sc < Sp; ++sc) {
             C g[MT], q[MT];
 #pragma unroll
             for (int i = 0; i < MT; ++i) {
-                const int r = ty + 16 * i, c = tx + 16 * i;
+                const int r = ty + G * i, c = tx + G * i;
                 g[i] = (r < d) ? Z11b[r * Sp + sc] : czero<C>();
                 q[i] = (c < d) ? Z12b[c * Sp + sc] : czero<C>();
             }
@@ -247,7 +253,7 @@ k_expm_adj(const DevParams* __restrict__ prm, SysView<R> sys, StateView<R> st, i
 #pragma unroll
                 for (int jj = 0; jj < MT; ++jj) cfma_bcj(acc[i][jj], g[i], q[jj]);
         }
-        store_acc<C, R, MT>(Ub, acc, R(1), R(0), d, LD, ty, tx);
+        store_acc<C, R, MT>(Ub, acc, R(1), R(0), d, LD, ty, tx, G);
     }
     __syncthreads();
     {   // Horner start: Z11 = I + XH / p, Z12 = Ubar / p
@@ -267,24 +273,28 @@ k_expm_adj(const DevParams* __restrict__ prm, SysView<R> sys, StateView<R> st, i
     __syncthreads();
     C *z11 = Z11a, *z12 = Z12a, *o11 = Z11b, *o12 = Z12b;
     for (int i = p - 1; i >= 1; --i) {
-        C a11[MT][MT], a12[MT][MT];
-        zero_acc<C, MT>(a11);
-        zero_acc<C, MT>(a12);
-        mm_block<C, MT>(a11, a12, XH, Ub, z11, z12, d, LD, ty, tx);
-        const R ri = R(1) / R(i);
-        store_acc<C, R, MT>(o11, a11, ri, R(1), d, LD, ty, tx);
-        store_acc<C, R, MT>(o12, a12, ri, R(0), d, LD, ty, tx);
+        if (act) {
+            C a11[MT][MT], a12[MT][MT];
+            zero_acc<C, MT>(a11);
+            zero_acc<C, MT>(a12);
+            mm_block<C, MT>(a11, a12, XH, Ub, z11, z12, d, LD, ty, tx, G);
+            const R ri = R(1) / R(i);
+            store_acc<C, R, MT>(o11, a11, ri, R(1), d, LD, ty, tx, G);
+            store_acc<C, R, MT>(o12, a12, ri, R(0), d, LD, ty, tx, G);
+        }
         __syncthreads();
         C* t = z11; z11 = o11; o11 = t;
         t = z12; z12 = o12; o12 = t;
     }
     for (int m = 0; m < n; ++m) {
-        C a11[MT][MT], a12[MT][MT];
-        zero_acc<C, MT>(a11);
-        zero_acc<C, MT>(a12);
-        mm_block<C, MT>(a11, a12, z11, z12, z11, z12, d, LD, ty, tx);
-        store_acc<C, R, MT>(o11, a11, R(1), R(0), d, LD, ty, tx);
-        store_acc<C, R, MT>(o12, a12, R(1), R(0), d, LD, ty, tx);
+        if (act) {
+            C a11[MT][MT], a12[MT][MT];
+            zero_acc<C, MT>(a11);
+            zero_acc<C, MT>(a12);
+            mm_block<C, MT>(a11, a12, z11, z12, z11, z12, d, LD, ty, tx, G);
+            store_acc<C, R, MT>(o11, a11, R(1), R(0), d, LD, ty, tx, G);
+            store_acc<C, R, MT>(o12, a12, R(1), R(0), d, LD, ty, tx, G);
+        }
         __syncthreads();
         C* t = z11; z11 = o11; o11 = t;
         t = z12; z12 = o12; o12 = t;
@@ -308,53 +318,54 @@ k_expm_adj(const DevParams* __restrict__ prm, SysView<R> sys, StateView<R> st, i
 // launchers
 // ------------------------------------------------------------------------------------------
 template <typename R>
-static size_t fused_smem(int MT, int nmat) {
-    const int D = 16 * MT;
+static size_t fused_smem(int d, int nmat) {
+    const int D = slice_tile(d).D;
     return (size_t)nmat * D * (D + 1) * sizeof(C_t<R>);
 }
 
 template <typename R>
 size_t fused_adj_smem(int d) {
-    return fused_smem<R>((d + 15) / 16, 6);
+    return fused_smem<R>(d, 6);
 }
 
 template <typename R>
 int fused_max_d() {
-    for (int MT = 5; MT >= 1; --MT)
-        if (fused_smem<R>(MT, 6) <= kMaxDynSmem) return 16 * MT;
+    for (int d = kMaxD; d >= 1; --d)
+        if (slice_tile(d).MT > 0 && fused_smem<R>(d, 6) <= kMaxDynSmem) return d;
     return 0;
 }
 
 template <typename R, int MT>
 static cudaError_t launch_fwd_mt(const DevParams* prm, const SysView<R>& sys, int j0, int wlen, int E,
-                                 C_t<R>* Ubuf, long long ustride, int wmax, cudaStream_t st) {
-    const size_t smem = fused_smem<R>(MT, 3);
+                                 C_t<R>* Ubuf, long long ustride, int wmax, int G, cudaStream_t st) {
+    const size_t smem = fused_smem<R>(sys.d, 3);
     cudaError_t err = cudaFuncSetAttribute(k_expm_fwd<R, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    k_expm_fwd<R, MT><<<dim3(wlen, E), 256, smem, st>>>(prm, sys, j0, Ubuf, ustride, wmax);
+    k_expm_fwd<R, MT><<<dim3(wlen, E), slice_threads(G), smem, st>>>(prm, sys, j0, Ubuf, ustride, wmax, G);
     return cudaGetLastError();
 }
 
 template <typename R, int MT>
 static cudaError_t launch_adj_mt(const DevParams* prm, const SysView<R>& sys, const StateView<R>& sv, int j0,
                                  int wlen, int E, const C_t<R>* states, const C_t<R>* Gbuf, int wmax,
-                                 double* gpart, cudaStream_t st) {
-    const size_t smem = fused_smem<R>(MT, 6);
+                                 double* gpart, int G, cudaStream_t st) {
+    const size_t smem = fused_smem<R>(sys.d, 6);
     cudaError_t err = cudaFuncSetAttribute(k_expm_adj<R, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    k_expm_adj<R, MT><<<dim3(wlen, E), 256, smem, st>>>(prm, sys, sv, j0, states, Gbuf, wmax, gpart);
+    k_expm_adj<R, MT><<<dim3(wlen, E), slice_threads(G), smem, st>>>(prm, sys, sv, j0, states, Gbuf, wmax, gpart, G);
     return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t launch_expm_fwd_fused(const DevParams* prm, const SysView<R>& sys, int j0, int wlen, int E,
                                   C_t<R>* Ubuf, long long ustride, int wmax, cudaStream_t st) {
-    const int MT = (sys.d + 15) / 16;
-    switch (MT) {
-        case 1: return launch_fwd_mt<R, 1>(prm, sys, j0, wlen, E, Ubuf, ustride, wmax, st);
-        case 2: return launch_fwd_mt<R, 2>(prm, sys, j0, wlen, E, Ubuf, ustride, wmax, st);
-        case 3: return launch_fwd_mt<R, 3>(prm, sys, j0, wlen, E, Ubuf, ustride, wmax, st);
-        case 4: if (sizeof(R) == 4) return launch_fwd_mt<R, 4>(prm, sys, j0, wlen, E, Ubuf, ustride, wmax, st);
+    const SliceTile tl = slice_tile(sys.d);
+    if (sys.d > fused_max_d<R>()) return cudaErrorInvalidValue;
+    switch (tl.MT) {
+        case 1: return launch_fwd_mt<R, 1>(prm, sys, j0, wlen, E, Ubuf, ustride, wmax, tl.G, st);
+        case 2: return launch_fwd_mt<R, 2>(prm, sys, j0, wlen, E, Ubuf, ustride, wmax, tl.G, st);
+        case 3: return launch_fwd_mt<R, 3>(prm, sys, j0, wlen, E, Ubuf, ustride, wmax, tl.G, st);
+        case 4: return launch_fwd_mt<R, 4>(prm, sys, j0, wlen, E, Ubuf, ustride, wmax, tl.G, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -363,12 +374,13 @@ template <typename R>
 cudaError_t launch_expm_adj_fused(const DevParams* prm, const SysView<R>& sys, const StateView<R>& sv, int j0,
                                   int wlen, int E, const C_t<R>* states, const C_t<R>* Gbuf, int wmax,
                                   double* gpart, cudaStream_t st) {
-    const int MT = (sys.d + 15) / 16;
-    switch (MT) {
-        case 1: return launch_adj_mt<R, 1>(prm, sys, sv, j0, wlen, E, states, Gbuf, wmax, gpart, st);
-        case 2: return launch_adj_mt<R, 2>(prm, sys, sv, j0, wlen, E, states, Gbuf, wmax, gpart, st);
-        case 3: return launch_adj_mt<R, 3>(prm, sys, sv, j0, wlen, E, states, Gbuf, wmax, gpart, st);
-        case 4: if (sizeof(R) == 4) return launch_adj_mt<R, 4>(prm, sys, sv, j0, wlen, E, states, Gbuf, wmax, gpart, st);
+    const SliceTile tl = slice_tile(sys.d);
+    if (sys.d > fused_max_d<R>()) return cudaErrorInvalidValue;
+    switch (tl.MT) {
+        case 1: return launch_adj_mt<R, 1>(prm, sys, sv, j0, wlen, E, states, Gbuf, wmax, gpart, tl.G, st);
+        case 2: return launch_adj_mt<R, 2>(prm, sys, sv, j0, wlen, E, states, Gbuf, wmax, gpart, tl.G, st);
+        case 3: return launch_adj_mt<R, 3>(prm, sys, sv, j0, wlen, E, states, Gbuf, wmax, gpart, tl.G, st);
+        case 4: return launch_adj_mt<R, 4>(prm, sys, sv, j0, wlen, E, states, Gbuf, wmax, gpart, tl.G, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -65,14 +65,14 @@ __device__ __forceinline__ void df_add1(float& hi, float& lo) {
 // loads per product; here each element is a float4 (re_h, im_h, re_l, im_l).
 template <int MT>
 __device__ __forceinline__ void mm_df(float (&ar)[MT][MT][2], float (&ai)[MT][MT][2], const float4* __restrict__ A,
-                                      const float4* __restrict__ B, int kd, int LD, int ty, int tx) {
+                                      const float4* __restrict__ B, int kd, int LD, int ty, int tx, int G) {
 #pragma unroll 1
     for (int k = 0; k < kd; ++k) {
         float4 a[MT], b[MT];
 #pragma unroll
-        for (int i = 0; i < MT; ++i) a[i] = A[(ty + 16 * i) * LD + k];
+        for (int i = 0; i < MT; ++i) a[i] = A[(ty + G * i) * LD + k];
 #pragma unroll
-        for (int i = 0; i < MT; ++i) b[i] = B[k * LD + tx + 16 * i];
+        for (int i = 0; i < MT; ++i) b[i] = B[k * LD + tx + G * i];
 #pragma unroll
         for (int i = 0; i < MT; ++i)
 #pragma unroll
@@ -89,18 +89,18 @@ __device__ __forceinline__ void mm_df(float (&ar)[MT][MT][2], float (&ai)[MT][MT
 // plain FP32 product of the hi parts (the early Horner steps)
 template <int MT>
 __device__ __forceinline__ void mm_hi(float2 (&acc)[MT][MT], const float4* __restrict__ A, const float4* __restrict__ B,
-                                      int kd, int LD, int ty, int tx) {
+                                      int kd, int LD, int ty, int tx, int G) {
 #pragma unroll 2
     for (int k = 0; k < kd; ++k) {
         float2 a[MT], b[MT];
 #pragma unroll
         for (int i = 0; i < MT; ++i) {
-            const float4 v = A[(ty + 16 * i) * LD + k];
+            const float4 v = A[(ty + G * i) * LD + k];
             a[i] = make_float2(v.x, v.y);
         }
 #pragma unroll
         for (int i = 0; i < MT; ++i) {
-            const float4 v = B[k * LD + tx + 16 * i];
+            const float4 v = B[k * LD + tx + G * i];
             b[i] = make_float2(v.x, v.y);
         }
 #pragma unroll
@@ -121,12 +121,12 @@ __device__ __forceinline__ void df_zero(float (&ar)[MT][MT][2], float (&ai)[MT][
 // out = [diag I] + acc / div  (div = 0: no division), zero in the padding
 template <int MT>
 __device__ __forceinline__ void df_store(float4* __restrict__ out, float (&ar)[MT][MT][2], float (&ai)[MT][MT][2],
-                                         int div, bool add_identity, int d, int LD, int ty, int tx) {
+                                         int div, bool add_identity, int d, int LD, int ty, int tx, int G) {
 #pragma unroll
     for (int i = 0; i < MT; ++i)
 #pragma unroll
         for (int j = 0; j < MT; ++j) {
-            const int r = ty + 16 * i, c = tx + 16 * j;
+            const int r = ty + G * i, c = tx + G * j;
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
             if (r < d && c < d) {
                 float rh = ar[i][j][0], rl = ar[i][j][1], ih = ai[i][j][0], il = ai[i][j][1];
@@ -144,17 +144,18 @@ __device__ __forceinline__ void df_store(float4* __restrict__ out, float (&ar)[M
 }
 
 template <int MT>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(512)
 k_expm_fwd_split(const DevParams* __restrict__ prm, SysView<float> sys, const double2* __restrict__ H64, int j0,
-                 float2* __restrict__ Ubuf, long long ustride, int wmax) {
-    constexpr int D = 16 * MT, LD = D + 1, SZ = D * LD;
+                 float2* __restrict__ Ubuf, long long ustride, int wmax, int G) {
+    const int D = G * MT, LD = D + 1, SZ = D * LD;
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ double us[kMaxControls];
     float4* X = reinterpret_cast<float4*>(smraw);
     float4* Za = X + SZ;
     float4* Zb = Za + SZ;
     const int jl = blockIdx.x, e = blockIdx.y, j = j0 + jl;
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int tid = threadIdx.x, tx = tid % G, ty = tid / G;
+    const bool act = tid < G * G;   // the block is rounded up to whole warps
     const int d = sys.d, M = sys.M, p = prm->p, n = prm->n;
     const double s = prm->s;
     for (int k = tid; k < M; k += blockDim.x) us[k] = sys.u[(size_t)k * sys.N + j];
@@ -200,19 +201,20 @@ k_expm_fwd_split(const DevParams* __restrict__ prm, SysView<float> sys, const do
     float4* zout = Zb;
     const int m_split = prm->m_split;
     for (int i = p - 1; i >= 1; --i) {        // Horner: Z <- I + X Z / i
-        if (i > m_split) {
+        if (!act) {
+        } else if (i > m_split) {
             float2 acc[MT][MT];
 #pragma unroll
             for (int a = 0; a < MT; ++a)
 #pragma unroll
                 for (int b = 0; b < MT; ++b) acc[a][b] = make_float2(0.f, 0.f);
-            mm_hi<MT>(acc, X, zin, d, LD, ty, tx);
+            mm_hi<MT>(acc, X, zin, d, LD, ty, tx, G);
             const float ri = 1.0f / (float)i;
 #pragma unroll
             for (int a = 0; a < MT; ++a)
 #pragma unroll
                 for (int b = 0; b < MT; ++b) {
-                    const int r = ty + 16 * a, c = tx + 16 * b;
+                    const int r = ty + G * a, c = tx + G * b;
                     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
                     if (r < d && c < d) {
                         v.x = fmaf(acc[a][b].x, ri, (r == c) ? 1.0f : 0.0f);
@@ -223,17 +225,19 @@ k_expm_fwd_split(const DevParams* __restrict__ prm, SysView<float> sys, const do
         } else {
             float ar[MT][MT][2], ai[MT][MT][2];
             df_zero<MT>(ar, ai);
-            mm_df<MT>(ar, ai, X, zin, d, LD, ty, tx);
-            df_store<MT>(zout, ar, ai, i, true, d, LD, ty, tx);
+            mm_df<MT>(ar, ai, X, zin, d, LD, ty, tx, G);
+            df_store<MT>(zout, ar, ai, i, true, d, LD, ty, tx, G);
         }
         __syncthreads();
         float4* t = zin; zin = zout; zout = t;
     }
     for (int m = 0; m < n; ++m) {             // squaring: Z <- Z Z
-        float ar[MT][MT][2], ai[MT][MT][2];
-        df_zero<MT>(ar, ai);
-        mm_df<MT>(ar, ai, zin, zin, d, LD, ty, tx);
-        df_store<MT>(zout, ar, ai, 0, false, d, LD, ty, tx);
+        if (act) {
+            float ar[MT][MT][2], ai[MT][MT][2];
+            df_zero<MT>(ar, ai);
+            mm_df<MT>(ar, ai, zin, zin, d, LD, ty, tx, G);
+            df_store<MT>(zout, ar, ai, 0, false, d, LD, ty, tx, G);
+        }
         __syncthreads();
         float4* t = zin; zin = zout; zout = t;
     }
@@ -249,34 +253,36 @@ k_expm_fwd_split(const DevParams* __restrict__ prm, SysView<float> sys, const do
     }
 }
 
-static size_t split_smem(int MT) {
-    const int D = 16 * MT;
+static size_t split_smem(int d) {
+    const int D = slice_tile(d).D;
     return (size_t)3 * D * (D + 1) * sizeof(float4);
 }
 
 template <int MT>
 static cudaError_t launch_split_mt(const DevParams* prm, const SysView<float>& sys, const double2* H64, int j0,
-                                   int wlen, int E, float2* Ubuf, long long ustride, int wmax, cudaStream_t st) {
-    const size_t smem = split_smem(MT);
+                                   int wlen, int E, float2* Ubuf, long long ustride, int wmax, int G, cudaStream_t st) {
+    const size_t smem = split_smem(sys.d);
     cudaError_t err = cudaFuncSetAttribute(k_expm_fwd_split<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    k_expm_fwd_split<MT><<<dim3(wlen, E), 256, smem, st>>>(prm, sys, H64, j0, Ubuf, ustride, wmax);
+    k_expm_fwd_split<MT><<<dim3(wlen, E), slice_threads(G), smem, st>>>(prm, sys, H64, j0, Ubuf, ustride, wmax, G);
     return cudaGetLastError();
 }
 
 int split_max_d() {
-    for (int MT = 4; MT >= 1; --MT)
-        if (split_smem(MT) <= kMaxDynSmem) return 16 * MT;
+    for (int d = kMaxD; d >= 1; --d)
+        if (slice_tile(d).MT > 0 && split_smem(d) <= kMaxDynSmem) return d;
     return 0;
 }
 
 cudaError_t launch_expm_fwd_split(const DevParams* prm, const SysView<float>& sys, const double2* H64, int j0, int wlen,
                                   int E, float2* Ubuf, long long ustride, int wmax, cudaStream_t st) {
-    switch ((sys.d + 15) / 16) {
-        case 1: return launch_split_mt<1>(prm, sys, H64, j0, wlen, E, Ubuf, ustride, wmax, st);
-        case 2: return launch_split_mt<2>(prm, sys, H64, j0, wlen, E, Ubuf, ustride, wmax, st);
-        case 3: return launch_split_mt<3>(prm, sys, H64, j0, wlen, E, Ubuf, ustride, wmax, st);
-        case 4: return launch_split_mt<4>(prm, sys, H64, j0, wlen, E, Ubuf, ustride, wmax, st);
+    const SliceTile tl = slice_tile(sys.d);
+    if (sys.d > split_max_d()) return cudaErrorInvalidValue;
+    switch (tl.MT) {
+        case 1: return launch_split_mt<1>(prm, sys, H64, j0, wlen, E, Ubuf, ustride, wmax, tl.G, st);
+        case 2: return launch_split_mt<2>(prm, sys, H64, j0, wlen, E, Ubuf, ustride, wmax, tl.G, st);
+        case 3: return launch_split_mt<3>(prm, sys, H64, j0, wlen, E, Ubuf, ustride, wmax, tl.G, st);
+        case 4: return launch_split_mt<4>(prm, sys, H64, j0, wlen, E, Ubuf, ustride, wmax, tl.G, st);
         default: return cudaErrorInvalidValue;
     }
 }

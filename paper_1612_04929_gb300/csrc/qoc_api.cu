@@ -136,6 +136,7 @@ struct qoc_ctx {
     int W = 0, nw = 0, seg = 0, nseg_total = 0, path_kind = 0;
     int Spad = 0, cb = 0, ncb = 0, pstride = 0, S_eff = 0;
     bool scan = false;                   // segmented-scan form of the two recursions
+    double theta_max = 0.0;              // in effect (the option, or the path's default)
     int nzmax = 0;                       // checkpoint segments per wave
     std::vector<int> cols;               // propagated columns (positive weight)
     size_t mstride = 0;                  // elements per matrix slot of the batched path
@@ -212,6 +213,10 @@ void plan_impl(qoc_ctx* c) {
     const size_t cs = sizeof(C);
     const int dmax = split_exp<R>(c) ? std::min(fused_max_d<R>(), split_max_d()) : fused_max_d<R>();
     c->path_kind = (d <= dmax) ? 0 : 1;   // 0: per-slice fused kernels, 1: batched tiled GEMMs
+    // default theta_max of the FP32 forms: 0.5 with the per-slice kernels (split squarings: one
+    // split product fewer than 1.0 on long evolutions); 1.0 on the batched path, whose plain
+    // FP32 adjoint loses accuracy with every extra squaring
+    c->theta_max = c->opt.theta_max > 0.0 ? c->opt.theta_max : (c->path_kind == 0 ? 0.5 : 1.0);
     // Columns whose weight is zero enter no cost term (every term is weighted by w_s), so they
     // are not propagated at all.
     c->cols.clear();
@@ -436,7 +441,7 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
     if (!known) {
         B(st);
         L(launch_theta(u, M, N, c->norms.as<double>(), c->delta.empty() ? nullptr : c->dDelta.as<double>(), E, c->dt,
-                       c->opt.theta_max, c->opt.tol, c->opt.p_override, c->opt.n_override, prm, st),
+                       c->theta_max, c->opt.tol, c->opt.p_override, c->opt.n_override, prm, st),
           "theta", st);
     } else {
         ++launches;
@@ -758,7 +763,7 @@ qoc_status qoc_create(qoc_ctx** out, const qoc_options* opt) {
         return QOC_ERR_ARG;
     const bool f64 = o.precision == QOC_PREC_FP64;
     if (o.tol == 0.0) o.tol = f64 ? 1e-15 : 1e-8;
-    if (o.theta_max == 0.0) o.theta_max = f64 ? 0.25 : 1.0;
+    if (o.theta_max == 0.0 && f64) o.theta_max = 0.25;   // FP32 forms: resolved by the planner
     qoc_ctx* ctx = new (std::nothrow) qoc_ctx;
     if (!ctx) return QOC_ERR_OOM;
     ctx->opt = o;
@@ -1035,7 +1040,7 @@ qoc_status qoc_evaluate_batch(int count, qoc_ctx* const* ctxs, const double* con
             check_cuda(c, cudaStreamWaitEvent(c->stream, f, 0), "fork wait");
             check_cuda(c, launch_theta(u_dev[i], c->M, c->N, c->norms.as<double>(),
                                        c->delta.empty() ? nullptr : c->dDelta.as<double>(), c->E, c->dt,
-                                       c->opt.theta_max, c->opt.tol, c->opt.p_override, c->opt.n_override,
+                                       c->theta_max, c->opt.tol, c->opt.p_override, c->opt.n_override,
                                        c->prm.as<DevParams>(), c->stream),
                        "theta");
             if (c->path_kind == 1) {

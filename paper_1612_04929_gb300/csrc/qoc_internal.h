@@ -69,6 +69,23 @@ cudaError_t launch_to_panels(const double2* src, C_t<R>* dst, int d, int S, Stat
                              int copies, size_t dst_stride, size_t src_stride, cudaStream_t st);
 
 // ---- fused per-slice exponential kernels ----
+// Thread layout of the per-slice kernels: a G x G grid of threads, thread (ty, tx) owning the
+// MT x MT outputs (ty + G a, tx + G b), so the padded dimension is D = MT G.  MT in 1..4 is the
+// one with the least padding for G <= 22 (at most 484 threads); on ties the smaller MT (more
+// threads).
+struct SliceTile { int MT, G, D; };
+inline SliceTile slice_tile(int d) {
+    SliceTile best{0, 0, 1 << 30};
+    for (int mt = 1; mt <= 4; ++mt) {
+        const int g = (d + mt - 1) / mt;
+        if (g > 22) continue;
+        if (mt * g < best.D) best = {mt, g, mt * g};
+    }
+    return best;
+}
+// threads of a per-slice CTA: G x G rounded up to whole warps (the extra threads take part in
+// the element-wise loops and reductions only)
+inline int slice_threads(int G) { return (G * G + 31) / 32 * 32; }
 template <typename R> int fused_max_d();
 template <typename R> size_t fused_adj_smem(int d);   // dynamic SMEM of the per-slice adjoint kernel
 template <typename R>

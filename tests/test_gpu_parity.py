@@ -107,7 +107,9 @@ CASES32 = [
     dict(d=13, M=3, N=37, S=1, seed=202, nF=2, path=True),
     dict(d=40, M=2, N=64, S=1, seed=203, nF=13),
     dict(d=40, M=2, N=30, S=40, seed=204, nF=6, E=2),
-    dict(d=64, M=3, N=21, S=8, seed=205, nF=4, weights=True),   # largest fused FP32 size
+    dict(d=64, M=3, N=21, S=8, seed=205, nF=4, weights=True),   # 4 x 4 outputs per thread
+    dict(d=68, M=2, N=11, S=3, seed=206, nF=2),                 # largest fused FP32 size
+    dict(d=23, M=2, N=19, S=2, seed=207, nF=2, E=2),            # 2 x 2 outputs, one padding row
 ]
 
 
