@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--profile-batch", action="store_true", help="per-kernel event times (--workload batch)")
     ap.add_argument("--cpu-sample", type=int, default=0, help="slices in the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-form", action="store_true", help="skip timing the plain FP64 GPU form")
     return ap.parse_args()
 
 
@@ -114,11 +115,13 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ oracle (CPU) timing
-def oracle_sample_time(workload, nslices, repeats=1):
+def oracle_sample_time(workload, nslices, repeats=1, ref_slices=0):
     """Times the CPU FP64 oracle on the first `nslices` slices of the workload in a child
-    process limited to one BLAS thread.  Returns (seconds per evaluation, slices)."""
+    process limited to one BLAS thread.  With ref_slices > 0 the child also evaluates the oracle
+    once on the first ref_slices slices (untimed) and returns its cost and gradient, the
+    reference for the GPU result's error.  Returns (seconds per evaluation, slices, reference)."""
     code = f"""
-import os, sys, time
+import json, os, sys, time
 sys.path.insert(0, {ROOT!r})
 import synthetic as sy
 from oracle import qoc_oracle as orc
@@ -127,13 +130,19 @@ orc.cost_and_grad(p, p.u)
 ts = []
 for _ in range({repeats}):
     t0 = time.perf_counter(); orc.cost_and_grad(p, p.u); ts.append(time.perf_counter() - t0)
-print(sum(ts) / len(ts))
+ref = None
+if {ref_slices} > 0:
+    q = sy.WORKLOADS[{workload!r}](N={ref_slices})
+    c, g, _ = orc.cost_and_grad(q, q.u)
+    ref = {{"N": {ref_slices}, "cost": float(c), "grad": [float(x) for x in g.ravel()]}}
+print(json.dumps({{"t": sum(ts) / len(ts), "ref": ref}}))
 """
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
     if r.returncode != 0:
         raise RuntimeError(r.stderr)
-    return float(r.stdout.strip().split()[-1]), nslices
+    res = json.loads(r.stdout.strip().splitlines()[-1])
+    return float(res["t"]), nslices, res["ref"]
 
 
 def reference_arm(args):
@@ -274,24 +283,66 @@ def ours_arm(args):
     e2e_value = units * world / (sum(e2e_t) / len(e2e_t))
     mn_bytes = prob.M * prob.N * 8
 
+    # the plain FP64 GPU form on the same workload (the metric's second part: speedup of the
+    # mixed form over it, at the error stated below)
+    fp64_form = None
+    if precision != "fp64" and not args.no_fp64_form:
+        c64 = Context("fp64", device=local, stream=stream.cuda_stream, ckpt_stride=args.ckpt_stride)
+        c64.set_problem(prob)
+        g64 = torch.empty_like(u)
+        o64 = torch.empty(6, dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            c64.evaluate_device(u.data_ptr(), g64.data_ptr(), o64.data_ptr())
+        c64.sync()
+        K64 = max(1, min(K, 5))
+        s64 = [torch.cuda.Event(enable_timing=True) for _ in range(K64)]
+        e64 = [torch.cuda.Event(enable_timing=True) for _ in range(K64)]
+        torch.cuda.synchronize()
+        for k in range(K64):
+            flush.zero_()
+            s64[k].record(stream)
+            c64.evaluate_device(u.data_ptr(), g64.data_ptr(), o64.data_ptr())
+            e64[k].record(stream)
+        torch.cuda.synchronize()
+        ms64 = sum(s.elapsed_time(e) for s, e in zip(s64, e64)) / K64
+        i64 = c64.info()
+        fp64_form = {"value": units / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64, "steps": K64,
+                     "p": i64["p"], "n": i64["n"]}
+        c64.close()
+
     cpu = None
+    error = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         nsl = args.cpu_sample or max(20, prob.N // 10)
+        # the error reference: the whole workload where the oracle takes seconds, else the sample
+        ref_n = prob.N if prob.d <= 81 else nsl
         try:
-            t, nsl = oracle_sample_time(args.workload, nsl)
+            t, nsl, ref = oracle_sample_time(args.workload, nsl, ref_slices=ref_n)
             cpu = {"value": nsl * prob.E / t, "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": f"first {nsl} of {prob.N} slices of the same workload, FP64 oracle, 1 BLAS thread, "
                              f"{t:.2f} s per evaluation"}
+            if ref is not None:
+                if ref_n == prob.N:
+                    c_gpu, g_gpu = float(out[0].item()), grad.cpu().numpy()
+                else:   # evaluate the same form on the sample problem
+                    q = make_problem(args.workload, ref_n)
+                    with Context(precision, device=local, stream=stream.cuda_stream) as cq:
+                        cq.set_problem(q)
+                        c_gpu, g_gpu, _ = cq.evaluate(q.u)
+                g_ref = np.asarray(ref["grad"])
+                error = {"precision": precision, "slices": ref_n,
+                         "cost_rel": abs(c_gpu - ref["cost"]) / abs(ref["cost"]),
+                         "grad_rel": float(np.linalg.norm(np.ravel(g_gpu) - g_ref) / np.linalg.norm(g_ref)),
+                         "against": "CPU FP64 oracle (eigendecomposition exponentials, explicit adjoint)"}
         except Exception as exc:   # keep the GPU line even if the CPU leg fails
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {exc}"}
 
-    # error of this evaluation against the oracle is checked by the tests; report the cost here
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
                 "warmup": max(args.warmup, 3), "ms_per_step": t_max, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": {"fp64": "f64", "fp32": "f32", "tf32": "tf32x3", "bf16": "bf16x3"}[precision],
-                "data": "synthetic (seeded transmon-cavity system, random controls)",
+                "data": f"synthetic (seeded {prob.name} system, random controls)",
                 "config": config_of(prob, precision, info["ckpt_stride"],
                                     {"p": p, "n": n, "wave_slices": info["wave_slices"], "n_waves": info["n_waves"]}),
                 "roofline": roof, "cpu_baseline": cpu,
@@ -299,6 +350,9 @@ def ours_arm(args):
                         "d2h_bytes_per_step": mn_bytes + 6 * 8 + 32},
                 "gpu_launches": info["launches_per_eval"] * K,
                 "clocks": clk.summary(), "kernels": kernels,
+                "fp64_form": fp64_form,
+                "speedup_vs_fp64_form": (value / fp64_form["value"]) if fp64_form else None,
+                "error_vs_oracle": error,
                 "cost": float(out[0].item())}
         print(json.dumps(line), flush=True)
     ctx.close()

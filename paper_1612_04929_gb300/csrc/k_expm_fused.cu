@@ -13,6 +13,12 @@
 //               costate, Appendix A), then dC/du_{k,j} = Re tr(Xbar^dag (-i s H_k)) (Eq. A3).
 //               This differentiates the truncated series exactly (not the first-order Eq. 11)
 //               without storing the p + n intermediate matrices.
+//  k_expm_adj_rev : the same derivative in reverse mode over the forward products, when the
+//               forward kernel stored their right operands (ZStore): per squaring
+//               Sbar_m = Sbar_{m+1} S_m^dag + S_m^dag Sbar_{m+1}, per Horner step
+//               Xbar += Zbar_i Z_{i+1}^dag / i and Zbar_{i+1} = X^dag Zbar_i / i, starting from
+//               Ubar and ending with Xbar += Zbar_p / p: two products per step instead of three,
+//               and four matrices in shared memory instead of six.
 //
 // Thread layout: a G x G grid of threads (slice_tile); thread (ty, tx) owns the MT x MT outputs
 // (ty + G a, tx + G b).  Matrices sit in shared memory padded to D = G MT rows with a leading
@@ -96,6 +102,17 @@ __device__ __forceinline__ void store_acc(C* __restrict__ out, const C (&acc)[MT
         }
 }
 
+// dst (d x d, global) = conjugate transpose of the d x d block of src (shared, leading dim LD)
+template <typename C>
+__device__ __forceinline__ void store_ct(C* __restrict__ dst, const C* __restrict__ src, int d, int LD) {
+    for (int idx = threadIdx.x; idx < d * d; idx += blockDim.x) {
+        const int a = idx / d, b = idx - a * d;
+        C v = src[b * LD + a];
+        v.y = -v.y;
+        dst[idx] = v;
+    }
+}
+
 // Assemble H_j (+ delta_e Hdet) and write X = -i s H into padded shared memory (rows/cols >= d
 // zero).  us: the M control values of this slice (shared).
 template <typename C, typename R>
@@ -129,7 +146,7 @@ __device__ __forceinline__ void assemble_X(C* __restrict__ X, int d, int D, int 
 template <typename R, int MT>
 __global__ void __launch_bounds__(512)
 k_expm_fwd(const DevParams* __restrict__ prm, SysView<R> sys, int j0, C_t<R>* __restrict__ Ubuf,
-           long long ustride, int wmax, int G) {
+           long long ustride, int wmax, ZStore<R> zs, int G) {
     using C = C_t<R>;
     const int D = G * MT, LD = D + 1, SZ = D * LD;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -161,7 +178,9 @@ k_expm_fwd(const DevParams* __restrict__ prm, SysView<R> sys, int j0, C_t<R>* __
     __syncthreads();
     C* zin = Za;
     C* zout = Zb;
+    C* zst = (zs.Z && p - 1 + n <= zs.cap) ? zs.Z + ((size_t)e * zs.wmax + jl) * zs.cap * zs.mstride : nullptr;
     for (int i = p - 1; i >= 1; --i) {          // Horner: Z <- I + X Z / i
+        if (zst) store_ct<C>(zst + (size_t)(p - 1 - i) * zs.mstride, zin, d, LD);
         if (act) {
             C acc[MT][MT];
             zero_acc<C, MT>(acc);
@@ -172,6 +191,7 @@ k_expm_fwd(const DevParams* __restrict__ prm, SysView<R> sys, int j0, C_t<R>* __
         C* t = zin; zin = zout; zout = t;
     }
     for (int m = 0; m < n; ++m) {               // squaring: Z <- Z Z
+        if (zst) store_ct<C>(zst + (size_t)(p - 1 + m) * zs.mstride, zin, d, LD);
         if (act) {
             C acc[MT][MT];
             zero_acc<C, MT>(acc);
@@ -198,8 +218,9 @@ template <typename R, int MT>
 __global__ void __launch_bounds__(512)
 k_expm_adj(const DevParams* __restrict__ prm, SysView<R> sys, StateView<R> st, int j0,
            const C_t<R>* __restrict__ states, const C_t<R>* __restrict__ Gbuf, int wmax,
-           double* __restrict__ gpart, int G) {
+           double* __restrict__ gpart, ZStore<R> zs, int G) {
     using C = C_t<R>;
+    if (zs.Z && prm->p - 1 + prm->n <= zs.cap) return;   // k_expm_adj_rev handles this evaluation
     const int D = G * MT, LD = D + 1, SZ = D * LD;
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ R us[kMaxControls];
@@ -213,7 +234,9 @@ k_expm_adj(const DevParams* __restrict__ prm, SysView<R> sys, StateView<R> st, i
     const int jl = blockIdx.x, e = blockIdx.y, j = j0 + jl;
     const int tid = threadIdx.x, tx = tid % G, ty = tid / G;
     const bool act = tid < G * G;   // the block is rounded up to whole warps
-    const int d = sys.d, p = prm->p, n = prm->n, Sp = st.Spad, cb = st.cb, ps = st.pstride;
+    // only the S propagated columns are staged (d x S <= d x d fits a matrix slot; the padding
+    // columns of the panel layout are zero and add nothing to Ubar)
+    const int d = sys.d, p = prm->p, n = prm->n, Sp = st.S, cb = st.cb, ps = st.pstride;
     const R s = (R)prm->s;
     for (int k = tid; k < sys.M; k += blockDim.x) us[k] = (R)sys.u[(size_t)k * sys.N + j];
     __syncthreads();
@@ -314,6 +337,150 @@ k_expm_adj(const DevParams* __restrict__ prm, SysView<R> sys, StateView<R> st, i
     }
 }
 
+template <typename R, int MT>
+__global__ void __launch_bounds__(512, (MT <= 2 && sizeof(R) == 4) ? 3 : 1)
+k_expm_adj_rev(const DevParams* __restrict__ prm, SysView<R> sys, StateView<R> st, int j0,
+               const C_t<R>* __restrict__ states, const C_t<R>* __restrict__ Gbuf, int wmax,
+               double* __restrict__ gpart, ZStore<R> zs, int G) {
+    using C = C_t<R>;
+    const int p = prm->p, n = prm->n;
+    if (!(zs.Z && p - 1 + n <= zs.cap)) return;           // k_expm_adj recomputes instead
+    const int D = G * MT, LD = D + 1, SZ = D * LD;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ R us[kMaxControls];
+    __shared__ double red[32];
+    C* XH = reinterpret_cast<C*>(smraw);
+    C* ZA = XH + SZ;
+    C* ZB = ZA + SZ;
+    C* SB = ZB + SZ;
+    const int jl = blockIdx.x, e = blockIdx.y, j = j0 + jl;
+    const int tid = threadIdx.x, tx = tid % G, ty = tid / G;
+    const bool act = tid < G * G;   // the block is rounded up to whole warps
+    const int d = sys.d, Sr = st.S, cb = st.cb, ps = st.pstride;
+    const R s = (R)prm->s;
+    for (int k = tid; k < sys.M; k += blockDim.x) us[k] = (R)sys.u[(size_t)k * sys.N + j];
+    __syncthreads();
+    const R de = sys.delta ? (R)sys.delta[e] : R(0);
+    assemble_X<C, R>(ZA, d, D, LD, sys.M, sys.H0, sys.Hk, sys.Hdet, de, us, s);
+    // G_j (ZB) and Psi_{j-1} (SB) as d x S row-major; the padding columns are zero
+    const size_t slice = st.slice();
+    const C* Gj = Gbuf + ((size_t)e * wmax + jl) * slice;
+    const C* Pj = states + ((size_t)e * (wmax + 1) + jl) * slice;
+    for (int idx = tid; idx < d * Sr; idx += blockDim.x) {
+        const int a = idx / Sr, sc = idx - a * Sr;
+        const size_t off = (size_t)(sc / cb) * ps + (size_t)a * cb + (sc % cb);
+        ZB[idx] = Gj[off];
+        SB[idx] = Pj[off];
+    }
+    __syncthreads();
+    for (int idx = tid; idx < D * D; idx += blockDim.x) {
+        const int a = idx / D, b = idx - a * D;
+        C x = ZA[b * LD + a];
+        x.y = -x.y;
+        XH[a * LD + b] = x;
+    }
+    __syncthreads();
+    if (act) {   // Ubar = G Psi^dag, the cotangent of U_j = S_n
+        C acc[MT][MT];
+        zero_acc<C, MT>(acc);
+        for (int sc = 0; sc < Sr; ++sc) {
+            C g[MT], q[MT];
+#pragma unroll
+            for (int i = 0; i < MT; ++i) {
+                const int r = ty + G * i, c = tx + G * i;
+                g[i] = (r < d) ? ZB[r * Sr + sc] : czero<C>();
+                q[i] = (c < d) ? SB[c * Sr + sc] : czero<C>();
+            }
+#pragma unroll
+            for (int i = 0; i < MT; ++i)
+#pragma unroll
+                for (int jj = 0; jj < MT; ++jj) cfma_bcj(acc[i][jj], g[i], q[jj]);
+        }
+        store_acc<C, R, MT>(ZA, acc, R(1), R(0), d, LD, ty, tx, G);
+    }
+    __syncthreads();
+    const C* zst = zs.Z + ((size_t)e * zs.wmax + jl) * zs.cap * zs.mstride;
+    auto load = [&](int r) {   // stored conjugate transpose of the right operand of product r
+        const C* src = zst + (size_t)r * zs.mstride;
+        for (int idx = tid; idx < d * d; idx += blockDim.x) {
+            const int a = idx / d, b = idx - a * d;
+            SB[a * LD + b] = src[idx];
+        }
+    };
+    C* zb = ZA;
+    C* zo = ZB;
+    for (int m = n - 1; m >= 0; --m) {          // squarings in reverse
+        load(p - 1 + m);
+        __syncthreads();
+        if (act) {
+            C acc[MT][MT];
+            zero_acc<C, MT>(acc);
+            mm_acc<C, MT>(acc, zb, SB, d, LD, ty, tx, G);      // Sbar S^dag
+            mm_acc<C, MT>(acc, SB, zb, d, LD, ty, tx, G);      // S^dag Sbar
+            store_acc<C, R, MT>(zo, acc, R(1), R(0), d, LD, ty, tx, G);
+        }
+        __syncthreads();
+        C* t = zb; zb = zo; zo = t;
+    }
+    C xb[MT][MT];                               // Xbar, accumulated over the Horner steps
+    zero_acc<C, MT>(xb);
+    for (int i = 1; i <= p - 1; ++i) {          // Horner steps in reverse
+        load(p - 1 - i);
+        __syncthreads();
+        if (act) {
+            const R ri = R(1) / R(i);
+            C acc[MT][MT];
+            zero_acc<C, MT>(acc);
+            mm_acc<C, MT>(acc, zb, SB, d, LD, ty, tx, G);      // Zbar_i Z_{i+1}^dag
+#pragma unroll
+            for (int a = 0; a < MT; ++a)
+#pragma unroll
+                for (int b = 0; b < MT; ++b) {
+                    xb[a][b].x += acc[a][b].x * ri;
+                    xb[a][b].y += acc[a][b].y * ri;
+                }
+            zero_acc<C, MT>(acc);
+            mm_acc<C, MT>(acc, XH, zb, d, LD, ty, tx, G);      // X^dag Zbar_i
+            store_acc<C, R, MT>(zo, acc, ri, R(0), d, LD, ty, tx, G);
+        }
+        __syncthreads();
+        C* t = zb; zb = zo; zo = t;
+    }
+    // Z_p = I + X / p: Xbar += Zbar_p / p; then dC/du_{k,j} = s sum_ab (Xbar_re Hk_im - Xbar_im Hk_re)
+    const R rp = R(1) / R(p);
+    if (act) {
+#pragma unroll
+        for (int a = 0; a < MT; ++a)
+#pragma unroll
+            for (int b = 0; b < MT; ++b) {
+                const int r = ty + G * a, c = tx + G * b;
+                if (r < d && c < d) {
+                    const C z = zb[r * LD + c];
+                    xb[a][b].x += z.x * rp;
+                    xb[a][b].y += z.y * rp;
+                }
+            }
+    }
+    const size_t dd = (size_t)d * d;
+    for (int k = 0; k < sys.M; ++k) {
+        double v = 0.0;
+        if (act) {
+#pragma unroll
+            for (int a = 0; a < MT; ++a)
+#pragma unroll
+                for (int b = 0; b < MT; ++b) {
+                    const int r = ty + G * a, c = tx + G * b;
+                    if (r < d && c < d) {
+                        const C hk = sys.Hk[k * dd + (size_t)r * d + c];
+                        v += (double)xb[a][b].x * (double)hk.y - (double)xb[a][b].y * (double)hk.x;
+                    }
+                }
+        }
+        v = block_sum(v, red);
+        if (tid == 0) gpart[((size_t)e * sys.M + k) * sys.N + j] = prm->s * v;
+    }
+}
+
 // ------------------------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------------------------
@@ -337,35 +504,46 @@ int fused_max_d() {
 
 template <typename R, int MT>
 static cudaError_t launch_fwd_mt(const DevParams* prm, const SysView<R>& sys, int j0, int wlen, int E,
-                                 C_t<R>* Ubuf, long long ustride, int wmax, int G, cudaStream_t st) {
+                                 C_t<R>* Ubuf, long long ustride, int wmax, const ZStore<R>& zs, int G,
+                                 cudaStream_t st) {
     const size_t smem = fused_smem<R>(sys.d, 3);
     cudaError_t err = cudaFuncSetAttribute(k_expm_fwd<R, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    k_expm_fwd<R, MT><<<dim3(wlen, E), slice_threads(G), smem, st>>>(prm, sys, j0, Ubuf, ustride, wmax, G);
+    k_expm_fwd<R, MT><<<dim3(wlen, E), slice_threads(G), smem, st>>>(prm, sys, j0, Ubuf, ustride, wmax, zs, G);
     return cudaGetLastError();
 }
 
 template <typename R, int MT>
 static cudaError_t launch_adj_mt(const DevParams* prm, const SysView<R>& sys, const StateView<R>& sv, int j0,
                                  int wlen, int E, const C_t<R>* states, const C_t<R>* Gbuf, int wmax,
-                                 double* gpart, int G, cudaStream_t st) {
+                                 double* gpart, const ZStore<R>& zs, int G, cudaStream_t st, int* launches) {
     const size_t smem = fused_smem<R>(sys.d, 6);
     cudaError_t err = cudaFuncSetAttribute(k_expm_adj<R, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    k_expm_adj<R, MT><<<dim3(wlen, E), slice_threads(G), smem, st>>>(prm, sys, sv, j0, states, Gbuf, wmax, gpart, G);
+    k_expm_adj<R, MT><<<dim3(wlen, E), slice_threads(G), smem, st>>>(prm, sys, sv, j0, states, Gbuf, wmax, gpart,
+                                                                       zs, G);
+    err = cudaGetLastError();
+    *launches = 1;
+    if (err != cudaSuccess || !zs.Z) return err;
+    const size_t smem_r = fused_smem<R>(sys.d, 4);
+    err = cudaFuncSetAttribute(k_expm_adj_rev<R, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r);
+    if (err != cudaSuccess) return err;
+    k_expm_adj_rev<R, MT><<<dim3(wlen, E), slice_threads(G), smem_r, st>>>(prm, sys, sv, j0, states, Gbuf, wmax,
+                                                                             gpart, zs, G);
+    *launches = 2;
     return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t launch_expm_fwd_fused(const DevParams* prm, const SysView<R>& sys, int j0, int wlen, int E,
-                                  C_t<R>* Ubuf, long long ustride, int wmax, cudaStream_t st) {
+                                  C_t<R>* Ubuf, long long ustride, int wmax, const ZStore<R>& zs, cudaStream_t st) {
     const SliceTile tl = slice_tile(sys.d);
     if (sys.d > fused_max_d<R>()) return cudaErrorInvalidValue;
     switch (tl.MT) {
-        case 1: return launch_fwd_mt<R, 1>(prm, sys, j0, wlen, E, Ubuf, ustride, wmax, tl.G, st);
-        case 2: return launch_fwd_mt<R, 2>(prm, sys, j0, wlen, E, Ubuf, ustride, wmax, tl.G, st);
-        case 3: return launch_fwd_mt<R, 3>(prm, sys, j0, wlen, E, Ubuf, ustride, wmax, tl.G, st);
-        case 4: return launch_fwd_mt<R, 4>(prm, sys, j0, wlen, E, Ubuf, ustride, wmax, tl.G, st);
+        case 1: return launch_fwd_mt<R, 1>(prm, sys, j0, wlen, E, Ubuf, ustride, wmax, zs, tl.G, st);
+        case 2: return launch_fwd_mt<R, 2>(prm, sys, j0, wlen, E, Ubuf, ustride, wmax, zs, tl.G, st);
+        case 3: return launch_fwd_mt<R, 3>(prm, sys, j0, wlen, E, Ubuf, ustride, wmax, zs, tl.G, st);
+        case 4: return launch_fwd_mt<R, 4>(prm, sys, j0, wlen, E, Ubuf, ustride, wmax, zs, tl.G, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -373,14 +551,15 @@ cudaError_t launch_expm_fwd_fused(const DevParams* prm, const SysView<R>& sys, i
 template <typename R>
 cudaError_t launch_expm_adj_fused(const DevParams* prm, const SysView<R>& sys, const StateView<R>& sv, int j0,
                                   int wlen, int E, const C_t<R>* states, const C_t<R>* Gbuf, int wmax,
-                                  double* gpart, cudaStream_t st) {
+                                  double* gpart, const ZStore<R>& zs, cudaStream_t st, int* launches) {
     const SliceTile tl = slice_tile(sys.d);
+    *launches = 0;
     if (sys.d > fused_max_d<R>()) return cudaErrorInvalidValue;
     switch (tl.MT) {
-        case 1: return launch_adj_mt<R, 1>(prm, sys, sv, j0, wlen, E, states, Gbuf, wmax, gpart, tl.G, st);
-        case 2: return launch_adj_mt<R, 2>(prm, sys, sv, j0, wlen, E, states, Gbuf, wmax, gpart, tl.G, st);
-        case 3: return launch_adj_mt<R, 3>(prm, sys, sv, j0, wlen, E, states, Gbuf, wmax, gpart, tl.G, st);
-        case 4: return launch_adj_mt<R, 4>(prm, sys, sv, j0, wlen, E, states, Gbuf, wmax, gpart, tl.G, st);
+        case 1: return launch_adj_mt<R, 1>(prm, sys, sv, j0, wlen, E, states, Gbuf, wmax, gpart, zs, tl.G, st, launches);
+        case 2: return launch_adj_mt<R, 2>(prm, sys, sv, j0, wlen, E, states, Gbuf, wmax, gpart, zs, tl.G, st, launches);
+        case 3: return launch_adj_mt<R, 3>(prm, sys, sv, j0, wlen, E, states, Gbuf, wmax, gpart, zs, tl.G, st, launches);
+        case 4: return launch_adj_mt<R, 4>(prm, sys, sv, j0, wlen, E, states, Gbuf, wmax, gpart, zs, tl.G, st, launches);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -389,9 +568,15 @@ template size_t fused_adj_smem<float>(int);
 template size_t fused_adj_smem<double>(int);
 template int fused_max_d<float>();
 template int fused_max_d<double>();
-template cudaError_t launch_expm_fwd_fused<float>(const DevParams*, const SysView<float>&, int, int, int, float2*, long long, int, cudaStream_t);
-template cudaError_t launch_expm_fwd_fused<double>(const DevParams*, const SysView<double>&, int, int, int, double2*, long long, int, cudaStream_t);
-template cudaError_t launch_expm_adj_fused<float>(const DevParams*, const SysView<float>&, const StateView<float>&, int, int, int, const float2*, const float2*, int, double*, cudaStream_t);
-template cudaError_t launch_expm_adj_fused<double>(const DevParams*, const SysView<double>&, const StateView<double>&, int, int, int, const double2*, const double2*, int, double*, cudaStream_t);
+template cudaError_t launch_expm_fwd_fused<float>(const DevParams*, const SysView<float>&, int, int, int, float2*,
+                                                  long long, int, const ZStore<float>&, cudaStream_t);
+template cudaError_t launch_expm_fwd_fused<double>(const DevParams*, const SysView<double>&, int, int, int, double2*,
+                                                   long long, int, const ZStore<double>&, cudaStream_t);
+template cudaError_t launch_expm_adj_fused<float>(const DevParams*, const SysView<float>&, const StateView<float>&,
+                                                  int, int, int, const float2*, const float2*, int, double*,
+                                                  const ZStore<float>&, cudaStream_t, int*);
+template cudaError_t launch_expm_adj_fused<double>(const DevParams*, const SysView<double>&, const StateView<double>&,
+                                                   int, int, int, const double2*, const double2*, int, double*,
+                                                   const ZStore<double>&, cudaStream_t, int*);
 
 }  // namespace qoc

@@ -10,7 +10,8 @@
 //   * the Horner division by i and the identity shift are done in the same pair arithmetic,
 //   * Horner steps i > m_split use plain FP32 on the hi parts: an error made there reaches T
 //     scaled by ts^m / m! < 2^-6 (m_split is picked with (p, n) from the FP64 norm bound).
-// Only the rounded U_j (the hi part) is stored: propagation, costates and the adjoint stay FP32.
+// Only the rounded U_j is kept for the propagation (costates and the adjoint stay FP32), plus,
+// for the reverse-mode adjoint, the rounded right operand of every product (ZStore).
 // The same kernel is used for the recomputation in the backward sweep, so the forward and
 // backward propagators are bitwise identical.
 #include "qoc_device.cuh"
@@ -146,7 +147,7 @@ __device__ __forceinline__ void df_store(float4* __restrict__ out, float (&ar)[M
 template <int MT>
 __global__ void __launch_bounds__(512)
 k_expm_fwd_split(const DevParams* __restrict__ prm, SysView<float> sys, const double2* __restrict__ H64, int j0,
-                 float2* __restrict__ Ubuf, long long ustride, int wmax, int G) {
+                 float2* __restrict__ Ubuf, long long ustride, int wmax, ZStore<float> zs, int G) {
     const int D = G * MT, LD = D + 1, SZ = D * LD;
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ double us[kMaxControls];
@@ -200,7 +201,18 @@ k_expm_fwd_split(const DevParams* __restrict__ prm, SysView<float> sys, const do
     float4* zin = Za;
     float4* zout = Zb;
     const int m_split = prm->m_split;
+    float2* zst = (zs.Z && p - 1 + n <= zs.cap) ? zs.Z + ((size_t)e * zs.wmax + jl) * zs.cap * zs.mstride : nullptr;
+    // the right operand of product r, rounded to FP32 and conjugate-transposed, for the adjoint
+    auto store = [&](int r) {
+        float2* dst = zst + (size_t)r * zs.mstride;
+        for (int idx = tid; idx < d * d; idx += blockDim.x) {
+            const int a = idx / d, b = idx - a * d;
+            const float4 v = zin[b * LD + a];
+            dst[idx] = make_float2(v.x + v.z, -(v.y + v.w));
+        }
+    };
     for (int i = p - 1; i >= 1; --i) {        // Horner: Z <- I + X Z / i
+        if (zst) store(p - 1 - i);
         if (!act) {
         } else if (i > m_split) {
             float2 acc[MT][MT];
@@ -232,6 +244,7 @@ k_expm_fwd_split(const DevParams* __restrict__ prm, SysView<float> sys, const do
         float4* t = zin; zin = zout; zout = t;
     }
     for (int m = 0; m < n; ++m) {             // squaring: Z <- Z Z
+        if (zst) store(p - 1 + m);
         if (act) {
             float ar[MT][MT][2], ai[MT][MT][2];
             df_zero<MT>(ar, ai);
@@ -260,11 +273,12 @@ static size_t split_smem(int d) {
 
 template <int MT>
 static cudaError_t launch_split_mt(const DevParams* prm, const SysView<float>& sys, const double2* H64, int j0,
-                                   int wlen, int E, float2* Ubuf, long long ustride, int wmax, int G, cudaStream_t st) {
+                                   int wlen, int E, float2* Ubuf, long long ustride, int wmax, const ZStore<float>& zs,
+                                   int G, cudaStream_t st) {
     const size_t smem = split_smem(sys.d);
     cudaError_t err = cudaFuncSetAttribute(k_expm_fwd_split<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    k_expm_fwd_split<MT><<<dim3(wlen, E), slice_threads(G), smem, st>>>(prm, sys, H64, j0, Ubuf, ustride, wmax, G);
+    k_expm_fwd_split<MT><<<dim3(wlen, E), slice_threads(G), smem, st>>>(prm, sys, H64, j0, Ubuf, ustride, wmax, zs, G);
     return cudaGetLastError();
 }
 
@@ -275,14 +289,15 @@ int split_max_d() {
 }
 
 cudaError_t launch_expm_fwd_split(const DevParams* prm, const SysView<float>& sys, const double2* H64, int j0, int wlen,
-                                  int E, float2* Ubuf, long long ustride, int wmax, cudaStream_t st) {
+                                  int E, float2* Ubuf, long long ustride, int wmax, const ZStore<float>& zs,
+                                  cudaStream_t st) {
     const SliceTile tl = slice_tile(sys.d);
     if (sys.d > split_max_d()) return cudaErrorInvalidValue;
     switch (tl.MT) {
-        case 1: return launch_split_mt<1>(prm, sys, H64, j0, wlen, E, Ubuf, ustride, wmax, tl.G, st);
-        case 2: return launch_split_mt<2>(prm, sys, H64, j0, wlen, E, Ubuf, ustride, wmax, tl.G, st);
-        case 3: return launch_split_mt<3>(prm, sys, H64, j0, wlen, E, Ubuf, ustride, wmax, tl.G, st);
-        case 4: return launch_split_mt<4>(prm, sys, H64, j0, wlen, E, Ubuf, ustride, wmax, tl.G, st);
+        case 1: return launch_split_mt<1>(prm, sys, H64, j0, wlen, E, Ubuf, ustride, wmax, zs, tl.G, st);
+        case 2: return launch_split_mt<2>(prm, sys, H64, j0, wlen, E, Ubuf, ustride, wmax, zs, tl.G, st);
+        case 3: return launch_split_mt<3>(prm, sys, H64, j0, wlen, E, Ubuf, ustride, wmax, zs, tl.G, st);
+        case 4: return launch_split_mt<4>(prm, sys, H64, j0, wlen, E, Ubuf, ustride, wmax, zs, tl.G, st);
         default: return cudaErrorInvalidValue;
     }
 }

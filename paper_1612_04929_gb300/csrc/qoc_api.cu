@@ -149,12 +149,14 @@ struct qoc_ctx {
         gpart, prm, u_h, grad_h, out_h, scratch, tc_planes;
     // segmented scan: segment products (two wave sets), tree levels, scan states, costate carries
     DevBuf Pbuf, lv0, lv1, scanst, hbuf, Ybuf;
+    DevBuf Zbuf;                         // product operands for the reverse-mode adjoint (per-slice path)
+    size_t zmstride = 0;
     TcMaps tc_maps{};
 
     size_t device_bytes() const {
         const DevBuf* all[] = {&H64, &HR, &dDelta, &norms, &psiTR, &pathR, &fmask, &colw, &ckpt, &Ubuf, &states,
                                &Gbuf, &src, &carry, &Oj, &C5j, &Ofin, &gpart, &prm, &u_h, &grad_h, &out_h, &scratch,
-                               &tc_planes, &Pbuf, &lv0, &lv1, &scanst, &hbuf, &Ybuf};
+                               &tc_planes, &Pbuf, &lv0, &lv1, &scanst, &hbuf, &Ybuf, &Zbuf};
         size_t s = 0;
         for (auto* b : all) s += b->bytes;
         return s;
@@ -257,6 +259,7 @@ void plan_impl(qoc_ctx* c) {
         if (c->path_kind == 1) per += big_scratch_per_item(d, sizeof(R) == 8);
         if (use_tc(c)) per += tc_scratch_floats(d, 1) * sizeof(float);
         if (c->scan) per += dd0 * ks + (2 * (size_t)c->ustride * ks + seg - 1) / seg;
+        if (c->path_kind == 0) per += 2 * (size_t)kZCap * ((dd0 + 31) / 32 * 32) * cs;
         per *= (size_t)E;
         size_t free_b = 0, total_b = 0;
         if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = (size_t)8 << 30;
@@ -273,7 +276,7 @@ void plan_impl(qoc_ctx* c) {
     c->nzmax = W / seg;
     const int nseg_total = c->nseg_total;
 
-    StateView<R> sv{c->Spad, c->cb, c->ncb, c->pstride};
+    StateView<R> sv{c->Spad, c->cb, c->ncb, c->pstride, c->S_eff};
     cudaStream_t st = c->stream;
     auto A = [&](DevBuf& b, size_t bytes, const char* what) { check_cuda(c, b.alloc(bytes), what); };
 
@@ -349,6 +352,12 @@ void plan_impl(qoc_ctx* c) {
     } else {
         c->tc_planes.release();
     }
+    if (c->path_kind == 0) {
+        c->zmstride = (dd + 31) / 32 * 32;
+        A(c->Zbuf, 2 * (size_t)E * W * kZCap * c->zmstride * cs, "alloc product operands");
+    } else {
+        c->Zbuf.release();
+    }
     if (c->scan) {
         const size_t nz = (size_t)c->nzmax, ks = sizeof(K_t<R>);
         const size_t half = (size_t)((seg + 1) / 2);
@@ -389,7 +398,7 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
     const int d = c->d, N = c->N, E = c->E, M = c->M, W = c->W, nw = c->nw;
     cudaStream_t st = c->stream;   // parallel kernels (the caller's stream)
     cudaStream_t sx = c->aux;      // serial sweeps and the small per-slice kernels
-    StateView<R> sv{c->Spad, c->cb, c->ncb, c->pstride};
+    StateView<R> sv{c->Spad, c->cb, c->ncb, c->pstride, c->S_eff};
     const size_t slice = sv.slice();
     const size_t dd = (size_t)d * d;
     C* HR = c->HR.as<C>();
@@ -469,6 +478,12 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
         return BigArgs<R>{prm, bsys, d, E, j0, std::min(W, N - j0), W, c->scratch.p, c->mstride, Ub(w), c->ustride};
     };
     int extra = 0;   // kernels of the batched calls beyond the one counted by L
+    // stored product operands of the per-slice path (two wave sets)
+    auto zstore = [&](int w) {
+        ZStore<R> z{nullptr, kZCap, c->zmstride, W};
+        if (c->Zbuf.p) z.Z = c->Zbuf.as<C>() + (size_t)(w & 1) * E * W * kZCap * c->zmstride;
+        return z;
+    };
     auto expm_fwd = [&](int w) -> cudaError_t {
         const int j0 = w * W, wlen = std::min(W, N - j0);
         if (big) {
@@ -479,9 +494,10 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
         }
         if constexpr (sizeof(R) == 4) {
             if (split)
-                return launch_expm_fwd_split(prm, sys, c->H64.as<double2>(), j0, wlen, E, Ub(w), c->ustride, W, st);
+                return launch_expm_fwd_split(prm, sys, c->H64.as<double2>(), j0, wlen, E, Ub(w), c->ustride, W,
+                                             zstore(w), st);
         }
-        return launch_expm_fwd_fused<R>(prm, sys, j0, wlen, E, Ub(w), c->ustride, W, st);
+        return launch_expm_fwd_fused<R>(prm, sys, j0, wlen, E, Ub(w), c->ustride, W, zstore(w), st);
     };
     auto expm_adj = [&](int w) -> cudaError_t {
         const int j0 = w * W, wlen = std::min(W, N - j0);
@@ -502,7 +518,11 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
             extra += n_l - 1;
             return e;
         }
-        return launch_expm_adj_fused<R>(prm, sys, sv, j0, wlen, E, Sb(w), Gb(w), W, c->gpart.as<double>(), st);
+        int n_l = 0;
+        cudaError_t e = launch_expm_adj_fused<R>(prm, sys, sv, j0, wlen, E, Sb(w), Gb(w), W, c->gpart.as<double>(),
+                                                 zstore(w), st, &n_l);
+        extra += n_l - 1;
+        return e;
     };
     const int nzmax = c->nzmax;
     const size_t p_set = (size_t)E * nzmax * c->ustride;

@@ -40,6 +40,7 @@ struct SysView {
 template <typename R>
 struct StateView {
     int Spad, cb, ncb, pstride;
+    int S;                  // propagated columns (<= Spad; the padding columns are zero)
     __host__ __device__ size_t slice() const { return (size_t)ncb * pstride; }
 };
 
@@ -86,20 +87,36 @@ inline SliceTile slice_tile(int d) {
 // threads of a per-slice CTA: G x G rounded up to whole warps (the extra threads take part in
 // the element-wise loops and reductions only)
 inline int slice_threads(int G) { return (G * G + 31) / 32 * 32; }
+// Inputs of the forward products of every slice exponential, kept for the reverse-mode adjoint:
+// product r (r = 0 .. p-2: Horner step i = p-1-r, right operand Z_{i+1}; r = p-1+m: squaring m,
+// operand S_m = T^(2^m)) stores the conjugate transpose of its right operand, rounded to the
+// compute precision, at Z + ((e * wmax + j) * cap + r) * mstride.  Used when p - 1 + n <= cap.
+template <typename R>
+struct ZStore {
+    C_t<R>* Z;              // nullptr: no stores (the adjoint recomputes, block recursion)
+    int cap;
+    size_t mstride;
+    int wmax;
+};
+constexpr int kZCap = 24;
+
 template <typename R> int fused_max_d();
 template <typename R> size_t fused_adj_smem(int d);   // dynamic SMEM of the per-slice adjoint kernel
 template <typename R>
 cudaError_t launch_expm_fwd_fused(const DevParams* prm, const SysView<R>& sys, int j0, int wlen, int E,
-                                  C_t<R>* Ubuf, long long ustride, int wmax, cudaStream_t st);
+                                  C_t<R>* Ubuf, long long ustride, int wmax, const ZStore<R>& zs, cudaStream_t st);
+// the adjoint: reverse mode over the stored products when they are there (two products per step),
+// else the block recursion (three); the kernel of the other mode exits at once
 template <typename R>
 cudaError_t launch_expm_adj_fused(const DevParams* prm, const SysView<R>& sys, const StateView<R>& sv, int j0,
                                   int wlen, int E, const C_t<R>* states, const C_t<R>* Gbuf, int wmax,
-                                  double* gpart, cudaStream_t st);
+                                  double* gpart, const ZStore<R>& zs, cudaStream_t st, int* launches);
 
 // ---- split hi+lo FP32 slice exponential (FP32 form) ----
 int split_max_d();
 cudaError_t launch_expm_fwd_split(const DevParams* prm, const SysView<float>& sys, const double2* H64, int j0, int wlen,
-                                  int E, float2* Ubuf, long long ustride, int wmax, cudaStream_t st);
+                                  int E, float2* Ubuf, long long ustride, int wmax, const ZStore<float>& zs,
+                                  cudaStream_t st);
 
 // ---- large-d batched slice exponentials and adjoint (k_big.cu) ----
 struct BigSys {

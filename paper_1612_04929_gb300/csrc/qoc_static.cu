@@ -72,6 +72,7 @@ extern "C" qoc_status qoc_evaluate_static(int d, int M, int N, int S, double dt,
     sv.ncb = (S + sv.cb - 1) / sv.cb;
     sv.Spad = sv.ncb * sv.cb;
     sv.pstride = d * sv.cb;                       // 16-byte elements: always aligned
+    sv.S = S;
     const size_t slice = sv.slice();
     const long long ustride = 2 * (((long long)d * d + 15) / 16 * 16);   // U_j and U_j^dag
 
@@ -115,7 +116,8 @@ extern "C" qoc_status qoc_evaluate_static(int d, int M, int N, int S, double dt,
                      {alpha[0], alpha[1], alpha[2], alpha[3], alpha[4]}};
     ChainArgs<R> ch{d, sv, N, N, 0, 1, ckpt, slice, 0, 1, Ubuf, ustride, N, states};
     if (!ok(launch_theta(u_dev, M, N, norms, nullptr, 1, dt, 0.25, 1e-15, 0, -1, prm, st))) return QOC_ERR_CUDA;
-    if (!ok(launch_expm_fwd_fused<R>(prm, sys, 0, N, 1, Ubuf, ustride, N, st))) return QOC_ERR_CUDA;
+    const ZStore<R> nostore{nullptr, 0, 0, 0};   // the arena holds no product operands: block recursion
+    if (!ok(launch_expm_fwd_fused<R>(prm, sys, 0, N, 1, Ubuf, ustride, N, nostore, st))) return QOC_ERR_CUDA;
     if (!ok(launch_chain<R>(ch, st))) return QOC_ERR_CUDA;
     if (!ok(launch_slice_costs<R>(d, sv, 0, N, N, 1, states, N, cost, Oj, C5j, Ofin, st))) return QOC_ERR_CUDA;
     if (!ok(launch_sources<R>(d, sv, 0, N, N, 1, states, N, cost, Oj, Ofin, src, st))) return QOC_ERR_CUDA;
@@ -130,7 +132,9 @@ extern "C" qoc_status qoc_evaluate_static(int d, int M, int N, int S, double dt,
     co.G = Gbuf;
     co.cin = co.cout = carry;
     if (!ok(launch_costate<R>(co, st))) return QOC_ERR_CUDA;
-    if (!ok(launch_expm_adj_fused<R>(prm, sys, sv, 0, N, 1, states, Gbuf, N, gpart, st))) return QOC_ERR_CUDA;
+    int n_adj = 0;
+    if (!ok(launch_expm_adj_fused<R>(prm, sys, sv, 0, N, 1, states, Gbuf, N, gpart, nostore, st, &n_adj)))
+        return QOC_ERR_CUDA;
     if (!ok(launch_finalize(1, M, N, u_dev, alpha, Oj, C5j, Ofin, gpart, grad_dev, out_dev, st)))
         return QOC_ERR_CUDA;
     return QOC_OK;

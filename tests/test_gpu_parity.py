@@ -102,6 +102,21 @@ def test_fp64_short_series_is_differentiated_exactly():
     assert rel(grad, g_e) > 1e-6
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("fp32", 1e-5)])
+@pytest.mark.parametrize("pn", [(12, 2), (26, 0)], ids=["stored-products", "recomputed"])
+def test_both_adjoint_modes_differentiate_the_series_exactly(precision, tol, pn):
+    """The per-slice adjoint runs in reverse mode over the forward's stored product operands when
+    p - 1 + n fits the store (24 products), else by the block recursion that recomputes them;
+    both are the exact derivative of the same truncated map."""
+    p, n = pn
+    prob = sy.random_problem(d=9, M=2, N=14, S=3, seed=111, nF=2, path=True, E=2, dt=0.1, u_scale=0.5)
+    cost, grad, terms, info = run(prob, precision, p_override=p, n_override=n)
+    assert (info["p"], info["n"]) == (p, n)
+    c_t, g_t, _ = orc.taylor_cost_and_grad(prob, prob.u, p, n)
+    assert abs(cost - c_t) <= tol * abs(c_t)
+    assert rel(grad, g_t) <= tol
+
+
 CASES32 = [
     dict(d=4, M=2, N=50, S=4, seed=201, nF=1),
     dict(d=13, M=3, N=37, S=1, seed=202, nF=2, path=True),
@@ -110,7 +125,8 @@ CASES32 = [
     dict(d=64, M=3, N=21, S=8, seed=205, nF=4, weights=True),   # 4 x 4 outputs per thread
     dict(d=68, M=2, N=11, S=3, seed=206, nF=2),                 # largest fused FP32 size
     dict(d=23, M=2, N=19, S=2, seed=207, nF=2, E=2),            # 2 x 2 outputs, one padding row
-]
+    dict(d=40, M=2, N=6, S=40, seed=208, nF=3, E=16),           # unitary, 3-column panels: padded
+]                                                               # columns beyond the matrix slot
 
 
 @pytest.mark.parametrize("case", CASES32, ids=lambda c: f"d{c['d']}S{c['S']}N{c['N']}")

@@ -15,12 +15,15 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-10   # the FP64 tolerance of the parity tests
 
 
-def test_static_entry_point_matches_context_entry_point_twice():
+@pytest.mark.parametrize("case", [dict(d=8, M=3, N=60, S=3, seed=901, nF=2),
+                                  dict(d=44, M=2, N=12, S=41, seed=903, nF=3)],   # 8-column panels padded
+                         ids=["d8S3", "d44S41"])                                   # past the d x d slot
+def test_static_entry_point_matches_context_entry_point_twice(case):
     import torch
     from paper_1612_04929_gb300 import Context, build, qoc_evaluate_static
 
     build.build()
-    prob = sy.random_problem(d=8, M=3, N=60, S=3, seed=901, nF=2, dt=0.2, u_scale=0.8)
+    prob = sy.random_problem(**case, dt=0.2, u_scale=0.8)
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
 
