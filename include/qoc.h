@@ -58,10 +58,15 @@ typedef enum qoc_precision {
     QOC_PREC_FP64 = 0,          /* plain FP64 form: parity anchor */
     QOC_PREC_FP32 = 1,          /* FP32 propagation, costates and adjoint; slice exponentials in
                                    split hi+lo FP32 (see qoc_options.plain_fp32_exp) */
-    QOC_PREC_TF32_SPLIT = 2,    /* the FP32 form, with the products of the large-d adjoint (d > 64)
-                                   on tcgen05 tensor cores: TF32 hi + lo split, three MMAs per real
-                                   product, FP32 accumulation in tensor memory */
-    QOC_PREC_BF16_SPLIT = 3     /* reserved; qoc_create returns QOC_ERR_UNSUPPORTED */
+    QOC_PREC_TF32_SPLIT = 2,    /* the FP32 form, with the products of the large-d adjoint (d > 68)
+                                   on tcgen05 tensor cores: TF32 hi + mid + lo split, six MMAs per
+                                   real product, FP32 accumulation in tensor memory (the
+                                   accumulator's truncation leaves ~2e-5 relative gradient error on
+                                   long evolutions) */
+    QOC_PREC_BF16_SPLIT = 3     /* the FP32 form, with the products of the large-d adjoint (d > 68)
+                                   on tcgen05 tensor cores with exact accumulation: four six-bit
+                                   integer slices per value in BF16, per-row / per-column
+                                   power-of-two scales, every accumulator an exact integer */
 } qoc_precision;
 
 typedef struct qoc_options {

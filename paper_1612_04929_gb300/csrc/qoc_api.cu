@@ -202,6 +202,8 @@ bool is_fp64(const qoc_ctx* c) { return c->opt.precision == QOC_PREC_FP64; }
 
 // TF32_SPLIT: the FP32 form with the large-d adjoint products on tcgen05 (TF32 x3 split)
 bool use_tc(const qoc_ctx* c) { return c->opt.precision == QOC_PREC_TF32_SPLIT && c->path_kind == 1; }
+// BF16_SPLIT: the FP32 form with the large-d adjoint products on tcgen05 with exact accumulation
+bool use_oz(const qoc_ctx* c) { return c->opt.precision == QOC_PREC_BF16_SPLIT && c->path_kind == 1; }
 
 template <typename R>
 bool split_exp(const qoc_ctx* c) {
@@ -226,25 +228,28 @@ void plan_impl(qoc_ctx* c) {
         if (c->w[s] > 0.0) c->cols.push_back(s);
     const int S = (int)c->cols.size();
     c->S_eff = S;
-    // column panel width: one CTA of a serial sweep per panel and member; narrow panels spread
-    // a wide block over more SMs (about two sweep CTAs per SM), up to 8 columns per panel
+    // checkpoint stride (sqrt N by default) and the form of the recursions
+    int seg = c->opt.ckpt_stride > 0 ? c->opt.ckpt_stride : (int)std::ceil(std::sqrt((double)N));
+    seg = std::max(1, std::min(seg, N));
+    c->scan = c->opt.sweep == QOC_SWEEP_SCAN || (c->opt.sweep == QOC_SWEEP_AUTO && seg >= 4);
+    // column panel width: a sweep CTA owns one panel of one member (and, in the segmented form,
+    // one segment); wide panels read each U_j once for more columns, narrow ones spread the work
+    // over more SMs: about two sweep CTAs per SM, up to 8 columns per panel.  The segments of a
+    // (default, half-evolution) wave count towards the parallelism of the segmented form.
     int sms0 = 0;
     cudaDeviceGetAttribute(&sms0, cudaDevAttrMultiProcessorCount, c->opt.device);
     const long want_ctas = 2L * std::max(sms0, 1);
-    c->cb = (int)std::max(1L, std::min<long>(8, ((long)S * E + want_ctas - 1) / want_ctas));
+    const long par = c->scan ? std::max(1L, ((long)(N + 1) / 2 + seg - 1) / seg) : 1L;
+    c->cb = (int)std::max(1L, std::min<long>(8, ((long)S * E * par + want_ctas - 1) / want_ctas));
     c->cb = std::min(c->cb, S);
     c->ncb = (S + c->cb - 1) / c->cb;
     c->Spad = c->ncb * c->cb;
     const int align_elems = (int)(16 / cs) > 0 ? (int)(16 / cs) : 1;
     c->pstride = ((d * c->cb + align_elems - 1) / align_elems) * align_elems;
     const size_t slice = (size_t)c->ncb * c->pstride;
-    // checkpoint stride (sqrt N by default)
-    int seg = c->opt.ckpt_stride > 0 ? c->opt.ckpt_stride : (int)std::ceil(std::sqrt((double)N));
-    seg = std::max(1, std::min(seg, N));
     // one slice of the propagator buffer holds U_j and U_j^dag, each padded to 256 bytes
     const long long ue = 256 / (long long)cs;
     c->ustride = 2 * ((((long long)d * d + ue - 1) / ue) * ue);
-    c->scan = c->opt.sweep == QOC_SWEEP_SCAN || (c->opt.sweep == QOC_SWEEP_AUTO && seg >= 4);
     // Wave: the slices whose propagators are held at once (a multiple of the stride).  Two wave
     // sets alternate, and after the forward pass they still hold the last two waves, so with at
     // most two waves nothing is recomputed in the backward pass.  By default the wave is half the
@@ -258,6 +263,7 @@ void plan_impl(qoc_ctx* c) {
         size_t per = 2 * ((size_t)c->ustride * cs + 3 * slice * cs);          // U, states, G, sources
         if (c->path_kind == 1) per += big_scratch_per_item(d, sizeof(R) == 8);
         if (use_tc(c)) per += tc_scratch_floats(d, 1) * sizeof(float);
+        if (use_oz(c)) per += oz_scratch_bytes(d, 1);
         if (c->scan) per += dd0 * ks + (2 * (size_t)c->ustride * ks + seg - 1) / seg;
         if (c->path_kind == 0) per += 2 * (size_t)kZCap * ((dd0 + 31) / 32 * 32) * cs;
         per *= (size_t)E;
@@ -345,7 +351,12 @@ void plan_impl(qoc_ctx* c) {
     } else {
         c->scratch.release();
     }
-    if (use_tc(c)) {
+    if (use_oz(c)) {
+        const size_t pbytes = (size_t)E * W * kOzMats * 8 * (size_t)d * oz_ld(d) * 2;
+        A(c->tc_planes, oz_scratch_bytes(d, E * W) + 512, "alloc tensor-core slices");
+        check_cuda(c, cudaMemsetAsync(c->tc_planes.p, 0, pbytes, st), "clear slices");
+        check_cuda(c, oz_make_maps(c->tc_planes.p, d, E * W, &c->tc_maps), "tensor maps");
+    } else if (use_tc(c)) {
         A(c->tc_planes, tc_scratch_floats(d, E * W) * sizeof(float), "alloc tensor-core planes");
         check_cuda(c, cudaMemsetAsync(c->tc_planes.p, 0, c->tc_planes.bytes, st), "clear planes");
         check_cuda(c, tc_make_maps(c->tc_planes.as<float>(), d, E * W, &c->tc_maps), "tensor maps");
@@ -502,6 +513,14 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
     auto expm_adj = [&](int w) -> cudaError_t {
         const int j0 = w * W, wlen = std::min(W, N - j0);
         if constexpr (sizeof(R) == 4) {
+            if (big && use_oz(c)) {
+                int n_l = 0;
+                OzAdjArgs oa{prm, sys, sv, d, E, j0, wlen, W, hp.p, hp.n, Sb(w), Gb(w), c->tc_planes.as<unsigned char>(),
+                             c->tc_maps, c->gpart.as<double>()};
+                cudaError_t e = launch_oz_adj(oa, st, &n_l);
+                extra += n_l - 1;
+                return e;
+            }
             if (big && use_tc(c)) {
                 int n_l = 0;
                 TcAdjArgs ta{prm, sys, sv, d, E, j0, wlen, W, hp.p, hp.n, Sb(w), Gb(w), c->tc_planes.as<float>(),
@@ -777,7 +796,6 @@ qoc_status qoc_create(qoc_ctx** out, const qoc_options* opt) {
     qoc_default_options(&o);
     if (opt) o = *opt;
     if (o.precision < QOC_PREC_FP64 || o.precision > QOC_PREC_BF16_SPLIT) return QOC_ERR_ARG;
-    if (o.precision == QOC_PREC_BF16_SPLIT) return QOC_ERR_UNSUPPORTED;
     if (!(o.tol >= 0.0) || !(o.theta_max >= 0.0) || o.ckpt_stride < 0 || o.wave_slices < 0 || o.sweep < 0 ||
         o.sweep > QOC_SWEEP_SCAN)
         return QOC_ERR_ARG;

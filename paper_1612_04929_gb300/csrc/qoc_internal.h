@@ -178,6 +178,36 @@ size_t tc_scratch_floats(int d, int items);
 cudaError_t tc_make_maps(float* planes, int d, int items, TcMaps* maps);
 cudaError_t launch_tc_adj(const TcAdjArgs& a, cudaStream_t st, int* launches);
 
+// ---- tensor-core adjoint products with exact accumulation, BF16_SPLIT form (k_oz.cu) ----
+constexpr int kOzMats = 10;   // sliced matrices: XH, Ubar (row), two sets of Z11 / Z12 (row, col)
+constexpr int kOzVals = 6;    // FP32 values: XH, Ubar, Z11 (two sets), Z12 (two sets)
+inline int oz_ld(int d) { return (d + 7) / 8 * 8; }   // plane row stride (BF16): 16-byte rows for TMA
+struct OzSliceJob { int val, mat, col; };
+struct OzSliceJobs { OzSliceJob job[6]; };
+struct OzTerm { int a_mat, b_mat; };
+struct OzOut {
+    int nterms, val, identity;
+    OzTerm t[2];
+};
+struct OzStep {
+    int kind, i;            // 0: Horner step i, 1: squaring
+    OzOut o[2];             // Z11', Z12'
+};
+struct OzAdjArgs {
+    DevParams* prm;
+    SysView<float> sys;
+    StateView<float> sv;
+    int d, E, j0, wlen, wmax, p, n;
+    const float2* states;
+    const float2* Gbuf;
+    unsigned char* scratch; // oz_scratch_bytes(d, items)
+    TcMaps maps;
+    double* gpart;
+};
+size_t oz_scratch_bytes(int d, int items);
+cudaError_t oz_make_maps(void* planes, int d, int items, TcMaps* maps);
+cudaError_t launch_oz_adj(const OzAdjArgs& a, cudaStream_t st, int* launches);
+
 // ---- serial sweeps (k_serial.cu) ----
 // mode 0: forward propagation of one wave (grid z = 1) from checkpoint `seg0`, storing the
 //         states of the wave and the carried block every `seg` slices (checkpoints seg0 + 1, ..)

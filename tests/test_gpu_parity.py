@@ -13,7 +13,7 @@ from oracle import qoc_oracle as orc
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-10, "fp32": 1e-5, "tf32": 1e-5}
+TOL = {"fp64": 1e-10, "fp32": 1e-5, "tf32": 1e-5, "bf16": 1e-5}
 
 
 @pytest.fixture(scope="module", autouse=True)
