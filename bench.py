@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=0, help="slices in the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-form", action="store_true", help="skip timing the plain FP64 GPU form")
+    ap.add_argument("--gradient", choices=["exact", "first_order"], default="exact",
+                    help="exact derivative of the truncated series, or the paper's first-order Eq. 11")
     return ap.parse_args()
 
 
@@ -115,7 +117,7 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ oracle (CPU) timing
-def oracle_sample_time(workload, nslices, repeats=1, ref_slices=0):
+def oracle_sample_time(workload, nslices, repeats=1, ref_slices=0, exact=True):
     """Times the CPU FP64 oracle on the first `nslices` slices of the workload in a child
     process limited to one BLAS thread.  With ref_slices > 0 the child also evaluates the oracle
     once on the first ref_slices slices (untimed) and returns its cost and gradient, the
@@ -133,7 +135,7 @@ for _ in range({repeats}):
 ref = None
 if {ref_slices} > 0:
     q = sy.WORKLOADS[{workload!r}](N={ref_slices})
-    c, g, _ = orc.cost_and_grad(q, q.u)
+    c, g, _ = orc.cost_and_grad(q, q.u, exact={exact!r})
     ref = {{"N": {ref_slices}, "cost": float(c), "grad": [float(x) for x in g.ravel()]}}
 print(json.dumps({{"t": sum(ts) / len(ts), "ref": ref}}))
 """
@@ -202,7 +204,8 @@ def ours_arm(args):
     precision = args.precision or prob.precision
     stream = torch.cuda.Stream()          # every kernel of the step and every event on one stream
     torch.cuda.set_stream(stream)
-    ctx = Context(precision, device=local, stream=stream.cuda_stream, ckpt_stride=args.ckpt_stride, profile=True)
+    ctx = Context(precision, device=local, stream=stream.cuda_stream, ckpt_stride=args.ckpt_stride, profile=True,
+                  gradient=args.gradient)
     ctx.set_problem(prob)
     u = torch.tensor(prob.u, dtype=torch.float64, device="cuda")
     grad = torch.empty_like(u)
@@ -287,7 +290,8 @@ def ours_arm(args):
     # mixed form over it, at the error stated below)
     fp64_form = None
     if precision != "fp64" and not args.no_fp64_form:
-        c64 = Context("fp64", device=local, stream=stream.cuda_stream, ckpt_stride=args.ckpt_stride)
+        c64 = Context("fp64", device=local, stream=stream.cuda_stream, ckpt_stride=args.ckpt_stride,
+                      gradient=args.gradient)
         c64.set_problem(prob)
         g64 = torch.empty_like(u)
         o64 = torch.empty(6, dtype=torch.float64, device="cuda")
@@ -317,7 +321,8 @@ def ours_arm(args):
         # the error reference: the whole workload where the oracle takes seconds, else the sample
         ref_n = prob.N if prob.d <= 81 else nsl
         try:
-            t, nsl, ref = oracle_sample_time(args.workload, nsl, ref_slices=ref_n)
+            t, nsl, ref = oracle_sample_time(args.workload, nsl, ref_slices=ref_n,
+                                             exact=args.gradient == "exact")
             cpu = {"value": nsl * prob.E / t, "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": f"first {nsl} of {prob.N} slices of the same workload, FP64 oracle, 1 BLAS thread, "
                              f"{t:.2f} s per evaluation"}
@@ -326,7 +331,7 @@ def ours_arm(args):
                     c_gpu, g_gpu = float(out[0].item()), grad.cpu().numpy()
                 else:   # evaluate the same form on the sample problem
                     q = make_problem(args.workload, ref_n)
-                    with Context(precision, device=local, stream=stream.cuda_stream) as cq:
+                    with Context(precision, device=local, stream=stream.cuda_stream, gradient=args.gradient) as cq:
                         cq.set_problem(q)
                         c_gpu, g_gpu, _ = cq.evaluate(q.u)
                 g_ref = np.asarray(ref["grad"])
@@ -344,7 +349,8 @@ def ours_arm(args):
                 "dtype": {"fp64": "f64", "fp32": "f32", "tf32": "tf32x3", "bf16": "bf16x3"}[precision],
                 "data": f"synthetic (seeded {prob.name} system, random controls)",
                 "config": config_of(prob, precision, info["ckpt_stride"],
-                                    {"p": p, "n": n, "wave_slices": info["wave_slices"], "n_waves": info["n_waves"]}),
+                                    {"p": p, "n": n, "wave_slices": info["wave_slices"], "n_waves": info["n_waves"],
+                                     "gradient": args.gradient}),
                 "roofline": roof, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": mn_bytes,
                         "d2h_bytes_per_step": mn_bytes + 6 * 8 + 32},

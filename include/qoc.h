@@ -98,9 +98,14 @@ typedef struct qoc_options {
                              QOC_SWEEP_AUTO (0), QOC_SWEEP_SERIAL (1: one step per slice), or
                              QOC_SWEEP_SCAN (2: products of the U_j over each checkpoint segment by
                              a parallel tree, a scan over segments, then all segments in parallel) */
+    int gradient;         /* QOC_GRAD_EXACT (0): the exact derivative of the truncated series;
+                             QOC_GRAD_FIRST_ORDER (1): the paper's approximate gradient (Eq. 11,
+                             dU_j/du_kj ~ -i dt H_k U_j), O(M d^2 S) per slice instead of an adjoint
+                             exponential; its error is O(dt ||[H_j, H_k]||) */
 } qoc_options;
 
 enum { QOC_SWEEP_AUTO = 0, QOC_SWEEP_SERIAL = 1, QOC_SWEEP_SCAN = 2 };
+enum { QOC_GRAD_EXACT = 0, QOC_GRAD_FIRST_ORDER = 1 };
 
 /* Information about the last evaluation (reading it synchronises the context stream). */
 typedef struct qoc_info {

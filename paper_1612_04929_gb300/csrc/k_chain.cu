@@ -7,6 +7,8 @@
 //                         terms that Algorithm 3 adds at every slice; the fidelity term at j = N).
 //  * k_finalize         : FP64 cost reduction (Table I weighted sum), the C3/C4 gradient terms
 //                         and the ensemble sum of the per-slice gradients.
+//  * k_grad_first_order : the paper's approximate gradient (Eq. 11, dU_j ~ -i dt H_k U_j), an
+//                         option in place of the exact adjoint of the truncated exponential.
 #include <math.h>
 
 #include "qoc_device.cuh"
@@ -329,6 +331,52 @@ cudaError_t launch_finalize(int E, int M, int N, const double* u, const double* 
 }
 
 // ------------------------------------------------------------------------------------------
+// first-order gradient (Eq. 11): dC/du_{k,j} = Re tr(Ubar_j^dag (-i dt H_k U_j)) with
+// Ubar_j = G_j Psi_{j-1}^dag; since U_j Ubar_j^dag = Psi_j G_j^dag this is
+//   dt Im sum_s G_j[:, s]^dag H_k Psi_j[:, s],
+// O(M d^2 S) per slice and no exponential.  One CTA per (slice, member).
+// ------------------------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(256)
+k_grad_first_order(SysView<R> sys, StateView<R> sv, int j0, const C_t<R>* __restrict__ states,
+                   const C_t<R>* __restrict__ Gbuf, int wmax, double dt, double* __restrict__ gpart) {
+    using C = C_t<R>;
+    __shared__ double red[32];
+    const int jl = blockIdx.x, e = blockIdx.y, j = j0 + jl;
+    const int d = sys.d, S = sv.S;
+    const size_t slice = sv.slice(), dd = (size_t)d * d;
+    const C* Gj = Gbuf + ((size_t)e * wmax + jl) * slice;
+    const C* Pj = states + ((size_t)e * (wmax + 1) + jl + 1) * slice;   // Psi_j, after slice j
+    auto at = [&](int a, int s) { return (size_t)(s / sv.cb) * sv.pstride + (size_t)a * sv.cb + (s % sv.cb); };
+    for (int k = 0; k < sys.M; ++k) {
+        const C* hk = sys.Hk + (size_t)k * dd;
+        double v = 0.0;
+        for (int idx = threadIdx.x; idx < d * S; idx += blockDim.x) {   // (a, s): conj(G[a][s]) (H_k Psi)[a][s]
+            const int a = idx / S, s = idx - a * S;
+            double hr = 0.0, hi = 0.0;
+            for (int b = 0; b < d; ++b) {
+                const C h = hk[(size_t)a * d + b], q = Pj[at(b, s)];
+                hr += (double)h.x * (double)q.x - (double)h.y * (double)q.y;
+                hi += (double)h.x * (double)q.y + (double)h.y * (double)q.x;
+            }
+            const C g = Gj[at(a, s)];
+            v += (double)g.x * hi - (double)g.y * hr;   // Im(conj(g) (hr + i hi))
+        }
+        v = block_sum(v, red);
+        if (threadIdx.x == 0) gpart[((size_t)e * sys.M + k) * sys.N + j] = dt * v;
+    }
+}
+
+template <typename R>
+cudaError_t launch_grad_first_order(const SysView<R>& sys, const StateView<R>& sv, int j0, int wlen, int E,
+                                    const C_t<R>* states, const C_t<R>* Gbuf, int wmax, double dt, double* gpart,
+                                    cudaStream_t st) {
+    if (sys.M == 0) return cudaSuccess;
+    k_grad_first_order<R><<<dim3(wlen, E), 256, 0, st>>>(sys, sv, j0, states, Gbuf, wmax, dt, gpart);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
 // instantiations
 // ------------------------------------------------------------------------------------------
 #define QOC_INST(R)                                                                                              \
@@ -340,6 +388,9 @@ cudaError_t launch_finalize(int E, int M, int N, const double* u, const double* 
     template cudaError_t launch_sources<R>(int, StateView<R>, int, int, int, int, const C_t<R>*, int,            \
                                            const CostView<R>&, const double2*, const double2*, C_t<R>*,          \
                                            cudaStream_t);                                                        \
+    template cudaError_t launch_grad_first_order<R>(const SysView<R>&, const StateView<R>&, int, int, int,       \
+                                                    const C_t<R>*, const C_t<R>*, int, double, double*,          \
+                                                    cudaStream_t);                                               \
 
 QOC_INST(float)
 QOC_INST(double)

@@ -265,7 +265,8 @@ void plan_impl(qoc_ctx* c) {
         if (use_tc(c)) per += tc_scratch_floats(d, 1) * sizeof(float);
         if (use_oz(c)) per += oz_scratch_bytes(d, 1);
         if (c->scan) per += dd0 * ks + (2 * (size_t)c->ustride * ks + seg - 1) / seg;
-        if (c->path_kind == 0) per += 2 * (size_t)kZCap * ((dd0 + 31) / 32 * 32) * cs;
+        if (c->path_kind == 0 && c->opt.gradient == QOC_GRAD_EXACT)
+            per += 2 * (size_t)kZCap * ((dd0 + 31) / 32 * 32) * cs;
         per *= (size_t)E;
         size_t free_b = 0, total_b = 0;
         if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = (size_t)8 << 30;
@@ -363,7 +364,7 @@ void plan_impl(qoc_ctx* c) {
     } else {
         c->tc_planes.release();
     }
-    if (c->path_kind == 0) {
+    if (c->path_kind == 0 && c->opt.gradient == QOC_GRAD_EXACT) {
         c->zmstride = (dd + 31) / 32 * 32;
         A(c->Zbuf, 2 * (size_t)E * W * kZCap * c->zmstride * cs, "alloc product operands");
     } else {
@@ -512,6 +513,8 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
     };
     auto expm_adj = [&](int w) -> cudaError_t {
         const int j0 = w * W, wlen = std::min(W, N - j0);
+        if (c->opt.gradient == QOC_GRAD_FIRST_ORDER)
+            return launch_grad_first_order<R>(sys, sv, j0, wlen, E, Sb(w), Gb(w), W, c->dt, c->gpart.as<double>(), st);
         if constexpr (sizeof(R) == 4) {
             if (big && use_oz(c)) {
                 int n_l = 0;
@@ -797,7 +800,7 @@ qoc_status qoc_create(qoc_ctx** out, const qoc_options* opt) {
     if (opt) o = *opt;
     if (o.precision < QOC_PREC_FP64 || o.precision > QOC_PREC_BF16_SPLIT) return QOC_ERR_ARG;
     if (!(o.tol >= 0.0) || !(o.theta_max >= 0.0) || o.ckpt_stride < 0 || o.wave_slices < 0 || o.sweep < 0 ||
-        o.sweep > QOC_SWEEP_SCAN)
+        o.sweep > QOC_SWEEP_SCAN || o.gradient < QOC_GRAD_EXACT || o.gradient > QOC_GRAD_FIRST_ORDER)
         return QOC_ERR_ARG;
     const bool f64 = o.precision == QOC_PREC_FP64;
     if (o.tol == 0.0) o.tol = f64 ? 1e-15 : 1e-8;

@@ -283,6 +283,11 @@ template <typename R>
 cudaError_t launch_sources(int d, StateView<R> sv, int j0, int wlen, int N, int E, const C_t<R>* states,
                            int wmax, const CostView<R>& cv, const double2* Oj, const double2* Ofin,
                            C_t<R>* src, cudaStream_t st);
+// the paper's first-order gradient (Eq. 11) from Psi_j and G_j, in place of the exact adjoint
+template <typename R>
+cudaError_t launch_grad_first_order(const SysView<R>& sys, const StateView<R>& sv, int j0, int wlen, int E,
+                                    const C_t<R>* states, const C_t<R>* Gbuf, int wmax, double dt, double* gpart,
+                                    cudaStream_t st);
 cudaError_t launch_finalize(int E, int M, int N, const double* u, const double* alpha, const double2* Oj,
                             const double* C5j, const double2* Ofin, const double* gpart, double* grad,
                             double* out, cudaStream_t st);

@@ -117,6 +117,25 @@ def test_both_adjoint_modes_differentiate_the_series_exactly(precision, tol, pn)
     assert rel(grad, g_t) <= tol
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
+@pytest.mark.parametrize("case", [dict(d=5, M=2, N=30, S=2, seed=121, nF=2, path=True, E=2),
+                                  dict(d=40, M=2, N=120, S=1, seed=122, nF=13),
+                                  dict(d=81, M=3, N=9, S=6, seed=123, nF=5, weights=True)],
+                         ids=lambda c: f"d{c['d']}S{c['S']}N{c['N']}")
+def test_first_order_gradient_matches_oracle(precision, tol, case):
+    """The paper's approximate gradient (Eq. 11) against the oracle's first-order form; it is
+    not the exact gradient (that differs at O(dt) relative)."""
+    if precision == "fp64" and case["d"] > 48:
+        pytest.skip("FP64 large-d path: covered by the FP32 case")
+    prob = sy.random_problem(**case, dt=0.2, u_scale=0.8)
+    cost, grad, terms, info = run(prob, precision, gradient="first_order")
+    c_ref, g_ref, t_ref = orc.cost_and_grad(prob, prob.u, exact=False)
+    assert abs(cost - c_ref) <= tol * abs(c_ref)
+    assert rel(grad, g_ref) <= tol, rel(grad, g_ref)
+    _, g_exact, _ = orc.cost_and_grad(prob, prob.u)
+    assert rel(grad, g_exact) > 10 * tol
+
+
 CASES32 = [
     dict(d=4, M=2, N=50, S=4, seed=201, nF=1),
     dict(d=13, M=3, N=37, S=1, seed=202, nF=2, path=True),
