@@ -113,8 +113,13 @@ template <typename E, int T, int MODE>   // MODE 0 plain, 1 pair, 2 hi-only (E =
 __global__ void __launch_bounds__(256)
 k_big_mm(int d, const E* __restrict__ A, const E* __restrict__ B, E* __restrict__ Cm, size_t mstride, int kind, int i) {
     constexpr int MT = T / 16;
-    __shared__ __align__(16) E As[T][KC + 1];
-    __shared__ __align__(16) E Bs[KC][T + 1];
+    // two buffers of (As[T][KC + 1], Bs[KC][T + 1]): the next K-chunk is copied (cp.async) while
+    // the current one is multiplied
+    extern __shared__ __align__(16) unsigned char smraw[];
+    typedef E ATile[T][KC + 1];
+    typedef E BTile[KC][T + 1];
+    ATile* Abuf = reinterpret_cast<ATile*>(smraw);
+    BTile* Bbuf = reinterpret_cast<BTile*>(smraw + 2 * sizeof(ATile));
     const int item = blockIdx.y;
     const int ntn = (d + T - 1) / T;
     const int tm = blockIdx.x / ntn, tn = blockIdx.x - tm * ntn;
@@ -131,18 +136,30 @@ k_big_mm(int d, const E* __restrict__ A, const E* __restrict__ B, E* __restrict_
             ar[x][y][0] = ar[x][y][1] = ai_[x][y][0] = ai_[x][y][1] = 0.f;
             acc[x][y] = ezero<E>();
         }
-    for (int k0 = 0; k0 < d; k0 += KC) {
+    auto issue = [&](int buf, int k0) {
         for (int idx = tid; idx < T * KC; idx += 256) {
             const int r = idx / KC, k = idx - r * KC;
             const int gr = r0 + r, gk = k0 + k;
-            As[r][k] = (gr < d && gk < d) ? Ai[(size_t)gr * d + gk] : ezero<E>();
+            if (gr < d && gk < d) cp_async_elem(&Abuf[buf][r][k], &Ai[(size_t)gr * d + gk]);
+            else Abuf[buf][r][k] = ezero<E>();
         }
         for (int idx = tid; idx < KC * T; idx += 256) {
             const int k = idx / T, c = idx - k * T;
             const int gk = k0 + k, gc = c0 + c;
-            Bs[k][c] = (gk < d && gc < d) ? Bi[(size_t)gk * d + gc] : ezero<E>();
+            if (gk < d && gc < d) cp_async_elem(&Bbuf[buf][k][c], &Bi[(size_t)gk * d + gc]);
+            else Bbuf[buf][k][c] = ezero<E>();
         }
+    };
+    const int nch = (d + KC - 1) / KC;
+    issue(0, 0);
+    cp_async_commit();
+    for (int ch = 0; ch < nch; ++ch) {
+        if (ch + 1 < nch) issue((ch + 1) & 1, (ch + 1) * KC);
+        cp_async_commit();
+        cp_async_wait<1>();   // chunk ch has landed
         __syncthreads();
+        const ATile& As = Abuf[ch & 1];
+        const BTile& Bs = Bbuf[ch & 1];
 #pragma unroll 4
         for (int k = 0; k < KC; ++k) {
             E a[MT], b[MT];
@@ -173,7 +190,7 @@ k_big_mm(int d, const E* __restrict__ A, const E* __restrict__ B, E* __restrict_
                     }
                 }
         }
-        __syncthreads();
+        __syncthreads();   // before this buffer is refilled
     }
     E* Ci = Cm + (size_t)item * mstride;
 #pragma unroll
@@ -300,10 +317,14 @@ __global__ void __launch_bounds__(256)
 k_big_mm_blk(int d, const C* __restrict__ A11, const C* __restrict__ A12, const C* __restrict__ B11,
              const C* __restrict__ B12, C* __restrict__ O11, C* __restrict__ O12, size_t mstride, int kind, int i) {
     constexpr int MT = T / 16;
-    __shared__ __align__(16) C A1s[T][KC + 1];
-    __shared__ __align__(16) C A2s[T][KC + 1];
-    __shared__ __align__(16) C B1s[KC][T + 1];
-    __shared__ __align__(16) C B2s[KC][T + 1];
+    // two buffers of (A1s, A2s [T][KC + 1], B1s, B2s [KC][T + 1]), filled by cp.async one K-chunk ahead
+    extern __shared__ __align__(16) unsigned char smraw[];
+    typedef C ATile[T][KC + 1];
+    typedef C BTile[KC][T + 1];
+    ATile* A1b = reinterpret_cast<ATile*>(smraw);
+    ATile* A2b = A1b + 2;
+    BTile* B1b = reinterpret_cast<BTile*>(smraw + 4 * sizeof(ATile));
+    BTile* B2b = B1b + 2;
     const int item = blockIdx.y;
     const int ntn = (d + T - 1) / T;
     const int tm = blockIdx.x / ntn, tn = blockIdx.x - tm * ntn;
@@ -315,22 +336,42 @@ k_big_mm_blk(int d, const C* __restrict__ A11, const C* __restrict__ A12, const 
     for (int x = 0; x < MT; ++x)
 #pragma unroll
         for (int y = 0; y < MT; ++y) acc1[x][y] = acc2[x][y] = czero<C>();
-    for (int k0 = 0; k0 < d; k0 += KC) {
+    auto issue = [&](int buf, int k0) {
         for (int idx = tid; idx < T * KC; idx += 256) {
             const int r = idx / KC, k = idx - r * KC;
             const int gr = r0 + r, gk = k0 + k;
-            const bool ok = gr < d && gk < d;
-            A1s[r][k] = ok ? A11[off + (size_t)gr * d + gk] : czero<C>();
-            A2s[r][k] = ok ? A12[off + (size_t)gr * d + gk] : czero<C>();
+            if (gr < d && gk < d) {
+                cp_async_elem(&A1b[buf][r][k], &A11[off + (size_t)gr * d + gk]);
+                cp_async_elem(&A2b[buf][r][k], &A12[off + (size_t)gr * d + gk]);
+            } else {
+                A1b[buf][r][k] = czero<C>();
+                A2b[buf][r][k] = czero<C>();
+            }
         }
         for (int idx = tid; idx < KC * T; idx += 256) {
             const int k = idx / T, c = idx - k * T;
             const int gk = k0 + k, gc = c0 + c;
-            const bool ok = gk < d && gc < d;
-            B1s[k][c] = ok ? B11[off + (size_t)gk * d + gc] : czero<C>();
-            B2s[k][c] = ok ? B12[off + (size_t)gk * d + gc] : czero<C>();
+            if (gk < d && gc < d) {
+                cp_async_elem(&B1b[buf][k][c], &B11[off + (size_t)gk * d + gc]);
+                cp_async_elem(&B2b[buf][k][c], &B12[off + (size_t)gk * d + gc]);
+            } else {
+                B1b[buf][k][c] = czero<C>();
+                B2b[buf][k][c] = czero<C>();
+            }
         }
+    };
+    const int nch = (d + KC - 1) / KC;
+    issue(0, 0);
+    cp_async_commit();
+    for (int ch = 0; ch < nch; ++ch) {
+        if (ch + 1 < nch) issue((ch + 1) & 1, (ch + 1) * KC);
+        cp_async_commit();
+        cp_async_wait<1>();   // chunk ch has landed
         __syncthreads();
+        const ATile& A1s = A1b[ch & 1];
+        const ATile& A2s = A2b[ch & 1];
+        const BTile& B1s = B1b[ch & 1];
+        const BTile& B2s = B2b[ch & 1];
 #pragma unroll 4
         for (int k = 0; k < KC; ++k) {
             C a1[MT], a2[MT], b1[MT], b2[MT];
@@ -353,7 +394,7 @@ k_big_mm_blk(int d, const C* __restrict__ A11, const C* __restrict__ A12, const 
                     cfma(acc2[x][y], a2[x], b1[y]);
                 }
         }
-        __syncthreads();
+        __syncthreads();   // before this buffer is refilled
     }
     using S = decltype(acc1[0][0].x);
     const S ri = (kind == 0) ? S(1) / S(i) : S(1);
@@ -396,13 +437,43 @@ k_big_grad(const DevParams* __restrict__ prm, SysView<R> sys, int j0, int wlen, 
 // ------------------------------------------------------------------------------------------
 static int big_tile(int d) { return d <= 96 ? 32 : 64; }
 
+template <typename E, int T> constexpr size_t mm_smem() { return 2 * sizeof(E) * ((size_t)T * (KC + 1) + (size_t)KC * (T + 1)); }
+template <typename E, int T> constexpr size_t blk_smem() { return 2 * mm_smem<E, T>(); }
+
+template <typename E, int T, int MODE>
+static cudaError_t mm_launch_t(int d, int items, const E* A, const E* B, E* Cm, size_t mstride, int kind, int i,
+                               cudaStream_t st) {
+    constexpr size_t smem = mm_smem<E, T>();
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_big_mm<E, T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int nt = ((d + T - 1) / T) * ((d + T - 1) / T);
+    k_big_mm<E, T, MODE><<<dim3(nt, items), 256, smem, st>>>(d, A, B, Cm, mstride, kind, i);
+    return cudaGetLastError();
+}
+
 template <typename E, int MODE>
 static cudaError_t mm_launch(int d, int items, const E* A, const E* B, E* Cm, size_t mstride, int kind, int i,
                              cudaStream_t st) {
-    const int T = big_tile(d);
+    if (big_tile(d) == 32) return mm_launch_t<E, 32, MODE>(d, items, A, B, Cm, mstride, kind, i, st);
+    return mm_launch_t<E, 64, MODE>(d, items, A, B, Cm, mstride, kind, i, st);
+}
+
+template <typename C, int T>
+static cudaError_t blk_launch_t(int d, int items, const C* A11, const C* A12, const C* B11, const C* B12, C* O11,
+                                C* O12, size_t ms, int kind, int i, cudaStream_t st) {
+    constexpr size_t smem = blk_smem<C, T>();
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_big_mm_blk<C, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
     const int nt = ((d + T - 1) / T) * ((d + T - 1) / T);
-    if (T == 32) k_big_mm<E, 32, MODE><<<dim3(nt, items), 256, 0, st>>>(d, A, B, Cm, mstride, kind, i);
-    else k_big_mm<E, 64, MODE><<<dim3(nt, items), 256, 0, st>>>(d, A, B, Cm, mstride, kind, i);
+    k_big_mm_blk<C, T><<<dim3(nt, items), 256, smem, st>>>(d, A11, A12, B11, B12, O11, O12, ms, kind, i);
     return cudaGetLastError();
 }
 
@@ -487,20 +558,16 @@ cudaError_t launch_big_adj(const BigArgs<R>& a, const SysView<R>& sys, const Sta
     count();
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
-    const int T = (sizeof(C) == 16) ? 32 : big_tile(d);
-    const int nt = ((d + T - 1) / T) * ((d + T - 1) / T);
+    const int T = (sizeof(C) == 16) ? 32 : big_tile(d);   // 16-byte elements: 32 x 32 tiles (SMEM, registers)
     C *z11 = Z11a, *z12 = Z12a, *o11 = Z11b, *o12 = Z12b;
     auto blk = [&](const C* A11, const C* A12, const C* B11, const C* B12, int kind, int i) {
-        if constexpr (sizeof(C) == 16) {   // 16-byte elements: 32 x 32 tiles keep the static SMEM < 48 KB
-            k_big_mm_blk<C, 32><<<dim3(nt, items), 256, 0, st>>>(d, A11, A12, B11, B12, o11, o12, ms, kind, i);
-        } else {
-            if (T == 32) k_big_mm_blk<C, 32><<<dim3(nt, items), 256, 0, st>>>(d, A11, A12, B11, B12, o11, o12, ms, kind, i);
-            else k_big_mm_blk<C, 64><<<dim3(nt, items), 256, 0, st>>>(d, A11, A12, B11, B12, o11, o12, ms, kind, i);
-        }
+        cudaError_t e2;
+        if (T == 32) e2 = blk_launch_t<C, 32>(d, items, A11, A12, B11, B12, o11, o12, ms, kind, i, st);
+        else e2 = blk_launch_t<C, 64>(d, items, A11, A12, B11, B12, o11, o12, ms, kind, i, st);
         count();
         std::swap(z11, o11);
         std::swap(z12, o12);
-        return cudaGetLastError();
+        return e2;
     };
     for (int i = p - 1; i >= 1; --i)
         if ((err = blk(XH, Ub, z11, z12, 0, i)) != cudaSuccess) return err;
