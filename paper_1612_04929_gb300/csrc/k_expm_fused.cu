@@ -18,7 +18,8 @@
 //               Sbar_m = Sbar_{m+1} S_m^dag + S_m^dag Sbar_{m+1}, per Horner step
 //               Xbar += Zbar_i Z_{i+1}^dag / i and Zbar_{i+1} = X^dag Zbar_i / i, starting from
 //               Ubar and ending with Xbar += Zbar_p / p: two products per step instead of three,
-//               and four matrices in shared memory instead of six.
+//               and five matrices in shared memory instead of six (the stored operand of the
+//               next product arrives by cp.async while the current one is multiplied).
 //
 // Thread layout: a G x G grid of threads (slice_tile); thread (ty, tx) owns the MT x MT outputs
 // (ty + G a, tx + G b).  Matrices sit in shared memory padded to D = G MT rows with a leading
@@ -352,7 +353,8 @@ k_expm_adj_rev(const DevParams* __restrict__ prm, SysView<R> sys, StateView<R> s
     C* XH = reinterpret_cast<C*>(smraw);
     C* ZA = XH + SZ;
     C* ZB = ZA + SZ;
-    C* SB = ZB + SZ;
+    C* SB = ZB + SZ;       // stored operand of the current product ...
+    C* SN = SB + SZ;       // ... and of the next one, arriving by cp.async meanwhile
     const int jl = blockIdx.x, e = blockIdx.y, j = j0 + jl;
     const int tid = threadIdx.x, tx = tid % G, ty = tid / G;
     const bool act = tid < G * G;   // the block is rounded up to whole warps
@@ -400,17 +402,29 @@ k_expm_adj_rev(const DevParams* __restrict__ prm, SysView<R> sys, StateView<R> s
     }
     __syncthreads();
     const C* zst = zs.Z + ((size_t)e * zs.wmax + jl) * zs.cap * zs.mstride;
-    auto load = [&](int r) {   // stored conjugate transpose of the right operand of product r
-        const C* src = zst + (size_t)r * zs.mstride;
-        for (int idx = tid; idx < d * d; idx += blockDim.x) {
-            const int a = idx / d, b = idx - a * d;
-            SB[a * LD + b] = src[idx];
+    // the stored conjugate transpose of the right operand of product r; the products run in
+    // reverse, r = p - 2 + n down to 0, and r - 1 is fetched while r is multiplied
+    auto issue = [&](int r) {
+        if (r >= 0) {
+            const C* src = zst + (size_t)r * zs.mstride;
+            for (int idx = tid; idx < d * d; idx += blockDim.x) {
+                const int a = idx / d, b = idx - a * d;
+                cp_async_elem(&SN[a * LD + b], &src[idx]);
+            }
         }
+        cp_async_commit();
     };
+    auto next = [&](int r) {   // operand r into SB, r - 1 on its way into SN
+        C* t = SB; SB = SN; SN = t;   // SN (now SB) received r; SB (now SN) is free
+        issue(r - 1);
+        cp_async_wait<1>();
+    };
+    issue(p - 2 + n);          // the first product's operand into SN
+    __syncthreads();
     C* zb = ZA;
     C* zo = ZB;
     for (int m = n - 1; m >= 0; --m) {          // squarings in reverse
-        load(p - 1 + m);
+        next(p - 1 + m);
         __syncthreads();
         if (act) {
             C acc[MT][MT];
@@ -425,7 +439,7 @@ k_expm_adj_rev(const DevParams* __restrict__ prm, SysView<R> sys, StateView<R> s
     C xb[MT][MT];                               // Xbar, accumulated over the Horner steps
     zero_acc<C, MT>(xb);
     for (int i = 1; i <= p - 1; ++i) {          // Horner steps in reverse
-        load(p - 1 - i);
+        next(p - 1 - i);
         __syncthreads();
         if (act) {
             const R ri = R(1) / R(i);
@@ -525,7 +539,7 @@ static cudaError_t launch_adj_mt(const DevParams* prm, const SysView<R>& sys, co
     err = cudaGetLastError();
     *launches = 1;
     if (err != cudaSuccess || !zs.Z) return err;
-    const size_t smem_r = fused_smem<R>(sys.d, 4);
+    const size_t smem_r = fused_smem<R>(sys.d, 5);
     err = cudaFuncSetAttribute(k_expm_adj_rev<R, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r);
     if (err != cudaSuccess) return err;
     k_expm_adj_rev<R, MT><<<dim3(wlen, E), slice_threads(G), smem_r, st>>>(prm, sys, sv, j0, states, Gbuf, wmax,
