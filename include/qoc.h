@@ -102,6 +102,12 @@ typedef struct qoc_options {
                              QOC_GRAD_FIRST_ORDER (1): the paper's approximate gradient (Eq. 11,
                              dU_j/du_kj ~ -i dt H_k U_j), O(M d^2 S) per slice instead of an adjoint
                              exponential; its error is O(dt ||[H_j, H_k]||) */
+    int fault_inject;     /* test of the failure path, 0 (default) off.  1: the tensor-core adjoint
+                             kernels (TF32_SPLIT, BF16_SPLIT, d > 68) withhold their first operand
+                             copy, so their bounded mbarrier wait (shortened to 4096 polls) runs
+                             out; later kernels of the evaluation skip their work, the evaluation
+                             reports QOC_ERR_TIMEOUT and the context and device stay usable.
+                             Nothing faults or hangs. */
 } qoc_options;
 
 enum { QOC_SWEEP_AUTO = 0, QOC_SWEEP_SERIAL = 1, QOC_SWEEP_SCAN = 2 };

@@ -66,6 +66,15 @@ __global__ void k_theta(const double* __restrict__ u, int M, int N, const double
     if (delta)
         for (int e = 0; e < E; ++e) dmax = fmax(dmax, fabs(delta[e]));
     const double theta = dt * (norms[0] + dmax * norms[M + 1] + best);
+    if (!isfinite(theta)) {   // a NaN or Inf control (device input): flag it, keep the work small
+        prm->m_split = 1;
+        prm->theta = theta;
+        prm->p = 1;
+        prm->n = 0;
+        prm->s = dt;
+        prm->err = kErrNonfinite;
+        return;
+    }
     int n = 0;
     while (ldexp(theta, -n) > theta_max && n < 1000) ++n;
     if (n_override >= 0) n = n_override;
@@ -276,10 +285,11 @@ struct Alpha5 { double a[5]; };
 __global__ void __launch_bounds__(1024)
 k_finalize(int E, int M, int N, const double* __restrict__ u, Alpha5 al, const double2* __restrict__ Oj,
            const double* __restrict__ C5j, const double2* __restrict__ Ofin, const double* __restrict__ gpart,
-           double* __restrict__ grad, double* __restrict__ out) {
+           double* __restrict__ grad, double* __restrict__ out, DevParams* __restrict__ prm) {
     __shared__ double red[32];
     const int tid = threadIdx.x;
     double c3 = 0, c4 = 0, c5 = 0, t67 = 0;
+    bool finite = true;   // outputs scanned for NaN / Inf (a flag, read by the host)
     for (int i = tid; i < M * N; i += blockDim.x) {
         const int k = i / N, j = i - k * N;
         const double x = u[i];
@@ -296,7 +306,9 @@ k_finalize(int E, int M, int N, const double* __restrict__ u, Alpha5 al, const d
         if (j < N - 1) gv -= 2.0 * (u[i + 1] - x);
         g += al.a[2] * gv;
         grad[i] = g;
+        finite = finite && isfinite(g);
     }
+    if (!finite) atomicOr(&prm->err, kErrNonfinite);
     for (int i = tid; i < E * N; i += blockDim.x) {
         c5 += C5j[i];
         const double2 o = Oj[i];
@@ -318,15 +330,16 @@ k_finalize(int E, int M, int N, const double* __restrict__ u, Alpha5 al, const d
         out[4] = c5;
         out[5] = c67;
         out[0] = al.a[0] * fid + al.a[1] * c3 + al.a[2] * c4 + al.a[3] * c5 + al.a[4] * c67;
+        if (!isfinite(out[0])) atomicOr(&prm->err, kErrNonfinite);
     }
 }
 
 cudaError_t launch_finalize(int E, int M, int N, const double* u, const double* alpha, const double2* Oj,
                             const double* C5j, const double2* Ofin, const double* gpart, double* grad, double* out,
-                            cudaStream_t st) {
+                            DevParams* prm, cudaStream_t st) {
     Alpha5 al;
     for (int i = 0; i < 5; ++i) al.a[i] = alpha[i];
-    k_finalize<<<1, 1024, 0, st>>>(E, M, N, u, al, Oj, C5j, Ofin, gpart, grad, out);
+    k_finalize<<<1, 1024, 0, st>>>(E, M, N, u, al, Oj, C5j, Ofin, gpart, grad, out, prm);
     return cudaGetLastError();
 }
 

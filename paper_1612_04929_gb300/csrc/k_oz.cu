@@ -44,6 +44,7 @@ constexpr int STAGE = NPART * (ATILE + BTILE);     // 160 KB
 constexpr int OZ_SMEM = STAGE + 1024;              // + alignment slack
 constexpr uint32_t TMEM_COLS = 512;                // two terms x 4 levels x (re, im) x 32 columns
 constexpr uint32_t WAIT_LIMIT = 1u << 24;
+constexpr uint32_t WAIT_LIMIT_TEST = 1u << 12;   // fault-injection runs
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
@@ -52,8 +53,8 @@ __device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
-    for (uint32_t it = 0; it < WAIT_LIMIT; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, uint32_t limit = WAIT_LIMIT) {
+    for (uint32_t it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
@@ -217,6 +218,13 @@ k_oz_step(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     __shared__ __align__(8) uint64_t full, empty, done;
     __shared__ uint32_t tmem_holder;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    __shared__ int skip, s_ok;
+    // once a wait has run out in this evaluation, later steps skip their work (the result is
+    // reported as QOC_ERR_TIMEOUT); thread 0 decides for the whole CTA
+    if (tid == 0) skip = (*(volatile int*)&prm->err & kErrTimeout) != 0;
+    __syncthreads();
+    if (skip) return;
+    const uint32_t limit = step.fault ? WAIT_LIMIT_TEST : WAIT_LIMIT;
     const int item = blockIdx.y, out = blockIdx.z;
     const OzOut oo = step.o[out];
     const int ntn = (d + BN - 1) / BN;
@@ -256,9 +264,9 @@ k_oz_step(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
             }
         };
         uint32_t started = 0;   // bit (term * 8 + level * 2 + part): accumulator written once
-        load(0);
+        if (!step.fault) load(0);   // fault injection: the first copy is withheld, its wait runs out
         for (int s = 0; s < nsteps && ok; ++s) {
-            ok = mbar_wait(&full, (uint32_t)(s & 1));
+            ok = mbar_wait(&full, (uint32_t)(s & 1), limit);
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int t = s / nk;
@@ -291,7 +299,7 @@ k_oz_step(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
             }
             mma_commit(&empty);
             if (s + 1 < nsteps) {   // refill the stage once its products have completed
-                ok = mbar_wait(&empty, (uint32_t)(s & 1));
+                ok = mbar_wait(&empty, (uint32_t)(s & 1), limit);
                 if (!ok) break;
                 load(s + 1);
             }
@@ -299,14 +307,17 @@ k_oz_step(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
         mma_commit(&done);
         if (!ok) {
             atomicOr(&prm->err, kErrTimeout);
-            if (loaded > 0) mbar_wait(&full, (uint32_t)((loaded - 1) & 1));   // let the last copy land (bounded)
+            if (loaded > 0) mbar_wait(&full, (uint32_t)((loaded - 1) & 1), limit);   // let the last copy land (bounded)
         }
     }
+    if (tid == 0) s_ok = ok ? 1 : 0;   // only the issuing thread knows whether its waits ran out
     __syncthreads();
-    const bool fin = mbar_wait(&done, 0);
+    const bool fin = mbar_wait(&done, 0, limit);
     if (!fin && tid == 0) atomicOr(&prm->err, kErrTimeout);
+    // the epilogue's TMEM loads are warp-collective: the decision is the same for every thread
+    const bool go = __syncthreads_and(fin && s_ok != 0) != 0;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (fin && ok) {
+    if (go) {
         const int r = r0 + warp * 32 + lane;
         const bool horner = step.kind == 0;
         const float ri = horner ? 1.0f / (float)step.i : 1.0f;
@@ -522,6 +533,7 @@ cudaError_t launch_oz_adj(const OzAdjArgs& a, cudaStream_t st, int* launches) {
             s.o[1].t[0] = {z11r(q), z12c(q)};
             s.o[1].t[1] = {z12r(q), z11c(q)};
         }
+        s.fault = a.fault;
         k_oz_step<<<dim3(ntiles, items, 2), 128, OZ_SMEM, st>>>(*mapA, *mapB, s, vals, exps, d, a.prm);
         count();
         cudaError_t e2 = cudaGetLastError();

@@ -40,6 +40,7 @@ constexpr int TC_SMEM = NST * STAGE + 1024;        // + alignment slack
 constexpr uint32_t TMEM_COLS = 512;                // two complex accumulators of 64 columns, each twice
 constexpr uint32_t CORR = 256;                     // column offset of the correction accumulators
 constexpr uint32_t WAIT_LIMIT = 1u << 24;
+constexpr uint32_t WAIT_LIMIT_TEST = 1u << 12;   // fault-injection runs
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -49,8 +50,8 @@ __device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
-    for (uint32_t it = 0; it < WAIT_LIMIT; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, uint32_t limit = WAIT_LIMIT) {
+    for (uint32_t it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
@@ -124,6 +125,13 @@ k_tc_step(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     __shared__ __align__(8) uint64_t full[NST], empty[NST], done;
     __shared__ uint32_t tmem_holder;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    __shared__ int skip, s_ok;
+    // once a wait has run out in this evaluation, later steps skip their work (the result is
+    // reported as QOC_ERR_TIMEOUT); thread 0 decides for the whole CTA
+    if (tid == 0) skip = (*(volatile int*)&prm->err & kErrTimeout) != 0;
+    __syncthreads();
+    if (skip) return;
+    const uint32_t limit = step.fault ? WAIT_LIMIT_TEST : WAIT_LIMIT;
     const int item = blockIdx.y;
     const int ntn = (d + BN - 1) / BN;
     const int r0 = (blockIdx.x / ntn) * BM, c0 = (blockIdx.x % ntn) * BN;
@@ -165,12 +173,13 @@ k_tc_step(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
             }
         };
         bool started[2] = {false, false};
-        for (int q = 0; q < NST && q < nsteps; ++q) load(q);
+        for (int q = 0; q < NST && q < nsteps; ++q)
+            if (!(step.fault && q == 0)) load(q);   // fault injection: the first copy is withheld
         // products kept of (x_h + x_m + x_l)(y_h + y_m + y_l): hh, hm, mh, hl, lh, mm
         const int pa[6] = {0, 0, 1, 0, 2, 1}, pb[6] = {0, 1, 0, 2, 0, 1};
         for (int s = 0; s < nsteps && ok; ++s) {
             const int b = s % NST;
-            ok = mbar_wait(&full[b], (uint32_t)((s / NST) & 1));
+            ok = mbar_wait(&full[b], (uint32_t)((s / NST) & 1), limit);
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int t = s / nk, acc = step.t[t].acc;
@@ -205,7 +214,7 @@ k_tc_step(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
             }
             mma_commit(&empty[b]);
             if (s + NST < nsteps) {   // refill this stage once its products have completed
-                ok = mbar_wait(&empty[b], (uint32_t)((s / NST) & 1));
+                ok = mbar_wait(&empty[b], (uint32_t)((s / NST) & 1), limit);
                 if (!ok) break;
                 load(s + NST);
             }
@@ -218,15 +227,18 @@ k_tc_step(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                 int last = -1;
                 for (int s2 = loaded - 1; s2 >= 0; --s2)
                     if (s2 % NST == b2) { last = s2; break; }
-                if (last >= 0) mbar_wait(&full[b2], (uint32_t)((last / NST) & 1));
+                if (last >= 0) mbar_wait(&full[b2], (uint32_t)((last / NST) & 1), limit);
             }
         }
     }
+    if (tid == 0) s_ok = ok ? 1 : 0;   // only the issuing thread knows whether its waits ran out
     __syncthreads();
-    const bool fin = mbar_wait(&done, 0);
+    const bool fin = mbar_wait(&done, 0, limit);
     if (!fin && tid == 0) atomicOr(&prm->err, kErrTimeout);
+    // the epilogue's TMEM loads are warp-collective: the decision is the same for every thread
+    const bool go = __syncthreads_and(fin && s_ok != 0) != 0;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (fin && ok) {
+    if (go) {
         const int r = r0 + warp * 32 + lane;
         const size_t psz = (size_t)d * ld;
         const bool horner = step.kind == 0;
@@ -434,6 +446,7 @@ cudaError_t launch_tc_adj(const TcAdjArgs& a, cudaStream_t st, int* launches) {
         s.out0_col = out.z11_col;
         s.out1_row = out.z12_row;
         s.out1_col = out.z12_col;
+        s.fault = a.fault;
         k_tc_step<<<dim3(ntiles, items), 128, TC_SMEM, st>>>(*mapA, *mapB, a.planes, s, d, ld, kTcMats, a.prm);
         count();
         return cudaGetLastError();

@@ -518,7 +518,8 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
         if constexpr (sizeof(R) == 4) {
             if (big && use_oz(c)) {
                 int n_l = 0;
-                OzAdjArgs oa{prm, sys, sv, d, E, j0, wlen, W, hp.p, hp.n, Sb(w), Gb(w), c->tc_planes.as<unsigned char>(),
+                OzAdjArgs oa{c->opt.fault_inject, prm, sys, sv, d, E, j0, wlen, W, hp.p, hp.n, Sb(w), Gb(w),
+                             c->tc_planes.as<unsigned char>(),
                              c->tc_maps, c->gpart.as<double>()};
                 cudaError_t e = launch_oz_adj(oa, st, &n_l);
                 extra += n_l - 1;
@@ -526,7 +527,8 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
             }
             if (big && use_tc(c)) {
                 int n_l = 0;
-                TcAdjArgs ta{prm, sys, sv, d, E, j0, wlen, W, hp.p, hp.n, Sb(w), Gb(w), c->tc_planes.as<float>(),
+                TcAdjArgs ta{c->opt.fault_inject, prm, sys, sv, d, E, j0, wlen, W, hp.p, hp.n, Sb(w), Gb(w),
+                             c->tc_planes.as<float>(),
                              c->tc_maps, c->gpart.as<double>()};
                 cudaError_t e = launch_tc_adj(ta, st, &n_l);
                 extra += n_l - 1;
@@ -723,7 +725,7 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
     wait(st, ev_join);
     B(st);
     L(launch_finalize(E, M, N, u, c->alpha, c->Oj.as<double2>(), c->C5j.as<double>(), c->Ofin.as<double2>(),
-                      c->gpart.as<double>(), grad, out, st),
+                      c->gpart.as<double>(), grad, out, prm, st),
       "finalize", st);
     c->launches = launches + extra;
 }
@@ -745,6 +747,7 @@ qoc_status device_error(qoc_ctx* c) {
     check_cuda(c, cudaStreamSynchronize(c->stream), "sync");
     c->prof.harvest();
     if (h.err & kErrTimeout) return set_err(c, QOC_ERR_TIMEOUT, "a bounded device wait ran out");
+    if (h.err & kErrNonfinite) return set_err(c, QOC_ERR_NONFINITE, "NaN or Inf in the controls or the results");
     if (h.err & kErrRange)
         return set_err(c, QOC_ERR_RANGE, "Taylor order above its maximum for theta = " + std::to_string(h.theta));
     return QOC_OK;
@@ -800,7 +803,8 @@ qoc_status qoc_create(qoc_ctx** out, const qoc_options* opt) {
     if (opt) o = *opt;
     if (o.precision < QOC_PREC_FP64 || o.precision > QOC_PREC_BF16_SPLIT) return QOC_ERR_ARG;
     if (!(o.tol >= 0.0) || !(o.theta_max >= 0.0) || o.ckpt_stride < 0 || o.wave_slices < 0 || o.sweep < 0 ||
-        o.sweep > QOC_SWEEP_SCAN || o.gradient < QOC_GRAD_EXACT || o.gradient > QOC_GRAD_FIRST_ORDER)
+        o.sweep > QOC_SWEEP_SCAN || o.gradient < QOC_GRAD_EXACT || o.gradient > QOC_GRAD_FIRST_ORDER ||
+        o.fault_inject < 0 || o.fault_inject > 1)
         return QOC_ERR_ARG;
     const bool f64 = o.precision == QOC_PREC_FP64;
     if (o.tol == 0.0) o.tol = f64 ? 1e-15 : 1e-8;

@@ -44,7 +44,7 @@ struct DevParams {
     int m_split;    // Horner steps i <= m_split need hi+lo arithmetic in the split exponential
 };
 
-enum : int { kErrRange = 1, kErrTimeout = 2 };
+enum : int { kErrRange = 1, kErrTimeout = 2, kErrNonfinite = 4 };
 
 // ------------------------------------------------------------------------------------------
 // cp.async (16-byte) helpers for the prefetch rings of the serial propagation kernels.

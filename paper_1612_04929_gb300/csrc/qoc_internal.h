@@ -157,6 +157,7 @@ struct TcStep {
     TcTerm t[3];
     int kind, i, nacc;            // kind 0: Horner step i, 1: squaring
     int out0_row, out0_col, out1_row, out1_col;
+    int fault;              // withhold the first operand copy (test of the bounded wait)
 };
 struct TcMats { int xh, ub, z11_row, z11_col, z12_row, z12_col; };
 struct TcMaps {                   // two CUtensorMap (128 bytes, 64-byte aligned) over the planes
@@ -164,6 +165,7 @@ struct TcMaps {                   // two CUtensorMap (128 bytes, 64-byte aligned
     alignas(64) unsigned char b[128];
 };
 struct TcAdjArgs {
+    int fault;              // qoc_options.fault_inject
     DevParams* prm;
     SysView<float> sys;
     StateView<float> sv;
@@ -192,8 +194,10 @@ struct OzOut {
 struct OzStep {
     int kind, i;            // 0: Horner step i, 1: squaring
     OzOut o[2];             // Z11', Z12'
+    int fault;              // withhold the first operand copy (test of the bounded wait)
 };
 struct OzAdjArgs {
+    int fault;              // qoc_options.fault_inject
     DevParams* prm;
     SysView<float> sys;
     StateView<float> sv;
@@ -290,6 +294,6 @@ cudaError_t launch_grad_first_order(const SysView<R>& sys, const StateView<R>& s
                                     cudaStream_t st);
 cudaError_t launch_finalize(int E, int M, int N, const double* u, const double* alpha, const double2* Oj,
                             const double* C5j, const double2* Ofin, const double* gpart, double* grad,
-                            double* out, cudaStream_t st);
+                            double* out, DevParams* prm, cudaStream_t st);
 
 }  // namespace qoc

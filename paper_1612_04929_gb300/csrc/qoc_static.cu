@@ -135,7 +135,7 @@ extern "C" qoc_status qoc_evaluate_static(int d, int M, int N, int S, double dt,
     int n_adj = 0;
     if (!ok(launch_expm_adj_fused<R>(prm, sys, sv, 0, N, 1, states, Gbuf, N, gpart, nostore, st, &n_adj)))
         return QOC_ERR_CUDA;
-    if (!ok(launch_finalize(1, M, N, u_dev, alpha, Oj, C5j, Ofin, gpart, grad_dev, out_dev, st)))
+    if (!ok(launch_finalize(1, M, N, u_dev, alpha, Oj, C5j, Ofin, gpart, grad_dev, out_dev, prm, st)))
         return QOC_ERR_CUDA;
     return QOC_OK;
 }

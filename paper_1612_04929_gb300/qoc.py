@@ -46,7 +46,7 @@ class qoc_options(ct.Structure):
                 ("ckpt_stride", ct.c_int), ("device", ct.c_int), ("stream", ct.c_void_p),
                 ("p_override", ct.c_int), ("n_override", ct.c_int), ("profile", ct.c_int),
                 ("wave_slices", ct.c_int), ("plain_fp32_exp", ct.c_int), ("sweep", ct.c_int),
-                ("gradient", ct.c_int)]
+                ("gradient", ct.c_int), ("fault_inject", ct.c_int)]
 
 
 PROFILE_SLOTS = 16
@@ -261,7 +261,8 @@ class Context:
     def __init__(self, precision: str = "fp64", *, tol: float = 0.0, theta_max: float = 0.0,
                  ckpt_stride: int = 0, wave_slices: int = 0, device: int = 0, stream: Optional[int] = None,
                  p_override: int = 0, n_override: int = -1, profile: bool = False,
-                 plain_fp32_exp: bool = False, sweep: str = "auto", gradient: str = "exact"):
+                 plain_fp32_exp: bool = False, sweep: str = "auto", gradient: str = "exact",
+                 fault_inject: int = 0):
         opt = qoc_default_options()
         opt.precision = PRECISIONS[precision]
         opt.tol = tol
@@ -278,6 +279,7 @@ class Context:
         opt.plain_fp32_exp = 1 if plain_fp32_exp else 0
         opt.sweep = SWEEPS[sweep]
         opt.gradient = GRADIENTS[gradient]
+        opt.fault_inject = fault_inject
         self.precision = precision
         self._ctx = qoc_create(opt)
         self.M = self.N = 0

@@ -146,3 +146,40 @@ def test_transmon4_bf16_full_size():
 
 def test_gue256_bf16_reduced_N():
     check(sy.gue256(N=40), "bf16")
+
+
+# ------------------------------------------------------------------ failure path (no fault, no hang)
+def test_nonfinite_device_controls_are_reported():
+    """Controls passed by device pointer cannot be checked on the host: the norm-bound kernel
+    flags a NaN and the next synchronising call reports QOC_ERR_NONFINITE."""
+    import torch
+    from paper_1612_04929_gb300 import Context, QocError
+    prob = sy.random_problem(d=6, M=2, N=8, S=2, seed=631, nF=1)
+    u = torch.tensor(prob.u, dtype=torch.float64, device="cuda")
+    u[1, 3] = float("nan")
+    g = torch.empty_like(u)
+    out = torch.empty(6, dtype=torch.float64, device="cuda")
+    with Context("fp32") as c:
+        c.set_problem(prob)
+        c.evaluate_device(u.data_ptr(), g.data_ptr(), out.data_ptr())
+        with pytest.raises(QocError) as e:
+            c.sync()
+        assert e.value.status == 4                          # QOC_ERR_NONFINITE
+        cost, grad, _ = c.evaluate(prob.u)                   # the context stays usable
+        assert np.isfinite(cost) and np.all(np.isfinite(grad))
+
+
+@pytest.mark.parametrize("precision", ["tf32", "bf16"])
+def test_bounded_wait_runs_out_and_reports_timeout(precision):
+    """fault_inject = 1 withholds the first operand copy of the tensor-core adjoint step: its
+    mbarrier wait (shortened for the test) runs out, the kernel frees its tensor memory and
+    returns, later steps skip their work, and the evaluation reports QOC_ERR_TIMEOUT.  A new
+    context on the same device then evaluates normally."""
+    from paper_1612_04929_gb300 import Context, QocError
+    prob = sy.random_problem(d=69, M=2, N=3, S=2, seed=632, nF=2, dt=0.15)
+    with Context(precision, fault_inject=1) as c:
+        c.set_problem(prob)
+        with pytest.raises(QocError) as e:
+            c.evaluate(prob.u)
+        assert e.value.status == 8                          # QOC_ERR_TIMEOUT
+    check(prob, precision, tol=1e-5)
