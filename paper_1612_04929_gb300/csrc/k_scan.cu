@@ -148,6 +148,81 @@ k_seg_mm(SegProdArgs<R> a, int level, const EI* __restrict__ src, size_t src_ite
         }
 }
 
+// The same level for d <= 68: one CTA per product, both factors in shared memory (padded to
+// D = G MT with leading dimension D + 1), thread (ty, tx) of a G x G grid owning the MT x MT
+// outputs (ty + G a, tx + G b) as in the per-slice kernels.  Level 1 keeps its plain factors
+// (exact products, TwoSum accumulation); later levels multiply carried pairs.
+__device__ __forceinline__ void kmac_any(float4& acc, const float4 a, const float4 b) { kmac2(acc, a, b); }
+__device__ __forceinline__ void kmac_any(float4& acc, const float2 a, const float2 b) {
+    mac_pair(acc.x, acc.z, a.x, 0.f, b.x, 0.f);
+    mac_pair(acc.x, acc.z, -a.y, 0.f, b.y, 0.f);
+    mac_pair(acc.y, acc.w, a.x, 0.f, b.y, 0.f);
+    mac_pair(acc.y, acc.w, a.y, 0.f, b.x, 0.f);
+}
+__device__ __forceinline__ void kmac_any(double2& acc, const double2 a, const double2 b) { cfma(acc, a, b); }
+
+template <typename R, typename EI, int MT>
+__global__ void __launch_bounds__(512)
+k_seg_mm_small(SegProdArgs<R> a, int level, const EI* __restrict__ src, size_t src_item, size_t src_seg, size_t src_e,
+               K_t<R>* __restrict__ dst, int cap, int G) {
+    using K = K_t<R>;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int d = a.d, D = G * MT, LD = D + 1;
+    EI* As = reinterpret_cast<EI*>(smraw);
+    EI* Bs = As + (size_t)D * LD;
+    const int q = blockIdx.x;
+    const int e = q / (a.nzmax * cap);
+    const int z = (q / cap) % a.nzmax;
+    const int i = q % cap;
+    const int a0 = z * a.seg;
+    if (a0 >= a.wlen) return;
+    const int len = min(a.wlen, a0 + a.seg) - a0;
+    const int n_prev = (len + (1 << (level - 1)) - 1) >> (level - 1);
+    const int n_cur = (len + (1 << level) - 1) >> level;
+    if (i >= n_cur) return;
+    const EI* base = src + e * src_e + z * src_seg;
+    const EI* Bm = base + (size_t)(2 * i) * src_item;          // earlier factor (right)
+    const EI* Am = base + (size_t)(2 * i + 1) * src_item;      // later factor (left)
+    K* out = dst + ((size_t)(e * a.nzmax + z) * cap + i) * a.mstride;
+    const int tid = threadIdx.x;
+    if (2 * i + 1 >= n_prev) {   // odd tail: carried up unchanged
+        for (int idx = tid; idx < d * d; idx += blockDim.x) out[idx] = widen(Bm[idx]);
+        return;
+    }
+    for (int idx = tid; idx < d * d; idx += blockDim.x) {
+        const int r = idx / d, c = idx - r * d;
+        As[r * LD + c] = Am[idx];
+        Bs[r * LD + c] = Bm[idx];
+    }
+    __syncthreads();
+    if (tid >= G * G) return;   // the block is rounded up to whole warps; no barrier follows
+    const int tx = tid % G, ty = tid / G;
+    K acc[MT][MT];
+#pragma unroll
+    for (int x = 0; x < MT; ++x)
+#pragma unroll
+        for (int y = 0; y < MT; ++y) acc[x][y] = kz<K>();
+#pragma unroll 2
+    for (int k = 0; k < d; ++k) {
+        EI av[MT], bv[MT];
+#pragma unroll
+        for (int x = 0; x < MT; ++x) av[x] = As[(ty + G * x) * LD + k];
+#pragma unroll
+        for (int y = 0; y < MT; ++y) bv[y] = Bs[k * LD + tx + G * y];
+#pragma unroll
+        for (int x = 0; x < MT; ++x)
+#pragma unroll
+            for (int y = 0; y < MT; ++y) kmac_any(acc[x][y], av[x], bv[y]);
+    }
+#pragma unroll
+    for (int x = 0; x < MT; ++x)
+#pragma unroll
+        for (int y = 0; y < MT; ++y) {
+            const int r = ty + G * x, c = tx + G * y;
+            if (r < d && c < d) out[(size_t)r * d + c] = knorm2(acc[x][y]);
+        }
+}
+
 // P_z and P_z^dag (carried) from item 0 of the last level (or from U_a when seg = 1)
 template <typename R, typename EI>
 __global__ void k_seg_store(SegProdArgs<R> a, const EI* __restrict__ src, size_t src_seg, size_t src_e) {
@@ -168,11 +243,36 @@ __global__ void k_seg_store(SegProdArgs<R> a, const EI* __restrict__ src, size_t
     }
 }
 
+template <typename R, typename EI, int MT>
+cudaError_t small_level(const SegProdArgs<R>& a, int level, const EI* src, size_t s_item, size_t s_seg, size_t s_e,
+                        K_t<R>* dst, int cap, int G, cudaStream_t st) {
+    const int D = G * MT;
+    const size_t smem = 2 * (size_t)D * (D + 1) * sizeof(EI);
+    cudaError_t err =
+        cudaFuncSetAttribute(k_seg_mm_small<R, EI, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    k_seg_mm_small<R, EI, MT><<<a.E * a.nzmax * cap, slice_threads(G), smem, st>>>(a, level, src, s_item, s_seg, s_e,
+                                                                                  dst, cap, G);
+    return cudaGetLastError();
+}
+
+template <typename R, typename EI>
+cudaError_t small_level_mt(const SegProdArgs<R>& a, int level, const EI* src, size_t s_item, size_t s_seg, size_t s_e,
+                           K_t<R>* dst, int cap, cudaStream_t st) {
+    const SliceTile tl = slice_tile(a.d);
+    switch (tl.MT) {
+        case 1: return small_level<R, EI, 1>(a, level, src, s_item, s_seg, s_e, dst, cap, tl.G, st);
+        case 2: return small_level<R, EI, 2>(a, level, src, s_item, s_seg, s_e, dst, cap, tl.G, st);
+        case 3: return small_level<R, EI, 3>(a, level, src, s_item, s_seg, s_e, dst, cap, tl.G, st);
+        default: return small_level<R, EI, 4>(a, level, src, s_item, s_seg, s_e, dst, cap, tl.G, st);
+    }
+}
+
 template <typename R, int T>
 cudaError_t seg_levels(const SegProdArgs<R>& a, cudaStream_t st, int* launches) {
     using C = C_t<R>;
     using K = K_t<R>;
-    const int ntile = (a.d + T - 1) / T;
+    const int ntile = T > 0 ? (a.d + T - 1) / T : 1;
     const int nz = (a.wlen + a.seg - 1) / a.seg;
     int levels = 0;
     while ((1 << levels) < a.seg) ++levels;
@@ -182,12 +282,24 @@ cudaError_t seg_levels(const SegProdArgs<R>& a, cudaStream_t st, int* launches) 
         const int cap = (a.seg + (1 << l) - 1) >> l;
         K* dst = (l & 1) ? a.lv0 : a.lv1;
         const dim3 grid(ntile * ntile, a.E * a.nzmax * cap);
-        if (l == 1) {
-            k_seg_mm<R, C, T><<<grid, 256, 0, st>>>(a, 1, a.U, (size_t)a.ustride, (size_t)a.seg * a.ustride,
+        const bool small = T == 0;   // whole products per CTA (d <= 68)
+        if (small) {
+            cudaError_t e2;
+            if (l == 1)
+                e2 = small_level_mt<R, C>(a, 1, a.U, (size_t)a.ustride, (size_t)a.seg * a.ustride,
+                                          (size_t)a.wmax * a.ustride, dst, cap, st);
+            else {
+                const int pcap = (a.seg + (1 << (l - 1)) - 1) >> (l - 1);
+                e2 = small_level_mt<R, K>(a, l, last, a.mstride, (size_t)pcap * a.mstride,
+                                          (size_t)a.nzmax * pcap * a.mstride, dst, cap, st);
+            }
+            if (e2 != cudaSuccess) return e2;
+        } else if (l == 1) {
+            k_seg_mm<R, C, (T > 0 ? T : 16)><<<grid, 256, 0, st>>>(a, 1, a.U, (size_t)a.ustride, (size_t)a.seg * a.ustride,
                                                   (size_t)a.wmax * a.ustride, dst, cap);
         } else {
             const int pcap = (a.seg + (1 << (l - 1)) - 1) >> (l - 1);
-            k_seg_mm<R, K, T><<<grid, 256, 0, st>>>(a, l, last, a.mstride, (size_t)pcap * a.mstride,
+            k_seg_mm<R, K, (T > 0 ? T : 16)><<<grid, 256, 0, st>>>(a, l, last, a.mstride, (size_t)pcap * a.mstride,
                                                   (size_t)a.nzmax * pcap * a.mstride, dst, cap);
         }
         cudaError_t err = cudaGetLastError();
@@ -215,6 +327,7 @@ template <typename R>
 cudaError_t launch_seg_products(const SegProdArgs<R>& a, cudaStream_t st, int* launches) {
     *launches = 0;
     if (a.wlen <= 0 || a.seg <= 0 || a.E <= 0 || (a.wlen + a.seg - 1) / a.seg > a.nzmax) return cudaErrorInvalidValue;
+    if (a.d <= 68 && slice_tile(a.d).MT > 0) return seg_levels<R, 0>(a, st, launches);
     if (a.d <= 48) return seg_levels<R, 16>(a, st, launches);
     if (a.d <= 128) return seg_levels<R, 32>(a, st, launches);
     return seg_levels<R, 64>(a, st, launches);
