@@ -578,6 +578,44 @@ cudaError_t launch_expm_adj_fused(const DevParams* prm, const SysView<R>& sys, c
     }
 }
 
+// resident CTAs per SM of the forward and adjoint kernels at dimension d (wave sizing)
+template <typename R>
+int fused_ctas_per_sm(int d, bool adjoint) {
+    const SliceTile tl = slice_tile(d);
+    if (tl.MT <= 0) return 1;
+    int n = 0;
+    const int thr = slice_threads(tl.G);
+    cudaError_t e;
+    if (!adjoint) {
+        const size_t smem = fused_smem<R>(d, 3);
+        switch (tl.MT) {
+            case 1: cudaFuncSetAttribute(k_expm_fwd<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_expm_fwd<R, 1>, thr, smem); break;
+            case 2: cudaFuncSetAttribute(k_expm_fwd<R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_expm_fwd<R, 2>, thr, smem); break;
+            case 3: cudaFuncSetAttribute(k_expm_fwd<R, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_expm_fwd<R, 3>, thr, smem); break;
+            default: cudaFuncSetAttribute(k_expm_fwd<R, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_expm_fwd<R, 4>, thr, smem); break;
+        }
+    } else {
+        const size_t smem = fused_smem<R>(d, 5);
+        switch (tl.MT) {
+            case 1: cudaFuncSetAttribute(k_expm_adj_rev<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_expm_adj_rev<R, 1>, thr, smem); break;
+            case 2: cudaFuncSetAttribute(k_expm_adj_rev<R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_expm_adj_rev<R, 2>, thr, smem); break;
+            case 3: cudaFuncSetAttribute(k_expm_adj_rev<R, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_expm_adj_rev<R, 3>, thr, smem); break;
+            default: cudaFuncSetAttribute(k_expm_adj_rev<R, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_expm_adj_rev<R, 4>, thr, smem); break;
+        }
+    }
+    return (e == cudaSuccess && n > 0) ? n : 1;
+}
+
+template int fused_ctas_per_sm<float>(int, bool);
+template int fused_ctas_per_sm<double>(int, bool);
 template size_t fused_adj_smem<float>(int);
 template size_t fused_adj_smem<double>(int);
 template int fused_max_d<float>();

@@ -282,6 +282,26 @@ static cudaError_t launch_split_mt(const DevParams* prm, const SysView<float>& s
     return cudaGetLastError();
 }
 
+int split_ctas_per_sm(int d) {
+    const SliceTile tl = slice_tile(d);
+    if (tl.MT <= 0) return 1;
+    const size_t smem = split_smem(d);
+    const int thr = slice_threads(tl.G);
+    int n = 0;
+    cudaError_t e;
+    switch (tl.MT) {
+        case 1: cudaFuncSetAttribute(k_expm_fwd_split<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_expm_fwd_split<1>, thr, smem); break;
+        case 2: cudaFuncSetAttribute(k_expm_fwd_split<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_expm_fwd_split<2>, thr, smem); break;
+        case 3: cudaFuncSetAttribute(k_expm_fwd_split<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_expm_fwd_split<3>, thr, smem); break;
+        default: cudaFuncSetAttribute(k_expm_fwd_split<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_expm_fwd_split<4>, thr, smem); break;
+    }
+    return (e == cudaSuccess && n > 0) ? n : 1;
+}
+
 int split_max_d() {
     for (int d = kMaxD; d >= 1; --d)
         if (slice_tile(d).MT > 0 && split_smem(d) <= kMaxDynSmem) return d;

@@ -274,6 +274,28 @@ void plan_impl(qoc_ctx* c) {
         const long long w_mem = std::max<long long>(seg, (long long)(budget / std::max<size_t>(per, 1)) / seg * seg);
         const long long w_half = (((long long)N + 1) / 2 + seg - 1) / seg * seg;
         W = (int)std::min<long long>(w_half, w_mem);
+        if (c->path_kind == 0 && W == w_half && 2 * (long long)seg < N) {
+            // Per-slice kernels run in whole rounds of resident CTAs: among the two-wave sizes
+            // that fit, take the one with the fewest rounds of the forward exponential (weight 2)
+            // and of the adjoint (weight 1) over both waves.
+            int sms1 = 0;
+            cudaDeviceGetAttribute(&sms1, cudaDevAttrMultiProcessorCount, c->opt.device);
+            const long slots_f = (long)std::max(sms1, 1) *
+                                 (split_exp<R>(c) ? split_ctas_per_sm(d) : fused_ctas_per_sm<R>(d, false));
+            const long slots_a = (long)std::max(sms1, 1) * fused_ctas_per_sm<R>(d, true);
+            const bool adj = c->opt.gradient == QOC_GRAD_EXACT;
+            auto rounds = [](long units, long slots) { return (units + slots - 1) / slots; };
+            long best = -1;
+            for (long long w = w_half; w < N && w <= w_mem; w += seg) {
+                const long len0 = (long)w * E, len1 = (long)(N - w) * E;
+                const long cost = 2 * (rounds(len0, slots_f) + rounds(len1, slots_f)) +
+                                  (adj ? rounds(len0, slots_a) + rounds(len1, slots_a) : 0);
+                if (best < 0 || cost < best) {
+                    best = cost;
+                    W = (int)w;
+                }
+            }
+        }
     }
     W = std::max(seg, std::min(W, ((N + seg - 1) / seg) * seg));
     c->seg = seg;

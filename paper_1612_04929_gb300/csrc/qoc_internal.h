@@ -101,6 +101,9 @@ struct ZStore {
 constexpr int kZCap = 24;
 
 template <typename R> int fused_max_d();
+// resident CTAs per SM of the per-slice forward (adjoint = false) or reverse-mode adjoint kernel
+template <typename R> int fused_ctas_per_sm(int d, bool adjoint);
+int split_ctas_per_sm(int d);
 template <typename R> size_t fused_adj_smem(int d);   // dynamic SMEM of the per-slice adjoint kernel
 template <typename R>
 cudaError_t launch_expm_fwd_fused(const DevParams* prm, const SysView<R>& sys, int j0, int wlen, int E,
