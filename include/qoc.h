@@ -102,6 +102,10 @@ typedef struct qoc_options {
                              QOC_GRAD_FIRST_ORDER (1): the paper's approximate gradient (Eq. 11,
                              dU_j/du_kj ~ -i dt H_k U_j), O(M d^2 S) per slice instead of an adjoint
                              exponential; its error is O(dt ||[H_j, H_k]||) */
+    int adjoint;          /* QOC_ADJ_AUTO (0): the exact adjoint runs in reverse mode over the stored
+                             operands of the forward products (two products per step) when the store
+                             fits, else by the block recursion; QOC_ADJ_RECOMPUTE (1): always the
+                             block recursion (three products per step, nothing stored) */
     int fault_inject;     /* test of the failure path, 0 (default) off.  1: the tensor-core adjoint
                              kernels (TF32_SPLIT, BF16_SPLIT, d > 68) withhold their first operand
                              copy, so their bounded mbarrier wait (shortened to 4096 polls) runs
@@ -112,6 +116,7 @@ typedef struct qoc_options {
 
 enum { QOC_SWEEP_AUTO = 0, QOC_SWEEP_SERIAL = 1, QOC_SWEEP_SCAN = 2 };
 enum { QOC_GRAD_EXACT = 0, QOC_GRAD_FIRST_ORDER = 1 };
+enum { QOC_ADJ_AUTO = 0, QOC_ADJ_RECOMPUTE = 1 };
 
 /* Information about the last evaluation (reading it synchronises the context stream). */
 typedef struct qoc_info {

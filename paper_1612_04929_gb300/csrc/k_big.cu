@@ -11,6 +11,7 @@
 //     truncated series), FP32 (FP32 form) or FP64 (FP64 form);
 //   * dC/du_{k,j} = Re tr(Xbar^dag (-i s H_k)) reduced in FP64.
 // Matrices of item b sit at base + b * mstride, row-major d x d.
+#include <type_traits>
 #include <utility>
 
 #include "qoc_device.cuh"
@@ -432,6 +433,153 @@ k_big_grad(const DevParams* __restrict__ prm, SysView<R> sys, int j0, int wlen, 
     if (threadIdx.x == 0) gpart[((size_t)e * sys.M + k) * sys.N + j] = prm->s * v;
 }
 
+// the conjugate transpose of Z (the right operand of forward product r), rounded to the compute
+// precision, into the operand store: zst + (item * cap + r) * mstride
+template <typename E, typename C>
+__global__ void k_big_store_ct(int d, const E* __restrict__ Z, size_t mstride, C* __restrict__ zst, int cap, int r) {
+    const int item = blockIdx.y;
+    const size_t dd = (size_t)d * d;
+    const E* Zi = Z + (size_t)item * mstride;
+    C* dst = zst + ((size_t)item * cap + r) * mstride;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < dd; idx += (size_t)gridDim.x * blockDim.x) {
+        const int a = (int)(idx / d), b = (int)(idx - (size_t)a * d);
+        C v = to_c<E, C>(Zi[(size_t)b * d + a]);
+        v.y = -v.y;
+        dst[idx] = v;
+    }
+}
+
+// Reverse mode over the stored products (two products per tile, operands at their own item strides):
+//   mode 0 (Horner step i): O1 = A1 B1 / i,  O2 += A2 B2 / i   (Zbar' = X^dag Zbar / i, Xbar += Zbar Z^dag / i)
+//   mode 1 (squaring):      O1 = A1 B1 + A2 B2                (Sbar' = Sbar S^dag + S^dag Sbar)
+template <typename C>
+struct RevOps {
+    const C* p[4];          // A1, B1, A2, B2
+    size_t s[4];            // item strides
+};
+template <typename C, int T>
+__global__ void __launch_bounds__(256)
+k_big_rev(int d, RevOps<C> ops, C* __restrict__ O1, C* __restrict__ O2, size_t mstride, int mode, int i) {
+    constexpr int MT = T / 16;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    typedef C ATile[T][KC + 1];
+    typedef C BTile[KC][T + 1];
+    ATile* A1b = reinterpret_cast<ATile*>(smraw);
+    ATile* A2b = A1b + 2;
+    BTile* B1b = reinterpret_cast<BTile*>(smraw + 4 * sizeof(ATile));
+    BTile* B2b = B1b + 2;
+    const int item = blockIdx.y;
+    const int ntn = (d + T - 1) / T;
+    const int tm = blockIdx.x / ntn, tn = blockIdx.x - tm * ntn;
+    const int r0 = tm * T, c0 = tn * T;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const C* A1 = ops.p[0] + (size_t)item * ops.s[0];
+    const C* B1 = ops.p[1] + (size_t)item * ops.s[1];
+    const C* A2 = ops.p[2] + (size_t)item * ops.s[2];
+    const C* B2 = ops.p[3] + (size_t)item * ops.s[3];
+    C acc1[MT][MT], acc2[MT][MT];
+#pragma unroll
+    for (int x = 0; x < MT; ++x)
+#pragma unroll
+        for (int y = 0; y < MT; ++y) acc1[x][y] = acc2[x][y] = czero<C>();
+    auto issue = [&](int buf, int k0) {
+        for (int idx = tid; idx < T * KC; idx += 256) {
+            const int r = idx / KC, k = idx - r * KC;
+            const int gr = r0 + r, gk = k0 + k;
+            if (gr < d && gk < d) {
+                cp_async_elem(&A1b[buf][r][k], &A1[(size_t)gr * d + gk]);
+                cp_async_elem(&A2b[buf][r][k], &A2[(size_t)gr * d + gk]);
+            } else {
+                A1b[buf][r][k] = czero<C>();
+                A2b[buf][r][k] = czero<C>();
+            }
+        }
+        for (int idx = tid; idx < KC * T; idx += 256) {
+            const int k = idx / T, c = idx - k * T;
+            const int gk = k0 + k, gc = c0 + c;
+            if (gk < d && gc < d) {
+                cp_async_elem(&B1b[buf][k][c], &B1[(size_t)gk * d + gc]);
+                cp_async_elem(&B2b[buf][k][c], &B2[(size_t)gk * d + gc]);
+            } else {
+                B1b[buf][k][c] = czero<C>();
+                B2b[buf][k][c] = czero<C>();
+            }
+        }
+    };
+    const int nch = (d + KC - 1) / KC;
+    issue(0, 0);
+    cp_async_commit();
+    for (int ch = 0; ch < nch; ++ch) {
+        if (ch + 1 < nch) issue((ch + 1) & 1, (ch + 1) * KC);
+        cp_async_commit();
+        cp_async_wait<1>();   // chunk ch has landed
+        __syncthreads();
+        const ATile& A1s = A1b[ch & 1];
+        const ATile& A2s = A2b[ch & 1];
+        const BTile& B1s = B1b[ch & 1];
+        const BTile& B2s = B2b[ch & 1];
+#pragma unroll 4
+        for (int k = 0; k < KC; ++k) {
+            C a1[MT], a2[MT], b1[MT], b2[MT];
+#pragma unroll
+            for (int x = 0; x < MT; ++x) {
+                a1[x] = A1s[ty + 16 * x][k];
+                a2[x] = A2s[ty + 16 * x][k];
+            }
+#pragma unroll
+            for (int y = 0; y < MT; ++y) {
+                b1[y] = B1s[k][tx + 16 * y];
+                b2[y] = B2s[k][tx + 16 * y];
+            }
+#pragma unroll
+            for (int x = 0; x < MT; ++x)
+#pragma unroll
+                for (int y = 0; y < MT; ++y) {
+                    cfma(acc1[x][y], a1[x], b1[y]);
+                    if (mode == 0) cfma(acc2[x][y], a2[x], b2[y]);
+                    else cfma(acc1[x][y], a2[x], b2[y]);
+                }
+        }
+        __syncthreads();   // before this buffer is refilled
+    }
+    using S = decltype(acc1[0][0].x);
+    const S ri = (mode == 0) ? S(1) / S(i) : S(1);
+    const size_t off = (size_t)item * mstride;
+#pragma unroll
+    for (int x = 0; x < MT; ++x)
+#pragma unroll
+        for (int y = 0; y < MT; ++y) {
+            const int r = r0 + ty + 16 * x, c = c0 + tx + 16 * y;
+            if (r >= d || c >= d) continue;
+            C v1 = acc1[x][y];
+            v1.x *= ri;
+            v1.y *= ri;
+            O1[off + (size_t)r * d + c] = v1;
+            if (mode == 0) {
+                C v2 = O2[off + (size_t)r * d + c];
+                v2.x += acc2[x][y].x * ri;
+                v2.y += acc2[x][y].y * ri;
+                O2[off + (size_t)r * d + c] = v2;
+            }
+        }
+}
+
+// Xbar += Zbar / p (the last Horner factor Z_p = I + X / p)
+template <typename C>
+__global__ void k_big_axpy(int d, const C* __restrict__ Z, C* __restrict__ X, size_t mstride, int p) {
+    const int item = blockIdx.y;
+    const size_t dd = (size_t)d * d, off = (size_t)item * mstride;
+    using S = decltype(Z[0].x);
+    const S rp = S(1) / S(p);
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < dd; idx += (size_t)gridDim.x * blockDim.x) {
+        const C z = Z[off + idx];
+        C x = X[off + idx];
+        x.x += z.x * rp;
+        x.y += z.y * rp;
+        X[off + idx] = x;
+    }
+}
+
 // ------------------------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------------------------
@@ -483,13 +631,22 @@ static int ew_blocks(size_t dd) {
 }
 
 template <typename R>
-cudaError_t launch_big_expm(const BigArgs<R>& a, int p, int n, int m_split, bool split, cudaStream_t st, int* launches) {
+cudaError_t launch_big_expm(const BigArgs<R>& a, int p, int n, int m_split, bool split, cudaStream_t st, int* launches,
+                            C_t<R>* zst) {
     const int d = a.d, items = a.wlen * a.E;
     const size_t dd = (size_t)d * d;
     const int eb = ew_blocks(dd);
     cudaError_t err;
     auto count = [&]() { if (launches) ++*launches; };
-    if (sizeof(R) == 4 && split) {
+    const int cap = p - 1 + n;
+    auto store = [&](const auto* Z, int r) -> cudaError_t {   // right operand of product r, for the adjoint
+        if (!zst) return cudaSuccess;
+        using E = std::remove_cv_t<std::remove_pointer_t<decltype(Z)>>;
+        k_big_store_ct<E, C_t<R>><<<dim3(eb, items), 256, 0, st>>>(d, Z, a.mstride, zst, cap, r);
+        count();
+        return cudaGetLastError();
+    };
+    if constexpr (sizeof(R) == 4) if (split) {
         float4* X = reinterpret_cast<float4*>(a.scratch);
         float4* Za = X + (size_t)items * a.mstride;
         float4* Zb = Za + (size_t)items * a.mstride;
@@ -498,6 +655,7 @@ cudaError_t launch_big_expm(const BigArgs<R>& a, int p, int n, int m_split, bool
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
         float4 *zin = Za, *zout = Zb;
         for (int i = p - 1; i >= 1; --i) {
+            if ((err = store(zin, p - 1 - i)) != cudaSuccess) return err;
             err = (i > m_split) ? mm_launch<float4, 2>(d, items, X, zin, zout, a.mstride, 0, i, st)
                                 : mm_launch<float4, 1>(d, items, X, zin, zout, a.mstride, 0, i, st);
             count();
@@ -505,6 +663,7 @@ cudaError_t launch_big_expm(const BigArgs<R>& a, int p, int n, int m_split, bool
             std::swap(zin, zout);
         }
         for (int m = 0; m < n; ++m) {
+            if ((err = store(zin, p - 1 + m)) != cudaSuccess) return err;
             if ((err = mm_launch<float4, 1>(d, items, zin, zin, zout, a.mstride, 1, 0, st)) != cudaSuccess) return err;
             count();
             std::swap(zin, zout);
@@ -524,11 +683,13 @@ cudaError_t launch_big_expm(const BigArgs<R>& a, int p, int n, int m_split, bool
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     C *zin = Za, *zout = Zb;
     for (int i = p - 1; i >= 1; --i) {
+        if ((err = store(zin, p - 1 - i)) != cudaSuccess) return err;
         if ((err = mm_launch<C, 0>(d, items, X, zin, zout, a.mstride, 0, i, st)) != cudaSuccess) return err;
         count();
         std::swap(zin, zout);
     }
     for (int m = 0; m < n; ++m) {
+        if ((err = store(zin, p - 1 + m)) != cudaSuccess) return err;
         if ((err = mm_launch<C, 0>(d, items, zin, zin, zout, a.mstride, 1, 0, st)) != cudaSuccess) return err;
         count();
         std::swap(zin, zout);
@@ -580,8 +741,76 @@ cudaError_t launch_big_adj(const BigArgs<R>& a, const SysView<R>& sys, const Sta
     return cudaGetLastError();
 }
 
-template cudaError_t launch_big_expm<float>(const BigArgs<float>&, int, int, int, bool, cudaStream_t, int*);
-template cudaError_t launch_big_expm<double>(const BigArgs<double>&, int, int, int, bool, cudaStream_t, int*);
+template <typename C, int T>
+static cudaError_t rev_launch_t(int d, int items, const RevOps<C>& ops, C* O1, C* O2, size_t ms, int mode, int i,
+                                cudaStream_t st) {
+    constexpr size_t smem = blk_smem<C, T>();
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_big_rev<C, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int nt = ((d + T - 1) / T) * ((d + T - 1) / T);
+    k_big_rev<C, T><<<dim3(nt, items), 256, smem, st>>>(d, ops, O1, O2, ms, mode, i);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_big_adj_rev(const BigArgs<R>& a, const SysView<R>& sys, const StateView<R>& sv, const C_t<R>* states,
+                               const C_t<R>* Gbuf, double* gpart, int p, int n, const C_t<R>* zst, cudaStream_t st,
+                               int* launches) {
+    using C = C_t<R>;
+    const int d = a.d, items = a.wlen * a.E, cap = p - 1 + n;
+    const size_t dd = (size_t)d * d, ms = a.mstride, zs = (size_t)cap * ms;
+    const int eb = ew_blocks(dd);
+    auto count = [&]() { if (launches) ++*launches; };
+    C* XH = reinterpret_cast<C*>(a.scratch);
+    C* Za = XH + (size_t)items * ms;
+    C* Zb = Za + (size_t)items * ms;
+    C* Xb = Zb + (size_t)items * ms;
+    // XH and Ubar (into Za); the initial Z11 / Z12 land in Zb / Xb and are not used
+    k_big_adj_init<R><<<dim3(eb, items), 256, 0, st>>>(a.prm, sys, sv, a.j0, a.wlen, states, Gbuf, a.wmax, XH, Za, Zb,
+                                                        Xb, ms);
+    count();
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    if ((err = cudaMemsetAsync(Xb, 0, (size_t)items * ms * sizeof(C), st)) != cudaSuccess) return err;
+    const int T = (sizeof(C) == 16) ? 32 : big_tile(d);
+    C *zb = Za, *zo = Zb;
+    auto rev = [&](const RevOps<C>& ops, C* O2, int mode, int i) {
+        cudaError_t e2 = (T == 32) ? rev_launch_t<C, 32>(d, items, ops, zo, O2, ms, mode, i, st)
+                                   : rev_launch_t<C, 64>(d, items, ops, zo, O2, ms, mode, i, st);
+        count();
+        std::swap(zb, zo);
+        return e2;
+    };
+    for (int m = n - 1; m >= 0; --m) {          // Sbar_m = Sbar_{m+1} S_m^dag + S_m^dag Sbar_{m+1}
+        const C* S = zst + (size_t)(p - 1 + m) * ms;
+        if ((err = rev(RevOps<C>{{zb, S, S, zb}, {ms, zs, zs, ms}}, nullptr, 1, 0)) != cudaSuccess) return err;
+    }
+    for (int i = 1; i <= p - 1; ++i) {          // Zbar_{i+1} = X^dag Zbar_i / i, Xbar += Zbar_i Z_{i+1}^dag / i
+        const C* S = zst + (size_t)(p - 1 - i) * ms;
+        if ((err = rev(RevOps<C>{{XH, zb, zb, S}, {ms, ms, ms, zs}}, Xb, 0, i)) != cudaSuccess) return err;
+    }
+    k_big_axpy<C><<<dim3(eb, items), 256, 0, st>>>(d, zb, Xb, ms, p);
+    count();
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    if (sys.M > 0) {
+        k_big_grad<R><<<dim3(items, sys.M), 256, 0, st>>>(a.prm, sys, a.j0, a.wlen, Xb, ms, gpart);
+        count();
+    }
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_big_expm<float>(const BigArgs<float>&, int, int, int, bool, cudaStream_t, int*, float2*);
+template cudaError_t launch_big_expm<double>(const BigArgs<double>&, int, int, int, bool, cudaStream_t, int*, double2*);
+template cudaError_t launch_big_adj_rev<float>(const BigArgs<float>&, const SysView<float>&, const StateView<float>&,
+                                               const float2*, const float2*, double*, int, int, const float2*,
+                                               cudaStream_t, int*);
+template cudaError_t launch_big_adj_rev<double>(const BigArgs<double>&, const SysView<double>&,
+                                                const StateView<double>&, const double2*, const double2*, double*, int,
+                                                int, const double2*, cudaStream_t, int*);
 template cudaError_t launch_big_adj<float>(const BigArgs<float>&, const SysView<float>&, const StateView<float>&,
                                            const float2*, const float2*, double*, int, int, cudaStream_t, int*);
 template cudaError_t launch_big_adj<double>(const BigArgs<double>&, const SysView<double>&, const StateView<double>&,

@@ -151,12 +151,13 @@ struct qoc_ctx {
     DevBuf Pbuf, lv0, lv1, scanst, hbuf, Ybuf;
     DevBuf Zbuf;                         // product operands for the reverse-mode adjoint (per-slice path)
     size_t zmstride = 0;
+    DevBuf Zbig;                         // the same for the batched path, sized at evaluation for p - 1 + n
     TcMaps tc_maps{};
 
     size_t device_bytes() const {
         const DevBuf* all[] = {&H64, &HR, &dDelta, &norms, &psiTR, &pathR, &fmask, &colw, &ckpt, &Ubuf, &states,
                                &Gbuf, &src, &carry, &Oj, &C5j, &Ofin, &gpart, &prm, &u_h, &grad_h, &out_h, &scratch,
-                               &tc_planes, &Pbuf, &lv0, &lv1, &scanst, &hbuf, &Ybuf, &Zbuf};
+                               &tc_planes, &Pbuf, &lv0, &lv1, &scanst, &hbuf, &Ybuf, &Zbuf, &Zbig};
         size_t s = 0;
         for (auto* b : all) s += b->bytes;
         return s;
@@ -265,7 +266,7 @@ void plan_impl(qoc_ctx* c) {
         if (use_tc(c)) per += tc_scratch_floats(d, 1) * sizeof(float);
         if (use_oz(c)) per += oz_scratch_bytes(d, 1);
         if (c->scan) per += dd0 * ks + (2 * (size_t)c->ustride * ks + seg - 1) / seg;
-        if (c->path_kind == 0 && c->opt.gradient == QOC_GRAD_EXACT)
+        if (c->path_kind == 0 && c->opt.gradient == QOC_GRAD_EXACT && c->opt.adjoint == QOC_ADJ_AUTO)
             per += 2 * (size_t)kZCap * ((dd0 + 31) / 32 * 32) * cs;
         per *= (size_t)E;
         size_t free_b = 0, total_b = 0;
@@ -386,7 +387,7 @@ void plan_impl(qoc_ctx* c) {
     } else {
         c->tc_planes.release();
     }
-    if (c->path_kind == 0 && c->opt.gradient == QOC_GRAD_EXACT) {
+    if (c->path_kind == 0 && c->opt.gradient == QOC_GRAD_EXACT && c->opt.adjoint == QOC_ADJ_AUTO) {
         c->zmstride = (dd + 31) / 32 * 32;
         A(c->Zbuf, 2 * (size_t)E * W * kZCap * c->zmstride * cs, "alloc product operands");
     } else {
@@ -507,6 +508,26 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
     }
     BigSys bsys{d, M, N, c->H64.as<double2>(), u, c->delta.empty() ? nullptr : c->dDelta.as<double>(),
                 c->Hdet.empty() ? 0 : 1};
+    // batched path: reverse-mode adjoint over stored product operands when the store fits (1/4 of
+    // the free device memory); else the block recursion, which stores nothing
+    bool big_rev = false;
+    size_t zbig_set = 0;
+    if (big && c->opt.gradient == QOC_GRAD_EXACT && c->opt.adjoint == QOC_ADJ_AUTO && !use_tc(c) && !use_oz(c)) {
+        zbig_set = (size_t)E * W * (size_t)(hp.p - 1 + hp.n) * c->mstride;
+        const size_t need = 2 * zbig_set * sizeof(C);
+        if (c->Zbig.bytes >= need) {
+            big_rev = true;
+        } else {
+            c->Zbig.release();
+            size_t free_b = 0, total_b = 0;
+            if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && need <= free_b / 4 &&
+                c->Zbig.alloc(need) == cudaSuccess)
+                big_rev = true;
+            else
+                cudaGetLastError();   // a failed allocation only means: block recursion
+        }
+    }
+    auto zbig = [&](int w) { return big_rev ? c->Zbig.as<C>() + (size_t)(w & 1) * zbig_set : nullptr; };
     auto big_args = [&](int w) {
         const int j0 = w * W;
         return BigArgs<R>{prm, bsys, d, E, j0, std::min(W, N - j0), W, c->scratch.p, c->mstride, Ub(w), c->ustride};
@@ -522,7 +543,7 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
         const int j0 = w * W, wlen = std::min(W, N - j0);
         if (big) {
             int n_l = 0;
-            cudaError_t e = launch_big_expm<R>(big_args(w), hp.p, hp.n, hp.m_split, split, st, &n_l);
+            cudaError_t e = launch_big_expm<R>(big_args(w), hp.p, hp.n, hp.m_split, split, st, &n_l, zbig(w));
             extra += n_l - 1;
             return e;
         }
@@ -559,8 +580,10 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
         }
         if (big) {
             int n_l = 0;
-            cudaError_t e = launch_big_adj<R>(big_args(w), sys, sv, Sb(w), Gb(w), c->gpart.as<double>(), hp.p, hp.n, st,
-                                              &n_l);
+            cudaError_t e = big_rev ? launch_big_adj_rev<R>(big_args(w), sys, sv, Sb(w), Gb(w), c->gpart.as<double>(),
+                                                            hp.p, hp.n, zbig(w), st, &n_l)
+                                    : launch_big_adj<R>(big_args(w), sys, sv, Sb(w), Gb(w), c->gpart.as<double>(), hp.p,
+                                                        hp.n, st, &n_l);
             extra += n_l - 1;
             return e;
         }
@@ -826,7 +849,7 @@ qoc_status qoc_create(qoc_ctx** out, const qoc_options* opt) {
     if (o.precision < QOC_PREC_FP64 || o.precision > QOC_PREC_BF16_SPLIT) return QOC_ERR_ARG;
     if (!(o.tol >= 0.0) || !(o.theta_max >= 0.0) || o.ckpt_stride < 0 || o.wave_slices < 0 || o.sweep < 0 ||
         o.sweep > QOC_SWEEP_SCAN || o.gradient < QOC_GRAD_EXACT || o.gradient > QOC_GRAD_FIRST_ORDER ||
-        o.fault_inject < 0 || o.fault_inject > 1)
+        o.fault_inject < 0 || o.fault_inject > 1 || o.adjoint < QOC_ADJ_AUTO || o.adjoint > QOC_ADJ_RECOMPUTE)
         return QOC_ERR_ARG;
     const bool f64 = o.precision == QOC_PREC_FP64;
     if (o.tol == 0.0) o.tol = f64 ? 1e-15 : 1e-8;

@@ -27,6 +27,7 @@ STATUS_NAMES = {0: "QOC_OK", 1: "QOC_ERR_ARG", 2: "QOC_ERR_SHAPE", 3: "QOC_ERR_N
 PRECISIONS = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
 SWEEPS = {"auto": 0, "serial": 1, "scan": 2}
 GRADIENTS = {"exact": 0, "first_order": 1}
+ADJOINTS = {"auto": 0, "recompute": 1}
 
 # every symbol exported by include/qoc.h
 ABI_SYMBOLS = ("qoc_default_options", "qoc_create", "qoc_destroy", "qoc_last_error", "qoc_status_string",
@@ -46,7 +47,7 @@ class qoc_options(ct.Structure):
                 ("ckpt_stride", ct.c_int), ("device", ct.c_int), ("stream", ct.c_void_p),
                 ("p_override", ct.c_int), ("n_override", ct.c_int), ("profile", ct.c_int),
                 ("wave_slices", ct.c_int), ("plain_fp32_exp", ct.c_int), ("sweep", ct.c_int),
-                ("gradient", ct.c_int), ("fault_inject", ct.c_int)]
+                ("gradient", ct.c_int), ("adjoint", ct.c_int), ("fault_inject", ct.c_int)]
 
 
 PROFILE_SLOTS = 16
@@ -262,7 +263,7 @@ class Context:
                  ckpt_stride: int = 0, wave_slices: int = 0, device: int = 0, stream: Optional[int] = None,
                  p_override: int = 0, n_override: int = -1, profile: bool = False,
                  plain_fp32_exp: bool = False, sweep: str = "auto", gradient: str = "exact",
-                 fault_inject: int = 0):
+                 adjoint: str = "auto", fault_inject: int = 0):
         opt = qoc_default_options()
         opt.precision = PRECISIONS[precision]
         opt.tol = tol
@@ -279,6 +280,7 @@ class Context:
         opt.plain_fp32_exp = 1 if plain_fp32_exp else 0
         opt.sweep = SWEEPS[sweep]
         opt.gradient = GRADIENTS[gradient]
+        opt.adjoint = ADJOINTS[adjoint]
         opt.fault_inject = fault_inject
         self.precision = precision
         self._ctx = qoc_create(opt)

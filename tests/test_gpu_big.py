@@ -183,3 +183,14 @@ def test_bounded_wait_runs_out_and_reports_timeout(precision):
             c.evaluate(prob.u)
         assert e.value.status == 8                          # QOC_ERR_TIMEOUT
     check(prob, precision, tol=1e-5)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_big_adjoint_forms_agree_with_oracle(precision):
+    """The batched path's adjoint in reverse mode over the stored forward operands (default) and
+    by the block recursion (adjoint="recompute"), both against the oracle."""
+    prob = sy.random_problem(d=72, M=2, N=11, S=4, seed=641, nF=3, path=True, E=2, dt=0.15, u_scale=0.8)
+    a = check(prob, precision)
+    b = check(prob, precision, adjoint="recompute")
+    assert a[3]["kernel_path"] == 1 and b[3]["kernel_path"] == 1
+    assert rel(a[1], b[1]) <= (1e-12 if precision == "fp64" else 2e-6)
