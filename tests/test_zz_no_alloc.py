@@ -69,3 +69,49 @@ def test_static_entry_point_rejects_oversized_problems():
     with pytest.raises(QocError) as e:     # N * d^2 beyond the fixed array
         qoc_evaluate_static(48, 0, 20000, 1, 0.1, 1, 0, 0, 1, 1, 0, [1, 0, 0, 0, 0], 0, 1)
     assert e.value.status == 2
+
+
+def test_static_entry_point_replays_from_a_cuda_graph():
+    """Captured once in a CUDA graph (where allocation is not permitted) and replayed with new
+    controls written into the same device buffer: each replay matches the context evaluation."""
+    import torch
+    from paper_1612_04929_gb300 import Context, build, qoc_evaluate_static
+
+    build.build()
+    prob = sy.random_problem(d=6, M=2, N=40, S=2, seed=905, nF=1, dt=0.2, u_scale=0.8)
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+
+    def c128(a):
+        return torch.from_numpy(np.ascontiguousarray(a, np.complex128)).to(dev)
+
+    H0, Hk, psi0, psiT = c128(prob.H0), c128(prob.Hk), c128(prob.psi0), c128(prob.psiT)
+    fmask = torch.zeros(prob.d, dtype=torch.int32, device=dev)
+    fmask[torch.from_numpy(prob.forbidden.astype(np.int64))] = 1
+    u = torch.from_numpy(np.ascontiguousarray(prob.u)).to(dev)
+    grad = torch.empty((prob.M, prob.N), dtype=torch.float64, device=dev)
+    out = torch.empty(6, dtype=torch.float64, device=dev)
+    side = torch.cuda.Stream()
+
+    def call():
+        qoc_evaluate_static(prob.d, prob.M, prob.N, prob.S, prob.dt, H0.data_ptr(), Hk.data_ptr(), u.data_ptr(),
+                            psi0.data_ptr(), psiT.data_ptr(), fmask.data_ptr(), prob.alpha, grad.data_ptr(),
+                            out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        call()                                   # first use outside the capture
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        call()
+    rng = np.random.default_rng(906)
+    with Context("fp64") as ctx:
+        ctx.set_problem(prob)
+        for u_np in (prob.u, prob.u + 0.3 * rng.standard_normal(prob.u.shape)):
+            u.copy_(torch.from_numpy(np.ascontiguousarray(u_np)))
+            graph.replay()
+            torch.cuda.synchronize()
+            c_ref, g_ref, _ = ctx.evaluate(u_np)
+            assert abs(out[0].item() - c_ref) <= TOL * abs(c_ref)
+            assert np.linalg.norm(grad.cpu().numpy() - g_ref) <= TOL * np.linalg.norm(g_ref)
