@@ -117,7 +117,7 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ oracle (CPU) timing
-def oracle_sample_time(workload, nslices, repeats=1, ref_slices=0, exact=True):
+def oracle_sample_time(workload, nslices, repeats=1, ref_slices=0, exact=True, maker=None):
     """Times the CPU FP64 oracle on the first `nslices` slices of the workload in a child
     process limited to one BLAS thread.  With ref_slices > 0 the child also evaluates the oracle
     once on the first ref_slices slices (untimed) and returns its cost and gradient, the
@@ -127,14 +127,15 @@ import json, os, sys, time
 sys.path.insert(0, {ROOT!r})
 import synthetic as sy
 from oracle import qoc_oracle as orc
-p = sy.WORKLOADS[{workload!r}](N={nslices})
+make = (lambda n: {maker}) if {maker!r} else (lambda n: sy.WORKLOADS[{workload!r}](N=n))
+p = make({nslices})
 orc.cost_and_grad(p, p.u)
 ts = []
 for _ in range({repeats}):
     t0 = time.perf_counter(); orc.cost_and_grad(p, p.u); ts.append(time.perf_counter() - t0)
 ref = None
 if {ref_slices} > 0:
-    q = sy.WORKLOADS[{workload!r}](N={ref_slices})
+    q = make({ref_slices})
     c, g, _ = orc.cost_and_grad(q, q.u, exact={exact!r})
     ref = {{"N": {ref_slices}, "cost": float(c), "grad": [float(x) for x in g.ravel()]}}
 print(json.dumps({{"t": sum(ts) / len(ts), "ref": ref}}))
@@ -444,12 +445,96 @@ def batch_arm(args):
         c.close()
 
 
+def dsweep_arm(args):
+    """The per-d sweep: for d = 2 .. 256 (log2(d) qubits, GUE drift, Pauli controls, Haar target,
+    full unitary, FP32 form), the fwd+grad slice-steps/s, the plain FP64 GPU form's and the
+    speedup over it, and the relative error against the oracle (whole evolution for d <= 64, the
+    first 100 slices above).  Each point is timed over `steps` evaluations after `warmup`, with
+    the L2 flushed before each."""
+    import numpy as np
+    import torch
+    import synthetic as sy
+    from paper_1612_04929_gb300 import Context, build as qbuild
+    qbuild.build()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def timed(ctx, u, steps):
+        g = torch.empty_like(u)
+        o = torch.empty(6, dtype=torch.float64, device="cuda")
+        for _ in range(max(args.warmup, 3)):
+            ctx.evaluate_device(u.data_ptr(), g.data_ptr(), o.data_ptr())
+        ctx.sync()
+        ts = []
+        for _ in range(steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.evaluate_device(u.data_ptr(), g.data_ptr(), o.data_ptr())
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return sum(ts) / len(ts), g, o
+
+    per_d = {}
+    tot_units = tot_ms = 0.0
+    with ClockSampler(0) as clk:
+        for d in sy.DSWEEP_D:
+            N = 2000 if d <= 64 else 500
+            prob = sy.dsweep_problem(d, N=N)
+            u = torch.tensor(prob.u, dtype=torch.float64, device="cuda")
+            with Context("fp32", stream=stream.cuda_stream) as c:
+                c.set_problem(prob)
+                ms, g, o = timed(c, u, args.steps)
+                info = c.info()
+                g32, c32 = g.cpu().numpy(), float(o[0].item())
+            with Context("fp64", stream=stream.cuda_stream) as c:
+                c.set_problem(prob)
+                ms64, _, _ = timed(c, u, max(1, min(args.steps, 3)))
+            row = {"N": N, "ms_per_step": ms, "value": N / (ms / 1e3), "fp64_ms_per_step": ms64,
+                   "speedup_vs_fp64_form": ms64 / ms, "p": info["p"], "n": info["n"],
+                   "kernel_path": info["kernel_path"]}
+            if not args.no_cpu_baseline:
+                ref_n = N if d <= 64 else 100
+                try:
+                    t, _, ref = oracle_sample_time("dsweep", min(N, 50), ref_slices=ref_n,
+                                                   maker=f"sy.dsweep_problem({d}, N=n)")
+                    if ref_n == N:
+                        c_gpu, g_gpu = c32, g32
+                    else:
+                        q = sy.dsweep_problem(d, N=ref_n)
+                        with Context("fp32", stream=stream.cuda_stream) as cq:
+                            cq.set_problem(q)
+                            c_gpu, g_gpu, _ = cq.evaluate(q.u)
+                    g_ref = np.asarray(ref["grad"])
+                    row["grad_rel"] = float(np.linalg.norm(np.ravel(g_gpu) - g_ref) / np.linalg.norm(g_ref))
+                    row["cost_rel"] = abs(c_gpu - ref["cost"]) / abs(ref["cost"])
+                    row["error_slices"] = ref_n
+                    row["oracle_slice_steps_per_s"] = min(N, 50) / t
+                except Exception as exc:
+                    row["oracle"] = f"failed: {exc}"
+            per_d[str(d)] = row
+            tot_units += N
+            tot_ms += ms
+    line = {"metric": METRIC, "value": tot_units / (tot_ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": tot_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded GUE-drift qubit registers)",
+            "config": {"workload": "dsweep", "d": list(sy.DSWEEP_D), "precision": "fp32",
+                       "l2": "flushed before every timed evaluation"},
+            "per_d": per_d, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
     elif args.workload.startswith("batch"):
         batch_arm(args)
+    elif args.workload == "dsweep":
+        dsweep_arm(args)
     else:
         ours_arm(args)
 

@@ -273,6 +273,23 @@ def batch_problems(count: int = 128, ensemble: int = 1, **kw) -> List[Problem]:
     return [batch_problem(i, ensemble=ensemble, **kw) for i in range(count)]
 
 
+def dsweep_problem(d: int, seed: int = 6000, N: int = 2000) -> Problem:
+    """One point of the per-d sweep, d a power of two: log2(d) qubits, GUE drift with spectral norm
+    2pi*0.05, Pauli x/y controls on the first two qubits (one x control for d = 2), Haar target,
+    full unitary, dt = 0.5 ns, u ~ N(0, (2pi*0.02)^2); FP32."""
+    rng = np.random.default_rng(seed + d)
+    nq = int(round(math.log2(d)))
+    H0 = gue(d, rng, TWO_PI * 0.05)
+    Hk = pauli_controls(nq, 1 if nq == 1 else 4)
+    M = Hk.shape[0]
+    V = haar_unitary(d, rng)
+    u = rng.normal(0.0, TWO_PI * 0.02, size=(M, N))
+    return Problem(f"dsweep_d{d}", H0, Hk, 0.5, N, np.eye(d, dtype=np.complex128), V, np.zeros(0, np.int32),
+                   np.ones(d), default_alpha(), u, precision="fp32")
+
+
+DSWEEP_D = (2, 4, 8, 16, 32, 64, 128, 256)
+
 WORKLOADS = {
     "cnot2q": cnot2q,
     "transmon_cavity": transmon_cavity,
