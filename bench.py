@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=0, help="slices in the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-form", action="store_true", help="skip timing the plain FP64 GPU form")
+    ap.add_argument("--graph", action="store_true", help="replay each evaluation from a captured CUDA graph")
     ap.add_argument("--gradient", choices=["exact", "first_order"], default="exact",
                     help="exact derivative of the truncated series, or the paper's first-order Eq. 11")
     return ap.parse_args()
@@ -205,8 +206,9 @@ def ours_arm(args):
     precision = args.precision or prob.precision
     stream = torch.cuda.Stream()          # every kernel of the step and every event on one stream
     torch.cuda.set_stream(stream)
-    ctx = Context(precision, device=local, stream=stream.cuda_stream, ckpt_stride=args.ckpt_stride, profile=True,
-                  gradient=args.gradient)
+    # per-kernel events (profile) need plain launches; with --graph the step is a graph replay
+    ctx = Context(precision, device=local, stream=stream.cuda_stream, ckpt_stride=args.ckpt_stride,
+                  profile=not args.graph, gradient=args.gradient, graph=args.graph)
     ctx.set_problem(prob)
     u = torch.tensor(prob.u, dtype=torch.float64, device="cuda")
     grad = torch.empty_like(u)
@@ -287,6 +289,32 @@ def ours_arm(args):
     e2e_value = units * world / (sum(e2e_t) / len(e2e_t))
     mn_bytes = prob.M * prob.N * 8
 
+    # the same evaluation replayed from a captured CUDA graph (per-slice path only; the timed
+    # region above uses plain launches so that every kernel carries its own events)
+    graph_replay = None
+    if not args.graph and info["kernel_path"] == 0:
+        cg = Context(precision, device=local, stream=stream.cuda_stream, ckpt_stride=args.ckpt_stride,
+                     gradient=args.gradient, graph=True)
+        cg.set_problem(prob)
+        gg = torch.empty_like(u)
+        og = torch.empty(6, dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            cg.evaluate_device(u.data_ptr(), gg.data_ptr(), og.data_ptr())
+        cg.sync()
+        sg = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        eg = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        torch.cuda.synchronize()
+        for k in range(K):
+            flush.zero_()
+            sg[k].record(stream)
+            cg.evaluate_device(u.data_ptr(), gg.data_ptr(), og.data_ptr())
+            eg[k].record(stream)
+        torch.cuda.synchronize()
+        msg = sum(s.elapsed_time(e) for s, e in zip(sg, eg)) / K
+        graph_replay = {"value": units / (msg / 1e3), "unit": UNIT, "ms_per_step": msg, "steps": K,
+                        "identical_to_plain_launches": bool(torch.equal(gg, grad) and torch.equal(og, out))}
+        cg.close()
+
     # the plain FP64 GPU form on the same workload (the metric's second part: speedup of the
     # mixed form over it, at the error stated below)
     fp64_form = None
@@ -351,12 +379,13 @@ def ours_arm(args):
                 "data": f"synthetic (seeded {prob.name} system, random controls)",
                 "config": config_of(prob, precision, info["ckpt_stride"],
                                     {"p": p, "n": n, "wave_slices": info["wave_slices"], "n_waves": info["n_waves"],
-                                     "gradient": args.gradient}),
+                                     "gradient": args.gradient, "graph": args.graph}),
                 "roofline": roof, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": mn_bytes,
                         "d2h_bytes_per_step": mn_bytes + 6 * 8 + 32},
                 "gpu_launches": info["launches_per_eval"] * K,
                 "clocks": clk.summary(), "kernels": kernels,
+                "graph_replay": graph_replay,
                 "fp64_form": fp64_form,
                 "speedup_vs_fp64_form": (value / fp64_form["value"]) if fp64_form else None,
                 "error_vs_oracle": error,

@@ -106,6 +106,11 @@ typedef struct qoc_options {
                              operands of the forward products (two products per step) when the store
                              fits, else by the block recursion; QOC_ADJ_RECOMPUTE (1): always the
                              block recursion (three products per step, nothing stored) */
+    int graph;            /* != 0: on the per-slice path (d <= 68 FP32, <= 48 FP64), where every decision
+                             of an evaluation is taken on the device, qoc_evaluate_device captures its
+                             launches once into a CUDA graph (per (u_dev, grad_dev, out_dev) triple) and
+                             replays it on later calls with the same pointers; a new triple or a new
+                             plan captures again.  Ignored with profile != 0 and on the batched path. */
     int fault_inject;     /* test of the failure path, 0 (default) off.  1: the tensor-core adjoint
                              kernels (TF32_SPLIT, BF16_SPLIT, d > 68) withhold their first operand
                              copy, so their bounded mbarrier wait (shortened to 4096 polls) runs

@@ -152,6 +152,13 @@ struct qoc_ctx {
     DevBuf Zbuf;                         // product operands for the reverse-mode adjoint (per-slice path)
     size_t zmstride = 0;
     DevBuf Zbig;                         // the same for the batched path, sized at evaluation for p - 1 + n
+    cudaGraphExec_t gexec = nullptr;     // captured evaluation (qoc_options.graph) and its pointers
+    const void* gkey[3] = {nullptr, nullptr, nullptr};
+    void drop_graph() {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        gexec = nullptr;
+        gkey[0] = gkey[1] = gkey[2] = nullptr;
+    }
     TcMaps tc_maps{};
 
     size_t device_bytes() const {
@@ -776,6 +783,7 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
 }
 
 void plan(qoc_ctx* c) {
+    c->drop_graph();   // a captured evaluation refers to the buffers of the previous plan
     if (is_fp64(c)) plan_impl<double>(c);
     else plan_impl<float>(c);
 }
@@ -878,6 +886,7 @@ void qoc_destroy(qoc_ctx* ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->opt.device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    ctx->drop_graph();
     if (ctx->aux) {
         cudaStreamSynchronize(ctx->aux);
         cudaStreamDestroy(ctx->aux);
@@ -1022,6 +1031,29 @@ qoc_status qoc_evaluate_device(qoc_ctx* ctx, const double* u_dev, double* grad_d
     if (!u_dev || !grad_dev || !out_dev) return set_err(ctx, QOC_ERR_ARG, "NULL device pointer");
     QOC_GUARD_BEGIN
     check_cuda(ctx, cudaSetDevice(ctx->opt.device), "set device");
+    if (!ctx->planned) plan(ctx);
+    if (ctx->opt.graph && !ctx->opt.profile && ctx->path_kind == 0) {
+        const void* key[3] = {u_dev, grad_dev, out_dev};
+        if (!(ctx->gexec && key[0] == ctx->gkey[0] && key[1] == ctx->gkey[1] && key[2] == ctx->gkey[2])) {
+            ctx->drop_graph();
+            cudaGraph_t g = nullptr;
+            check_cuda(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+            try {
+                evaluate(ctx, u_dev, grad_dev, out_dev);
+            } catch (...) {
+                cudaStreamEndCapture(ctx->stream, &g);   // leave the stream usable
+                if (g) cudaGraphDestroy(g);
+                throw;
+            }
+            check_cuda(ctx, cudaStreamEndCapture(ctx->stream, &g), "end capture");
+            cudaError_t e = cudaGraphInstantiate(&ctx->gexec, g, 0);
+            cudaGraphDestroy(g);
+            check_cuda(ctx, e, "instantiate graph");
+            for (int i = 0; i < 3; ++i) ctx->gkey[i] = key[i];
+        }
+        check_cuda(ctx, cudaGraphLaunch(ctx->gexec, ctx->stream), "graph launch");
+        return QOC_OK;
+    }
     evaluate(ctx, u_dev, grad_dev, out_dev);
     return QOC_OK;
     QOC_GUARD_END

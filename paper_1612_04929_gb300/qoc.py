@@ -47,7 +47,7 @@ class qoc_options(ct.Structure):
                 ("ckpt_stride", ct.c_int), ("device", ct.c_int), ("stream", ct.c_void_p),
                 ("p_override", ct.c_int), ("n_override", ct.c_int), ("profile", ct.c_int),
                 ("wave_slices", ct.c_int), ("plain_fp32_exp", ct.c_int), ("sweep", ct.c_int),
-                ("gradient", ct.c_int), ("adjoint", ct.c_int), ("fault_inject", ct.c_int)]
+                ("gradient", ct.c_int), ("adjoint", ct.c_int), ("graph", ct.c_int), ("fault_inject", ct.c_int)]
 
 
 PROFILE_SLOTS = 16
@@ -263,7 +263,7 @@ class Context:
                  ckpt_stride: int = 0, wave_slices: int = 0, device: int = 0, stream: Optional[int] = None,
                  p_override: int = 0, n_override: int = -1, profile: bool = False,
                  plain_fp32_exp: bool = False, sweep: str = "auto", gradient: str = "exact",
-                 adjoint: str = "auto", fault_inject: int = 0):
+                 adjoint: str = "auto", graph: bool = False, fault_inject: int = 0):
         opt = qoc_default_options()
         opt.precision = PRECISIONS[precision]
         opt.tol = tol
@@ -281,6 +281,7 @@ class Context:
         opt.sweep = SWEEPS[sweep]
         opt.gradient = GRADIENTS[gradient]
         opt.adjoint = ADJOINTS[adjoint]
+        opt.graph = 1 if graph else 0
         opt.fault_inject = fault_inject
         self.precision = precision
         self._ctx = qoc_create(opt)

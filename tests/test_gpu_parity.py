@@ -276,6 +276,37 @@ def test_error_statuses():
     big.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_graph_replay_matches_plain_launches(precision):
+    """graph=True captures an evaluation by device pointer into a CUDA graph and replays it; the
+    results are bitwise those of plain launches, for new control values written in place and
+    after a new output buffer forces a new capture."""
+    import torch
+    from paper_1612_04929_gb300 import Context
+    prob = sy.random_problem(d=12, M=2, N=90, S=3, seed=131, nF=2, path=True, E=2)
+    rng = np.random.default_rng(132)
+    us = [prob.u, prob.u + 0.2 * rng.standard_normal(prob.u.shape)]
+    u = torch.tensor(prob.u, dtype=torch.float64, device="cuda")
+    outs = {}
+    for graph in (False, True):
+        with Context(precision, graph=graph) as c:
+            c.set_problem(prob)
+            g = torch.empty_like(u)
+            res = []
+            for trial in range(3):
+                o = torch.empty(6, dtype=torch.float64, device="cuda") if trial == 2 else (
+                    outs.setdefault(("o", graph), torch.empty(6, dtype=torch.float64, device="cuda")))
+                u.copy_(torch.from_numpy(np.ascontiguousarray(us[trial % 2])))
+                c.evaluate_device(u.data_ptr(), g.data_ptr(), o.data_ptr())
+                c.sync()
+                res.append((o.cpu().numpy().copy(), g.cpu().numpy().copy()))
+            outs[graph] = res
+    for (o1, g1), (o2, g2) in zip(outs[False], outs[True]):
+        assert np.array_equal(o1, o2) and np.array_equal(g1, g2)
+    c_ref, g_ref, _ = orc.cost_and_grad(prob, us[1])
+    assert rel(outs[True][1][1], g_ref) <= TOL[precision]
+
+
 # ------------------------------------------------------------------ torch autograd
 def test_autograd_function_matches_oracle():
     import torch
