@@ -29,6 +29,8 @@ sys.path.insert(0, ROOT)
 METRIC = "fwd+grad slice-steps/s"
 UNIT = "slice-steps/s"
 # FP32 FMA peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (max SM clock)
+# DRAM bytes per launch measured by ncu, keyed by (workload, precision, kernel, wave slices)
+MEASURED_TRAFFIC = {}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 L2_FLUSH_BYTES = 256 << 20
 
@@ -266,13 +268,18 @@ def ours_arm(args):
         flops = per_slice[top_name] * slices * prob.E * K
         achieved = flops / (top_ms / 1e3) / 1e12
         fp32 = precision != "fp64"
+        # DRAM bytes per launch of the dominant kernel, from an ncu capture of the same kernel at
+        # this workload (dram__bytes_read.sum + dram__bytes_write.sum); None where none was taken
+        traffic = MEASURED_TRAFFIC.get((prob.name, precision, top_name, info["wave_slices"]))
         roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS if fp32 else None,
                 "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS if fp32 else None,
-                "traffic": None, "kernel": top_name, "launches": top_launches,
+                "traffic": traffic, "kernel": top_name, "launches": top_launches,
                 "avg_launch_ms": top_ms / top_launches,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
                 "note": "algorithmic flops (8 d^3 per complex product); the split hi+lo products "
-                        "execute ~12 FP32 instructions per algorithmic multiply-add"}
+                        "execute ~12 FP32 instructions per algorithmic multiply-add",
+                "traffic_source": ("dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of this "
+                                   "kernel at this workload") if traffic else None}
     kernels = {k: {"launches": v[0], "ms_per_step": v[1] / K} for k, v in prof.items()}
 
     # end to end through the host API with pinned buffers

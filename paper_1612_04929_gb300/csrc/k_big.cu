@@ -4,13 +4,15 @@
 // FP64), every Horner / squaring product of Eqs. 9-10 runs as one launch over all slices of the
 // wave: CTA (tile, item) computes a T x T tile of C_item = A_item B_item with the operands
 // streamed through shared memory in K-chunks.  The same arithmetic as the per-slice kernels:
-//   * FP32 form: X_j in split hi+lo FP32 from an FP64 assembly, pair (double-float) products
-//     for the squarings and for the Horner steps i <= m_split, plain products of the hi parts
-//     for the earlier steps; U_j is the rounded pair;
+//   * FP32 form: X_j grid-split (qoc_device.cuh) from an FP64 assembly, split products (exact
+//     FP32 sums of the grid parts plus rounded cross terms) for the squarings and for the
+//     Horner steps i <= m_split, plain FP32 products for the earlier steps; U_j is the rounded
+//     sum of its two parts;
 //   * adjoint: the block recursion on [[X^dag, Ubar], [0, X^dag]] (exact derivative of the
 //     truncated series), FP32 (FP32 form) or FP64 (FP64 form);
 //   * dC/du_{k,j} = Re tr(Xbar^dag (-i s H_k)) reduced in FP64.
 // Matrices of item b sit at base + b * mstride, row-major d x d.
+#include <cmath>
 #include <type_traits>
 #include <utility>
 
@@ -22,16 +24,6 @@ namespace qoc {
 // ------------------------------------------------------------------------------------------
 // element helpers: E = float4 (pair), float2, double2
 // ------------------------------------------------------------------------------------------
-__device__ __forceinline__ void big_mac_pair(float& hi, float& lo, float ah, float al, float bh, float bl) {
-    const float p = ah * bh;
-    float e = fmaf(ah, bh, -p);
-    e = fmaf(ah, bl, e);
-    e = fmaf(al, bh, e);
-    const float t = hi + p;
-    const float bv = t - hi;
-    lo += (hi - (t - bv)) + (p - bv) + e;
-    hi = t;
-}
 __device__ __forceinline__ void big_norm(float& hi, float& lo) {
     const float s = hi + lo;
     lo = lo - (s - hi);
@@ -60,18 +52,24 @@ template <> __device__ __forceinline__ double2 ezero<double2>() { return make_do
 // ------------------------------------------------------------------------------------------
 // assembly: X = -i s H_j (+ delta_e H_det) from FP64 H; Z = I + X / p
 // ------------------------------------------------------------------------------------------
-__device__ __forceinline__ void put(float4& o, double x, double y) {
-    o.x = (float)x;
-    o.y = (float)y;
+// float4: grid-split with exponent e (e == kFullForm: the full FP32 value in .x, .y, zero .z, .w)
+constexpr int kFullForm = 1000;
+__device__ __forceinline__ void put(float4& o, double x, double y, int e) {
+    if (e == kFullForm) {
+        o = make_float4((float)x, (float)y, 0.f, 0.f);
+        return;
+    }
+    o.x = (float)ldexp(rint(ldexp(x, 12 - e)), e - 12);
+    o.y = (float)ldexp(rint(ldexp(y, 12 - e)), e - 12);
     o.z = (float)(x - (double)o.x);
     o.w = (float)(y - (double)o.y);
 }
-__device__ __forceinline__ void put(double2& o, double x, double y) { o = make_double2(x, y); }
-__device__ __forceinline__ void put(float2& o, double x, double y) { o = make_float2((float)x, (float)y); }
+__device__ __forceinline__ void put(double2& o, double x, double y, int) { o = make_double2(x, y); }
+__device__ __forceinline__ void put(float2& o, double x, double y, int) { o = make_float2((float)x, (float)y); }
 
 template <typename E>
 __global__ void k_big_assemble(const DevParams* __restrict__ prm, BigSys sys, int j0, int wlen, E* __restrict__ X,
-                               E* __restrict__ Z, size_t mstride) {
+                               E* __restrict__ Z, size_t mstride, int ex, int ezp) {
     const int item = blockIdx.y, jl = item % wlen, e = item / wlen, j = j0 + jl;
     const int d = sys.d, M = sys.M;
     const size_t dd = (size_t)d * d;
@@ -94,8 +92,8 @@ __global__ void k_big_assemble(const DevParams* __restrict__ prm, BigSys sys, in
         const double xr = s * h.y, xi = -s * h.x;
         const int a = (int)(idx / d), b = (int)(idx - (size_t)a * d);
         E xv, zv;
-        put(xv, xr, xi);
-        put(zv, xr * ip + (a == b ? 1.0 : 0.0), xi * ip);
+        put(xv, xr, xi, ex);
+        put(zv, xr * ip + (a == b ? 1.0 : 0.0), xi * ip, ezp);
         X[(size_t)item * mstride + idx] = xv;
         Z[(size_t)item * mstride + idx] = zv;
     }
@@ -105,14 +103,16 @@ __global__ void k_big_assemble(const DevParams* __restrict__ prm, BigSys sys, in
 // batched product C = A B (T x T tile per CTA), epilogue:
 //   kind 0: C = I + AB / i     (Horner step i)
 //   kind 1: C = AB             (squaring)
-// PAIR: pair arithmetic on float4 operands; HI: plain FP32 product of the hi parts of float4
-// operands (result stored with lo = 0); otherwise plain products of E = float2 / double2.
+// SPLIT: split product of grid-split float4 operands, the result grid-split with `magic`;
+// PLAIN32: plain FP32 product of a grid-split A (X) and a full-form B, the result in full form
+// (magic == 0) or grid-split; otherwise plain products of E = float2 / double2.
 // ------------------------------------------------------------------------------------------
 constexpr int KC = 16;
 
-template <typename E, int T, int MODE>   // MODE 0 plain, 1 pair, 2 hi-only (E = float4)
+template <typename E, int T, int MODE>   // MODE 0 plain, 1 split, 2 plain FP32 (E = float4)
 __global__ void __launch_bounds__(256)
-k_big_mm(int d, const E* __restrict__ A, const E* __restrict__ B, E* __restrict__ Cm, size_t mstride, int kind, int i) {
+k_big_mm(int d, const E* __restrict__ A, const E* __restrict__ B, E* __restrict__ Cm, size_t mstride, int kind, int i,
+         float magic) {
     constexpr int MT = T / 16;
     // two buffers of (As[T][KC + 1], Bs[KC][T + 1]): the next K-chunk is copied (cp.async) while
     // the current one is multiplied
@@ -128,13 +128,14 @@ k_big_mm(int d, const E* __restrict__ A, const E* __restrict__ B, E* __restrict_
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const E* Ai = A + (size_t)item * mstride;
     const E* Bi = B + (size_t)item * mstride;
-    float ar[MT][MT][2], ai_[MT][MT][2];     // pair accumulators (re hi/lo, im hi/lo)
+    // split accumulators: grid sums (re, im) exact, cross terms (re, im); MODE 2 uses [0], [1]
+    float sa[MT][MT][4];
     E acc[MT][MT];
 #pragma unroll
     for (int x = 0; x < MT; ++x)
 #pragma unroll
         for (int y = 0; y < MT; ++y) {
-            ar[x][y][0] = ar[x][y][1] = ai_[x][y][0] = ai_[x][y][1] = 0.f;
+            sa[x][y][0] = sa[x][y][1] = sa[x][y][2] = sa[x][y][3] = 0.f;
             acc[x][y] = ezero<E>();
         }
     auto issue = [&](int buf, int k0) {
@@ -168,6 +169,18 @@ k_big_mm(int d, const E* __restrict__ A, const E* __restrict__ B, E* __restrict_
             for (int x = 0; x < MT; ++x) a[x] = As[ty + 16 * x][k];
 #pragma unroll
             for (int y = 0; y < MT; ++y) b[y] = Bs[k][tx + 16 * y];
+            float2 bf[MT], af[MT];   // full values: of B (MODE 1), of A (MODE 2)
+#pragma unroll
+            for (int y = 0; y < MT; ++y) {
+                if constexpr (MODE == 1) {
+                    const float4 bv = *reinterpret_cast<const float4*>(&b[y]);
+                    bf[y] = make_float2(bv.x + bv.z, bv.y + bv.w);
+                }
+                if constexpr (MODE == 2) {
+                    const float4 av = *reinterpret_cast<const float4*>(&a[y]);
+                    af[y] = make_float2(av.x + av.z, av.y + av.w);
+                }
+            }
 #pragma unroll
             for (int x = 0; x < MT; ++x)
 #pragma unroll
@@ -175,17 +188,26 @@ k_big_mm(int d, const E* __restrict__ A, const E* __restrict__ B, E* __restrict_
                     if constexpr (MODE == 1) {
                         const float4 av = *reinterpret_cast<const float4*>(&a[x]);
                         const float4 bv = *reinterpret_cast<const float4*>(&b[y]);
-                        big_mac_pair(ar[x][y][0], ar[x][y][1], av.x, av.z, bv.x, bv.z);
-                        big_mac_pair(ar[x][y][0], ar[x][y][1], -av.y, -av.w, bv.y, bv.w);
-                        big_mac_pair(ai_[x][y][0], ai_[x][y][1], av.x, av.z, bv.y, bv.w);
-                        big_mac_pair(ai_[x][y][0], ai_[x][y][1], av.y, av.w, bv.x, bv.z);
+                        float* c = sa[x][y];
+                        c[0] = fmaf(av.x, bv.x, c[0]);
+                        c[0] = fmaf(-av.y, bv.y, c[0]);
+                        c[1] = fmaf(av.x, bv.y, c[1]);
+                        c[1] = fmaf(av.y, bv.x, c[1]);
+                        c[2] = fmaf(av.x, bv.z, c[2]);
+                        c[2] = fmaf(-av.y, bv.w, c[2]);
+                        c[2] = fmaf(av.z, bf[y].x, c[2]);
+                        c[2] = fmaf(-av.w, bf[y].y, c[2]);
+                        c[3] = fmaf(av.x, bv.w, c[3]);
+                        c[3] = fmaf(av.y, bv.z, c[3]);
+                        c[3] = fmaf(av.z, bf[y].y, c[3]);
+                        c[3] = fmaf(av.w, bf[y].x, c[3]);
                     } else if constexpr (MODE == 2) {
-                        const float4 av = *reinterpret_cast<const float4*>(&a[x]);
                         const float4 bv = *reinterpret_cast<const float4*>(&b[y]);
-                        ar[x][y][0] = fmaf(av.x, bv.x, ar[x][y][0]);
-                        ar[x][y][0] = fmaf(-av.y, bv.y, ar[x][y][0]);
-                        ai_[x][y][0] = fmaf(av.x, bv.y, ai_[x][y][0]);
-                        ai_[x][y][0] = fmaf(av.y, bv.x, ai_[x][y][0]);
+                        float* c = sa[x][y];
+                        c[0] = fmaf(af[x].x, bv.x, c[0]);
+                        c[0] = fmaf(-af[x].y, bv.y, c[0]);
+                        c[1] = fmaf(af[x].x, bv.y, c[1]);
+                        c[1] = fmaf(af[x].y, bv.x, c[1]);
                     } else {
                         cfma(acc[x][y], a[x], b[y]);
                     }
@@ -203,19 +225,25 @@ k_big_mm(int d, const E* __restrict__ A, const E* __restrict__ B, E* __restrict_
             const bool diag = (kind == 0) && (r == c);
             E out;
             if constexpr (MODE == 1) {
-                float rh = ar[x][y][0], rl = ar[x][y][1], ih = ai_[x][y][0], il = ai_[x][y][1];
-                big_norm(rh, rl);
-                big_norm(ih, il);
+                float rh, rl, ih, il;
+                two_sum(sa[x][y][0], sa[x][y][2], rh, rl);
+                two_sum(sa[x][y][1], sa[x][y][3], ih, il);
                 if (kind == 0 && i > 1) {
                     big_div(rh, rl, (float)i);
                     big_div(ih, il, (float)i);
                 }
                 if (diag) big_add1(rh, rl);
-                float4 o = make_float4(rh, ih, rl, il);
+                float4 o;
+                grid_split(rh, rl, magic, o.x, o.z);
+                grid_split(ih, il, magic, o.y, o.w);
                 out = *reinterpret_cast<E*>(&o);
             } else if constexpr (MODE == 2) {
                 const float ri = 1.0f / (float)i;
-                float4 o = make_float4(fmaf(ar[x][y][0], ri, diag ? 1.0f : 0.0f), ai_[x][y][0] * ri, 0.f, 0.f);
+                float4 o = make_float4(fmaf(sa[x][y][0], ri, diag ? 1.0f : 0.0f), sa[x][y][1] * ri, 0.f, 0.f);
+                if (magic != 0.f) {   // read by a split product
+                    grid_split(o.x, 0.f, magic, o.x, o.z);
+                    grid_split(o.y, 0.f, magic, o.y, o.w);
+                }
                 out = *reinterpret_cast<E*>(&o);
             } else {
                 out = acc[x][y];
@@ -590,7 +618,7 @@ template <typename E, int T> constexpr size_t blk_smem() { return 2 * mm_smem<E,
 
 template <typename E, int T, int MODE>
 static cudaError_t mm_launch_t(int d, int items, const E* A, const E* B, E* Cm, size_t mstride, int kind, int i,
-                               cudaStream_t st) {
+                               float magic, cudaStream_t st) {
     constexpr size_t smem = mm_smem<E, T>();
     static bool attr = false;
     if (!attr) {
@@ -599,15 +627,15 @@ static cudaError_t mm_launch_t(int d, int items, const E* A, const E* B, E* Cm, 
         attr = true;
     }
     const int nt = ((d + T - 1) / T) * ((d + T - 1) / T);
-    k_big_mm<E, T, MODE><<<dim3(nt, items), 256, smem, st>>>(d, A, B, Cm, mstride, kind, i);
+    k_big_mm<E, T, MODE><<<dim3(nt, items), 256, smem, st>>>(d, A, B, Cm, mstride, kind, i, magic);
     return cudaGetLastError();
 }
 
 template <typename E, int MODE>
 static cudaError_t mm_launch(int d, int items, const E* A, const E* B, E* Cm, size_t mstride, int kind, int i,
-                             cudaStream_t st) {
-    if (big_tile(d) == 32) return mm_launch_t<E, 32, MODE>(d, items, A, B, Cm, mstride, kind, i, st);
-    return mm_launch_t<E, 64, MODE>(d, items, A, B, Cm, mstride, kind, i, st);
+                             cudaStream_t st, float magic = 0.f) {
+    if (big_tile(d) == 32) return mm_launch_t<E, 32, MODE>(d, items, A, B, Cm, mstride, kind, i, magic, st);
+    return mm_launch_t<E, 64, MODE>(d, items, A, B, Cm, mstride, kind, i, magic, st);
 }
 
 template <typename C, int T>
@@ -631,8 +659,9 @@ static int ew_blocks(size_t dd) {
 }
 
 template <typename R>
-cudaError_t launch_big_expm(const BigArgs<R>& a, int p, int n, int m_split, bool split, cudaStream_t st, int* launches,
+cudaError_t launch_big_expm(const BigArgs<R>& a, const DevParams& hp, bool split, cudaStream_t st, int* launches,
                             C_t<R>* zst) {
+    const int p = hp.p, n = hp.n, m_split = hp.m_split;
     const int d = a.d, items = a.wlen * a.E;
     const size_t dd = (size_t)d * d;
     const int eb = ew_blocks(dd);
@@ -650,21 +679,27 @@ cudaError_t launch_big_expm(const BigArgs<R>& a, int p, int n, int m_split, bool
         float4* X = reinterpret_cast<float4*>(a.scratch);
         float4* Za = X + (size_t)items * a.mstride;
         float4* Zb = Za + (size_t)items * a.mstride;
-        k_big_assemble<float4><<<dim3(eb, items), 256, 0, st>>>(a.prm, a.bsys, a.j0, a.wlen, X, Za, a.mstride);
+        // the operand of a split product is grid-split (X: ex; Z_i, i >= 2: ez; T and its
+        // squarings: eu), the operand of a plain FP32 Horner step is in full form
+        const float mz = std::ldexp(1.5f, hp.ez + 11), mu = std::ldexp(1.5f, hp.eu + 11);
+        const int ezp = (p == 1) ? hp.eu : ((p - 1 <= m_split) ? hp.ez : kFullForm);
+        k_big_assemble<float4><<<dim3(eb, items), 256, 0, st>>>(a.prm, a.bsys, a.j0, a.wlen, X, Za, a.mstride,
+                                                                hp.ex, ezp);
         count();
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
         float4 *zin = Za, *zout = Zb;
         for (int i = p - 1; i >= 1; --i) {
             if ((err = store(zin, p - 1 - i)) != cudaSuccess) return err;
-            err = (i > m_split) ? mm_launch<float4, 2>(d, items, X, zin, zout, a.mstride, 0, i, st)
-                                : mm_launch<float4, 1>(d, items, X, zin, zout, a.mstride, 0, i, st);
+            err = (i > m_split) ? mm_launch<float4, 2>(d, items, X, zin, zout, a.mstride, 0, i, st,
+                                                       i == m_split + 1 ? mz : 0.f)
+                                : mm_launch<float4, 1>(d, items, X, zin, zout, a.mstride, 0, i, st, i >= 2 ? mz : mu);
             count();
             if (err != cudaSuccess) return err;
             std::swap(zin, zout);
         }
         for (int m = 0; m < n; ++m) {
             if ((err = store(zin, p - 1 + m)) != cudaSuccess) return err;
-            if ((err = mm_launch<float4, 1>(d, items, zin, zin, zout, a.mstride, 1, 0, st)) != cudaSuccess) return err;
+            if ((err = mm_launch<float4, 1>(d, items, zin, zin, zout, a.mstride, 1, 0, st, mu)) != cudaSuccess) return err;
             count();
             std::swap(zin, zout);
         }
@@ -678,7 +713,7 @@ cudaError_t launch_big_expm(const BigArgs<R>& a, int p, int n, int m_split, bool
     C* X = reinterpret_cast<C*>(a.scratch);
     C* Za = X + (size_t)items * a.mstride;
     C* Zb = Za + (size_t)items * a.mstride;
-    k_big_assemble<C><<<dim3(eb, items), 256, 0, st>>>(a.prm, a.bsys, a.j0, a.wlen, X, Za, a.mstride);
+    k_big_assemble<C><<<dim3(eb, items), 256, 0, st>>>(a.prm, a.bsys, a.j0, a.wlen, X, Za, a.mstride, 0, 0);
     count();
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     C *zin = Za, *zout = Zb;
@@ -803,8 +838,8 @@ cudaError_t launch_big_adj_rev(const BigArgs<R>& a, const SysView<R>& sys, const
     return cudaGetLastError();
 }
 
-template cudaError_t launch_big_expm<float>(const BigArgs<float>&, int, int, int, bool, cudaStream_t, int*, float2*);
-template cudaError_t launch_big_expm<double>(const BigArgs<double>&, int, int, int, bool, cudaStream_t, int*, double2*);
+template cudaError_t launch_big_expm<float>(const BigArgs<float>&, const DevParams&, bool, cudaStream_t, int*, float2*);
+template cudaError_t launch_big_expm<double>(const BigArgs<double>&, const DevParams&, bool, cudaStream_t, int*, double2*);
 template cudaError_t launch_big_adj_rev<float>(const BigArgs<float>&, const SysView<float>&, const StateView<float>&,
                                                const float2*, const float2*, double*, int, int, const float2*,
                                                cudaStream_t, int*);

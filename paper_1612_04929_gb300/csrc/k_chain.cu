@@ -73,6 +73,7 @@ __global__ void k_theta(const double* __restrict__ u, int M, int N, const double
         prm->n = 0;
         prm->s = dt;
         prm->err = kErrNonfinite;
+        prm->ex = prm->ez = prm->eu = 0;
         return;
     }
     int n = 0;
@@ -99,6 +100,27 @@ __global__ void k_theta(const double* __restrict__ u, int M, int N, const double
         ++m;
         f *= ts / m;
     }
+    // Grid exponents of the split FP32 exponential (smallest e with 2^e >= bound, 1/16 margin on
+    // the Z bounds).  ||X||_2 <= ||X||_1 <= ts; ||Z_i||_2 <= sum_k ts^k / k! = e^ts; H_j is
+    // Hermitian, so X is normal and ||T^(2^m)||_2 <= (1 + R)^(2^n) with R the truncation
+    // remainder sum_{k > p} ts^k / k! <= ts^(p+1) / (p+1)! / (1 - ts / (p+2)).
+    double rem_t = 1e300;
+    if (ts < p + 2.0) {
+        double fp = 1.0;
+        for (int k = 2; k <= p + 1; ++k) fp *= k;
+        rem_t = pow(ts, (double)(p + 1)) / fp / (1.0 - ts / (p + 2.0));
+    }
+    auto grid_exp = [](double b) {
+        if (!(b > 0.0)) return -100;
+        if (!(b < 1e30)) return 100;
+        int e = 0;
+        const double f = frexp(b, &e);   // b = f 2^e, f in [0.5, 1)
+        if (f == 0.5) --e;
+        return e < -100 ? -100 : (e > 100 ? 100 : e);
+    };
+    prm->ex = grid_exp(ts);
+    prm->ez = grid_exp(1.0625 * exp(ts));
+    prm->eu = grid_exp(1.0625 * exp(ldexp(log1p(rem_t), n)));
     prm->m_split = m;
     prm->theta = theta;
     prm->p = p;

@@ -1,15 +1,18 @@
-// Slice exponential in split (hi + lo) FP32 arithmetic for the FP32 form.
+// Slice exponential in split FP32 arithmetic for the FP32 form.
 //
 // Over long evolutions the FP32 rounding of H_j dt and of the Taylor / squaring products is
 // nearly the same at every slice (the drift H_0 does not change), so it accumulates coherently
 // along the N-slice chain.  The FP32 form therefore evaluates U_j = [T_p(X_j)]^(2^n) (Eqs. 9,
-// 10) with every matrix held as an unevaluated sum hi + lo of two FP32 numbers ("double-float"):
-//   * X_j = -i s H_j is assembled in FP64 from FP64 copies of H_0, H_k, H_det and split,
-//   * each product uses an exact FP32 product (hi*hi and its FMA residual), the two cross
-//     terms hi*lo + lo*hi, and an error-free TwoSum accumulation of the high parts,
-//   * the Horner division by i and the identity shift are done in the same pair arithmetic,
-//   * Horner steps i > m_split use plain FP32 on the hi parts: an error made there reaches T
-//     scaled by ts^m / m! < 2^-6 (m_split is picked with (p, n) from the FP64 norm bound).
+// 10) with every matrix held as an unevaluated sum of two FP32 numbers:
+//   * X_j = -i s H_j is assembled in FP64 from FP64 copies of H_0, H_k, H_det,
+//   * matrices are stored grid-split (qoc_device.cuh): v = v1 + v2, v1 on the power-of-two grid
+//     2^(e - 12) set by a norm bound of the matrix, so that the sums of the grid-part products
+//     are exact FP32 FMAs and only the cross terms a1 b2 + a2 b are rounded (about 2^-36 of
+//     the product's scale), 12 FMAs per complex multiply-add,
+//   * the Horner division by i and the identity shift are done in pair (double-float)
+//     arithmetic on the error-free sum of the two accumulators,
+//   * Horner steps i > m_split use plain FP32: an error made there reaches T scaled by
+//     ts^m / m! < 2^-6 (m_split is picked with (p, n) from the FP64 norm bound).
 // Only the rounded U_j is kept for the propagation (costates and the adjoint stay FP32), plus,
 // for the reverse-mode adjoint, the rounded right operand of every product (ZStore).
 // The same kernel is used for the recomputation in the backward sweep, so the forward and
@@ -18,23 +21,6 @@
 #include "qoc_internal.h"
 
 namespace qoc {
-
-struct DF {        // one real double-float: value = h + l, |l| <= ulp(h) / 2 after renormalisation
-    float h, l;
-};
-
-// hi/lo accumulation of a * b for pair operands; the low-order terms are gathered in lo
-__device__ __forceinline__ void df_mac(float& hi, float& lo, float ah, float al, float bh, float bl) {
-    const float p = ah * bh;
-    float e = fmaf(ah, bh, -p);
-    e = fmaf(ah, bl, e);
-    e = fmaf(al, bh, e);
-    const float t = hi + p;
-    const float bv = t - hi;
-    const float err = (hi - (t - bv)) + (p - bv);
-    hi = t;
-    lo += err + e;
-}
 
 __device__ __forceinline__ void df_norm(float& hi, float& lo) {   // Fast2Sum(hi, lo)
     const float s = hi + lo;
@@ -62,32 +48,44 @@ __device__ __forceinline__ void df_add1(float& hi, float& lo) {
     df_norm(hi, lo);
 }
 
-// split-complex matrices in shared memory: four planes re_h, re_l, im_h, im_l would halve the
-// loads per product; here each element is a float4 (re_h, im_h, re_l, im_l).
+// Split product of two grid-split matrices (float4 = re1, im1, re2, im2 per element):
+// acc[0], acc[1] = exact sums of the grid parts (re, im), acc[2], acc[3] = the cross terms.
 template <int MT>
-__device__ __forceinline__ void mm_df(float (&ar)[MT][MT][2], float (&ai)[MT][MT][2], const float4* __restrict__ A,
-                                      const float4* __restrict__ B, int kd, int LD, int ty, int tx, int G) {
-#pragma unroll 1
+__device__ __forceinline__ void mm_sl(float (&acc)[MT][MT][4], const float4* __restrict__ A,
+                                     const float4* __restrict__ B, int kd, int LD, int ty, int tx, int G) {
+#pragma unroll(MT >= 4 ? 1 : 2)
     for (int k = 0; k < kd; ++k) {
         float4 a[MT], b[MT];
+        float2 bf[MT];
 #pragma unroll
         for (int i = 0; i < MT; ++i) a[i] = A[(ty + G * i) * LD + k];
 #pragma unroll
-        for (int i = 0; i < MT; ++i) b[i] = B[k * LD + tx + G * i];
+        for (int j = 0; j < MT; ++j) {
+            b[j] = B[k * LD + tx + G * j];
+            bf[j] = make_float2(b[j].x + b[j].z, b[j].y + b[j].w);
+        }
 #pragma unroll
         for (int i = 0; i < MT; ++i)
 #pragma unroll
             for (int j = 0; j < MT; ++j) {
-                // (a.x + a.z) + i (a.y + a.w)   times   (b.x + b.z) + i (b.y + b.w)
-                df_mac(ar[i][j][0], ar[i][j][1], a[i].x, a[i].z, b[j].x, b[j].z);
-                df_mac(ar[i][j][0], ar[i][j][1], -a[i].y, -a[i].w, b[j].y, b[j].w);
-                df_mac(ai[i][j][0], ai[i][j][1], a[i].x, a[i].z, b[j].y, b[j].w);
-                df_mac(ai[i][j][0], ai[i][j][1], a[i].y, a[i].w, b[j].x, b[j].z);
+                float* c = acc[i][j];
+                c[0] = fmaf(a[i].x, b[j].x, c[0]);
+                c[0] = fmaf(-a[i].y, b[j].y, c[0]);
+                c[1] = fmaf(a[i].x, b[j].y, c[1]);
+                c[1] = fmaf(a[i].y, b[j].x, c[1]);
+                c[2] = fmaf(a[i].x, b[j].z, c[2]);
+                c[2] = fmaf(-a[i].y, b[j].w, c[2]);
+                c[2] = fmaf(a[i].z, bf[j].x, c[2]);
+                c[2] = fmaf(-a[i].w, bf[j].y, c[2]);
+                c[3] = fmaf(a[i].x, b[j].w, c[3]);
+                c[3] = fmaf(a[i].y, b[j].z, c[3]);
+                c[3] = fmaf(a[i].z, bf[j].y, c[3]);
+                c[3] = fmaf(a[i].w, bf[j].x, c[3]);
             }
     }
 }
 
-// plain FP32 product of the hi parts (the early Horner steps)
+// plain FP32 product for the early Horner steps: A grid-split (X), B in full form (.x, .y)
 template <int MT>
 __device__ __forceinline__ void mm_hi(float2 (&acc)[MT][MT], const float4* __restrict__ A, const float4* __restrict__ B,
                                       int kd, int LD, int ty, int tx, int G) {
@@ -97,7 +95,7 @@ __device__ __forceinline__ void mm_hi(float2 (&acc)[MT][MT], const float4* __res
 #pragma unroll
         for (int i = 0; i < MT; ++i) {
             const float4 v = A[(ty + G * i) * LD + k];
-            a[i] = make_float2(v.x, v.y);
+            a[i] = make_float2(v.x + v.z, v.y + v.w);
         }
 #pragma unroll
         for (int i = 0; i < MT; ++i) {
@@ -111,18 +109,17 @@ __device__ __forceinline__ void mm_hi(float2 (&acc)[MT][MT], const float4* __res
     }
 }
 
-template <int MT>
-__device__ __forceinline__ void df_zero(float (&ar)[MT][MT][2], float (&ai)[MT][MT][2]) {
-#pragma unroll
-    for (int i = 0; i < MT; ++i)
-#pragma unroll
-        for (int j = 0; j < MT; ++j) ar[i][j][0] = ar[i][j][1] = ai[i][j][0] = ai[i][j][1] = 0.f;
+// grid split of an FP64 value (the assembled X_j and Z_p)
+__device__ __forceinline__ void grid_split_d(double v, int e, float& v1, float& v2) {
+    v1 = (float)ldexp(rint(ldexp(v, 12 - e)), e - 12);
+    v2 = (float)(v - (double)v1);
 }
 
-// out = [diag I] + acc / div  (div = 0: no division), zero in the padding
+// out = [diag I] + (grid sums + cross terms) / div  (div = 0: no division), grid-split with
+// the given magic constant; zero in the padding
 template <int MT>
-__device__ __forceinline__ void df_store(float4* __restrict__ out, float (&ar)[MT][MT][2], float (&ai)[MT][MT][2],
-                                         int div, bool add_identity, int d, int LD, int ty, int tx, int G) {
+__device__ __forceinline__ void sl_store(float4* __restrict__ out, float (&acc)[MT][MT][4], int div,
+                                         bool add_identity, float magic, int d, int LD, int ty, int tx, int G) {
 #pragma unroll
     for (int i = 0; i < MT; ++i)
 #pragma unroll
@@ -130,15 +127,16 @@ __device__ __forceinline__ void df_store(float4* __restrict__ out, float (&ar)[M
             const int r = ty + G * i, c = tx + G * j;
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
             if (r < d && c < d) {
-                float rh = ar[i][j][0], rl = ar[i][j][1], ih = ai[i][j][0], il = ai[i][j][1];
-                df_norm(rh, rl);
-                df_norm(ih, il);
+                float rh, rl, ih, il;
+                two_sum(acc[i][j][0], acc[i][j][2], rh, rl);
+                two_sum(acc[i][j][1], acc[i][j][3], ih, il);
                 if (div > 1) {
                     df_div(rh, rl, (float)div);
                     df_div(ih, il, (float)div);
                 }
                 if (add_identity && r == c) df_add1(rh, rl);
-                v = make_float4(rh, ih, rl, il);
+                grid_split(rh, rl, magic, v.x, v.z);
+                grid_split(ih, il, magic, v.y, v.w);
             }
             out[r * LD + c] = v;
         }
@@ -166,7 +164,14 @@ k_expm_fwd_split(const DevParams* __restrict__ prm, SysView<float> sys, const do
     const double2* H0 = H64;
     const double2* Hk = H64 + dd;
     const double2* Hd = H64 + (size_t)(M + 1) * dd;
-    // X = -i s H_j in FP64, split into hi + lo; Z = I + X / p in pair arithmetic
+    // Grid exponents and the form each Z is kept in: the operand of a split product is
+    // grid-split (X with ex; Z_i, i >= 2, with ez; T = Z_1 and its squarings with eu), the
+    // operand of a plain Horner step is the full FP32 value in (.x, .y) with zero (.z, .w).
+    const int m_split = prm->m_split;
+    const int ex = prm->ex, ez = prm->ez, eu = prm->eu;
+    const float mz = grid_magic(ez), mu = grid_magic(eu);
+    // X = -i s H_j in FP64, grid-split; Z_p = I + X / p in the form step p - 1 reads
+    const int ezp = (p == 1) ? eu : ((p - 1 <= m_split) ? ez : 1000);   // 1000: full form
     for (int idx = tid; idx < D * D; idx += blockDim.x) {
         const int a = idx / D, b = idx - a * D;
         float4 x = make_float4(0.f, 0.f, 0.f, 0.f), z = x;
@@ -184,15 +189,16 @@ k_expm_fwd_split(const DevParams* __restrict__ prm, SysView<float> sys, const do
                 h.y = fma(de, hd.y, h.y);
             }
             const double xr = s * h.y, xi = -s * h.x;
-            x.x = (float)xr;
-            x.z = (float)(xr - (double)x.x);
-            x.y = (float)xi;
-            x.w = (float)(xi - (double)x.y);
+            grid_split_d(xr, ex, x.x, x.z);
+            grid_split_d(xi, ex, x.y, x.w);
             const double zr = xr / p + (a == b ? 1.0 : 0.0), zi = xi / p;
-            z.x = (float)zr;
-            z.z = (float)(zr - (double)z.x);
-            z.y = (float)zi;
-            z.w = (float)(zi - (double)z.y);
+            if (ezp == 1000) {
+                z.x = (float)zr;
+                z.y = (float)zi;
+            } else {
+                grid_split_d(zr, ezp, z.x, z.z);
+                grid_split_d(zi, ezp, z.y, z.w);
+            }
         }
         X[a * LD + b] = x;
         Za[a * LD + b] = z;
@@ -200,7 +206,6 @@ k_expm_fwd_split(const DevParams* __restrict__ prm, SysView<float> sys, const do
     __syncthreads();
     float4* zin = Za;
     float4* zout = Zb;
-    const int m_split = prm->m_split;
     float2* zst = (zs.Z && p - 1 + n <= zs.cap) ? zs.Z + ((size_t)e * zs.wmax + jl) * zs.cap * zs.mstride : nullptr;
     // the right operand of product r, rounded to FP32 and conjugate-transposed, for the adjoint
     auto store = [&](int r) {
@@ -231,14 +236,17 @@ k_expm_fwd_split(const DevParams* __restrict__ prm, SysView<float> sys, const do
                     if (r < d && c < d) {
                         v.x = fmaf(acc[a][b].x, ri, (r == c) ? 1.0f : 0.0f);
                         v.y = acc[a][b].y * ri;
+                        if (i == m_split + 1) {   // read by the first split step: grid-split
+                            grid_split(v.x, 0.f, mz, v.x, v.z);
+                            grid_split(v.y, 0.f, mz, v.y, v.w);
+                        }
                     }
                     zout[r * LD + c] = v;
                 }
         } else {
-            float ar[MT][MT][2], ai[MT][MT][2];
-            df_zero<MT>(ar, ai);
-            mm_df<MT>(ar, ai, X, zin, d, LD, ty, tx, G);
-            df_store<MT>(zout, ar, ai, i, true, d, LD, ty, tx, G);
+            float acc[MT][MT][4] = {};
+            mm_sl<MT>(acc, X, zin, d, LD, ty, tx, G);
+            sl_store<MT>(zout, acc, i, true, i >= 2 ? mz : mu, d, LD, ty, tx, G);
         }
         __syncthreads();
         float4* t = zin; zin = zout; zout = t;
@@ -246,10 +254,9 @@ k_expm_fwd_split(const DevParams* __restrict__ prm, SysView<float> sys, const do
     for (int m = 0; m < n; ++m) {             // squaring: Z <- Z Z
         if (zst) store(p - 1 + m);
         if (act) {
-            float ar[MT][MT][2], ai[MT][MT][2];
-            df_zero<MT>(ar, ai);
-            mm_df<MT>(ar, ai, zin, zin, d, LD, ty, tx, G);
-            df_store<MT>(zout, ar, ai, 0, false, d, LD, ty, tx, G);
+            float acc[MT][MT][4] = {};
+            mm_sl<MT>(acc, zin, zin, d, LD, ty, tx, G);
+            sl_store<MT>(zout, acc, 0, false, mu, d, LD, ty, tx, G);
         }
         __syncthreads();
         float4* t = zin; zin = zout; zout = t;

@@ -550,7 +550,7 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
         const int j0 = w * W, wlen = std::min(W, N - j0);
         if (big) {
             int n_l = 0;
-            cudaError_t e = launch_big_expm<R>(big_args(w), hp.p, hp.n, hp.m_split, split, st, &n_l, zbig(w));
+            cudaError_t e = launch_big_expm<R>(big_args(w), hp, split, st, &n_l, zbig(w));
             extra += n_l - 1;
             return e;
         }

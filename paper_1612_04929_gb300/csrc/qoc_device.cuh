@@ -42,9 +42,38 @@ struct DevParams {
     int n;          // squaring count
     int err;        // error bits (kErr*)
     int m_split;    // Horner steps i <= m_split need hi+lo arithmetic in the split exponential
+    // grid exponents of the split FP32 exponential: 2^e bounds the row and column 2-norms of
+    // X (ex), of the Horner matrices Z_i, i >= 2 (ez), and of T and its squarings (eu)
+    int ex, ez, eu;
 };
 
 enum : int { kErrRange = 1, kErrTimeout = 2, kErrNonfinite = 4 };
+
+// ------------------------------------------------------------------------------------------
+// Grid split of FP32 operands (split exponentials of the FP32 form).  A value v = h + l held as
+// two FP32 numbers is stored as v1 + v2: v1 = h rounded to a multiple of g = 2^(e - 12), where
+// 2^e bounds the row / column 2-norms of the matrix, and v2 = (h - v1) + l.  Then v1 has at
+// most 13 significant bits, every product a1 b1 of two grid parts is exact in FP32, and by
+// Cauchy-Schwarz every partial sum of a row-times-column contraction of grid parts stays below
+// 2^24 units of g_a g_b, so it is exact as well: the FMAs sum a1 b1 without rounding, and only
+// the cross terms a1 b2 + a2 b (of relative size 2^-12) are rounded.  If a bound is ever
+// exceeded the grid sums round like plain FP32; nothing else changes.
+// ------------------------------------------------------------------------------------------
+// 1.5 * 2^(e + 11): adding and subtracting it rounds |h| <= 2^e to a multiple of 2^(e - 12)
+__device__ __forceinline__ float grid_magic(int e) { return ldexpf(1.5f, e + 11); }
+
+__device__ __forceinline__ void grid_split(float h, float l, float magic, float& v1, float& v2) {
+    v1 = __fsub_rn(__fadd_rn(h, magic), magic);
+    v2 = __fadd_rn(__fsub_rn(h, v1), l);
+}
+
+// error-free sum: s + e = a + b exactly
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bv = __fsub_rn(s, a);
+    const float av = __fsub_rn(s, bv);
+    e = __fadd_rn(__fsub_rn(a, av), __fsub_rn(b, bv));
+}
 
 // ------------------------------------------------------------------------------------------
 // cp.async (16-byte) helpers for the prefetch rings of the serial propagation kernels.

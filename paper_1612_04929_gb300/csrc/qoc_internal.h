@@ -147,7 +147,7 @@ inline size_t big_scratch_per_item(int d, bool fp64) {
 // zst (or nullptr): store of the p - 1 + n product operands for the reverse-mode adjoint
 // (conjugate transposes, rounded, at zst + (item * (p - 1 + n) + r) * mstride)
 template <typename R>
-cudaError_t launch_big_expm(const BigArgs<R>& a, int p, int n, int m_split, bool split, cudaStream_t st, int* launches,
+cudaError_t launch_big_expm(const BigArgs<R>& a, const DevParams& hp, bool split, cudaStream_t st, int* launches,
                             C_t<R>* zst = nullptr);
 template <typename R>
 cudaError_t launch_big_adj_rev(const BigArgs<R>& a, const SysView<R>& sys, const StateView<R>& sv, const C_t<R>* states,
