@@ -109,10 +109,35 @@ __device__ __forceinline__ void mm_hi(float2 (&acc)[MT][MT], const float4* __res
     }
 }
 
-// grid split of an FP64 value (the assembled X_j and Z_p)
-__device__ __forceinline__ void grid_split_d(double v, int e, float& v1, float& v2) {
-    v1 = (float)ldexp(rint(ldexp(v, 12 - e)), e - 12);
-    v2 = (float)(v - (double)v1);
+// (hi, lo) += (u.x + u.y) (bh + bl), the exact product residual and the rounding of the sum in lo
+__device__ __forceinline__ void pair_fma(float& hi, float& lo, float2 u, float bh, float bl) {
+    const float p = u.x * bh;
+    float e = fmaf(u.x, bh, -p);
+    e = fmaf(u.x, bl, e);
+    e = fmaf(u.y, bh, e);
+    float s, r;
+    two_sum(hi, p, s, r);
+    hi = s;
+    lo += r + e;
+}
+
+// s H_0, s H_1 .. s H_M, s H_det (s = dt / 2^n) as FP32 pairs (re_hi, im_hi, re_lo, im_lo), once
+// per evaluation: the slice assembly above then needs no FP64 arithmetic
+__global__ void k_split_scale(const DevParams* __restrict__ prm, const double2* __restrict__ H64, size_t count,
+                              float4* __restrict__ sH) {
+    const double s = prm->s;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+        const double2 h = H64[i];
+        const double xr = s * h.x, xi = s * h.y;
+        const float rh = (float)xr, ih = (float)xi;
+        sH[i] = make_float4(rh, ih, (float)(xr - (double)rh), (float)(xi - (double)ih));
+    }
+}
+
+cudaError_t launch_split_scale(const DevParams* prm, const double2* H64, size_t count, float4* sH, cudaStream_t st) {
+    const size_t b = (count + 255) / 256;
+    k_split_scale<<<(int)(b < 1024 ? b : 1024), 256, 0, st>>>(prm, H64, count, sH);
+    return cudaGetLastError();
 }
 
 // out = [diag I] + (grid sums + cross terms) / div  (div = 0: no division), grid-split with
@@ -144,11 +169,11 @@ __device__ __forceinline__ void sl_store(float4* __restrict__ out, float (&acc)[
 
 template <int MT>
 __global__ void __launch_bounds__(512)
-k_expm_fwd_split(const DevParams* __restrict__ prm, SysView<float> sys, const double2* __restrict__ H64, int j0,
+k_expm_fwd_split(const DevParams* __restrict__ prm, SysView<float> sys, const float4* __restrict__ sH, int j0,
                  float2* __restrict__ Ubuf, long long ustride, int wmax, ZStore<float> zs, int G) {
     const int D = G * MT, LD = D + 1, SZ = D * LD;
     extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ double us[kMaxControls];
+    __shared__ float2 us[kMaxControls + 1];   // u_kj and delta_e as (hi, lo) pairs
     float4* X = reinterpret_cast<float4*>(smraw);
     float4* Za = X + SZ;
     float4* Zb = Za + SZ;
@@ -156,48 +181,60 @@ k_expm_fwd_split(const DevParams* __restrict__ prm, SysView<float> sys, const do
     const int tid = threadIdx.x, tx = tid % G, ty = tid / G;
     const bool act = tid < G * G;   // the block is rounded up to whole warps
     const int d = sys.d, M = sys.M, p = prm->p, n = prm->n;
-    const double s = prm->s;
-    for (int k = tid; k < M; k += blockDim.x) us[k] = sys.u[(size_t)k * sys.N + j];
+    for (int k = tid; k <= M; k += blockDim.x) {
+        const double v = (k < M) ? sys.u[(size_t)k * sys.N + j] : (sys.delta ? sys.delta[e] : 0.0);
+        const float h = (float)v;
+        us[k] = make_float2(h, (float)(v - (double)h));
+    }
     __syncthreads();
-    const double de = sys.delta ? sys.delta[e] : 0.0;
     const size_t dd = (size_t)d * d;
-    const double2* H0 = H64;
-    const double2* Hk = H64 + dd;
-    const double2* Hd = H64 + (size_t)(M + 1) * dd;
+    const float4* H0 = sH;
+    const float4* Hk = sH + dd;
+    const float4* Hd = sH + (size_t)(M + 1) * dd;
     // Grid exponents and the form each Z is kept in: the operand of a split product is
     // grid-split (X with ex; Z_i, i >= 2, with ez; T = Z_1 and its squarings with eu), the
     // operand of a plain Horner step is the full FP32 value in (.x, .y) with zero (.z, .w).
     const int m_split = prm->m_split;
     const int ex = prm->ex, ez = prm->ez, eu = prm->eu;
     const float mz = grid_magic(ez), mu = grid_magic(eu);
-    // X = -i s H_j in FP64, grid-split; Z_p = I + X / p in the form step p - 1 reads
+    // X = -i s H_j in pair arithmetic from the pairs s H_0, s H_k, s H_det, grid-split;
+    // Z_p = I + X / p in the form step p - 1 reads
     const int ezp = (p == 1) ? eu : ((p - 1 <= m_split) ? ez : 1000);   // 1000: full form
+    const float mx = grid_magic(ex), mzp = grid_magic(ezp == 1000 ? 0 : ezp);
     for (int idx = tid; idx < D * D; idx += blockDim.x) {
         const int a = idx / D, b = idx - a * D;
         float4 x = make_float4(0.f, 0.f, 0.f, 0.f), z = x;
         if (a < d && b < d) {
             const int o = a * d + b;
-            double2 h = H0[o];
+            const float4 h0 = H0[o];
+            float rh = h0.x, rl = h0.z, ih = h0.y, il = h0.w;
             for (int k = 0; k < M; ++k) {
-                const double2 hk = Hk[k * dd + o];
-                h.x = fma(us[k], hk.x, h.x);
-                h.y = fma(us[k], hk.y, h.y);
+                const float4 hk = Hk[k * dd + o];
+                pair_fma(rh, rl, us[k], hk.x, hk.z);
+                pair_fma(ih, il, us[k], hk.y, hk.w);
             }
             if (sys.Hdet) {
-                const double2 hd = Hd[o];
-                h.x = fma(de, hd.x, h.x);
-                h.y = fma(de, hd.y, h.y);
+                const float4 hd = Hd[o];
+                pair_fma(rh, rl, us[M], hd.x, hd.z);
+                pair_fma(ih, il, us[M], hd.y, hd.w);
             }
-            const double xr = s * h.y, xi = -s * h.x;
-            grid_split_d(xr, ex, x.x, x.z);
-            grid_split_d(xi, ex, x.y, x.w);
-            const double zr = xr / p + (a == b ? 1.0 : 0.0), zi = xi / p;
+            df_norm(rh, rl);
+            df_norm(ih, il);
+            // X = -i (s H): re X = im(s H), im X = -re(s H)
+            float xrh = ih, xrl = il, xih = -rh, xil = -rl;
+            grid_split(xrh, xrl, mx, x.x, x.z);
+            grid_split(xih, xil, mx, x.y, x.w);
+            if (p > 1) {
+                df_div(xrh, xrl, (float)p);
+                df_div(xih, xil, (float)p);
+            }
+            if (a == b) df_add1(xrh, xrl);
             if (ezp == 1000) {
-                z.x = (float)zr;
-                z.y = (float)zi;
+                z.x = xrh + xrl;
+                z.y = xih + xil;
             } else {
-                grid_split_d(zr, ezp, z.x, z.z);
-                grid_split_d(zi, ezp, z.y, z.w);
+                grid_split(xrh, xrl, mzp, z.x, z.z);
+                grid_split(xih, xil, mzp, z.y, z.w);
             }
         }
         X[a * LD + b] = x;
@@ -279,13 +316,13 @@ static size_t split_smem(int d) {
 }
 
 template <int MT>
-static cudaError_t launch_split_mt(const DevParams* prm, const SysView<float>& sys, const double2* H64, int j0,
+static cudaError_t launch_split_mt(const DevParams* prm, const SysView<float>& sys, const float4* sH, int j0,
                                    int wlen, int E, float2* Ubuf, long long ustride, int wmax, const ZStore<float>& zs,
                                    int G, cudaStream_t st) {
     const size_t smem = split_smem(sys.d);
     cudaError_t err = cudaFuncSetAttribute(k_expm_fwd_split<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    k_expm_fwd_split<MT><<<dim3(wlen, E), slice_threads(G), smem, st>>>(prm, sys, H64, j0, Ubuf, ustride, wmax, zs, G);
+    k_expm_fwd_split<MT><<<dim3(wlen, E), slice_threads(G), smem, st>>>(prm, sys, sH, j0, Ubuf, ustride, wmax, zs, G);
     return cudaGetLastError();
 }
 
@@ -315,16 +352,16 @@ int split_max_d() {
     return 0;
 }
 
-cudaError_t launch_expm_fwd_split(const DevParams* prm, const SysView<float>& sys, const double2* H64, int j0, int wlen,
+cudaError_t launch_expm_fwd_split(const DevParams* prm, const SysView<float>& sys, const float4* sH, int j0, int wlen,
                                   int E, float2* Ubuf, long long ustride, int wmax, const ZStore<float>& zs,
                                   cudaStream_t st) {
     const SliceTile tl = slice_tile(sys.d);
     if (sys.d > split_max_d()) return cudaErrorInvalidValue;
     switch (tl.MT) {
-        case 1: return launch_split_mt<1>(prm, sys, H64, j0, wlen, E, Ubuf, ustride, wmax, zs, tl.G, st);
-        case 2: return launch_split_mt<2>(prm, sys, H64, j0, wlen, E, Ubuf, ustride, wmax, zs, tl.G, st);
-        case 3: return launch_split_mt<3>(prm, sys, H64, j0, wlen, E, Ubuf, ustride, wmax, zs, tl.G, st);
-        case 4: return launch_split_mt<4>(prm, sys, H64, j0, wlen, E, Ubuf, ustride, wmax, zs, tl.G, st);
+        case 1: return launch_split_mt<1>(prm, sys, sH, j0, wlen, E, Ubuf, ustride, wmax, zs, tl.G, st);
+        case 2: return launch_split_mt<2>(prm, sys, sH, j0, wlen, E, Ubuf, ustride, wmax, zs, tl.G, st);
+        case 3: return launch_split_mt<3>(prm, sys, sH, j0, wlen, E, Ubuf, ustride, wmax, zs, tl.G, st);
+        case 4: return launch_split_mt<4>(prm, sys, sH, j0, wlen, E, Ubuf, ustride, wmax, zs, tl.G, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -147,6 +147,7 @@ struct qoc_ctx {
 
     DevBuf H64, HR, dDelta, norms, psiTR, pathR, fmask, colw, ckpt, Ubuf, states, Gbuf, src, carry, Oj, C5j, Ofin,
         gpart, prm, u_h, grad_h, out_h, scratch, tc_planes;
+    DevBuf sH;                           // s H_0 .. s H_det as FP32 pairs (per-slice split exponential)
     // segmented scan: segment products (two wave sets), tree levels, scan states, costate carries
     DevBuf Pbuf, lv0, lv1, scanst, hbuf, Ybuf;
     DevBuf Zbuf;                         // product operands for the reverse-mode adjoint (per-slice path)
@@ -164,7 +165,7 @@ struct qoc_ctx {
     size_t device_bytes() const {
         const DevBuf* all[] = {&H64, &HR, &dDelta, &norms, &psiTR, &pathR, &fmask, &colw, &ckpt, &Ubuf, &states,
                                &Gbuf, &src, &carry, &Oj, &C5j, &Ofin, &gpart, &prm, &u_h, &grad_h, &out_h, &scratch,
-                               &tc_planes, &Pbuf, &lv0, &lv1, &scanst, &hbuf, &Ybuf, &Zbuf, &Zbig};
+                               &tc_planes, &Pbuf, &lv0, &lv1, &scanst, &hbuf, &Ybuf, &Zbuf, &Zbig, &sH};
         size_t s = 0;
         for (auto* b : all) s += b->bytes;
         return s;
@@ -321,6 +322,7 @@ void plan_impl(qoc_ctx* c) {
     const size_t dd = (size_t)d * d;
     A(c->HR, (M + 2) * dd * cs, "alloc H");
     check_cuda(c, launch_convert<R>(c->H64.as<double2>(), c->HR.as<C>(), (M + 2) * dd, st), "convert H");
+    if (split_exp<R>(c) && c->path_kind == 0) A(c->sH, (M + 2) * dd * sizeof(float4), "alloc sH");
     // costs
     std::vector<int> mask(d, 0);
     for (int f : c->forb) mask[f] = 1;
@@ -497,6 +499,12 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
     } else {
         ++launches;
     }
+    if constexpr (sizeof(R) == 4) {
+        if (split_exp<R>(c) && c->path_kind == 0) {   // s H_k pairs for this evaluation's (p, n)
+            B(st);
+            L(launch_split_scale(prm, c->H64.as<double2>(), (M + 2) * dd, c->sH.as<float4>(), st), "theta", st);
+        }
+    }
     rec(ev_fork, st);
     wait(sx, ev_fork);
     // slice exponentials: split hi+lo FP32 for the FP32 form (unless disabled), else plain
@@ -556,7 +564,7 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
         }
         if constexpr (sizeof(R) == 4) {
             if (split)
-                return launch_expm_fwd_split(prm, sys, c->H64.as<double2>(), j0, wlen, E, Ub(w), c->ustride, W,
+                return launch_expm_fwd_split(prm, sys, c->sH.as<float4>(), j0, wlen, E, Ub(w), c->ustride, W,
                                              zstore(w), st);
         }
         return launch_expm_fwd_fused<R>(prm, sys, j0, wlen, E, Ub(w), c->ustride, W, zstore(w), st);

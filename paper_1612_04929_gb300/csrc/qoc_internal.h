@@ -117,7 +117,10 @@ cudaError_t launch_expm_adj_fused(const DevParams* prm, const SysView<R>& sys, c
 
 // ---- split hi+lo FP32 slice exponential (FP32 form) ----
 int split_max_d();
-cudaError_t launch_expm_fwd_split(const DevParams* prm, const SysView<float>& sys, const double2* H64, int j0, int wlen,
+// sH: s H_0, s H_1 .. s H_M, s H_det as FP32 pairs, written by launch_split_scale after the
+// (p, n) pick of the evaluation
+cudaError_t launch_split_scale(const DevParams* prm, const double2* H64, size_t count, float4* sH, cudaStream_t st);
+cudaError_t launch_expm_fwd_split(const DevParams* prm, const SysView<float>& sys, const float4* sH, int j0, int wlen,
                                   int E, float2* Ubuf, long long ustride, int wmax, const ZStore<float>& zs,
                                   cudaStream_t st);
 
