@@ -33,13 +33,24 @@ namespace qoc {
 template <typename C, int MT>
 __device__ __forceinline__ void mm_acc(C (&acc)[MT][MT], const C* __restrict__ A,
                                        const C* __restrict__ B, int kd, int LD, int ty, int tx, int G) {
+    // one pointer per operand row / column: A rows advance by k, B columns step down one row
+    const C* pa[MT];
+    const C* pb[MT];
+#pragma unroll
+    for (int i = 0; i < MT; ++i) {
+        pa[i] = A + (ty + G * i) * LD;
+        pb[i] = B + tx + G * i;
+    }
 #pragma unroll 2
     for (int k = 0; k < kd; ++k) {
         C a[MT], b[MT];
 #pragma unroll
-        for (int i = 0; i < MT; ++i) a[i] = A[(ty + G * i) * LD + k];
+        for (int i = 0; i < MT; ++i) a[i] = pa[i][k];
 #pragma unroll
-        for (int i = 0; i < MT; ++i) b[i] = B[k * LD + tx + G * i];
+        for (int i = 0; i < MT; ++i) {
+            b[i] = *pb[i];
+            pb[i] += LD;
+        }
 #pragma unroll
         for (int i = 0; i < MT; ++i)
 #pragma unroll
@@ -106,12 +117,11 @@ __device__ __forceinline__ void store_acc(C* __restrict__ out, const C (&acc)[MT
 // dst (d x d, global) = conjugate transpose of the d x d block of src (shared, leading dim LD)
 template <typename C>
 __device__ __forceinline__ void store_ct(C* __restrict__ dst, const C* __restrict__ src, int d, int LD) {
-    for (int idx = threadIdx.x; idx < d * d; idx += blockDim.x) {
-        const int a = idx / d, b = idx - a * d;
+    for_rc(d, d, [&](int idx, int a, int b) {
         C v = src[b * LD + a];
         v.y = -v.y;
         dst[idx] = v;
-    }
+    });
 }
 
 // Assemble H_j (+ delta_e Hdet) and write X = -i s H into padded shared memory (rows/cols >= d
@@ -403,29 +413,28 @@ k_expm_adj_rev(const DevParams* __restrict__ prm, SysView<R> sys, StateView<R> s
     __syncthreads();
     const C* zst = zs.Z + ((size_t)e * zs.wmax + jl) * zs.cap * zs.mstride;
     // the stored conjugate transpose of the right operand of product r; the products run in
-    // reverse, r = p - 2 + n down to 0, and r - 1 is fetched while r is multiplied
+    // reverse, r = p - 2 + n down to 0, and r - 1 is fetched while r is multiplied.  One barrier
+    // per product: after it the copy of r is visible to every thread and every thread has
+    // finished product r + 1, so its operand slot takes the copy of r - 1 and its input
+    // matrix becomes the output of r.
     auto issue = [&](int r) {
         if (r >= 0) {
             const C* src = zst + (size_t)r * zs.mstride;
-            for (int idx = tid; idx < d * d; idx += blockDim.x) {
-                const int a = idx / d, b = idx - a * d;
-                cp_async_elem(&SN[a * LD + b], &src[idx]);
-            }
+            for_rc(d, d, [&](int idx, int a, int b) { cp_async_elem(&SN[a * LD + b], &src[idx]); });
         }
         cp_async_commit();
     };
-    auto next = [&](int r) {   // operand r into SB, r - 1 on its way into SN
-        C* t = SB; SB = SN; SN = t;   // SN (now SB) received r; SB (now SN) is free
+    auto next = [&](int r) {   // wait for operand r (in SN), make it SB, start r - 1 into the old SB
+        cp_async_wait<0>();
+        __syncthreads();
+        C* t = SB; SB = SN; SN = t;
         issue(r - 1);
-        cp_async_wait<1>();
     };
     issue(p - 2 + n);          // the first product's operand into SN
-    __syncthreads();
     C* zb = ZA;
     C* zo = ZB;
     for (int m = n - 1; m >= 0; --m) {          // squarings in reverse
         next(p - 1 + m);
-        __syncthreads();
         if (act) {
             C acc[MT][MT];
             zero_acc<C, MT>(acc);
@@ -433,14 +442,12 @@ k_expm_adj_rev(const DevParams* __restrict__ prm, SysView<R> sys, StateView<R> s
             mm_acc<C, MT>(acc, SB, zb, d, LD, ty, tx, G);      // S^dag Sbar
             store_acc<C, R, MT>(zo, acc, R(1), R(0), d, LD, ty, tx, G);
         }
-        __syncthreads();
         C* t = zb; zb = zo; zo = t;
     }
     C xb[MT][MT];                               // Xbar, accumulated over the Horner steps
     zero_acc<C, MT>(xb);
     for (int i = 1; i <= p - 1; ++i) {          // Horner steps in reverse
         next(p - 1 - i);
-        __syncthreads();
         if (act) {
             const R ri = R(1) / R(i);
             C acc[MT][MT];
@@ -457,9 +464,10 @@ k_expm_adj_rev(const DevParams* __restrict__ prm, SysView<R> sys, StateView<R> s
             mm_acc<C, MT>(acc, XH, zb, d, LD, ty, tx, G);      // X^dag Zbar_i
             store_acc<C, R, MT>(zo, acc, ri, R(0), d, LD, ty, tx, G);
         }
-        __syncthreads();
         C* t = zb; zb = zo; zo = t;
     }
+    cp_async_wait<0>();
+    __syncthreads();
     // Z_p = I + X / p: Xbar += Zbar_p / p; then dC/du_{k,j} = s sum_ab (Xbar_re Hk_im - Xbar_im Hk_re)
     const R rp = R(1) / R(p);
     if (act) {

@@ -48,58 +48,29 @@ __device__ __forceinline__ void df_add1(float& hi, float& lo) {
     df_norm(hi, lo);
 }
 
-// Split product of two grid-split matrices (float4 = re1, im1, re2, im2 per element):
-// acc[0], acc[1] = exact sums of the grid parts (re, im), acc[2], acc[3] = the cross terms.
-template <int MT>
-__device__ __forceinline__ void mm_sl(float (&acc)[MT][MT][4], const float4* __restrict__ A,
-                                     const float4* __restrict__ B, int kd, int LD, int ty, int tx, int G) {
-#pragma unroll(MT >= 4 ? 1 : 2)
-    for (int k = 0; k < kd; ++k) {
-        float4 a[MT], b[MT];
-        float2 bf[MT];
-#pragma unroll
-        for (int i = 0; i < MT; ++i) a[i] = A[(ty + G * i) * LD + k];
-#pragma unroll
-        for (int j = 0; j < MT; ++j) {
-            b[j] = B[k * LD + tx + G * j];
-            bf[j] = make_float2(b[j].x + b[j].z, b[j].y + b[j].w);
-        }
-#pragma unroll
-        for (int i = 0; i < MT; ++i)
-#pragma unroll
-            for (int j = 0; j < MT; ++j) {
-                float* c = acc[i][j];
-                c[0] = fmaf(a[i].x, b[j].x, c[0]);
-                c[0] = fmaf(-a[i].y, b[j].y, c[0]);
-                c[1] = fmaf(a[i].x, b[j].y, c[1]);
-                c[1] = fmaf(a[i].y, b[j].x, c[1]);
-                c[2] = fmaf(a[i].x, b[j].z, c[2]);
-                c[2] = fmaf(-a[i].y, b[j].w, c[2]);
-                c[2] = fmaf(a[i].z, bf[j].x, c[2]);
-                c[2] = fmaf(-a[i].w, bf[j].y, c[2]);
-                c[3] = fmaf(a[i].x, b[j].w, c[3]);
-                c[3] = fmaf(a[i].y, b[j].z, c[3]);
-                c[3] = fmaf(a[i].z, bf[j].y, c[3]);
-                c[3] = fmaf(a[i].w, bf[j].x, c[3]);
-            }
-    }
-}
-
 // plain FP32 product for the early Horner steps: A grid-split (X), B in full form (.x, .y)
 template <int MT>
 __device__ __forceinline__ void mm_hi(float2 (&acc)[MT][MT], const float4* __restrict__ A, const float4* __restrict__ B,
                                       int kd, int LD, int ty, int tx, int G) {
+    const float4* pa[MT];
+    const float4* pb[MT];
+#pragma unroll
+    for (int i = 0; i < MT; ++i) {
+        pa[i] = A + (ty + G * i) * LD;
+        pb[i] = B + tx + G * i;
+    }
 #pragma unroll 2
     for (int k = 0; k < kd; ++k) {
         float2 a[MT], b[MT];
 #pragma unroll
         for (int i = 0; i < MT; ++i) {
-            const float4 v = A[(ty + G * i) * LD + k];
+            const float4 v = pa[i][k];
             a[i] = make_float2(v.x + v.z, v.y + v.w);
         }
 #pragma unroll
         for (int i = 0; i < MT; ++i) {
-            const float4 v = B[k * LD + tx + G * i];
+            const float4 v = *pb[i];
+            pb[i] += LD;
             b[i] = make_float2(v.x, v.y);
         }
 #pragma unroll
@@ -247,11 +218,10 @@ k_expm_fwd_split(const DevParams* __restrict__ prm, SysView<float> sys, const fl
     // the right operand of product r, rounded to FP32 and conjugate-transposed, for the adjoint
     auto store = [&](int r) {
         float2* dst = zst + (size_t)r * zs.mstride;
-        for (int idx = tid; idx < d * d; idx += blockDim.x) {
-            const int a = idx / d, b = idx - a * d;
+        for_rc(d, d, [&](int idx, int a, int b) {
             const float4 v = zin[b * LD + a];
             dst[idx] = make_float2(v.x + v.z, -(v.y + v.w));
-        }
+        });
     };
     for (int i = p - 1; i >= 1; --i) {        // Horner: Z <- I + X Z / i
         if (zst) store(p - 1 - i);

@@ -10,9 +10,12 @@
 // level l multiplies neighbouring partial products of level l - 1 (the later one on the left),
 // ceil(log2(seg)) batched launches in all, each over every (member, segment, pair) of the wave.
 // The partial products and P_z are carried in extended precision (the hi + lo FP32 pair of the
-// FP32 form, FP64 in the FP64 form), like the block that the recursions carry, so the scan adds
-// no rounding of its own beyond the pair's.
+// FP32 form, FP64 in the FP64 form), like the block that the recursions carry.  In the FP32 form
+// the per-CTA products (d <= 68) multiply grid-split factors (qoc_device.cuh; the factors are
+// products of U_j, whose norms the exponent eu bounds), so the grid parts sum exactly and only
+// the cross terms are rounded, about 2^-36 of the product's scale.
 #include <algorithm>
+#include <type_traits>
 
 #include "qoc_device.cuh"
 #include "qoc_internal.h"
@@ -150,26 +153,38 @@ k_seg_mm(SegProdArgs<R> a, int level, const EI* __restrict__ src, size_t src_ite
 
 // The same level for d <= 68: one CTA per product, both factors in shared memory (padded to
 // D = G MT with leading dimension D + 1), thread (ty, tx) of a G x G grid owning the MT x MT
-// outputs (ty + G a, tx + G b) as in the per-slice kernels.  Level 1 keeps its plain factors
-// (exact products, TwoSum accumulation); later levels multiply carried pairs.
-__device__ __forceinline__ void kmac_any(float4& acc, const float4 a, const float4 b) { kmac2(acc, a, b); }
-__device__ __forceinline__ void kmac_any(float4& acc, const float2 a, const float2 b) {
-    mac_pair(acc.x, acc.z, a.x, 0.f, b.x, 0.f);
-    mac_pair(acc.x, acc.z, -a.y, 0.f, b.y, 0.f);
-    mac_pair(acc.y, acc.w, a.x, 0.f, b.y, 0.f);
-    mac_pair(acc.y, acc.w, a.y, 0.f, b.x, 0.f);
-}
+// outputs (ty + G a, tx + G b) as in the per-slice kernels.  FP32 form: both factors grid-split
+// on staging (level 1 from the plain U_j, later levels from the carried pairs), the result the
+// error-free sum of the grid sums and the cross terms; FP64 form: plain FP64 products.
+
 __device__ __forceinline__ void kmac_any(double2& acc, const double2 a, const double2 b) { cfma(acc, a, b); }
+
+// a factor element as grid-split float4 (re1, im1, re2, im2): from a plain FP32 value (exact
+// split) or from a carried (hi, lo) pair
+__device__ __forceinline__ float4 to_grid(const float2 v, float magic) {
+    float4 o;
+    grid_split(v.x, 0.f, magic, o.x, o.z);
+    grid_split(v.y, 0.f, magic, o.y, o.w);
+    return o;
+}
+__device__ __forceinline__ float4 to_grid(const float4 v, float magic) {
+    float4 o;
+    grid_split(v.x, v.z, magic, o.x, o.z);
+    grid_split(v.y, v.w, magic, o.y, o.w);
+    return o;
+}
 
 template <typename R, typename EI, int MT>
 __global__ void __launch_bounds__(512)
 k_seg_mm_small(SegProdArgs<R> a, int level, const EI* __restrict__ src, size_t src_item, size_t src_seg, size_t src_e,
                K_t<R>* __restrict__ dst, int cap, int G) {
     using K = K_t<R>;
+    constexpr bool kGrid = std::is_same<K, float4>::value;   // FP32 form: grid-split factors
+    using SE = std::conditional_t<kGrid, float4, EI>;         // staged element
     extern __shared__ __align__(16) unsigned char smraw[];
     const int d = a.d, D = G * MT, LD = D + 1;
-    EI* As = reinterpret_cast<EI*>(smraw);
-    EI* Bs = As + (size_t)D * LD;
+    SE* As = reinterpret_cast<SE*>(smraw);
+    SE* Bs = As + (size_t)D * LD;
     const int q = blockIdx.x;
     const int e = q / (a.nzmax * cap);
     const int z = (q / cap) % a.nzmax;
@@ -189,38 +204,62 @@ k_seg_mm_small(SegProdArgs<R> a, int level, const EI* __restrict__ src, size_t s
         for (int idx = tid; idx < d * d; idx += blockDim.x) out[idx] = widen(Bm[idx]);
         return;
     }
-    for (int idx = tid; idx < d * d; idx += blockDim.x) {
-        const int r = idx / d, c = idx - r * d;
-        As[r * LD + c] = Am[idx];
-        Bs[r * LD + c] = Bm[idx];
+    if constexpr (kGrid) {
+        const float mg = grid_magic(a.prm ? a.prm->eu : 1);
+        for_rc(d, d, [&](int idx, int r, int c) {
+            As[r * LD + c] = to_grid(Am[idx], mg);
+            Bs[r * LD + c] = to_grid(Bm[idx], mg);
+        });
+    } else {
+        for_rc(d, d, [&](int idx, int r, int c) {
+            As[r * LD + c] = Am[idx];
+            Bs[r * LD + c] = Bm[idx];
+        });
     }
     __syncthreads();
     if (tid >= G * G) return;   // the block is rounded up to whole warps; no barrier follows
     const int tx = tid % G, ty = tid / G;
-    K acc[MT][MT];
-#pragma unroll
-    for (int x = 0; x < MT; ++x)
-#pragma unroll
-        for (int y = 0; y < MT; ++y) acc[x][y] = kz<K>();
-#pragma unroll 2
-    for (int k = 0; k < d; ++k) {
-        EI av[MT], bv[MT];
-#pragma unroll
-        for (int x = 0; x < MT; ++x) av[x] = As[(ty + G * x) * LD + k];
-#pragma unroll
-        for (int y = 0; y < MT; ++y) bv[y] = Bs[k * LD + tx + G * y];
+    if constexpr (kGrid) {
+        float acc[MT][MT][4] = {};
+        mm_sl<MT>(acc, As, Bs, d, LD, ty, tx, G);
 #pragma unroll
         for (int x = 0; x < MT; ++x)
 #pragma unroll
-            for (int y = 0; y < MT; ++y) kmac_any(acc[x][y], av[x], bv[y]);
-    }
+            for (int y = 0; y < MT; ++y) {
+                const int r = ty + G * x, c = tx + G * y;
+                if (r < d && c < d) {
+                    float4 o;
+                    two_sum(acc[x][y][0], acc[x][y][2], o.x, o.z);
+                    two_sum(acc[x][y][1], acc[x][y][3], o.y, o.w);
+                    out[(size_t)r * d + c] = o;
+                }
+            }
+    } else {
+        K acc[MT][MT];
 #pragma unroll
-    for (int x = 0; x < MT; ++x)
+        for (int x = 0; x < MT; ++x)
 #pragma unroll
-        for (int y = 0; y < MT; ++y) {
-            const int r = ty + G * x, c = tx + G * y;
-            if (r < d && c < d) out[(size_t)r * d + c] = knorm2(acc[x][y]);
+            for (int y = 0; y < MT; ++y) acc[x][y] = kz<K>();
+#pragma unroll 2
+        for (int k = 0; k < d; ++k) {
+            EI av[MT], bv[MT];
+#pragma unroll
+            for (int x = 0; x < MT; ++x) av[x] = As[(ty + G * x) * LD + k];
+#pragma unroll
+            for (int y = 0; y < MT; ++y) bv[y] = Bs[k * LD + tx + G * y];
+#pragma unroll
+            for (int x = 0; x < MT; ++x)
+#pragma unroll
+                for (int y = 0; y < MT; ++y) kmac_any(acc[x][y], av[x], bv[y]);
         }
+#pragma unroll
+        for (int x = 0; x < MT; ++x)
+#pragma unroll
+            for (int y = 0; y < MT; ++y) {
+                const int r = ty + G * x, c = tx + G * y;
+                if (r < d && c < d) out[(size_t)r * d + c] = knorm2(acc[x][y]);
+            }
+    }
 }
 
 // P_z and P_z^dag (carried) from item 0 of the last level (or from U_a when seg = 1)
@@ -247,7 +286,8 @@ template <typename R, typename EI, int MT>
 cudaError_t small_level(const SegProdArgs<R>& a, int level, const EI* src, size_t s_item, size_t s_seg, size_t s_e,
                         K_t<R>* dst, int cap, int G, cudaStream_t st) {
     const int D = G * MT;
-    const size_t smem = 2 * (size_t)D * (D + 1) * sizeof(EI);
+    const size_t esz = sizeof(K_t<R>) == sizeof(float4) && sizeof(R) == 4 ? sizeof(float4) : sizeof(EI);
+    const size_t smem = 2 * (size_t)D * (D + 1) * esz;
     cudaError_t err =
         cudaFuncSetAttribute(k_seg_mm_small<R, EI, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;

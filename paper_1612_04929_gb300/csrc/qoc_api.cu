@@ -612,12 +612,12 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
     const size_t p_set = (size_t)E * nzmax * c->ustride;
     auto Pb = [&](int w) { return c->Pbuf.as<K>() + (w & 1) * p_set; };
     auto Yb = [&](int w) { return c->Ybuf.as<K>() + (w & 1) * (size_t)E * nzmax * slice; };
-    auto seg_products = [&](int w) -> cudaError_t {
+    auto seg_products = [&](int w, cudaStream_t s) -> cudaError_t {
         const int j0 = w * W;
         SegProdArgs<R> a{d, E, std::min(W, N - j0), seg, nzmax, Ub(w), c->ustride, W,
-                         c->lv0.as<K>(), c->lv1.as<K>(), dd, Pb(w)};
+                         c->lv0.as<K>(), c->lv1.as<K>(), dd, Pb(w), prm};
         int n_l = 0;
-        cudaError_t e = launch_seg_products<R>(a, st, &n_l);
+        cudaError_t e = launch_seg_products<R>(a, s, &n_l);
         extra += n_l - 1;
         return e;
     };
@@ -689,8 +689,10 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
             L(expm_adj(w), "expm_adj", st);
         }
     } else {
-        // ---- forward: exponentials and segment products on st; the scan over segments
-        //      (checkpoints) on sx; replay of every segment and the per-slice costs on st ----
+        // ---- forward: exponentials on st; the segment products and the scan over segments
+        //      (checkpoints) on sx, overlapping the next wave's exponentials; replay of every
+        //      segment and the per-slice costs on st.  The tree buffers are used on sx only
+        //      until the last scan, which st waits for before any backward recomputation. ----
         cudaEvent_t* ev_scan = ev_fwd;
         auto replay_costs = [&](int w) {
             const int j0 = w * W, wlen = std::min(W, N - j0);
@@ -707,10 +709,10 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
             const int nz = (wlen + seg - 1) / seg;
             B(st);
             L(expm_fwd(w), "expm_fwd", st);
-            B(st);
-            L(seg_products(w), "seg_products", st);
             rec(ev_exp[w], st);
             wait(sx, ev_exp[w]);
+            B(sx);
+            L(seg_products(w, sx), "seg_products", sx);
             B(sx);
             L(launch_chain<R>(ChainArgs<R>{d, sv, nz, 1, 0, E, c->ckpt.as<K>(), (size_t)c->nseg_total * slice, j0 / seg,
                                            c->nseg_total, nullptr, c->ustride, nzmax, c->scanst.as<C>(), Pb(w)},
@@ -770,7 +772,7 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
                     B(st);
                     L(expm_fwd(w - 1), "expm_fwd (recompute)", st);
                     B(st);
-                    L(seg_products(w - 1), "seg_products", st);
+                    L(seg_products(w - 1, st), "seg_products", st);
                     B(st);
                     L(launch_chain<R>(chain_args(w - 1, 1), st), "chain (replay)", st);
                 }

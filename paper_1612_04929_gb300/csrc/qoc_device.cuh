@@ -50,6 +50,26 @@ struct DevParams {
 enum : int { kErrRange = 1, kErrTimeout = 2, kErrNonfinite = 4 };
 
 // ------------------------------------------------------------------------------------------
+// Block-strided loop over a rows x cols array, f(idx, r, c) with r = idx / cols, c = idx % cols:
+// the row and column are stepped, not divided out per element.
+// ------------------------------------------------------------------------------------------
+template <typename F>
+__device__ __forceinline__ void for_rc(int rows, int cols, F f) {
+    const int n = rows * cols, step = blockDim.x;
+    const int sr = step / cols, sc = step - sr * cols;
+    int r = threadIdx.x / cols, c = threadIdx.x - r * cols;
+    for (int idx = threadIdx.x; idx < n; idx += step) {
+        f(idx, r, c);
+        r += sr;
+        c += sc;
+        if (c >= cols) {
+            c -= cols;
+            ++r;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
 // Grid split of FP32 operands (split exponentials of the FP32 form).  A value v = h + l held as
 // two FP32 numbers is stored as v1 + v2: v1 = h rounded to a multiple of g = 2^(e - 12), where
 // 2^e bounds the row / column 2-norms of the matrix, and v2 = (h - v1) + l.  Then v1 has at
@@ -73,6 +93,51 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     const float bv = __fsub_rn(s, a);
     const float av = __fsub_rn(s, bv);
     e = __fadd_rn(__fsub_rn(a, av), __fsub_rn(b, bv));
+}
+
+// Split product of two grid-split matrices (float4 = re1, im1, re2, im2 per element):
+// acc[0], acc[1] = exact sums of the grid parts (re, im), acc[2], acc[3] = the cross terms.
+template <int MT>
+__device__ __forceinline__ void mm_sl(float (&acc)[MT][MT][4], const float4* __restrict__ A,
+                                     const float4* __restrict__ B, int kd, int LD, int ty, int tx, int G) {
+    const float4* pa[MT];
+    const float4* pb[MT];
+#pragma unroll
+    for (int i = 0; i < MT; ++i) {
+        pa[i] = A + (ty + G * i) * LD;
+        pb[i] = B + tx + G * i;
+    }
+#pragma unroll(MT >= 4 ? 1 : 2)
+    for (int k = 0; k < kd; ++k) {
+        float4 a[MT], b[MT];
+        float2 bf[MT];
+#pragma unroll
+        for (int i = 0; i < MT; ++i) a[i] = pa[i][k];
+#pragma unroll
+        for (int j = 0; j < MT; ++j) {
+            b[j] = *pb[j];
+            pb[j] += LD;
+            bf[j] = make_float2(b[j].x + b[j].z, b[j].y + b[j].w);
+        }
+#pragma unroll
+        for (int i = 0; i < MT; ++i)
+#pragma unroll
+            for (int j = 0; j < MT; ++j) {
+                float* c = acc[i][j];
+                c[0] = fmaf(a[i].x, b[j].x, c[0]);
+                c[0] = fmaf(-a[i].y, b[j].y, c[0]);
+                c[1] = fmaf(a[i].x, b[j].y, c[1]);
+                c[1] = fmaf(a[i].y, b[j].x, c[1]);
+                c[2] = fmaf(a[i].x, b[j].z, c[2]);
+                c[2] = fmaf(-a[i].y, b[j].w, c[2]);
+                c[2] = fmaf(a[i].z, bf[j].x, c[2]);
+                c[2] = fmaf(-a[i].w, bf[j].y, c[2]);
+                c[3] = fmaf(a[i].x, b[j].w, c[3]);
+                c[3] = fmaf(a[i].y, b[j].z, c[3]);
+                c[3] = fmaf(a[i].z, bf[j].y, c[3]);
+                c[3] = fmaf(a[i].w, bf[j].x, c[3]);
+            }
+    }
 }
 
 // ------------------------------------------------------------------------------------------

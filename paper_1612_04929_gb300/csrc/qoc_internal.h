@@ -285,6 +285,7 @@ struct SegProdArgs {
     K_t<R>* lv1;
     size_t mstride;
     K_t<R>* P;
+    const DevParams* prm;   // grid exponent eu of the FP32 form (bound on the norms of U_j)
 };
 template <typename R> cudaError_t launch_seg_products(const SegProdArgs<R>& a, cudaStream_t st, int* launches);
 template <typename R>

@@ -197,13 +197,20 @@ def test_sweep_forms_match_oracle(precision, case, layout, sweep):
     check(prob, precision, sweep=sweep, **layout)
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-7)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-6)])
 def test_scan_agrees_with_serial_sweep(precision, tol):
-    """The segment products P_z are carried in the same extended precision as the propagated
-    block, so the two forms differ only in where that precision's roundings fall."""
+    """Both sweep layouts meet the oracle bound, and they agree with each other to `tol`.  FP64:
+    the two differ only in where FP64 roundings fall.  FP32: the serial sweep carries the block
+    as an hi + lo pair (~2^-48), the scan's segment products P_z are grid-split products whose
+    cross terms round at ~2^-36 of their scale, and the FP32-rounded states that the adjoint
+    reads then differ by a few ulps here and there, so the gradients agree to a few FP32 ulps."""
     prob = sy.random_problem(d=12, M=2, N=150, S=3, seed=316, nF=2, path=True, E=2)
     a = run(prob, precision, sweep="serial", ckpt_stride=10, wave_slices=40)
     b = run(prob, precision, sweep="scan", ckpt_stride=10, wave_slices=40)
+    c_ref, g_ref, _ = orc.cost_and_grad(prob, prob.u)
+    for r in (a, b):
+        assert abs(r[0] - c_ref) <= TOL[precision] * abs(c_ref)
+        assert rel(r[1], g_ref) <= TOL[precision]
     assert abs(a[0] - b[0]) <= tol * abs(a[0])
     assert np.max(np.abs(a[1] - b[1])) <= tol * np.max(np.abs(a[1]))
 
