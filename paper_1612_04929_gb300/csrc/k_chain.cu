@@ -11,6 +11,8 @@
 //                         option in place of the exact adjoint of the truncated exponential.
 #include <math.h>
 
+#include <algorithm>
+
 #include "qoc_device.cuh"
 #include "qoc_internal.h"
 
@@ -81,14 +83,16 @@ __global__ void k_theta(const double* __restrict__ u, int M, int N, const double
     if (n_override >= 0) n = n_override;
     const double ts = ldexp(theta, -n);
     int p = 1;
-    double fact = 2.0;   // (p + 1)!
+    double fact = 2.0;     // (p + 1)!
+    double pw = ts * ts;   // ts^(p + 1)
     int err = 0;
     for (;;) {
-        const double rem = ldexp(1.0, n) * pow(ts, (double)(p + 1)) / fact / (1.0 - ts / (p + 2));
+        const double rem = ldexp(pw, n) / fact / (1.0 - ts / (p + 2));
         if (rem <= tol) break;
         if (p >= kPMax) { err |= kErrRange; break; }
         ++p;
         fact *= (double)(p + 1);
+        pw *= ts;
     }
     if (p_override >= 1) { p = p_override; err &= ~kErrRange; }
     // A rounding error e made in Horner step i + 1 reaches T = Z_1 multiplied by at most
@@ -106,9 +110,12 @@ __global__ void k_theta(const double* __restrict__ u, int M, int N, const double
     // remainder sum_{k > p} ts^k / k! <= ts^(p+1) / (p+1)! / (1 - ts / (p+2)).
     double rem_t = 1e300;
     if (ts < p + 2.0) {
-        double fp = 1.0;
-        for (int k = 2; k <= p + 1; ++k) fp *= k;
-        rem_t = pow(ts, (double)(p + 1)) / fp / (1.0 - ts / (p + 2.0));
+        double fp = 1.0, pt = ts;
+        for (int k = 2; k <= p + 1; ++k) {
+            fp *= k;
+            pt *= ts;
+        }
+        rem_t = pt / fp / (1.0 - ts / (p + 2.0));
     }
     auto grid_exp = [](double b) {
         if (!(b > 0.0)) return -100;
@@ -120,7 +127,8 @@ __global__ void k_theta(const double* __restrict__ u, int M, int N, const double
     };
     prm->ex = grid_exp(ts);
     prm->ez = grid_exp(1.0625 * exp(ts));
-    prm->eu = grid_exp(1.0625 * exp(ldexp(log1p(rem_t), n)));
+    const double rn = ldexp(rem_t, n);   // (1 + R)^(2^n) <= 1 + 2^(n+1) R while 2^n R <= 1/2
+    prm->eu = grid_exp(1.0625 * (rn <= 0.5 ? 1.0 + 2.0 * rn : exp(ldexp(log1p(rem_t), n))));
     prm->m_split = m;
     prm->theta = theta;
     prm->p = p;
@@ -194,19 +202,24 @@ cudaError_t launch_to_panels(const double2* src, C_t<R>* dst, int d, int S, Stat
 // ------------------------------------------------------------------------------------------
 // per-slice costs and sources
 // ------------------------------------------------------------------------------------------
-template <typename R>
+// WARP: one warp per slice (8 slices per block) for panels of at most 256 elements, with warp
+// shuffles for the sums; else one block per slice
+template <typename R, bool WARP>
 __global__ void __launch_bounds__(256)
-k_slice_costs(int d, StateView<R> sv, int j0, int N, const C_t<R>* __restrict__ states, int wmax, CostView<R> cv,
-              double2* __restrict__ Oj, double* __restrict__ C5j, double2* __restrict__ Ofin) {
+k_slice_costs(int d, StateView<R> sv, int j0, int wlen, int N, const C_t<R>* __restrict__ states, int wmax,
+              CostView<R> cv, double2* __restrict__ Oj, double* __restrict__ C5j, double2* __restrict__ Ofin) {
     using C = C_t<R>;
     __shared__ double red[32];
-    const int jl = blockIdx.x, e = blockIdx.y, j = j0 + jl, cb = sv.cb, ps = sv.pstride;
+    const int jl = WARP ? blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5) : blockIdx.x;
+    if (WARP && jl >= wlen) return;   // whole warps leave; no block barrier in this mode
+    const int e = blockIdx.y, j = j0 + jl, cb = sv.cb, ps = sv.pstride;
+    const int t0 = WARP ? (threadIdx.x & 31) : threadIdx.x, ts = WARP ? 32 : blockDim.x;
     const size_t slice = sv.slice();
     const C* psi = states + ((size_t)e * (wmax + 1) + jl + 1) * slice;
     const C* T = cv.path ? cv.path + (size_t)j * slice : cv.psiT;
     const bool last = (j == N - 1);
     double ore = 0, oim = 0, c5 = 0, fre = 0, fim = 0;
-    for (size_t i = threadIdx.x; i < slice; i += blockDim.x) {
+    for (size_t i = t0; i < slice; i += ts) {
         const int kb = (int)(i / ps);
         const int rem = (int)(i - (size_t)kb * ps);
         if (rem >= d * cb) continue;
@@ -223,14 +236,21 @@ k_slice_costs(int d, StateView<R> sv, int j0, int N, const C_t<R>* __restrict__ 
             fim += w * ((double)f.x * z.y - (double)f.y * z.x);
         }
     }
-    ore = block_sum(ore, red);
-    oim = block_sum(oim, red);
-    c5 = block_sum(c5, red);
-    if (last) {
-        fre = block_sum(fre, red);
-        fim = block_sum(fim, red);
+    auto sum = [&](double v) {
+        if (WARP) {
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            return v;
+        }
+        return block_sum(v, red);
+    };
+    ore = sum(ore);
+    oim = sum(oim);
+    c5 = sum(c5);
+    if (last) {   // uniform over the warp (WARP) or the block
+        fre = sum(fre);
+        fim = sum(fim);
     }
-    if (threadIdx.x == 0) {
+    if (t0 == 0) {
         Oj[(size_t)e * N + j] = make_double2(ore / cv.Wsum, oim / cv.Wsum);
         C5j[(size_t)e * N + j] = c5;
         if (last) Ofin[e] = make_double2(fre / cv.Wsum, fim / cv.Wsum);
@@ -240,16 +260,23 @@ k_slice_costs(int d, StateView<R> sv, int j0, int N, const C_t<R>* __restrict__ 
 template <typename R>
 cudaError_t launch_slice_costs(int d, StateView<R> sv, int j0, int wlen, int N, int E, const C_t<R>* states, int wmax,
                                const CostView<R>& cv, double2* Oj, double* C5j, double2* Ofin, cudaStream_t st) {
-    k_slice_costs<R><<<dim3(wlen, E), 256, 0, st>>>(d, sv, j0, N, states, wmax, cv, Oj, C5j, Ofin);
+    if (sv.slice() <= 256)
+        k_slice_costs<R, true><<<dim3((wlen + 7) / 8, E), 256, 0, st>>>(d, sv, j0, wlen, N, states, wmax, cv, Oj,
+                                                                         C5j, Ofin);
+    else
+        k_slice_costs<R, false><<<dim3(wlen, E), 256, 0, st>>>(d, sv, j0, wlen, N, states, wmax, cv, Oj, C5j, Ofin);
     return cudaGetLastError();
 }
 
-template <typename R>
+template <typename R, bool WARP>
 __global__ void __launch_bounds__(256)
-k_sources(int d, StateView<R> sv, int j0, int N, int E, const C_t<R>* __restrict__ states, int wmax, CostView<R> cv,
-          const double2* __restrict__ Oj, const double2* __restrict__ Ofin, C_t<R>* __restrict__ src) {
+k_sources(int d, StateView<R> sv, int j0, int wlen, int N, int E, const C_t<R>* __restrict__ states, int wmax,
+          CostView<R> cv, const double2* __restrict__ Oj, const double2* __restrict__ Ofin, C_t<R>* __restrict__ src) {
     using C = C_t<R>;
-    const int jl = blockIdx.x, e = blockIdx.y, j = j0 + jl, cb = sv.cb, ps = sv.pstride;
+    const int jl = WARP ? blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5) : blockIdx.x;
+    if (WARP && jl >= wlen) return;
+    const int t0 = WARP ? (threadIdx.x & 31) : threadIdx.x, ts = WARP ? 32 : blockDim.x;
+    const int e = blockIdx.y, j = j0 + jl, cb = sv.cb, ps = sv.pstride;
     const size_t slice = sv.slice();
     const C* psi = states + ((size_t)e * (wmax + 1) + jl + 1) * slice;
     const C* T = cv.path ? cv.path + (size_t)j * slice : cv.psiT;
@@ -262,7 +289,7 @@ k_sources(int d, StateView<R> sv, int j0, int N, int E, const C_t<R>* __restrict
     const double ct = -2.0 * cv.alpha[4] / N * invE / cv.Wsum;
     const double cf = -2.0 * cv.alpha[0] * invE / cv.Wsum;
     const double c5 = 2.0 * cv.alpha[3] * invE;
-    for (size_t i = threadIdx.x; i < slice; i += blockDim.x) {
+    for (size_t i = t0; i < slice; i += ts) {
         const int kb = (int)(i / ps);
         const int rem = (int)(i - (size_t)kb * ps);
         const bool valid = rem < d * cb;
@@ -295,7 +322,11 @@ template <typename R>
 cudaError_t launch_sources(int d, StateView<R> sv, int j0, int wlen, int N, int E, const C_t<R>* states, int wmax,
                            const CostView<R>& cv, const double2* Oj, const double2* Ofin, C_t<R>* src,
                            cudaStream_t st) {
-    k_sources<R><<<dim3(wlen, E), 256, 0, st>>>(d, sv, j0, N, E, states, wmax, cv, Oj, Ofin, src);
+    if (sv.slice() <= 256)
+        k_sources<R, true><<<dim3((wlen + 7) / 8, E), 256, 0, st>>>(d, sv, j0, wlen, N, E, states, wmax, cv, Oj, Ofin,
+                                                                     src);
+    else
+        k_sources<R, false><<<dim3(wlen, E), 256, 0, st>>>(d, sv, j0, wlen, N, E, states, wmax, cv, Oj, Ofin, src);
     return cudaGetLastError();
 }
 
@@ -304,15 +335,17 @@ cudaError_t launch_sources(int d, StateView<R> sv, int j0, int wlen, int N, int 
 // ------------------------------------------------------------------------------------------
 struct Alpha5 { double a[5]; };
 
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(256)
 k_finalize(int E, int M, int N, const double* __restrict__ u, Alpha5 al, const double2* __restrict__ Oj,
            const double* __restrict__ C5j, const double2* __restrict__ Ofin, const double* __restrict__ gpart,
            double* __restrict__ grad, double* __restrict__ out, DevParams* __restrict__ prm) {
     __shared__ double red[32];
-    const int tid = threadIdx.x;
+    __shared__ bool last;
+    const int tid = threadIdx.x, nb = gridDim.x;
+    const int gt = blockIdx.x * blockDim.x + tid, gs = nb * blockDim.x;
     double c3 = 0, c4 = 0, c5 = 0, t67 = 0;
     bool finite = true;   // outputs scanned for NaN / Inf (a flag, read by the host)
-    for (int i = tid; i < M * N; i += blockDim.x) {
+    for (int i = gt; i < M * N; i += gs) {
         const int k = i / N, j = i - k * N;
         const double x = u[i];
         c3 += x * x;
@@ -331,7 +364,7 @@ k_finalize(int E, int M, int N, const double* __restrict__ u, Alpha5 al, const d
         finite = finite && isfinite(g);
     }
     if (!finite) atomicOr(&prm->err, kErrNonfinite);
-    for (int i = tid; i < E * N; i += blockDim.x) {
+    for (int i = gt; i < E * N; i += gs) {
         c5 += C5j[i];
         const double2 o = Oj[i];
         t67 += o.x * o.x + o.y * o.y;
@@ -340,20 +373,41 @@ k_finalize(int E, int M, int N, const double* __restrict__ u, Alpha5 al, const d
     c4 = block_sum(c4, red);
     c5 = block_sum(c5, red);
     t67 = block_sum(t67, red);
+    // the partial sums of every block, then the last block to finish adds them in block order
+    // (the same order every time: the result does not depend on which block finishes last)
     if (tid == 0) {
-        double fid = 0.0;
-        for (int e = 0; e < E; ++e) fid += 1.0 - (Ofin[e].x * Ofin[e].x + Ofin[e].y * Ofin[e].y);
-        fid /= E;
-        c5 /= E;
-        const double c67 = 1.0 - t67 / ((double)N * E);
-        out[1] = fid;
-        out[2] = c3;
-        out[3] = c4;
-        out[4] = c5;
-        out[5] = c67;
-        out[0] = al.a[0] * fid + al.a[1] * c3 + al.a[2] * c4 + al.a[3] * c5 + al.a[4] * c67;
-        if (!isfinite(out[0])) atomicOr(&prm->err, kErrNonfinite);
+        double* pp = prm->fin_part + 4 * blockIdx.x;
+        pp[0] = c3;
+        pp[1] = c4;
+        pp[2] = c5;
+        pp[3] = t67;
+        __threadfence();
+        last = atomicAdd(&prm->fin_count, 1u) == (unsigned)(nb - 1);
     }
+    __syncthreads();
+    if (!last || tid != 0) return;
+    __threadfence();
+    c3 = c4 = c5 = t67 = 0.0;
+    const volatile double* vp = prm->fin_part;
+    for (int b = 0; b < nb; ++b) {
+        c3 += vp[4 * b];
+        c4 += vp[4 * b + 1];
+        c5 += vp[4 * b + 2];
+        t67 += vp[4 * b + 3];
+    }
+    prm->fin_count = 0;
+    double fid = 0.0;
+    for (int e = 0; e < E; ++e) fid += 1.0 - (Ofin[e].x * Ofin[e].x + Ofin[e].y * Ofin[e].y);
+    fid /= E;
+    c5 /= E;
+    const double c67 = 1.0 - t67 / ((double)N * E);
+    out[1] = fid;
+    out[2] = c3;
+    out[3] = c4;
+    out[4] = c5;
+    out[5] = c67;
+    out[0] = al.a[0] * fid + al.a[1] * c3 + al.a[2] * c4 + al.a[3] * c5 + al.a[4] * c67;
+    if (!isfinite(out[0])) atomicOr(&prm->err, kErrNonfinite);
 }
 
 cudaError_t launch_finalize(int E, int M, int N, const double* u, const double* alpha, const double2* Oj,
@@ -361,7 +415,9 @@ cudaError_t launch_finalize(int E, int M, int N, const double* u, const double* 
                             DevParams* prm, cudaStream_t st) {
     Alpha5 al;
     for (int i = 0; i < 5; ++i) al.a[i] = alpha[i];
-    k_finalize<<<1, 1024, 0, st>>>(E, M, N, u, al, Oj, C5j, Ofin, gpart, grad, out, prm);
+    const int work = std::max(M * N, E * N);
+    const int nb = std::max(1, std::min(kFinBlocks, (work + 255) / 256));
+    k_finalize<<<nb, 256, 0, st>>>(E, M, N, u, al, Oj, C5j, Ofin, gpart, grad, out, prm);
     return cudaGetLastError();
 }
 

@@ -45,7 +45,13 @@ struct DevParams {
     // grid exponents of the split FP32 exponential: 2^e bounds the row and column 2-norms of
     // X (ex), of the Horner matrices Z_i, i >= 2 (ez), and of T and its squarings (eu)
     int ex, ez, eu;
+    // cross-block reduction of the final cost terms (k_finalize): per-block partials and the
+    // count of blocks that have written theirs (the last block sums them in block order and
+    // resets the count)
+    unsigned fin_count;
+    double fin_part[4 * 32];
 };
+constexpr int kFinBlocks = 32;
 
 enum : int { kErrRange = 1, kErrTimeout = 2, kErrNonfinite = 4 };
 
