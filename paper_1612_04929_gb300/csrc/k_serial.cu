@@ -10,6 +10,13 @@
 // up to gradient errors near 1e-5; the pair keeps the recursion at ~1e-12 while U_j, the stored
 // states and costates (inputs of the parallel kernels) stay FP32.
 //
+// FP32 form: every step multiplies grid-split operands (qoc_device.cuh).  The carried pair block
+// is re-split at the start of each step on a power-of-two grid set by a bound on its column
+// norms, sqrt(2d) max |component| (the maximum is gathered while the previous step writes the
+// block), and the elements of U_j^(dag) (or of P_z) are split as they are read.  The grid sums
+// are exact; only the cross terms round (about 2^-36 of the scale), so a step costs 12 FMAs and
+// the operand splits per complex multiply-add instead of the pair arithmetic's ~44 operations.
+//
 // Checkpointing: the forward sweep stores the carried block every `seg` slices (seg = ceil(sqrt
 // N) by default).  In the backward sweep the states of a wave are regenerated from those
 // checkpoints, one CTA per checkpoint segment in parallel (mode 1 below), so regeneration
@@ -138,6 +145,91 @@ __device__ __forceinline__ void sweep_step(const C* __restrict__ Mx, const K* __
     }
 }
 
+// FP32 grid step.  Element of the matrix operand, split with the magic constant mu: (u1, u2) in
+// s and the full value in uf (a plain FP32 value is its own full value; a carried pair rounds).
+__device__ __forceinline__ void gsplit_elem(const float2 u, float mu, float4& s, float2& uf) {
+    grid_split(u.x, 0.f, mu, s.x, s.z);
+    grid_split(u.y, 0.f, mu, s.y, s.w);
+    uf = u;
+}
+__device__ __forceinline__ void gsplit_elem(const float4 u, float mu, float4& s, float2& uf) {
+    grid_split(u.x, u.z, mu, s.x, s.z);
+    grid_split(u.y, u.w, mu, s.y, s.w);
+    uf = make_float2(s.x + s.z, s.y + s.w);
+}
+// magic constant of the block's grid from the largest |component| m (float bits): the column
+// 2-norms are at most sqrt(2d) m
+__device__ __forceinline__ float block_magic(unsigned mbits, int d) {
+    const float b = sqrtf(2.0f * d) * __uint_as_float(mbits) * 1.0625f;
+    int e = -100;
+    if (b > 0.f) e = (b < 1e30f) ? ilogbf(b) + 1 : 100;
+    return grid_magic(e < -100 ? -100 : e);
+}
+__device__ __forceinline__ float4 pair_to_grid(const float4 v, float mx) {
+    float4 o;
+    grid_split(v.x, v.z, mx, o.x, o.z);
+    grid_split(v.y, v.w, mx, o.y, o.w);
+    return o;
+}
+__device__ __forceinline__ unsigned pair_maxbits(const float4 v) {
+    return __float_as_uint(fmaxf(fabsf(v.x), fabsf(v.y)));
+}
+
+// One FP32 step y = Mx x (+ add) from the grid-split block xg: g lanes per output sum the grid
+// parts (S, exact) and the cross terms (L) of b = q, q + g, ...; the shuffle reduction adds S
+// and L with plain adds (S stays exact); lane q = 0 forms the pair S + L without error, adds the
+// source, normalises, keeps it in y, hands it to `emit` and raises *ymax to its largest component.
+template <typename Mt, typename S, typename Emit>
+__device__ __forceinline__ void sweep_step_grid(const Mt* __restrict__ Mx, const float4* __restrict__ xg,
+                                                float4* __restrict__ y, const S* __restrict__ add, int d, int cb,
+                                                int g, float mu, unsigned* ymax, Emit emit) {
+    const int O = d * cb;
+    const int ngroups = blockDim.x / g;
+    const int gi = threadIdx.x / g, q = threadIdx.x - gi * g;
+    for (int base = 0; base < O; base += ngroups) {
+        const int o = base + gi;
+        float sr = 0.f, si = 0.f, lr = 0.f, li = 0.f;
+        if (o < O) {
+            const int a = o / cb, sl = o - a * cb;
+            const Mt* Mr = Mx + (size_t)a * d;
+            for (int b = q; b < d; b += g) {
+                float4 u;
+                float2 uf;
+                gsplit_elem(Mr[b], mu, u, uf);
+                const float4 x = xg[b * cb + sl];
+                sr = fmaf(u.x, x.x, sr);
+                sr = fmaf(-u.y, x.y, sr);
+                si = fmaf(u.x, x.y, si);
+                si = fmaf(u.y, x.x, si);
+                lr = fmaf(u.z, x.x, lr);
+                lr = fmaf(-u.w, x.y, lr);
+                lr = fmaf(uf.x, x.z, lr);
+                lr = fmaf(-uf.y, x.w, lr);
+                li = fmaf(u.z, x.y, li);
+                li = fmaf(u.w, x.x, li);
+                li = fmaf(uf.x, x.w, li);
+                li = fmaf(uf.y, x.z, li);
+            }
+        }
+        for (int off = g >> 1; off > 0; off >>= 1) {
+            sr += __shfl_xor_sync(0xffffffffu, sr, off);
+            si += __shfl_xor_sync(0xffffffffu, si, off);
+            lr += __shfl_xor_sync(0xffffffffu, lr, off);
+            li += __shfl_xor_sync(0xffffffffu, li, off);
+        }
+        if (o < O && q == 0) {
+            float4 acc;
+            two_sum(sr, lr, acc.x, acc.z);
+            two_sum(si, li, acc.y, acc.w);
+            if (add) kadd(acc, kfrom(add[o]));
+            knorm(acc);
+            y[o] = acc;
+            atomicMax(ymax, pair_maxbits(acc));
+            emit(o, acc);
+        }
+    }
+}
+
 // lanes per output and block size: minimise the issue time of one step on one SM
 // (passes x warps per scheduler x instructions per lane)
 static void pick_sweep_shape(int d, int cb, bool pair, int& g, int& threads) {
@@ -149,7 +241,7 @@ static void pick_sweep_shape(int d, int cb, bool pair, int& g, int& threads) {
         const int groups = thr / gg;
         const int passes = (O + groups - 1) / groups;
         const int wps = (thr / 32 + 3) / 4;
-        const long cost = (long)passes * wps * (((d + gg - 1) / gg) * (pair ? 44 : 10) + 12 * lg);
+        const long cost = (long)passes * wps * (((d + gg - 1) / gg) * (pair ? 20 : 10) + (pair ? 8 : 12) * lg);
         if (best < 0 || cost < best) {
             best = cost;
             g = gg;
@@ -165,7 +257,7 @@ template <typename R, int RING, typename Mt>
 __global__ void __launch_bounds__(1024)
 k_chain(int d, StateView<R> sv, int wlen, int seg, int mode, K_t<R>* __restrict__ ckpt, size_t ck_estride, int seg0,
         int nseg_total, const Mt* __restrict__ Ubuf, long long ustride, int wmax, C_t<R>* __restrict__ states,
-        int g) {
+        int g, const DevParams* __restrict__ prm) {
     using C = C_t<R>;
     using K = K_t<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -175,17 +267,41 @@ k_chain(int d, StateView<R> sv, int wlen, int seg, int mode, K_t<R>* __restrict_
     unsigned char* ring = smraw;
     K* xa = reinterpret_cast<K*>(smraw + RING * ub);   // RING 0: no ring, rows read from global
     K* xb = xa + panel;
+    float4* xg = reinterpret_cast<float4*>(xb + panel);   // FP32: grid-split block of the step
+    __shared__ unsigned smax[2];                           // FP32: largest component, by step parity
     const int t0 = (mode == 0) ? 0 : z * seg;
     const int t1 = (mode == 0) ? wlen : min(wlen, t0 + seg);
     if (t0 >= t1) return;
+    if (tid == 0) smax[0] = smax[1] = 0u;
+    __syncthreads();
     K* ck_e = ckpt + e * ck_estride;
     const K* s0 = ck_e + (size_t)(seg0 + t0 / seg) * slice + (size_t)kb * sv.pstride;
     C* sdst = states + (size_t)e * (wmax + 1) * slice + (size_t)kb * sv.pstride;
+    // the first state of a replayed segment z > 0 is the last state of segment z - 1, which that
+    // segment's CTA writes: one writer per state (the checkpoint and the stepped value differ in
+    // their last bits)
+    const bool own_first = (mode == 0 || z == 0);
     for (int i = tid; i < (int)panel; i += blockDim.x) {
         const K v = s0[i];
         xa[i] = v;
-        sdst[(size_t)t0 * slice + i] = kround(v);
+        if (own_first) sdst[(size_t)t0 * slice + i] = kround(v);
+        if constexpr (sizeof(R) == 4) atomicMax(&smax[0], pair_maxbits(v));
     }
+    float mu = 0.f;
+    if constexpr (sizeof(R) == 4) mu = grid_magic(prm ? prm->eu : 1);
+    // one step from the block in xa into xb (the caller has passed a barrier since xa was written)
+    auto step = [&](const Mt* M, int k, auto emit) {
+        if constexpr (sizeof(R) == 4) {
+            const float mx = block_magic(smax[k & 1], d);
+            if (tid == 0) smax[(k + 1) & 1] = 0u;
+            for (int i = tid; i < (int)panel; i += blockDim.x) xg[i] = pair_to_grid(xa[i], mx);
+            __syncthreads();
+            sweep_step_grid<Mt, C>(M, xg, xb, static_cast<const C*>(nullptr), d, cb, g, mu, &smax[(k + 1) & 1], emit);
+        } else {
+            sweep_step<Mt, K, C>(M, xa, xb, nullptr, d, cb, g, emit);
+        }
+        K* tmp = xa; xa = xb; xb = tmp;
+    };
     const Mt* Ue = Ubuf + (size_t)e * wmax * ustride;
     auto emit_for = [&](int t) {
         C* dst = sdst + (size_t)(t + 1) * slice;
@@ -201,8 +317,7 @@ k_chain(int d, StateView<R> sv, int wlen, int seg, int mode, K_t<R>* __restrict_
 #pragma unroll 1
         for (int t = t0; t < t1; ++t) {
             __syncthreads();
-            sweep_step<Mt, K, C>(Ue + (size_t)t * ustride, xa, xb, nullptr, d, cb, g, emit_for(t));
-            K* tmp = xa; xa = xb; xb = tmp;
+            step(Ue + (size_t)t * ustride, t - t0, emit_for(t));
         }
     } else if constexpr (RING == 1) {   // one slot: synchronous copy
 #pragma unroll 1
@@ -212,8 +327,7 @@ k_chain(int d, StateView<R> sv, int wlen, int seg, int mode, K_t<R>* __restrict_
             cp_async_commit();
             cp_async_wait<0>();
             __syncthreads();
-            sweep_step<Mt, K, C>(reinterpret_cast<const Mt*>(ring), xa, xb, nullptr, d, cb, g, emit_for(t));
-            K* tmp = xa; xa = xb; xb = tmp;
+            step(reinterpret_cast<const Mt*>(ring), t - t0, emit_for(t));
         }
     } else {
 #pragma unroll 1
@@ -229,8 +343,7 @@ k_chain(int d, StateView<R> sv, int wlen, int seg, int mode, K_t<R>* __restrict_
             const int tn = t + RING - 1;
             if (tn < t1) ring_issue(ring + ((k + RING - 1) % RING) * ub, Ue + (size_t)tn * ustride, ub);
             cp_async_commit();
-            sweep_step<Mt, K, C>(reinterpret_cast<const Mt*>(ring + (k % RING) * ub), xa, xb, nullptr, d, cb, g, emit_for(t));
-            K* tmp = xa; xa = xb; xb = tmp;
+            step(reinterpret_cast<const Mt*>(ring + (k % RING) * ub), k, emit_for(t));
         }
     }
 }
@@ -245,14 +358,14 @@ static cudaError_t chain_ring(const ChainArgs<R>& a, const Mt* U, size_t smem, c
     const int nz = a.mode == 0 ? 1 : (a.wlen + a.seg - 1) / a.seg;
     k_chain<R, RING, Mt><<<dim3(a.sv.ncb, a.E, nz), threads, smem, st>>>(a.d, a.sv, a.wlen, a.seg, a.mode, a.ckpt,
                                                                           a.ck_estride, a.seg0, a.nseg_total, U,
-                                                                          a.ustride, a.wmax, a.states, g);
+                                                                          a.ustride, a.wmax, a.states, g, a.prm);
     return cudaGetLastError();
 }
 
 template <typename R, typename Mt>
 static cudaError_t chain_dispatch(const ChainArgs<R>& a, const Mt* U, cudaStream_t st) {
     const size_t ub = ring_bytes((size_t)a.d * a.d, sizeof(Mt));
-    const size_t xs = 2 * (size_t)a.d * a.sv.cb * sizeof(K_t<R>);
+    const size_t xs = (2 * sizeof(K_t<R>) + (sizeof(R) == 4 ? sizeof(float4) : 0)) * (size_t)a.d * a.sv.cb;
     if (xs > kMaxDynSmem) return cudaErrorInvalidValue;
     for (int ring : {8, 4, 2, 1}) {
         const size_t smem = ring * ub + xs;
@@ -297,6 +410,10 @@ __global__ void __launch_bounds__(1024) k_costate(CostateArgs<R> A, int g) {
     unsigned char* ring = smraw;
     K* xa = reinterpret_cast<K*>(smraw + RING * slot);   // RING 0: no ring
     K* xb = xa + panel;
+    float4* xg = reinterpret_cast<float4*>(xb + panel);   // FP32: grid-split block of the step
+    __shared__ unsigned smax[2];
+    if (tid == 0) smax[0] = smax[1] = 0u;
+    __syncthreads();
     const Mt* UHe = reinterpret_cast<const Mt*>(A.Uk ? (const void*)A.Uk : (const void*)A.U) + e * A.u_es +
                     A.ustride / 2;                        // U_j^dag of every slice
     const S* Se = reinterpret_cast<const S*>(A.srck ? (const void*)A.srck : (const void*)A.src) + e * A.src_es + poff;
@@ -310,6 +427,7 @@ __global__ void __launch_bounds__(1024) k_costate(CostateArgs<R> A, int g) {
             kadd(v, kfrom(s_last[i]));
             knorm(v);
             xa[i] = v;
+            if constexpr (sizeof(R) == 4) atomicMax(&smax[0], pair_maxbits(v));
             if (Ge) Ge[(size_t)b0 * slice + i] = kround(v);
             if (Gk) Gk[(size_t)b0 * slice + i] = v;
         }
@@ -322,15 +440,28 @@ __global__ void __launch_bounds__(1024) k_costate(CostateArgs<R> A, int g) {
             if (gk) gk[o] = v;
         };
     };
+    float mu = 0.f;
+    if constexpr (sizeof(R) == 4) mu = grid_magic(A.prm ? A.prm->eu : 1);
+    // one step from the block in xa into xb (the caller has passed a barrier since xa was written)
+    auto step = [&](const Mt* M, const S* add, int k, auto emit) {
+        if constexpr (sizeof(R) == 4) {
+            const float mx = block_magic(smax[k & 1], d);
+            if (tid == 0) smax[(k + 1) & 1] = 0u;
+            for (int i = tid; i < (int)panel; i += blockDim.x) xg[i] = pair_to_grid(xa[i], mx);
+            __syncthreads();
+            sweep_step_grid<Mt, S>(M, xg, xb, add, d, cb, g, mu, &smax[(k + 1) & 1], emit);
+        } else {
+            sweep_step<Mt, K, S>(M, xa, xb, add, d, cb, g, emit);
+        }
+        K* tmp = xa; xa = xb; xb = tmp;
+    };
     // step t handles slice jl = b0 - t: U_jl^dag and src_{jl-1} (none at the segment's first slice)
     if constexpr (RING == 0) {          // rows of U^dag and the sources read from global/L2
 #pragma unroll 1
         for (int t = 0; t < n; ++t) {
             const int jl = b0 - t;
             __syncthreads();
-            sweep_step<Mt, K, S>(UHe + (size_t)jl * A.ustride, xa, xb, (jl > a0) ? Se + (size_t)(jl - 1) * slice : nullptr,
-                                d, cb, g, emit_for(jl));
-            K* tmp = xa; xa = xb; xb = tmp;
+            step(UHe + (size_t)jl * A.ustride, (jl > a0) ? Se + (size_t)(jl - 1) * slice : nullptr, t, emit_for(jl));
         }
     } else if constexpr (RING == 1) {
 #pragma unroll 1
@@ -342,9 +473,8 @@ __global__ void __launch_bounds__(1024) k_costate(CostateArgs<R> A, int g) {
             cp_async_commit();
             cp_async_wait<0>();
             __syncthreads();
-            sweep_step<Mt, K, S>(reinterpret_cast<const Mt*>(ring), xa, xb,
-                                (jl > a0) ? reinterpret_cast<const S*>(ring + ub) : nullptr, d, cb, g, emit_for(jl));
-            K* tmp = xa; xa = xb; xb = tmp;
+            step(reinterpret_cast<const Mt*>(ring), (jl > a0) ? reinterpret_cast<const S*>(ring + ub) : nullptr, t,
+                 emit_for(jl));
         }
     } else {
         auto issue = [&](int t) {
@@ -367,9 +497,8 @@ __global__ void __launch_bounds__(1024) k_costate(CostateArgs<R> A, int g) {
             if (tn < n) issue(tn);
             cp_async_commit();
             const unsigned char* sl = ring + (t % RING) * slot;
-            sweep_step<Mt, K, S>(reinterpret_cast<const Mt*>(sl), xa, xb,
-                                (jl > a0) ? reinterpret_cast<const S*>(sl + ub) : nullptr, d, cb, g, emit_for(jl));
-            K* tmp = xa; xa = xb; xb = tmp;
+            step(reinterpret_cast<const Mt*>(sl), (jl > a0) ? reinterpret_cast<const S*>(sl + ub) : nullptr, t,
+                 emit_for(jl));
         }
     }
     __syncthreads();
@@ -400,7 +529,7 @@ static cudaError_t costate_dispatch(const CostateArgs<R>& a, cudaStream_t st) {
     const size_t panel = (size_t)a.d * a.sv.cb;
     const size_t ub = ring_bytes((size_t)a.d * a.d, sizeof(Mt));
     const size_t pb = (size_t)a.sv.pstride * sizeof(S);
-    const size_t fixed = 2 * panel * sizeof(K_t<R>);
+    const size_t fixed = (2 * sizeof(K_t<R>) + (sizeof(R) == 4 ? sizeof(float4) : 0)) * panel;
     if (fixed > kMaxDynSmem) return cudaErrorInvalidValue;
     for (int ring : {8, 4, 2, 1}) {
         const size_t smem = ring * (ub + pb) + fixed;

@@ -462,7 +462,7 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
     auto chain_args = [&](int w, int mode) {
         const int j0 = w * W;
         return ChainArgs<R>{d, sv, std::min(W, N - j0), seg, mode, E, c->ckpt.as<K>(), (size_t)c->nseg_total * slice,
-                            j0 / seg, c->nseg_total, Ub(w), c->ustride, W, Sb(w)};
+                            j0 / seg, c->nseg_total, Ub(w), c->ustride, W, Sb(w), nullptr, prm};
     };
     int launches = 0;
     const bool prof = c->opt.profile != 0;
@@ -635,6 +635,7 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
         a.src = Rb(w);
         a.src_es = (size_t)W * slice;
         a.g_es = (size_t)W * slice;
+        a.prm = prm;
         return a;
     };
     if (!c->scan) {
@@ -715,7 +716,7 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
             L(seg_products(w, sx), "seg_products", sx);
             B(sx);
             L(launch_chain<R>(ChainArgs<R>{d, sv, nz, 1, 0, E, c->ckpt.as<K>(), (size_t)c->nseg_total * slice, j0 / seg,
-                                           c->nseg_total, nullptr, c->ustride, nzmax, c->scanst.as<C>(), Pb(w)},
+                                           c->nseg_total, nullptr, c->ustride, nzmax, c->scanst.as<C>(), Pb(w), prm},
                               sx),
               "scan", sx);
             rec(ev_scan[w], sx);
@@ -742,6 +743,7 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
             B(sx);
             L(launch_costate<R>(loc, sx), "costate (segments)", sx);
             CostateArgs<R> sc{};
+            sc.prm = prm;
             sc.d = d;
             sc.sv = sv;
             sc.wlen = nz;

@@ -242,6 +242,7 @@ struct ChainArgs {
     int wmax;
     C_t<R>* states;         // [E][wmax + 1] FP32/FP64 blocks of the wave
     const K_t<R>* Uk;       // ... carried segment products (exactly one of the two is set)
+    const DevParams* prm;   // grid exponent eu of the FP32 form (nullptr: 1)
 };
 template <typename R> cudaError_t launch_chain(const ChainArgs<R>& a, cudaStream_t st);
 // Costate sweep G_{j-1} = U_j^dag G_j + src_{j-1}, split into segments of `seg` slices that run in
@@ -268,6 +269,7 @@ struct CostateArgs {
     K_t<R>* cout;           // out-carries or nullptr
     size_t cout_es;
     int zero_next;          // also clear block (e, nz) of cout
+    const DevParams* prm;   // grid exponent eu of the FP32 form (nullptr: 1)
 };
 template <typename R> cudaError_t launch_costate(const CostateArgs<R>& a, cudaStream_t st);
 

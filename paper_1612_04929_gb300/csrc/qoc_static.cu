@@ -114,7 +114,7 @@ extern "C" qoc_status qoc_evaluate_static(int d, int M, int N, int S, double dt,
     SysView<R> sys{d, M, N, H0, Hk, nullptr, nullptr, u_dev};
     CostView<R> cost{0, fmask_dev ? fmask_dev : fmask_zero, colw, (double)S, psiT, nullptr,
                      {alpha[0], alpha[1], alpha[2], alpha[3], alpha[4]}};
-    ChainArgs<R> ch{d, sv, N, N, 0, 1, ckpt, slice, 0, 1, Ubuf, ustride, N, states};
+    ChainArgs<R> ch{d, sv, N, N, 0, 1, ckpt, slice, 0, 1, Ubuf, ustride, N, states, nullptr, prm};
     if (!ok(launch_theta(u_dev, M, N, norms, nullptr, 1, dt, 0.25, 1e-15, 0, -1, prm, st))) return QOC_ERR_CUDA;
     const ZStore<R> nostore{nullptr, 0, 0, 0};   // the arena holds no product operands: block recursion
     if (!ok(launch_expm_fwd_fused<R>(prm, sys, 0, N, 1, Ubuf, ustride, N, nostore, st))) return QOC_ERR_CUDA;
@@ -131,6 +131,7 @@ extern "C" qoc_status qoc_evaluate_static(int d, int M, int N, int S, double dt,
     co.src = src;
     co.G = Gbuf;
     co.cin = co.cout = carry;
+    co.prm = prm;
     if (!ok(launch_costate<R>(co, st))) return QOC_ERR_CUDA;
     int n_adj = 0;
     if (!ok(launch_expm_adj_fused<R>(prm, sys, sv, 0, N, 1, states, Gbuf, N, gpart, nostore, st, &n_adj)))
