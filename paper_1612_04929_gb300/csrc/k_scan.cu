@@ -26,18 +26,6 @@ namespace {
 
 constexpr int KC = 16;   // K-chunk staged in shared memory
 
-// (hi, lo) += (ah + al)(bh + bl), dropping al * bl
-__device__ __forceinline__ void mac_pair(float& hi, float& lo, float ah, float al, float bh, float bl) {
-    const float p = ah * bh;
-    float e = fmaf(ah, bh, -p);
-    e = fmaf(ah, bl, e);
-    e = fmaf(al, bh, e);
-    const float t = hi + p;
-    const float bv = t - hi;
-    lo += (hi - (t - bv)) + (p - bv) + e;
-    hi = t;
-}
-
 // operands widened to the carried type on load
 __device__ __forceinline__ float4 widen(const float2 v) { return make_float4(v.x, v.y, 0.f, 0.f); }
 __device__ __forceinline__ float4 widen(const float4 v) { return v; }
@@ -46,29 +34,29 @@ template <typename K> __device__ __forceinline__ K kz();
 template <> __device__ __forceinline__ float4 kz<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
 template <> __device__ __forceinline__ double2 kz<double2>() { return make_double2(0.0, 0.0); }
 
-// acc += a b (complex, carried)
-__device__ __forceinline__ void kmac2(float4& acc, const float4 a, const float4 b) {
-    mac_pair(acc.x, acc.z, a.x, a.z, b.x, b.z);
-    mac_pair(acc.x, acc.z, -a.y, -a.w, b.y, b.w);
-    mac_pair(acc.y, acc.w, a.x, a.z, b.y, b.w);
-    mac_pair(acc.y, acc.w, a.y, a.w, b.x, b.z);
-}
+// acc += a b (FP64 form; the FP32 form multiplies grid-split factors)
 __device__ __forceinline__ void kmac2(double2& acc, const double2 a, const double2 b) { cfma(acc, a, b); }
-__device__ __forceinline__ float4 knorm2(float4 v) {
-    float s = v.x + v.z;
-    v.z = v.z - (s - v.x);
-    v.x = s;
-    s = v.y + v.w;
-    v.w = v.w - (s - v.y);
-    v.y = s;
-    return v;
-}
 __device__ __forceinline__ double2 knorm2(double2 v) { return v; }
 __device__ __forceinline__ void kconj(float4& v) {
     v.y = -v.y;
     v.w = -v.w;
 }
 __device__ __forceinline__ void kconj(double2& v) { v.y = -v.y; }
+
+// a factor element as grid-split float4 (re1, im1, re2, im2): from a plain FP32 value (exact
+// split) or from a carried (hi, lo) pair
+__device__ __forceinline__ float4 to_grid(const float2 v, float magic) {
+    float4 o;
+    grid_split(v.x, 0.f, magic, o.x, o.z);
+    grid_split(v.y, 0.f, magic, o.y, o.w);
+    return o;
+}
+__device__ __forceinline__ float4 to_grid(const float4 v, float magic) {
+    float4 o;
+    grid_split(v.x, v.z, magic, o.x, o.z);
+    grid_split(v.y, v.w, magic, o.y, o.w);
+    return o;
+}
 
 // Level l of the tree.  Item i of segment z at level l covers slices a + i 2^l .. ; it is the
 // product of items 2i + 1 (left) and 2i of level l - 1, or item 2i itself when that one has no
@@ -81,7 +69,8 @@ k_seg_mm(SegProdArgs<R> a, int level, const EI* __restrict__ src, size_t src_ite
          K_t<R>* __restrict__ dst, int cap) {
     using K = K_t<R>;
     constexpr int MT = T / 16;
-    __shared__ __align__(16) K As[T][KC + 1];
+    constexpr bool kGrid = std::is_same<K, float4>::value;   // FP32 form: grid-split factors
+    __shared__ __align__(16) K As[T][KC + 1];                 // (grid-split float4 in the FP32 form)
     __shared__ __align__(16) K Bs[KC][T + 1];
     const int d = a.d;
     const int q = blockIdx.y;
@@ -111,6 +100,14 @@ k_seg_mm(SegProdArgs<R> a, int level, const EI* __restrict__ src, size_t src_ite
             }
         return;
     }
+    float mg = 0.f;
+    if constexpr (kGrid) mg = grid_magic(a.prm ? a.prm->eu : 1);
+    auto stage = [&](const EI& v) -> K {
+        if constexpr (kGrid) return to_grid(v, mg);
+        else return widen(v);
+    };
+    // FP32: grid sums (re, im) and cross terms (re, im) per output; FP64: plain accumulators
+    float sa[kGrid ? MT : 1][kGrid ? MT : 1][4] = {};
     K acc[MT][MT];
 #pragma unroll
     for (int x = 0; x < MT; ++x)
@@ -120,12 +117,12 @@ k_seg_mm(SegProdArgs<R> a, int level, const EI* __restrict__ src, size_t src_ite
         for (int idx = tid; idx < T * KC; idx += 256) {
             const int r = idx / KC, k = idx - r * KC;
             const int gr = r0 + r, gk = k0 + k;
-            As[r][k] = (gr < d && gk < d) ? widen(Am[(size_t)gr * d + gk]) : kz<K>();
+            As[r][k] = (gr < d && gk < d) ? stage(Am[(size_t)gr * d + gk]) : kz<K>();
         }
         for (int idx = tid; idx < KC * T; idx += 256) {
             const int k = idx / T, c = idx - k * T;
             const int gk = k0 + k, gc = c0 + c;
-            Bs[k][c] = (gk < d && gc < d) ? widen(Bm[(size_t)gk * d + gc]) : kz<K>();
+            Bs[k][c] = (gk < d && gc < d) ? stage(Bm[(size_t)gk * d + gc]) : kz<K>();
         }
         __syncthreads();
 #pragma unroll 4
@@ -135,10 +132,34 @@ k_seg_mm(SegProdArgs<R> a, int level, const EI* __restrict__ src, size_t src_ite
             for (int x = 0; x < MT; ++x) av[x] = As[ty + 16 * x][k];
 #pragma unroll
             for (int y = 0; y < MT; ++y) bv[y] = Bs[k][tx + 16 * y];
+            if constexpr (kGrid) {
+                float2 bf[MT];
 #pragma unroll
-            for (int x = 0; x < MT; ++x)
+                for (int y = 0; y < MT; ++y) bf[y] = make_float2(bv[y].x + bv[y].z, bv[y].y + bv[y].w);
 #pragma unroll
-                for (int y = 0; y < MT; ++y) kmac2(acc[x][y], av[x], bv[y]);
+                for (int x = 0; x < MT; ++x)
+#pragma unroll
+                    for (int y = 0; y < MT; ++y) {
+                        float* c = sa[x][y];
+                        c[0] = fmaf(av[x].x, bv[y].x, c[0]);
+                        c[0] = fmaf(-av[x].y, bv[y].y, c[0]);
+                        c[1] = fmaf(av[x].x, bv[y].y, c[1]);
+                        c[1] = fmaf(av[x].y, bv[y].x, c[1]);
+                        c[2] = fmaf(av[x].x, bv[y].z, c[2]);
+                        c[2] = fmaf(-av[x].y, bv[y].w, c[2]);
+                        c[2] = fmaf(av[x].z, bf[y].x, c[2]);
+                        c[2] = fmaf(-av[x].w, bf[y].y, c[2]);
+                        c[3] = fmaf(av[x].x, bv[y].w, c[3]);
+                        c[3] = fmaf(av[x].y, bv[y].z, c[3]);
+                        c[3] = fmaf(av[x].z, bf[y].y, c[3]);
+                        c[3] = fmaf(av[x].w, bf[y].x, c[3]);
+                    }
+            } else {
+#pragma unroll
+                for (int x = 0; x < MT; ++x)
+#pragma unroll
+                    for (int y = 0; y < MT; ++y) kmac2(acc[x][y], av[x], bv[y]);
+            }
         }
         __syncthreads();
     }
@@ -147,7 +168,16 @@ k_seg_mm(SegProdArgs<R> a, int level, const EI* __restrict__ src, size_t src_ite
 #pragma unroll
         for (int y = 0; y < MT; ++y) {
             const int r = r0 + ty + 16 * x, c = c0 + tx + 16 * y;
-            if (r < d && c < d) out[(size_t)r * d + c] = knorm2(acc[x][y]);
+            if (r < d && c < d) {
+                if constexpr (kGrid) {
+                    float4 o;
+                    two_sum(sa[x][y][0], sa[x][y][2], o.x, o.z);
+                    two_sum(sa[x][y][1], sa[x][y][3], o.y, o.w);
+                    out[(size_t)r * d + c] = o;
+                } else {
+                    out[(size_t)r * d + c] = knorm2(acc[x][y]);
+                }
+            }
         }
 }
 
@@ -158,21 +188,6 @@ k_seg_mm(SegProdArgs<R> a, int level, const EI* __restrict__ src, size_t src_ite
 // error-free sum of the grid sums and the cross terms; FP64 form: plain FP64 products.
 
 __device__ __forceinline__ void kmac_any(double2& acc, const double2 a, const double2 b) { cfma(acc, a, b); }
-
-// a factor element as grid-split float4 (re1, im1, re2, im2): from a plain FP32 value (exact
-// split) or from a carried (hi, lo) pair
-__device__ __forceinline__ float4 to_grid(const float2 v, float magic) {
-    float4 o;
-    grid_split(v.x, 0.f, magic, o.x, o.z);
-    grid_split(v.y, 0.f, magic, o.y, o.w);
-    return o;
-}
-__device__ __forceinline__ float4 to_grid(const float4 v, float magic) {
-    float4 o;
-    grid_split(v.x, v.z, magic, o.x, o.z);
-    grid_split(v.y, v.w, magic, o.y, o.w);
-    return o;
-}
 
 template <typename R, typename EI, int MT>
 __global__ void __launch_bounds__(512)
