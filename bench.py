@@ -29,8 +29,12 @@ sys.path.insert(0, ROOT)
 METRIC = "fwd+grad slice-steps/s"
 UNIT = "slice-steps/s"
 # FP32 FMA peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (max SM clock)
-# DRAM bytes per launch measured by ncu, keyed by (workload, precision, kernel, wave slices)
-MEASURED_TRAFFIC = {}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, averaged over the launches
+# of one evaluation) measured by ncu, keyed by (workload, precision, kernel, wave slices)
+MEASURED_TRAFFIC = {
+    # split exponential, waves of 1125 and 875 slices: 139,826,432 and 91,752,192 bytes
+    ("transmon_cavity_d40", "fp32", "expm_fwd", 1125): 115789312.0,
+}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 L2_FLUSH_BYTES = 256 << 20
 

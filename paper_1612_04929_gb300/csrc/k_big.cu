@@ -99,6 +99,67 @@ __global__ void k_big_assemble(const DevParams* __restrict__ prm, BigSys sys, in
     }
 }
 
+// FP32 split form: X = -i s H_j and Z = I + X / p in pair arithmetic from the pairs s H_0,
+// s H_k, s H_det (as the per-slice split kernel assembles them), grid-split (ex; Z with ezp).
+__device__ __forceinline__ void big_pair_fma(float& hi, float& lo, float2 u, float bh, float bl) {
+    const float p = u.x * bh;
+    float e = fmaf(u.x, bh, -p);
+    e = fmaf(u.x, bl, e);
+    e = fmaf(u.y, bh, e);
+    float s, r;
+    two_sum(hi, p, s, r);
+    hi = s;
+    lo += r + e;
+}
+__device__ __forceinline__ float4 big_gsplit(float rh, float rl, float ih, float il, int e) {
+    if (e == kFullForm) return make_float4(rh + rl, ih + il, 0.f, 0.f);
+    const float m = grid_magic(e);
+    float4 o;
+    grid_split(rh, rl, m, o.x, o.z);
+    grid_split(ih, il, m, o.y, o.w);
+    return o;
+}
+__global__ void k_big_assemble_split(const DevParams* __restrict__ prm, BigSys sys, const float4* __restrict__ sH,
+                                     int j0, int wlen, float4* __restrict__ X, float4* __restrict__ Z, size_t mstride,
+                                     int ex, int ezp) {
+    __shared__ float2 us[kMaxControls + 1];
+    const int item = blockIdx.y, jl = item % wlen, e = item / wlen, j = j0 + jl;
+    const int d = sys.d, M = sys.M;
+    const size_t dd = (size_t)d * d;
+    for (int k = threadIdx.x; k <= M; k += blockDim.x) {
+        const double v = (k < M) ? sys.u[(size_t)k * sys.N + j] : (sys.delta ? sys.delta[e] : 0.0);
+        const float h = (float)v;
+        us[k] = make_float2(h, (float)(v - (double)h));
+    }
+    __syncthreads();
+    const float fp = (float)prm->p;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < dd; idx += (size_t)gridDim.x * blockDim.x) {
+        const float4 h0 = sH[idx];
+        float rh = h0.x, rl = h0.z, ih = h0.y, il = h0.w;
+        for (int k = 0; k < M; ++k) {
+            const float4 hk = sH[(size_t)(1 + k) * dd + idx];
+            big_pair_fma(rh, rl, us[k], hk.x, hk.z);
+            big_pair_fma(ih, il, us[k], hk.y, hk.w);
+        }
+        if (sys.has_det) {
+            const float4 hd = sH[(size_t)(M + 1) * dd + idx];
+            big_pair_fma(rh, rl, us[M], hd.x, hd.z);
+            big_pair_fma(ih, il, us[M], hd.y, hd.w);
+        }
+        big_norm(rh, rl);
+        big_norm(ih, il);
+        float xrh = ih, xrl = il, xih = -rh, xil = -rl;   // X = -i (s H)
+        X[(size_t)item * mstride + idx] = big_gsplit(xrh, xrl, xih, xil, ex);
+        if (prm->p > 1) {
+            big_div(xrh, xrl, fp);
+            big_div(xih, xil, fp);
+        }
+        const int a = (int)(idx / d), b = (int)(idx - (size_t)a * d);
+        if (a == b) big_add1(xrh, xrl);
+        Z[(size_t)item * mstride + idx] = big_gsplit(xrh, xrl, xih, xil, ezp);
+    }
+}
+
 // ------------------------------------------------------------------------------------------
 // batched product C = A B (T x T tile per CTA), epilogue:
 //   kind 0: C = I + AB / i     (Horner step i)
@@ -286,22 +347,17 @@ __global__ void k_big_store_u(int d, const E* __restrict__ Z, size_t mstride, C*
 // adjoint
 // ------------------------------------------------------------------------------------------
 // XH = X^dag with X = -i s H_j assembled in the compute precision R (as the per-slice adjoint
-// kernel does); Ubar = G_j Psi_{j-1}^dag from the panel-layout states and costates;
-// Z11 = I + XH / p; Z12 = Ubar / p.
+// kernel does) and, for the block recursion (Z11 set), Z11 = I + XH / p.
 template <typename R>
-__global__ void k_big_adj_init(const DevParams* __restrict__ prm, SysView<R> sys, StateView<R> sv, int j0, int wlen,
-                               const C_t<R>* __restrict__ states, const C_t<R>* __restrict__ Gbuf, int wmax,
-                               C_t<R>* __restrict__ XH, C_t<R>* __restrict__ Ubar, C_t<R>* __restrict__ Z11,
-                               C_t<R>* __restrict__ Z12, size_t mstride) {
+__global__ void k_big_adj_init(const DevParams* __restrict__ prm, SysView<R> sys, int j0, int wlen,
+                               C_t<R>* __restrict__ XH, C_t<R>* __restrict__ Z11, size_t mstride) {
     using C = C_t<R>;
     const int item = blockIdx.y, jl = item % wlen, e = item / wlen, j = j0 + jl;
     const int d = sys.d, M = sys.M;
-    const size_t dd = (size_t)d * d, slice = sv.slice();
+    const size_t dd = (size_t)d * d;
     const R s = (R)prm->s;
     const R ip = R(1) / R(prm->p);
     const R de = sys.delta ? (R)sys.delta[e] : R(0);
-    const C* Gj = Gbuf + ((size_t)e * wmax + jl) * slice;
-    const C* Pj = states + ((size_t)e * (wmax + 1) + jl) * slice;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < dd; idx += (size_t)gridDim.x * blockDim.x) {
         const int a = (int)(idx / d), b = (int)(idx - (size_t)a * d);
         // X[b][a] = -i s H[b][a]  ->  XH[a][b] = conj(X[b][a])
@@ -321,22 +377,55 @@ __global__ void k_big_adj_init(const DevParams* __restrict__ prm, SysView<R> sys
         C xh;
         xh.x = s * h.y;      // X = (s hi, -s hr); conj -> (s hi, s hr)
         xh.y = s * h.x;
-        C ub = czero<C>();
-        for (int sc = 0; sc < sv.Spad; ++sc) {
-            const size_t pa = (size_t)(sc / sv.cb) * sv.pstride + (size_t)a * sv.cb + (sc % sv.cb);
-            const size_t pb = (size_t)(sc / sv.cb) * sv.pstride + (size_t)b * sv.cb + (sc % sv.cb);
-            cfma_bcj(ub, Gj[pa], Pj[pb]);
-        }
         const size_t base = (size_t)item * mstride + idx;
         XH[base] = xh;
-        Ubar[base] = ub;
-        C z1, z2;
-        z1.x = xh.x * ip + (a == b ? R(1) : R(0));
-        z1.y = xh.y * ip;
-        z2.x = ub.x * ip;
-        z2.y = ub.y * ip;
-        Z11[base] = z1;
-        Z12[base] = z2;
+        if (Z11) {
+            C z1;
+            z1.x = xh.x * ip + (a == b ? R(1) : R(0));
+            z1.y = xh.y * ip;
+            Z11[base] = z1;
+        }
+    }
+}
+
+// The factors of Ubar = G_j Psi_{j-1}^dag as d x d row-major matrices for the tiled product:
+// Gm[a][c] = G_j[a][c] and Ph[c][b] = conj(Psi_{j-1}[b][c]) for the S propagated columns c,
+// zero for c >= S (panel layout in: column c of panel c / cb).
+template <typename C>
+__global__ void k_big_ubar_factors(int d, StateView<typename std::conditional<sizeof(C) == 8, float, double>::type> sv,
+                                   int wlen, const C* __restrict__ states, const C* __restrict__ Gbuf, int wmax,
+                                   C* __restrict__ Gm, C* __restrict__ Ph, size_t mstride) {
+    const int item = blockIdx.y, jl = item % wlen, e = item / wlen;
+    const size_t dd = (size_t)d * d, slice = sv.slice();
+    const C* Gj = Gbuf + ((size_t)e * wmax + jl) * slice;
+    const C* Pj = states + ((size_t)e * (wmax + 1) + jl) * slice;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < dd; idx += (size_t)gridDim.x * blockDim.x) {
+        const int a = (int)(idx / d), c = (int)(idx - (size_t)a * d);   // Gm row a col c; Ph row c col a
+        C g = czero<C>(), q = czero<C>();
+        if (c < sv.S) {
+            const size_t pa = (size_t)(c / sv.cb) * sv.pstride + (size_t)a * sv.cb + (c % sv.cb);
+            g = Gj[pa];
+            q = Pj[pa];
+            q.y = -q.y;
+        }
+        Gm[(size_t)item * mstride + idx] = g;
+        Ph[(size_t)item * mstride + (size_t)c * d + a] = q;
+    }
+}
+
+// Z12 = Ubar / p (block recursion start)
+template <typename C>
+__global__ void k_big_scale_p(const DevParams* __restrict__ prm, int d, const C* __restrict__ Ub, C* __restrict__ Z12,
+                              size_t mstride) {
+    using S = decltype(C{}.x);
+    const int item = blockIdx.y;
+    const size_t dd = (size_t)d * d;
+    const S ip = S(1) / S(prm->p);
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < dd; idx += (size_t)gridDim.x * blockDim.x) {
+        C v = Ub[(size_t)item * mstride + idx];
+        v.x *= ip;
+        v.y *= ip;
+        Z12[(size_t)item * mstride + idx] = v;
     }
 }
 
@@ -454,9 +543,20 @@ k_big_grad(const DevParams* __restrict__ prm, SysView<R> sys, int j0, int wlen, 
     const size_t dd = (size_t)d * d;
     const C_t<R>* xb = Xbar + (size_t)item * mstride;
     const C_t<R>* hk = sys.Hk + (size_t)k * dd;
+    // per-thread partials: FP32 form as (hi, lo) pairs of exact products, FP64 form in FP64; the
+    // block sum in FP64
     double v = 0.0;
-    for (size_t idx = threadIdx.x; idx < dd; idx += blockDim.x)
-        v += (double)xb[idx].x * (double)hk[idx].y - (double)xb[idx].y * (double)hk[idx].x;
+    if constexpr (sizeof(R) == 4) {
+        float hi = 0.f, lo = 0.f;
+        for (size_t idx = threadIdx.x; idx < dd; idx += blockDim.x) {
+            pair_acc(hi, lo, xb[idx].x, hk[idx].y);
+            pair_acc(hi, lo, -xb[idx].y, hk[idx].x);
+        }
+        v = (double)hi + (double)lo;
+    } else {
+        for (size_t idx = threadIdx.x; idx < dd; idx += blockDim.x)
+            v += (double)xb[idx].x * (double)hk[idx].y - (double)xb[idx].y * (double)hk[idx].x;
+    }
     v = block_sum(v, red);
     if (threadIdx.x == 0) gpart[((size_t)e * sys.M + k) * sys.N + j] = prm->s * v;
 }
@@ -683,8 +783,12 @@ cudaError_t launch_big_expm(const BigArgs<R>& a, const DevParams& hp, bool split
         // squarings: eu), the operand of a plain FP32 Horner step is in full form
         const float mz = std::ldexp(1.5f, hp.ez + 11), mu = std::ldexp(1.5f, hp.eu + 11);
         const int ezp = (p == 1) ? hp.eu : ((p - 1 <= m_split) ? hp.ez : kFullForm);
-        k_big_assemble<float4><<<dim3(eb, items), 256, 0, st>>>(a.prm, a.bsys, a.j0, a.wlen, X, Za, a.mstride,
-                                                                hp.ex, ezp);
+        if (a.sH)
+            k_big_assemble_split<<<dim3(eb, items), 256, 0, st>>>(a.prm, a.bsys, a.sH, a.j0, a.wlen, X, Za, a.mstride,
+                                                                  hp.ex, ezp);
+        else
+            k_big_assemble<float4><<<dim3(eb, items), 256, 0, st>>>(a.prm, a.bsys, a.j0, a.wlen, X, Za, a.mstride,
+                                                                    hp.ex, ezp);
         count();
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
         float4 *zin = Za, *zout = Zb;
@@ -749,11 +853,19 @@ cudaError_t launch_big_adj(const BigArgs<R>& a, const SysView<R>& sys, const Sta
     C* Z12a = Z11a + (size_t)items * ms;
     C* Z11b = Z12a + (size_t)items * ms;
     C* Z12b = Z11b + (size_t)items * ms;
-    k_big_adj_init<R><<<dim3(eb, items), 256, 0, st>>>(a.prm, sys, sv, a.j0, a.wlen, states, Gbuf, a.wmax, XH, Ub,
-                                                        Z11a, Z12a, ms);
+    k_big_adj_init<R><<<dim3(eb, items), 256, 0, st>>>(a.prm, sys, a.j0, a.wlen, XH, Z11a, ms);
     count();
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
+    // Ubar = G Psi^dag as a tiled product (factors staged in Z11b / Z12b, free until the first step)
+    k_big_ubar_factors<C><<<dim3(eb, items), 256, 0, st>>>(d, sv, a.wlen, states, Gbuf, a.wmax, Z11b, Z12b, ms);
+    count();
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    if ((err = mm_launch<C, 0>(d, items, Z11b, Z12b, Ub, ms, 1, 0, st)) != cudaSuccess) return err;
+    count();
+    k_big_scale_p<C><<<dim3(eb, items), 256, 0, st>>>(a.prm, d, Ub, Z12a, ms);
+    count();
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
     const int T = (sizeof(C) == 16) ? 32 : big_tile(d);   // 16-byte elements: 32 x 32 tiles (SMEM, registers)
     C *z11 = Z11a, *z12 = Z12a, *o11 = Z11b, *o12 = Z12b;
     auto blk = [&](const C* A11, const C* A12, const C* B11, const C* B12, int kind, int i) {
@@ -804,12 +916,16 @@ cudaError_t launch_big_adj_rev(const BigArgs<R>& a, const SysView<R>& sys, const
     C* Za = XH + (size_t)items * ms;
     C* Zb = Za + (size_t)items * ms;
     C* Xb = Zb + (size_t)items * ms;
-    // XH and Ubar (into Za); the initial Z11 / Z12 land in Zb / Xb and are not used
-    k_big_adj_init<R><<<dim3(eb, items), 256, 0, st>>>(a.prm, sys, sv, a.j0, a.wlen, states, Gbuf, a.wmax, XH, Za, Zb,
-                                                        Xb, ms);
+    // XH; Ubar = G Psi^dag into Za by a tiled product (factors staged in Zb / Xb)
+    k_big_adj_init<R><<<dim3(eb, items), 256, 0, st>>>(a.prm, sys, a.j0, a.wlen, XH, static_cast<C*>(nullptr), ms);
     count();
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
+    k_big_ubar_factors<C><<<dim3(eb, items), 256, 0, st>>>(d, sv, a.wlen, states, Gbuf, a.wmax, Zb, Xb, ms);
+    count();
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    if ((err = mm_launch<C, 0>(d, items, Zb, Xb, Za, ms, 1, 0, st)) != cudaSuccess) return err;
+    count();
     if ((err = cudaMemsetAsync(Xb, 0, (size_t)items * ms * sizeof(C), st)) != cudaSuccess) return err;
     const int T = (sizeof(C) == 16) ? 32 : big_tile(d);
     C *zb = Za, *zo = Zb;

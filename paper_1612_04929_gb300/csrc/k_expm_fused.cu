@@ -335,13 +335,27 @@ k_expm_adj(const DevParams* __restrict__ prm, SysView<R> sys, StateView<R> st, i
     }
     // dC/du_{k,j} = Re tr(Xbar^dag (-i s H_k)) = s sum_ab (Xbar_re Hk_im - Xbar_im Hk_re)
     const size_t dd = (size_t)d * d;
+    // per-thread partials: FP32 form as (hi, lo) pairs of exact products, FP64 form in FP64; the
+    // block sum in FP64
     for (int k = 0; k < sys.M; ++k) {
         double v = 0.0;
-        for (int idx = tid; idx < d * d; idx += blockDim.x) {
-            const int a = idx / d, b = idx - a * d;
-            const C xb = z12[a * LD + b];
-            const C hk = sys.Hk[k * dd + idx];
-            v += (double)xb.x * (double)hk.y - (double)xb.y * (double)hk.x;
+        if constexpr (sizeof(R) == 4) {
+            float hi = 0.f, lo = 0.f;
+            for (int idx = tid; idx < d * d; idx += blockDim.x) {
+                const int a = idx / d, b = idx - a * d;
+                const C xb = z12[a * LD + b];
+                const C hk = sys.Hk[k * dd + idx];
+                pair_acc(hi, lo, xb.x, hk.y);
+                pair_acc(hi, lo, -xb.y, hk.x);
+            }
+            v = (double)hi + (double)lo;
+        } else {
+            for (int idx = tid; idx < d * d; idx += blockDim.x) {
+                const int a = idx / d, b = idx - a * d;
+                const C xb = z12[a * LD + b];
+                const C hk = sys.Hk[k * dd + idx];
+                v += (double)xb.x * (double)hk.y - (double)xb.y * (double)hk.x;
+            }
         }
         v = block_sum(v, red);
         if (tid == 0) gpart[((size_t)e * sys.M + k) * sys.N + j] = prm->s * v;
@@ -484,9 +498,10 @@ k_expm_adj_rev(const DevParams* __restrict__ prm, SysView<R> sys, StateView<R> s
             }
     }
     const size_t dd = (size_t)d * d;
-    for (int k = 0; k < sys.M; ++k) {
+    for (int k = 0; k < sys.M; ++k) {   // partials: FP32 pairs of exact products (FP32 form); FP64 sum
         double v = 0.0;
         if (act) {
+            float hi = 0.f, lo = 0.f;
 #pragma unroll
             for (int a = 0; a < MT; ++a)
 #pragma unroll
@@ -494,9 +509,15 @@ k_expm_adj_rev(const DevParams* __restrict__ prm, SysView<R> sys, StateView<R> s
                     const int r = ty + G * a, c = tx + G * b;
                     if (r < d && c < d) {
                         const C hk = sys.Hk[k * dd + (size_t)r * d + c];
-                        v += (double)xb[a][b].x * (double)hk.y - (double)xb[a][b].y * (double)hk.x;
+                        if constexpr (sizeof(R) == 4) {
+                            pair_acc(hi, lo, xb[a][b].x, hk.y);
+                            pair_acc(hi, lo, -xb[a][b].y, hk.x);
+                        } else {
+                            v += (double)xb[a][b].x * (double)hk.y - (double)xb[a][b].y * (double)hk.x;
+                        }
                     }
                 }
+            if constexpr (sizeof(R) == 4) v = (double)hi + (double)lo;
         }
         v = block_sum(v, red);
         if (tid == 0) gpart[((size_t)e * sys.M + k) * sys.N + j] = prm->s * v;

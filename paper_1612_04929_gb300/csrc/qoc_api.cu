@@ -322,7 +322,8 @@ void plan_impl(qoc_ctx* c) {
     const size_t dd = (size_t)d * d;
     A(c->HR, (M + 2) * dd * cs, "alloc H");
     check_cuda(c, launch_convert<R>(c->H64.as<double2>(), c->HR.as<C>(), (M + 2) * dd, st), "convert H");
-    if (split_exp<R>(c) && c->path_kind == 0) A(c->sH, (M + 2) * dd * sizeof(float4), "alloc sH");
+    if (split_exp<R>(c)) A(c->sH, (M + 2) * dd * sizeof(float4), "alloc sH");
+    else c->sH.release();
     // costs
     std::vector<int> mask(d, 0);
     for (int f : c->forb) mask[f] = 1;
@@ -500,7 +501,7 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
         ++launches;
     }
     if constexpr (sizeof(R) == 4) {
-        if (split_exp<R>(c) && c->path_kind == 0) {   // s H_k pairs for this evaluation's (p, n)
+        if (split_exp<R>(c)) {   // s H_k pairs for this evaluation's (p, n)
             B(st);
             L(launch_split_scale(prm, c->H64.as<double2>(), (M + 2) * dd, c->sH.as<float4>(), st), "theta", st);
         }
@@ -545,7 +546,8 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
     auto zbig = [&](int w) { return big_rev ? c->Zbig.as<C>() + (size_t)(w & 1) * zbig_set : nullptr; };
     auto big_args = [&](int w) {
         const int j0 = w * W;
-        return BigArgs<R>{prm, bsys, d, E, j0, std::min(W, N - j0), W, c->scratch.p, c->mstride, Ub(w), c->ustride};
+        return BigArgs<R>{prm,      bsys,          d,     E,          j0, std::min(W, N - j0), W, c->scratch.p,
+                          c->mstride, Ub(w), c->ustride, c->sH.p ? c->sH.as<float4>() : nullptr};
     };
     int extra = 0;   // kernels of the batched calls beyond the one counted by L
     // stored product operands of the per-slice path (two wave sets)

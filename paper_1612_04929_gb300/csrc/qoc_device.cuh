@@ -169,6 +169,17 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
 }
 
 // FP64 block reduction (blockDim.x multiple of 32, <= 1024); result valid in thread 0.
+// (hi, lo) += a b with the exact FP32 product (FMA residual) and an error-free sum: per-thread
+// partial sums of products at pair precision without the FP64 pipe
+__device__ __forceinline__ void pair_acc(float& hi, float& lo, float a, float b) {
+    const float p = a * b;
+    const float e = fmaf(a, b, -p);
+    float s, r;
+    two_sum(hi, p, s, r);
+    hi = s;
+    lo += r + e;
+}
+
 __device__ __forceinline__ double block_sum(double v, double* scratch /* >= 32 doubles */) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;

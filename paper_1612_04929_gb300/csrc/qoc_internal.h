@@ -141,6 +141,7 @@ struct BigArgs {
     size_t mstride;       // elements per matrix slot (>= d * d)
     void* Ubuf;           // propagator buffer of the wave (C_t<R>, U at 0 and U^dag at ustride / 2)
     long long ustride;
+    const float4* sH;     // FP32 split form: s H_0 .. s H_det as pairs (launch_split_scale), or nullptr
 };
 // bytes of scratch per wave item
 inline size_t big_scratch_per_item(int d, bool fp64) {
