@@ -175,73 +175,97 @@ __device__ __forceinline__ unsigned pair_maxbits(const float4 v) {
     return __float_as_uint(fmaxf(fabsf(v.x), fabsf(v.y)));
 }
 
-// One FP32 step y = Mx x (+ add) from the grid-split block xg: g lanes per output sum the grid
-// parts (S, exact) and the cross terms (L) of b = q, q + g, ...; the shuffle reduction adds S
-// and L with plain adds (S stays exact); lane q = 0 forms the pair S + L without error, adds the
-// source, normalises, keeps it in y, hands it to `emit` and raises *ymax to its largest component.
-template <typename Mt, typename S, typename Emit>
+// One FP32 step y = Mx x (+ add) from the grid-split block xg.  A group of g lanes owns row a of
+// the output and NCB consecutive columns of the panel (NCB = cb when the panel has 8 columns,
+// else 1), so each element of Mx is read and split once for NCB outputs; the lanes sum the grid
+// parts (S, exact) and the cross terms (L) of b = q, q + g, ...; the shuffle reduction adds S and
+// L with plain adds (S stays exact); lane q = 0 forms each pair S + L without error, adds the
+// source, normalises, keeps it in y, hands it to `emit` and raises *ymax to the largest component.
+template <int NCB, typename Mt, typename S, typename Emit>
 __device__ __forceinline__ void sweep_step_grid(const Mt* __restrict__ Mx, const float4* __restrict__ xg,
                                                 float4* __restrict__ y, const S* __restrict__ add, int d, int cb,
                                                 int g, float mu, unsigned* ymax, Emit emit) {
-    const int O = d * cb;
+    const int per_row = cb / NCB;
+    const int groups = d * per_row;
     const int ngroups = blockDim.x / g;
     const int gi = threadIdx.x / g, q = threadIdx.x - gi * g;
-    for (int base = 0; base < O; base += ngroups) {
-        const int o = base + gi;
-        float sr = 0.f, si = 0.f, lr = 0.f, li = 0.f;
-        if (o < O) {
-            const int a = o / cb, sl = o - a * cb;
+    for (int base = 0; base < groups; base += ngroups) {
+        const int grp = base + gi;
+        float acc[NCB][4];
+#pragma unroll
+        for (int c = 0; c < NCB; ++c) acc[c][0] = acc[c][1] = acc[c][2] = acc[c][3] = 0.f;
+        int a = 0, sl0 = 0;
+        if (grp < groups) {
+            a = grp / per_row;
+            sl0 = (grp - a * per_row) * NCB;
             const Mt* Mr = Mx + (size_t)a * d;
             for (int b = q; b < d; b += g) {
                 float4 u;
                 float2 uf;
                 gsplit_elem(Mr[b], mu, u, uf);
-                const float4 x = xg[b * cb + sl];
-                sr = fmaf(u.x, x.x, sr);
-                sr = fmaf(-u.y, x.y, sr);
-                si = fmaf(u.x, x.y, si);
-                si = fmaf(u.y, x.x, si);
-                lr = fmaf(u.z, x.x, lr);
-                lr = fmaf(-u.w, x.y, lr);
-                lr = fmaf(uf.x, x.z, lr);
-                lr = fmaf(-uf.y, x.w, lr);
-                li = fmaf(u.z, x.y, li);
-                li = fmaf(u.w, x.x, li);
-                li = fmaf(uf.x, x.w, li);
-                li = fmaf(uf.y, x.z, li);
+                const float4* xr = xg + b * cb + sl0;
+#pragma unroll
+                for (int c = 0; c < NCB; ++c) {
+                    const float4 x = xr[c];
+                    float* s = acc[c];
+                    s[0] = fmaf(u.x, x.x, s[0]);
+                    s[0] = fmaf(-u.y, x.y, s[0]);
+                    s[1] = fmaf(u.x, x.y, s[1]);
+                    s[1] = fmaf(u.y, x.x, s[1]);
+                    s[2] = fmaf(u.z, x.x, s[2]);
+                    s[2] = fmaf(-u.w, x.y, s[2]);
+                    s[2] = fmaf(uf.x, x.z, s[2]);
+                    s[2] = fmaf(-uf.y, x.w, s[2]);
+                    s[3] = fmaf(u.z, x.y, s[3]);
+                    s[3] = fmaf(u.w, x.x, s[3]);
+                    s[3] = fmaf(uf.x, x.w, s[3]);
+                    s[3] = fmaf(uf.y, x.z, s[3]);
+                }
             }
         }
-        for (int off = g >> 1; off > 0; off >>= 1) {
-            sr += __shfl_xor_sync(0xffffffffu, sr, off);
-            si += __shfl_xor_sync(0xffffffffu, si, off);
-            lr += __shfl_xor_sync(0xffffffffu, lr, off);
-            li += __shfl_xor_sync(0xffffffffu, li, off);
-        }
-        if (o < O && q == 0) {
-            float4 acc;
-            two_sum(sr, lr, acc.x, acc.z);
-            two_sum(si, li, acc.y, acc.w);
-            if (add) kadd(acc, kfrom(add[o]));
-            knorm(acc);
-            y[o] = acc;
-            atomicMax(ymax, pair_maxbits(acc));
-            emit(o, acc);
+        for (int off = g >> 1; off > 0; off >>= 1)
+#pragma unroll
+            for (int c = 0; c < NCB; ++c)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) acc[c][i] += __shfl_xor_sync(0xffffffffu, acc[c][i], off);
+        if (grp < groups && q == 0) {
+            unsigned mb = 0u;
+#pragma unroll
+            for (int c = 0; c < NCB; ++c) {
+                const int o = a * cb + sl0 + c;
+                float4 v;
+                two_sum(acc[c][0], acc[c][2], v.x, v.z);
+                two_sum(acc[c][1], acc[c][3], v.y, v.w);
+                if (add) kadd(v, kfrom(add[o]));
+                knorm(v);
+                y[o] = v;
+                mb = max(mb, pair_maxbits(v));
+                emit(o, v);
+            }
+            atomicMax(ymax, mb);
         }
     }
 }
 
-// lanes per output and block size: minimise the issue time of one step on one SM
-// (passes x warps per scheduler x instructions per lane)
-static void pick_sweep_shape(int d, int cb, bool pair, int& g, int& threads) {
-    const int O = d * cb;
+// lanes per output group and block size: minimise the issue time of one step on one SM
+// (passes x warps per scheduler x instructions per lane).  FP32 (grid step): a group is one row
+// and NCB columns (NCB = 8 for 8-column panels, else 1); FP64 (pair-free step): one output.
+static void pick_sweep_shape(int d, int cb, bool fp32, int& g, int& threads) {
+    const int ncb = (fp32 && cb == 8) ? 8 : 1;
+    const int O = d * (cb / ncb);
     long best = -1;
     for (int gg = 1, lg = 0; gg <= 32; gg <<= 1, ++lg) {
+        const int tmax = fp32 ? 512 : 1024;   // the kernels' launch bounds
         int thr = ((O * gg + 31) / 32) * 32;
-        thr = thr > 1024 ? 1024 : thr;
+        thr = thr > tmax ? tmax : thr;
         const int groups = thr / gg;
         const int passes = (O + groups - 1) / groups;
         const int wps = (thr / 32 + 3) / 4;
-        const long cost = (long)passes * wps * (((d + gg - 1) / gg) * (pair ? 20 : 10) + (pair ? 8 : 12) * lg);
+        // instructions per lane: per b of the row, the reduction, the row-group epilogue
+        const long per_b = !fp32 ? 10 : (ncb == 1 ? 20 : 8 + 14L * ncb);
+        const long red = !fp32 ? 12L * lg : 8L * ncb * lg;
+        const long epi = (fp32 && ncb > 1) ? 30L * ncb : 0;
+        const long cost = (long)passes * wps * (((d + gg - 1) / gg) * per_b + red + epi);
         if (best < 0 || cost < best) {
             best = cost;
             g = gg;
@@ -253,8 +277,8 @@ static void pick_sweep_shape(int d, int cb, bool pair, int& g, int& threads) {
 // ------------------------------------------------------------------------------------------
 // forward propagation (mode 0) and checkpoint replay (mode 1)
 // ------------------------------------------------------------------------------------------
-template <typename R, int RING, typename Mt>
-__global__ void __launch_bounds__(1024)
+template <typename R, int RING, typename Mt, int NCB>
+__global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 1024)
 k_chain(int d, StateView<R> sv, int wlen, int seg, int mode, K_t<R>* __restrict__ ckpt, size_t ck_estride, int seg0,
         int nseg_total, const Mt* __restrict__ Ubuf, long long ustride, int wmax, C_t<R>* __restrict__ states,
         int g, const DevParams* __restrict__ prm) {
@@ -296,7 +320,8 @@ k_chain(int d, StateView<R> sv, int wlen, int seg, int mode, K_t<R>* __restrict_
             if (tid == 0) smax[(k + 1) & 1] = 0u;
             for (int i = tid; i < (int)panel; i += blockDim.x) xg[i] = pair_to_grid(xa[i], mx);
             __syncthreads();
-            sweep_step_grid<Mt, C>(M, xg, xb, static_cast<const C*>(nullptr), d, cb, g, mu, &smax[(k + 1) & 1], emit);
+            sweep_step_grid<NCB, Mt, C>(M, xg, xb, static_cast<const C*>(nullptr), d, cb, g, mu, &smax[(k + 1) & 1],
+                                        emit);
         } else {
             sweep_step<Mt, K, C>(M, xa, xb, nullptr, d, cb, g, emit);
         }
@@ -348,18 +373,25 @@ k_chain(int d, StateView<R> sv, int wlen, int seg, int mode, K_t<R>* __restrict_
     }
 }
 
-template <typename R, int RING, typename Mt>
-static cudaError_t chain_ring(const ChainArgs<R>& a, const Mt* U, size_t smem, cudaStream_t st) {
+template <typename R, int RING, typename Mt, int NCB>
+static cudaError_t chain_ring_n(const ChainArgs<R>& a, const Mt* U, size_t smem, cudaStream_t st) {
     cudaError_t err =
-        cudaFuncSetAttribute(k_chain<R, RING, Mt>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_chain<R, RING, Mt, NCB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     int g = 1, threads = 256;
     pick_sweep_shape(a.d, a.sv.cb, sizeof(R) == 4, g, threads);
     const int nz = a.mode == 0 ? 1 : (a.wlen + a.seg - 1) / a.seg;
-    k_chain<R, RING, Mt><<<dim3(a.sv.ncb, a.E, nz), threads, smem, st>>>(a.d, a.sv, a.wlen, a.seg, a.mode, a.ckpt,
-                                                                          a.ck_estride, a.seg0, a.nseg_total, U,
-                                                                          a.ustride, a.wmax, a.states, g, a.prm);
+    k_chain<R, RING, Mt, NCB><<<dim3(a.sv.ncb, a.E, nz), threads, smem, st>>>(
+        a.d, a.sv, a.wlen, a.seg, a.mode, a.ckpt, a.ck_estride, a.seg0, a.nseg_total, U, a.ustride, a.wmax, a.states,
+        g, a.prm);
     return cudaGetLastError();
+}
+
+// FP32: 8-column panels take the row-group step (NCB = 8)
+template <typename R, int RING, typename Mt>
+static cudaError_t chain_ring(const ChainArgs<R>& a, const Mt* U, size_t smem, cudaStream_t st) {
+    if (sizeof(R) == 4 && a.sv.cb == 8) return chain_ring_n<R, RING, Mt, (sizeof(R) == 4 ? 8 : 1)>(a, U, smem, st);
+    return chain_ring_n<R, RING, Mt, 1>(a, U, smem, st);
 }
 
 template <typename R, typename Mt>
@@ -392,8 +424,8 @@ cudaError_t launch_chain(const ChainArgs<R>& a, cudaStream_t st) {
 // (zero when a.cin is null) the CTA sets G_b = Y + src_b, runs G_{jl-1} = U_jl^dag G_jl + src_{jl-1}
 // down to jl = a + 1, and leaves out = U_a^dag G_a, the in-carry of the segment below; `out`
 // goes to a.cout.  A whole wave is one segment (seg = wlen) with the carry as in- and out-carry.
-template <typename R, int RING, typename S, typename Mt>
-__global__ void __launch_bounds__(1024) k_costate(CostateArgs<R> A, int g) {
+template <typename R, int RING, typename S, typename Mt, int NCB>
+__global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 1024) k_costate(CostateArgs<R> A, int g) {
     using C = C_t<R>;
     using K = K_t<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -449,7 +481,7 @@ __global__ void __launch_bounds__(1024) k_costate(CostateArgs<R> A, int g) {
             if (tid == 0) smax[(k + 1) & 1] = 0u;
             for (int i = tid; i < (int)panel; i += blockDim.x) xg[i] = pair_to_grid(xa[i], mx);
             __syncthreads();
-            sweep_step_grid<Mt, S>(M, xg, xb, add, d, cb, g, mu, &smax[(k + 1) & 1], emit);
+            sweep_step_grid<NCB, Mt, S>(M, xg, xb, add, d, cb, g, mu, &smax[(k + 1) & 1], emit);
         } else {
             sweep_step<Mt, K, S>(M, xa, xb, add, d, cb, g, emit);
         }
@@ -512,16 +544,22 @@ __global__ void __launch_bounds__(1024) k_costate(CostateArgs<R> A, int g) {
     }
 }
 
-template <typename R, int RING, typename S, typename Mt>
-static cudaError_t costate_ring(const CostateArgs<R>& a, size_t smem, cudaStream_t st) {
+template <typename R, int RING, typename S, typename Mt, int NCB>
+static cudaError_t costate_ring_n(const CostateArgs<R>& a, size_t smem, cudaStream_t st) {
     cudaError_t err =
-        cudaFuncSetAttribute(k_costate<R, RING, S, Mt>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_costate<R, RING, S, Mt, NCB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     int g = 1, threads = 256;
     pick_sweep_shape(a.d, a.sv.cb, sizeof(R) == 4, g, threads);
     const int nz = (a.wlen + a.seg - 1) / a.seg;
-    k_costate<R, RING, S, Mt><<<dim3(a.sv.ncb, a.E, nz), threads, smem, st>>>(a, g);
+    k_costate<R, RING, S, Mt, NCB><<<dim3(a.sv.ncb, a.E, nz), threads, smem, st>>>(a, g);
     return cudaGetLastError();
+}
+
+template <typename R, int RING, typename S, typename Mt>
+static cudaError_t costate_ring(const CostateArgs<R>& a, size_t smem, cudaStream_t st) {
+    if (sizeof(R) == 4 && a.sv.cb == 8) return costate_ring_n<R, RING, S, Mt, (sizeof(R) == 4 ? 8 : 1)>(a, smem, st);
+    return costate_ring_n<R, RING, S, Mt, 1>(a, smem, st);
 }
 
 template <typename R, typename S, typename Mt>
