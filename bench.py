@@ -259,9 +259,13 @@ def ours_arm(args):
     d, p, n = prob.d, info["p"], info["n"]
     per_slice = {"expm_fwd": expm_flops_per_slice(d, p, n),
                  "expm_fwd (recompute)": expm_flops_per_slice(d, p, n),
-                 "expm_adj": 3 * expm_flops_per_slice(d, p, n) + 8.0 * d * d * prob.S}
+                 # reverse mode: 2 products per forward product; block recursion: 3
+                 "expm_adj": (2 if info.get("adjoint_form", 1) == 0 else 3) * expm_flops_per_slice(d, p, n)
+                             + 8.0 * d * d * prob.S}
     # the roofline line covers the dominant kernel that has an algorithmic flop count (the
     # exponential kernels); the serial sweeps are latency-bound and reported in "kernels"
+    if info.get("adjoint_form") == 2:   # first-order gradient: no adjoint exponential
+        per_slice.pop("expm_adj")
     cands = {k: v for k, v in prof.items() if k in per_slice}
     roof = None
     if cands:
@@ -390,7 +394,9 @@ def ours_arm(args):
                 "data": f"synthetic (seeded {prob.name} system, random controls)",
                 "config": config_of(prob, precision, info["ckpt_stride"],
                                     {"p": p, "n": n, "wave_slices": info["wave_slices"], "n_waves": info["n_waves"],
-                                     "gradient": args.gradient, "graph": args.graph}),
+                                     "gradient": args.gradient, "graph": args.graph,
+                                     "adjoint": {0: "reverse mode", 1: "block recursion", 2: "none (first-order)"}.get(
+                                         info.get("adjoint_form"), "?")}),
                 "roofline": roof, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": mn_bytes,
                         "d2h_bytes_per_step": mn_bytes + 6 * 8 + 32},

@@ -133,6 +133,9 @@ typedef struct qoc_info {
     int launches_per_eval;/* kernels launched by one evaluation */
     int kernel_path;      /* 0: fused per-slice kernels (small d); 1: batched tiled GEMM (large d) */
     long long device_bytes; /* device memory held by the context */
+    int adjoint_form;     /* gradient of the last evaluation: 0 reverse mode over the stored products
+                             (2 products per forward product), 1 block recursion (3), 2 first-order
+                             (Eq. 11, no adjoint exponential) */
 } qoc_info;
 
 /* Per-kernel timings gathered while qoc_options.profile is set: for each kernel class the number

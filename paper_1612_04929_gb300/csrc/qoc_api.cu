@@ -153,6 +153,7 @@ struct qoc_ctx {
     DevBuf Zbuf;                         // product operands for the reverse-mode adjoint (per-slice path)
     size_t zmstride = 0;
     DevBuf Zbig;                         // the same for the batched path, sized at evaluation for p - 1 + n
+    bool last_big_rev = false;           // the last batched-path evaluation used the reverse mode
     cudaGraphExec_t gexec = nullptr;     // captured evaluation (qoc_options.graph) and its pointers
     const void* gkey[3] = {nullptr, nullptr, nullptr};
     void drop_graph() {
@@ -543,6 +544,7 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
                 cudaGetLastError();   // a failed allocation only means: block recursion
         }
     }
+    if (big) c->last_big_rev = big_rev;
     auto zbig = [&](int w) { return big_rev ? c->Zbig.as<C>() + (size_t)(w & 1) * zbig_set : nullptr; };
     auto big_args = [&](int w) {
         const int j0 = w * W;
@@ -1133,6 +1135,9 @@ qoc_status qoc_get_info(qoc_ctx* ctx, qoc_info* info) {
     info->launches_per_eval = ctx->launches;
     info->kernel_path = ctx->path_kind;
     info->device_bytes = (long long)ctx->device_bytes();
+    if (ctx->opt.gradient == QOC_GRAD_FIRST_ORDER) info->adjoint_form = 2;
+    else if (ctx->path_kind == 1) info->adjoint_form = ctx->last_big_rev ? 0 : 1;
+    else info->adjoint_form = (ctx->Zbuf.p && info->p - 1 + info->n <= kZCap) ? 0 : 1;
     return QOC_OK;
     QOC_GUARD_END
 }

@@ -61,7 +61,7 @@ class qoc_profile(ct.Structure):
 class qoc_info(ct.Structure):
     _fields_ = [("p", ct.c_int), ("n", ct.c_int), ("theta", ct.c_double), ("ckpt_stride", ct.c_int),
                 ("wave_slices", ct.c_int), ("n_waves", ct.c_int), ("launches_per_eval", ct.c_int), ("kernel_path", ct.c_int),
-                ("device_bytes", ct.c_longlong)]
+                ("device_bytes", ct.c_longlong), ("adjoint_form", ct.c_int)]
 
 
 _lib = None
