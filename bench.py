@@ -192,6 +192,18 @@ def expm_flops_per_slice(d, p, n):
     return (p - 1 + n) * 8.0 * d ** 3
 
 
+def adj_flops_per_slice(form, d, p, n, S):
+    """Algorithmic flops of one slice's adjoint: reverse mode 2 products per forward product plus
+    Ubar = G Psi^dag; block recursion 3; low-rank reverse mode (cotangent as d x r factors,
+    r = 2^n S): 2 d x d by d x r products per squaring level (r doubling from S), 3 per Horner step
+    and one final rank-r update."""
+    if form == 3:
+        r = S << n
+        return 8.0 * d * d * (2 * S * ((1 << n) - 1) + 3 * (p - 1) * r + r)
+    k = 2 if form == 0 else 3
+    return k * expm_flops_per_slice(d, p, n) + 8.0 * d * d * S
+
+
 def ours_arm(args):
     import numpy as np
     import torch
@@ -259,9 +271,7 @@ def ours_arm(args):
     d, p, n = prob.d, info["p"], info["n"]
     per_slice = {"expm_fwd": expm_flops_per_slice(d, p, n),
                  "expm_fwd (recompute)": expm_flops_per_slice(d, p, n),
-                 # reverse mode: 2 products per forward product; block recursion: 3
-                 "expm_adj": (2 if info.get("adjoint_form", 1) == 0 else 3) * expm_flops_per_slice(d, p, n)
-                             + 8.0 * d * d * prob.S}
+                 "expm_adj": adj_flops_per_slice(info.get("adjoint_form", 1), d, p, n, prob.S)}
     # the roofline line covers the dominant kernel that has an algorithmic flop count (the
     # exponential kernels); the serial sweeps are latency-bound and reported in "kernels"
     if info.get("adjoint_form") == 2:   # first-order gradient: no adjoint exponential
@@ -395,7 +405,8 @@ def ours_arm(args):
                 "config": config_of(prob, precision, info["ckpt_stride"],
                                     {"p": p, "n": n, "wave_slices": info["wave_slices"], "n_waves": info["n_waves"],
                                      "gradient": args.gradient, "graph": args.graph,
-                                     "adjoint": {0: "reverse mode", 1: "block recursion", 2: "none (first-order)"}.get(
+                                     "adjoint": {0: "reverse mode", 1: "block recursion", 2: "none (first-order)",
+                                                 3: "low-rank reverse mode"}.get(
                                          info.get("adjoint_form"), "?")}),
                 "roofline": roof, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": mn_bytes,

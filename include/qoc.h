@@ -135,7 +135,8 @@ typedef struct qoc_info {
     long long device_bytes; /* device memory held by the context */
     int adjoint_form;     /* gradient of the last evaluation: 0 reverse mode over the stored products
                              (2 products per forward product), 1 block recursion (3), 2 first-order
-                             (Eq. 11, no adjoint exponential) */
+                             (Eq. 11, no adjoint exponential), 3 low-rank reverse mode (the cotangent
+                             kept as d x r factors, r = 2^n S; small S, per-slice kernels) */
 } qoc_info;
 
 /* Per-kernel timings gathered while qoc_options.profile is set: for each kernel class the number

@@ -362,6 +362,189 @@ k_expm_adj(const DevParams* __restrict__ prm, SysView<R> sys, StateView<R> st, i
     }
 }
 
+// Low-rank reverse mode.  The cotangent of U_j is Ubar = G_j Psi_{j-1}^dag, of rank S (the
+// propagated columns).  Through the squarings in reverse, Sbar = L R^dag becomes
+// Sbar S^dag + S^dag Sbar = [L, S^dag L] [S R, R]^dag: the rank doubles, so T = Z_1 receives a
+// rank r = 2^n S cotangent.  Through the Horner steps in reverse R stays fixed and only
+// L_{i+1} = X^dag L_i / i changes, with Xbar += L_i (Z_{i+1} R)^dag / i and, for Z_p = I + X / p,
+// Xbar += L_p R^dag / p: the same exact derivative as the dense reverse mode, with d x d by d x r
+// products (r <= kLrMax) in place of d x d by d x d ones.  Used when 8 r <= d (qoc_internal.h).
+
+template <typename R, int MT>
+__global__ void __launch_bounds__(512, (MT <= 2 && sizeof(R) == 4) ? 3 : 1)
+k_expm_adj_lr(const DevParams* __restrict__ prm, SysView<R> sys, StateView<R> st, int j0,
+              const C_t<R>* __restrict__ states, const C_t<R>* __restrict__ Gbuf, int wmax,
+              double* __restrict__ gpart, ZStore<R> zs, int G) {
+    using C = C_t<R>;
+    const int p = prm->p, n = prm->n;
+    if (!(zs.Z && p - 1 + n <= zs.cap)) return;
+    const int d = sys.d, Sr = st.S, cb = st.cb, ps = st.pstride;
+    if (!adj_lowrank_applies(Sr, n, d)) return;
+    const int D = G * MT, LD = D + 1, SZ = D * LD, RL = kLrMax;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ R us[kMaxControls];
+    __shared__ double red[32];
+    C* XH = reinterpret_cast<C*>(smraw);
+    C* SB = XH + SZ;       // stored operand of the current product ...
+    C* SN = SB + SZ;       // ... and of the next one, arriving by cp.async meanwhile
+    C* Lb = SN + SZ;       // L (d x r, leading dimension RL)
+    C* Lt = Lb + d * RL;   // X^dag L / i (next L), or the scratch of a squaring
+    C* Rb = Lt + d * RL;   // R
+    C* Wb = Rb + d * RL;   // Z R (Horner), S R (squaring)
+    const int jl = blockIdx.x, e = blockIdx.y, j = j0 + jl;
+    const int tid = threadIdx.x, tx = tid % G, ty = tid / G;
+    const bool act = tid < G * G;
+    const R s = (R)prm->s;
+    for (int k = tid; k < sys.M; k += blockDim.x) us[k] = (R)sys.u[(size_t)k * sys.N + j];
+    __syncthreads();
+    const R de = sys.delta ? (R)sys.delta[e] : R(0);
+    assemble_X<C, R>(SN, d, D, LD, sys.M, sys.H0, sys.Hk, sys.Hdet, de, us, s);
+    // L = G_j and R = Psi_{j-1} (d x S, from the panel layout)
+    const size_t slice = st.slice();
+    const C* Gj = Gbuf + ((size_t)e * wmax + jl) * slice;
+    const C* Pj = states + ((size_t)e * (wmax + 1) + jl) * slice;
+    for (int idx = tid; idx < d * Sr; idx += blockDim.x) {
+        const int a = idx / Sr, sc = idx - a * Sr;
+        const size_t off = (size_t)(sc / cb) * ps + (size_t)a * cb + (sc % cb);
+        Lb[a * RL + sc] = Gj[off];
+        Rb[a * RL + sc] = Pj[off];
+    }
+    __syncthreads();
+    for (int idx = tid; idx < D * D; idx += blockDim.x) {
+        const int a = idx / D, b = idx - a * D;
+        C x = SN[b * LD + a];
+        x.y = -x.y;
+        XH[a * LD + b] = x;
+    }
+    __syncthreads();   // SN is free again
+    const C* zst = zs.Z + ((size_t)e * zs.wmax + jl) * zs.cap * zs.mstride;
+    auto issue = [&](int r) {
+        if (r >= 0) {
+            const C* src = zst + (size_t)r * zs.mstride;
+            for_rc(d, d, [&](int idx, int a, int b) { cp_async_elem(&SN[a * LD + b], &src[idx]); });
+        }
+        cp_async_commit();
+    };
+    auto next = [&](int r) {   // wait for operand r (in SN), make it SB, start r - 1 into the old SB
+        cp_async_wait<0>();
+        __syncthreads();
+        C* tt = SB; SB = SN; SN = tt;
+        issue(r - 1);
+    };
+    // The two d x r products of a step in one pass: Wo = M Rin with M = SB^dag (SB holds the
+    // conjugate transpose of the stored operand), and Lo = A Lin * scale (A = XH or SB, row-major).
+    // A thread owns rows a and a + H (H = ceil(d / 2)) of one column t of both outputs: four
+    // independent accumulators sharing the operand loads.
+    auto step_products = [&](C* Wo, const C* Rin, C* Lo, const C* A, const C* Lin, int rr, R scale) {
+        const int H = (d + 1) >> 1;
+        for (int o = tid; o < H * rr; o += blockDim.x) {
+            const int a0 = o / rr, tcol = o - a0 * rr;
+            const int a1 = (a0 + H < d) ? a0 + H : a0;
+            C w0 = czero<C>(), w1 = czero<C>(), l0 = czero<C>(), l1 = czero<C>();
+            const C* A0 = A + a0 * LD;
+            const C* A1 = A + a1 * LD;
+#pragma unroll 1
+            for (int b = 0; b < d; ++b) {
+                const C rv = Rin[b * RL + tcol], lv = Lin[b * RL + tcol];
+                const C s0 = SB[b * LD + a0], s1 = SB[b * LD + a1];
+                cfma_cj(w0, s0, rv);
+                cfma_cj(w1, s1, rv);
+                cfma(l0, A0[b], lv);
+                cfma(l1, A1[b], lv);
+            }
+            l0.x *= scale;
+            l0.y *= scale;
+            l1.x *= scale;
+            l1.y *= scale;
+            Wo[a0 * RL + tcol] = w0;
+            Lo[a0 * RL + tcol] = l0;
+            if (a0 + H < d) {
+                Wo[a1 * RL + tcol] = w1;
+                Lo[a1 * RL + tcol] = l1;
+            }
+        }
+    };
+    issue(p - 2 + n);
+    int r = Sr;
+    for (int m = n - 1; m >= 0; --m) {          // squarings in reverse: L <- [L, S^dag L], R <- [S R, R]
+        next(p - 1 + m);
+        step_products(Wb, Rb, Lb + r, SB, Lb, r, R(1));   // S R; S^dag L into columns r .. 2r - 1
+        __syncthreads();
+        for (int o = tid; o < d * r; o += blockDim.x) {
+            const int a = o / r, tcol = o - a * r;
+            Rb[a * RL + tcol + r] = Rb[a * RL + tcol];
+            Rb[a * RL + tcol] = Wb[a * RL + tcol];
+        }
+        r *= 2;
+    }
+    C xb[MT][MT];                               // Xbar
+    zero_acc<C, MT>(xb);
+    // Xbar += scale * sum_t Lm[row][t] conj(Rm[col][t])
+    auto rank_update = [&](const C* Lm, const C* Rm, R scale) {
+        if (!act) return;
+        C acc[MT][MT];
+        zero_acc<C, MT>(acc);
+        for (int tcol = 0; tcol < r; ++tcol) {
+            C a[MT], b[MT];
+#pragma unroll
+            for (int i = 0; i < MT; ++i) {
+                const int row = ty + G * i, col = tx + G * i;
+                a[i] = row < d ? Lm[row * RL + tcol] : czero<C>();
+                b[i] = col < d ? Rm[col * RL + tcol] : czero<C>();
+            }
+#pragma unroll
+            for (int i = 0; i < MT; ++i)
+#pragma unroll
+                for (int jj = 0; jj < MT; ++jj) cfma_bcj(acc[i][jj], a[i], b[jj]);
+        }
+#pragma unroll
+        for (int i = 0; i < MT; ++i)
+#pragma unroll
+            for (int jj = 0; jj < MT; ++jj) {
+                xb[i][jj].x += acc[i][jj].x * scale;
+                xb[i][jj].y += acc[i][jj].y * scale;
+            }
+    };
+    C* Lc = Lb;
+    C* Ln = Lt;
+    for (int i = 1; i <= p - 1; ++i) {          // Horner steps in reverse
+        next(p - 1 - i);                        // SB = Z_{i+1}^dag
+        const R ri = R(1) / R(i);
+        step_products(Wb, Rb, Ln, XH, Lc, r, ri);   // W = Z_{i+1} R; L_{i+1} = X^dag L_i / i
+        __syncthreads();
+        rank_update(Lc, Wb, ri);                // Xbar += L_i (Z_{i+1} R)^dag / i
+        C* tt = Lc; Lc = Ln; Ln = tt;
+    }
+    cp_async_wait<0>();
+    __syncthreads();
+    rank_update(Lc, Rb, R(1) / R(p));           // Z_p = I + X / p: Xbar += L_p R^dag / p
+    const size_t dd = (size_t)d * d;
+    for (int k = 0; k < sys.M; ++k) {   // partials: FP32 pairs of exact products (FP32 form); FP64 sum
+        double v = 0.0;
+        if (act) {
+            float hi = 0.f, lo = 0.f;
+#pragma unroll
+            for (int a = 0; a < MT; ++a)
+#pragma unroll
+                for (int b = 0; b < MT; ++b) {
+                    const int rr = ty + G * a, c = tx + G * b;
+                    if (rr < d && c < d) {
+                        const C hk = sys.Hk[k * dd + (size_t)rr * d + c];
+                        if constexpr (sizeof(R) == 4) {
+                            pair_acc(hi, lo, xb[a][b].x, hk.y);
+                            pair_acc(hi, lo, -xb[a][b].y, hk.x);
+                        } else {
+                            v += (double)xb[a][b].x * (double)hk.y - (double)xb[a][b].y * (double)hk.x;
+                        }
+                    }
+                }
+            if constexpr (sizeof(R) == 4) v = (double)hi + (double)lo;
+        }
+        v = block_sum(v, red);
+        if (tid == 0) gpart[((size_t)e * sys.M + k) * sys.N + j] = prm->s * v;
+    }
+}
+
 template <typename R, int MT>
 __global__ void __launch_bounds__(512, (MT <= 2 && sizeof(R) == 4) ? 3 : 1)
 k_expm_adj_rev(const DevParams* __restrict__ prm, SysView<R> sys, StateView<R> st, int j0,
@@ -370,6 +553,7 @@ k_expm_adj_rev(const DevParams* __restrict__ prm, SysView<R> sys, StateView<R> s
     using C = C_t<R>;
     const int p = prm->p, n = prm->n;
     if (!(zs.Z && p - 1 + n <= zs.cap)) return;           // k_expm_adj recomputes instead
+    if (adj_lowrank_applies(st.S, n, sys.d)) return;        // k_expm_adj_lr handles this evaluation
     const int D = G * MT, LD = D + 1, SZ = D * LD;
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ R us[kMaxControls];
@@ -574,6 +758,14 @@ static cudaError_t launch_adj_mt(const DevParams* prm, const SysView<R>& sys, co
     k_expm_adj_rev<R, MT><<<dim3(wlen, E), slice_threads(G), smem_r, st>>>(prm, sys, sv, j0, states, Gbuf, wmax,
                                                                              gpart, zs, G);
     *launches = 2;
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    if (!adj_lowrank_applies(sv.S, 0, sys.d)) return cudaSuccess;   // no squaring count makes it apply
+    const size_t smem_l = fused_smem<R>(sys.d, 3) + 4 * (size_t)sys.d * kLrMax * sizeof(C_t<R>);
+    err = cudaFuncSetAttribute(k_expm_adj_lr<R, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_l);
+    if (err != cudaSuccess) return err;
+    k_expm_adj_lr<R, MT><<<dim3(wlen, E), slice_threads(G), smem_l, st>>>(prm, sys, sv, j0, states, Gbuf, wmax,
+                                                                            gpart, zs, G);
+    *launches = 3;
     return cudaGetLastError();
 }
 

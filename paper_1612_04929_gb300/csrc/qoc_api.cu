@@ -1137,7 +1137,9 @@ qoc_status qoc_get_info(qoc_ctx* ctx, qoc_info* info) {
     info->device_bytes = (long long)ctx->device_bytes();
     if (ctx->opt.gradient == QOC_GRAD_FIRST_ORDER) info->adjoint_form = 2;
     else if (ctx->path_kind == 1) info->adjoint_form = ctx->last_big_rev ? 0 : 1;
-    else info->adjoint_form = (ctx->Zbuf.p && info->p - 1 + info->n <= kZCap) ? 0 : 1;
+    else if (ctx->Zbuf.p && info->p - 1 + info->n <= kZCap)
+        info->adjoint_form = adj_lowrank_applies(ctx->S_eff, info->n, ctx->d) ? 3 : 0;
+    else info->adjoint_form = 1;
     return QOC_OK;
     QOC_GUARD_END
 }

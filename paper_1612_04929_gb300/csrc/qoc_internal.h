@@ -115,6 +115,18 @@ cudaError_t launch_expm_adj_fused(const DevParams* prm, const SysView<R>& sys, c
                                   int wlen, int E, const C_t<R>* states, const C_t<R>* Gbuf, int wmax,
                                   double* gpart, const ZStore<R>& zs, cudaStream_t st, int* launches);
 
+// The per-slice low-rank reverse-mode adjoint (k_expm_adj_lr) applies when the cotangent's rank
+// after the squarings, r = 2^n S, is at most kLrMax and at most d / 8.  Measured on GB300 (FP32,
+// N = 2000): r = 2 at d = 64 takes the adjoint from 1.81 to 0.73 ms, r = 2 at d = 40 from 0.54 to
+// 0.33 ms, r = 4 at d = 48 from 0.75 to 0.52 ms; r = 16 at d = 40 is slower (1.27 against 0.88 ms):
+// its d x r products reuse operands less than the dense d x d ones.
+constexpr int kLrMax = 16;
+__host__ __device__ inline bool adj_lowrank_applies(int S, int n, int d) {
+    if (n > 10) return false;
+    const int r = S << n;
+    return r <= kLrMax && 8 * r <= d;
+}
+
 // ---- split hi+lo FP32 slice exponential (FP32 form) ----
 int split_max_d();
 // sH: s H_0, s H_1 .. s H_M, s H_det as FP32 pairs, written by launch_split_scale after the

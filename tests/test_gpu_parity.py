@@ -118,6 +118,23 @@ def test_both_adjoint_modes_differentiate_the_series_exactly(precision, tol, pn)
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
+@pytest.mark.parametrize("S,pn", [(1, (9, 2)), (2, (7, 1)), (1, (5, 0)), (3, (6, 1)), (1, (9, 4))])
+def test_low_rank_adjoint_differentiates_the_series_exactly(precision, tol, S, pn):
+    """With few propagated columns the per-slice adjoint keeps the cotangent as d x r factors
+    (r = 2^n S after the squarings, used when 8 r <= d): the exact derivative of the same
+    truncated map, against the oracle's derivative of that polynomial (forced p, n); the last
+    case (r = 16) takes the dense reverse mode."""
+    p, n = pn
+    prob = sy.random_problem(d=48, M=2, N=16, S=S, seed=140 + S, nF=3, E=2, dt=0.1, u_scale=0.5)
+    cost, grad, terms, info = run(prob, precision, p_override=p, n_override=n)
+    assert (info["p"], info["n"]) == (p, n)
+    assert info["adjoint_form"] == (3 if 8 * (S << n) <= 48 else 0)
+    c_t, g_t, _ = orc.taylor_cost_and_grad(prob, prob.u, p, n)
+    assert abs(cost - c_t) <= tol * abs(c_t)
+    assert rel(grad, g_t) <= tol
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
 @pytest.mark.parametrize("case", [dict(d=5, M=2, N=30, S=2, seed=121, nF=2, path=True, E=2),
                                   dict(d=40, M=2, N=120, S=1, seed=122, nF=13),
                                   dict(d=81, M=3, N=9, S=6, seed=123, nF=5, weights=True)],
