@@ -124,11 +124,12 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ oracle (CPU) timing
-def oracle_sample_time(workload, nslices, repeats=1, ref_slices=0, exact=True, maker=None):
+def oracle_sample_time(workload, nslices, repeats=1, ref_slices=0, exact=True, maker=None, min_seconds=0.0):
     """Times the CPU FP64 oracle on the first `nslices` slices of the workload in a child
-    process limited to one BLAS thread.  With ref_slices > 0 the child also evaluates the oracle
-    once on the first ref_slices slices (untimed) and returns its cost and gradient, the
-    reference for the GPU result's error.  Returns (seconds per evaluation, slices, reference)."""
+    process limited to one BLAS thread: at least `repeats` evaluations, and more until
+    `min_seconds` of timed work.  With ref_slices > 0 the child also evaluates the oracle once on
+    the first ref_slices slices (untimed) and returns its cost and gradient, the reference for
+    the GPU result's error.  Returns (seconds per evaluation, slices, reference, evaluations)."""
     code = f"""
 import json, os, sys, time
 sys.path.insert(0, {ROOT!r})
@@ -138,21 +139,21 @@ make = (lambda n: {maker}) if {maker!r} else (lambda n: sy.WORKLOADS[{workload!r
 p = make({nslices})
 orc.cost_and_grad(p, p.u)
 ts = []
-for _ in range({repeats}):
+while len(ts) < {repeats} or (sum(ts) < {min_seconds} and len(ts) < 1000):
     t0 = time.perf_counter(); orc.cost_and_grad(p, p.u); ts.append(time.perf_counter() - t0)
 ref = None
 if {ref_slices} > 0:
     q = make({ref_slices})
     c, g, _ = orc.cost_and_grad(q, q.u, exact={exact!r})
     ref = {{"N": {ref_slices}, "cost": float(c), "grad": [float(x) for x in g.ravel()]}}
-print(json.dumps({{"t": sum(ts) / len(ts), "ref": ref}}))
+print(json.dumps({{"t": sum(ts) / len(ts), "n": len(ts), "ref": ref}}))
 """
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
     if r.returncode != 0:
         raise RuntimeError(r.stderr)
     res = json.loads(r.stdout.strip().splitlines()[-1])
-    return float(res["t"]), nslices, res["ref"]
+    return float(res["t"]), nslices, res["ref"], int(res["n"])
 
 
 def reference_arm(args):
@@ -375,11 +376,11 @@ def ours_arm(args):
         # the error reference: the whole workload where the oracle takes seconds, else the sample
         ref_n = prob.N if prob.d <= 81 else nsl
         try:
-            t, nsl, ref = oracle_sample_time(args.workload, nsl, ref_slices=ref_n,
-                                             exact=args.gradient == "exact")
+            t, nsl, ref, nev = oracle_sample_time(args.workload, nsl, ref_slices=ref_n,
+                                                  exact=args.gradient == "exact", min_seconds=10.0)
             cpu = {"value": nsl * prob.E / t, "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": f"first {nsl} of {prob.N} slices of the same workload, FP64 oracle, 1 BLAS thread, "
-                             f"{t:.2f} s per evaluation"}
+                             f"{nev} evaluations in {t * nev:.1f} s ({t:.2f} s each)"}
             if ref is not None:
                 if ref_n == prob.N:
                     c_gpu, g_gpu = float(out[0].item()), grad.cpu().numpy()
@@ -556,7 +557,7 @@ def dsweep_arm(args):
             if not args.no_cpu_baseline:
                 ref_n = N if d <= 64 else 100
                 try:
-                    t, _, ref = oracle_sample_time("dsweep", min(N, 50), ref_slices=ref_n,
+                    t, _, ref, _ = oracle_sample_time("dsweep", min(N, 50), ref_slices=ref_n,
                                                    maker=f"sy.dsweep_problem({d}, N=n)")
                     if ref_n == N:
                         c_gpu, g_gpu = c32, g32
