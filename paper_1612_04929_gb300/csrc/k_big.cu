@@ -223,8 +223,9 @@ k_big_mm(int d, const E* __restrict__ A, const E* __restrict__ B, E* __restrict_
         __syncthreads();
         const ATile& As = Abuf[ch & 1];
         const BTile& Bs = Bbuf[ch & 1];
+        const int kmax = min(KC, d - ch * KC);   // the last chunk may be partial (zero-padded)
 #pragma unroll 4
-        for (int k = 0; k < KC; ++k) {
+        for (int k = 0; k < kmax; ++k) {
             E a[MT], b[MT];
 #pragma unroll
             for (int x = 0; x < MT; ++x) a[x] = As[ty + 16 * x][k];
@@ -490,8 +491,9 @@ k_big_mm_blk(int d, const C* __restrict__ A11, const C* __restrict__ A12, const 
         const ATile& A2s = A2b[ch & 1];
         const BTile& B1s = B1b[ch & 1];
         const BTile& B2s = B2b[ch & 1];
+        const int kmax = min(KC, d - ch * KC);   // the last chunk may be partial (zero-padded)
 #pragma unroll 4
-        for (int k = 0; k < KC; ++k) {
+        for (int k = 0; k < kmax; ++k) {
             C a1[MT], a2[MT], b1[MT], b2[MT];
 #pragma unroll
             for (int x = 0; x < MT; ++x) {
@@ -646,8 +648,9 @@ k_big_rev(int d, RevOps<C> ops, C* __restrict__ O1, C* __restrict__ O2, size_t m
         const ATile& A2s = A2b[ch & 1];
         const BTile& B1s = B1b[ch & 1];
         const BTile& B2s = B2b[ch & 1];
+        const int kmax = min(KC, d - ch * KC);   // the last chunk may be partial (zero-padded)
 #pragma unroll 4
-        for (int k = 0; k < KC; ++k) {
+        for (int k = 0; k < kmax; ++k) {
             C a1[MT], a2[MT], b1[MT], b2[MT];
 #pragma unroll
             for (int x = 0; x < MT; ++x) {

@@ -125,8 +125,9 @@ k_seg_mm(SegProdArgs<R> a, int level, const EI* __restrict__ src, size_t src_ite
             Bs[k][c] = (gk < d && gc < d) ? stage(Bm[(size_t)gk * d + gc]) : kz<K>();
         }
         __syncthreads();
+        const int kmax = min(KC, d - k0);   // the last chunk may be partial (zero-padded)
 #pragma unroll 4
-        for (int k = 0; k < KC; ++k) {
+        for (int k = 0; k < kmax; ++k) {
             K av[MT], bv[MT];
 #pragma unroll
             for (int x = 0; x < MT; ++x) av[x] = As[ty + 16 * x][k];
