@@ -49,6 +49,14 @@ template <> __device__ __forceinline__ float4 ezero<float4>() { return make_floa
 template <> __device__ __forceinline__ float2 ezero<float2>() { return make_float2(0.f, 0.f); }
 template <> __device__ __forceinline__ double2 ezero<double2>() { return make_double2(0.0, 0.0); }
 
+// Tile rows owned by a thread are ty + 16 x; rows at or past d (edge tiles) add nothing.  The
+// number of x a warp has to run: the largest over its lanes, so that the skip is warp-uniform.
+__device__ __forceinline__ int warp_rows(int valid, int ty, int MT) {
+    int xs = 0;
+    while (xs < MT && ty + 16 * xs < valid) ++xs;
+    return __reduce_max_sync(0xffffffffu, (unsigned)xs);
+}
+
 // ------------------------------------------------------------------------------------------
 // assembly: X = -i s H_j (+ delta_e H_det) from FP64 H; Z = I + X / p
 // ------------------------------------------------------------------------------------------
@@ -187,6 +195,7 @@ k_big_mm(int d, const E* __restrict__ A, const E* __restrict__ B, E* __restrict_
     const int tm = blockIdx.x / ntn, tn = blockIdx.x - tm * ntn;
     const int r0 = tm * T, c0 = tn * T;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int xw = warp_rows(d - r0, ty, MT);
     const E* Ai = A + (size_t)item * mstride;
     const E* Bi = B + (size_t)item * mstride;
     // split accumulators: grid sums (re, im) exact, cross terms (re, im); MODE 2 uses [0], [1]
@@ -244,7 +253,8 @@ k_big_mm(int d, const E* __restrict__ A, const E* __restrict__ B, E* __restrict_
                 }
             }
 #pragma unroll
-            for (int x = 0; x < MT; ++x)
+            for (int x = 0; x < MT; ++x) {
+                if (x >= xw) break;   // rows past d in every lane of this warp
 #pragma unroll
                 for (int y = 0; y < MT; ++y) {
                     if constexpr (MODE == 1) {
@@ -274,6 +284,7 @@ k_big_mm(int d, const E* __restrict__ A, const E* __restrict__ B, E* __restrict_
                         cfma(acc[x][y], a[x], b[y]);
                     }
                 }
+            }
         }
         __syncthreads();   // before this buffer is refilled
     }
@@ -603,6 +614,7 @@ k_big_rev(int d, RevOps<C> ops, C* __restrict__ O1, C* __restrict__ O2, size_t m
     const int tm = blockIdx.x / ntn, tn = blockIdx.x - tm * ntn;
     const int r0 = tm * T, c0 = tn * T;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int xw = warp_rows(d - r0, ty, MT);
     const C* A1 = ops.p[0] + (size_t)item * ops.s[0];
     const C* B1 = ops.p[1] + (size_t)item * ops.s[1];
     const C* A2 = ops.p[2] + (size_t)item * ops.s[2];
@@ -663,13 +675,15 @@ k_big_rev(int d, RevOps<C> ops, C* __restrict__ O1, C* __restrict__ O2, size_t m
                 b2[y] = B2s[k][tx + 16 * y];
             }
 #pragma unroll
-            for (int x = 0; x < MT; ++x)
+            for (int x = 0; x < MT; ++x) {
+                if (x >= xw) break;   // rows past d in every lane of this warp
 #pragma unroll
                 for (int y = 0; y < MT; ++y) {
                     cfma(acc1[x][y], a1[x], b1[y]);
                     if (mode == 0) cfma(acc2[x][y], a2[x], b2[y]);
                     else cfma(acc1[x][y], a2[x], b2[y]);
                 }
+            }
         }
         __syncthreads();   // before this buffer is refilled
     }
