@@ -82,13 +82,15 @@ __global__ void k_theta(const double* __restrict__ u, int M, int N, const double
     while (ldexp(theta, -n) > theta_max && n < 1000) ++n;
     if (n_override >= 0) n = n_override;
     const double ts = ldexp(theta, -n);
+    // 2^n ts^(p+1) / (p+1)! / (1 - ts / (p+2)) <= tol, compared without divisions (FP64 division
+    // on one thread is slow here): 2^n ts^(p+1) (p+2) <= tol (p+1)! (p+2 - ts)
     int p = 1;
     double fact = 2.0;     // (p + 1)!
     double pw = ts * ts;   // ts^(p + 1)
     int err = 0;
     for (;;) {
-        const double rem = ldexp(pw, n) / fact / (1.0 - ts / (p + 2));
-        if (rem <= tol) break;
+        const double q = p + 2.0;
+        if (q > ts && ldexp(pw, n) * q <= tol * fact * (q - ts)) break;
         if (p >= kPMax) { err |= kErrRange; break; }
         ++p;
         fact *= (double)(p + 1);
@@ -99,10 +101,11 @@ __global__ void k_theta(const double* __restrict__ u, int M, int N, const double
     // ts^i / i! (the X / i' factors of steps i..1).  Steps i <= m need the hi+lo pair; beyond m
     // the factor is below 2^-6 and plain FP32 is exact enough.
     int m = 1;
-    double f = ts;
-    while (m < p && f > 0.015625) {
+    double fnum = ts, fden = 1.0;   // ts^m and m!
+    while (m < p && fnum > 0.015625 * fden) {
         ++m;
-        f *= ts / m;
+        fnum *= ts;
+        fden *= m;
     }
     // Grid exponents of the split FP32 exponential (smallest e with 2^e >= bound, 1/16 margin on
     // the Z bounds).  ||X||_2 <= ||X||_1 <= ts; ||Z_i||_2 <= sum_k ts^k / k! = e^ts; H_j is
