@@ -56,8 +56,10 @@ typedef enum qoc_status {
  * traces, costs and gradient sums are FP64 in every mode; so is the norm bound that picks n. */
 typedef enum qoc_precision {
     QOC_PREC_FP64 = 0,          /* plain FP64 form: parity anchor */
-    QOC_PREC_FP32 = 1,          /* FP32 propagation, costates and adjoint; slice exponentials in
-                                   split hi+lo FP32 (see qoc_options.plain_fp32_exp) */
+    QOC_PREC_FP32 = 1,          /* FP32 adjoint and stored states; slice exponentials and the
+                                   carried recursions in extended FP32 (values as hi + lo pairs,
+                                   products of grid-split operands: exact FP32 sums of the 12-bit
+                                   parts plus rounded cross terms; see qoc_options.plain_fp32_exp) */
     QOC_PREC_TF32_SPLIT = 2,    /* the FP32 form, with the products of the large-d adjoint (d > 68)
                                    on tcgen05 tensor cores: TF32 hi + mid + lo split, six MMAs per
                                    real product, FP32 accumulation in tensor memory (the
@@ -91,9 +93,10 @@ typedef struct qoc_options {
                              so that nothing is recomputed, else the largest wave that fits.
                              Device memory is O(wave d^2 + N / ckpt_stride d S). */
     int plain_fp32_exp;   /* FP32 form only.  0 (default): the slice exponentials (forward and
-                             recomputation) use split hi+lo FP32 arithmetic from an FP64 H_j, which
-                             keeps the coherent rounding of H_j dt out of long evolutions;
-                             != 0: plain FP32 exponentials (faster, diagnostics) */
+                             recomputation) use extended FP32 arithmetic (X_j from s H_k held as
+                             FP32 pairs, grid-split products), which keeps the coherent rounding of
+                             H_j dt out of long evolutions; != 0: plain FP32 exponentials
+                             (faster, diagnostics) */
     int sweep;            /* form of the two recursions Psi_j = U_j Psi_{j-1} and the costate:
                              QOC_SWEEP_AUTO (0), QOC_SWEEP_SERIAL (1: one step per slice), or
                              QOC_SWEEP_SCAN (2: products of the U_j over each checkpoint segment by
