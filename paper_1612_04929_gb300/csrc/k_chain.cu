@@ -63,6 +63,7 @@ __global__ void k_theta(const double* __restrict__ u, int M, int N, const double
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
     __syncthreads();
     if (threadIdx.x != 0) return;
+    prm->fin_count = 0;   // the final reduction of this evaluation counts its blocks from zero
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) best = fmax(best, red[w]);
     double dmax = 0.0;
     if (delta)
