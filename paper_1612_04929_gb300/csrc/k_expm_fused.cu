@@ -711,15 +711,18 @@ k_expm_adj_rev(const DevParams* __restrict__ prm, SysView<R> sys, StateView<R> s
 // ------------------------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------------------------
+// the adjoint kernels of the FP32 form take the wide tile (equal padding, more outputs per thread)
+template <typename R> constexpr bool adj_wide() { return sizeof(R) == 4; }
+
 template <typename R>
-static size_t fused_smem(int d, int nmat) {
-    const int D = slice_tile(d).D;
+static size_t fused_smem(int d, int nmat, bool wide = false) {
+    const int D = slice_tile(d, wide).D;
     return (size_t)nmat * D * (D + 1) * sizeof(C_t<R>);
 }
 
 template <typename R>
 size_t fused_adj_smem(int d) {
-    return fused_smem<R>(d, 6);
+    return fused_smem<R>(d, 6, adj_wide<R>());
 }
 
 template <typename R>
@@ -744,7 +747,7 @@ template <typename R, int MT>
 static cudaError_t launch_adj_mt(const DevParams* prm, const SysView<R>& sys, const StateView<R>& sv, int j0,
                                  int wlen, int E, const C_t<R>* states, const C_t<R>* Gbuf, int wmax,
                                  double* gpart, const ZStore<R>& zs, int G, cudaStream_t st, int* launches) {
-    const size_t smem = fused_smem<R>(sys.d, 6);
+    const size_t smem = fused_smem<R>(sys.d, 6, adj_wide<R>());
     cudaError_t err = cudaFuncSetAttribute(k_expm_adj<R, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     k_expm_adj<R, MT><<<dim3(wlen, E), slice_threads(G), smem, st>>>(prm, sys, sv, j0, states, Gbuf, wmax, gpart,
@@ -752,7 +755,7 @@ static cudaError_t launch_adj_mt(const DevParams* prm, const SysView<R>& sys, co
     err = cudaGetLastError();
     *launches = 1;
     if (err != cudaSuccess || !zs.Z) return err;
-    const size_t smem_r = fused_smem<R>(sys.d, 5);
+    const size_t smem_r = fused_smem<R>(sys.d, 5, adj_wide<R>());
     err = cudaFuncSetAttribute(k_expm_adj_rev<R, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r);
     if (err != cudaSuccess) return err;
     k_expm_adj_rev<R, MT><<<dim3(wlen, E), slice_threads(G), smem_r, st>>>(prm, sys, sv, j0, states, Gbuf, wmax,
@@ -760,7 +763,7 @@ static cudaError_t launch_adj_mt(const DevParams* prm, const SysView<R>& sys, co
     *launches = 2;
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     if (!adj_lowrank_applies(sv.S, 0, sys.d)) return cudaSuccess;   // no squaring count makes it apply
-    const size_t smem_l = fused_smem<R>(sys.d, 3) + 4 * (size_t)sys.d * kLrMax * sizeof(C_t<R>);
+    const size_t smem_l = fused_smem<R>(sys.d, 3, adj_wide<R>()) + 4 * (size_t)sys.d * kLrMax * sizeof(C_t<R>);
     err = cudaFuncSetAttribute(k_expm_adj_lr<R, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_l);
     if (err != cudaSuccess) return err;
     k_expm_adj_lr<R, MT><<<dim3(wlen, E), slice_threads(G), smem_l, st>>>(prm, sys, sv, j0, states, Gbuf, wmax,
@@ -787,7 +790,7 @@ template <typename R>
 cudaError_t launch_expm_adj_fused(const DevParams* prm, const SysView<R>& sys, const StateView<R>& sv, int j0,
                                   int wlen, int E, const C_t<R>* states, const C_t<R>* Gbuf, int wmax,
                                   double* gpart, const ZStore<R>& zs, cudaStream_t st, int* launches) {
-    const SliceTile tl = slice_tile(sys.d);
+    const SliceTile tl = slice_tile(sys.d, adj_wide<R>());
     *launches = 0;
     if (sys.d > fused_max_d<R>()) return cudaErrorInvalidValue;
     switch (tl.MT) {
@@ -802,7 +805,7 @@ cudaError_t launch_expm_adj_fused(const DevParams* prm, const SysView<R>& sys, c
 // resident CTAs per SM of the forward and adjoint kernels at dimension d (wave sizing)
 template <typename R>
 int fused_ctas_per_sm(int d, bool adjoint) {
-    const SliceTile tl = slice_tile(d);
+    const SliceTile tl = slice_tile(d, adjoint && adj_wide<R>());
     if (tl.MT <= 0) return 1;
     int n = 0;
     const int thr = slice_threads(tl.G);
@@ -820,7 +823,7 @@ int fused_ctas_per_sm(int d, bool adjoint) {
                     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_expm_fwd<R, 4>, thr, smem); break;
         }
     } else {
-        const size_t smem = fused_smem<R>(d, 5);
+        const size_t smem = fused_smem<R>(d, 5, adj_wide<R>());
         switch (tl.MT) {
             case 1: cudaFuncSetAttribute(k_expm_adj_rev<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
                     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_expm_adj_rev<R, 1>, thr, smem); break;
