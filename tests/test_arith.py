@@ -1,0 +1,125 @@
+"""CPU checks of two arithmetic facts the FP32 kernels rely on, written out in NumPy:
+
+* grid split: with v1 = v rounded to the power-of-two grid 2^(e-12), where 2^e bounds the row
+  (column) 2-norms, every partial sum of a row-times-column contraction of grid parts is exact in
+  FP32 (products of 13-bit grid parts are exact and, by Cauchy-Schwarz, the sums stay below 2^24
+  grid units), and grid sums plus FP32 cross terms reproduce the FP64 product to ~2^-36;
+* low-rank reverse mode: for a cotangent Ubar = L R^dag of rank S, the reverse mode through the
+  squarings and the Horner steps of the truncated series keeps it as factors (the rank doubles at
+  each squaring, R stays fixed through Horner), and gives the same Xbar as the dense reverse mode,
+  which itself matches a finite-difference derivative of the truncated series.
+"""
+import numpy as np
+import pytest
+
+f32 = np.float32
+
+
+def grid_split(v, e):
+    """FP64 array -> (v1, v2) FP32 with v1 on the grid 2^(e-12) and v2 = v - v1 rounded."""
+    g = 2.0 ** (e - 12)
+    v1 = (np.rint(v / g) * g).astype(f32)
+    v2 = (v - v1.astype(np.float64)).astype(f32)
+    return v1, v2
+
+
+def random_unitary(d, rng):
+    q, r = np.linalg.qr(rng.normal(size=(d, d)) + 1j * rng.normal(size=(d, d)))
+    return q * (np.diag(r) / np.abs(np.diag(r)))
+
+
+@pytest.mark.parametrize("d", [8, 40, 81])
+def test_grid_sums_are_exact_and_products_accurate(d):
+    rng = np.random.default_rng(d)
+    A, B = random_unitary(d, rng), random_unitary(d, rng)   # row / column 2-norms 1 <= 2^1
+    a1r, a2r = grid_split(A.real, 1)
+    a1i, a2i = grid_split(A.imag, 1)
+    b1r, b2r = grid_split(B.real, 1)
+    b1i, b2i = grid_split(B.imag, 1)
+    bfr, bfi = (b1r + b2r).astype(f32), (b1i + b2i).astype(f32)
+    Sr = np.zeros((d, d), f32)
+    Lr = np.zeros((d, d), f32)
+    for k in range(d):   # FP32 accumulation in k order; each step's products are exact here
+        Sr = (Sr + a1r[:, k:k + 1] * b1r[k]).astype(f32)
+        Sr = (Sr - a1i[:, k:k + 1] * b1i[k]).astype(f32)
+        Lr = (Lr + a1r[:, k:k + 1] * b2r[k]).astype(f32)
+        Lr = (Lr - a1i[:, k:k + 1] * b2i[k]).astype(f32)
+        Lr = (Lr + a2r[:, k:k + 1] * bfr[k]).astype(f32)
+        Lr = (Lr - a2i[:, k:k + 1] * bfi[k]).astype(f32)
+    exact_S = a1r.astype(float) @ b1r.astype(float) - a1i.astype(float) @ b1i.astype(float)
+    assert np.array_equal(Sr.astype(float), exact_S)
+    err = np.abs(Sr.astype(float) + Lr.astype(float) - (A @ B).real).max()
+    assert err < 2e-9
+    plain = np.abs((A.astype(np.complex64) @ B.astype(np.complex64)).real - (A @ B).real).max()
+    assert err < plain / 50
+
+
+def taylor_forward(X, p, n):
+    """Horner T = I + X(I + X/2(... (I + X/p))) and n squarings; returns U and the right operand of
+    every product in the order the forward meets them (Z_{i+1} for Horner step i = p-1..1, then
+    S_m = T^(2^m))."""
+    d = X.shape[0]
+    I = np.eye(d)
+    Z = I + X / p
+    ops = []
+    for i in range(p - 1, 0, -1):
+        ops.append(Z)
+        Z = I + X @ Z / i
+    for _ in range(n):
+        ops.append(Z)
+        Z = Z @ Z
+    return Z, ops
+
+
+def reverse_dense(X, Ubar, p, n):
+    _, ops = taylor_forward(X, p, n)
+    XH = X.conj().T
+    Sbar = Ubar
+    for m in range(n - 1, -1, -1):
+        S = ops[p - 1 + m]
+        Sbar = Sbar @ S.conj().T + S.conj().T @ Sbar
+    Zbar = Sbar
+    Xbar = np.zeros_like(X)
+    for i in range(1, p):
+        Znext = ops[p - 1 - i]   # Z_{i+1}
+        Xbar = Xbar + Zbar @ Znext.conj().T / i
+        Zbar = XH @ Zbar / i
+    return Xbar + Zbar / p
+
+
+def reverse_low_rank(X, L, R, p, n):
+    _, ops = taylor_forward(X, p, n)
+    XH = X.conj().T
+    for m in range(n - 1, -1, -1):   # Sbar = L R^dag -> [L, S^dag L] [S R, R]^dag
+        S = ops[p - 1 + m]
+        L, R = np.hstack([L, S.conj().T @ L]), np.hstack([S @ R, R])
+    Xbar = np.zeros_like(X)
+    for i in range(1, p):            # R fixed; L_{i+1} = X^dag L_i / i
+        Znext = ops[p - 1 - i]
+        Xbar = Xbar + L @ (Znext @ R).conj().T / i
+        L = XH @ L / i
+    return Xbar + L @ R.conj().T / p, L.shape[1]
+
+
+@pytest.mark.parametrize("d,S,p,n", [(12, 1, 9, 3), (16, 2, 7, 2), (10, 3, 5, 0), (20, 1, 12, 4)])
+def test_low_rank_reverse_mode_equals_dense(d, S, p, n):
+    rng = np.random.default_rng(100 * d + S)
+    H = rng.normal(size=(d, d)) + 1j * rng.normal(size=(d, d))
+    H = (H + H.conj().T) / 2
+    X = -1j * 0.4 * H / np.abs(H).sum(0).max()
+    L = rng.normal(size=(d, S)) + 1j * rng.normal(size=(d, S))
+    R = rng.normal(size=(d, S)) + 1j * rng.normal(size=(d, S))
+    dense = reverse_dense(X, L @ R.conj().T, p, n)
+    low, r = reverse_low_rank(X, L, R, p, n)
+    assert r == S << n
+    assert np.abs(low - dense).max() <= 1e-12 * np.abs(dense).max()
+    # the dense reverse mode is the adjoint of the truncated series' derivative:
+    # Re tr(Ubar^dag dU) = Re tr(Xbar^dag dX) for a direction dX (central differences)
+    dX = rng.normal(size=(d, d)) + 1j * rng.normal(size=(d, d))
+    h = 1e-6
+    Up, _ = taylor_forward(X + h * dX, p, n)
+    Um, _ = taylor_forward(X - h * dX, p, n)
+    Ubar = L @ R.conj().T
+    lhs = np.real(np.trace(Ubar.conj().T @ (Up - Um) / (2 * h)))
+    rhs = np.real(np.trace(dense.conj().T @ dX))
+    assert abs(lhs - rhs) <= 1e-7 * max(1.0, abs(rhs))
