@@ -5,10 +5,11 @@
 // (and sources) into a shared-memory ring with cp.async while the current step computes.
 //
 // The running block is carried in extended precision: FP64 in the FP64 form, and an unevaluated
-// hi + lo pair of FP32 numbers in the FP32 form (exact products via FMA, error-free TwoSum
-// accumulation).  Over thousands of slices the FP32 rounding of a plainly carried state adds
-// up to gradient errors near 1e-5; the pair keeps the recursion at ~1e-12 while U_j, the stored
-// states and costates (inputs of the parallel kernels) stay FP32.
+// hi + lo pair of FP32 numbers in the FP32 form.  Over thousands of slices the FP32 rounding of a
+// plainly carried state adds up to gradient errors near 1e-5; the carried pair keeps each step's
+// rounding near 2^-36 of the block's scale while U_j, the stored states and costates (inputs of
+// the parallel kernels) stay FP32.  (The FP64 form's steps and the pair helpers below with
+// TwoSum accumulation serve the FP64 form and the sources' additions.)
 //
 // FP32 form: every step multiplies grid-split operands (qoc_device.cuh).  The carried pair block
 // is re-split at the start of each step on a power-of-two grid set by a bound on its column
@@ -35,43 +36,8 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float p) {
     lo += (hi - (t - bv)) + (p - bv);
     hi = t;
 }
-// (hi, lo) += a * (bh + bl) with the exact product residual
-__device__ __forceinline__ void pair_mac(float& hi, float& lo, float a, float bh, float bl) {
-    const float p = a * bh;
-    lo += fmaf(a, bh, -p) + a * bl;
-    two_sum_acc(hi, lo, p);
-}
-
-// (hi, lo) += (ah + al)(bh + bl), dropping al * bl
-__device__ __forceinline__ void pair_mac2(float& hi, float& lo, float ah, float al, float bh, float bl) {
-    const float p = ah * bh;
-    lo += fmaf(ah, bh, -p) + fmaf(ah, bl, al * bh);
-    two_sum_acc(hi, lo, p);
-}
-// acc += u x    (u and x carried: segment products)
-__device__ __forceinline__ void kmac(float4& acc, const float4 u, const float4 x) {
-    pair_mac2(acc.x, acc.z, u.x, u.z, x.x, x.z);
-    pair_mac2(acc.x, acc.z, -u.y, -u.w, x.y, x.w);
-    pair_mac2(acc.y, acc.w, u.x, u.z, x.y, x.w);
-    pair_mac2(acc.y, acc.w, u.y, u.w, x.x, x.z);
-}
-// acc += u x    (u plain, x carried)
-__device__ __forceinline__ void kmac(float4& acc, const float2 u, const float4 x) {
-    pair_mac(acc.x, acc.z, u.x, x.x, x.z);
-    pair_mac(acc.x, acc.z, -u.y, x.y, x.w);
-    pair_mac(acc.y, acc.w, u.x, x.y, x.w);
-    pair_mac(acc.y, acc.w, u.y, x.x, x.z);
-}
+// acc += u x (FP64 form; the FP32 form takes the grid step)
 __device__ __forceinline__ void kmac(double2& acc, const double2 u, const double2 x) { cfma(acc, u, x); }
-// acc += conj(u) x
-__device__ __forceinline__ void kmac_cj(float4& acc, const float2 u, const float4 x) {
-    pair_mac(acc.x, acc.z, u.x, x.x, x.z);
-    pair_mac(acc.x, acc.z, u.y, x.y, x.w);
-    pair_mac(acc.y, acc.w, u.x, x.y, x.w);
-    pair_mac(acc.y, acc.w, -u.y, x.x, x.z);
-}
-__device__ __forceinline__ void kmac_cj(double2& acc, const double2 u, const double2 x) { cfma_cj(acc, u, x); }
-
 __device__ __forceinline__ void kadd(float4& a, const float4 b) {
     two_sum_acc(a.x, a.z, b.x);
     a.z += b.z;
