@@ -35,6 +35,11 @@ MEASURED_TRAFFIC = {
     # split exponential, waves of 1125 and 875 slices: 139,826,432 and 91,752,192 bytes
     ("transmon_cavity_d40", "fp32", "expm_fwd", 1125): 115789312.0,
 }
+# executed side of the same kernel from one full ncu capture (1125-slice launch): FMA pipe and
+# issue activity, % of peak over active cycles
+MEASURED_PIPES = {
+    ("transmon_cavity_d40", "fp32", "expm_fwd", 1125): {"fma_pipe_pct": 47.2, "issue_active_pct": 68.7},
+}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 L2_FLUSH_BYTES = 256 << 20
 
@@ -290,6 +295,7 @@ def ours_arm(args):
         # DRAM bytes per launch of the dominant kernel, from an ncu capture of the same kernel at
         # this workload (dram__bytes_read.sum + dram__bytes_write.sum); None where none was taken
         traffic = MEASURED_TRAFFIC.get((prob.name, precision, top_name, info["wave_slices"]))
+        pipes = MEASURED_PIPES.get((prob.name, precision, top_name, info["wave_slices"]))
         roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS if fp32 else None,
                 "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS if fp32 else None,
                 "traffic": traffic, "kernel": top_name, "launches": top_launches,
@@ -299,6 +305,9 @@ def ours_arm(args):
                         "execute ~12 FP32 instructions per algorithmic multiply-add",
                 "traffic_source": ("dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of this "
                                    "kernel at this workload") if traffic else None}
+        if pipes:
+            roof["executed"] = dict(pipes, source="ncu --set full, one launch of this kernel at this workload "
+                                                  "(sm__pipe_fma_cycles_active, smsp__issue_active)")
     kernels = {k: {"launches": v[0], "ms_per_step": v[1] / K} for k, v in prof.items()}
 
     # end to end through the host API with pinned buffers
