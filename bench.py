@@ -301,8 +301,9 @@ def ours_arm(args):
                 "traffic": traffic, "kernel": top_name, "launches": top_launches,
                 "avg_launch_ms": top_ms / top_launches,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
-                "note": "algorithmic flops (8 d^3 per complex product); the split hi+lo products "
-                        "execute ~12 FP32 instructions per algorithmic multiply-add",
+                "note": "algorithmic flops (8 d^3 per complex product); the FP32 form's grid-split "
+                        "products execute 12 FMAs per complex multiply-add (3.25 per algorithmic one), "
+                        "so the split exponential's fraction is bounded near 0.3 by construction",
                 "traffic_source": ("dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of this "
                                    "kernel at this workload") if traffic else None}
         if pipes:
