@@ -28,7 +28,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "fwd+grad slice-steps/s"
 UNIT = "slice-steps/s"
-# FP32 FMA peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (max SM clock)
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, averaged over the launches
 # of one evaluation) measured by ncu, keyed by (workload, precision, kernel, wave slices)
 MEASURED_TRAFFIC = {
@@ -40,6 +39,7 @@ MEASURED_TRAFFIC = {
 MEASURED_PIPES = {
     ("transmon_cavity_d40", "fp32", "expm_fwd", 1125): {"fma_pipe_pct": 47.2, "issue_active_pct": 68.7},
 }
+# FP32 FMA peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (max SM clock)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 L2_FLUSH_BYTES = 256 << 20
 
@@ -210,6 +210,23 @@ def adj_flops_per_slice(form, d, p, n, S):
     return k * expm_flops_per_slice(d, p, n) + 8.0 * d * d * S
 
 
+def slowest_rank_ms(ms, world, device):
+    """The job's time per step: the largest of the ranks' times (every rank must call this)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_value(units_per_rank, world, t_max_ms):
+    """Whole-job throughput of `world` replicas (weak scaling): every rank's units over the slowest
+    rank's time."""
+    return units_per_rank * world / (t_max_ms / 1e3)
+
+
 def ours_arm(args):
     import numpy as np
     import torch
@@ -265,13 +282,9 @@ def ours_arm(args):
     ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / K
     prof = ctx.profile()
     ctx.sync()
-    t_max = ms
-    if world > 1:
-        tt = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
+    t_max = slowest_rank_ms(ms, world, "cuda")
     units = prob.N * prob.E
-    value = units * world / (t_max / 1e3)
+    value = job_value(units, world, t_max)
 
     # dominant kernel and its roofline (algorithmic flops / measured launch time)
     d, p, n = prob.d, info["p"], info["n"]
