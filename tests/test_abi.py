@@ -104,3 +104,18 @@ def test_null_context_is_rejected(lib):
     assert lib.qoc_set_system(None, 2, 0, None, None, 1.0, 1) == 1
     assert lib.qoc_evaluate_device(None, None, None, None) == 1
     lib.qoc_destroy(None)
+
+
+@pytest.mark.parametrize("field,value", [("precision", 4), ("precision", -1), ("tol", -1.0), ("theta_max", -0.5),
+                                         ("ckpt_stride", -2), ("wave_slices", -1), ("sweep", 3), ("gradient", 2),
+                                         ("adjoint", 2), ("fault_inject", 2)])
+def test_invalid_options_are_rejected_before_the_device(lib, field, value):
+    """qoc_create validates every option on the host before it touches a device: an out-of-range
+    value is QOC_ERR_ARG (1) on any machine, and no context is returned."""
+    import ctypes as ct
+    opt = qmod.qoc_options()
+    lib.qoc_default_options(ct.byref(opt))
+    setattr(opt, field, value)
+    out = ct.c_void_p(1)
+    assert lib.qoc_create(ct.byref(out), ct.byref(opt)) == 1
+    assert not out.value
