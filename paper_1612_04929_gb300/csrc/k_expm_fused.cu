@@ -20,6 +20,12 @@
 //               Ubar and ending with Xbar += Zbar_p / p: two products per step instead of three,
 //               and five matrices in shared memory instead of six (the stored operand of the
 //               next product arrives by cp.async while the current one is multiplied).
+//  k_expm_adj_lr : the same reverse mode when the cotangent has low rank.  The cotangent
+//               Ubar_j = G_j Psi_{j-1}^dag, with G_j and Psi_{j-1} both d x S (S propagated
+//               states), has rank at most S, so it is kept as factors L R^dag: each squaring
+//               appends a block to each factor (rank doubles), each Horner step maps
+//               L -> X^dag L / i with R fixed, and the products become d x d by d x r ones
+//               (r = S 2^n).  Taken when r <= 16 and 8 r <= d.
 //
 // Thread layout: a G x G grid of threads (slice_tile); thread (ty, tx) owns the MT x MT outputs
 // (ty + G a, tx + G b).  Matrices sit in shared memory padded to D = G MT rows with a leading
