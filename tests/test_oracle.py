@@ -97,6 +97,43 @@ def test_single_qubit_time_optimal_closed_form():
     assert np.max(np.abs(g[0] - ref)) < 1e-14
 
 
+def test_single_qubit_ensemble_closed_form():
+    # detuning delta_e on H_det = sx shifts every slice: T_{J,e} = dt sum_{j<=J} (u_j + delta_e).
+    # C_fid and C5 are means over the members: C_fid = mean_e cos^2(T_{N,e}),
+    # C5 = mean_e sum_J sin^2(T_{J,e}), with gradients mean_e of the one-member closed forms.
+    rng = np.random.default_rng(4)
+    u = rng.normal(0, 0.8, size=8)
+    p = single_qubit(u, [1, 0, 0, 0.5, 0], forbidden=[1])
+    p.delta = np.array([-0.3, 0.0, 0.45])
+    p.Hdet = SX.copy()
+    TJ = p.dt * np.cumsum(u[None, :] + p.delta[:, None], axis=1)     # (E, N)
+    c, g, terms = orc.cost_and_grad(p, p.u)
+    assert abs(terms[0] - np.mean(np.cos(TJ[:, -1]) ** 2)) < 1e-14
+    assert abs(terms[3] - np.mean(np.sum(np.sin(TJ) ** 2, axis=1))) < 1e-13
+    assert abs(c - terms[0] - 0.5 * terms[3]) < 1e-14
+    g_fid = -p.dt * np.mean(np.sin(2 * TJ[:, -1]))
+    g5 = p.dt * np.mean(np.cumsum(np.sin(2 * TJ)[:, ::-1], axis=1)[:, ::-1], axis=0)
+    assert np.max(np.abs(g[0] - (g_fid + 0.5 * g5))) < 1e-13
+
+
+def test_single_qubit_per_slice_targets_closed_form():
+    # per-slice targets |J mod 2> at slice J: |O_J|^2 = sin^2(T_J) for odd J, cos^2(T_J) for even J,
+    # so C67 = 1 - (1/N) sum_J |O_J|^2 and dC67/du_j = -(dt/N) sum_{J>=j} s_J sin(2 T_J), s_J = +-1
+    rng = np.random.default_rng(5)
+    u = rng.normal(0, 0.8, size=7)
+    N = len(u)
+    p = single_qubit(u, [0, 0, 0, 0, 1])
+    J = np.arange(1, N + 1)
+    p.psiT_path = np.stack([sy.basis_state(2, int(k % 2)) for k in J])
+    TJ = p.dt * np.cumsum(u)
+    occ = np.where(J % 2 == 1, np.sin(TJ) ** 2, np.cos(TJ) ** 2)
+    sgn = np.where(J % 2 == 1, 1.0, -1.0)
+    c, g, _ = orc.cost_and_grad(p, p.u)
+    assert abs(c - (1 - np.mean(occ))) < 1e-14
+    ref = -(p.dt / N) * np.cumsum((sgn * np.sin(2 * TJ))[::-1])[::-1]
+    assert np.max(np.abs(g[0] - ref)) < 1e-14
+
+
 def test_control_terms_closed_form():
     u = np.array([[1.0, -2.0, 0.5], [0.0, 3.0, 1.0]])
     p = single_qubit(u[:1], [0, 1, 1, 0, 0])
@@ -334,6 +371,24 @@ def test_pins_catch_planted_mistakes(monkeypatch):
     assert fails()
     monkeypatch.setattr(orc, "_sources", orig_src)
     assert not fails()
+
+
+def test_closed_form_pins_catch_planted_mistakes(monkeypatch):
+    """A per-slice target read one slice late, and every member seeing the first member's
+    detuning, each make a closed-form pin above fail."""
+    def off_by_one(prob, j):
+        return prob.psiT_path[min(j, prob.N - 1)] if prob.psiT_path is not None else prob.psiT
+    monkeypatch.setattr(orc, "_targets", off_by_one)
+    with pytest.raises(AssertionError):
+        test_single_qubit_per_slice_targets_closed_form()
+    monkeypatch.undo()
+    orig_h = orc.slice_hamiltonians
+    monkeypatch.setattr(orc, "slice_hamiltonians", lambda prob, u, e=0: orig_h(prob, u, 0))
+    with pytest.raises(AssertionError):
+        test_single_qubit_ensemble_closed_form()
+    monkeypatch.undo()
+    test_single_qubit_per_slice_targets_closed_form()
+    test_single_qubit_ensemble_closed_form()
 
 
 # ---------------------------------------------------------------- synthetic inputs
