@@ -134,6 +134,24 @@ def test_single_qubit_per_slice_targets_closed_form():
     assert np.max(np.abs(g[0] - ref)) < 1e-14
 
 
+def test_single_qubit_weighted_columns_closed_form():
+    # columns |0>, |1> both aimed at |1> with weights w0, w1: overlaps -i sin T and cos T, so
+    # O = (-i w0 sin T + w1 cos T) / (w0 + w1), C_fid = 1 - (w0^2 sin^2 T + w1^2 cos^2 T) / (w0 + w1)^2,
+    # dC_fid/du_j = -dt (w0^2 - w1^2) sin(2T) / (w0 + w1)^2
+    rng = np.random.default_rng(6)
+    u = rng.normal(0, 0.8, size=5)
+    p = single_qubit(u, [1, 0, 0, 0, 0])
+    p.psi0 = np.eye(2, dtype=np.complex128)
+    p.psiT = np.hstack([sy.basis_state(2, 1), sy.basis_state(2, 1)])
+    w0, w1 = 0.7, 2.3
+    p.col_weight = np.array([w0, w1])
+    T = p.dt * u.sum()
+    W2 = (w0 + w1) ** 2
+    c, g, _ = orc.cost_and_grad(p, p.u)
+    assert abs(c - (1 - (w0 ** 2 * math.sin(T) ** 2 + w1 ** 2 * math.cos(T) ** 2) / W2)) < 1e-14
+    assert np.max(np.abs(g[0] - (-p.dt * (w0 ** 2 - w1 ** 2) * math.sin(2 * T) / W2))) < 1e-14
+
+
 def test_control_terms_closed_form():
     u = np.array([[1.0, -2.0, 0.5], [0.0, 3.0, 1.0]])
     p = single_qubit(u[:1], [0, 1, 1, 0, 0])
@@ -374,8 +392,8 @@ def test_pins_catch_planted_mistakes(monkeypatch):
 
 
 def test_closed_form_pins_catch_planted_mistakes(monkeypatch):
-    """A per-slice target read one slice late, and every member seeing the first member's
-    detuning, each make a closed-form pin above fail."""
+    """A per-slice target read one slice late, every member seeing the first member's detuning,
+    and column weights ignored in the overlap each make a closed-form pin above fail."""
     def off_by_one(prob, j):
         return prob.psiT_path[min(j, prob.N - 1)] if prob.psiT_path is not None else prob.psiT
     monkeypatch.setattr(orc, "_targets", off_by_one)
@@ -387,8 +405,14 @@ def test_closed_form_pins_catch_planted_mistakes(monkeypatch):
     with pytest.raises(AssertionError):
         test_single_qubit_ensemble_closed_form()
     monkeypatch.undo()
+    orig_ov = orc._overlap
+    monkeypatch.setattr(orc, "_overlap", lambda target, psi, w: orig_ov(target, psi, np.ones_like(w)))
+    with pytest.raises(AssertionError):
+        test_single_qubit_weighted_columns_closed_form()
+    monkeypatch.undo()
     test_single_qubit_per_slice_targets_closed_form()
     test_single_qubit_ensemble_closed_form()
+    test_single_qubit_weighted_columns_closed_form()
 
 
 # ---------------------------------------------------------------- synthetic inputs
