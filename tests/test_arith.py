@@ -7,7 +7,9 @@
 * low-rank reverse mode: for a cotangent Ubar = L R^dag of rank S, the reverse mode through the
   squarings and the Horner steps of the truncated series keeps it as factors (the rank doubles at
   each squaring, R stays fixed through Horner), and gives the same Xbar as the dense reverse mode,
-  which itself matches a finite-difference derivative of the truncated series.
+  which itself matches a finite-difference derivative of the truncated series;
+* block form: for the polynomial map f (Horner series, then squarings) with real coefficients, the
+  same Xbar is the (1,2) block of f applied to [[X^dag, Ubar], [0, X^dag]].
 """
 import numpy as np
 import pytest
@@ -123,3 +125,18 @@ def test_low_rank_reverse_mode_equals_dense(d, S, p, n):
     lhs = np.real(np.trace(Ubar.conj().T @ (Up - Um) / (2 * h)))
     rhs = np.real(np.trace(dense.conj().T @ dX))
     assert abs(lhs - rhs) <= 1e-7 * max(1.0, abs(rhs))
+
+
+@pytest.mark.parametrize("d,p,n", [(6, 9, 3), (11, 5, 0), (8, 14, 5)])
+def test_block_triangular_form_equals_reverse_mode(d, p, n):
+    rng = np.random.default_rng(d + 17 * p)
+    H = rng.normal(size=(d, d)) + 1j * rng.normal(size=(d, d))
+    H = (H + H.conj().T) / 2
+    X = -1j * 0.5 * H / np.abs(H).sum(0).max()
+    Ubar = rng.normal(size=(d, d)) + 1j * rng.normal(size=(d, d))
+    XH = X.conj().T
+    B = np.block([[XH, Ubar], [np.zeros((d, d)), XH]])
+    FB, _ = taylor_forward(B, p, n)
+    dense = reverse_dense(X, Ubar, p, n)
+    assert np.abs(FB[:d, d:] - dense).max() <= 1e-12 * np.abs(dense).max()
+    assert np.abs(FB[:d, :d] - taylor_forward(XH, p, n)[0]).max() < 1e-13
