@@ -161,6 +161,26 @@ print(json.dumps({{"t": sum(ts) / len(ts), "n": len(ts), "ref": ref}}))
     return float(res["t"]), nslices, res["ref"], int(res["n"])
 
 
+def thread_cpu_ticks():
+    """{thread id: utime + stime clock ticks} of this process's threads (Linux /proc), or None."""
+    try:
+        out = {}
+        for tid in os.listdir("/proc/self/task"):
+            with open(f"/proc/self/task/{tid}/stat") as f:
+                fields = f.read().rsplit(")", 1)[1].split()
+            out[tid] = int(fields[11]) + int(fields[12])   # utime, stime (stat fields 14, 15)
+        return out
+    except (OSError, ValueError, IndexError):
+        return None
+
+
+def busy_threads(before, after):
+    """Threads that accumulated CPU time between two thread_cpu_ticks() snapshots."""
+    if before is None or after is None:
+        return None
+    return sum(1 for tid, t in after.items() if t > before.get(tid, 0))
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -173,19 +193,23 @@ def reference_arm(args):
     for _ in range(args.warmup):
         orc.cost_and_grad(sample, sample.u)
     ts = []
+    ticks0 = thread_cpu_ticks()
     for _ in range(args.steps):
         t0 = time.perf_counter()
         orc.cost_and_grad(sample, sample.u)
         ts.append(time.perf_counter() - t0)
+    used = busy_threads(ticks0, thread_cpu_ticks())
     t = sum(ts) / len(ts)
     value = nsl * sample.E / t
     desc = (f"CPU FP64 oracle (eigendecomposition exponentials, explicit adjoint) on the first {nsl} of "
-            f"{prob.N} slices, steps={args.steps}, numpy BLAS default threads")
+            f"{prob.N} slices, steps={args.steps}, numpy BLAS default threads; cores = threads of this "
+            f"process that gained CPU time in the timed steps ({os.cpu_count()} host cores)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_of(prob, "fp64-oracle", 0, {"sample_slices": nsl}),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "config": config_of(prob, "fp64-oracle", 0, {"sample_slices": nsl,
+                                                          "l2": "not applicable (host CPU timing)"}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
                              "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
