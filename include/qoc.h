@@ -171,9 +171,12 @@ const char* qoc_last_error(const qoc_ctx* ctx);
 const char* qoc_status_string(qoc_status s);
 
 /* The system of Eq. 1.  H0: d x d complex; Hk: M consecutive d x d complex matrices (may be
- * NULL when M = 0); dt > 0; N >= 1 slices; 1 <= d <= 512; 0 <= M <= 64.
- * Checks Hermiticity (QOC_ERR_NOT_HERMITIAN) and finiteness (QOC_ERR_NONFINITE).  Resets the
- * targets and the ensemble (a later evaluate needs qoc_set_targets again). */
+ * NULL when M = 0); dt > 0; N >= 1 slices; 1 <= d <= 512; 0 <= M <= 64.  The matrices are
+ * copied; the caller keeps its buffers.  Resets the targets and the ensemble (a later evaluate
+ * needs qoc_set_targets again).  Errors, all raised before any device work: QOC_ERR_ARG (NULL
+ * matrix, dt not finite and positive), QOC_ERR_SHAPE (d, M or N out of range),
+ * QOC_ERR_NONFINITE, QOC_ERR_NOT_HERMITIAN (|H_ab - conj(H_ba)| above 1e-12 max(1, max|H|));
+ * then QOC_ERR_CUDA / QOC_ERR_OOM from the device copies. */
 qoc_status qoc_set_system(qoc_ctx* ctx, int d, int M, const double* H0, const double* Hk,
                           double dt, int N);
 
@@ -181,15 +184,20 @@ qoc_status qoc_set_system(qoc_ctx* ctx, int d, int M, const double* H0, const do
  * basis indices in [0, d) (may be NULL when nF = 0); col_weight: S non-negative weights with a
  * positive sum (NULL: all 1); psiT_path: N consecutive d x S targets for the per-slice time cost
  * C67 (NULL: psiT at every slice); alpha: 5 weights [fid, C3 amplitude, C4 variation,
- * C5 forbidden, C67 time].  Requires qoc_set_system (else QOC_ERR_STATE). */
+ * C5 forbidden, C67 time].  Everything is copied.  Requires qoc_set_system (else
+ * QOC_ERR_STATE).  Other errors: QOC_ERR_ARG (NULL argument, a negative or non-finite weight,
+ * weights summing to 0), QOC_ERR_SHAPE (S or nF out of range, a forbidden index outside
+ * [0, d)), QOC_ERR_NONFINITE.  No device work. */
 qoc_status qoc_set_targets(qoc_ctx* ctx, int S, const double* psi0, const double* psiT, int nF,
                            const int* forbidden, const double* col_weight,
                            const double* psiT_path, const double* alpha);
 
 /* Detuning ensemble for robust control: member e propagates H_j + delta[e] Hdet; the
- * state-dependent cost terms and their gradients are averaged over the E members.  E >= 1;
- * delta: E doubles; Hdet: d x d complex Hermitian (may be NULL when every delta is 0).
- * Requires qoc_set_system. */
+ * state-dependent cost terms and their gradients are averaged over the E members.
+ * 1 <= E <= 65535; delta: E doubles; Hdet: d x d complex Hermitian (may be NULL when every
+ * delta is 0); both are copied.  Requires qoc_set_system (else QOC_ERR_STATE).  Other errors:
+ * QOC_ERR_SHAPE (E), QOC_ERR_ARG (delta NULL, or Hdet NULL with a non-zero delta),
+ * QOC_ERR_NONFINITE, QOC_ERR_NOT_HERMITIAN; then QOC_ERR_CUDA / QOC_ERR_OOM. */
 qoc_status qoc_set_ensemble(qoc_ctx* ctx, int E, const double* delta, const double* Hdet);
 
 /* One forward + gradient evaluation from host memory.  u: M x N doubles (row k holds control k
