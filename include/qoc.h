@@ -200,17 +200,19 @@ qoc_status qoc_set_targets(qoc_ctx* ctx, int S, const double* psi0, const double
  * QOC_ERR_NONFINITE, QOC_ERR_NOT_HERMITIAN; then QOC_ERR_CUDA / QOC_ERR_OOM. */
 qoc_status qoc_set_ensemble(qoc_ctx* ctx, int E, const double* delta, const double* Hdet);
 
-/* One forward + gradient evaluation from host memory.  u: M x N doubles (row k holds control k
+/* One forward + gradient evaluation from host memory: the cost C of Table I (Sec. II) and its
+ * exact gradient dC/du (Sec. II.B, Appendix A).  u: M x N doubles (row k holds control k
  * over the N slices); *cost receives C; grad (M x N doubles) receives dC/du; terms (5 doubles,
  * may be NULL) receives the unweighted [C_fid, C3, C4, C5, C67].  Copies u to the device, runs,
  * copies the results back and synchronises the stream.  Requires set_system and set_targets. */
 qoc_status qoc_evaluate_cost_and_grad(qoc_ctx* ctx, const double* u, double* cost, double* grad,
                                       double* terms);
 
-/* The same evaluation on device memory, asynchronous on the context stream: u_dev (M x N
- * doubles), grad_dev (M x N doubles) and out_dev (6 doubles: C then the 5 terms) are device
- * pointers owned by the caller.  Returns after enqueueing; errors raised inside kernels are
- * reported by the next synchronising call (qoc_sync, qoc_get_info or a host evaluation). */
+/* The same evaluation (Table I cost, Sec. II.B / Appendix A gradient) on device memory,
+ * asynchronous on the context stream: u_dev (M x N doubles), grad_dev (M x N doubles) and
+ * out_dev (6 doubles: C then the 5 terms) are device pointers owned by the caller.  Returns
+ * after enqueueing; errors raised inside kernels are reported by the next synchronising call
+ * (qoc_sync, qoc_get_info or a host evaluation). */
 qoc_status qoc_evaluate_device(qoc_ctx* ctx, const double* u_dev, double* grad_dev,
                                double* out_dev);
 
