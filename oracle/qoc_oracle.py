@@ -2,8 +2,9 @@
 quantum-control cost (Leung, Abdelhafez, Koch, Schuster, "Speedup for quantum optimal control
 from automatic differentiation based on graphics processing units", arXiv:1612.04929).
 
-TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline
-leg of ``bench.py`` may import this module.  It shares no code with the CUDA path.
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and, in ``bench.py``, the
+CPU-baseline leg and the oracle arm (``--impl reference``) may import this module.  It shares no
+code with the CUDA path.
 
 What it computes (notation of the paper, Sec. II):
 
