@@ -58,8 +58,9 @@ typedef enum qoc_precision {
     QOC_PREC_FP64 = 0,          /* plain FP64 form: parity anchor */
     QOC_PREC_FP32 = 1,          /* FP32 adjoint and stored states; slice exponentials and the
                                    carried recursions in extended FP32 (values as hi + lo pairs,
-                                   products of grid-split operands: exact FP32 sums of the 12-bit
-                                   parts plus rounded cross terms; see qoc_options.plain_fp32_exp) */
+                                   products of grid-split operands: exact FP32 sums of products
+                                   of parts of at most 13 significant bits, plus rounded cross
+                                   terms; see qoc_options.plain_fp32_exp) */
     QOC_PREC_TF32_SPLIT = 2,    /* the FP32 form, with the products of the large-d adjoint (d > 68)
                                    on tcgen05 tensor cores: TF32 hi + mid + lo split, six MMAs per
                                    real product, FP32 accumulation in tensor memory (the
