@@ -1,6 +1,8 @@
-"""The oracle arm of bench.py (--impl reference) runs on the host CPU alone: its JSON line carries
-the keys the benchmark contract asks for, describes its own CPU run, and prints nothing on a
-rank other than 0.  CPU only."""
+"""Host-side parts of bench.py, CPU only.  The oracle arm (--impl reference) runs on the host CPU
+alone: its JSON line carries the keys the benchmark contract asks for, describes its own CPU run,
+and prints nothing on a rank other than 0.  The roofline's algorithmic flop counts equal a walk
+over each adjoint form's products, and the whole-job value is every rank's units over the slowest
+rank's time."""
 import json
 import os
 import subprocess
@@ -36,3 +38,42 @@ def test_reference_line_has_the_contract_keys():
 
 def test_reference_line_only_on_rank_zero():
     assert run({"RANK": "1", "WORLD_SIZE": "2"}) == []
+
+
+def _bench():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def _walk_flops(form, d, p, n, S):
+    """Algorithmic flops of one slice's exponential adjoint, counted by walking its products:
+    a complex (m x k) by (k x q) product is 8 m k q real flops."""
+    mm = lambda m, k, q: 8.0 * m * k * q
+    if form == 3:                                   # low-rank reverse mode
+        f, r = 0.0, S
+        for _ in range(n):                          # S R and S^dag L per squaring, rank doubles
+            f += mm(d, d, r) + mm(d, d, r)
+            r *= 2
+        for _ in range(p - 1):                      # W = Z R, X^dag L, L W^dag per Horner step
+            f += mm(d, d, r) + mm(d, d, r) + mm(d, r, d)
+        return f + mm(d, r, d)                      # L_p R^dag / p
+    per_product = {0: 2, 1: 3}[form]                # reverse mode: 2, block recursion: 3
+    return per_product * (p - 1 + n) * mm(d, d, d) + mm(d, S, d)   # plus Ubar = G Psi^dag
+
+
+def test_roofline_flop_counts():
+    b = _bench()
+    assert b.expm_flops_per_slice(40, 9, 4) == 12 * 8.0 * 40 ** 3
+    for form in (0, 1, 3):
+        for d, p, n, S in [(40, 9, 4, 1), (64, 7, 1, 2), (48, 5, 0, 3), (81, 12, 2, 16)]:
+            assert b.adj_flops_per_slice(form, d, p, n, S) == _walk_flops(form, d, p, n, S), (form, d, p, n, S)
+
+
+def test_job_value_is_all_ranks_over_the_slowest():
+    b = _bench()
+    assert b.job_value(2000, 1, 2.5) == 2000 / 2.5e-3
+    assert b.job_value(2000, 4, 5.0) == 4 * 2000 / 5e-3
+    assert b.slowest_rank_ms(3.0, 1, "cpu") == 3.0
