@@ -243,6 +243,14 @@ qoc_status qoc_get_profile(qoc_ctx* ctx, qoc_profile* out);
 /* Clears the accumulated per-kernel timings. */
 qoc_status qoc_reset_profile(qoc_ctx* ctx);
 
+/* Measured multiply-add throughput of a device, the peak against which the FP32 (fp64 = 0) or
+ * FP64 (fp64 != 0) arithmetic of the products is reported: one launch of independent FMA chains
+ * on every SM, best of three CUDA-event timings on a stream of its own.  *tflops receives
+ * 2 x FMAs / second / 1e12; *sms (may be NULL) the device's SM count.  No device setting is read
+ * or changed.  Not a step of the paper's method.  Errors: QOC_ERR_ARG (tflops NULL),
+ * QOC_ERR_CUDA (no device, or a failed launch). */
+qoc_status qoc_measure_fma_peak(int device, int fp64, double* tflops, int* sms);
+
 /* Bytes of the device array that qoc_evaluate_static works in (32 MiB).  Every GPU that loads
  * the library holds this array until the process exits. */
 #define QOC_STATIC_ARENA_BYTES (32u << 20)
@@ -264,9 +272,15 @@ qoc_status qoc_reset_profile(qoc_ctx* ctx);
  *   grad_dev (M x N doubles) and out_dev (6 doubles: C then the 5 terms) receive the results.
  *   stream: cudaStream_t to enqueue on (NULL: the legacy default stream).
  * The call enqueues its kernels and returns without synchronising.  Its status covers the
- * argument checks, the size check and launch errors only; device-side conditions (a Taylor
- * order above its maximum) are not reported.  QOC_ERR_SHAPE also means that the problem does
- * not fit the array: about (N d^2 + 4 N d S) 16-byte numbers must stay below its size.
+ * argument checks, the size check and launch errors only.  Conditions found on the device (a
+ * NaN or Inf in the controls or the results, a Taylor order at its cap) are not returned; they
+ * leave out_dev[0] = NaN, so a caller checks that value after synchronising.
+ * QOC_ERR_SHAPE also means that the problem does not fit the array, and that check comes before
+ * any CUDA call.  With Spad = S rounded up to a multiple of min(S, 8) and d2 = d^2 rounded up to
+ * a multiple of 16, the array holds, each piece rounded up to 256 bytes: U_j and U_j^dag
+ * (32 N d2 bytes), the states (16 (N + 1) d Spad), costates and sources (16 N d Spad each),
+ * three d x Spad blocks, per-slice overlaps and occupations (24 N), the gradient parts
+ * (8 (M N + 1)) and a few small pieces: about 32 N d^2 + 48 N d Spad + 8 M N bytes in all.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
  * that device current; make that first call before capturing a stream.  All calls share the
  * one array and every call overwrites it: calls that may overlap on the GPU (different streams

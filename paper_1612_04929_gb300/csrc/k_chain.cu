@@ -412,6 +412,10 @@ k_finalize(int E, int M, int N, const double* __restrict__ u, Alpha5 al, const d
     out[5] = c67;
     out[0] = al.a[0] * fid + al.a[1] * c3 + al.a[2] * c4 + al.a[3] * c5 + al.a[4] * c67;
     if (!isfinite(out[0])) atomicOr(&prm->err, kErrNonfinite);
+    // every failure flagged on the device in this evaluation (non-finite input or result, a
+    // Taylor order at its cap, a bounded wait that ran out) also leaves C = NaN, so a caller
+    // that cannot read the flag still cannot mistake the result for a valid one
+    if (*(volatile int*)&prm->err != 0) out[0] = __longlong_as_double(0x7ff8000000000000ll);
 }
 
 cudaError_t launch_finalize(int E, int M, int N, const double* u, const double* alpha, const double2* Oj,

@@ -4,7 +4,9 @@
 // nearly the same at every slice (the drift H_0 does not change), so it accumulates coherently
 // along the N-slice chain.  The FP32 form therefore evaluates U_j = [T_p(X_j)]^(2^n) (Eqs. 9,
 // 10) with every matrix held as an unevaluated sum of two FP32 numbers:
-//   * X_j = -i s H_j is assembled in FP64 from FP64 copies of H_0, H_k, H_det,
+//   * X_j = -i s H_j is assembled in FP32 pair arithmetic from s H_0, s H_k, s H_det held as
+//     FP32 pairs (written once per evaluation by k_split_scale after the (p, n) pick), with
+//     no FP64 arithmetic per slice,
 //   * matrices are stored grid-split (qoc_device.cuh): v = v1 + v2, v1 on the power-of-two grid
 //     2^(e - 12) set by a norm bound of the matrix, so that the sums of the grid-part products
 //     are exact FP32 FMAs and only the cross terms a1 b2 + a2 b are rounded (about 2^-36 of

@@ -160,10 +160,12 @@ k_tc_step(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
         // instruction descriptor: D f32, A/B tf32, both K-major, N = 64, M = 128
         const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
         const uint32_t idesc_nA = idesc | (1u << 13);   // negate A
-        int loaded = 0;
+        int last_issued[NST];   // per ring stage: the last step whose copy was issued (-1: none)
+#pragma unroll
+        for (int b2 = 0; b2 < NST; ++b2) last_issued[b2] = -1;
         auto load = [&](int s) {   // planes: A re (NPL), A im (NPL), B re (NPL), B im (NPL)
-            ++loaded;
             const int t = s / nk, kc = s % nk, b = s % NST;
+            last_issued[b] = s;
             unsigned char* st = base + b * STAGE;
             mbar_expect_tx(&full[b], STAGE);
             for (int part = 0; part < 2 * NPL; ++part) {
@@ -222,13 +224,10 @@ k_tc_step(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
         mma_commit(&done);
         if (!ok) {
             atomicOr(&prm->err, kErrTimeout);
-            // let the last copy issued into each ring stage land before the CTA leaves (bounded)
-            for (int b2 = 0; b2 < NST; ++b2) {
-                int last = -1;
-                for (int s2 = loaded - 1; s2 >= 0; --s2)
-                    if (s2 % NST == b2) { last = s2; break; }
-                if (last >= 0) mbar_wait(&full[b2], (uint32_t)((last / NST) & 1), limit);
-            }
+            // let the last copy issued into each ring stage land before the CTA leaves (bounded);
+            // the issued steps need not be a prefix (fault injection withholds step 0)
+            for (int b2 = 0; b2 < NST; ++b2)
+                if (last_issued[b2] >= 0) mbar_wait(&full[b2], (uint32_t)((last_issued[b2] / NST) & 1), limit);
         }
     }
     if (tid == 0) s_ok = ok ? 1 : 0;   // only the issuing thread knows whether its waits ran out

@@ -27,9 +27,10 @@ static __device__ __align__(256) unsigned char g_arena[QOC_STATIC_ARENA_BYTES];
 constexpr int kMaxDevices = 64;
 void* g_arena_addr[kMaxDevices] = {nullptr};
 
-// carve 256-byte-aligned pieces out of the arena (pointer arithmetic only)
+// carve 256-byte-aligned pieces out of the arena: offsets first (no base), pointers once the
+// device address is known
 struct Carver {
-    unsigned char* base;
+    uintptr_t base = 0;
     size_t used = 0;
     template <typename T>
     T* take(size_t count) {
@@ -37,6 +38,41 @@ struct Carver {
         T* p = reinterpret_cast<T*>(base + used);
         used += count * sizeof(T);
         return p;
+    }
+};
+
+// The arena's layout for one problem; with base = 0 only the size (used) is meaningful.
+template <typename R>
+struct StaticLayout {
+    using C = C_t<R>;
+    using K = K_t<R>;
+    DevParams* prm;
+    double* norms;
+    C *psiT, *Ubuf, *states, *Gbuf, *src;
+    K *ckpt, *carry;
+    double2 *Oj, *Ofin;
+    double *C5j, *gpart, *colw;
+    int* fmask_zero;
+    size_t used;
+    StaticLayout(uintptr_t base, int d, int M, int N, size_t slice, int Spad, long long ustride) {
+        Carver cv;
+        cv.base = base;
+        prm = cv.take<DevParams>(1);
+        norms = cv.take<double>(M + 2);
+        psiT = cv.take<C>(slice);
+        ckpt = cv.take<K>(slice);
+        Ubuf = cv.take<C>((size_t)N * ustride);
+        states = cv.take<C>((size_t)(N + 1) * slice);
+        Gbuf = cv.take<C>((size_t)N * slice);
+        src = cv.take<C>((size_t)N * slice);
+        carry = cv.take<K>(slice);
+        Oj = cv.take<double2>(N);
+        C5j = cv.take<double>(N);
+        Ofin = cv.take<double2>(1);
+        gpart = cv.take<double>((size_t)M * N + 1);
+        colw = cv.take<double>(Spad);
+        fmask_zero = cv.take<int>(d);
+        used = cv.used;
     }
 };
 
@@ -56,14 +92,6 @@ extern "C" qoc_status qoc_evaluate_static(int d, int M, int N, int S, double dt,
     if (d < 1 || d > fused_max_d<double>() || M < 0 || M > kMaxControls || N < 1 || S < 1 || S > d)
         return QOC_ERR_SHAPE;
     if (!(dt > 0.0)) return QOC_ERR_ARG;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return QOC_ERR_CUDA;
-    if (!g_arena_addr[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_arena) != cudaSuccess || !p) return QOC_ERR_CUDA;
-        g_arena_addr[dev] = p;
-    }
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     using R = double;
     using C = C_t<R>;
     using K = K_t<R>;
@@ -75,24 +103,33 @@ extern "C" qoc_status qoc_evaluate_static(int d, int M, int N, int S, double dt,
     sv.S = S;
     const size_t slice = sv.slice();
     const long long ustride = 2 * (((long long)d * d + 15) / 16 * 16);   // U_j and U_j^dag
-
-    Carver cv{reinterpret_cast<unsigned char*>(g_arena_addr[dev])};
-    DevParams* prm = cv.take<DevParams>(1);
-    double* norms = cv.take<double>(M + 2);
-    C* psiT = cv.take<C>(slice);
-    K* ckpt = cv.take<K>(slice);
-    C* Ubuf = cv.take<C>((size_t)N * ustride);
-    C* states = cv.take<C>((size_t)(N + 1) * slice);
-    C* Gbuf = cv.take<C>((size_t)N * slice);
-    C* src = cv.take<C>((size_t)N * slice);
-    K* carry = cv.take<K>(slice);
-    double2* Oj = cv.take<double2>(N);
-    double* C5j = cv.take<double>(N);
-    double2* Ofin = cv.take<double2>(1);
-    double* gpart = cv.take<double>((size_t)M * N + 1);
-    double* colw = cv.take<double>(sv.Spad);
-    int* fmask_zero = cv.take<int>(d);
-    if (cv.used > QOC_STATIC_ARENA_BYTES) return QOC_ERR_SHAPE;   // the problem does not fit
+    // the size check comes before any CUDA call
+    if (StaticLayout<R>(0, d, M, N, slice, sv.Spad, ustride).used > QOC_STATIC_ARENA_BYTES)
+        return QOC_ERR_SHAPE;   // the problem does not fit
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return QOC_ERR_CUDA;
+    if (!g_arena_addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_arena) != cudaSuccess || !p) return QOC_ERR_CUDA;
+        g_arena_addr[dev] = p;
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const StaticLayout<R> L(reinterpret_cast<uintptr_t>(g_arena_addr[dev]), d, M, N, slice, sv.Spad, ustride);
+    DevParams* prm = L.prm;
+    double* norms = L.norms;
+    C* psiT = L.psiT;
+    K* ckpt = L.ckpt;
+    C* Ubuf = L.Ubuf;
+    C* states = L.states;
+    C* Gbuf = L.Gbuf;
+    C* src = L.src;
+    K* carry = L.carry;
+    double2* Oj = L.Oj;
+    double* C5j = L.C5j;
+    double2* Ofin = L.Ofin;
+    double* gpart = L.gpart;
+    double* colw = L.colw;
+    int* fmask_zero = L.fmask_zero;
 
     auto ok = [](cudaError_t e) { return e == cudaSuccess; };
     const double2* H0 = reinterpret_cast<const double2*>(H0_dev);

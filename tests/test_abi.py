@@ -119,3 +119,65 @@ def test_invalid_options_are_rejected_before_the_device(lib, field, value):
     out = ct.c_void_p(1)
     assert lib.qoc_create(ct.byref(out), ct.byref(opt)) == 1
     assert not out.value
+
+
+# ------------------------------------------------------------------ allocation-free entry point
+ARENA_BYTES = 32 << 20
+PARAM_BLOCK_BYTES = 1072     # the device parameter block at the start of the array
+
+
+def static_arena_bytes(d, M, N, S):
+    """The fixed array's use by qoc_evaluate_static, as include/qoc.h states it: every piece
+    starts on a 256-byte boundary; U_j and U_j^dag take 2 ceil16(d^2) complex128 numbers per
+    slice, the d x S blocks are padded to Spad columns (panels of min(S, 8) columns)."""
+    cb = min(S, 8)
+    spad = -(-S // cb) * cb
+    blk = d * spad
+    d2 = -(-d * d // 16) * 16
+    pieces = [PARAM_BLOCK_BYTES, 8 * (M + 2), 16 * blk, 16 * blk, 16 * N * 2 * d2, 16 * (N + 1) * blk,
+              16 * N * blk, 16 * N * blk, 16 * blk, 16 * N, 8 * N, 16, 8 * (M * N + 1), 8 * spad, 4 * d]
+    used = 0
+    for p in pieces:
+        used = -(-used // 256) * 256 + p
+    return used
+
+
+def static_n_max(d, M, S):
+    lo, hi = 1, 1 << 22
+    while lo < hi:
+        mid = (lo + hi + 1) // 2
+        if static_arena_bytes(d, M, mid, S) <= ARENA_BYTES:
+            lo = mid
+        else:
+            hi = mid - 1
+    return lo
+
+
+STATIC_SHAPES = [(48, 2, 1), (48, 3, 8), (44, 2, 41), (8, 3, 3), (1, 0, 1), (30, 64, 30)]
+
+
+def _static_status(lib, d, M, N, S):
+    import ctypes as ct
+    alpha = (ct.c_double * 5)(1, 0, 0, 0, 0)
+    fake = ct.c_void_p(16)   # never dereferenced: these calls return before any device work
+    return lib.qoc_evaluate_static(d, M, N, S, ct.c_double(0.1), fake, fake, fake, fake, fake, None, alpha,
+                                   fake, fake, None)
+
+
+@pytest.mark.parametrize("shape", STATIC_SHAPES, ids=lambda s: "d%dM%dS%d" % s)
+def test_static_arena_rejects_one_slice_past_the_stated_bound(lib, shape):
+    """The size check comes before any CUDA call: one slice beyond the bound that the header
+    states is QOC_ERR_SHAPE on any machine (the GPU test runs the largest admitted N)."""
+    d, M, S = shape
+    n = static_n_max(d, M, S)
+    assert _static_status(lib, d, M, n + 1, S) == 2
+    assert _static_status(lib, d, M, 10 * n, S) == 2
+
+
+@pytest.mark.skipif(_has_gpu(), reason="the admitted size would run kernels on a GPU")
+@pytest.mark.parametrize("shape", STATIC_SHAPES, ids=lambda s: "d%dM%dS%d" % s)
+def test_static_arena_admits_the_stated_bound_without_gpu(lib, shape):
+    """Up to the stated bound the size check passes, and without a GPU the call then fails
+    loudly at its first CUDA call (QOC_ERR_CUDA), with no fallback."""
+    d, M, S = shape
+    assert _static_status(lib, d, M, static_n_max(d, M, S), S) == 7
