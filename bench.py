@@ -39,9 +39,39 @@ MEASURED_TRAFFIC = {
 MEASURED_PIPES = {
     ("transmon_cavity_d40", "fp32", "expm_fwd", 1125): {"fma_pipe_pct": 47.2, "issue_active_pct": 68.7},
 }
-# FP32 FMA peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (max SM clock)
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# FP32 FMA peak from unit counts (context only; the roofline uses the measured peak):
+# SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (the maximum SM clock)
+def derived_fp32_peak_tflops(sms):
+    return sms * 128 * 2 * 2.07e9 / 1e12
+
+
 L2_FLUSH_BYTES = 256 << 20
+
+
+def measured_peaks(device):
+    """Denominators of the roofline fractions: FP32 and FP64 FMA throughput measured on this
+    device by the library's FMA-chain kernel (qoc_measure_fma_peak), the SM count read from the
+    device, and the BF16 tensor and HBM peaks of MEASURED_PEAKS.json (copy and cuBLAS GEMM
+    measured on the GB300s) when that file is present."""
+    from paper_1612_04929_gb300 import qoc_measure_fma_peak
+    fp32, sms = qoc_measure_fma_peak(device, fp64=False)
+    fp64, _ = qoc_measure_fma_peak(device, fp64=True)
+    peaks = {"fp32_tflops": fp32, "fp64_tflops": fp64, "sms": sms,
+             "fp32_derived_tflops": derived_fp32_peak_tflops(sms),
+             "fp_source": "measured: qoc_measure_fma_peak (independent FMA chains on every SM, best of 3 "
+                          "CUDA-event timings)"}
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            mp = json.load(open(path))
+            peaks.update({"bf16_tflops": mp.get("bf16_tflops"), "bf16_tflops_sustained": mp.get("bf16_tflops_sustained"),
+                          "hbm_gbs": mp.get("hbm_gbs"), "tensor_source": "MEASURED_PEAKS.json (measured)"})
+        except (OSError, ValueError):
+            pass
+    if peaks.get("bf16_tflops") is None:
+        peaks.update({"bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "hbm_gbs": 6800.0,
+                      "tensor_source": "fallback (no MEASURED_PEAKS.json)"})
+    return peaks
 
 
 def parse():
@@ -60,6 +90,8 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=0, help="slices in the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-form", action="store_true", help="skip timing the plain FP64 GPU form")
+    ap.add_argument("--no-per-config", action="store_true",
+                    help="skip the per-config lines (the other four configurations, a few seconds each)")
     ap.add_argument("--graph", action="store_true", help="replay each evaluation from a captured CUDA graph")
     ap.add_argument("--gradient", choices=["exact", "first_order"], default="exact",
                     help="exact derivative of the truncated series, or the paper's first-order Eq. 11")
@@ -129,36 +161,57 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ oracle (CPU) timing
-def oracle_sample_time(workload, nslices, repeats=1, ref_slices=0, exact=True, maker=None, min_seconds=0.0):
+def oracle_sample_time(workload, nslices, repeats=1, ref_slices=0, exact=True, maker=None, min_seconds=0.0,
+                       threads=1):
     """Times the CPU FP64 oracle on the first `nslices` slices of the workload in a child
-    process limited to one BLAS thread: at least `repeats` evaluations, and more until
-    `min_seconds` of timed work.  With ref_slices > 0 the child also evaluates the oracle once on
-    the first ref_slices slices (untimed) and returns its cost and gradient, the reference for
-    the GPU result's error.  Returns (seconds per evaluation, slices, reference, evaluations)."""
+    process with `threads` BLAS threads (0: the library's default, all host cores): at least
+    `repeats` evaluations, and more until `min_seconds` of timed work.  With ref_slices > 0 the
+    child also evaluates the oracle once on the first ref_slices slices (untimed) and returns its
+    cost and gradient, the reference for the GPU result's error.  `maker` is an expression in n
+    that builds the problem (default: the named workload with N = n).  Returns (seconds per
+    evaluation, slices, reference, evaluations, threads that gained CPU time while timing)."""
     code = f"""
 import json, os, sys, time
 sys.path.insert(0, {ROOT!r})
 import synthetic as sy
 from oracle import qoc_oracle as orc
+def ticks():
+    out = {{}}
+    try:
+        for tid in os.listdir("/proc/self/task"):
+            with open("/proc/self/task/%s/stat" % tid) as f:
+                fl = f.read().rsplit(")", 1)[1].split()
+            out[tid] = int(fl[11]) + int(fl[12])
+    except (OSError, ValueError, IndexError):
+        return None
+    return out
 make = (lambda n: {maker}) if {maker!r} else (lambda n: sy.WORKLOADS[{workload!r}](N=n))
 p = make({nslices})
 orc.cost_and_grad(p, p.u)
 ts = []
+t0k = ticks()
 while len(ts) < {repeats} or (sum(ts) < {min_seconds} and len(ts) < 1000):
     t0 = time.perf_counter(); orc.cost_and_grad(p, p.u); ts.append(time.perf_counter() - t0)
+t1k = ticks()
+busy = None if t0k is None or t1k is None else sum(1 for k, v in t1k.items() if v > t0k.get(k, 0))
 ref = None
 if {ref_slices} > 0:
     q = make({ref_slices})
     c, g, _ = orc.cost_and_grad(q, q.u, exact={exact!r})
     ref = {{"N": {ref_slices}, "cost": float(c), "grad": [float(x) for x in g.ravel()]}}
-print(json.dumps({{"t": sum(ts) / len(ts), "n": len(ts), "ref": ref}}))
+print(json.dumps({{"t": sum(ts) / len(ts), "n": len(ts), "ref": ref, "busy": busy}}))
 """
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    env = dict(os.environ)
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        if threads > 0:
+            env[var] = str(threads)
+        else:
+            env.pop(var, None)
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
     if r.returncode != 0:
         raise RuntimeError(r.stderr)
     res = json.loads(r.stdout.strip().splitlines()[-1])
-    return float(res["t"]), nslices, res["ref"], int(res["n"])
+    return float(res["t"]), nslices, res["ref"], int(res["n"]), res.get("busy")
 
 
 def thread_cpu_ticks():
@@ -251,6 +304,294 @@ def job_value(units_per_rank, world, t_max_ms):
     return units_per_rank * world / (t_max_ms / 1e3)
 
 
+def roofline_of(prob, precision, info, prof, K, peaks, traffic_key=None):
+    """The dominant exponential kernel of one evaluation: its algorithmic flops (8 d^3 per
+    complex product) over its summed event time, against the measured peak of the arithmetic
+    it runs on (FP32 or FP64 FMA lanes; BF16 tensor cores for the exact-accumulation tensor-core
+    products, whose executed MMA flops are reported beside)."""
+    d, p, n = prob.d, info["p"], info["n"]
+    per_slice = {"expm_fwd": expm_flops_per_slice(d, p, n),
+                 "expm_fwd (recompute)": expm_flops_per_slice(d, p, n),
+                 "expm_adj": adj_flops_per_slice(info.get("adjoint_form", 1), d, p, n, prob.S)}
+    if info.get("adjoint_form") == 2:   # first-order gradient: no adjoint exponential
+        per_slice.pop("expm_adj")
+    cands = {k: v for k, v in prof.items() if k in per_slice}
+    if not cands:
+        return None
+    top_name, (top_launches, top_ms) = max(cands.items(), key=lambda kv: kv[1][1])
+    N_w = info["wave_slices"]
+    last = prob.N - (info["n_waves"] - 1) * N_w
+    slices = prob.N if top_name != "expm_fwd (recompute)" else prob.N - last
+    flops = per_slice[top_name] * slices * prob.E * K
+    achieved = flops / (top_ms / 1e3) / 1e12
+    tensor = precision == "bf16" and top_name == "expm_adj" and info["kernel_path"] == 1
+    if tensor:
+        peak, bound, src = peaks["bf16_tflops"], "tensor", peaks["tensor_source"] + ", BF16 burst"
+    elif precision == "fp64":
+        peak, bound, src = peaks["fp64_tflops"], "alu", peaks["fp_source"] + ", FP64"
+    else:
+        peak, bound, src = peaks["fp32_tflops"], "alu", peaks["fp_source"] + ", FP32"
+    traffic = MEASURED_TRAFFIC.get(traffic_key) if traffic_key else None
+    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": traffic, "kernel": top_name, "launches": top_launches, "avg_launch_ms": top_ms / top_launches,
+            "peak_source": src + " (of measured)",
+            "traffic_source": ("dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of this kernel at "
+                               "this workload") if traffic else None}
+    if tensor:
+        roof["executed_mma_tflops"] = achieved * OZ_MMA_PER_COMPLEX_PRODUCT / 4.0
+        roof["note"] = ("algorithmic flops count 8 d^3 per complex product; the exact-accumulation tensor-core "
+                        "products issue %d real BF16 GEMMs of d^3 per complex product" % OZ_MMA_PER_COMPLEX_PRODUCT)
+    elif precision != "fp64" and top_name.startswith("expm_fwd") and info["kernel_path"] == 0:
+        roof["note"] = ("algorithmic flops (8 d^3 per complex product); the FP32 form's grid-split products "
+                        "execute 12 FMAs per complex multiply-add (3.25 per algorithmic one), so the split "
+                        "exponential's fraction is bounded near 0.3 by construction")
+    return roof
+
+
+# real BF16 GEMMs of d^3 per complex product in the exact-accumulation tensor-core form: 10 slice
+# pairs x 4 real products
+OZ_MMA_PER_COMPLEX_PRODUCT = 40
+
+
+def time_device_evals(ctx, u, grad, out, K, warmup, flush, stream):
+    """K evaluations after `warmup`, each bracketed by CUDA events on the evaluation's stream
+    with the L2 flushed before it (outside the events); returns the mean ms."""
+    import torch
+    for _ in range(max(warmup, 1)):
+        ctx.evaluate_device(u.data_ptr(), grad.data_ptr(), out.data_ptr())
+    ctx.sync()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    torch.cuda.synchronize()
+    for k in range(K):
+        flush.zero_()
+        starts[k].record(stream)
+        ctx.evaluate_device(u.data_ptr(), grad.data_ptr(), out.data_ptr())
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    ctx.sync()
+    return sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / K
+
+
+def truncated(prob, n):
+    """The same system, targets and controls restricted to the first n slices."""
+    import dataclasses
+    path = None if prob.psiT_path is None else prob.psiT_path[:n]
+    return dataclasses.replace(prob, N=n, u=prob.u[:, :n].copy(), psiT_path=path)
+
+
+def oracle_reference(q, threads=0):
+    """Cost and gradient of problem q by the CPU FP64 oracle, in a child process with `threads`
+    BLAS threads (0: the library default)."""
+    import pickle
+    import tempfile
+    with tempfile.NamedTemporaryFile(suffix=".pkl", delete=False) as f:
+        pickle.dump(q, f)
+        path = f.name
+    code = f"""
+import json, pickle, sys
+sys.path.insert(0, {ROOT!r})
+from oracle import qoc_oracle as orc
+q = pickle.load(open({path!r}, "rb"))
+c, g, _ = orc.cost_and_grad(q, q.u)
+print(json.dumps({{"cost": float(c), "grad": [float(x) for x in g.ravel()]}}))
+"""
+    env = dict(os.environ)
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        if threads > 0:
+            env[var] = str(threads)
+        else:
+            env.pop(var, None)
+    try:
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+        if r.returncode != 0:
+            raise RuntimeError(r.stderr[-500:])
+        return json.loads(r.stdout.strip().splitlines()[-1])
+    finally:
+        os.unlink(path)
+
+
+def gpu_error_vs_oracle(prob, precision, stream, ref_slices, threads=0):
+    """Relative cost and gradient error of the GPU form against the CPU FP64 oracle on the first
+    ref_slices slices of the problem (the whole problem when ref_slices >= N)."""
+    import numpy as np
+    from paper_1612_04929_gb300 import Context
+    q = prob if ref_slices >= prob.N else truncated(prob, ref_slices)
+    ref = oracle_reference(q, threads)
+    with Context(precision, device=0, stream=stream.cuda_stream) as cq:
+        cq.set_problem(q)
+        c_gpu, g_gpu, _ = cq.evaluate(q.u)
+    g_ref = np.asarray(ref["grad"])
+    return {"precision": precision, "slices": q.N, "cost_rel": abs(c_gpu - ref["cost"]) / abs(ref["cost"]),
+            "grad_rel": float(np.linalg.norm(np.ravel(g_gpu) - g_ref) / np.linalg.norm(g_ref))}
+
+
+def measure_config(name, precision, peaks, stream, flush, K, warmup, fp64_N=0, err_slices=0, fp64_cache=None):
+    """One per-config line: device time per evaluation, slice-steps/s, its own roofline, the
+    plain FP64 GPU form's time on the same workload (on its first fp64_N slices, scaled by N,
+    when fp64_N > 0), and the error against the oracle on the first err_slices slices."""
+    import torch
+    from paper_1612_04929_gb300 import Context
+    prob = make_problem(name)
+    u = torch.tensor(prob.u, dtype=torch.float64, device="cuda")
+    grad = torch.empty_like(u)
+    out = torch.empty(6, dtype=torch.float64, device="cuda")
+    with Context(precision, device=0, stream=stream.cuda_stream, profile=True) as ctx:
+        ctx.set_problem(prob)
+        ms = time_device_evals(ctx, u, grad, out, K, warmup, flush, stream)
+        ctx.reset_profile()
+        ms_p = time_device_evals(ctx, u, grad, out, K, 0, flush, stream)   # per-kernel events
+        info, prof = ctx.info(), ctx.profile()
+    units = prob.N * prob.E
+    row = {"workload": prob.name, "precision": precision, "d": prob.d, "N": prob.N, "M": prob.M, "S": prob.S,
+           "E": prob.E, "p": info["p"], "n": info["n"], "kernel_path": info["kernel_path"],
+           "ms_per_step": ms, "value": units / (ms / 1e3), "unit": UNIT, "steps": K,
+           "roofline": roofline_of(prob, precision, info, prof, K, peaks)}
+    row["roofline_events_ms_per_step"] = ms_p
+    if precision != "fp64":
+        key = (name, fp64_N)
+        if fp64_cache is not None and key in fp64_cache:
+            row["fp64_form"] = fp64_cache[key]
+        else:
+            q = prob if not fp64_N else truncated(prob, fp64_N)
+            uq = torch.tensor(q.u, dtype=torch.float64, device="cuda")
+            gq = torch.empty_like(uq)
+            with Context("fp64", device=0, stream=stream.cuda_stream) as c64:
+                c64.set_problem(q)
+                ms64 = time_device_evals(c64, uq, gq, out, 1 if fp64_N else 2, 1, flush, stream)
+            scale = prob.N / q.N
+            row["fp64_form"] = {"ms_per_step": ms64 * scale, "value": units / (ms64 * scale / 1e3),
+                                "measured_slices": q.N,
+                                "how": "timed on the whole workload" if q is prob else
+                                       f"timed on the first {q.N} slices and scaled by N (time is linear in N)"}
+            if fp64_cache is not None:
+                fp64_cache[key] = row["fp64_form"]
+        row["speedup_vs_fp64_form"] = row["fp64_form"]["ms_per_step"] / ms
+    if err_slices:
+        try:
+            row["error_vs_oracle"] = gpu_error_vs_oracle(prob, precision, stream, err_slices)
+        except Exception as exc:
+            row["error_vs_oracle"] = {"failed": str(exc)[:200]}
+    return row
+
+
+def measure_batch(count, ensemble, K, warmup, stream, flush, one_by_one=True, profile=False, err_problems=()):
+    """The batched sweep: `count` problems of uneven d, N, M with `ensemble`-member detuning
+    ensembles, FP32 form, one qoc_evaluate_batch call per step; optionally compared with
+    evaluating the same contexts one after another, and checked against the oracle on the first
+    40 slices of the listed problems."""
+    import torch
+    import synthetic as sy
+    from paper_1612_04929_gb300 import Context, qoc_evaluate_batch
+    probs = sy.batch_problems(count, ensemble=ensemble)
+    ctxs = []
+    for p in probs:
+        c = Context("fp32", profile=profile)
+        c.set_problem(p)
+        ctxs.append(c)
+    us = [torch.tensor(p.u, dtype=torch.float64, device="cuda") for p in probs]
+    gs = [torch.empty_like(u) for u in us]
+    outs = [torch.empty(6, dtype=torch.float64, device="cuda") for _ in probs]
+    ptr = lambda ts: [t.data_ptr() for t in ts]
+
+    def batch():
+        qoc_evaluate_batch(ctxs, ptr(us), ptr(gs), ptr(outs), stream.cuda_stream)
+
+    def seq():
+        for c, u, g, o in zip(ctxs, us, gs, outs):
+            c.evaluate_device(u.data_ptr(), g.data_ptr(), o.data_ptr())
+            c.sync()
+
+    for _ in range(max(warmup, 1)):
+        batch()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(K):
+        flush.zero_()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        batch()
+        e.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(e))
+    ms = sum(ts) / len(ts)
+    by_d = {}
+    if profile:     # per-kernel event time summed over the contexts (overlapping)
+        for c, p in zip(ctxs, probs):
+            for k, (n_l, t) in c.profile().items():
+                key = f"d{p.d}:{k}"
+                by_d[key] = by_d.get(key, 0.0) + t / K
+    ms_seq = None
+    if one_by_one:
+        seq()
+        t0 = time.perf_counter()
+        reps = max(1, min(K, 2))
+        for _ in range(reps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            seq()
+        ms_seq = (time.perf_counter() - t0) * 1e3 / reps
+    infos = [c.info() for c in ctxs]
+    for c in ctxs:
+        c.close()
+    units = sum(p.N * p.E for p in probs)
+    flops = 0.0
+    for p, inf in zip(probs, infos):
+        flops += p.N * p.E * (expm_flops_per_slice(p.d, inf["p"], inf["n"]) +
+                              adj_flops_per_slice(inf.get("adjoint_form", 1), p.d, inf["p"], inf["n"], p.S))
+    row = {"workload": f"batch{count}_E{ensemble}", "problems": count, "members": ensemble, "precision": "fp32",
+           "slice_steps_per_step": units, "ms_per_step": ms, "value": units / (ms / 1e3), "unit": UNIT, "steps": K,
+           "d_counts": {str(d): sum(1 for p in probs if p.d == d) for d in sorted({p.d for p in probs})},
+           "one_by_one_ms_per_step": ms_seq, "batch_speedup_vs_one_by_one": (ms_seq / ms) if ms_seq else None,
+           "step_algorithmic_tflops": flops / (ms / 1e3) / 1e12,
+           "note": "step_algorithmic_tflops: the exponentials' and adjoints' algorithmic flops (8 d^3 per complex "
+                   "product) of every problem over the batch's time (no single dominant kernel)"}
+    if by_d:
+        row["kernel_ms_by_d"] = {k: round(v, 3) for k, v in sorted(by_d.items(), key=lambda kv: -kv[1])[:16]}
+    if err_problems:
+        errs = []
+        for i in err_problems:
+            try:
+                e = gpu_error_vs_oracle(probs[i], "fp32", stream, 40)
+                e["problem"] = probs[i].name
+            except Exception as exc:
+                e = {"problem": probs[i].name, "failed": str(exc)[:200]}
+            errs.append(e)
+        row["error_vs_oracle"] = errs
+    return row
+
+
+def per_config_lines(args, peaks, stream, flush):
+    """The other configurations, each bounded to a few seconds of GPU time: the gate (d = 4,
+    FP64), the 81-level and 256-level systems in the FP32 and BF16_SPLIT forms, and the batched
+    sweep with 1 and 32 ensemble members (32 members on the first 16 problems, 512 trajectories)."""
+    rows = {}
+    fp64_cache = {}
+    plan = [("c1_cnot2q_fp64", "cnot2q", "fp64", 5, 0, 200),
+            ("c3_transmon4_fp32", "transmon4", "fp32", 3, 0, 1000),
+            ("c3_transmon4_bf16", "transmon4", "bf16", 3, 0, 1000),
+            ("c4_gue256_fp32", "gue256", "fp32", 2, 200, 40),
+            ("c4_gue256_bf16", "gue256", "bf16", 2, 200, 40)]
+    for key, name, prec, K, fp64_N, err in plan:
+        try:
+            rows[key] = measure_config(name, prec, peaks, stream, flush, K, 1, fp64_N=fp64_N, err_slices=err,
+                                       fp64_cache=fp64_cache)
+        except Exception as exc:
+            rows[key] = {"failed": str(exc)[:300]}
+        print(f"# per_config {key}: {json.dumps(rows[key])[:300]}", file=sys.stderr, flush=True)
+    # error samples: problems 2 (d = 81), 7 (d = 40) and 15 (d = 128) of the sweep
+    for key, count, ens, K, seq, errs in (("c5_batch128_E1", 128, 1, 2, True, (2, 7, 15)),
+                                          ("c5_batch16_E32", 16, 32, 1, False, (15,))):
+        try:
+            rows[key] = measure_batch(count, ens, K, 1, stream, flush, one_by_one=seq, err_problems=errs)
+        except Exception as exc:
+            rows[key] = {"failed": str(exc)[:300]}
+        print(f"# per_config {key}: {json.dumps(rows[key])[:300]}", file=sys.stderr, flush=True)
+    return rows
+
+
 def ours_arm(args):
     import numpy as np
     import torch
@@ -267,13 +608,13 @@ def ours_arm(args):
         qbuild.build()
     if world > 1:
         dist.barrier()
+    peaks = measured_peaks(local)
     prob = make_problem(args.workload, args.N)
     precision = args.precision or prob.precision
     stream = torch.cuda.Stream()          # every kernel of the step and every event on one stream
     torch.cuda.set_stream(stream)
-    # per-kernel events (profile) need plain launches; with --graph the step is a graph replay
     ctx = Context(precision, device=local, stream=stream.cuda_stream, ckpt_stride=args.ckpt_stride,
-                  profile=not args.graph, gradient=args.gradient, graph=args.graph)
+                  gradient=args.gradient, graph=args.graph)
     ctx.set_problem(prob)
     u = torch.tensor(prob.u, dtype=torch.float64, device="cuda")
     grad = torch.empty_like(u)
@@ -293,7 +634,6 @@ def ours_arm(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    ctx.reset_profile()
     with ClockSampler(local) as clk:
         for k in range(K):
             flush.zero_()
@@ -304,48 +644,32 @@ def ours_arm(args):
     if world > 1:
         dist.barrier()
     ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / K
-    prof = ctx.profile()
     ctx.sync()
     t_max = slowest_rank_ms(ms, world, "cuda")
     units = prob.N * prob.E
     value = job_value(units, world, t_max)
 
-    # dominant kernel and its roofline (algorithmic flops / measured launch time)
-    d, p, n = prob.d, info["p"], info["n"]
-    per_slice = {"expm_fwd": expm_flops_per_slice(d, p, n),
-                 "expm_fwd (recompute)": expm_flops_per_slice(d, p, n),
-                 "expm_adj": adj_flops_per_slice(info.get("adjoint_form", 1), d, p, n, prob.S)}
-    # the roofline line covers the dominant kernel that has an algorithmic flop count (the
-    # exponential kernels); the serial sweeps are latency-bound and reported in "kernels"
-    if info.get("adjoint_form") == 2:   # first-order gradient: no adjoint exponential
-        per_slice.pop("expm_adj")
-    cands = {k: v for k, v in prof.items() if k in per_slice}
-    roof = None
-    if cands:
-        top_name, (top_launches, top_ms) = max(cands.items(), key=lambda kv: kv[1][1])
-        N_w = info["wave_slices"]
-        last = prob.N - (info["n_waves"] - 1) * N_w
-        slices = prob.N if top_name != "expm_fwd (recompute)" else prob.N - last
-        flops = per_slice[top_name] * slices * prob.E * K
-        achieved = flops / (top_ms / 1e3) / 1e12
-        fp32 = precision != "fp64"
-        # DRAM bytes per launch of the dominant kernel, from an ncu capture of the same kernel at
-        # this workload (dram__bytes_read.sum + dram__bytes_write.sum); None where none was taken
-        traffic = MEASURED_TRAFFIC.get((prob.name, precision, top_name, info["wave_slices"]))
-        pipes = MEASURED_PIPES.get((prob.name, precision, top_name, info["wave_slices"]))
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS if fp32 else None,
-                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS if fp32 else None,
-                "traffic": traffic, "kernel": top_name, "launches": top_launches,
-                "avg_launch_ms": top_ms / top_launches,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
-                "note": "algorithmic flops (8 d^3 per complex product); the FP32 form's grid-split "
-                        "products execute 12 FMAs per complex multiply-add (3.25 per algorithmic one), "
-                        "so the split exponential's fraction is bounded near 0.3 by construction",
-                "traffic_source": ("dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of this "
-                                   "kernel at this workload") if traffic else None}
+    # The per-kernel times come from a second timed pass of the same K steps with every kernel
+    # bracketed by CUDA events on the context stream (the headline above runs without them).
+    # The dominant kernel's roofline: algorithmic flops / its summed event time.
+    cp = Context(precision, device=local, stream=stream.cuda_stream, ckpt_stride=args.ckpt_stride,
+                 profile=True, gradient=args.gradient)
+    cp.set_problem(prob)
+    gp = torch.empty_like(u)
+    op = torch.empty(6, dtype=torch.float64, device="cuda")
+    ms_prof = time_device_evals(cp, u, gp, op, K, max(args.warmup, 3), flush, stream)
+    cp.reset_profile()
+    time_device_evals(cp, u, gp, op, K, 0, flush, stream)
+    prof = cp.profile()
+    cp.close()
+    roof = roofline_of(prob, precision, info, prof, K, peaks,
+                       traffic_key=(prob.name, precision, "expm_fwd", info["wave_slices"]))
+    if roof is not None:
+        pipes = MEASURED_PIPES.get((prob.name, precision, roof["kernel"], info["wave_slices"]))
         if pipes:
             roof["executed"] = dict(pipes, source="ncu --set full, one launch of this kernel at this workload "
                                                   "(sm__pipe_fma_cycles_active, smsp__issue_active)")
+        roof["events_pass_ms_per_step"] = ms_prof
     kernels = {k: {"launches": v[0], "ms_per_step": v[1] / K} for k, v in prof.items()}
 
     # end to end through the host API with pinned buffers
@@ -362,8 +686,7 @@ def ours_arm(args):
     e2e_value = units * world / (sum(e2e_t) / len(e2e_t))
     mn_bytes = prob.M * prob.N * 8
 
-    # the same evaluation replayed from a captured CUDA graph (per-slice path only; the timed
-    # region above uses plain launches so that every kernel carries its own events)
+    # the same evaluation replayed from a captured CUDA graph (per-slice path only)
     graph_replay = None
     if not args.graph and info["kernel_path"] == 0:
         cg = Context(precision, device=local, stream=stream.cuda_stream, ckpt_stride=args.ckpt_stride,
@@ -371,19 +694,7 @@ def ours_arm(args):
         cg.set_problem(prob)
         gg = torch.empty_like(u)
         og = torch.empty(6, dtype=torch.float64, device="cuda")
-        for _ in range(3):
-            cg.evaluate_device(u.data_ptr(), gg.data_ptr(), og.data_ptr())
-        cg.sync()
-        sg = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-        eg = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-        torch.cuda.synchronize()
-        for k in range(K):
-            flush.zero_()
-            sg[k].record(stream)
-            cg.evaluate_device(u.data_ptr(), gg.data_ptr(), og.data_ptr())
-            eg[k].record(stream)
-        torch.cuda.synchronize()
-        msg = sum(s.elapsed_time(e) for s, e in zip(sg, eg)) / K
+        msg = time_device_evals(cg, u, gg, og, K, 3, flush, stream)
         graph_replay = {"value": units / (msg / 1e3), "unit": UNIT, "ms_per_step": msg, "steps": K,
                         "identical_to_plain_launches": bool(torch.equal(gg, grad) and torch.equal(og, out))}
         cg.close()
@@ -397,20 +708,8 @@ def ours_arm(args):
         c64.set_problem(prob)
         g64 = torch.empty_like(u)
         o64 = torch.empty(6, dtype=torch.float64, device="cuda")
-        for _ in range(3):
-            c64.evaluate_device(u.data_ptr(), g64.data_ptr(), o64.data_ptr())
-        c64.sync()
         K64 = max(1, min(K, 5))
-        s64 = [torch.cuda.Event(enable_timing=True) for _ in range(K64)]
-        e64 = [torch.cuda.Event(enable_timing=True) for _ in range(K64)]
-        torch.cuda.synchronize()
-        for k in range(K64):
-            flush.zero_()
-            s64[k].record(stream)
-            c64.evaluate_device(u.data_ptr(), g64.data_ptr(), o64.data_ptr())
-            e64[k].record(stream)
-        torch.cuda.synchronize()
-        ms64 = sum(s.elapsed_time(e) for s, e in zip(s64, e64)) / K64
+        ms64 = time_device_evals(c64, u, g64, o64, K64, 3, flush, stream)
         i64 = c64.info()
         fp64_form = {"value": units / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64, "steps": K64,
                      "p": i64["p"], "n": i64["n"]}
@@ -423,11 +722,18 @@ def ours_arm(args):
         # the error reference: the whole workload where the oracle takes seconds, else the sample
         ref_n = prob.N if prob.d <= 81 else nsl
         try:
-            t, nsl, ref, nev = oracle_sample_time(args.workload, nsl, ref_slices=ref_n,
-                                                  exact=args.gradient == "exact", min_seconds=10.0)
-            cpu = {"value": nsl * prob.E / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": f"first {nsl} of {prob.N} slices of the same workload, FP64 oracle, 1 BLAS thread, "
-                             f"{nev} evaluations in {t * nev:.1f} s ({t:.2f} s each)"}
+            t, nsl, ref, nev, busy = oracle_sample_time(args.workload, nsl, ref_slices=ref_n,
+                                                        exact=args.gradient == "exact", min_seconds=10.0,
+                                                        threads=0)
+            t1, _, _, nev1, _ = oracle_sample_time(args.workload, nsl, min_seconds=5.0, threads=1)
+            cpu = {"value": nsl * prob.E / t, "unit": UNIT, "cores": busy, "kind": "oracle",
+                   "sample": f"first {nsl} of {prob.N} slices of the same workload, FP64 oracle, BLAS default "
+                             f"threads on {os.cpu_count()} host cores ({busy} threads gained CPU time), "
+                             f"{nev} evaluations in {t * nev:.1f} s ({t:.2f} s each)",
+                   "host_cores": os.cpu_count(),
+                   "one_thread": {"value": nsl * prob.E / t1, "unit": UNIT, "cores": 1,
+                                  "sample": f"the same sample with 1 BLAS thread, {nev1} evaluations in "
+                                            f"{t1 * nev1:.1f} s"}}
             if ref is not None:
                 if ref_n == prob.N:
                     c_gpu, g_gpu = float(out[0].item()), grad.cpu().numpy()
@@ -444,6 +750,10 @@ def ours_arm(args):
         except Exception as exc:   # keep the GPU line even if the CPU leg fails
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {exc}"}
 
+    per_config = None
+    if rank == 0 and world == 1 and not args.no_per_config:
+        per_config = per_config_lines(args, peaks, stream, flush)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
                 "warmup": max(args.warmup, 3), "ms_per_step": t_max, "higher_is_better": True,
@@ -451,8 +761,8 @@ def ours_arm(args):
                 "dtype": {"fp64": "f64", "fp32": "f32", "tf32": "tf32x3", "bf16": "bf16x3"}[precision],
                 "data": f"synthetic (seeded {prob.name} system, random controls)",
                 "config": config_of(prob, precision, info["ckpt_stride"],
-                                    {"p": p, "n": n, "wave_slices": info["wave_slices"], "n_waves": info["n_waves"],
-                                     "gradient": args.gradient, "graph": args.graph,
+                                    {"p": p_of(info), "n": info["n"], "wave_slices": info["wave_slices"],
+                                     "n_waves": info["n_waves"], "gradient": args.gradient, "graph": args.graph,
                                      "adjoint": {0: "reverse mode", 1: "block recursion", 2: "none (first-order)",
                                                  3: "low-rank reverse mode"}.get(
                                          info.get("adjoint_form"), "?")}),
@@ -461,10 +771,12 @@ def ours_arm(args):
                         "d2h_bytes_per_step": mn_bytes + 6 * 8 + 32},
                 "gpu_launches": info["launches_per_eval"] * K,
                 "clocks": clk.summary(), "kernels": kernels,
+                "peaks": peaks,
                 "graph_replay": graph_replay,
                 "fp64_form": fp64_form,
                 "speedup_vs_fp64_form": (value / fp64_form["value"]) if fp64_form else None,
                 "error_vs_oracle": error,
+                "per_config": per_config,
                 "cost": float(out[0].item())}
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -472,82 +784,34 @@ def ours_arm(args):
         dist.destroy_process_group()
 
 
+def p_of(info):
+    return info["p"]
+
+
 def batch_arm(args):
-    """The batched sweep: `count` problems of uneven d in {4, 8, 16, 40, 81, 128}, N in
-    [200, 4000], M in [2, 8], each with an `ensemble`-member detuning ensemble, FP32 form,
-    evaluated by one qoc_evaluate_batch call per step; compared with evaluating the same
-    contexts one after another.  Metric: sum_i N_i E_i / seconds per step."""
+    """The batched sweep alone (--workload batch): `count` problems of uneven d in
+    {4, 8, 16, 40, 81, 128}, N in [200, 4000], M in [2, 8], each with an `ensemble`-member
+    detuning ensemble, FP32 form, evaluated by one qoc_evaluate_batch call per step; compared
+    with evaluating the same contexts one after another.  Metric: sum_i N_i E_i / seconds per
+    step."""
     import torch
-    import synthetic as sy
-    from paper_1612_04929_gb300 import Context, build as qbuild, qoc_evaluate_batch
+    from paper_1612_04929_gb300 import build as qbuild
     qbuild.build()
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    probs = sy.batch_problems(args.count, ensemble=args.ensemble)
-    ctxs = []
-    for p in probs:
-        c = Context("fp32", profile=args.profile_batch)
-        c.set_problem(p)
-        ctxs.append(c)
-    us = [torch.tensor(p.u, dtype=torch.float64, device="cuda") for p in probs]
-    gs = [torch.empty_like(u) for u in us]
-    outs = [torch.empty(6, dtype=torch.float64, device="cuda") for _ in probs]
-    ptr = lambda ts: [t.data_ptr() for t in ts]
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-
-    def batch():
-        qoc_evaluate_batch(ctxs, ptr(us), ptr(gs), ptr(outs), stream.cuda_stream)
-
-    def one_by_one():
-        for c, u, g, o in zip(ctxs, us, gs, outs):
-            c.evaluate_device(u.data_ptr(), g.data_ptr(), o.data_ptr())
-            c.sync()
-
-    for _ in range(max(args.warmup, 1)):
-        batch()
-    torch.cuda.synchronize()
-    K = args.steps
-    ts = []
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
-        for _ in range(K):
-            flush.zero_()
-            torch.cuda.synchronize()
-            a = torch.cuda.Event(enable_timing=True)
-            e = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            batch()
-            e.record(stream)
-            torch.cuda.synchronize()
-            ts.append(a.elapsed_time(e))
-    ms = sum(ts) / len(ts)
-    by_d = {}
-    if args.profile_batch:     # per-kernel event time summed over the contexts (overlapping)
-        for c, p in zip(ctxs, probs):
-            for k, (n_l, t) in c.profile().items():
-                key = f"d{p.d}:{k}"
-                by_d[key] = by_d.get(key, 0.0) + t / K
-        for c in ctxs:
-            c.reset_profile()
-    one_by_one()
-    t0 = time.perf_counter()
-    for _ in range(max(1, min(K, 2))):
-        flush.zero_()
-        torch.cuda.synchronize()
-        one_by_one()
-    ms_seq = (time.perf_counter() - t0) * 1e3 / max(1, min(K, 2))
-    units = sum(p.N * p.E for p in probs)
-    line = {"metric": METRIC, "value": units / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": K,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        row = measure_batch(args.count, args.ensemble, args.steps, args.warmup, stream, flush,
+                            profile=args.profile_batch)
+    line = {"metric": METRIC, "value": row["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": row["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded batched sweep)",
-            "config": {"workload": f"batch{args.count}_E{args.ensemble}", "problems": args.count,
-                       "members": args.ensemble, "slice_steps_per_step": units,
-                       "d_counts": {str(d): sum(1 for p in probs if p.d == d) for d in sorted({p.d for p in probs})}},
-            "one_by_one_ms_per_step": ms_seq, "batch_speedup_vs_one_by_one": ms_seq / ms,
-            "kernel_ms_by_d": {k: round(v, 3) for k, v in sorted(by_d.items(), key=lambda kv: -kv[1])[:16]},
-            "clocks": clk.summary()}
+            "config": {"workload": row["workload"], "problems": args.count, "members": args.ensemble,
+                       "slice_steps_per_step": row["slice_steps_per_step"], "d_counts": row["d_counts"]},
+            "one_by_one_ms_per_step": row["one_by_one_ms_per_step"],
+            "batch_speedup_vs_one_by_one": row["batch_speedup_vs_one_by_one"],
+            "kernel_ms_by_d": row.get("kernel_ms_by_d"), "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
-    for c in ctxs:
-        c.close()
 
 
 def dsweep_arm(args):
@@ -604,7 +868,7 @@ def dsweep_arm(args):
             if not args.no_cpu_baseline:
                 ref_n = N if d <= 64 else 100
                 try:
-                    t, _, ref, _ = oracle_sample_time("dsweep", min(N, 50), ref_slices=ref_n,
+                    t, _, ref, _, _ = oracle_sample_time("dsweep", min(N, 50), ref_slices=ref_n,
                                                    maker=f"sy.dsweep_problem({d}, N=n)")
                     if ref_n == N:
                         c_gpu, g_gpu = c32, g32

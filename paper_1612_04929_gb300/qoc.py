@@ -33,7 +33,7 @@ ADJOINTS = {"auto": 0, "recompute": 1}
 ABI_SYMBOLS = ("qoc_default_options", "qoc_create", "qoc_destroy", "qoc_last_error", "qoc_status_string",
                "qoc_set_system", "qoc_set_targets", "qoc_set_ensemble", "qoc_evaluate_cost_and_grad",
                "qoc_evaluate_device", "qoc_sync", "qoc_get_info", "qoc_get_profile", "qoc_reset_profile",
-               "qoc_evaluate_static", "qoc_evaluate_batch")
+               "qoc_evaluate_static", "qoc_evaluate_batch", "qoc_measure_fma_peak")
 
 
 class QocError(RuntimeError):
@@ -110,6 +110,8 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     PP = ct.POINTER(ct.c_void_p)
     lib.qoc_evaluate_batch.argtypes = [I, PP, PP, PP, PP, VP]
     lib.qoc_evaluate_batch.restype = I
+    lib.qoc_measure_fma_peak.argtypes = [I, I, DP, ct.POINTER(ct.c_int)]
+    lib.qoc_measure_fma_peak.restype = I
     _lib = lib
     return lib
 
@@ -253,6 +255,17 @@ def qoc_evaluate_batch(ctxs, u_dev, grad_dev, out_dev, stream: int = 0) -> None:
     if st != QOC_OK:
         msgs = [load().qoc_last_error(c.handle if isinstance(c, Context) else c).decode() for c in ctxs]
         raise QocError(st, "; ".join(m for m in msgs if m))
+
+
+def qoc_measure_fma_peak(device: int = 0, fp64: bool = False):
+    """Measured FP32 (or FP64) multiply-add throughput of the device in TFLOP/s and its SM count
+    (see include/qoc.h)."""
+    t = ct.c_double(0.0)
+    n = ct.c_int(0)
+    st = load().qoc_measure_fma_peak(int(device), 1 if fp64 else 0, ct.byref(t), ct.byref(n))
+    if st != QOC_OK:
+        raise QocError(st, "qoc_measure_fma_peak failed")
+    return t.value, n.value
 
 
 # ------------------------------------------------------------------ convenience wrapper

@@ -43,11 +43,17 @@ def check(prob, precision, tol=None, **opt):
     assert np.max(np.abs(terms - t_ref) / np.maximum(np.abs(t_ref), 1.0)) <= tol, (terms, t_ref)
     if prob.M:
         assert rel(grad, g_ref) <= tol, rel(grad, g_ref)
-        # per component: within 10 tol of the component or within an absolute floor; the floor
-        # is tol ||g||_inf (FP64) and 2 tol ||g||_inf (FP32, whose adjoint rounding leaves a
-        # uniform absolute error on small components)
+        # per component: within 10 tol of the component or within an absolute floor.
+        # FP64: 1e-12 ||g||_inf (measured: at most 3.4e-14 over the parity cases).
+        # FP32 forms: the FP32 adjoint's rounding (of Ubar, of the stored operands, of the
+        # products) leaves an absolute error that is spread over the components rather than
+        # proportional to each; measured over the parity cases and workloads, the largest
+        # component error is 0.2 to 2.2 times the evaluation's own norm-wise relative error in
+        # units of ||g||_inf (transmon4 d = 81: 1.3e-5 against 7.8e-6; random d = 40, S = 40:
+        # 2.8e-6 against 1.3e-6).  So the floor is 3 times that norm-wise error (itself held to
+        # tol above), and an error concentrated on the small-gradient slices fails.
         ginf = np.max(np.abs(g_ref))
-        floor = (1.0 if precision == "fp64" else 2.0) * tol * ginf
+        floor = 1e-12 * ginf if precision == "fp64" else 3.0 * max(rel(grad, g_ref), 1e-7) * ginf
         diff = np.abs(grad - g_ref)
         assert np.all((diff <= 10 * tol * np.abs(g_ref)) | (diff <= floor)), float(np.max(diff / ginf))
     return cost, grad, terms, info
