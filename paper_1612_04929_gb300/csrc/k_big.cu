@@ -923,7 +923,7 @@ static cudaError_t rev_launch_t(int d, int items, const RevOps<C>& ops, C* O1, C
 template <typename R>
 cudaError_t launch_big_adj_rev(const BigArgs<R>& a, const SysView<R>& sys, const StateView<R>& sv, const C_t<R>* states,
                                const C_t<R>* Gbuf, double* gpart, int p, int n, const C_t<R>* zst, cudaStream_t st,
-                               int* launches) {
+                               int* launches, const OzRev* oz) {
     using C = C_t<R>;
     const int d = a.d, items = a.wlen * a.E, cap = p - 1 + n;
     const size_t dd = (size_t)d * d, ms = a.mstride, zs = (size_t)cap * ms;
@@ -946,9 +946,26 @@ cudaError_t launch_big_adj_rev(const BigArgs<R>& a, const SysView<R>& sys, const
     if ((err = cudaMemsetAsync(Xb, 0, (size_t)items * ms * sizeof(C), st)) != cudaSuccess) return err;
     const int T = (sizeof(C) == 16) ? 32 : big_tile(d);
     C *zb = Za, *zo = Zb;
+    // tensor-core products (BF16_SPLIT): X^dag is sliced once for the wave
+    int xh_sliced = 0;
+    OzRev tc{};
+    if (oz) {
+        tc = *oz;
+        tc.xh = reinterpret_cast<const float2*>(XH);
+        tc.xh_sliced = &xh_sliced;
+    }
     auto rev = [&](const RevOps<C>& ops, C* O2, int mode, int i) {
-        cudaError_t e2 = (T == 32) ? rev_launch_t<C, 32>(d, items, ops, zo, O2, ms, mode, i, st)
-                                   : rev_launch_t<C, 64>(d, items, ops, zo, O2, ms, mode, i, st);
+        cudaError_t e2;
+        if constexpr (sizeof(C) == 8) {
+            if (oz) {
+                const float2* o4[4] = {ops.p[0], ops.p[1], ops.p[2], ops.p[3]};
+                e2 = oz_rev_step(tc, o4, ops.s, zo, O2, ms, mode, i, st, launches);
+                std::swap(zb, zo);
+                return e2;
+            }
+        }
+        e2 = (T == 32) ? rev_launch_t<C, 32>(d, items, ops, zo, O2, ms, mode, i, st)
+                       : rev_launch_t<C, 64>(d, items, ops, zo, O2, ms, mode, i, st);
         count();
         std::swap(zb, zo);
         return e2;
@@ -975,10 +992,10 @@ template cudaError_t launch_big_expm<float>(const BigArgs<float>&, const DevPara
 template cudaError_t launch_big_expm<double>(const BigArgs<double>&, const DevParams&, bool, cudaStream_t, int*, double2*);
 template cudaError_t launch_big_adj_rev<float>(const BigArgs<float>&, const SysView<float>&, const StateView<float>&,
                                                const float2*, const float2*, double*, int, int, const float2*,
-                                               cudaStream_t, int*);
+                                               cudaStream_t, int*, const OzRev*);
 template cudaError_t launch_big_adj_rev<double>(const BigArgs<double>&, const SysView<double>&,
                                                 const StateView<double>&, const double2*, const double2*, double*, int,
-                                                int, const double2*, cudaStream_t, int*);
+                                                int, const double2*, cudaStream_t, int*, const OzRev*);
 template cudaError_t launch_big_adj<float>(const BigArgs<float>&, const SysView<float>&, const StateView<float>&,
                                            const float2*, const float2*, double*, int, int, cudaStream_t, int*);
 template cudaError_t launch_big_adj<double>(const BigArgs<double>&, const SysView<double>&, const StateView<double>&,

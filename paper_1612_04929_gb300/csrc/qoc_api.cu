@@ -387,9 +387,9 @@ void plan_impl(qoc_ctx* c) {
         c->scratch.release();
     }
     if (use_oz(c)) {
-        const size_t pbytes = (size_t)E * W * kOzMats * 8 * (size_t)d * oz_ld(d) * 2;
-        A(c->tc_planes, oz_scratch_bytes(d, E * W) + 512, "alloc tensor-core slices");
-        check_cuda(c, cudaMemsetAsync(c->tc_planes.p, 0, pbytes, st), "clear slices");
+        // the tensor maps cover exactly d x d of every plane (reads past d fill zeros), so the
+        // padding columns of the planes are never read and need no clearing
+        A(c->tc_planes, oz_scratch_bytes(d, E * W), "alloc tensor-core slices");
         check_cuda(c, oz_make_maps(c->tc_planes.p, d, E * W, &c->tc_maps), "tensor maps");
     } else if (use_tc(c)) {
         A(c->tc_planes, tc_scratch_floats(d, E * W) * sizeof(float), "alloc tensor-core planes");
@@ -529,7 +529,7 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
     // the free device memory); else the block recursion, which stores nothing
     bool big_rev = false;
     size_t zbig_set = 0;
-    if (big && c->opt.gradient == QOC_GRAD_EXACT && c->opt.adjoint == QOC_ADJ_AUTO && !use_tc(c) && !use_oz(c)) {
+    if (big && c->opt.gradient == QOC_GRAD_EXACT && c->opt.adjoint == QOC_ADJ_AUTO && !use_tc(c)) {
         zbig_set = (size_t)E * W * (size_t)(hp.p - 1 + hp.n) * c->mstride;
         const size_t need = 2 * zbig_set * sizeof(C);
         if (c->Zbig.bytes >= need) {
@@ -578,12 +578,12 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
         if (c->opt.gradient == QOC_GRAD_FIRST_ORDER)
             return launch_grad_first_order<R>(sys, sv, j0, wlen, E, Sb(w), Gb(w), W, c->dt, c->gpart.as<double>(), st);
         if constexpr (sizeof(R) == 4) {
-            if (big && use_oz(c)) {
+            if (big && use_oz(c) && big_rev) {   // reverse mode, products on the tensor cores
                 int n_l = 0;
-                OzAdjArgs oa{c->opt.fault_inject, prm, sys, sv, d, E, j0, wlen, W, hp.p, hp.n, Sb(w), Gb(w),
-                             c->tc_planes.as<unsigned char>(),
-                             c->tc_maps, c->gpart.as<double>()};
-                cudaError_t e = launch_oz_adj(oa, st, &n_l);
+                OzRev oz{c->opt.fault_inject, prm, d, E * wlen, E * W, c->tc_planes.as<unsigned char>(), c->tc_maps,
+                         nullptr, nullptr};
+                cudaError_t e = launch_big_adj_rev<R>(big_args(w), sys, sv, Sb(w), Gb(w), c->gpart.as<double>(), hp.p,
+                                                      hp.n, zbig(w), st, &n_l, &oz);
                 extra += n_l - 1;
                 return e;
             }

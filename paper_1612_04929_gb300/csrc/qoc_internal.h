@@ -168,10 +168,12 @@ inline size_t big_scratch_per_item(int d, bool fp64) {
 template <typename R>
 cudaError_t launch_big_expm(const BigArgs<R>& a, const DevParams& hp, bool split, cudaStream_t st, int* launches,
                             C_t<R>* zst = nullptr);
+struct OzRev;
+// oz (FP32 form only, or nullptr): run the reverse-mode products on the tensor cores (BF16_SPLIT)
 template <typename R>
 cudaError_t launch_big_adj_rev(const BigArgs<R>& a, const SysView<R>& sys, const StateView<R>& sv, const C_t<R>* states,
                                const C_t<R>* Gbuf, double* gpart, int p, int n, const C_t<R>* zst, cudaStream_t st,
-                               int* launches);
+                               int* launches, const OzRev* oz = nullptr);
 template <typename R>
 cudaError_t launch_big_adj(const BigArgs<R>& a, const SysView<R>& sys, const StateView<R>& sv, const C_t<R>* states,
                            const C_t<R>* Gbuf, double* gpart, int p, int n, cudaStream_t st, int* launches);
@@ -209,37 +211,49 @@ size_t tc_scratch_floats(int d, int items);
 cudaError_t tc_make_maps(float* planes, int d, int items, TcMaps* maps);
 cudaError_t launch_tc_adj(const TcAdjArgs& a, cudaStream_t st, int* launches);
 
-// ---- tensor-core adjoint products with exact accumulation, BF16_SPLIT form (k_oz.cu) ----
-constexpr int kOzMats = 10;   // sliced matrices: XH, Ubar (row), two sets of Z11 / Z12 (row, col)
-constexpr int kOzVals = 6;    // FP32 values: XH, Ubar, Z11 (two sets), Z12 (two sets)
+// ---- tensor-core adjoint products with exact leading-level accumulation, BF16_SPLIT (k_oz.cu) ----
+constexpr int kOzSlices = 4;  // seven-bit slices per value
+constexpr int kOzMats = 5;    // sliced matrices per item: A1, B1, A2, B2 of a reverse step, X^dag
 inline int oz_ld(int d) { return (d + 7) / 8 * 8; }   // plane row stride (BF16): 16-byte rows for TMA
-struct OzSliceJob { int val, mat, col; };
-struct OzSliceJobs { OzSliceJob job[6]; };
-struct OzTerm { int a_mat, b_mat; };
-struct OzOut {
-    int nterms, val, identity;
-    OzTerm t[2];
+struct OzSliceJob {
+    const float2* src;      // d x d row-major FP32 complex matrices, item i at src + i * stride
+    size_t stride;
+    int mat;                // plane matrix to write
+    int col;                // 0: row layout (A operand), 1: column layout (B operand)
 };
-struct OzStep {
-    int kind, i;            // 0: Horner step i, 1: squaring
-    OzOut o[2];             // Z11', Z12'
+struct OzSliceJobs { OzSliceJob job[4]; };
+struct OzJob {              // out = alpha A B (+ out if beta) (+ I if ident), per item
+    int a_mat, b_mat;
+    float2* out;
+    long long ostride;
+    float alpha;
+    int beta, ident;
+};
+struct OzJobs {
+    OzJob j[2];
     int fault;              // withhold the first operand copy (test of the bounded wait)
 };
-struct OzAdjArgs {
+// the reverse-mode adjoint's products on the tensor cores: state of one wave
+struct OzRev {
     int fault;              // qoc_options.fault_inject
     DevParams* prm;
-    SysView<float> sys;
-    StateView<float> sv;
-    int d, E, j0, wlen, wmax, p, n;
-    const float2* states;
-    const float2* Gbuf;
-    unsigned char* scratch; // oz_scratch_bytes(d, items)
-    TcMaps maps;
-    double* gpart;
+    int d, items, cap;      // items of this wave; items the plane array holds
+    unsigned char* scratch; // oz_scratch_bytes(d, cap): planes, then exponents
+    TcMaps maps;            // oz_make_maps over the planes
+    const float2* xh;       // X^dag of the wave (sliced once, into matrix 4)
+    int* xh_sliced;         // host flag: X^dag already sliced for this wave
 };
+size_t oz_plane_bytes(int d, int items);
 size_t oz_scratch_bytes(int d, int items);
 cudaError_t oz_make_maps(void* planes, int d, int items, TcMaps* maps);
-cudaError_t launch_oz_adj(const OzAdjArgs& a, cudaStream_t st, int* launches);
+cudaError_t launch_oz_slice(const OzSliceJobs& jobs, int njobs, int d, int items, int cap, unsigned char* scratch,
+                            cudaStream_t st);
+cudaError_t launch_oz_mm(const OzJobs& jobs, int njobs, int d, int items, int cap, unsigned char* scratch,
+                         const TcMaps& maps, DevParams* prm, cudaStream_t st);
+// one reverse-mode step (the products of k_big_rev): mode 0 (Horner step i) O1 = A1 B1 / i and
+// O2 += A2 B2 / i; mode 1 (squaring) O1 = A1 B1 + A2 B2; ops = {A1, B1, A2, B2} with item strides
+cudaError_t oz_rev_step(const OzRev& z, const float2* const ops[4], const size_t strides[4], float2* O1, float2* O2,
+                        size_t ms, int mode, int i, cudaStream_t st, int* launches);
 
 // ---- serial sweeps (k_serial.cu) ----
 // mode 0: forward propagation of one wave (grid z = 1) from checkpoint `seg0`, storing the
