@@ -27,7 +27,7 @@
 // of B for a 16-wide K chunk, SWIZZLE_32B, 64 KB), warp 1 issues the tcgen05.mma (kind::f16,
 // BF16 in, FP32 accumulators in tensor memory: leading re, leading im, rest re, rest im, 128
 // columns each) and commits each stage back to the producer, warps 2-5 read tensor memory with
-// tcgen05.ld and write the result.  Every mbarrier wait is bounded; a wait that runs out sets
+// tcgen05.ld, stage the scaled tile in the idle ring and write it with coalesced stores.  Every mbarrier wait is bounded; a wait that runs out sets
 // kErrTimeout in DevParams.err and the CTA stops issuing, waits (bounded) for its copies in
 // flight, frees its tensor memory and returns.
 #include <cuda.h>
@@ -345,35 +345,63 @@ k_oz_mm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtens
     const bool go = __syncthreads_and(fin && s_ok != 0) != 0;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (go && warp >= 2) {
-        const int q4 = warp & 3;                       // the TMEM lane quarter this warp may read
+        // Each epilogue warp owns 32 tile rows (the TMEM lane quarter it may read).  It scales
+        // its rows into a staging area of the idle stage ring (every copy has landed and every
+        // MMA has read its operands once `done` completed), then writes them row by row with
+        // the lanes along the columns, so the global stores (and the reads of beta) coalesce.
+        constexpr int SROW = BN + 1;                   // padded row: fewer bank conflicts
+        const int q4 = warp & 3;
         const int r = r0 + q4 * 32 + lane;
+        const int ncols = min(BN, d - c0);
         const int eA = r < d ? exps[((size_t)item * kOzMats + jb.a_mat) * d + r] : 0;
         const int* eBp = exps + ((size_t)item * kOzMats + jb.b_mat) * d;
-        float2* out = jb.out + (size_t)item * jb.ostride;
+        float2* stg = reinterpret_cast<float2*>(base) + (size_t)(warp - 2) * 32 * SROW;
         const uint32_t lane_base = tmem + ((uint32_t)(q4 * 32) << 16);
-        for (int cc = 0; cc < BN && c0 + cc < d; cc += 16) {
+        for (int cc = 0; cc < ncols; cc += 16) {
             float lr[16], li[16], rr[16], ri[16];
             tmem_ld16(lane_base + (uint32_t)cc, lr);
             tmem_ld16(lane_base + (uint32_t)(BN + cc), li);
             tmem_ld16(lane_base + (uint32_t)(2 * BN + cc), rr);
             tmem_ld16(lane_base + (uint32_t)(3 * BN + cc), ri);
-            if (r < d) {
 #pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const int c = c0 + cc + q;
-                    if (c >= d) break;
-                    const float sc = ldexpf(jb.alpha, eA + eBp[c] - 3 * SBITS);
-                    float re = (lr[q] + rr[q]) * sc, im = (li[q] + ri[q]) * sc;
-                    float2* o = out + (size_t)r * d + c;
-                    if (jb.beta) {
-                        const float2 old = *o;
-                        re += old.x;
-                        im += old.y;
-                    }
-                    if (jb.ident && r == c) re += 1.0f;
-                    *o = make_float2(re, im);
-                }
+            for (int q = 0; q < 16; ++q) {
+                const int c = c0 + cc + q;
+                const float sc = ldexpf(jb.alpha, eA + (c < d ? eBp[c] : 0) - 3 * SBITS);
+                stg[lane * SROW + cc + q] = make_float2((lr[q] + rr[q]) * sc, (li[q] + ri[q]) * sc);
             }
+        }
+        __syncwarp();
+        // eight rows at a time, each lane four columns (c = lane + 32 j): the 32 reads of the
+        // accumulated output (beta) are in flight together
+        float2* out = jb.out + (size_t)item * jb.ostride;
+        const int nrows = min(32, d - (r0 + q4 * 32));
+        for (int rw0 = 0; rw0 < nrows; rw0 += 8) {
+            float2 old[8][BN / 32];
+            if (jb.beta) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+#pragma unroll
+                    for (int j = 0; j < BN / 32; ++j) {
+                        const int rw = rw0 + u, c = lane + 32 * j;
+                        old[u][j] = (rw < nrows && c < ncols) ? out[(size_t)(r0 + q4 * 32 + rw) * d + c0 + c]
+                                                              : make_float2(0.f, 0.f);
+                    }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+#pragma unroll
+                for (int j = 0; j < BN / 32; ++j) {
+                    const int rw = rw0 + u, c = lane + 32 * j;
+                    if (rw >= nrows || c >= ncols) continue;
+                    const int row = r0 + q4 * 32 + rw;
+                    float2 v = stg[rw * SROW + c];
+                    if (jb.beta) {
+                        v.x += old[u][j].x;
+                        v.y += old[u][j].y;
+                    }
+                    if (jb.ident && row == c0 + c) v.x += 1.0f;
+                    out[(size_t)row * d + c0 + c] = v;
+                }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
