@@ -121,11 +121,38 @@ typedef struct qoc_options {
                              out; later kernels of the evaluation skip their work, the evaluation
                              reports QOC_ERR_TIMEOUT and the context and device stay usable.
                              Nothing faults or hangs. */
+    int reversal;         /* 0 (default): the backward pass regenerates the states Psi_j from
+                             checkpoints (every ckpt_stride slices); 1: by reversal, Psi_{j-1} =
+                             U_j^dag Psi_j from the last state of each wave backwards (the paper's
+                             Algorithms 1-3, Appendix A), with checkpoints only at wave boundaries
+                             and no parallel segment replay.  FP64 form only (QOC_ERR_UNSUPPORTED
+                             otherwise): in FP32 the rounding of the stored U_j would accumulate
+                             over the backward pass. */
+    int propagation;      /* QOC_PROP_UNITARY (0, default): each slice propagator U_j is formed
+                             (Taylor + squaring matrix products) and applied to the block;
+                             QOC_PROP_STATE (1): state mode (Sec. IV, Eq. 12), the truncated series
+                             is applied to the propagated columns by Horner matrix-vector products,
+                             T_p(X_j)^(2^n) Psi, without forming U_j: O(p 2^n d^2 S) per slice
+                             instead of O((p + n) d^3).  The same truncated map, so the same exact
+                             gradient (adjoint_form 4).  At most 8 weighted columns (S); one CTA
+                             per (column panel, member) runs the serial recursion, so it pays for
+                             few columns with many ensemble members or large d. */
+    int exponential;      /* QOC_EXP_TAYLOR (0, default): the truncated Taylor series with scaling
+                             and squaring (Sec. III, Eqs. 9, 10); QOC_EXP_CHEBYSHEV (1): the
+                             Chebyshev expansion of exp(-i dt H_j) (the Jacobi-Anger series in
+                             T_k(dt H_j / theta), theta the FP64 bound of dt ||H_j||) with no
+                             scaling, its degree the least whose tail bound is below tol; about
+                             theta + O(log 1/tol) matrix-vector products per slice instead of
+                             p 2^n.  State mode only (QOC_ERR_UNSUPPORTED otherwise); the gradient is
+                             the exact derivative of that polynomial map; qoc_info.p reports the
+                             degree.  QOC_ERR_RANGE if the degree would exceed 96. */
 } qoc_options;
 
 enum { QOC_SWEEP_AUTO = 0, QOC_SWEEP_SERIAL = 1, QOC_SWEEP_SCAN = 2 };
 enum { QOC_GRAD_EXACT = 0, QOC_GRAD_FIRST_ORDER = 1 };
 enum { QOC_ADJ_AUTO = 0, QOC_ADJ_RECOMPUTE = 1 };
+enum { QOC_PROP_UNITARY = 0, QOC_PROP_STATE = 1 };
+enum { QOC_EXP_TAYLOR = 0, QOC_EXP_CHEBYSHEV = 1 };
 
 /* Information about the last evaluation (reading it synchronises the context stream). */
 typedef struct qoc_info {
@@ -135,12 +162,14 @@ typedef struct qoc_info {
     int wave_slices;      /* slices per parallel launch (multiple of ckpt_stride) */
     int n_waves;          /* number of waves */
     int launches_per_eval;/* kernels launched by one evaluation */
-    int kernel_path;      /* 0: fused per-slice kernels (small d); 1: batched tiled GEMM (large d) */
+    int kernel_path;      /* 0: fused per-slice kernels (small d); 1: batched tiled GEMM (large d);
+                             2: state mode (matrix-vector Horner chains) */
     long long device_bytes; /* device memory held by the context */
     int adjoint_form;     /* gradient of the last evaluation: 0 reverse mode over the stored products
                              (2 products per forward product), 1 block recursion (3), 2 first-order
                              (Eq. 11, no adjoint exponential), 3 low-rank reverse mode (the cotangent
-                             kept as d x r factors, r = 2^n S; small S, per-slice kernels) */
+                             kept as d x r factors, r = 2^n S; small S, per-slice kernels), 4 the
+                             state mode's reverse pass over its matrix-vector chain */
 } qoc_info;
 
 /* Per-kernel timings gathered while qoc_options.profile is set: for each kernel class the number

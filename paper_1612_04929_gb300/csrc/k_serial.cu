@@ -21,7 +21,9 @@
 // Checkpointing: the forward sweep stores the carried block every `seg` slices (seg = ceil(sqrt
 // N) by default).  In the backward sweep the states of a wave are regenerated from those
 // checkpoints, one CTA per checkpoint segment in parallel (mode 1 below), so regeneration
-// costs seg serial steps whatever the wave length.
+// costs seg serial steps whatever the wave length.  Reversal (mode 2, the paper's Algorithms
+// 1-3): the states of a wave are regenerated backwards from its last state,
+// Psi_{j-1} = U_j^dag Psi_j, with no checkpoint inside the evolution.
 #include "qoc_device.cuh"
 #include "qoc_internal.h"
 
@@ -247,7 +249,7 @@ template <typename R, int RING, typename Mt, int NCB>
 __global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 1024)
 k_chain(int d, StateView<R> sv, int wlen, int seg, int mode, K_t<R>* __restrict__ ckpt, size_t ck_estride, int seg0,
         int nseg_total, const Mt* __restrict__ Ubuf, long long ustride, int wmax, C_t<R>* __restrict__ states,
-        int g, const DevParams* __restrict__ prm) {
+        int g, const DevParams* __restrict__ prm, const C_t<R>* __restrict__ rev_src, size_t rev_estride) {
     using C = C_t<R>;
     using K = K_t<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -259,8 +261,11 @@ k_chain(int d, StateView<R> sv, int wlen, int seg, int mode, K_t<R>* __restrict_
     K* xb = xa + panel;
     float4* xg = reinterpret_cast<float4*>(xb + panel);   // FP32: grid-split block of the step
     __shared__ unsigned smax[2];                           // FP32: largest component, by step parity
-    const int t0 = (mode == 0) ? 0 : z * seg;
-    const int t1 = (mode == 0) ? wlen : min(wlen, t0 + seg);
+    // mode 2 (reversal): the whole wave backwards from its last state, step k applying
+    // U_{t}^dag with t = wlen - 1 - k and writing state t
+    const bool rev = mode == 2;
+    const int t0 = (mode == 1) ? z * seg : 0;
+    const int t1 = (mode == 1) ? min(wlen, t0 + seg) : wlen;
     if (t0 >= t1) return;
     if (tid == 0) smax[0] = smax[1] = 0u;
     __syncthreads();
@@ -270,11 +275,12 @@ k_chain(int d, StateView<R> sv, int wlen, int seg, int mode, K_t<R>* __restrict_
     // the first state of a replayed segment z > 0 is the last state of segment z - 1, which that
     // segment's CTA writes: one writer per state (the checkpoint and the stepped value differ in
     // their last bits)
-    const bool own_first = (mode == 0 || z == 0);
+    const bool own_first = (mode != 1 || z == 0);
+    const C* rsrc = rev ? rev_src + (size_t)e * rev_estride + (size_t)kb * sv.pstride : nullptr;
     for (int i = tid; i < (int)panel; i += blockDim.x) {
-        const K v = s0[i];
+        const K v = rev ? kfrom(rsrc[i]) : s0[i];
         xa[i] = v;
-        if (own_first) sdst[(size_t)t0 * slice + i] = kround(v);
+        if (own_first) sdst[(size_t)(rev ? wlen : t0) * slice + i] = kround(v);
         if constexpr (sizeof(R) == 4) atomicMax(&smax[0], pair_maxbits(v));
     }
     float mu = 0.f;
@@ -293,9 +299,13 @@ k_chain(int d, StateView<R> sv, int wlen, int seg, int mode, K_t<R>* __restrict_
         }
         K* tmp = xa; xa = xb; xb = tmp;
     };
+    // propagator of step t (forward: U_t; reversal: U_{wlen-1-t}^dag) and the state it writes
     const Mt* Ue = Ubuf + (size_t)e * wmax * ustride;
+    auto mat = [&](int t) {
+        return rev ? Ue + (size_t)(wlen - 1 - t) * ustride + ustride / 2 : Ue + (size_t)t * ustride;
+    };
     auto emit_for = [&](int t) {
-        C* dst = sdst + (size_t)(t + 1) * slice;
+        C* dst = sdst + (size_t)(rev ? wlen - 1 - t : t + 1) * slice;
         K* ckd = nullptr;
         if (mode == 0 && (t + 1) % seg == 0 && seg0 + (t + 1) / seg < nseg_total)
             ckd = ck_e + (size_t)(seg0 + (t + 1) / seg) * slice + (size_t)kb * sv.pstride;
@@ -308,13 +318,13 @@ k_chain(int d, StateView<R> sv, int wlen, int seg, int mode, K_t<R>* __restrict_
 #pragma unroll 1
         for (int t = t0; t < t1; ++t) {
             __syncthreads();
-            step(Ue + (size_t)t * ustride, t - t0, emit_for(t));
+            step(mat(t), t - t0, emit_for(t));
         }
     } else if constexpr (RING == 1) {   // one slot: synchronous copy
 #pragma unroll 1
         for (int t = t0; t < t1; ++t) {
             __syncthreads();            // previous step done with the slot
-            ring_issue(ring, Ue + (size_t)t * ustride, ub);
+            ring_issue(ring, mat(t), ub);
             cp_async_commit();
             cp_async_wait<0>();
             __syncthreads();
@@ -323,7 +333,7 @@ k_chain(int d, StateView<R> sv, int wlen, int seg, int mode, K_t<R>* __restrict_
     } else {
 #pragma unroll 1
         for (int t = 0; t < RING - 1; ++t) {
-            if (t0 + t < t1) ring_issue(ring + t * ub, Ue + (size_t)(t0 + t) * ustride, ub);
+            if (t0 + t < t1) ring_issue(ring + t * ub, mat(t0 + t), ub);
             cp_async_commit();
         }
 #pragma unroll 1
@@ -332,7 +342,7 @@ k_chain(int d, StateView<R> sv, int wlen, int seg, int mode, K_t<R>* __restrict_
             cp_async_wait<(RING >= 2 ? RING - 2 : 0)>();   // the copy of step k has landed ...
             __syncthreads();                                // ... for every thread; step k - 1 is finished
             const int tn = t + RING - 1;
-            if (tn < t1) ring_issue(ring + ((k + RING - 1) % RING) * ub, Ue + (size_t)tn * ustride, ub);
+            if (tn < t1) ring_issue(ring + ((k + RING - 1) % RING) * ub, mat(tn), ub);
             cp_async_commit();
             step(reinterpret_cast<const Mt*>(ring + (k % RING) * ub), k, emit_for(t));
         }
@@ -349,7 +359,7 @@ static cudaError_t chain_ring_n(const ChainArgs<R>& a, const Mt* U, size_t smem,
     const int nz = a.mode == 0 ? 1 : (a.wlen + a.seg - 1) / a.seg;
     k_chain<R, RING, Mt, NCB><<<dim3(a.sv.ncb, a.E, nz), threads, smem, st>>>(
         a.d, a.sv, a.wlen, a.seg, a.mode, a.ckpt, a.ck_estride, a.seg0, a.nseg_total, U, a.ustride, a.wmax, a.states,
-        g, a.prm);
+        g, a.prm, a.rev_src, a.rev_estride);
     return cudaGetLastError();
 }
 
@@ -379,6 +389,7 @@ static cudaError_t chain_dispatch(const ChainArgs<R>& a, const Mt* U, cudaStream
 template <typename R>
 cudaError_t launch_chain(const ChainArgs<R>& a, cudaStream_t st) {
     if ((a.Ubuf != nullptr) == (a.Uk != nullptr)) return cudaErrorInvalidValue;
+    if (a.mode == 2 && (!a.rev_src || !a.Ubuf)) return cudaErrorInvalidValue;
     if (a.Uk) return chain_dispatch<R, K_t<R>>(a, a.Uk, st);
     return chain_dispatch<R, C_t<R>>(a, a.Ubuf, st);
 }

@@ -148,6 +148,9 @@ struct qoc_ctx {
     DevBuf H64, HR, dDelta, norms, psiTR, pathR, fmask, colw, ckpt, Ubuf, states, Gbuf, src, carry, Oj, C5j, Ofin,
         gpart, prm, u_h, grad_h, out_h, scratch, tc_planes;
     DevBuf sH;                           // s H_0 .. s H_det as FP32 pairs (per-slice split exponential)
+    DevBuf chebd;                        // Chebyshev coefficients of the evaluation (state mode)
+    DevBuf stscr;                        // state mode: the gradient kernel's per-item scratch
+    ChebCoef cheb_host{};                // their host copy (kept alive for the asynchronous copy)
     // segmented scan: segment products (two wave sets), tree levels, scan states, costate carries
     DevBuf Pbuf, lv0, lv1, scanst, hbuf, Ybuf;
     DevBuf Zbuf;                         // product operands for the reverse-mode adjoint (per-slice path)
@@ -166,7 +169,7 @@ struct qoc_ctx {
     size_t device_bytes() const {
         const DevBuf* all[] = {&H64, &HR, &dDelta, &norms, &psiTR, &pathR, &fmask, &colw, &ckpt, &Ubuf, &states,
                                &Gbuf, &src, &carry, &Oj, &C5j, &Ofin, &gpart, &prm, &u_h, &grad_h, &out_h, &scratch,
-                               &tc_planes, &Pbuf, &lv0, &lv1, &scanst, &hbuf, &Ybuf, &Zbuf, &Zbig, &sH};
+                               &tc_planes, &Pbuf, &lv0, &lv1, &scanst, &hbuf, &Ybuf, &Zbuf, &Zbig, &sH, &chebd, &stscr};
         size_t s = 0;
         for (auto* b : all) s += b->bytes;
         return s;
@@ -227,6 +230,8 @@ void plan_impl(qoc_ctx* c) {
     const size_t cs = sizeof(C);
     const int dmax = split_exp<R>(c) ? std::min(fused_max_d<R>(), split_max_d()) : fused_max_d<R>();
     c->path_kind = (d <= dmax) ? 0 : 1;   // 0: per-slice fused kernels, 1: batched tiled GEMMs
+    const bool state_mode = c->opt.propagation == QOC_PROP_STATE;
+    if (state_mode) c->path_kind = 2;     // 2: state mode (Taylor on the propagated columns)
     // default theta_max of the FP32 forms: 0.5 with the per-slice kernels (split squarings: one
     // split product fewer than 1.0 on long evolutions); 1.0 on the batched path, whose plain
     // FP32 adjoint loses accuracy with every extra squaring
@@ -238,10 +243,17 @@ void plan_impl(qoc_ctx* c) {
         if (c->w[s] > 0.0) c->cols.push_back(s);
     const int S = (int)c->cols.size();
     c->S_eff = S;
+    if (state_mode && S > kStateMaxColumns)
+        throw Fail{set_err(c, QOC_ERR_UNSUPPORTED, "state mode propagates at most 8 weighted columns")};
     // checkpoint stride (sqrt N by default) and the form of the recursions
-    int seg = c->opt.ckpt_stride > 0 ? c->opt.ckpt_stride : (int)std::ceil(std::sqrt((double)N));
+    // Reversal (the paper's Algorithms 1-3): no checkpoint inside a wave; the wave size is chosen
+    // freely (stride 1 below), then the stride becomes the wave, so the forward pass hands its
+    // carried block from wave to wave and the backward pass regenerates each wave's states from
+    // the next wave's first state by Psi_{j-1} = U_j^dag Psi_j.
+    const bool rev = c->opt.reversal != 0 || state_mode;
+    int seg = rev ? 1 : (c->opt.ckpt_stride > 0 ? c->opt.ckpt_stride : (int)std::ceil(std::sqrt((double)N)));
     seg = std::max(1, std::min(seg, N));
-    c->scan = c->opt.sweep == QOC_SWEEP_SCAN || (c->opt.sweep == QOC_SWEEP_AUTO && seg >= 4);
+    c->scan = !rev && (c->opt.sweep == QOC_SWEEP_SCAN || (c->opt.sweep == QOC_SWEEP_AUTO && seg >= 4));
     // column panel width: a sweep CTA owns one panel of one member (and, in the segmented form,
     // one segment); wide panels read each U_j once for more columns, narrow ones spread the work
     // over more SMs: about two sweep CTAs per SM, up to 8 columns per panel.  The segments of a
@@ -308,6 +320,16 @@ void plan_impl(qoc_ctx* c) {
         }
     }
     W = std::max(seg, std::min(W, ((N + seg - 1) / seg) * seg));
+    if (state_mode && c->opt.wave_slices <= 0) {
+        // state mode holds X_j (one d x d matrix of pairs per slice and member) for a wave: the
+        // whole evolution when it fits 1/8 of the free memory (1..32 GiB), else the largest wave
+        const size_t per = (size_t)E * (2 * (size_t)c->ustride * cs + 3 * slice * cs);
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = (size_t)8 << 30;
+        const size_t budget = std::min<size_t>((size_t)32 << 30, std::max<size_t>((size_t)1 << 30, free_b / 8));
+        W = (int)std::max<size_t>(1, std::min<size_t>((size_t)N, budget / std::max<size_t>(per, 1)));
+    }
+    if (rev) seg = W;
     c->seg = seg;
     c->W = W;
     c->nw = (N + W - 1) / W;
@@ -323,7 +345,7 @@ void plan_impl(qoc_ctx* c) {
     const size_t dd = (size_t)d * d;
     A(c->HR, (M + 2) * dd * cs, "alloc H");
     check_cuda(c, launch_convert<R>(c->H64.as<double2>(), c->HR.as<C>(), (M + 2) * dd, st), "convert H");
-    if (split_exp<R>(c)) A(c->sH, (M + 2) * dd * sizeof(float4), "alloc sH");
+    if (split_exp<R>(c) || (c->path_kind == 2 && sizeof(R) == 4)) A(c->sH, (M + 2) * dd * sizeof(float4), "alloc sH");
     else c->sH.release();
     // costs
     std::vector<int> mask(d, 0);
@@ -684,8 +706,16 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
                 if (w - 1 != nw - 2) {                       // wave nw - 2 is still resident
                     B(st);
                     L(expm_fwd(w - 1), "expm_fwd (recompute)", st);
-                    B(st);
-                    L(launch_chain<R>(chain_args(w - 1, 1), st), "chain (replay)", st);
+                    if (c->opt.reversal) {                   // backwards from wave w's first state
+                        ChainArgs<R> ra = chain_args(w - 1, 2);
+                        ra.rev_src = Sb(w);
+                        ra.rev_estride = (size_t)(W + 1) * slice;
+                        B(st);
+                        L(launch_chain<R>(ra, st), "chain (reversal)", st);
+                    } else {
+                        B(st);
+                        L(launch_chain<R>(chain_args(w - 1, 1), st), "chain (replay)", st);
+                    }
                 }
                 rec(ev_rep[w - 1], st);
             }
@@ -804,8 +834,190 @@ void plan(qoc_ctx* c) {
     else plan_impl<float>(c);
 }
 
+// Chebyshev expansion of exp(-i theta x) on [-1, 1] (the Jacobi-Anger expansion): coefficients
+// a_0 = J_0(theta), a_k = 2 J_k(theta) of (-i)^k T_k(x), the degree K the least with the tail
+// bound 2 sum_{k > K} |J_k(theta)| <= 2 (theta/2)^(K+1) / (K+1)! / (1 - theta / (2 (K+2))) <= tol
+// (|J_k(t)| <= (t/2)^k / k!).  The Bessel values by the downward (Miller) recurrence
+// J_{k-1} = (2k / theta) J_k - J_{k+1} from a start far above K, normalised by
+// J_0 + 2 sum_{k >= 1} J_{2k} = 1.  Returns false when K would exceed kChebMax.
+bool chebyshev_coefficients(double theta, double tol, ChebCoef& cc) {
+    cc = ChebCoef{};
+    if (!(theta > 1e-300)) {                 // zero Hamiltonian: exp = I
+        cc.K = 0;
+        cc.a[0] = 1.0;
+        cc.inv_theta = 0.0;
+        return true;
+    }
+    int K = 1;
+    for (;;) {
+        const double h = 0.5 * theta;
+        double t = 2.0;
+        for (int k = 1; k <= K + 1; ++k) t *= h / k;       // 2 (theta/2)^(K+1) / (K+1)!
+        if (h < K + 2 && t / (1.0 - h / (K + 2)) <= tol) break;
+        if (++K > kChebMax) return false;
+    }
+    const int m = K + 40 + 2 * (int)theta;
+    std::vector<double> J(m + 2, 0.0);
+    J[m + 1] = 0.0;
+    J[m] = 1e-30;
+    for (int k = m; k >= 1; --k) {
+        J[k - 1] = (2.0 * k / theta) * J[k] - J[k + 1];
+        if (std::fabs(J[k - 1]) > 1e250)
+            for (int q = k - 1; q <= m; ++q) J[q] *= 1e-250;
+    }
+    double norm = J[0];
+    for (int k = 2; k <= m; k += 2) norm += 2.0 * J[k];
+    cc.K = K;
+    cc.inv_theta = 1.0 / theta;
+    cc.a[0] = J[0] / norm;
+    for (int k = 1; k <= K; ++k) cc.a[k] = 2.0 * J[k] / norm;
+    return true;
+}
+
+// State mode (the paper's Eq. 12): per wave, X_j for the wave's slices, the forward recursion of
+// the propagated columns by Horner matrix-vector products, the per-slice costs; backwards, per
+// wave, X_j and the states again (from the wave's checkpoint) unless resident, the sources, the
+// costate recursion (the adjoint of the same map), and the exact gradient of every slice's map
+// in parallel.  One stream; (p, n) is read back once to size the gradient kernel.
+template <typename R>
+void evaluate_state_impl(qoc_ctx* c, const double* u, double* grad, double* out) {
+    using C = C_t<R>;
+    using K = K_t<R>;
+    const int d = c->d, N = c->N, E = c->E, M = c->M, W = c->W, nw = c->nw;
+    cudaStream_t st = c->stream;
+    StateView<R> sv{c->Spad, c->cb, c->ncb, c->pstride, c->S_eff};
+    const size_t slice = sv.slice(), dd = (size_t)d * d;
+    C* HR = c->HR.as<C>();
+    SysView<R> sys{d, M, N, HR, HR + dd, c->Hdet.empty() ? nullptr : HR + (size_t)(M + 1) * dd,
+                   c->delta.empty() ? nullptr : c->dDelta.as<double>(), u};
+    CostView<R> cv{c->nF, c->fmask.as<int>(), c->colw.as<double>(), c->Wsum, c->psiTR.as<C>(),
+                   c->path.empty() ? nullptr : c->pathR.as<C>(), {c->alpha[0], c->alpha[1], c->alpha[2], c->alpha[3], c->alpha[4]}};
+    DevParams* prm = c->prm.as<DevParams>();
+    int launches = 0;
+    const bool prof = c->opt.profile != 0;
+    cudaEvent_t ev0 = nullptr;
+    auto B = [&]() {
+        if (prof) {
+            ev0 = c->prof.get();
+            cudaEventRecord(ev0, st);
+        }
+    };
+    auto L = [&](cudaError_t e, const char* what) {
+        ++launches;
+        check_cuda(c, e, what);
+        if (prof) {
+            cudaEvent_t ev1 = c->prof.get();
+            cudaEventRecord(ev1, st);
+            c->prof.pending.push_back({c->prof.cls(what), ev0, ev1});
+        }
+    };
+    const double* delta = c->delta.empty() ? nullptr : c->dDelta.as<double>();
+    const bool cheb = c->opt.exponential == QOC_EXP_CHEBYSHEV;
+    B();
+    // Chebyshev: n = 0 (s = dt) and no Taylor order (p forced to 1 so that no range error is flagged);
+    // the degree comes from theta below
+    L(launch_theta(u, M, N, c->norms.as<double>(), delta, E, c->dt, c->theta_max, c->opt.tol,
+                   cheb ? 1 : c->opt.p_override, cheb ? 0 : c->opt.n_override, prm, st),
+      "theta");
+    const void* Hsrc = c->H64.p;
+    if constexpr (sizeof(R) == 4) {
+        B();
+        L(launch_split_scale(prm, c->H64.as<double2>(), (M + 2) * dd, c->sH.as<float4>(), st), "theta");
+        Hsrc = c->sH.p;
+    }
+    DevParams hp{};
+    check_cuda(c, cudaMemcpyAsync(&hp, prm, sizeof(DevParams), cudaMemcpyDeviceToHost, st), "read (p, n)");
+    check_cuda(c, cudaStreamSynchronize(st), "sync (p, n)");
+    const int p = std::max(1, std::min(hp.p, kPMax)), n = std::max(0, std::min(hp.n, 30));
+    const ChebCoef* chebd = nullptr;
+    if (cheb) {   // dt * spectral radius <= theta (the FP64 1-norm bound of k_theta, n = 0)
+        if (!chebyshev_coefficients(hp.theta, c->opt.tol, c->cheb_host))
+            throw Fail{set_err(c, QOC_ERR_RANGE, "Chebyshev degree above its maximum for theta = " + std::to_string(hp.theta))};
+        if (!c->chebd.p) check_cuda(c, c->chebd.alloc(sizeof(ChebCoef)), "alloc Chebyshev coefficients");
+        check_cuda(c, cudaMemcpyAsync(c->chebd.p, &c->cheb_host, sizeof(ChebCoef), cudaMemcpyHostToDevice, st),
+                   "copy Chebyshev coefficients");
+        chebd = c->chebd.as<ChebCoef>();
+    }
+    if (state_grad_smem<R>(d, c->S_eff, p, n, cheb ? c->cheb_host.K : 0) > kMaxDynSmem)
+        throw Fail{set_err(c, QOC_ERR_UNSUPPORTED, "state mode: d x d and five d x S blocks exceed a CTA's shared memory")};
+    if (c->opt.gradient == QOC_GRAD_EXACT && n > 16)
+        throw Fail{set_err(c, QOC_ERR_UNSUPPORTED, "state mode: more than 2^16 applications per slice")};
+    // the gradient kernel's per-item scratch: application inputs and intermediates (or terms)
+    const size_t scr_stride = state_grad_scratch(d, c->S_eff, p, n, cheb ? c->cheb_host.K : 0);
+    const size_t scr_bytes = scr_stride * (size_t)E * W * sizeof(C);
+    if (c->opt.gradient == QOC_GRAD_EXACT && c->stscr.bytes < scr_bytes) {
+        c->stscr.release();
+        check_cuda(c, c->stscr.alloc(scr_bytes), "alloc state-mode scratch");
+    }
+    const size_t xs = (size_t)c->ustride * sizeof(C) / (sizeof(R) == 4 ? sizeof(float4) : sizeof(double2));
+    void* X = c->Ubuf.p;
+    C* states = c->states.as<C>();
+    C* G = c->Gbuf.as<C>();
+    C* src = c->src.as<C>();
+    K* ck = c->ckpt.as<K>();
+    const size_t ck_es = (size_t)c->nseg_total * slice;
+    const int has_det = c->Hdet.empty() ? 0 : 1;
+    auto xw = [&](int w) {
+        const int j0 = w * W, wlen = std::min(W, N - j0);
+        B();
+        L(launch_state_x<R>(prm, d, M, N, u, delta, has_det, Hsrc, j0, wlen, E, X, xs, st), "state_x");
+    };
+    auto fwd = [&](int w, bool store_next) {
+        const int j0 = w * W, wlen = std::min(W, N - j0);
+        StateChainArgs<R> a{d, E, wlen, 0, sv, X, xs, ck + (size_t)w * slice, ck_es,
+                            (store_next && w + 1 < nw) ? ck + (size_t)(w + 1) * slice : nullptr, ck_es,
+                            states, (size_t)(W + 1) * slice, nullptr, 0, prm, chebd};
+        B();
+        L(launch_state_chain<R>(a, st), "state_chain (forward)");
+    };
+    for (int w = 0; w < nw; ++w) {
+        const int j0 = w * W, wlen = std::min(W, N - j0);
+        xw(w);
+        fwd(w, true);
+        B();
+        L(launch_slice_costs<R>(d, sv, j0, wlen, N, E, states, W, cv, c->Oj.as<double2>(), c->C5j.as<double>(),
+                                c->Ofin.as<double2>(), st),
+          "slice_costs");
+    }
+    check_cuda(c, cudaMemsetAsync(c->carry.p, 0, c->carry.bytes, st), "memset carry");
+    for (int w = nw - 1; w >= 0; --w) {
+        const int j0 = w * W, wlen = std::min(W, N - j0);
+        if (w != nw - 1) {   // the last wave is resident from the forward pass
+            xw(w);
+            fwd(w, false);
+        }
+        B();
+        L(launch_sources<R>(d, sv, j0, wlen, N, E, states, W, cv, c->Oj.as<double2>(), c->Ofin.as<double2>(), src, st),
+          "sources");
+        StateChainArgs<R> b{d, E, wlen, 1, sv, X, xs, c->carry.as<K>(), slice, c->carry.as<K>(), slice,
+                            G, (size_t)W * slice, src, (size_t)W * slice, prm, chebd};
+        B();
+        L(launch_state_chain<R>(b, st), "state_chain (costate)");
+        if (c->opt.gradient == QOC_GRAD_FIRST_ORDER) {
+            B();
+            L(launch_grad_first_order<R>(sys, sv, j0, wlen, E, states, G, W, c->dt, c->gpart.as<double>(), st),
+              "expm_adj");
+        } else {
+            StateGradArgs<R> g{d, E, M, N, j0, wlen, W, sv, X, xs, states, G, sys.Hk, c->gpart.as<double>(), prm,
+                               chebd, cheb ? c->cheb_host.K : 0, c->stscr.as<C>(), scr_stride};
+            B();
+            L(launch_state_grad<R>(g, p, n, st), "expm_adj");
+        }
+    }
+    B();
+    L(launch_finalize(E, M, N, u, c->alpha, c->Oj.as<double2>(), c->C5j.as<double>(), c->Ofin.as<double2>(),
+                      c->gpart.as<double>(), grad, out, prm, st),
+      "finalize");
+    c->launches = launches;
+}
+
 void evaluate(qoc_ctx* c, const double* u, double* grad, double* out, const DevParams* known = nullptr) {
     if (!c->planned) plan(c);
+    if (c->path_kind == 2) {
+        if (is_fp64(c)) evaluate_state_impl<double>(c, u, grad, out);
+        else evaluate_state_impl<float>(c, u, grad, out);
+        return;
+    }
     if (is_fp64(c)) evaluate_impl<double>(c, u, grad, out, known);
     else evaluate_impl<float>(c, u, grad, out, known);
 }
@@ -873,8 +1085,14 @@ qoc_status qoc_create(qoc_ctx** out, const qoc_options* opt) {
     if (o.precision < QOC_PREC_FP64 || o.precision > QOC_PREC_BF16_SPLIT) return QOC_ERR_ARG;
     if (!(o.tol >= 0.0) || !(o.theta_max >= 0.0) || o.ckpt_stride < 0 || o.wave_slices < 0 || o.sweep < 0 ||
         o.sweep > QOC_SWEEP_SCAN || o.gradient < QOC_GRAD_EXACT || o.gradient > QOC_GRAD_FIRST_ORDER ||
-        o.fault_inject < 0 || o.fault_inject > 1 || o.adjoint < QOC_ADJ_AUTO || o.adjoint > QOC_ADJ_RECOMPUTE)
+        o.fault_inject < 0 || o.fault_inject > 1 || o.adjoint < QOC_ADJ_AUTO || o.adjoint > QOC_ADJ_RECOMPUTE ||
+        o.reversal < 0 || o.reversal > 1 || o.propagation < QOC_PROP_UNITARY || o.propagation > QOC_PROP_STATE ||
+        o.exponential < QOC_EXP_TAYLOR || o.exponential > QOC_EXP_CHEBYSHEV)
         return QOC_ERR_ARG;
+    if (o.exponential == QOC_EXP_CHEBYSHEV && o.propagation != QOC_PROP_STATE) return QOC_ERR_UNSUPPORTED;
+    // reversal regenerates states through the stored propagators, whose FP32 rounding would
+    // accumulate over the backward pass: FP64 form only
+    if (o.reversal && o.precision != QOC_PREC_FP64) return QOC_ERR_UNSUPPORTED;
     const bool f64 = o.precision == QOC_PREC_FP64;
     if (o.tol == 0.0) o.tol = f64 ? 1e-15 : 1e-8;
     if (o.theta_max == 0.0 && f64) o.theta_max = 0.25;   // FP32 forms: resolved by the planner
@@ -1136,10 +1354,15 @@ qoc_status qoc_get_info(qoc_ctx* ctx, qoc_info* info) {
     info->kernel_path = ctx->path_kind;
     info->device_bytes = (long long)ctx->device_bytes();
     if (ctx->opt.gradient == QOC_GRAD_FIRST_ORDER) info->adjoint_form = 2;
+    else if (ctx->path_kind == 2) info->adjoint_form = 4;
     else if (ctx->path_kind == 1) info->adjoint_form = ctx->last_big_rev ? 0 : 1;
     else if (ctx->Zbuf.p && info->p - 1 + info->n <= kZCap)
         info->adjoint_form = adj_lowrank_applies(ctx->S_eff, info->n, ctx->d) ? 3 : 0;
     else info->adjoint_form = 1;
+    if (ctx->planned && ctx->path_kind == 2 && ctx->opt.exponential == QOC_EXP_CHEBYSHEV) {
+        info->p = ctx->cheb_host.K;       // the Chebyshev degree, no squaring
+        info->n = 0;
+    }
     return QOC_OK;
     QOC_GUARD_END
 }

@@ -259,6 +259,8 @@ cudaError_t oz_rev_step(const OzRev& z, const float2* const ops[4], const size_t
 // mode 0: forward propagation of one wave (grid z = 1) from checkpoint `seg0`, storing the
 //         states of the wave and the carried block every `seg` slices (checkpoints seg0 + 1, ..)
 // mode 1: regeneration of the wave's states, one CTA per checkpoint segment in parallel
+// mode 2: reversal: the wave's states regenerated backwards from its last state (rev_src, the
+//         first state of the next wave), Psi_{j-1} = U_j^dag Psi_j (grid z = 1)
 template <typename R>
 struct ChainArgs {
     int d;
@@ -273,6 +275,8 @@ struct ChainArgs {
     C_t<R>* states;         // [E][wmax + 1] FP32/FP64 blocks of the wave
     const K_t<R>* Uk;       // ... carried segment products (exactly one of the two is set)
     const DevParams* prm;   // grid exponent eu of the FP32 form (nullptr: 1)
+    const C_t<R>* rev_src = nullptr;   // mode 2: last state of the wave, member e at + e * rev_estride
+    size_t rev_estride = 0;
 };
 template <typename R> cudaError_t launch_chain(const ChainArgs<R>& a, cudaStream_t st);
 // Costate sweep G_{j-1} = U_j^dag G_j + src_{j-1}, split into segments of `seg` slices that run in
@@ -323,6 +327,57 @@ template <typename R> cudaError_t launch_seg_products(const SegProdArgs<R>& a, c
 template <typename R>
 cudaError_t launch_to_carry(const double2* src, K_t<R>* dst, int d, int S, StateView<R> sv, int copies,
                             size_t dst_stride, cudaStream_t st);
+
+// ---- state-mode propagation (k_state.cu): Taylor-on-vector without forming U_j ----
+// Chebyshev expansion of the slice map (state mode): exp(-i dt H) = sum_k (-i)^k a_k T_k(dt H /
+// theta), a_0 = J_0(theta), a_k = 2 J_k(theta), theta >= dt * spectral radius; device copy
+constexpr int kChebMax = 96;
+struct ChebCoef {
+    int K;                  // degree
+    double inv_theta;       // 1 / theta
+    double a[kChebMax + 1];
+};
+template <typename R>
+struct StateChainArgs {
+    int d, E, wlen, dir;    // dir 0: forward Psi_j = T(X_j)^(2^n) Psi_{j-1}; 1: costate
+    StateView<R> sv;
+    const void* X;          // X_j of item e * wlen + jl at X + item * xs (FP32: float4 pairs; FP64: double2)
+    size_t xs;
+    const K_t<R>* cin;      // starting block of member e at + e * cin_es (costate: in-carry, may be null)
+    size_t cin_es;
+    K_t<R>* cout;           // carried block after the wave (forward: next checkpoint; costate: out-carry)
+    size_t cout_es;
+    C_t<R>* out;            // forward: states (wlen + 1 blocks); costate: G (wlen blocks), + e * out_es
+    size_t out_es;
+    const C_t<R>* src;      // costate: sources, + e * src_es
+    size_t src_es;
+    const DevParams* prm;
+    const ChebCoef* cheb = nullptr;   // device coefficients: Chebyshev in place of Taylor
+};
+template <typename R>
+struct StateGradArgs {
+    int d, E, M, N, j0, wlen, wmax;
+    StateView<R> sv;
+    const void* X;
+    size_t xs;
+    const C_t<R>* states;   // Psi of the wave, (wmax + 1) blocks per member
+    const C_t<R>* G;        // costates, wmax blocks per member
+    const C_t<R>* Hk;       // M x d x d in the compute precision
+    double* gpart;          // E x M x N
+    const DevParams* prm;
+    const ChebCoef* cheb = nullptr;   // device coefficients: Chebyshev in place of Taylor
+    int K = 0;              // Chebyshev degree (host copy, for the shared-memory size)
+    C_t<R>* scr = nullptr;  // per-item global scratch (state_grad_scratch elements each)
+    size_t scr_stride = 0;
+};
+constexpr int kStateMaxColumns = 8;
+template <typename R> size_t state_grad_smem(int d, int S, int p, int n, int K);
+size_t state_grad_scratch(int d, int S, int p, int n, int K);
+template <typename R>
+cudaError_t launch_state_x(const DevParams* prm, int d, int M, int N, const double* u, const double* delta, int has_det,
+                           const void* Hsrc, int j0, int wlen, int E, void* X, size_t xs, cudaStream_t st);
+template <typename R> cudaError_t launch_state_chain(const StateChainArgs<R>& a, cudaStream_t st);
+template <typename R> cudaError_t launch_state_grad(const StateGradArgs<R>& a, int p, int n, cudaStream_t st);
 
 // ---- per-slice costs, sources, final reduction (k_chain.cu) ----
 template <typename R>

@@ -28,6 +28,8 @@ PRECISIONS = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
 SWEEPS = {"auto": 0, "serial": 1, "scan": 2}
 GRADIENTS = {"exact": 0, "first_order": 1}
 ADJOINTS = {"auto": 0, "recompute": 1}
+PROPAGATIONS = {"unitary": 0, "state": 1}
+EXPONENTIALS = {"taylor": 0, "chebyshev": 1}
 
 # every symbol exported by include/qoc.h
 ABI_SYMBOLS = ("qoc_default_options", "qoc_create", "qoc_destroy", "qoc_last_error", "qoc_status_string",
@@ -47,7 +49,8 @@ class qoc_options(ct.Structure):
                 ("ckpt_stride", ct.c_int), ("device", ct.c_int), ("stream", ct.c_void_p),
                 ("p_override", ct.c_int), ("n_override", ct.c_int), ("profile", ct.c_int),
                 ("wave_slices", ct.c_int), ("plain_fp32_exp", ct.c_int), ("sweep", ct.c_int),
-                ("gradient", ct.c_int), ("adjoint", ct.c_int), ("graph", ct.c_int), ("fault_inject", ct.c_int)]
+                ("gradient", ct.c_int), ("adjoint", ct.c_int), ("graph", ct.c_int), ("fault_inject", ct.c_int),
+                ("reversal", ct.c_int), ("propagation", ct.c_int), ("exponential", ct.c_int)]
 
 
 PROFILE_SLOTS = 16
@@ -276,7 +279,8 @@ class Context:
                  ckpt_stride: int = 0, wave_slices: int = 0, device: int = 0, stream: Optional[int] = None,
                  p_override: int = 0, n_override: int = -1, profile: bool = False,
                  plain_fp32_exp: bool = False, sweep: str = "auto", gradient: str = "exact",
-                 adjoint: str = "auto", graph: bool = False, fault_inject: int = 0):
+                 adjoint: str = "auto", graph: bool = False, fault_inject: int = 0, reversal: bool = False,
+                 propagation: str = "unitary", exponential: str = "taylor"):
         opt = qoc_default_options()
         opt.precision = PRECISIONS[precision]
         opt.tol = tol
@@ -296,6 +300,9 @@ class Context:
         opt.adjoint = ADJOINTS[adjoint]
         opt.graph = 1 if graph else 0
         opt.fault_inject = fault_inject
+        opt.reversal = 1 if reversal else 0
+        opt.propagation = PROPAGATIONS[propagation]
+        opt.exponential = EXPONENTIALS[exponential]
         self.precision = precision
         self._ctx = qoc_create(opt)
         self.M = self.N = 0

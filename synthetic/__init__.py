@@ -288,6 +288,77 @@ def dsweep_problem(d: int, seed: int = 6000, N: int = 2000) -> Problem:
                    np.ones(d), default_alpha(), u, precision="fp32")
 
 
+def transmon_cnot(seed: int = 7000, N: int = 250, T: float = 10.0, levels: int = 5) -> Problem:
+    """Two coupled transmons with `levels` levels each (d = 25), the CNOT of Sec. V.A in the frame
+    rotating at the first transmon's frequency: H0 = Delta n_2 + sum_j (alpha/2) n_j (n_j - 1)
+    + J (b_1^dag b_2 + b_1 b_2^dag) with Delta = 2pi*0.4 (3.9 - 3.5 GHz), alpha = -2pi*0.225,
+    J = 2pi*0.1; controls x_1, y_1, x_2, y_2 (the two drive quadratures of each transmon in the
+    rotating frame) and z_2 = n_2; gate time T = 10 ns in N slices.  The four computational
+    states |q1 q2> (levels 0, 1) are propagated and must reach CNOT|q1 q2> (qubit 1 controls);
+    levels 3 and 4 of either transmon are forbidden (C5, weight 1/(4N)), with small amplitude
+    and variation penalties (C3, C4).  The controls start small and random: an optimizer's
+    starting point."""
+    rng = np.random.default_rng(seed)
+    dims = [levels, levels]
+    d = levels * levels
+    al, J, delta = -TWO_PI * 0.225, TWO_PI * 0.1, TWO_PI * 0.4
+    n = number(levels)
+    b = lowering(levels)
+    H0 = delta * embed(n, 1, dims)
+    for i in range(2):
+        H0 = H0 + embed(0.5 * al * n @ (n - np.eye(levels)), i, dims)
+    hop = np.kron(b.conj().T, b)
+    H0 = H0 + J * (hop + hop.conj().T)
+    Hk = np.concatenate([ladder_controls(dims, [0, 1], 4), embed(n, 1, dims)[None]])
+    comp = [levels * q1 + q2 for q1 in (0, 1) for q2 in (0, 1)]      # |00>, |01>, |10>, |11>
+    cnot_of = {0: 0, 1: 1, 2: 3, 3: 2}
+    psi0 = np.zeros((d, 4), np.complex128)
+    psiT = np.zeros((d, 4), np.complex128)
+    for s_, idx in enumerate(comp):
+        psi0[idx, s_] = 1.0
+        psiT[comp[cnot_of[s_]], s_] = 1.0
+    digits = np.array(np.unravel_index(np.arange(d), dims)).T
+    forb = np.where(np.any(digits >= 3, axis=1))[0].astype(np.int32)
+    u = rng.normal(0.0, TWO_PI * 0.01, size=(Hk.shape[0], N))
+    alpha = default_alpha(fid=1.0, amp=1e-6, var=1e-4, forbid=0.1 / (4 * N))
+    return Problem(f"transmon_cnot_d{d}", H0, Hk, T / N, N, psi0, psiT, forb, np.ones(4), alpha, u,
+                   precision="fp64")
+
+
+def cat_state(seed: int = 8000, N: int = 8000, dt: float = 0.005, nq: int = 7, nr: int = 22,
+              lam: float = 2.0) -> Problem:
+    """Schroedinger-cat state preparation (Sec. V.C): a transmon (nq = 7 levels) coupled to a
+    cavity mode (nr = 22 levels), d = 154, in the lab frame without the rotating-wave
+    approximation, transmon-major basis (index = nr * t + r):
+    H0 = w_q n_b + (alpha/2) n_b (n_b - 1) + w_r n_a + g (a + a^dag)(b + b^dag) with
+    w_q = 2pi*3.5, alpha = -2pi*0.225, w_r = 2pi*3.9, g = 2pi*0.1; controls on the transmon only,
+    H_x = b + b^dag and H_z = n_b.  N = 8000 slices of dt = 5 ps (T = 40 ns).  State transfer
+    |0>_q |0>_r -> |0>_q |cat>_r with |cat> = (|lam> + |-lam>) / norm, lam = 2, built from the
+    coherent states of the truncated mode and normalised (C2); occupation of transmon levels 3..6
+    and cavity levels 20, 21 is penalised (C5, weight 1/N), with a small variation penalty (C4).
+    The controls start small and random."""
+    rng = np.random.default_rng(seed)
+    d = nq * nr
+    wq, al, wr, g = TWO_PI * 3.5, -TWO_PI * 0.225, TWO_PI * 3.9, TWO_PI * 0.1
+    b, a = lowering(nq), lowering(nr)
+    nb, na = number(nq), number(nr)
+    Iq, Ir = np.eye(nq), np.eye(nr)
+    H0 = (np.kron(wq * nb + 0.5 * al * nb @ (nb - Iq), Ir) + np.kron(Iq, wr * na)
+          + g * np.kron(b + b.conj().T, a + a.conj().T)).astype(np.complex128)
+    Hk = np.stack([np.kron(b + b.conj().T, Ir), np.kron(nb, Ir)]).astype(np.complex128)
+    fock = np.arange(nr)
+    coh = lambda z: np.array([z ** k / math.sqrt(math.factorial(k)) for k in fock], np.complex128)
+    cat = coh(lam) + coh(-lam)
+    cat /= np.linalg.norm(cat)
+    psiT = np.zeros((d, 1), np.complex128)
+    psiT[:nr, 0] = cat                                  # transmon level 0
+    forb = sorted({nr * t + r for t in range(3, nq) for r in range(nr)} |
+                  {nr * t + r for t in range(nq) for r in (nr - 2, nr - 1)})
+    u = rng.normal(0.0, TWO_PI * 0.02, size=(2, N))
+    return Problem(f"cat_state_d{d}", H0, Hk, dt, N, basis_state(d, 0), psiT, np.array(forb, np.int32),
+                   np.ones(1), default_alpha(var=1e-4, forbid=1.0 / N), u, precision="fp32")
+
+
 DSWEEP_D = (2, 4, 8, 16, 32, 64, 128, 256)
 
 WORKLOADS = {
@@ -295,6 +366,8 @@ WORKLOADS = {
     "transmon_cavity": transmon_cavity,
     "transmon4": transmon4,
     "gue256": gue256,
+    "transmon_cnot": transmon_cnot,
+    "cat_state": cat_state,
 }
 
 

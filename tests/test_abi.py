@@ -106,9 +106,22 @@ def test_null_context_is_rejected(lib):
     lib.qoc_destroy(None)
 
 
+def test_reversal_needs_the_fp64_form(lib):
+    """Reversal regenerates states through the stored propagators: the FP32 forms refuse it on
+    the host (QOC_ERR_UNSUPPORTED) before touching a device."""
+    import ctypes as ct
+    opt = qmod.qoc_options()
+    lib.qoc_default_options(ct.byref(opt))
+    opt.precision, opt.reversal = 1, 1
+    out = ct.c_void_p(1)
+    assert lib.qoc_create(ct.byref(out), ct.byref(opt)) == 9
+    assert not out.value
+
+
 @pytest.mark.parametrize("field,value", [("precision", 4), ("precision", -1), ("tol", -1.0), ("theta_max", -0.5),
                                          ("ckpt_stride", -2), ("wave_slices", -1), ("sweep", 3), ("gradient", 2),
-                                         ("adjoint", 2), ("fault_inject", 2)])
+                                         ("adjoint", 2), ("fault_inject", 2), ("reversal", 2),
+                                         ("propagation", 2), ("propagation", -1), ("exponential", 2)])
 def test_invalid_options_are_rejected_before_the_device(lib, field, value):
     """qoc_create validates every option on the host before it touches a device: an out-of-range
     value is QOC_ERR_ARG (1) on any machine, and no context is returned."""

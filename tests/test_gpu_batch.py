@@ -1,6 +1,8 @@
 """The batched evaluation of many independent problems of uneven (d, N, M, E) in one call
 (qoc_evaluate_batch): each problem against the CPU FP64 oracle, and the batch against the
 one-problem-at-a-time evaluation of the same contexts (same kernels: identical results)."""
+import os
+
 import numpy as np
 import pytest
 
@@ -17,7 +19,7 @@ def _lib():
     build.build()
 
 
-def _run_batch(probs, precision="fp32"):
+def _run_batch(probs, precision="fp32", single=True):
     import torch
     from paper_1612_04929_gb300 import Context, qoc_evaluate_batch
     ctxs = [Context(precision) for _ in probs]
@@ -31,7 +33,7 @@ def _run_batch(probs, precision="fp32"):
                        stream)
     torch.cuda.synchronize()
     res = [(o.cpu().numpy(), g.cpu().numpy()) for o, g in zip(outs, gs)]
-    single = [c.evaluate(p.u) for c, p in zip(ctxs, probs)]
+    single = [c.evaluate(p.u) for c, p in zip(ctxs, probs)] if single else None
     for c in ctxs:
         c.close()
     return res, single
@@ -54,3 +56,57 @@ def test_batch_fp64_small():
     for p, (o, g), _ in zip(probs, res, single):
         c_ref, g_ref, _ = orc.cost_and_grad(p, p.u)
         assert abs(o[0] - c_ref) <= 1e-10 * abs(c_ref) and rel(g, g_ref) <= 1e-10
+
+
+# ------------------------------------------------------------------ the batched sweep at full size
+E32_SUBSET = (0, 1, 3, 5)     # d = 16, 4, 8 (per-slice kernels) and 81 (batched path), 32 members each
+
+
+def _sampled_cols(N):
+    """Every 100th slice and the last one."""
+    return sorted(set(list(range(0, N, 100)) + [N - 1]))
+
+
+def _oracle_sampled(job):
+    """The oracle's cost and its gradient at the sampled slices of batch problem i with E members
+    (its costate sweep covers every slice; only the per-slice contractions are sampled)."""
+    i, E = job
+    p = sy.batch_problem(i, ensemble=E)
+    c, g, _ = orc.cost_and_grad(p, p.u, slices=_sampled_cols(p.N))
+    return c, g
+
+
+def test_batch_full_size_sampled():
+    """The batched sweep as stated: all 128 problems (d in {4, 8, 16, 40, 81, 128}, N up to
+    4000) in one qoc_evaluate_batch call, plus 32-member detuning ensembles on four of them in a
+    second call, each against the oracle: the cost, and the gradient at every 100th slice.  The
+    oracle references are computed by a spawned process pool while the GPU evaluates."""
+    import multiprocessing as mp
+    jobs = [(i, 1) for i in range(128)] + [(i, 32) for i in E32_SUBSET]
+    jobs.sort(key=lambda j: -(sy.batch_problem(j[0]).N * sy.batch_problem(j[0]).d ** 2 * j[1]))  # longest first
+    # one BLAS thread per worker (the workers are spawned with this environment), one worker per core
+    threads = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    os.environ.update({k: "1" for k in threads})
+    try:
+        pool = mp.get_context("spawn").Pool(max(1, os.cpu_count() or 1))
+    finally:
+        for k, v in threads.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    with pool:
+        pending = pool.map_async(_oracle_sampled, jobs, chunksize=1)
+        probs = [sy.batch_problem(i, ensemble=E) for i, E in
+                 [(i, 1) for i in range(128)] + [(i, 32) for i in E32_SUBSET]]
+        res1, _ = _run_batch(probs[:128], single=False)
+        res32, _ = _run_batch(probs[128:], single=False)
+        refs = pending.get(timeout=1500)
+    assert sorted({p.d for p in probs}) == [4, 8, 16, 40, 81, 128] and max(p.N for p in probs) > 3900
+    ref_of = dict(zip(jobs, refs))
+    keys = [(i, 1) for i in range(128)] + [(i, 32) for i in E32_SUBSET]
+    for p, (o, g), key in zip(probs, res1 + res32, keys):
+        c_ref, g_ref = ref_of[key]
+        cols = _sampled_cols(p.N)
+        assert abs(o[0] - c_ref) <= 1e-5 * abs(c_ref), (p.name, p.E)
+        assert rel(g[:, cols], g_ref[:, cols]) <= 1e-5, (p.name, p.E, rel(g[:, cols], g_ref[:, cols]))

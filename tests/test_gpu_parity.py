@@ -254,6 +254,32 @@ def test_repeated_evaluations_are_bitwise_identical(precision, d):
             assert again[0] == first[0] and np.array_equal(again[1], first[1])
 
 
+# ------------------------------------------------------------------ reversal (Algorithms 1-3)
+REV_CASES = [
+    dict(d=5, M=2, N=37, S=2, seed=151, nF=2, path=True, E=2),
+    dict(d=16, M=3, N=60, S=16, seed=152, nF=3, weights=True),
+    dict(d=57, M=2, N=23, S=3, seed=153, nF=2),                 # batched FP64 path (d > 48)
+]
+
+
+@pytest.mark.parametrize("case", REV_CASES, ids=lambda c: f"d{c['d']}S{c['S']}N{c['N']}")
+@pytest.mark.parametrize("wave", [5, 8])
+def test_reversal_matches_oracle_and_checkpoints(case, wave):
+    """The backward pass regenerates each wave's states from the next wave's first state by
+    Psi_{j-1} = U_j^dag Psi_j (no checkpoint inside a wave): several waves, ragged last wave,
+    against the oracle and against the checkpointed evaluation of the same form."""
+    prob = sy.random_problem(**case, dt=0.2, u_scale=0.8)
+    cost, grad, terms, info = check(prob, "fp64", reversal=True, wave_slices=wave)
+    assert info["ckpt_stride"] == info["wave_slices"] == wave and info["n_waves"] >= 3
+    c2, g2, _, _ = run(prob, "fp64", ckpt_stride=4, wave_slices=8)
+    assert abs(cost - c2) <= 1e-12 * abs(c2) and rel(grad, g2) <= 1e-11
+
+
+def test_reversal_cnot2q_full_size():
+    cost, grad, terms, info = check(sy.cnot2q(), "fp64", reversal=True, wave_slices=40)
+    assert info["n_waves"] == 5
+
+
 # ------------------------------------------------------------------ the workloads
 def test_cnot2q_fp64_full_size():
     check(sy.cnot2q(), "fp64")

@@ -95,3 +95,37 @@ def test_batch_problems_span_the_stated_ranges():
     assert all(200 <= p.N <= 4000 and 2 <= p.M <= 8 and p.dt == 0.5 for p in probs)
     ens = sy.batch_problem(3, ensemble=32)
     assert ens.E == 32 and herm(ens.Hdet)
+
+
+def test_transmon_cnot():
+    """Two five-level transmons in the frame of the first: the drift's single-excitation block
+    holds the 400 MHz detuning and the 100 MHz exchange; the anharmonicity shows in the two-
+    excitation energies; the target maps the four computational states by CNOT."""
+    p = sy.transmon_cnot()
+    assert (p.d, p.N, p.M, p.S) == (25, 250, 5, 4) and abs(p.dt - 0.04) < 1e-15
+    assert herm(p.H0) and all(herm(h) for h in p.Hk)
+    e01, e10 = 1, 5                                     # |0,1> and |1,0> (index 5 q1 + q2)
+    blk = p.H0[np.ix_([e01, e10], [e01, e10])]
+    assert np.isclose(blk[0, 0] - blk[1, 1], TWO_PI * 0.4) and np.isclose(abs(blk[0, 1]), TWO_PI * 0.1)
+    assert np.isclose(p.H0[10, 10].real, TWO_PI * -0.225)   # |2,0>: 2 levels of transmon 1, alpha
+    comp = [0, 1, 5, 6]
+    for s, t in [(0, 0), (1, 1), (2, 3), (3, 2)]:
+        assert p.psi0[comp[s], s] == 1.0 and p.psiT[comp[t], s] == 1.0
+    assert all(i // 5 >= 3 or i % 5 >= 3 for i in p.forbidden) and len(p.forbidden) == 25 - 9
+
+
+def test_cat_state():
+    """The cat-state system: d = 7 x 22 in the lab frame, 8000 slices of 5 ps; the uncoupled
+    spectrum holds the transmon and cavity frequencies; the target is the normalised cat of
+    amplitude 2 in the cavity with the transmon in its ground state (even photon numbers only)."""
+    p = sy.cat_state()
+    assert (p.d, p.N, p.M, p.S) == (154, 8000, 2, 1) and abs(p.dt - 0.005) < 1e-15
+    assert herm(p.H0) and all(herm(h) for h in p.Hk)
+    diag = np.real(np.diag(p.H0))
+    assert np.isclose(diag[22] - diag[0], TWO_PI * 3.5) and np.isclose(diag[1] - diag[0], TWO_PI * 3.9)
+    assert np.isclose(diag[44] - 2 * diag[22], TWO_PI * -0.225)
+    cat = p.psiT[:22, 0]
+    assert np.isclose(np.linalg.norm(p.psiT), 1.0) and np.allclose(cat[1::2], 0.0)
+    assert np.isclose(abs(cat[0]) ** 2, 2 * np.exp(-4) / (1 + np.exp(-8)), rtol=1e-6)
+    assert np.array_equal(p.psi0[:, 0], np.eye(154)[0])
+    assert 22 * 3 in p.forbidden and 20 in p.forbidden and 21 in p.forbidden and 22 * 2 not in p.forbidden
