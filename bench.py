@@ -93,14 +93,22 @@ def parse():
     ap.add_argument("--no-per-config", action="store_true",
                     help="skip the per-config lines (the other four configurations, a few seconds each)")
     ap.add_argument("--graph", action="store_true", help="replay each evaluation from a captured CUDA graph")
+    ap.add_argument("--propagation", choices=["unitary", "state"], default="unitary",
+                    help="form U_j (unitary) or apply the series to the propagated columns (state mode)")
+    ap.add_argument("--exponential", choices=["taylor", "chebyshev"], default="taylor",
+                    help="slice exponential: Taylor with scaling and squaring, or Chebyshev (state mode)")
+    ap.add_argument("--members", type=int, default=1, help="detuning-ensemble members (cat_state workload)")
     ap.add_argument("--gradient", choices=["exact", "first_order"], default="exact",
                     help="exact derivative of the truncated series, or the paper's first-order Eq. 11")
     return ap.parse_args()
 
 
-def make_problem(name, N=0):
+def make_problem(name, N=0, members=1):
     import synthetic as sy
-    return sy.WORKLOADS[name](N=N) if N else sy.WORKLOADS[name]()
+    kw = {"N": N} if N else {}
+    if members > 1:
+        kw["ensemble"] = members
+    return sy.WORKLOADS[name](**kw)
 
 
 def config_of(prob, precision, stride, extra=None):
@@ -310,6 +318,8 @@ def roofline_of(prob, precision, info, prof, K, peaks, traffic_key=None):
     it runs on (FP32 or FP64 FMA lanes; BF16 tensor cores for the exact-accumulation tensor-core
     products, whose executed MMA flops are reported beside)."""
     d, p, n = prob.d, info["p"], info["n"]
+    if info["kernel_path"] == 2:
+        return state_roofline(prob, precision, info, prof, K, peaks)
     per_slice = {"expm_fwd": expm_flops_per_slice(d, p, n),
                  "expm_fwd (recompute)": expm_flops_per_slice(d, p, n),
                  "expm_adj": adj_flops_per_slice(info.get("adjoint_form", 1), d, p, n, prob.S)}
@@ -346,6 +356,31 @@ def roofline_of(prob, precision, info, prof, K, peaks, traffic_key=None):
                         "execute 12 FMAs per complex multiply-add (3.25 per algorithmic one), so the split "
                         "exponential's fraction is bounded near 0.3 by construction")
     return roof
+
+
+def state_matvecs_per_slice(info):
+    """Matrix-vector products per slice application in state mode: p 2^n (Taylor, Horner) or the
+    Chebyshev degree K (reported as p with n = 0)."""
+    return info["p"] * (1 << info["n"])
+
+
+def state_roofline(prob, precision, info, prof, K, peaks):
+    """State mode: the dominant kernel is one of the serial chains (forward or costate), one CTA per
+    (panel, member); its algorithmic flops are 8 d^2 S per matrix-vector product (complex), one
+    product per Horner step or Chebyshev term.  The peak is the FP32 (FP64) FMA peak of the whole
+    GPU although the chain runs on one SM per (panel, member): the fraction shows how far a single
+    trajectory is from the GPU's throughput."""
+    cands = {k: v for k, v in prof.items() if k.startswith("state_chain")}
+    if not cands:
+        return None
+    top_name, (top_launches, top_ms) = max(cands.items(), key=lambda kv: kv[1][1])
+    flops = prob.N * prob.E * state_matvecs_per_slice(info) * 8.0 * prob.d ** 2 * prob.S * K
+    achieved = flops / (top_ms / 1e3) / 1e12
+    peak = peaks["fp64_tflops"] if precision == "fp64" else peaks["fp32_tflops"]
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": top_name, "launches": top_launches, "avg_launch_ms": top_ms / top_launches,
+            "peak_source": peaks["fp_source"] + " (of measured)",
+            "note": "serial chain: one CTA per (column panel, member), so at most E * panels SMs are busy"}
 
 
 # real BF16 GEMMs of d^3 per complex product in the exact-accumulation tensor-core form: 10 slice
@@ -411,14 +446,14 @@ print(json.dumps({{"cost": float(c), "grad": [float(x) for x in g.ravel()]}}))
         os.unlink(path)
 
 
-def gpu_error_vs_oracle(prob, precision, stream, ref_slices, threads=0):
+def gpu_error_vs_oracle(prob, precision, stream, ref_slices, threads=0, form=None):
     """Relative cost and gradient error of the GPU form against the CPU FP64 oracle on the first
     ref_slices slices of the problem (the whole problem when ref_slices >= N)."""
     import numpy as np
     from paper_1612_04929_gb300 import Context
     q = prob if ref_slices >= prob.N else truncated(prob, ref_slices)
     ref = oracle_reference(q, threads)
-    with Context(precision, device=0, stream=stream.cuda_stream) as cq:
+    with Context(precision, device=0, stream=stream.cuda_stream, **(form or {})) as cq:
         cq.set_problem(q)
         c_gpu, g_gpu, _ = cq.evaluate(q.u)
     g_ref = np.asarray(ref["grad"])
@@ -426,17 +461,20 @@ def gpu_error_vs_oracle(prob, precision, stream, ref_slices, threads=0):
             "grad_rel": float(np.linalg.norm(np.ravel(g_gpu) - g_ref) / np.linalg.norm(g_ref))}
 
 
-def measure_config(name, precision, peaks, stream, flush, K, warmup, fp64_N=0, err_slices=0, fp64_cache=None):
+def measure_config(name, precision, peaks, stream, flush, K, warmup, fp64_N=0, err_slices=0, fp64_cache=None,
+                   form=None, members=1, N=0):
     """One per-config line: device time per evaluation, slice-steps/s, its own roofline, the
     plain FP64 GPU form's time on the same workload (on its first fp64_N slices, scaled by N,
-    when fp64_N > 0), and the error against the oracle on the first err_slices slices."""
+    when fp64_N > 0; fp64_N < 0: not timed), and the error against the oracle on the first
+    err_slices slices.  form: Context options (propagation, exponential)."""
     import torch
     from paper_1612_04929_gb300 import Context
-    prob = make_problem(name)
+    form = form or {}
+    prob = make_problem(name, N, members)
     u = torch.tensor(prob.u, dtype=torch.float64, device="cuda")
     grad = torch.empty_like(u)
     out = torch.empty(6, dtype=torch.float64, device="cuda")
-    with Context(precision, device=0, stream=stream.cuda_stream, profile=True) as ctx:
+    with Context(precision, device=0, stream=stream.cuda_stream, profile=True, **form) as ctx:
         ctx.set_problem(prob)
         ms = time_device_evals(ctx, u, grad, out, K, warmup, flush, stream)
         ctx.reset_profile()
@@ -446,9 +484,9 @@ def measure_config(name, precision, peaks, stream, flush, K, warmup, fp64_N=0, e
     row = {"workload": prob.name, "precision": precision, "d": prob.d, "N": prob.N, "M": prob.M, "S": prob.S,
            "E": prob.E, "p": info["p"], "n": info["n"], "kernel_path": info["kernel_path"],
            "ms_per_step": ms, "value": units / (ms / 1e3), "unit": UNIT, "steps": K,
-           "roofline": roofline_of(prob, precision, info, prof, K, peaks)}
+           "roofline": roofline_of(prob, precision, info, prof, K, peaks), **form}
     row["roofline_events_ms_per_step"] = ms_p
-    if precision != "fp64":
+    if precision != "fp64" and fp64_N >= 0:
         key = (name, fp64_N)
         if fp64_cache is not None and key in fp64_cache:
             row["fp64_form"] = fp64_cache[key]
@@ -469,7 +507,7 @@ def measure_config(name, precision, peaks, stream, flush, K, warmup, fp64_N=0, e
         row["speedup_vs_fp64_form"] = row["fp64_form"]["ms_per_step"] / ms
     if err_slices:
         try:
-            row["error_vs_oracle"] = gpu_error_vs_oracle(prob, precision, stream, err_slices)
+            row["error_vs_oracle"] = gpu_error_vs_oracle(prob, precision, stream, err_slices, form=form)
         except Exception as exc:
             row["error_vs_oracle"] = {"failed": str(exc)[:200]}
     return row
@@ -574,10 +612,21 @@ def per_config_lines(args, peaks, stream, flush):
             ("c3_transmon4_bf16", "transmon4", "bf16", 3, 0, 1000),
             ("c4_gue256_fp32", "gue256", "fp32", 2, 200, 40),
             ("c4_gue256_bf16", "gue256", "bf16", 2, 200, 40)]
-    for key, name, prec, K, fp64_N, err in plan:
+    state = {"propagation": "state"}
+    cheb = {"propagation": "state", "exponential": "chebyshev"}
+    # the cat-state system (d = 154, N = 8000): unitary form and state mode; and a 16-member
+    # robust-control ensemble on its first 1000 slices, where state mode runs the members at once
+    plan += [("f1_cat_state_unitary_fp32", "cat_state", "fp32", 2, -1, 200, {}, 1, 0),
+             ("f1_cat_state_chebyshev_fp32", "cat_state", "fp32", 1, -1, 200, cheb, 1, 0),
+             ("f1_cat_state_E16_N1000_unitary_fp32", "cat_state", "fp32", 2, -1, 0, {}, 16, 1000),
+             ("f1_cat_state_E16_N1000_taylor_fp32", "cat_state", "fp32", 2, -1, 0, state, 16, 1000),
+             ("f1_cat_state_E16_N1000_chebyshev_fp32", "cat_state", "fp32", 2, -1, 40, cheb, 16, 1000)]
+    for entry in plan:
+        key, name, prec, K, fp64_N, err = entry[:6]
+        form, members, nsl = (entry[6:] + ({}, 1, 0))[:3] if len(entry) > 6 else ({}, 1, 0)
         try:
             rows[key] = measure_config(name, prec, peaks, stream, flush, K, 1, fp64_N=fp64_N, err_slices=err,
-                                       fp64_cache=fp64_cache)
+                                       fp64_cache=fp64_cache, form=form, members=members, N=nsl)
         except Exception as exc:
             rows[key] = {"failed": str(exc)[:300]}
         print(f"# per_config {key}: {json.dumps(rows[key])[:300]}", file=sys.stderr, flush=True)
@@ -609,12 +658,13 @@ def ours_arm(args):
     if world > 1:
         dist.barrier()
     peaks = measured_peaks(local)
-    prob = make_problem(args.workload, args.N)
+    prob = make_problem(args.workload, args.N, args.members)
     precision = args.precision or prob.precision
     stream = torch.cuda.Stream()          # every kernel of the step and every event on one stream
     torch.cuda.set_stream(stream)
+    form = dict(propagation=args.propagation, exponential=args.exponential)
     ctx = Context(precision, device=local, stream=stream.cuda_stream, ckpt_stride=args.ckpt_stride,
-                  gradient=args.gradient, graph=args.graph)
+                  gradient=args.gradient, graph=args.graph, **form)
     ctx.set_problem(prob)
     u = torch.tensor(prob.u, dtype=torch.float64, device="cuda")
     grad = torch.empty_like(u)
@@ -653,7 +703,7 @@ def ours_arm(args):
     # bracketed by CUDA events on the context stream (the headline above runs without them).
     # The dominant kernel's roofline: algorithmic flops / its summed event time.
     cp = Context(precision, device=local, stream=stream.cuda_stream, ckpt_stride=args.ckpt_stride,
-                 profile=True, gradient=args.gradient)
+                 profile=True, gradient=args.gradient, **form)
     cp.set_problem(prob)
     gp = torch.empty_like(u)
     op = torch.empty(6, dtype=torch.float64, device="cuda")
@@ -722,10 +772,11 @@ def ours_arm(args):
         # the error reference: the whole workload where the oracle takes seconds, else the sample
         ref_n = prob.N if prob.d <= 81 else nsl
         try:
-            t, nsl, ref, nev, busy = oracle_sample_time(args.workload, nsl, ref_slices=ref_n,
+            mk = f"sy.WORKLOADS[{args.workload!r}](N=n, ensemble={args.members})" if args.members > 1 else None
+            t, nsl, ref, nev, busy = oracle_sample_time(args.workload, nsl, ref_slices=ref_n, maker=mk,
                                                         exact=args.gradient == "exact", min_seconds=10.0,
                                                         threads=0)
-            t1, _, _, nev1, _ = oracle_sample_time(args.workload, nsl, min_seconds=5.0, threads=1)
+            t1, _, _, nev1, _ = oracle_sample_time(args.workload, nsl, min_seconds=5.0, threads=1, maker=mk)
             cpu = {"value": nsl * prob.E / t, "unit": UNIT, "cores": busy, "kind": "oracle",
                    "sample": f"first {nsl} of {prob.N} slices of the same workload, FP64 oracle, BLAS default "
                              f"threads on {os.cpu_count()} host cores ({busy} threads gained CPU time), "
@@ -738,8 +789,9 @@ def ours_arm(args):
                 if ref_n == prob.N:
                     c_gpu, g_gpu = float(out[0].item()), grad.cpu().numpy()
                 else:   # evaluate the same form on the sample problem
-                    q = make_problem(args.workload, ref_n)
-                    with Context(precision, device=local, stream=stream.cuda_stream, gradient=args.gradient) as cq:
+                    q = make_problem(args.workload, ref_n, args.members)
+                    with Context(precision, device=local, stream=stream.cuda_stream, gradient=args.gradient,
+                                 **form) as cq:
                         cq.set_problem(q)
                         c_gpu, g_gpu, _ = cq.evaluate(q.u)
                 g_ref = np.asarray(ref["grad"])
@@ -763,8 +815,9 @@ def ours_arm(args):
                 "config": config_of(prob, precision, info["ckpt_stride"],
                                     {"p": p_of(info), "n": info["n"], "wave_slices": info["wave_slices"],
                                      "n_waves": info["n_waves"], "gradient": args.gradient, "graph": args.graph,
+                                     "propagation": args.propagation, "exponential": args.exponential,
                                      "adjoint": {0: "reverse mode", 1: "block recursion", 2: "none (first-order)",
-                                                 3: "low-rank reverse mode"}.get(
+                                                 3: "low-rank reverse mode", 4: "state-mode reverse pass"}.get(
                                          info.get("adjoint_form"), "?")}),
                 "roofline": roof, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": mn_bytes,

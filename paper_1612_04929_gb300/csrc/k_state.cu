@@ -100,7 +100,6 @@ __global__ void k_state_x32(const DevParams* __restrict__ prm, int d, int M, int
         us[k] = make_float2(h, (float)(v - (double)h));
     }
     __syncthreads();
-    (void)prm;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < dd; idx += (size_t)gridDim.x * blockDim.x) {
         const float4 h0 = sH[idx];
         float rh = h0.x, rl = h0.z, ih = h0.y, il = h0.w;
@@ -116,7 +115,13 @@ __global__ void k_state_x32(const DevParams* __restrict__ prm, int d, int M, int
         }
         st_norm(rh, rl);
         st_norm(ih, il);
-        X[(size_t)item * xs + idx] = make_float4(ih, -rh, il, -rl);   // X = -i (s H)
+        // X = -i (s H), stored grid-split on the grid of X (2^(ex - 12)) once per slice, so the
+        // chain's products read their parts directly
+        const float mu = grid_magic(prm->ex);
+        float4 x;
+        grid_split(ih, il, mu, x.x, x.z);
+        grid_split(-rh, -rl, mu, x.y, x.w);
+        X[(size_t)item * xs + idx] = x;
     }
 }
 
@@ -209,8 +214,8 @@ __device__ __forceinline__ void st_krot(double2& a, int r) {
 // ------------------------------------------------------------------------------------------
 // serial recursion over a wave: dir 0 forward, dir 1 costate
 // ------------------------------------------------------------------------------------------
-// Matrix element of X as read by the chain: FP32 pairs (float4: re hi, im hi, re lo, im lo)
-// split on the grid 2^(ex - 12) as they are read; FP64 plain.
+// Matrix element of X as read by the chain: FP32 grid-split pairs (float4: re and im grid parts on
+// 2^(ex - 12), then the remainders; written so by k_state_x32); FP64 plain.
 template <typename R> struct XElem;
 template <> struct XElem<float> { using T = float4; };
 template <> struct XElem<double> { using T = double2; };
@@ -223,49 +228,77 @@ template <> struct XElem<double> { using T = double2; };
 template <int CB>
 __device__ __forceinline__ void st_matvec32(const float4* __restrict__ X, const float4* __restrict__ zg,
                                             float4* __restrict__ y, int d, float mu, float sgn) {
+    // RB rows per warp at a time and UB columns per lane per chunk, every load of a chunk issued
+    // before its products: the chain is latency-bound, so loads in flight matter more than issue
+    constexpr int RB = CB <= 2 ? 4 : 1, UB = 4;
+    (void)mu;                                          // X arrives grid-split
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int a = warp; a < d; a += nw) {
-        float acc[CB][4];
+    for (int a0 = warp * RB; a0 < d; a0 += nw * RB) {
+        float acc[RB][CB][4];
 #pragma unroll
-        for (int c = 0; c < CB; ++c) acc[c][0] = acc[c][1] = acc[c][2] = acc[c][3] = 0.f;
-        const float4* Xr = X + (size_t)a * d;
-        for (int b = lane; b < d; b += 32) {
-            const float4 xv = Xr[b];
-            float4 u;
-            grid_split(xv.x, xv.z, mu, u.x, u.z);
-            grid_split(xv.y, xv.w, mu, u.y, u.w);
-            const float2 uf = make_float2(u.x + u.z, u.y + u.w);
+        for (int r = 0; r < RB; ++r)
 #pragma unroll
-            for (int c = 0; c < CB; ++c) {
-                const float4 x = zg[b * CB + c];
-                float* s = acc[c];
-                s[0] = fmaf(u.x, x.x, s[0]);
-                s[0] = fmaf(-u.y, x.y, s[0]);
-                s[1] = fmaf(u.x, x.y, s[1]);
-                s[1] = fmaf(u.y, x.x, s[1]);
-                s[2] = fmaf(u.z, x.x, s[2]);
-                s[2] = fmaf(-u.w, x.y, s[2]);
-                s[2] = fmaf(uf.x, x.z, s[2]);
-                s[2] = fmaf(-uf.y, x.w, s[2]);
-                s[3] = fmaf(u.z, x.y, s[3]);
-                s[3] = fmaf(u.w, x.x, s[3]);
-                s[3] = fmaf(uf.x, x.w, s[3]);
-                s[3] = fmaf(uf.y, x.z, s[3]);
+            for (int c = 0; c < CB; ++c) acc[r][c][0] = acc[r][c][1] = acc[r][c][2] = acc[r][c][3] = 0.f;
+        for (int b0 = 0; b0 < d; b0 += 32 * UB) {
+            float4 xv[RB][UB];
+#pragma unroll
+            for (int r = 0; r < RB; ++r)
+#pragma unroll
+                for (int q = 0; q < UB; ++q) {
+                    const int a = a0 + r, b = b0 + q * 32 + lane;
+                    xv[r][q] = (a < d && b < d) ? X[(size_t)a * d + b] : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+            for (int q = 0; q < UB; ++q) {
+                const int b = b0 + q * 32 + lane;
+                if (b >= d) break;
+                float4 zq[CB];
+#pragma unroll
+                for (int c = 0; c < CB; ++c) zq[c] = zg[b * CB + c];
+#pragma unroll
+                for (int r = 0; r < RB; ++r) {
+                    const float4 u = xv[r][q];        // grid part (x, y) and remainder (z, w)
+                    const float2 uf = make_float2(u.x + u.z, u.y + u.w);
+#pragma unroll
+                    for (int c = 0; c < CB; ++c) {
+                        const float4 x = zq[c];
+                        float* s = acc[r][c];
+                        s[0] = fmaf(u.x, x.x, s[0]);
+                        s[0] = fmaf(-u.y, x.y, s[0]);
+                        s[1] = fmaf(u.x, x.y, s[1]);
+                        s[1] = fmaf(u.y, x.x, s[1]);
+                        s[2] = fmaf(u.z, x.x, s[2]);
+                        s[2] = fmaf(-u.w, x.y, s[2]);
+                        s[2] = fmaf(uf.x, x.z, s[2]);
+                        s[2] = fmaf(-uf.y, x.w, s[2]);
+                        s[3] = fmaf(u.z, x.y, s[3]);
+                        s[3] = fmaf(u.w, x.x, s[3]);
+                        s[3] = fmaf(uf.x, x.w, s[3]);
+                        s[3] = fmaf(uf.y, x.z, s[3]);
+                    }
+                }
             }
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
-            for (int c = 0; c < CB; ++c)
+            for (int r = 0; r < RB; ++r)
 #pragma unroll
-                for (int i = 0; i < 4; ++i) acc[c][i] += __shfl_xor_sync(0xffffffffu, acc[c][i], off);
+                for (int c = 0; c < CB; ++c)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) acc[r][c][i] += __shfl_xor_sync(0xffffffffu, acc[r][c][i], off);
         if (lane == 0) {
 #pragma unroll
-            for (int c = 0; c < CB; ++c) {
-                float4 v;
-                two_sum(acc[c][0], acc[c][2], v.x, v.z);
-                two_sum(acc[c][1], acc[c][3], v.y, v.w);
-                y[a * CB + c] = make_float4(sgn * v.x, sgn * v.y, sgn * v.z, sgn * v.w);
+            for (int r = 0; r < RB; ++r) {
+                const int a = a0 + r;
+                if (a >= d) break;
+#pragma unroll
+                for (int c = 0; c < CB; ++c) {
+                    float4 v;
+                    two_sum(acc[r][c][0], acc[r][c][2], v.x, v.z);
+                    two_sum(acc[r][c][1], acc[r][c][3], v.y, v.w);
+                    y[a * CB + c] = make_float4(sgn * v.x, sgn * v.y, sgn * v.z, sgn * v.w);
+                }
             }
         }
     }
@@ -273,27 +306,52 @@ __device__ __forceinline__ void st_matvec32(const float4* __restrict__ X, const 
 template <int CB>
 __device__ __forceinline__ void st_matvec64(const double2* __restrict__ X, const double2* __restrict__ z,
                                             double2* __restrict__ y, int d, double sgn) {
+    constexpr int RB = CB <= 2 ? 4 : 1, UB = 4;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int a = warp; a < d; a += nw) {
-        double2 acc[CB];
+    for (int a0 = warp * RB; a0 < d; a0 += nw * RB) {
+        double2 acc[RB][CB];
 #pragma unroll
-        for (int c = 0; c < CB; ++c) acc[c] = make_double2(0.0, 0.0);
-        const double2* Xr = X + (size_t)a * d;
-        for (int b = lane; b < d; b += 32) {
-            const double2 xv = Xr[b];
+        for (int r = 0; r < RB; ++r)
 #pragma unroll
-            for (int c = 0; c < CB; ++c) cfma(acc[c], xv, z[b * CB + c]);
+            for (int c = 0; c < CB; ++c) acc[r][c] = make_double2(0.0, 0.0);
+        for (int b0 = 0; b0 < d; b0 += 32 * UB) {
+            double2 xv[RB][UB];
+#pragma unroll
+            for (int r = 0; r < RB; ++r)
+#pragma unroll
+                for (int q = 0; q < UB; ++q) {
+                    const int a = a0 + r, b = b0 + q * 32 + lane;
+                    xv[r][q] = (a < d && b < d) ? X[(size_t)a * d + b] : make_double2(0.0, 0.0);
+                }
+#pragma unroll
+            for (int q = 0; q < UB; ++q) {
+                const int b = b0 + q * 32 + lane;
+                if (b >= d) break;
+#pragma unroll
+                for (int c = 0; c < CB; ++c) {
+                    const double2 zz = z[b * CB + c];
+#pragma unroll
+                    for (int r = 0; r < RB; ++r) cfma(acc[r][c], xv[r][q], zz);
+                }
+            }
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
-            for (int c = 0; c < CB; ++c) {
-                acc[c].x += __shfl_xor_sync(0xffffffffu, acc[c].x, off);
-                acc[c].y += __shfl_xor_sync(0xffffffffu, acc[c].y, off);
-            }
+            for (int r = 0; r < RB; ++r)
+#pragma unroll
+                for (int c = 0; c < CB; ++c) {
+                    acc[r][c].x += __shfl_xor_sync(0xffffffffu, acc[r][c].x, off);
+                    acc[r][c].y += __shfl_xor_sync(0xffffffffu, acc[r][c].y, off);
+                }
         if (lane == 0)
 #pragma unroll
-            for (int c = 0; c < CB; ++c) y[a * CB + c] = make_double2(sgn * acc[c].x, sgn * acc[c].y);
+            for (int r = 0; r < RB; ++r) {
+                const int a = a0 + r;
+                if (a >= d) break;
+#pragma unroll
+                for (int c = 0; c < CB; ++c) y[a * CB + c] = make_double2(sgn * acc[r][c].x, sgn * acc[r][c].y);
+            }
     }
 }
 

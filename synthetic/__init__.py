@@ -326,7 +326,7 @@ def transmon_cnot(seed: int = 7000, N: int = 250, T: float = 10.0, levels: int =
 
 
 def cat_state(seed: int = 8000, N: int = 8000, dt: float = 0.005, nq: int = 7, nr: int = 22,
-              lam: float = 2.0) -> Problem:
+              lam: float = 2.0, ensemble: int = 1) -> Problem:
     """Schroedinger-cat state preparation (Sec. V.C): a transmon (nq = 7 levels) coupled to a
     cavity mode (nr = 22 levels), d = 154, in the lab frame without the rotating-wave
     approximation, transmon-major basis (index = nr * t + r):
@@ -336,7 +336,8 @@ def cat_state(seed: int = 8000, N: int = 8000, dt: float = 0.005, nq: int = 7, n
     |0>_q |0>_r -> |0>_q |cat>_r with |cat> = (|lam> + |-lam>) / norm, lam = 2, built from the
     coherent states of the truncated mode and normalised (C2); occupation of transmon levels 3..6
     and cavity levels 20, 21 is penalised (C5, weight 1/N), with a small variation penalty (C4).
-    The controls start small and random."""
+    The controls start small and random.  With ensemble > 1 the members add delta_e n_b (a
+    transmon frequency offset, delta ~ N(0, (2pi*0.001)^2)) for robust control."""
     rng = np.random.default_rng(seed)
     d = nq * nr
     wq, al, wr, g = TWO_PI * 3.5, -TWO_PI * 0.225, TWO_PI * 3.9, TWO_PI * 0.1
@@ -355,8 +356,11 @@ def cat_state(seed: int = 8000, N: int = 8000, dt: float = 0.005, nq: int = 7, n
     forb = sorted({nr * t + r for t in range(3, nq) for r in range(nr)} |
                   {nr * t + r for t in range(nq) for r in (nr - 2, nr - 1)})
     u = rng.normal(0.0, TWO_PI * 0.02, size=(2, N))
-    return Problem(f"cat_state_d{d}", H0, Hk, dt, N, basis_state(d, 0), psiT, np.array(forb, np.int32),
-                   np.ones(1), default_alpha(var=1e-4, forbid=1.0 / N), u, precision="fp32")
+    delta = np.zeros(1) if ensemble <= 1 else rng.normal(0.0, TWO_PI * 0.001, size=ensemble)
+    return Problem(f"cat_state_d{d}" + (f"_E{ensemble}" if ensemble > 1 else ""), H0, Hk, dt, N,
+                   basis_state(d, 0), psiT, np.array(forb, np.int32), np.ones(1),
+                   default_alpha(var=1e-4, forbid=1.0 / N), u, delta=delta,
+                   Hdet=np.kron(nb, Ir).astype(np.complex128), precision="fp32")
 
 
 DSWEEP_D = (2, 4, 8, 16, 32, 64, 128, 256)
