@@ -277,19 +277,42 @@ def reference_arm(args):
 
 
 # ------------------------------------------------------------------ GPU arm
-def expm_flops_per_slice(d, p, n):
-    """Algorithmic flops of one slice exponential: p - 1 Horner and n squaring complex d x d
-    products at 8 d^3 real flops each."""
-    return (p - 1 + n) * 8.0 * d ** 3
+def ps_top(p):
+    """Top block of the Paterson-Stockmeyer form (blocks of three Taylor terms)."""
+    return p // 3 - 1 if (p % 3 == 0 and p >= 3) else p // 3
 
 
-def adj_flops_per_slice(form, d, p, n, S):
-    """Algorithmic flops of one slice's adjoint: reverse mode 2 products per forward product plus
-    Ubar = G Psi^dag; block recursion 3; low-rank reverse mode (cotangent as d x r factors,
-    r = 2^n S): 2 d x d by d x r products per squaring level (r doubling from S), 3 per Horner step
-    and one final rank-r update."""
+def expm_products(p, n, scheme=0):
+    """Complex d x d products of one slice exponential: Horner p - 1 steps (scheme 0), or
+    Paterson-Stockmeyer X^2, X^3 and one chain product per block below the top (scheme 1); then
+    n squarings."""
+    if scheme == 1:
+        return (p >= 2) + (p >= 3) + ps_top(p) + n
+    return p - 1 + n
+
+
+def expm_flops_per_slice(d, p, n, scheme=0):
+    """Algorithmic flops of one slice exponential at 8 d^3 real flops per complex product."""
+    return expm_products(p, n, scheme) * 8.0 * d ** 3
+
+
+def adj_flops_per_slice(form, d, p, n, S, scheme=0):
+    """Algorithmic flops of one slice's adjoint.  Horner (scheme 0): reverse mode 2 products per
+    forward product plus Ubar = G Psi^dag; block recursion 3; low-rank reverse mode (cotangent as
+    d x r factors, r = 2^n S): 2 d x d by d x r products per squaring level (r doubling from S), 3
+    per Horner step and one final rank-r update.  Paterson-Stockmeyer (scheme 1): reverse mode
+    2 per squaring and chain product plus the four power products (two when p = 2); low-rank:
+    the same squaring levels, 3 d x d by d x r per chain product, the rank-r updates of the top
+    block and of the X and X^2 cotangents, and the dense power products."""
+    r = S << n
+    if scheme == 1 and form in (0, 3):
+        powers = 2 * (p >= 3) + 2 * (p >= 2)
+        qt = ps_top(p)
+        if form == 0:
+            return 8.0 * d ** 3 * (2 * n + 2 * qt + powers) + 8.0 * d * d * S
+        updates = 2 + (1 if (p % 3 == 0 and p >= 3) else 0)
+        return 8.0 * d * d * (2 * S * ((1 << n) - 1) + 3 * qt * r + updates * r) + 8.0 * d ** 3 * powers
     if form == 3:
-        r = S << n
         return 8.0 * d * d * (2 * S * ((1 << n) - 1) + 3 * (p - 1) * r + r)
     k = 2 if form == 0 else 3
     return k * expm_flops_per_slice(d, p, n) + 8.0 * d * d * S
@@ -320,9 +343,10 @@ def roofline_of(prob, precision, info, prof, K, peaks, traffic_key=None):
     d, p, n = prob.d, info["p"], info["n"]
     if info["kernel_path"] == 2:
         return state_roofline(prob, precision, info, prof, K, peaks)
-    per_slice = {"expm_fwd": expm_flops_per_slice(d, p, n),
-                 "expm_fwd (recompute)": expm_flops_per_slice(d, p, n),
-                 "expm_adj": adj_flops_per_slice(info.get("adjoint_form", 1), d, p, n, prob.S)}
+    scheme = info.get("taylor_scheme", 0)
+    per_slice = {"expm_fwd": expm_flops_per_slice(d, p, n, scheme),
+                 "expm_fwd (recompute)": expm_flops_per_slice(d, p, n, scheme),
+                 "expm_adj": adj_flops_per_slice(info.get("adjoint_form", 1), d, p, n, prob.S, scheme)}
     if info.get("adjoint_form") == 2:   # first-order gradient: no adjoint exponential
         per_slice.pop("expm_adj")
     cands = {k: v for k, v in prof.items() if k in per_slice}

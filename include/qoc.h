@@ -77,15 +77,16 @@ typedef struct qoc_options {
     double tol;           /* bound on the Taylor remainder per slice after squaring; <= 0: default
                              (1e-15 FP64, 1e-8 otherwise) */
     double theta_max;     /* n is the least n >= 0 with theta / 2^n <= theta_max; <= 0: default
-                             (0.25 FP64; FP32 forms: 0.5 for d <= 68, the per-slice kernels, and
-                             1.0 for larger d) */
+                             (0.25 FP64; FP32 forms: 2 with the Paterson-Stockmeyer form on the
+                             per-slice path (d <= 57), 0.5 with Horner there (d <= 68), 1.0 for
+                             larger d) */
     int ckpt_stride;      /* slices between stored checkpoints of the propagated block Psi
                              (0: ceil(sqrt(N))).  The backward sweep regenerates Psi_j and U_j
                              between checkpoints instead of storing all N of them. */
     int device;           /* CUDA device ordinal */
     void* stream;         /* cudaStream_t to run on (cudaStreamLegacy = (void*)1 selects the legacy
                              default stream); NULL: the context creates its own stream */
-    int p_override;       /* >= 1 forces the Taylor order p (diagnostics); <= 0: heuristic */
+    int p_override;       /* >= 1 forces the Taylor order p, at most 40 (diagnostics); <= 0: heuristic */
     int n_override;       /* >= 0 forces the squaring count n (diagnostics); < 0: heuristic */
     int profile;          /* != 0: bracket every kernel launch with CUDA events (qoc_get_profile) */
     int wave_slices;      /* slices whose propagators are held at once (one parallel launch),
@@ -146,6 +147,15 @@ typedef struct qoc_options {
                              p 2^n.  State mode only (QOC_ERR_UNSUPPORTED otherwise); the gradient is
                              the exact derivative of that polynomial map; qoc_info.p reports the
                              degree.  QOC_ERR_RANGE if the degree would exceed 96. */
+    int taylor_scheme;    /* how the Taylor polynomial of Eq. 10 is evaluated.  QOC_TAYLOR_AUTO (0,
+                             default): the Paterson-Stockmeyer form (blocks of three terms,
+                             T = B_0 + X^3 (B_1 + X^3 (B_2 + ...)), about p / 3 + 2 matrix products
+                             instead of p - 1) on the FP32 per-slice path (d <= 57), whose default
+                             theta_max is then 2 (fewer squarings), with its reverse-mode adjoints;
+                             Horner everywhere else.  QOC_TAYLOR_HORNER (1): Horner on every path
+                             (theta_max default 0.5 there).  The polynomial, its truncation and the
+                             gradient's definition are the same; qoc_info.taylor_scheme reports the
+                             form used. */
 } qoc_options;
 
 enum { QOC_SWEEP_AUTO = 0, QOC_SWEEP_SERIAL = 1, QOC_SWEEP_SCAN = 2 };
@@ -153,6 +163,7 @@ enum { QOC_GRAD_EXACT = 0, QOC_GRAD_FIRST_ORDER = 1 };
 enum { QOC_ADJ_AUTO = 0, QOC_ADJ_RECOMPUTE = 1 };
 enum { QOC_PROP_UNITARY = 0, QOC_PROP_STATE = 1 };
 enum { QOC_EXP_TAYLOR = 0, QOC_EXP_CHEBYSHEV = 1 };
+enum { QOC_TAYLOR_AUTO = 0, QOC_TAYLOR_HORNER = 1 };
 
 /* Information about the last evaluation (reading it synchronises the context stream). */
 typedef struct qoc_info {
@@ -170,6 +181,7 @@ typedef struct qoc_info {
                              (Eq. 11, no adjoint exponential), 3 low-rank reverse mode (the cotangent
                              kept as d x r factors, r = 2^n S; small S, per-slice kernels), 4 the
                              state mode's reverse pass over its matrix-vector chain */
+    int taylor_scheme;    /* 0 Horner, 1 Paterson-Stockmeyer (see qoc_options.taylor_scheme) */
 } qoc_info;
 
 /* Per-kernel timings gathered while qoc_options.profile is set: for each kernel class the number

@@ -49,26 +49,20 @@ cudaError_t launch_norms(const double2* mats, int count, int d, double* norms, c
     return cudaGetLastError();
 }
 
-__global__ void k_theta(const double* __restrict__ u, int M, int N, const double* __restrict__ norms,
-                        const double* __restrict__ delta, int E, double dt, double theta_max, double tol,
-                        int p_override, int n_override, DevParams* __restrict__ prm) {
-    __shared__ double red[32];
-    double best = 0.0;
-    for (int j = threadIdx.x; j < N; j += blockDim.x) {
-        double s = 0.0;
-        for (int k = 0; k < M; ++k) s += fabs(u[(size_t)k * N + j]) * norms[1 + k];
-        best = fmax(best, s);
-    }
-    for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
-    __syncthreads();
-    if (threadIdx.x != 0) return;
-    prm->fin_count = 0;   // the final reduction of this evaluation counts its blocks from zero
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) best = fmax(best, red[w]);
-    double dmax = 0.0;
-    if (delta)
-        for (int e = 0; e < E; ++e) dmax = fmax(dmax, fabs(delta[e]));
-    const double theta = dt * (norms[0] + dmax * norms[M + 1] + best);
+// smallest e with 2^e >= b (clamped to [-100, 100]; -100 for b <= 0)
+__device__ __forceinline__ int grid_exp(double b) {
+    if (!(b > 0.0)) return -100;
+    if (!(b < 1e30)) return 100;
+    int e = 0;
+    const double f = frexp(b, &e);   // b = f 2^e, f in [0.5, 1)
+    if (f == 0.5) --e;
+    return e < -100 ? -100 : (e > 100 ? 100 : e);
+}
+
+// (p, n) and the split exponential's parameters from the norm bound; thread 0 sets the scalars
+// and returns ts = theta / 2^n (negative for a non-finite theta)
+__device__ double pick_orders(double theta, double theta_max, double tol, int p_override, int n_override,
+                              DevParams* __restrict__ prm, double dt) {
     if (!isfinite(theta)) {   // a NaN or Inf control (device input): flag it, keep the work small
         prm->m_split = 1;
         prm->theta = theta;
@@ -76,8 +70,8 @@ __global__ void k_theta(const double* __restrict__ u, int M, int N, const double
         prm->n = 0;
         prm->s = dt;
         prm->err = kErrNonfinite;
-        prm->ex = prm->ez = prm->eu = 0;
-        return;
+        prm->ex = prm->ez = prm->eu = prm->e2 = prm->e3 = 0;
+        return -1.0;
     }
     int n = 0;
     while (ldexp(theta, -n) > theta_max && n < 1000) ++n;
@@ -97,7 +91,7 @@ __global__ void k_theta(const double* __restrict__ u, int M, int N, const double
         fact *= (double)(p + 1);
         pw *= ts;
     }
-    if (p_override >= 1) { p = p_override; err &= ~kErrRange; }
+    if (p_override >= 1) { p = p_override < kPMax ? p_override : kPMax; err &= ~kErrRange; }
     // A rounding error e made in Horner step i + 1 reaches T = Z_1 multiplied by at most
     // ts^i / i! (the X / i' factors of steps i..1).  Steps i <= m need the hi+lo pair; beyond m
     // the factor is below 2^-6 and plain FP32 is exact enough.
@@ -121,24 +115,77 @@ __global__ void k_theta(const double* __restrict__ u, int M, int N, const double
         }
         rem_t = pt / fp / (1.0 - ts / (p + 2.0));
     }
-    auto grid_exp = [](double b) {
-        if (!(b > 0.0)) return -100;
-        if (!(b < 1e30)) return 100;
-        int e = 0;
-        const double f = frexp(b, &e);   // b = f 2^e, f in [0.5, 1)
-        if (f == 0.5) --e;
-        return e < -100 ? -100 : (e > 100 ? 100 : e);
-    };
     prm->ex = grid_exp(ts);
     prm->ez = grid_exp(1.0625 * exp(ts));
     const double rn = ldexp(rem_t, n);   // (1 + R)^(2^n) <= 1 + 2^(n+1) R while 2^n R <= 1/2
     prm->eu = grid_exp(1.0625 * (rn <= 0.5 ? 1.0 + 2.0 * rn : exp(ldexp(log1p(rem_t), n))));
+    prm->e2 = grid_exp(1.0625 * ts * ts);        // ||X^2||_2 <= ts^2, ||X^3||_2 <= ts^3
+    prm->e3 = grid_exp(1.0625 * ts * ts * ts);
     prm->m_split = m;
     prm->theta = theta;
     prm->p = p;
     prm->n = n;
     prm->s = ldexp(dt, -n);
     prm->err = err;
+    return ts;
+}
+
+__global__ void k_theta(const double* __restrict__ u, int M, int N, const double* __restrict__ norms,
+                        const double* __restrict__ delta, int E, double dt, double theta_max, double tol,
+                        int p_override, int n_override, DevParams* __restrict__ prm) {
+    __shared__ double red[32];
+    __shared__ double sh_ts;
+    double best = 0.0;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        double s = 0.0;
+        for (int k = 0; k < M; ++k) s += fabs(u[(size_t)k * N + j]) * norms[1 + k];
+        best = fmax(best, s);
+    }
+    for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        prm->fin_count = 0;   // the final reduction of this evaluation counts its blocks from zero
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) best = fmax(best, red[w]);
+        double dmax = 0.0;
+        if (delta)
+            for (int e = 0; e < E; ++e) dmax = fmax(dmax, fabs(delta[e]));
+        const double theta = dt * (norms[0] + dmax * norms[M + 1] + best);
+        sh_ts = pick_orders(theta, theta_max, tol, p_override, n_override, prm, dt);
+    }
+    __syncthreads();
+    // Paterson-Stockmeyer tables, one entry per thread: the coefficients 1/k! (k <= p, zero beyond)
+    // as FP32 pairs, and the grid exponent of each chain matrix W_q = sum_{k >= 3q} X^(k - 3q) / k!,
+    // ||W_q||_2 <= sum_{k = 3q}^{p} ts^(k - 3q) / k! (1/16 margin); W_0 = T takes eu
+    const int t = threadIdx.x;
+    const double ts = sh_ts;
+    const bool ok = ts >= 0.0;
+    const int p = ok ? prm->p : 0;
+    if (t < kPsCoefs) {
+        double c = 0.0;
+        if (ok && t <= p) {
+            double f = 1.0;
+            for (int k = 2; k <= t; ++k) f *= k;
+            c = 1.0 / f;
+        }
+        const float h = (float)c;
+        prm->ch[t] = h;
+        prm->cl[t] = (float)(c - (double)h);
+    }
+    if (t < kPsMaxBlocks) {
+        int e = ok ? prm->eu : 0;
+        if (ok && t > 0) {
+            double f = 1.0, pw = 1.0, b = 0.0;
+            for (int k = 2; k < 3 * t; ++k) f *= k;   // (3t - 1)!
+            for (int k = 3 * t; k <= p; ++k) {
+                f *= k;
+                b += pw / f;
+                pw *= ts;
+            }
+            e = grid_exp(1.0625 * b);
+        }
+        prm->ew[t] = e;
+    }
 }
 
 cudaError_t launch_theta(const double* u, int M, int N, const double* norms, const double* delta, int E,

@@ -33,36 +33,9 @@
 // padding rows and columns are kept at zero.
 #include "qoc_device.cuh"
 #include "qoc_internal.h"
+#include "qoc_slice.cuh"
 
 namespace qoc {
-
-template <typename C, int MT>
-__device__ __forceinline__ void mm_acc(C (&acc)[MT][MT], const C* __restrict__ A,
-                                       const C* __restrict__ B, int kd, int LD, int ty, int tx, int G) {
-    // one pointer per operand row / column: A rows advance by k, B columns step down one row
-    const C* pa[MT];
-    const C* pb[MT];
-#pragma unroll
-    for (int i = 0; i < MT; ++i) {
-        pa[i] = A + (ty + G * i) * LD;
-        pb[i] = B + tx + G * i;
-    }
-#pragma unroll 2
-    for (int k = 0; k < kd; ++k) {
-        C a[MT], b[MT];
-#pragma unroll
-        for (int i = 0; i < MT; ++i) a[i] = pa[i][k];
-#pragma unroll
-        for (int i = 0; i < MT; ++i) {
-            b[i] = *pb[i];
-            pb[i] += LD;
-        }
-#pragma unroll
-        for (int i = 0; i < MT; ++i)
-#pragma unroll
-            for (int jj = 0; jj < MT; ++jj) cfma(acc[i][jj], a[i], b[jj]);
-    }
-}
 
 // acc11 += A11 B11 ;  acc12 += A11 B12 + A12 B11   (block-upper-triangular product)
 template <typename C, int MT>
@@ -91,72 +64,6 @@ __device__ __forceinline__ void mm_block(C (&acc11)[MT][MT], C (&acc12)[MT][MT],
                 cfma(acc12[i][jj], a1[i], b2[jj]);
                 cfma(acc12[i][jj], a2[i], b1[jj]);
             }
-    }
-}
-
-template <typename C, int MT>
-__device__ __forceinline__ void zero_acc(C (&acc)[MT][MT]) {
-#pragma unroll
-    for (int i = 0; i < MT; ++i)
-#pragma unroll
-        for (int jj = 0; jj < MT; ++jj) acc[i][jj] = czero<C>();
-}
-
-// out = diag * I + scale * acc on the d x d block, zero in the padding.
-template <typename C, typename R, int MT>
-__device__ __forceinline__ void store_acc(C* __restrict__ out, const C (&acc)[MT][MT], R scale,
-                                          R diag, int d, int LD, int ty, int tx, int G) {
-#pragma unroll
-    for (int i = 0; i < MT; ++i)
-#pragma unroll
-        for (int jj = 0; jj < MT; ++jj) {
-            const int r = ty + G * i, c = tx + G * jj;
-            C v = czero<C>();
-            if (r < d && c < d) {
-                v.x = acc[i][jj].x * scale + (r == c ? diag : R(0));
-                v.y = acc[i][jj].y * scale;
-            }
-            out[r * LD + c] = v;
-        }
-}
-
-// dst (d x d, global) = conjugate transpose of the d x d block of src (shared, leading dim LD)
-template <typename C>
-__device__ __forceinline__ void store_ct(C* __restrict__ dst, const C* __restrict__ src, int d, int LD) {
-    for_rc(d, d, [&](int idx, int a, int b) {
-        C v = src[b * LD + a];
-        v.y = -v.y;
-        dst[idx] = v;
-    });
-}
-
-// Assemble H_j (+ delta_e Hdet) and write X = -i s H into padded shared memory (rows/cols >= d
-// zero).  us: the M control values of this slice (shared).
-template <typename C, typename R>
-__device__ __forceinline__ void assemble_X(C* __restrict__ X, int d, int D, int LD, int M,
-                                           const C* __restrict__ H0, const C* __restrict__ Hk,
-                                           const C* __restrict__ Hdet, R de, const R* us, R s) {
-    const size_t dd = (size_t)d * d;
-    for (int idx = threadIdx.x; idx < D * D; idx += blockDim.x) {
-        const int a = idx / D, b = idx - a * D;
-        C x = czero<C>();
-        if (a < d && b < d) {
-            const int o = a * d + b;
-            C h = H0[o];
-            for (int k = 0; k < M; ++k) {
-                const C hk = Hk[k * dd + o];
-                h.x = fma(us[k], hk.x, h.x);
-                h.y = fma(us[k], hk.y, h.y);
-            }
-            if (Hdet) {
-                const C hd = Hdet[o];
-                h.x = fma(de, hd.x, h.x);
-                h.y = fma(de, hd.y, h.y);
-            }
-            x.x = s * h.y;      // -i s (hr + i hi) = s hi - i s hr
-            x.y = -s * h.x;
-        }
-        X[a * LD + b] = x;
     }
 }
 
@@ -237,7 +144,7 @@ k_expm_adj(const DevParams* __restrict__ prm, SysView<R> sys, StateView<R> st, i
            const C_t<R>* __restrict__ states, const C_t<R>* __restrict__ Gbuf, int wmax,
            double* __restrict__ gpart, ZStore<R> zs, int G) {
     using C = C_t<R>;
-    if (zs.Z && prm->p - 1 + prm->n <= zs.cap) return;   // k_expm_adj_rev handles this evaluation
+    if (zs_fits(zs, prm->p, prm->n)) return;   // a reverse-mode kernel handles this evaluation
     const int D = G * MT, LD = D + 1, SZ = D * LD;
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ R us[kMaxControls];
@@ -383,7 +290,7 @@ k_expm_adj_lr(const DevParams* __restrict__ prm, SysView<R> sys, StateView<R> st
               double* __restrict__ gpart, ZStore<R> zs, int G) {
     using C = C_t<R>;
     const int p = prm->p, n = prm->n;
-    if (!(zs.Z && p - 1 + n <= zs.cap)) return;
+    if (zs.ps || !zs_fits(zs, p, n)) return;
     const int d = sys.d, Sr = st.S, cb = st.cb, ps = st.pstride;
     if (!adj_lowrank_applies(Sr, n, d)) return;
     const int D = G * MT, LD = D + 1, SZ = D * LD, RL = kLrMax;
@@ -558,7 +465,7 @@ k_expm_adj_rev(const DevParams* __restrict__ prm, SysView<R> sys, StateView<R> s
                double* __restrict__ gpart, ZStore<R> zs, int G) {
     using C = C_t<R>;
     const int p = prm->p, n = prm->n;
-    if (!(zs.Z && p - 1 + n <= zs.cap)) return;           // k_expm_adj recomputes instead
+    if (zs.ps || !zs_fits(zs, p, n)) return;              // another kernel handles this evaluation
     if (adj_lowrank_applies(st.S, n, sys.d)) return;        // k_expm_adj_lr handles this evaluation
     const int D = G * MT, LD = D + 1, SZ = D * LD;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -761,6 +668,9 @@ static cudaError_t launch_adj_mt(const DevParams* prm, const SysView<R>& sys, co
     err = cudaGetLastError();
     *launches = 1;
     if (err != cudaSuccess || !zs.Z) return err;
+    if constexpr (sizeof(R) == 4) {
+        if (zs.ps) return launch_expm_adj_ps(prm, sys, sv, j0, wlen, E, states, Gbuf, wmax, gpart, zs, st, launches);
+    }
     const size_t smem_r = fused_smem<R>(sys.d, 5, adj_wide<R>());
     err = cudaFuncSetAttribute(k_expm_adj_rev<R, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r);
     if (err != cudaSuccess) return err;

@@ -94,6 +94,32 @@ __device__ __forceinline__ void pair_fma(float& hi, float& lo, float2 u, float b
     lo += r + e;
 }
 
+// X_ab = -i s H_ab (element o = a d + b) in pair arithmetic from the pairs s H_0, s H_k (times the
+// control pairs us[k]) and s H_det (times us[M]; Hd = nullptr: no ensemble term)
+__device__ __forceinline__ void x_pair(const float4* __restrict__ H0, const float4* __restrict__ Hk,
+                                       const float4* __restrict__ Hd, size_t dd, int M, const float2* us, int o,
+                                       float& xrh, float& xrl, float& xih, float& xil) {
+    const float4 h0 = H0[o];
+    float rh = h0.x, rl = h0.z, ih = h0.y, il = h0.w;
+    for (int k = 0; k < M; ++k) {
+        const float4 hk = Hk[k * dd + o];
+        pair_fma(rh, rl, us[k], hk.x, hk.z);
+        pair_fma(ih, il, us[k], hk.y, hk.w);
+    }
+    if (Hd) {
+        const float4 hd = Hd[o];
+        pair_fma(rh, rl, us[M], hd.x, hd.z);
+        pair_fma(ih, il, us[M], hd.y, hd.w);
+    }
+    df_norm(rh, rl);
+    df_norm(ih, il);
+    // X = -i (s H): re X = im(s H), im X = -re(s H)
+    xrh = ih;
+    xrl = il;
+    xih = -rh;
+    xil = -rl;
+}
+
 // s H_0, s H_1 .. s H_M, s H_det (s = dt / 2^n) as FP32 pairs (re_hi, im_hi, re_lo, im_lo), once
 // per evaluation: the slice assembly above then needs no FP64 arithmetic
 __global__ void k_split_scale(const DevParams* __restrict__ prm, const double2* __restrict__ H64, size_t count,
@@ -178,23 +204,8 @@ k_expm_fwd_split(const DevParams* __restrict__ prm, SysView<float> sys, const fl
         const int a = idx / D, b = idx - a * D;
         float4 x = make_float4(0.f, 0.f, 0.f, 0.f), z = x;
         if (a < d && b < d) {
-            const int o = a * d + b;
-            const float4 h0 = H0[o];
-            float rh = h0.x, rl = h0.z, ih = h0.y, il = h0.w;
-            for (int k = 0; k < M; ++k) {
-                const float4 hk = Hk[k * dd + o];
-                pair_fma(rh, rl, us[k], hk.x, hk.z);
-                pair_fma(ih, il, us[k], hk.y, hk.w);
-            }
-            if (sys.Hdet) {
-                const float4 hd = Hd[o];
-                pair_fma(rh, rl, us[M], hd.x, hd.z);
-                pair_fma(ih, il, us[M], hd.y, hd.w);
-            }
-            df_norm(rh, rl);
-            df_norm(ih, il);
-            // X = -i (s H): re X = im(s H), im X = -re(s H)
-            float xrh = ih, xrl = il, xih = -rh, xil = -rl;
+            float xrh, xrl, xih, xil;
+            x_pair(H0, Hk, sys.Hdet ? Hd : nullptr, dd, M, us, a * d + b, xrh, xrl, xih, xil);
             grid_split(xrh, xrl, mx, x.x, x.z);
             grid_split(xih, xil, mx, x.y, x.w);
             if (p > 1) {
@@ -336,6 +347,288 @@ cudaError_t launch_expm_fwd_split(const DevParams* prm, const SysView<float>& sy
         case 4: return launch_split_mt<4>(prm, sys, sH, j0, wlen, E, Ubuf, ustride, wmax, zs, tl.G, st);
         default: return cudaErrorInvalidValue;
     }
+}
+
+
+// ------------------------------------------------------------------------------------------
+// Paterson-Stockmeyer form (block size 3) of the same split exponential.  The order-p Taylor
+// polynomial of Eq. 10 is regrouped as T = sum_q Y^q B_q with Y = X^3 and
+// B_q = c_3q I + c_3q+1 X + c_3q+2 X^2 (c_k = 1/k!, zero for k > p), and evaluated from the top
+// block down, W_q = B_q + Y W_{q+1}: two products for X^2 and X^3 and about p / 3 chain products
+// instead of p - 1 Horner steps.  The series and its truncation are unchanged; only the order of
+// the products differs, so a larger theta_max (fewer squarings) pays.
+// Precision follows the Horner form's rule: a rounding error in W_q reaches T multiplied by at
+// most ts^3q / (3q)! (the same factor as an error in Horner's Z_{3q+1}), so chain products with
+// 3q + 1 <= m_split are split products and the others plain FP32.  X^2, X^3, T and the squarings
+// are always split; the B_q terms are added in pair arithmetic with the coefficients as FP32
+// pairs.  Every operand is grid-split on its own norm bound (e2, e3, ew[q] from the order pick).
+// Shared memory holds X, X^2, X^3 and W (written in place after a second barrier): four split
+// matrices, so d <= ps_max_d().
+// ------------------------------------------------------------------------------------------
+
+// (hi, lo) + (ch + cl), pair arithmetic
+__device__ __forceinline__ void df_addc(float& hi, float& lo, float2 c) {
+    float s, r;
+    two_sum(hi, c.x, s, r);
+    hi = s;
+    lo += r + c.y;
+}
+
+// a value given as pairs (re, im) in the form its reader takes: grid-split on magic, or the full
+// FP32 value in (.x, .y) with zero (.z, .w) when magic == 0 (the operand of a plain product)
+__device__ __forceinline__ float4 ps_form(float rh, float rl, float ih, float il, float magic) {
+    float4 v;
+    if (magic == 0.f) {
+        v = make_float4(rh + rl, ih + il, 0.f, 0.f);
+    } else {
+        grid_split(rh, rl, magic, v.x, v.z);
+        grid_split(ih, il, magic, v.y, v.w);
+    }
+    return v;
+}
+
+// (rh, rl, ih, il) += c_k0+1 X + c_k0+2 X^2 (+ c_k0 on the diagonal); x2 is read only when
+// p >= 2 (have2)
+__device__ __forceinline__ void ps_add_block(float& rh, float& rl, float& ih, float& il, const float2* cs, int k0,
+                                             bool diag, float4 x, bool have2, float4 x2) {
+    pair_fma(rh, rl, cs[k0 + 1], x.x, x.z);
+    pair_fma(ih, il, cs[k0 + 1], x.y, x.w);
+    if (have2) {
+        pair_fma(rh, rl, cs[k0 + 2], x2.x, x2.z);
+        pair_fma(ih, il, cs[k0 + 2], x2.y, x2.w);
+    }
+    if (diag) df_addc(rh, rl, cs[k0]);
+}
+
+template <int MT>
+__global__ void __launch_bounds__(512)
+k_expm_fwd_ps(const DevParams* __restrict__ prm, SysView<float> sys, const float4* __restrict__ sH, int j0,
+              float2* __restrict__ Ubuf, long long ustride, int wmax, ZStore<float> zs, int G) {
+    const int D = G * MT, LD = D + 1, SZ = D * LD;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ float2 us[kMaxControls + 1];   // u_kj and delta_e as (hi, lo) pairs
+    __shared__ float2 cs[kPsCoefs];           // 1/k! as (hi, lo) pairs
+    float4* X = reinterpret_cast<float4*>(smraw);
+    float4* P2 = X + SZ;
+    float4* P3 = P2 + SZ;
+    float4* W = P3 + SZ;
+    const int jl = blockIdx.x, e = blockIdx.y, j = j0 + jl;
+    const int tid = threadIdx.x, tx = tid % G, ty = tid / G;
+    const bool act = tid < G * G;   // the block is rounded up to whole warps
+    const int d = sys.d, M = sys.M, p = prm->p, n = prm->n;
+    for (int k = tid; k <= M; k += blockDim.x) {
+        const double v = (k < M) ? sys.u[(size_t)k * sys.N + j] : (sys.delta ? sys.delta[e] : 0.0);
+        const float h = (float)v;
+        us[k] = make_float2(h, (float)(v - (double)h));
+    }
+    for (int k = tid; k < kPsCoefs; k += blockDim.x) cs[k] = make_float2(prm->ch[k], prm->cl[k]);
+    __syncthreads();
+    const size_t dd = (size_t)d * d;
+    const int qt = ps_top(p), qs = (prm->m_split - 1) / 3;   // chain products q <= qs are split
+    const float mx = grid_magic(prm->ex), m2 = grid_magic(prm->e2), m3 = grid_magic(prm->e3);
+    const float mu = grid_magic(prm->eu);
+    // the form W_q is written in: its reader is chain product q - 1 (split iff q - 1 <= qs), or the
+    // squarings for W_0 = T
+    auto magic_w = [&](int q) { return q == 0 ? mu : (q - 1 <= qs ? grid_magic(prm->ew[q]) : 0.f); };
+    for (int idx = tid; idx < D * D; idx += blockDim.x) {   // X = -i s H_j, grid-split
+        const int a = idx / D, b = idx - a * D;
+        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (a < d && b < d) {
+            float xrh, xrl, xih, xil;
+            x_pair(sH, sH + dd, sys.Hdet ? sH + (size_t)(M + 1) * dd : nullptr, dd, M, us, a * d + b, xrh, xrl, xih,
+                   xil);
+            grid_split(xrh, xrl, mx, x.x, x.z);
+            grid_split(xih, xil, mx, x.y, x.w);
+        }
+        X[a * LD + b] = x;
+    }
+    __syncthreads();
+    float2* zst = zs_fits(zs, p, n) ? zs.Z + ((size_t)e * zs.wmax + jl) * zs.cap * zs.mstride : nullptr;
+    // the operand in a slot, rounded to FP32 and conjugate-transposed, for the adjoint
+    auto store = [&](int slot, const float4* src) {
+        float2* dst = zst + (size_t)slot * zs.mstride;
+        for_rc(d, d, [&](int idx, int a, int b) {
+            const float4 v = src[b * LD + a];
+            dst[idx] = make_float2(v.x + v.z, -(v.y + v.w));
+        });
+    };
+    if (p >= 2) {                               // X^2 = X X
+        if (act) {
+            float acc[MT][MT][4] = {};
+            mm_sl<MT>(acc, X, X, d, LD, ty, tx, G);
+            sl_store<MT>(P2, acc, 0, false, m2, d, LD, ty, tx, G);
+        }
+        __syncthreads();
+    }
+    if (p >= 3) {                               // X^3 = X^2 X
+        if (act) {
+            float acc[MT][MT][4] = {};
+            mm_sl<MT>(acc, P2, X, d, LD, ty, tx, G);
+            sl_store<MT>(P3, acc, 0, false, m3, d, LD, ty, tx, G);
+        }
+        __syncthreads();
+    }
+    {   // the top block W_qt = c_3qt I + c_3qt+1 X + c_3qt+2 X^2 + c_3qt+3 X^3, element-wise
+        const float mt = magic_w(qt);
+        for (int idx = tid; idx < D * D; idx += blockDim.x) {
+            const int a = idx / D, b = idx - a * D;
+            float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (a < d && b < d) {
+                const int o = a * LD + b;
+                float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+                ps_add_block(rh, rl, ih, il, cs, 3 * qt, a == b, X[o], p >= 2, p >= 2 ? P2[o] : w);
+                if (p >= 3) {
+                    const float4 y = P3[o];
+                    pair_fma(rh, rl, cs[3 * qt + 3], y.x, y.z);
+                    pair_fma(ih, il, cs[3 * qt + 3], y.y, y.w);
+                }
+                w = ps_form(rh, rl, ih, il, mt);
+            }
+            W[a * LD + b] = w;
+        }
+    }
+    if (zst) {
+        if (p >= 2) store(0, P2);
+        if (p >= 3) store(1, P3);
+    }
+    __syncthreads();
+    for (int q = qt - 1; q >= 0; --q) {         // W_q = B_q + X^3 W_{q+1}, in place
+        if (zst) store(2 + (qt - 1 - q), W);
+        float4 out[MT][MT];
+        if (act) {
+            const float mq = magic_w(q);
+            if (q <= qs) {
+                float acc[MT][MT][4] = {};
+                mm_sl<MT>(acc, P3, W, d, LD, ty, tx, G);
+#pragma unroll
+                for (int a = 0; a < MT; ++a)
+#pragma unroll
+                    for (int b = 0; b < MT; ++b) {
+                        const int r = ty + G * a, c = tx + G * b;
+                        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (r < d && c < d) {
+                            float rh, rl, ih, il;
+                            two_sum(acc[a][b][0], acc[a][b][2], rh, rl);
+                            two_sum(acc[a][b][1], acc[a][b][3], ih, il);
+                            ps_add_block(rh, rl, ih, il, cs, 3 * q, r == c, X[r * LD + c], true, P2[r * LD + c]);
+                            v = ps_form(rh, rl, ih, il, mq);
+                        }
+                        out[a][b] = v;
+                    }
+            } else {
+                float2 acc[MT][MT];
+#pragma unroll
+                for (int a = 0; a < MT; ++a)
+#pragma unroll
+                    for (int b = 0; b < MT; ++b) acc[a][b] = make_float2(0.f, 0.f);
+                mm_hi<MT>(acc, P3, W, d, LD, ty, tx, G);
+                const float c0 = cs[3 * q].x, c1 = cs[3 * q + 1].x, c2 = cs[3 * q + 2].x;
+#pragma unroll
+                for (int a = 0; a < MT; ++a)
+#pragma unroll
+                    for (int b = 0; b < MT; ++b) {
+                        const int r = ty + G * a, c = tx + G * b;
+                        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (r < d && c < d) {
+                            const float4 x = X[r * LD + c], y = P2[r * LD + c];
+                            float re = fmaf(c1, x.x + x.z, acc[a][b].x);
+                            float im = fmaf(c1, x.y + x.w, acc[a][b].y);
+                            re = fmaf(c2, y.x + y.z, re);
+                            im = fmaf(c2, y.y + y.w, im);
+                            if (r == c) re += c0;
+                            v = ps_form(re, 0.f, im, 0.f, mq);
+                        }
+                        out[a][b] = v;
+                    }
+            }
+        }
+        __syncthreads();   // every thread has read W
+        if (act) {
+#pragma unroll
+            for (int a = 0; a < MT; ++a)
+#pragma unroll
+                for (int b = 0; b < MT; ++b) W[(ty + G * a) * LD + tx + G * b] = out[a][b];
+        }
+        __syncthreads();
+    }
+    float4* zin = W;                            // squarings, ping-pong with the X^2 buffer
+    float4* zout = P2;
+    for (int m = 0; m < n; ++m) {
+        if (zst) store(qt + 2 + m, zin);
+        if (act) {
+            float acc[MT][MT][4] = {};
+            mm_sl<MT>(acc, zin, zin, d, LD, ty, tx, G);
+            sl_store<MT>(zout, acc, 0, false, mu, d, LD, ty, tx, G);
+        }
+        __syncthreads();
+        float4* t = zin; zin = zout; zout = t;
+    }
+    // U_j at offset 0, U_j^dag at offset ustride / 2; the pair is rounded to FP32
+    float2* U = Ubuf + ((size_t)e * wmax + jl) * ustride;
+    float2* UH = U + ustride / 2;
+    for (int idx = tid; idx < d * d; idx += blockDim.x) {
+        const int a = idx / d, b = idx - a * d;
+        const float4 z = zin[a * LD + b];
+        U[idx] = make_float2(z.x + z.z, z.y + z.w);
+        const float4 h = zin[b * LD + a];
+        UH[idx] = make_float2(h.x + h.z, -(h.y + h.w));
+    }
+}
+
+static size_t ps_smem(int d) {
+    const int D = slice_tile(d).D;
+    return (size_t)4 * D * (D + 1) * sizeof(float4);
+}
+
+int ps_max_d() {
+    for (int d = kMaxD; d >= 1; --d)
+        if (slice_tile(d).MT > 0 && ps_smem(d) <= kMaxDynSmem) return d;
+    return 0;
+}
+
+template <int MT>
+static cudaError_t launch_ps_mt(const DevParams* prm, const SysView<float>& sys, const float4* sH, int j0, int wlen,
+                                int E, float2* Ubuf, long long ustride, int wmax, const ZStore<float>& zs, int G,
+                                cudaStream_t st) {
+    const size_t smem = ps_smem(sys.d);
+    cudaError_t err = cudaFuncSetAttribute(k_expm_fwd_ps<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    k_expm_fwd_ps<MT><<<dim3(wlen, E), slice_threads(G), smem, st>>>(prm, sys, sH, j0, Ubuf, ustride, wmax, zs, G);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_expm_fwd_ps(const DevParams* prm, const SysView<float>& sys, const float4* sH, int j0, int wlen,
+                               int E, float2* Ubuf, long long ustride, int wmax, const ZStore<float>& zs,
+                               cudaStream_t st) {
+    const SliceTile tl = slice_tile(sys.d);
+    if (sys.d > ps_max_d() || !zs.ps) return cudaErrorInvalidValue;
+    switch (tl.MT) {
+        case 1: return launch_ps_mt<1>(prm, sys, sH, j0, wlen, E, Ubuf, ustride, wmax, zs, tl.G, st);
+        case 2: return launch_ps_mt<2>(prm, sys, sH, j0, wlen, E, Ubuf, ustride, wmax, zs, tl.G, st);
+        case 3: return launch_ps_mt<3>(prm, sys, sH, j0, wlen, E, Ubuf, ustride, wmax, zs, tl.G, st);
+        case 4: return launch_ps_mt<4>(prm, sys, sH, j0, wlen, E, Ubuf, ustride, wmax, zs, tl.G, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+int ps_fwd_ctas_per_sm(int d) {
+    const SliceTile tl = slice_tile(d);
+    if (tl.MT <= 0 || d > ps_max_d()) return 1;
+    const size_t smem = ps_smem(d);
+    const int thr = slice_threads(tl.G);
+    int n = 0;
+    cudaError_t e;
+    switch (tl.MT) {
+        case 1: cudaFuncSetAttribute(k_expm_fwd_ps<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_expm_fwd_ps<1>, thr, smem); break;
+        case 2: cudaFuncSetAttribute(k_expm_fwd_ps<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_expm_fwd_ps<2>, thr, smem); break;
+        case 3: cudaFuncSetAttribute(k_expm_fwd_ps<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_expm_fwd_ps<3>, thr, smem); break;
+        default: cudaFuncSetAttribute(k_expm_fwd_ps<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_expm_fwd_ps<4>, thr, smem); break;
+    }
+    return (e == cudaSuccess && n > 0) ? n : 1;
 }
 
 }  // namespace qoc

@@ -137,6 +137,7 @@ struct qoc_ctx {
     int Spad = 0, cb = 0, ncb = 0, pstride = 0, S_eff = 0;
     bool scan = false;                   // segmented-scan form of the two recursions
     double theta_max = 0.0;              // in effect (the option, or the path's default)
+    bool ps = false;                     // Paterson-Stockmeyer form of the per-slice FP32 exponential
     int nzmax = 0;                       // checkpoint segments per wave
     std::vector<int> cols;               // propagated columns (positive weight)
     size_t mstride = 0;                  // elements per matrix slot of the batched path
@@ -235,7 +236,11 @@ void plan_impl(qoc_ctx* c) {
     // default theta_max of the FP32 forms: 0.5 with the per-slice kernels (split squarings: one
     // split product fewer than 1.0 on long evolutions); 1.0 on the batched path, whose plain
     // FP32 adjoint loses accuracy with every extra squaring
-    c->theta_max = c->opt.theta_max > 0.0 ? c->opt.theta_max : (c->path_kind == 0 ? 0.5 : 1.0);
+    // The Paterson-Stockmeyer form costs about p / 3 + 2 products instead of p - 1, so a larger
+    // theta_max (fewer squarings, each a split product plus two adjoint products) pays: on the
+    // d = 40 workload theta_max = 2 (p = 14, n = 2) against Horner's 0.5 (p = 9, n = 4).
+    c->ps = split_exp<R>(c) && c->path_kind == 0 && d <= ps_max_d() && c->opt.taylor_scheme == QOC_TAYLOR_AUTO;
+    c->theta_max = c->opt.theta_max > 0.0 ? c->opt.theta_max : (c->ps ? 2.0 : (c->path_kind == 0 ? 0.5 : 1.0));
     // Columns whose weight is zero enter no cost term (every term is weighted by w_s), so they
     // are not propagated at all.
     c->cols.clear();
@@ -303,8 +308,9 @@ void plan_impl(qoc_ctx* c) {
             int sms1 = 0;
             cudaDeviceGetAttribute(&sms1, cudaDevAttrMultiProcessorCount, c->opt.device);
             const long slots_f = (long)std::max(sms1, 1) *
-                                 (split_exp<R>(c) ? split_ctas_per_sm(d) : fused_ctas_per_sm<R>(d, false));
-            const long slots_a = (long)std::max(sms1, 1) * fused_ctas_per_sm<R>(d, true);
+                                 (c->ps ? ps_fwd_ctas_per_sm(d)
+                                        : (split_exp<R>(c) ? split_ctas_per_sm(d) : fused_ctas_per_sm<R>(d, false)));
+            const long slots_a = (long)std::max(sms1, 1) * (c->ps ? ps_adj_ctas_per_sm(d) : fused_ctas_per_sm<R>(d, true));
             const bool adj = c->opt.gradient == QOC_GRAD_EXACT;
             auto rounds = [](long units, long slots) { return (units + slots - 1) / slots; };
             long best = -1;
@@ -576,7 +582,7 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
     int extra = 0;   // kernels of the batched calls beyond the one counted by L
     // stored product operands of the per-slice path (two wave sets)
     auto zstore = [&](int w) {
-        ZStore<R> z{nullptr, kZCap, c->zmstride, W};
+        ZStore<R> z{nullptr, kZCap, c->zmstride, W, c->ps ? 1 : 0};
         if (c->Zbuf.p) z.Z = c->Zbuf.as<C>() + (size_t)(w & 1) * E * W * kZCap * c->zmstride;
         return z;
     };
@@ -589,6 +595,9 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
             return e;
         }
         if constexpr (sizeof(R) == 4) {
+            if (c->ps)
+                return launch_expm_fwd_ps(prm, sys, c->sH.as<float4>(), j0, wlen, E, Ub(w), c->ustride, W, zstore(w),
+                                          st);
             if (split)
                 return launch_expm_fwd_split(prm, sys, c->sH.as<float4>(), j0, wlen, E, Ub(w), c->ustride, W,
                                              zstore(w), st);
@@ -1087,7 +1096,8 @@ qoc_status qoc_create(qoc_ctx** out, const qoc_options* opt) {
         o.sweep > QOC_SWEEP_SCAN || o.gradient < QOC_GRAD_EXACT || o.gradient > QOC_GRAD_FIRST_ORDER ||
         o.fault_inject < 0 || o.fault_inject > 1 || o.adjoint < QOC_ADJ_AUTO || o.adjoint > QOC_ADJ_RECOMPUTE ||
         o.reversal < 0 || o.reversal > 1 || o.propagation < QOC_PROP_UNITARY || o.propagation > QOC_PROP_STATE ||
-        o.exponential < QOC_EXP_TAYLOR || o.exponential > QOC_EXP_CHEBYSHEV)
+        o.exponential < QOC_EXP_TAYLOR || o.exponential > QOC_EXP_CHEBYSHEV || o.taylor_scheme < QOC_TAYLOR_AUTO ||
+        o.taylor_scheme > QOC_TAYLOR_HORNER)
         return QOC_ERR_ARG;
     if (o.exponential == QOC_EXP_CHEBYSHEV && o.propagation != QOC_PROP_STATE) return QOC_ERR_UNSUPPORTED;
     // reversal regenerates states through the stored propagators, whose FP32 rounding would
@@ -1356,9 +1366,10 @@ qoc_status qoc_get_info(qoc_ctx* ctx, qoc_info* info) {
     if (ctx->opt.gradient == QOC_GRAD_FIRST_ORDER) info->adjoint_form = 2;
     else if (ctx->path_kind == 2) info->adjoint_form = 4;
     else if (ctx->path_kind == 1) info->adjoint_form = ctx->last_big_rev ? 0 : 1;
-    else if (ctx->Zbuf.p && info->p - 1 + info->n <= kZCap)
+    else if (ctx->Zbuf.p && (ctx->ps ? ps_slots(info->p, info->n) : info->p - 1 + info->n) <= kZCap)
         info->adjoint_form = adj_lowrank_applies(ctx->S_eff, info->n, ctx->d) ? 3 : 0;
     else info->adjoint_form = 1;
+    info->taylor_scheme = ctx->planned && ctx->ps ? 1 : 0;
     if (ctx->planned && ctx->path_kind == 2 && ctx->opt.exponential == QOC_EXP_CHEBYSHEV) {
         info->p = ctx->cheb_host.K;       // the Chebyshev degree, no squaring
         info->n = 0;

@@ -34,6 +34,9 @@ template <typename C> __device__ __forceinline__ void cfma_bcj(C& acc, const C a
     acc.y = fma(-a.x, b.y, acc.y);
 }
 
+constexpr int kPsCoefs = 44;       // Taylor coefficients 1/k!, k = 0 .. kPMax + 3
+constexpr int kPsMaxBlocks = 15;   // blocks of three terms, q = 0 .. kPMax / 3 + 1
+
 // Per-evaluation scalars produced on the device by the norm kernel and read by every kernel.
 struct DevParams {
     double theta;   // dt * max_j ||H_j||_1 bound (FP64)
@@ -45,6 +48,12 @@ struct DevParams {
     // grid exponents of the split FP32 exponential: 2^e bounds the row and column 2-norms of
     // X (ex), of the Horner matrices Z_i, i >= 2 (ez), and of T and its squarings (eu)
     int ex, ez, eu;
+    // Paterson-Stockmeyer form of the split exponential (block size 3): 2^e2, 2^e3 bound the 2-norms
+    // of X^2 and X^3, 2^ew[q] that of the chain matrix W_q (ew[0] = eu: W_0 = T); the Taylor
+    // coefficients 1/k! as FP32 pairs (ch + cl), zero for k > p
+    int e2, e3;
+    int ew[kPsMaxBlocks];
+    float ch[kPsCoefs], cl[kPsCoefs];
     // cross-block reduction of the final cost terms (k_finalize): per-block partials and the
     // count of blocks that have written theirs (the last block sums them in block order and
     // resets the count)

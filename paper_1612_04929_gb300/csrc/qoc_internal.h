@@ -100,8 +100,26 @@ struct ZStore {
     int cap;
     size_t mstride;
     int wmax;
+    int ps;                 // 1: the forward evaluates T by Paterson-Stockmeyer (slot layout below)
 };
 constexpr int kZCap = 24;
+
+// Paterson-Stockmeyer form of the FP32 per-slice exponential (block size 3):
+//   T_p(X) = sum_q (X^3)^q B_q,  B_q = c_3q I + c_3q+1 X + c_3q+2 X^2  (c_k = 1/k!, 0 for k > p),
+// evaluated as W_qt (formed element-wise) and W_q = B_q + X^3 W_{q+1}, q = qt-1 .. 0, T = W_0.
+// The top block qt is p / 3, or p / 3 - 1 when 3 divides p (the last block c_p I is then folded
+// into the one below it as c_p X^3).  The stored operands (conjugate transposes, as in ZStore):
+// slot 0 X^2, slot 1 X^3, slot 2 + (qt - 1 - q) W_{q+1} (chain product q), slot qt + 2 + m the
+// squaring operand S_m.
+__host__ __device__ inline int ps_top(int p) { return (p % 3 == 0 && p >= 3) ? p / 3 - 1 : p / 3; }
+__host__ __device__ inline int ps_slots(int p, int n) { return ps_top(p) + 2 + n; }
+// the forward stored the operands of this evaluation's (p, n) (the reverse mode applies)
+template <typename R>
+__host__ __device__ inline bool zs_fits(const ZStore<R>& zs, int p, int n) {
+    return zs.Z && (zs.ps ? ps_slots(p, n) : p - 1 + n) <= zs.cap;
+}
+static_assert(kPsCoefs >= kPMax + 4, "coefficients up to index 3 qt + 3 <= p + 3");
+static_assert(kPsMaxBlocks > kPMax / 3, "one grid exponent per block");
 
 template <typename R> int fused_max_d();
 // resident CTAs per SM of the per-slice forward (adjoint = false) or reverse-mode adjoint kernel
@@ -138,6 +156,18 @@ cudaError_t launch_split_scale(const DevParams* prm, const double2* H64, size_t 
 cudaError_t launch_expm_fwd_split(const DevParams* prm, const SysView<float>& sys, const float4* sH, int j0, int wlen,
                                   int E, float2* Ubuf, long long ustride, int wmax, const ZStore<float>& zs,
                                   cudaStream_t st);
+// Paterson-Stockmeyer form of the same exponential (zs.ps = 1), d <= ps_max_d(): the forward
+// (k_expm_split.cu) and its reverse-mode adjoints, dense and low-rank (k_expm_ps.cu); without
+// stored operands the block recursion (k_expm_adj) differentiates the same polynomial
+int ps_max_d();
+int ps_fwd_ctas_per_sm(int d);
+int ps_adj_ctas_per_sm(int d);
+cudaError_t launch_expm_fwd_ps(const DevParams* prm, const SysView<float>& sys, const float4* sH, int j0, int wlen,
+                               int E, float2* Ubuf, long long ustride, int wmax, const ZStore<float>& zs,
+                               cudaStream_t st);
+cudaError_t launch_expm_adj_ps(const DevParams* prm, const SysView<float>& sys, const StateView<float>& sv, int j0,
+                               int wlen, int E, const float2* states, const float2* Gbuf, int wmax, double* gpart,
+                               const ZStore<float>& zs, cudaStream_t st, int* launches);
 
 // ---- large-d batched slice exponentials and adjoint (k_big.cu) ----
 struct BigSys {

@@ -58,9 +58,9 @@ def test_struct_layouts_match_c(lib):
 #include <stddef.h>
 #include "qoc.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(qoc_options), offsetof(qoc_options, stream),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(qoc_options), offsetof(qoc_options, stream),
          offsetof(qoc_options, profile), offsetof(qoc_options, plain_fp32_exp), sizeof(qoc_info),
-         offsetof(qoc_info, device_bytes));
+         offsetof(qoc_info, device_bytes), offsetof(qoc_options, taylor_scheme), offsetof(qoc_info, taylor_scheme));
   printf("%zu %zu %zu\n", sizeof(qoc_profile), offsetof(qoc_profile, launches), offsetof(qoc_profile, total_ms));
   return 0;
 }
@@ -75,7 +75,8 @@ int main(void) {
     a = [int(x) for x in lines[0].split()]
     b = [int(x) for x in lines[1].split()]
     assert a == [ct.sizeof(qmod.qoc_options), qmod.qoc_options.stream.offset, qmod.qoc_options.profile.offset,
-                 qmod.qoc_options.plain_fp32_exp.offset, ct.sizeof(qmod.qoc_info), qmod.qoc_info.device_bytes.offset]
+                 qmod.qoc_options.plain_fp32_exp.offset, ct.sizeof(qmod.qoc_info), qmod.qoc_info.device_bytes.offset,
+                 qmod.qoc_options.taylor_scheme.offset, qmod.qoc_info.taylor_scheme.offset]
     assert b == [ct.sizeof(qmod.qoc_profile), qmod.qoc_profile.launches.offset, qmod.qoc_profile.total_ms.offset]
 
 
@@ -121,7 +122,8 @@ def test_reversal_needs_the_fp64_form(lib):
 @pytest.mark.parametrize("field,value", [("precision", 4), ("precision", -1), ("tol", -1.0), ("theta_max", -0.5),
                                          ("ckpt_stride", -2), ("wave_slices", -1), ("sweep", 3), ("gradient", 2),
                                          ("adjoint", 2), ("fault_inject", 2), ("reversal", 2),
-                                         ("propagation", 2), ("propagation", -1), ("exponential", 2)])
+                                         ("propagation", 2), ("propagation", -1), ("exponential", 2),
+                                         ("taylor_scheme", 2), ("taylor_scheme", -1)])
 def test_invalid_options_are_rejected_before_the_device(lib, field, value):
     """qoc_create validates every option on the host before it touches a device: an out-of-range
     value is QOC_ERR_ARG (1) on any machine, and no context is returned."""

@@ -9,7 +9,11 @@
   each squaring, R stays fixed through Horner), and gives the same Xbar as the dense reverse mode,
   which itself matches a finite-difference derivative of the truncated series;
 * block form: for the polynomial map f (Horner series, then squarings) with real coefficients, the
-  same Xbar is the (1,2) block of f applied to [[X^dag, Ubar], [0, X^dag]].
+  same Xbar is the (1,2) block of f applied to [[X^dag, Ubar], [0, X^dag]];
+* Paterson-Stockmeyer form: the same truncated series evaluated in blocks of three terms,
+  T = B_0 + Y(B_1 + Y(B_2 + ...)) with Y = X^3 and B_q = c_3q I + c_3q+1 X + c_3q+2 X^2, and its
+  reverse mode (dense and low-rank), in the order and with the stored operands the FP32 per-slice
+  kernels use, agree with the Horner forms above.
 """
 import numpy as np
 import pytest
@@ -140,3 +144,133 @@ def test_block_triangular_form_equals_reverse_mode(d, p, n):
     dense = reverse_dense(X, Ubar, p, n)
     assert np.abs(FB[:d, d:] - dense).max() <= 1e-12 * np.abs(dense).max()
     assert np.abs(FB[:d, :d] - taylor_forward(XH, p, n)[0]).max() < 1e-13
+
+
+# ------------------------------------------------------------------ Paterson-Stockmeyer form
+def ps_coefficients(p):
+    """c_k = 1/k! for k <= p and 0 beyond (indices up to p + 3 are read)."""
+    c = np.zeros(p + 4)
+    f = 1.0
+    for k in range(p + 1):
+        if k:
+            f *= k
+        c[k] = 1.0 / f
+    return c
+
+
+def ps_top(p):
+    """Index qt of the top block, formed without a product: blocks q = 0 .. p // 3; when 3 divides
+    p the last block is c_p I alone and is folded into the one below it as c_p X^3."""
+    Q = p // 3
+    return Q - 1 if (p % 3 == 0 and p >= 3) else Q
+
+
+def ps_forward(X, p, n):
+    """The order-p Taylor polynomial by Paterson-Stockmeyer with block size 3, then n squarings.
+    Returns U and the operands the reverse mode reads, in store-slot order: X^2, X^3, then the
+    right operands W_{q+1} of the chain products q = qt-1 .. 0, then S_m = T^(2^m)."""
+    d = X.shape[0]
+    I = np.eye(d)
+    c = ps_coefficients(p)
+    P2 = X @ X
+    P3 = P2 @ X
+    qt = ps_top(p)
+    W = c[3 * qt] * I + c[3 * qt + 1] * X + c[3 * qt + 2] * P2 + c[3 * qt + 3] * P3
+    ops = [P2, P3]
+    for q in range(qt - 1, -1, -1):
+        ops.append(W)
+        W = c[3 * q] * I + c[3 * q + 1] * X + c[3 * q + 2] * P2 + P3 @ W
+    for _ in range(n):
+        ops.append(W)
+        W = W @ W
+    return W, ops
+
+
+def ps_slots(p, n):
+    return ps_top(p) + 2 + n
+
+
+def ps_powers_reverse(X, P2, P3bar, P2bar, Xbar):
+    """P3 = P2 X and P2 = X X in reverse: the four dense products that end both reverse modes."""
+    XH = X.conj().T
+    P2bar = P2bar + P3bar @ XH
+    Xbar = Xbar + P2.conj().T @ P3bar
+    return Xbar + P2bar @ XH + XH @ P2bar
+
+
+def ps_reverse_dense(X, Ubar, p, n):
+    _, ops = ps_forward(X, p, n)
+    c = ps_coefficients(p)
+    qt = ps_top(p)
+    P2, P3 = ops[0], ops[1]
+    Sbar = Ubar
+    for m in range(n - 1, -1, -1):
+        S = ops[qt + 2 + m]
+        Sbar = Sbar @ S.conj().T + S.conj().T @ Sbar
+    Wbar = Sbar
+    Xbar = np.zeros_like(X)
+    P2bar = np.zeros_like(X)
+    P3bar = np.zeros_like(X)
+    for q in range(qt):                      # chain products in reverse: W_q = B_q + P3 W_{q+1}
+        Wnext = ops[2 + (qt - 1 - q)]
+        Xbar = Xbar + c[3 * q + 1] * Wbar
+        P2bar = P2bar + c[3 * q + 2] * Wbar
+        P3bar = P3bar + Wbar @ Wnext.conj().T
+        Wbar = P3.conj().T @ Wbar
+    Xbar = Xbar + c[3 * qt + 1] * Wbar       # the top block
+    P2bar = P2bar + c[3 * qt + 2] * Wbar
+    P3bar = P3bar + c[3 * qt + 3] * Wbar
+    return ps_powers_reverse(X, P2, P3bar, P2bar, Xbar)
+
+
+def ps_reverse_low_rank(X, L, R, p, n):
+    """Ubar = L R^dag: the squarings append blocks to the factors; through the chain R stays fixed
+    and L_{q+1} = P3^dag L_q, so the X and X^2 cotangents are (sum c L_q) R^dag and the X^3
+    cotangent is sum_q L_q (W_{q+1} R)^dag; the powers then go dense."""
+    _, ops = ps_forward(X, p, n)
+    c = ps_coefficients(p)
+    qt = ps_top(p)
+    P2, P3 = ops[0], ops[1]
+    for m in range(n - 1, -1, -1):
+        S = ops[qt + 2 + m]
+        L, R = np.hstack([L, S.conj().T @ L]), np.hstack([S @ R, R])
+    A1 = np.zeros_like(L)
+    A2 = np.zeros_like(L)
+    P3bar = np.zeros_like(X)
+    for q in range(qt):
+        Wnext = ops[2 + (qt - 1 - q)]
+        A1 = A1 + c[3 * q + 1] * L
+        A2 = A2 + c[3 * q + 2] * L
+        P3bar = P3bar + L @ (Wnext @ R).conj().T
+        L = P3.conj().T @ L
+    A1 = A1 + c[3 * qt + 1] * L
+    A2 = A2 + c[3 * qt + 2] * L
+    P3bar = P3bar + c[3 * qt + 3] * L @ R.conj().T
+    RH = R.conj().T
+    return ps_powers_reverse(X, P2, P3bar, A2 @ RH, A1 @ RH), L.shape[1]
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6, 9, 11, 12, 14])
+@pytest.mark.parametrize("n", [0, 2])
+def test_paterson_stockmeyer_equals_horner(p, n):
+    """Same polynomial, another evaluation order: U and the dense and low-rank reverse modes agree
+    with the Horner forms to rounding, for every residue of p mod 3."""
+    d, S = 14, 1
+    rng = np.random.default_rng(7 * p + n)
+    H = rng.normal(size=(d, d)) + 1j * rng.normal(size=(d, d))
+    H = (H + H.conj().T) / 2
+    X = -1j * 1.6 * H / np.abs(H).sum(0).max()       # theta_s = 1.6, the FP32 kernels' range
+    U_ps, ops = ps_forward(X, p, n)
+    U_h, _ = taylor_forward(X, p, n)
+    assert np.abs(U_ps - U_h).max() <= 1e-13 * np.abs(U_h).max()
+    assert len(ops) == ps_slots(p, n)
+    L = rng.normal(size=(d, S)) + 1j * rng.normal(size=(d, S))
+    R = rng.normal(size=(d, S)) + 1j * rng.normal(size=(d, S))
+    Ubar = L @ R.conj().T
+    ref = reverse_dense(X, Ubar, p, n)
+    dense = ps_reverse_dense(X, Ubar, p, n)
+    low, r = ps_reverse_low_rank(X, L, R, p, n)
+    assert r == S << n
+    scale = np.abs(ref).max()
+    assert np.abs(dense - ref).max() <= 1e-12 * scale
+    assert np.abs(low - ref).max() <= 1e-12 * scale

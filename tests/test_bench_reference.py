@@ -64,12 +64,36 @@ def _walk_flops(form, d, p, n, S):
     return per_product * (p - 1 + n) * mm(d, d, d) + mm(d, S, d)   # plus Ubar = G Psi^dag
 
 
+def _walk_flops_ps(form, d, p, n, S):
+    """The same walk for the Paterson-Stockmeyer form (blocks of three terms, top block qt)."""
+    mm = lambda m, k, q: 8.0 * m * k * q
+    qt = p // 3 - 1 if (p % 3 == 0 and p >= 3) else p // 3
+    powers = (2 if p >= 3 else 0) + (2 if p >= 2 else 0)   # Ybar X^dag, X2^dag Ybar; X2bar X^dag, X^dag X2bar
+    if form == 0:
+        return (2 * n + 2 * qt + powers) * mm(d, d, d) + mm(d, S, d)
+    f, r = 0.0, S
+    for _ in range(n):
+        f += mm(d, d, r) + mm(d, d, r)
+        r *= 2
+    for _ in range(qt):                             # V = W R, Y^dag L, L V^dag
+        f += mm(d, d, r) + mm(d, d, r) + mm(d, r, d)
+    if p % 3 == 0 and p >= 3:                       # top block's c L R^dag into Ybar
+        f += mm(d, r, d)
+    f += 2 * mm(d, r, d)                            # (sum c L) R^dag into Xbar and X2bar
+    return f + powers * mm(d, d, d)
+
+
 def test_roofline_flop_counts():
     b = _bench()
     assert b.expm_flops_per_slice(40, 9, 4) == 12 * 8.0 * 40 ** 3
     for form in (0, 1, 3):
         for d, p, n, S in [(40, 9, 4, 1), (64, 7, 1, 2), (48, 5, 0, 3), (81, 12, 2, 16)]:
             assert b.adj_flops_per_slice(form, d, p, n, S) == _walk_flops(form, d, p, n, S), (form, d, p, n, S)
+    assert b.expm_flops_per_slice(40, 14, 2, 1) == 8 * 8.0 * 40 ** 3          # X^2, X^3, 4 chain, 2 squarings
+    assert b.expm_flops_per_slice(40, 12, 2, 1) == 7 * 8.0 * 40 ** 3          # 3 | p: the top block folds
+    for form in (0, 3):
+        for d, p, n, S in [(40, 14, 2, 1), (40, 12, 2, 1), (48, 5, 0, 3), (16, 2, 1, 1), (20, 1, 3, 2)]:
+            assert b.adj_flops_per_slice(form, d, p, n, S, 1) == _walk_flops_ps(form, d, p, n, S), (form, d, p, n, S)
 
 
 def test_job_value_is_all_ranks_over_the_slowest():

@@ -189,10 +189,12 @@ def test_plain_fp32_exponential_option_runs():
     assert rel(g2, g_ref) <= 1e-5 and rel(g1, g2) > 0
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("fp32", 1e-7)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("fp32", 3e-7)])
 def test_checkpoint_layout_does_not_change_results(precision, tol):
     """Checkpoint stride and wave size change only where partial sums are added (costate
-    carries between waves); the carried hi+lo recursion keeps that at rounding level."""
+    carries between waves); the carried hi+lo recursion keeps that at rounding level (FP32: a few
+    units of 2^-24 of the largest partial, against about 5e-7 from the oracle in both Taylor
+    forms)."""
     prob = sy.random_problem(d=9, M=2, N=50, S=3, seed=301, nF=2, path=True, E=2)
     ref = run(prob, precision, ckpt_stride=1000)
     for stride, wave in ((1, 1), (7, 14), (16, 16), (49, 0), (5, 45)):
