@@ -98,6 +98,8 @@ def parse():
     ap.add_argument("--exponential", choices=["taylor", "chebyshev"], default="taylor",
                     help="slice exponential: Taylor with scaling and squaring, or Chebyshev (state mode)")
     ap.add_argument("--members", type=int, default=1, help="detuning-ensemble members (cat_state workload)")
+    ap.add_argument("--taylor-scheme", choices=["auto", "horner"], default="auto",
+                    help="evaluation of the Taylor polynomial (auto: Paterson-Stockmeyer where built)")
     ap.add_argument("--gradient", choices=["exact", "first_order"], default="exact",
                     help="exact derivative of the truncated series, or the paper's first-order Eq. 11")
     return ap.parse_args()
@@ -507,6 +509,7 @@ def measure_config(name, precision, peaks, stream, flush, K, warmup, fp64_N=0, e
     units = prob.N * prob.E
     row = {"workload": prob.name, "precision": precision, "d": prob.d, "N": prob.N, "M": prob.M, "S": prob.S,
            "E": prob.E, "p": info["p"], "n": info["n"], "kernel_path": info["kernel_path"],
+           "taylor_scheme": ["horner", "paterson-stockmeyer"][info.get("taylor_scheme", 0)],
            "ms_per_step": ms, "value": units / (ms / 1e3), "unit": UNIT, "steps": K,
            "roofline": roofline_of(prob, precision, info, prof, K, peaks), **form}
     row["roofline_events_ms_per_step"] = ms_p
@@ -687,6 +690,8 @@ def ours_arm(args):
     stream = torch.cuda.Stream()          # every kernel of the step and every event on one stream
     torch.cuda.set_stream(stream)
     form = dict(propagation=args.propagation, exponential=args.exponential)
+    if args.taylor_scheme != "auto":
+        form["taylor_scheme"] = args.taylor_scheme
     ctx = Context(precision, device=local, stream=stream.cuda_stream, ckpt_stride=args.ckpt_stride,
                   gradient=args.gradient, graph=args.graph, **form)
     ctx.set_problem(prob)
@@ -840,6 +845,7 @@ def ours_arm(args):
                                     {"p": p_of(info), "n": info["n"], "wave_slices": info["wave_slices"],
                                      "n_waves": info["n_waves"], "gradient": args.gradient, "graph": args.graph,
                                      "propagation": args.propagation, "exponential": args.exponential,
+                                     "taylor_scheme": ["horner", "paterson-stockmeyer"][info.get("taylor_scheme", 0)],
                                      "adjoint": {0: "reverse mode", 1: "block recursion", 2: "none (first-order)",
                                                  3: "low-rank reverse mode", 4: "state-mode reverse pass"}.get(
                                          info.get("adjoint_form"), "?")}),

@@ -109,16 +109,6 @@ __global__ void k_big_assemble(const DevParams* __restrict__ prm, BigSys sys, in
 
 // FP32 split form: X = -i s H_j and Z = I + X / p in pair arithmetic from the pairs s H_0,
 // s H_k, s H_det (as the per-slice split kernel assembles them), grid-split (ex; Z with ezp).
-__device__ __forceinline__ void big_pair_fma(float& hi, float& lo, float2 u, float bh, float bl) {
-    const float p = u.x * bh;
-    float e = fmaf(u.x, bh, -p);
-    e = fmaf(u.x, bl, e);
-    e = fmaf(u.y, bh, e);
-    float s, r;
-    two_sum(hi, p, s, r);
-    hi = s;
-    lo += r + e;
-}
 __device__ __forceinline__ float4 big_gsplit(float rh, float rl, float ih, float il, int e) {
     if (e == kFullForm) return make_float4(rh + rl, ih + il, 0.f, 0.f);
     const float m = grid_magic(e);
@@ -146,13 +136,13 @@ __global__ void k_big_assemble_split(const DevParams* __restrict__ prm, BigSys s
         float rh = h0.x, rl = h0.z, ih = h0.y, il = h0.w;
         for (int k = 0; k < M; ++k) {
             const float4 hk = sH[(size_t)(1 + k) * dd + idx];
-            big_pair_fma(rh, rl, us[k], hk.x, hk.z);
-            big_pair_fma(ih, il, us[k], hk.y, hk.w);
+            pair_fma(rh, rl, us[k], hk.x, hk.z);
+            pair_fma(ih, il, us[k], hk.y, hk.w);
         }
         if (sys.has_det) {
             const float4 hd = sH[(size_t)(M + 1) * dd + idx];
-            big_pair_fma(rh, rl, us[M], hd.x, hd.z);
-            big_pair_fma(ih, il, us[M], hd.y, hd.w);
+            pair_fma(rh, rl, us[M], hd.x, hd.z);
+            pair_fma(ih, il, us[M], hd.y, hd.w);
         }
         big_norm(rh, rl);
         big_norm(ih, il);
@@ -162,6 +152,7 @@ __global__ void k_big_assemble_split(const DevParams* __restrict__ prm, BigSys s
             big_div(xrh, xrl, fp);
             big_div(xih, xil, fp);
         }
+        if (!Z) continue;   // the Paterson-Stockmeyer form starts from X alone
         const int a = (int)(idx / d), b = (int)(idx - (size_t)a * d);
         if (a == b) big_add1(xrh, xrl);
         Z[(size_t)item * mstride + idx] = big_gsplit(xrh, xrl, xih, xil, ezp);
@@ -172,16 +163,26 @@ __global__ void k_big_assemble_split(const DevParams* __restrict__ prm, BigSys s
 // batched product C = A B (T x T tile per CTA), epilogue:
 //   kind 0: C = I + AB / i     (Horner step i)
 //   kind 1: C = AB             (squaring)
+//   kind 2: C = AB + c0 I + c1 X + c2 X^2   (Paterson-Stockmeyer chain product; SPLIT and PLAIN32
+//           only: the block terms in pair arithmetic (SPLIT) or FP32 (PLAIN32), from PsAdd)
 // SPLIT: split product of grid-split float4 operands, the result grid-split with `magic`;
 // PLAIN32: plain FP32 product of a grid-split A (X) and a full-form B, the result in full form
 // (magic == 0) or grid-split; otherwise plain products of E = float2 / double2.
 // ------------------------------------------------------------------------------------------
 constexpr int KC = 16;
 
+// the block B_q = c0 I + c1 X + c2 X^2 added by a Paterson-Stockmeyer chain product (kind 2); the
+// coefficients as FP32 pairs, X and X^2 grid-split, item matrices mstride apart
+struct PsAdd {
+    const float4* X = nullptr;
+    const float4* X2 = nullptr;
+    float2 c0{0.f, 0.f}, c1{0.f, 0.f}, c2{0.f, 0.f};
+};
+
 template <typename E, int T, int MODE>   // MODE 0 plain, 1 split, 2 plain FP32 (E = float4)
 __global__ void __launch_bounds__(256)
 k_big_mm(int d, const E* __restrict__ A, const E* __restrict__ B, E* __restrict__ Cm, size_t mstride, int kind, int i,
-         float magic) {
+         float magic, PsAdd ps) {
     constexpr int MT = T / 16;
     // two buffers of (As[T][KC + 1], Bs[KC][T + 1]): the next K-chunk is copied (cp.async) while
     // the current one is multiplied
@@ -301,6 +302,15 @@ k_big_mm(int d, const E* __restrict__ A, const E* __restrict__ B, E* __restrict_
                 float rh, rl, ih, il;
                 two_sum(sa[x][y][0], sa[x][y][2], rh, rl);
                 two_sum(sa[x][y][1], sa[x][y][3], ih, il);
+                if (kind == 2) {
+                    const size_t o = (size_t)item * mstride + (size_t)r * d + c;
+                    const float4 xv = ps.X[o], yv = ps.X2[o];
+                    pair_fma(rh, rl, ps.c1, xv.x, xv.z);
+                    pair_fma(ih, il, ps.c1, xv.y, xv.w);
+                    pair_fma(rh, rl, ps.c2, yv.x, yv.z);
+                    pair_fma(ih, il, ps.c2, yv.y, yv.w);
+                    if (r == c) df_addc(rh, rl, ps.c0);
+                }
                 if (kind == 0 && i > 1) {
                     big_div(rh, rl, (float)i);
                     big_div(ih, il, (float)i);
@@ -311,8 +321,20 @@ k_big_mm(int d, const E* __restrict__ A, const E* __restrict__ B, E* __restrict_
                 grid_split(ih, il, magic, o.y, o.w);
                 out = *reinterpret_cast<E*>(&o);
             } else if constexpr (MODE == 2) {
-                const float ri = 1.0f / (float)i;
-                float4 o = make_float4(fmaf(sa[x][y][0], ri, diag ? 1.0f : 0.0f), sa[x][y][1] * ri, 0.f, 0.f);
+                float4 o;
+                if (kind == 2) {
+                    const size_t oi = (size_t)item * mstride + (size_t)r * d + c;
+                    const float4 xv = ps.X[oi], yv = ps.X2[oi];
+                    float re = fmaf(ps.c1.x, xv.x + xv.z, sa[x][y][0]);
+                    float im = fmaf(ps.c1.x, xv.y + xv.w, sa[x][y][1]);
+                    re = fmaf(ps.c2.x, yv.x + yv.z, re);
+                    im = fmaf(ps.c2.x, yv.y + yv.w, im);
+                    if (r == c) re += ps.c0.x;
+                    o = make_float4(re, im, 0.f, 0.f);
+                } else {
+                    const float ri = 1.0f / (float)i;
+                    o = make_float4(fmaf(sa[x][y][0], ri, diag ? 1.0f : 0.0f), sa[x][y][1] * ri, 0.f, 0.f);
+                }
                 if (magic != 0.f) {   // read by a split product
                     grid_split(o.x, 0.f, magic, o.x, o.z);
                     grid_split(o.y, 0.f, magic, o.y, o.w);
@@ -590,6 +612,61 @@ __global__ void k_big_store_ct(int d, const E* __restrict__ Z, size_t mstride, C
     }
 }
 
+// Paterson-Stockmeyer top block W_qt = c0 I + c1 X + c2 X^2 + c3 X^3 (pairs; X^2 read when p >= 2,
+// X^3 when p >= 3), in the form its reader takes (grid exponent e, or kFullForm)
+__global__ void k_big_ps_top(int d, const float4* __restrict__ X, const float4* __restrict__ X2,
+                             const float4* __restrict__ X3, float4* __restrict__ W, size_t mstride, float2 c0, float2 c1,
+                             float2 c2, float2 c3, int p, int e) {
+    const size_t dd = (size_t)d * d, off = (size_t)blockIdx.y * mstride;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < dd; idx += (size_t)gridDim.x * blockDim.x) {
+        float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+        const float4 xv = X[off + idx];
+        pair_fma(rh, rl, c1, xv.x, xv.z);
+        pair_fma(ih, il, c1, xv.y, xv.w);
+        if (p >= 2) {
+            const float4 yv = X2[off + idx];
+            pair_fma(rh, rl, c2, yv.x, yv.z);
+            pair_fma(ih, il, c2, yv.y, yv.w);
+        }
+        if (p >= 3) {
+            const float4 zv = X3[off + idx];
+            pair_fma(rh, rl, c3, zv.x, zv.z);
+            pair_fma(ih, il, c3, zv.y, zv.w);
+        }
+        const int a = (int)(idx / d), b = (int)(idx - (size_t)a * d);
+        if (a == b) df_addc(rh, rl, c0);
+        W[off + idx] = big_gsplit(rh, rl, ih, il, e);
+    }
+}
+
+// Cotangent accumulation of the Paterson-Stockmeyer reverse mode: Xbar += a Z, X2bar += b Z,
+// Ybar += c Z (a zero coefficient leaves its target untouched)
+__global__ void k_big_ps_acc(int d, const float2* __restrict__ Z, float2* __restrict__ Xb, float2* __restrict__ X2b,
+                             float2* __restrict__ Yb, size_t mstride, float a, float b, float c) {
+    const size_t dd = (size_t)d * d, off = (size_t)blockIdx.y * mstride;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < dd; idx += (size_t)gridDim.x * blockDim.x) {
+        const float2 z = Z[off + idx];
+        if (a != 0.f) {
+            float2 v = Xb[off + idx];
+            v.x = fmaf(a, z.x, v.x);
+            v.y = fmaf(a, z.y, v.y);
+            Xb[off + idx] = v;
+        }
+        if (b != 0.f) {
+            float2 v = X2b[off + idx];
+            v.x = fmaf(b, z.x, v.x);
+            v.y = fmaf(b, z.y, v.y);
+            X2b[off + idx] = v;
+        }
+        if (c != 0.f) {
+            float2 v = Yb[off + idx];
+            v.x = fmaf(c, z.x, v.x);
+            v.y = fmaf(c, z.y, v.y);
+            Yb[off + idx] = v;
+        }
+    }
+}
+
 // Reverse mode over the stored products (two products per tile, operands at their own item strides):
 //   mode 0 (Horner step i): O1 = A1 B1 / i,  O2 += A2 B2 / i   (Zbar' = X^dag Zbar / i, Xbar += Zbar Z^dag / i)
 //   mode 1 (squaring):      O1 = A1 B1 + A2 B2                (Sbar' = Sbar S^dag + S^dag Sbar)
@@ -735,7 +812,7 @@ template <typename E, int T> constexpr size_t blk_smem() { return 2 * mm_smem<E,
 
 template <typename E, int T, int MODE>
 static cudaError_t mm_launch_t(int d, int items, const E* A, const E* B, E* Cm, size_t mstride, int kind, int i,
-                               float magic, cudaStream_t st) {
+                               float magic, cudaStream_t st, const PsAdd& ps) {
     constexpr size_t smem = mm_smem<E, T>();
     static bool attr = false;
     if (!attr) {
@@ -744,15 +821,15 @@ static cudaError_t mm_launch_t(int d, int items, const E* A, const E* B, E* Cm, 
         attr = true;
     }
     const int nt = ((d + T - 1) / T) * ((d + T - 1) / T);
-    k_big_mm<E, T, MODE><<<dim3(nt, items), 256, smem, st>>>(d, A, B, Cm, mstride, kind, i, magic);
+    k_big_mm<E, T, MODE><<<dim3(nt, items), 256, smem, st>>>(d, A, B, Cm, mstride, kind, i, magic, ps);
     return cudaGetLastError();
 }
 
 template <typename E, int MODE>
 static cudaError_t mm_launch(int d, int items, const E* A, const E* B, E* Cm, size_t mstride, int kind, int i,
-                             cudaStream_t st, float magic = 0.f) {
-    if (big_tile(d) == 32) return mm_launch_t<E, 32, MODE>(d, items, A, B, Cm, mstride, kind, i, magic, st);
-    return mm_launch_t<E, 64, MODE>(d, items, A, B, Cm, mstride, kind, i, magic, st);
+                             cudaStream_t st, float magic = 0.f, const PsAdd& ps = PsAdd{}) {
+    if (big_tile(d) == 32) return mm_launch_t<E, 32, MODE>(d, items, A, B, Cm, mstride, kind, i, magic, st, ps);
+    return mm_launch_t<E, 64, MODE>(d, items, A, B, Cm, mstride, kind, i, magic, st, ps);
 }
 
 template <typename C, int T>
@@ -775,6 +852,83 @@ static int ew_blocks(size_t dd) {
     return (int)(b < 64 ? b : 64);
 }
 
+// Paterson-Stockmeyer form of the split exponential (the per-slice k_expm_fwd_ps as batched
+// products): X^2 and X^3, the top block element-wise, the chain W_q = B_q + X^3 W_{q+1} with B_q
+// added in the product's epilogue (split products for q <= (m_split - 1) / 3, plain FP32 above),
+// then the squarings.  Scratch per item: X, X^2, X^3 and the W ping-pong (five float4 matrices).
+// Stored operands (conjugate transposes) in the slot layout of ps_slots.
+static cudaError_t big_expm_ps(const BigArgs<float>& a, const DevParams& hp, cudaStream_t st, int* launches,
+                               float2* zst) {
+    const int p = hp.p, n = hp.n, d = a.d, items = a.wlen * a.E;
+    const size_t ms = a.mstride;
+    const int eb = ew_blocks((size_t)d * d);
+    const int qt = ps_top(p), qs = (hp.m_split - 1) / 3, cap = ps_slots(p, n);
+    if (!a.sH || qt >= kPsMaxBlocks) return cudaErrorInvalidValue;
+    auto count = [&]() { if (launches) ++*launches; };
+    float4* X = reinterpret_cast<float4*>(a.scratch);
+    float4* X2 = X + (size_t)items * ms;
+    float4* X3 = X2 + (size_t)items * ms;
+    float4* win = X3 + (size_t)items * ms;
+    float4* wout = win + (size_t)items * ms;
+    auto magic = [](int e) { return std::ldexp(1.5f, e + 11); };
+    // the form W_q is written in: its reader is chain product q - 1 (split iff q - 1 <= qs), or the
+    // squarings for W_0 = T
+    auto form_w = [&](int q) { return q == 0 ? hp.eu : (q - 1 <= qs ? hp.ew[q] : kFullForm); };
+    auto coef = [&](int k) { return make_float2(hp.ch[k], hp.cl[k]); };
+    cudaError_t err;
+    auto store = [&](const float4* Z, int slot) -> cudaError_t {
+        if (!zst) return cudaSuccess;
+        k_big_store_ct<float4, float2><<<dim3(eb, items), 256, 0, st>>>(d, Z, ms, zst, cap, slot);
+        count();
+        return cudaGetLastError();
+    };
+    k_big_assemble_split<<<dim3(eb, items), 256, 0, st>>>(a.prm, a.bsys, a.sH, a.j0, a.wlen, X, nullptr, ms, hp.ex,
+                                                          hp.eu);
+    count();
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    if (p >= 2) {
+        if ((err = mm_launch<float4, 1>(d, items, X, X, X2, ms, 1, 0, st, magic(hp.e2))) != cudaSuccess) return err;
+        count();
+        if ((err = store(X2, 0)) != cudaSuccess) return err;
+    }
+    if (p >= 3) {
+        if ((err = mm_launch<float4, 1>(d, items, X2, X, X3, ms, 1, 0, st, magic(hp.e3))) != cudaSuccess) return err;
+        count();
+        if ((err = store(X3, 1)) != cudaSuccess) return err;
+    }
+    k_big_ps_top<<<dim3(eb, items), 256, 0, st>>>(d, X, X2, X3, win, ms, coef(3 * qt), coef(3 * qt + 1),
+                                                  coef(3 * qt + 2), coef(3 * qt + 3), p, form_w(qt));
+    count();
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    for (int q = qt - 1; q >= 0; --q) {
+        if ((err = store(win, 2 + (qt - 1 - q))) != cudaSuccess) return err;
+        PsAdd ps;
+        ps.X = X;
+        ps.X2 = X2;
+        ps.c0 = coef(3 * q);
+        ps.c1 = coef(3 * q + 1);
+        ps.c2 = coef(3 * q + 2);
+        const int f = form_w(q);
+        const float mg = f == kFullForm ? 0.f : magic(f);
+        err = (q <= qs) ? mm_launch<float4, 1>(d, items, X3, win, wout, ms, 2, 0, st, mg, ps)
+                        : mm_launch<float4, 2>(d, items, X3, win, wout, ms, 2, 0, st, mg, ps);
+        count();
+        if (err != cudaSuccess) return err;
+        std::swap(win, wout);
+    }
+    for (int m = 0; m < n; ++m) {
+        if ((err = store(win, qt + 2 + m)) != cudaSuccess) return err;
+        if ((err = mm_launch<float4, 1>(d, items, win, win, wout, ms, 1, 0, st, magic(hp.eu))) != cudaSuccess)
+            return err;
+        count();
+        std::swap(win, wout);
+    }
+    k_big_store_u<float4, float2><<<dim3(eb, items), 256, 0, st>>>(d, win, ms, reinterpret_cast<float2*>(a.Ubuf),
+                                                                     a.ustride, a.wlen, a.wmax);
+    count();
+    return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t launch_big_expm(const BigArgs<R>& a, const DevParams& hp, bool split, cudaStream_t st, int* launches,
                             C_t<R>* zst) {
@@ -792,6 +946,7 @@ cudaError_t launch_big_expm(const BigArgs<R>& a, const DevParams& hp, bool split
         count();
         return cudaGetLastError();
     };
+    if constexpr (sizeof(R) == 4) if (split && a.ps) return big_expm_ps(a, hp, st, launches, zst);
     if constexpr (sizeof(R) == 4) if (split) {
         float4* X = reinterpret_cast<float4*>(a.scratch);
         float4* Za = X + (size_t)items * a.mstride;
@@ -988,6 +1143,94 @@ cudaError_t launch_big_adj_rev(const BigArgs<R>& a, const SysView<R>& sys, const
     return cudaGetLastError();
 }
 
+// Reverse mode of the Paterson-Stockmeyer form over its stored operands (the per-slice
+// k_expm_adj_ps as batched products; FP32 forms): the squarings in reverse, per chain product
+// Wbar_{q+1} = Y^dag Wbar_q with Ybar += Wbar_q W_{q+1}^dag in the same launch, the block
+// cotangents Xbar += c_3q+1 Wbar_q, X2bar += c_3q+2 Wbar_q element-wise, then the power products
+// X2bar += Ybar X^dag with Xbar += X2^dag Ybar, and Xbar += X2bar X^dag + X^dag X2bar.
+// Scratch per item: X^dag, the cotangent ping-pong, Xbar, X2bar, Ybar (six float2 matrices).
+template <typename R>
+cudaError_t launch_big_adj_rev_ps(const BigArgs<R>& a, const SysView<R>& sys, const StateView<R>& sv,
+                                  const C_t<R>* states, const C_t<R>* Gbuf, double* gpart, const DevParams& hp,
+                                  const C_t<R>* zst, cudaStream_t st, int* launches, const OzRev* oz) {
+    if constexpr (sizeof(R) != 4) {
+        return cudaErrorInvalidValue;
+    } else {
+        using C = float2;
+        const int p = hp.p, n = hp.n, d = a.d, items = a.wlen * a.E, cap = ps_slots(p, n), qt = ps_top(p);
+        const size_t dd = (size_t)d * d, ms = a.mstride, zs = (size_t)cap * ms;
+        const int eb = ew_blocks(dd);
+        auto count = [&]() { if (launches) ++*launches; };
+        C* XH = reinterpret_cast<C*>(a.scratch);
+        C* Za = XH + (size_t)items * ms;
+        C* Zb = Za + (size_t)items * ms;
+        C* Xb = Zb + (size_t)items * ms;
+        C* X2b = Xb + (size_t)items * ms;
+        C* Yb = X2b + (size_t)items * ms;
+        k_big_adj_init<R><<<dim3(eb, items), 256, 0, st>>>(a.prm, sys, a.j0, a.wlen, XH, static_cast<C*>(nullptr), ms);
+        count();
+        cudaError_t err = cudaGetLastError();
+        if (err != cudaSuccess) return err;
+        k_big_ubar_factors<C><<<dim3(eb, items), 256, 0, st>>>(d, sv, a.wlen, states, Gbuf, a.wmax, Zb, Xb, ms);
+        count();
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+        if ((err = mm_launch<C, 0>(d, items, Zb, Xb, Za, ms, 1, 0, st)) != cudaSuccess) return err;
+        count();
+        if ((err = cudaMemsetAsync(Xb, 0, 3 * (size_t)items * ms * sizeof(C), st)) != cudaSuccess) return err;
+        const int T = big_tile(d);
+        C *zb = Za, *zo = Zb;
+        int xh_sliced = 0;
+        OzRev tc{};
+        if (oz) {
+            tc = *oz;
+            tc.xh = XH;
+            tc.xh_sliced = &xh_sliced;
+        }
+        auto rev = [&](const RevOps<C>& ops, C* O2, int mode) {
+            cudaError_t e2;
+            if (oz) {
+                const float2* o4[4] = {ops.p[0], ops.p[1], ops.p[2], ops.p[3]};
+                e2 = oz_rev_step(tc, o4, ops.s, zo, O2, ms, mode, 1, st, launches);
+            } else {
+                e2 = (T == 32) ? rev_launch_t<C, 32>(d, items, ops, zo, O2, ms, mode, 1, st)
+                               : rev_launch_t<C, 64>(d, items, ops, zo, O2, ms, mode, 1, st);
+                count();
+            }
+            std::swap(zb, zo);
+            return e2;
+        };
+        auto acc = [&](const C* Z, float ca, float cb, float cc) {
+            k_big_ps_acc<<<dim3(eb, items), 256, 0, st>>>(d, Z, Xb, X2b, Yb, ms, ca, cb, cc);
+            count();
+            return cudaGetLastError();
+        };
+        auto slot = [&](int r) { return zst + (size_t)r * ms; };   // item stride zs
+        for (int m = n - 1; m >= 0; --m) {      // Sbar_m = Sbar_{m+1} S_m^dag + S_m^dag Sbar_{m+1}
+            const C* S = slot(qt + 2 + m);
+            if ((err = rev(RevOps<C>{{zb, S, S, zb}, {ms, zs, zs, ms}}, nullptr, 1)) != cudaSuccess) return err;
+        }
+        for (int q = 0; q < qt; ++q) {          // chain products in reverse
+            if ((err = acc(zb, hp.ch[3 * q + 1], hp.ch[3 * q + 2], 0.f)) != cudaSuccess) return err;
+            const C* Wn = slot(2 + (qt - 1 - q));
+            if ((err = rev(RevOps<C>{{slot(1), zb, zb, Wn}, {zs, ms, ms, zs}}, Yb, 0)) != cudaSuccess) return err;
+        }
+        if ((err = acc(zb, hp.ch[3 * qt + 1], hp.ch[3 * qt + 2], hp.ch[3 * qt + 3])) != cudaSuccess) return err;
+        if (p >= 3) {   // X2bar += Ybar X^dag, Xbar += X2^dag Ybar
+            if ((err = rev(RevOps<C>{{Yb, XH, slot(0), Yb}, {ms, ms, zs, ms}}, Xb, 0)) != cudaSuccess) return err;
+            if ((err = acc(zb, 0.f, 1.f, 0.f)) != cudaSuccess) return err;
+        }
+        if (p >= 2) {   // Xbar += X2bar X^dag + X^dag X2bar
+            if ((err = rev(RevOps<C>{{X2b, XH, XH, X2b}, {ms, ms, ms, ms}}, nullptr, 1)) != cudaSuccess) return err;
+            if ((err = acc(zb, 1.f, 0.f, 0.f)) != cudaSuccess) return err;
+        }
+        if (sys.M > 0) {
+            k_big_grad<R><<<dim3(items, sys.M), 256, 0, st>>>(a.prm, sys, a.j0, a.wlen, Xb, ms, gpart);
+            count();
+        }
+        return cudaGetLastError();
+    }
+}
+
 template cudaError_t launch_big_expm<float>(const BigArgs<float>&, const DevParams&, bool, cudaStream_t, int*, float2*);
 template cudaError_t launch_big_expm<double>(const BigArgs<double>&, const DevParams&, bool, cudaStream_t, int*, double2*);
 template cudaError_t launch_big_adj_rev<float>(const BigArgs<float>&, const SysView<float>&, const StateView<float>&,
@@ -1000,5 +1243,9 @@ template cudaError_t launch_big_adj<float>(const BigArgs<float>&, const SysView<
                                            const float2*, const float2*, double*, int, int, cudaStream_t, int*);
 template cudaError_t launch_big_adj<double>(const BigArgs<double>&, const SysView<double>&, const StateView<double>&,
                                             const double2*, const double2*, double*, int, int, cudaStream_t, int*);
+
+template cudaError_t launch_big_adj_rev_ps<float>(const BigArgs<float>&, const SysView<float>&,
+                                                  const StateView<float>&, const float2*, const float2*, double*,
+                                                  const DevParams&, const float2*, cudaStream_t, int*, const OzRev*);
 
 }  // namespace qoc

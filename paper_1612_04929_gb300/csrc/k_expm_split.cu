@@ -82,18 +82,6 @@ __device__ __forceinline__ void mm_hi(float2 (&acc)[MT][MT], const float4* __res
     }
 }
 
-// (hi, lo) += (u.x + u.y) (bh + bl), the exact product residual and the rounding of the sum in lo
-__device__ __forceinline__ void pair_fma(float& hi, float& lo, float2 u, float bh, float bl) {
-    const float p = u.x * bh;
-    float e = fmaf(u.x, bh, -p);
-    e = fmaf(u.x, bl, e);
-    e = fmaf(u.y, bh, e);
-    float s, r;
-    two_sum(hi, p, s, r);
-    hi = s;
-    lo += r + e;
-}
-
 // X_ab = -i s H_ab (element o = a d + b) in pair arithmetic from the pairs s H_0, s H_k (times the
 // control pairs us[k]) and s H_det (times us[M]; Hd = nullptr: no ensemble term)
 __device__ __forceinline__ void x_pair(const float4* __restrict__ H0, const float4* __restrict__ Hk,
@@ -365,14 +353,6 @@ cudaError_t launch_expm_fwd_split(const DevParams* prm, const SysView<float>& sy
 // Shared memory holds X, X^2, X^3 and W (written in place after a second barrier): four split
 // matrices, so d <= ps_max_d().
 // ------------------------------------------------------------------------------------------
-
-// (hi, lo) + (ch + cl), pair arithmetic
-__device__ __forceinline__ void df_addc(float& hi, float& lo, float2 c) {
-    float s, r;
-    two_sum(hi, c.x, s, r);
-    hi = s;
-    lo += r + c.y;
-}
 
 // a value given as pairs (re, im) in the form its reader takes: grid-split on magic, or the full
 // FP32 value in (.x, .y) with zero (.z, .w) when magic == 0 (the operand of a plain product)

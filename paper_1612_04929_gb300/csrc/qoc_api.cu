@@ -239,7 +239,8 @@ void plan_impl(qoc_ctx* c) {
     // The Paterson-Stockmeyer form costs about p / 3 + 2 products instead of p - 1, so a larger
     // theta_max (fewer squarings, each a split product plus two adjoint products) pays: on the
     // d = 40 workload theta_max = 2 (p = 14, n = 2) against Horner's 0.5 (p = 9, n = 4).
-    c->ps = split_exp<R>(c) && c->path_kind == 0 && d <= ps_max_d() && c->opt.taylor_scheme == QOC_TAYLOR_AUTO;
+    c->ps = split_exp<R>(c) && c->opt.taylor_scheme == QOC_TAYLOR_AUTO &&
+            ((c->path_kind == 0 && d <= ps_max_d()) || (c->path_kind == 1 && !use_tc(c)));
     c->theta_max = c->opt.theta_max > 0.0 ? c->opt.theta_max : (c->ps ? 2.0 : (c->path_kind == 0 ? 0.5 : 1.0));
     // Columns whose weight is zero enter no cost term (every term is weighted by w_s), so they
     // are not propagated at all.
@@ -288,7 +289,7 @@ void plan_impl(qoc_ctx* c) {
     } else {
         const size_t dd0 = (size_t)d * d, ks = sizeof(K_t<R>);
         size_t per = 2 * ((size_t)c->ustride * cs + 3 * slice * cs);          // U, states, G, sources
-        if (c->path_kind == 1) per += big_scratch_per_item(d, sizeof(R) == 8);
+        if (c->path_kind == 1) per += big_scratch_per_item(d, sizeof(R) == 8, c->ps);
         if (use_tc(c)) per += tc_scratch_floats(d, 1) * sizeof(float);
         if (use_oz(c)) per += oz_scratch_bytes(d, 1);
         if (c->scan) per += dd0 * ks + (2 * (size_t)c->ustride * ks + seg - 1) / seg;
@@ -409,7 +410,7 @@ void plan_impl(qoc_ctx* c) {
     A(c->src, 2 * (size_t)E * W * slice * cs, "alloc sources");
     if (c->path_kind == 1) {
         c->mstride = (((size_t)d * d + 15) / 16) * 16;
-        const size_t per = big_scratch_per_item(d, sizeof(R) == 8) / ((size_t)d * d) * c->mstride;
+        const size_t per = big_scratch_per_item(d, sizeof(R) == 8, c->ps) / ((size_t)d * d) * c->mstride;
         A(c->scratch, per * (size_t)E * W, "alloc batched scratch");
     } else {
         c->scratch.release();
@@ -558,7 +559,7 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
     bool big_rev = false;
     size_t zbig_set = 0;
     if (big && c->opt.gradient == QOC_GRAD_EXACT && c->opt.adjoint == QOC_ADJ_AUTO && !use_tc(c)) {
-        zbig_set = (size_t)E * W * (size_t)(hp.p - 1 + hp.n) * c->mstride;
+        zbig_set = (size_t)E * W * (size_t)(c->ps ? ps_slots(hp.p, hp.n) : hp.p - 1 + hp.n) * c->mstride;
         const size_t need = 2 * zbig_set * sizeof(C);
         if (c->Zbig.bytes >= need) {
             big_rev = true;
@@ -577,7 +578,7 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
     auto big_args = [&](int w) {
         const int j0 = w * W;
         return BigArgs<R>{prm,      bsys,          d,     E,          j0, std::min(W, N - j0), W, c->scratch.p,
-                          c->mstride, Ub(w), c->ustride, c->sH.p ? c->sH.as<float4>() : nullptr};
+                          c->mstride, Ub(w), c->ustride, c->sH.p ? c->sH.as<float4>() : nullptr, c->ps ? 1 : 0};
     };
     int extra = 0;   // kernels of the batched calls beyond the one counted by L
     // stored product operands of the per-slice path (two wave sets)
@@ -609,6 +610,15 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
         if (c->opt.gradient == QOC_GRAD_FIRST_ORDER)
             return launch_grad_first_order<R>(sys, sv, j0, wlen, E, Sb(w), Gb(w), W, c->dt, c->gpart.as<double>(), st);
         if constexpr (sizeof(R) == 4) {
+            if (big && big_rev && c->ps) {       // Paterson-Stockmeyer reverse mode (tensor cores: BF16_SPLIT)
+                int n_l = 0;
+                OzRev oz{c->opt.fault_inject, prm, d, E * wlen, E * W, c->tc_planes.as<unsigned char>(), c->tc_maps,
+                         nullptr, nullptr};
+                cudaError_t e = launch_big_adj_rev_ps<R>(big_args(w), sys, sv, Sb(w), Gb(w), c->gpart.as<double>(), hp,
+                                                         zbig(w), st, &n_l, use_oz(c) ? &oz : nullptr);
+                extra += n_l - 1;
+                return e;
+            }
             if (big && use_oz(c) && big_rev) {   // reverse mode, products on the tensor cores
                 int n_l = 0;
                 OzRev oz{c->opt.fault_inject, prm, d, E * wlen, E * W, c->tc_planes.as<unsigned char>(), c->tc_maps,

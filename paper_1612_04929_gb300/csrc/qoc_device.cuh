@@ -110,6 +110,26 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     e = __fadd_rn(__fsub_rn(a, av), __fsub_rn(b, bv));
 }
 
+// (hi, lo) += (u.x + u.y) (bh + bl), the exact product residual and the rounding of the sum in lo
+__device__ __forceinline__ void pair_fma(float& hi, float& lo, float2 u, float bh, float bl) {
+    const float p = u.x * bh;
+    float e = fmaf(u.x, bh, -p);
+    e = fmaf(u.x, bl, e);
+    e = fmaf(u.y, bh, e);
+    float s, r;
+    two_sum(hi, p, s, r);
+    hi = s;
+    lo += r + e;
+}
+
+// (hi, lo) + (ch + cl), pair arithmetic
+__device__ __forceinline__ void df_addc(float& hi, float& lo, float2 c) {
+    float s, r;
+    two_sum(hi, c.x, s, r);
+    hi = s;
+    lo += r + c.y;
+}
+
 // Split product of two grid-split matrices (float4 = re1, im1, re2, im2 per element):
 // acc[0], acc[1] = exact sums of the grid parts (re, im), acc[2], acc[3] = the cross terms.
 template <int MT>

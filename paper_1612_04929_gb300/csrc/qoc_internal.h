@@ -187,11 +187,13 @@ struct BigArgs {
     void* Ubuf;           // propagator buffer of the wave (C_t<R>, U at 0 and U^dag at ustride / 2)
     long long ustride;
     const float4* sH;     // FP32 split form: s H_0 .. s H_det as pairs (launch_split_scale), or nullptr
+    int ps;               // 1: Paterson-Stockmeyer form of the split exponential (FP32 forms)
 };
-// bytes of scratch per wave item
-inline size_t big_scratch_per_item(int d, bool fp64) {
-    const size_t dd = (size_t)d * d;
-    return fp64 ? 6 * dd * 16 : 6 * dd * 8 > 3 * dd * 16 ? 6 * dd * 8 : 3 * dd * 16;
+// bytes of scratch per wave item: FP64 six double2 matrices; FP32 the larger of the adjoint's six
+// float2 matrices and the forward's float4 matrices (three for Horner, five for Paterson-Stockmeyer)
+inline size_t big_scratch_per_item(int d, bool fp64, bool ps = false) {
+    const size_t dd = (size_t)d * d, fwd = (ps ? 5 : 3) * dd * 16;
+    return fp64 ? 6 * dd * 16 : (6 * dd * 8 > fwd ? 6 * dd * 8 : fwd);
 }
 // zst (or nullptr): store of the p - 1 + n product operands for the reverse-mode adjoint
 // (conjugate transposes, rounded, at zst + (item * (p - 1 + n) + r) * mstride)
@@ -204,6 +206,12 @@ template <typename R>
 cudaError_t launch_big_adj_rev(const BigArgs<R>& a, const SysView<R>& sys, const StateView<R>& sv, const C_t<R>* states,
                                const C_t<R>* Gbuf, double* gpart, int p, int n, const C_t<R>* zst, cudaStream_t st,
                                int* launches, const OzRev* oz = nullptr);
+// the reverse mode of the Paterson-Stockmeyer form (FP32 forms; hp: the evaluation's parameters,
+// zst: the ps_slots(p, n) operands of each item)
+template <typename R>
+cudaError_t launch_big_adj_rev_ps(const BigArgs<R>& a, const SysView<R>& sys, const StateView<R>& sv,
+                                  const C_t<R>* states, const C_t<R>* Gbuf, double* gpart, const DevParams& hp,
+                                  const C_t<R>* zst, cudaStream_t st, int* launches, const OzRev* oz = nullptr);
 template <typename R>
 cudaError_t launch_big_adj(const BigArgs<R>& a, const SysView<R>& sys, const StateView<R>& sv, const C_t<R>* states,
                            const C_t<R>* Gbuf, double* gpart, int p, int n, cudaStream_t st, int* launches);
