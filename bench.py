@@ -31,13 +31,15 @@ UNIT = "slice-steps/s"
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, averaged over the launches
 # of one evaluation) measured by ncu, keyed by (workload, precision, kernel, wave slices)
 MEASURED_TRAFFIC = {
-    # split exponential, waves of 1125 and 875 slices: 139,826,432 and 91,752,192 bytes
-    ("transmon_cavity_d40", "fp32", "expm_fwd", 1125): 115789312.0,
+    # Paterson-Stockmeyer split exponential (k_expm_fwd_ps), one full ncu capture of the
+    # 1125-slice launch: 163,072 bytes read + 83,686,144 written (74.5 KB per slice), scaled by the
+    # slices to the average launch of the two waves (1125 and 875 slices)
+    ("transmon_cavity_d40", "fp32", "expm_fwd", 1125, 1): (163072.0 + 83686144.0) * 1000 / 1125,
 }
-# executed side of the same kernel from one full ncu capture (1125-slice launch): FMA pipe and
-# issue activity, % of peak over active cycles
+# executed side of the same kernel from that capture: FMA pipe and issue activity, % of peak over
+# active cycles
 MEASURED_PIPES = {
-    ("transmon_cavity_d40", "fp32", "expm_fwd", 1125): {"fma_pipe_pct": 47.2, "issue_active_pct": 68.7},
+    ("transmon_cavity_d40", "fp32", "expm_fwd", 1125, 1): {"fma_pipe_pct": 52.0, "issue_active_pct": 69.5},
 }
 # FP32 FMA peak from unit counts (context only; the roofline uses the measured peak):
 # SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (the maximum SM clock)
@@ -367,7 +369,8 @@ def roofline_of(prob, precision, info, prof, K, peaks, traffic_key=None):
         peak, bound, src = peaks["fp64_tflops"], "alu", peaks["fp_source"] + ", FP64"
     else:
         peak, bound, src = peaks["fp32_tflops"], "alu", peaks["fp_source"] + ", FP32"
-    traffic = MEASURED_TRAFFIC.get(traffic_key) if traffic_key else None
+    # the counters belong to one kernel of one configuration: reported only when that kernel dominates
+    traffic = MEASURED_TRAFFIC.get(traffic_key) if traffic_key and traffic_key[2] == top_name else None
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": traffic, "kernel": top_name, "launches": top_launches, "avg_launch_ms": top_ms / top_launches,
             "peak_source": src + " (of measured)",
@@ -742,9 +745,11 @@ def ours_arm(args):
     prof = cp.profile()
     cp.close()
     roof = roofline_of(prob, precision, info, prof, K, peaks,
-                       traffic_key=(prob.name, precision, "expm_fwd", info["wave_slices"]))
+                       traffic_key=(prob.name, precision, "expm_fwd", info["wave_slices"],
+                                    info.get("taylor_scheme", 0)))
     if roof is not None:
-        pipes = MEASURED_PIPES.get((prob.name, precision, roof["kernel"], info["wave_slices"]))
+        pipes = MEASURED_PIPES.get((prob.name, precision, roof["kernel"], info["wave_slices"],
+                                    info.get("taylor_scheme", 0)))
         if pipes:
             roof["executed"] = dict(pipes, source="ncu --set full, one launch of this kernel at this workload "
                                                   "(sm__pipe_fma_cycles_active, smsp__issue_active)")
