@@ -858,7 +858,7 @@ static int ew_blocks(size_t dd) {
 // then the squarings.  Scratch per item: X, X^2, X^3 and the W ping-pong (five float4 matrices).
 // Stored operands (conjugate transposes) in the slot layout of ps_slots.
 static cudaError_t big_expm_ps(const BigArgs<float>& a, const DevParams& hp, cudaStream_t st, int* launches,
-                               float2* zst) {
+                               float2* zst, const OzFwd* ozf) {
     const int p = hp.p, n = hp.n, d = a.d, items = a.wlen * a.E;
     const size_t ms = a.mstride;
     const int eb = ew_blocks((size_t)d * d);
@@ -886,18 +886,35 @@ static cudaError_t big_expm_ps(const BigArgs<float>& a, const DevParams& hp, cud
                                                           hp.eu);
     count();
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    // With tensor-core products (ozf) every product is split-grade, so every chain matrix is written
+    // grid-split on its own bound.  Sliced matrices: 0 / 1 the A / B operand of X^2 and of the
+    // squarings (1 keeps X for X^3), 2 X^2, 3 X^3 (once for the whole chain), 4 the chain operand.
+    const PsAdd none{};
+    auto tc = [&](const float4* A, int am, const float4* B, int bm, float4* O, int kind, float mg,
+                  const PsAdd& ps) -> cudaError_t {
+        int n_l = 0;
+        const cudaError_t e2 = oz_fwd_product(*ozf, A, am, B, bm, O, ms, kind, mg, ps.X, ps.X2, ps.c0, ps.c1, ps.c2,
+                                              st, &n_l);
+        if (launches) *launches += n_l;
+        return e2;
+    };
     if (p >= 2) {
-        if ((err = mm_launch<float4, 1>(d, items, X, X, X2, ms, 1, 0, st, magic(hp.e2))) != cudaSuccess) return err;
-        count();
+        err = ozf ? tc(X, 0, X, 1, X2, 1, magic(hp.e2), none)
+                  : mm_launch<float4, 1>(d, items, X, X, X2, ms, 1, 0, st, magic(hp.e2));
+        if (!ozf) count();
+        if (err != cudaSuccess) return err;
         if ((err = store(X2, 0)) != cudaSuccess) return err;
     }
     if (p >= 3) {
-        if ((err = mm_launch<float4, 1>(d, items, X2, X, X3, ms, 1, 0, st, magic(hp.e3))) != cudaSuccess) return err;
-        count();
+        err = ozf ? tc(X2, 2, nullptr, 1, X3, 1, magic(hp.e3), none)
+                  : mm_launch<float4, 1>(d, items, X2, X, X3, ms, 1, 0, st, magic(hp.e3));
+        if (!ozf) count();
+        if (err != cudaSuccess) return err;
         if ((err = store(X3, 1)) != cudaSuccess) return err;
     }
+    auto form_of = [&](int q) { return ozf ? (q == 0 ? hp.eu : hp.ew[q]) : form_w(q); };
     k_big_ps_top<<<dim3(eb, items), 256, 0, st>>>(d, X, X2, X3, win, ms, coef(3 * qt), coef(3 * qt + 1),
-                                                  coef(3 * qt + 2), coef(3 * qt + 3), p, form_w(qt));
+                                                  coef(3 * qt + 2), coef(3 * qt + 3), p, form_of(qt));
     count();
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     for (int q = qt - 1; q >= 0; --q) {
@@ -908,19 +925,27 @@ static cudaError_t big_expm_ps(const BigArgs<float>& a, const DevParams& hp, cud
         ps.c0 = coef(3 * q);
         ps.c1 = coef(3 * q + 1);
         ps.c2 = coef(3 * q + 2);
-        const int f = form_w(q);
+        const int f = form_of(q);
         const float mg = f == kFullForm ? 0.f : magic(f);
-        err = (q <= qs) ? mm_launch<float4, 1>(d, items, X3, win, wout, ms, 2, 0, st, mg, ps)
-                        : mm_launch<float4, 2>(d, items, X3, win, wout, ms, 2, 0, st, mg, ps);
-        count();
+        if (ozf) {
+            err = tc(q == qt - 1 ? X3 : nullptr, 3, win, 4, wout, 2, mg, ps);
+        } else {
+            err = (q <= qs) ? mm_launch<float4, 1>(d, items, X3, win, wout, ms, 2, 0, st, mg, ps)
+                            : mm_launch<float4, 2>(d, items, X3, win, wout, ms, 2, 0, st, mg, ps);
+            count();
+        }
         if (err != cudaSuccess) return err;
         std::swap(win, wout);
     }
     for (int m = 0; m < n; ++m) {
         if ((err = store(win, qt + 2 + m)) != cudaSuccess) return err;
-        if ((err = mm_launch<float4, 1>(d, items, win, win, wout, ms, 1, 0, st, magic(hp.eu))) != cudaSuccess)
-            return err;
-        count();
+        if (ozf) {
+            err = tc(win, 0, win, 1, wout, 1, magic(hp.eu), none);
+        } else {
+            err = mm_launch<float4, 1>(d, items, win, win, wout, ms, 1, 0, st, magic(hp.eu));
+            count();
+        }
+        if (err != cudaSuccess) return err;
         std::swap(win, wout);
     }
     k_big_store_u<float4, float2><<<dim3(eb, items), 256, 0, st>>>(d, win, ms, reinterpret_cast<float2*>(a.Ubuf),
@@ -931,7 +956,7 @@ static cudaError_t big_expm_ps(const BigArgs<float>& a, const DevParams& hp, cud
 
 template <typename R>
 cudaError_t launch_big_expm(const BigArgs<R>& a, const DevParams& hp, bool split, cudaStream_t st, int* launches,
-                            C_t<R>* zst) {
+                            C_t<R>* zst, const OzFwd* ozf) {
     const int p = hp.p, n = hp.n, m_split = hp.m_split;
     const int d = a.d, items = a.wlen * a.E;
     const size_t dd = (size_t)d * d;
@@ -946,7 +971,7 @@ cudaError_t launch_big_expm(const BigArgs<R>& a, const DevParams& hp, bool split
         count();
         return cudaGetLastError();
     };
-    if constexpr (sizeof(R) == 4) if (split && a.ps) return big_expm_ps(a, hp, st, launches, zst);
+    if constexpr (sizeof(R) == 4) if (split && a.ps) return big_expm_ps(a, hp, st, launches, zst, ozf);
     if constexpr (sizeof(R) == 4) if (split) {
         float4* X = reinterpret_cast<float4*>(a.scratch);
         float4* Za = X + (size_t)items * a.mstride;
@@ -1231,8 +1256,10 @@ cudaError_t launch_big_adj_rev_ps(const BigArgs<R>& a, const SysView<R>& sys, co
     }
 }
 
-template cudaError_t launch_big_expm<float>(const BigArgs<float>&, const DevParams&, bool, cudaStream_t, int*, float2*);
-template cudaError_t launch_big_expm<double>(const BigArgs<double>&, const DevParams&, bool, cudaStream_t, int*, double2*);
+template cudaError_t launch_big_expm<float>(const BigArgs<float>&, const DevParams&, bool, cudaStream_t, int*, float2*,
+                                            const OzFwd*);
+template cudaError_t launch_big_expm<double>(const BigArgs<double>&, const DevParams&, bool, cudaStream_t, int*, double2*,
+                                             const OzFwd*);
 template cudaError_t launch_big_adj_rev<float>(const BigArgs<float>&, const SysView<float>&, const StateView<float>&,
                                                const float2*, const float2*, double*, int, int, const float2*,
                                                cudaStream_t, int*, const OzRev*);

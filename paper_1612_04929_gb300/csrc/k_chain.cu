@@ -49,6 +49,23 @@ cudaError_t launch_norms(const double2* mats, int count, int d, double* norms, c
     return cudaGetLastError();
 }
 
+// 1/k!, k = 0 .. kPsCoefs - 1, evaluated at compile time (no FP64 division on the device: the
+// FP64 pipe of this part issues a warp instruction in tens of cycles, and the order pick is on the
+// critical path of every evaluation)
+struct InvFactorials {
+    double v[kPsCoefs];
+};
+constexpr InvFactorials make_inv_factorials() {
+    InvFactorials t{};
+    double f = 1.0;
+    for (int k = 0; k < kPsCoefs; ++k) {
+        if (k > 1) f *= k;
+        t.v[k] = 1.0 / f;
+    }
+    return t;
+}
+__constant__ InvFactorials kInvFact = make_inv_factorials();
+
 // smallest e with 2^e >= b (clamped to [-100, 100]; -100 for b <= 0)
 __device__ __forceinline__ int grid_exp(double b) {
     if (!(b > 0.0)) return -100;
@@ -108,12 +125,9 @@ __device__ double pick_orders(double theta, double theta_max, double tol, int p_
     // remainder sum_{k > p} ts^k / k! <= ts^(p+1) / (p+1)! / (1 - ts / (p+2)).
     double rem_t = 1e300;
     if (ts < p + 2.0) {
-        double fp = 1.0, pt = ts;
-        for (int k = 2; k <= p + 1; ++k) {
-            fp *= k;
-            pt *= ts;
-        }
-        rem_t = pt / fp / (1.0 - ts / (p + 2.0));
+        double pt = ts;
+        for (int k = 2; k <= p + 1; ++k) pt *= ts;
+        rem_t = pt * kInvFact.v[p + 1] * (p + 2.0) / (p + 2.0 - ts);
     }
     prm->ex = grid_exp(ts);
     prm->ez = grid_exp(1.0625 * exp(ts));
@@ -162,12 +176,7 @@ __global__ void k_theta(const double* __restrict__ u, int M, int N, const double
     const bool ok = ts >= 0.0;
     const int p = ok ? prm->p : 0;
     if (t < kPsCoefs) {
-        double c = 0.0;
-        if (ok && t <= p) {
-            double f = 1.0;
-            for (int k = 2; k <= t; ++k) f *= k;
-            c = 1.0 / f;
-        }
+        const double c = (ok && t <= p) ? kInvFact.v[t] : 0.0;
         const float h = (float)c;
         prm->ch[t] = h;
         prm->cl[t] = (float)(c - (double)h);
@@ -175,13 +184,8 @@ __global__ void k_theta(const double* __restrict__ u, int M, int N, const double
     if (t < kPsMaxBlocks) {
         int e = ok ? prm->eu : 0;
         if (ok && t > 0) {
-            double f = 1.0, pw = 1.0, b = 0.0;
-            for (int k = 2; k < 3 * t; ++k) f *= k;   // (3t - 1)!
-            for (int k = 3 * t; k <= p; ++k) {
-                f *= k;
-                b += pw / f;
-                pw *= ts;
-            }
+            double b = 0.0;   // sum_{k = 3t}^{p} ts^(k - 3t) / k!, by Horner from the top
+            for (int k = p; k >= 3 * t; --k) b = fma(b, ts, kInvFact.v[k]);
             e = grid_exp(1.0625 * b);
         }
         prm->ew[t] = e;

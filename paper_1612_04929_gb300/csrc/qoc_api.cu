@@ -166,6 +166,7 @@ struct qoc_ctx {
         gkey[0] = gkey[1] = gkey[2] = nullptr;
     }
     TcMaps tc_maps{};
+    TcMaps tc_fwd_maps{};                // the tensor-core forward products' maps over the same planes
 
     size_t device_bytes() const {
         const DevBuf* all[] = {&H64, &HR, &dDelta, &norms, &psiTR, &pathR, &fmask, &colw, &ckpt, &Ubuf, &states,
@@ -218,6 +219,12 @@ bool is_fp64(const qoc_ctx* c) { return c->opt.precision == QOC_PREC_FP64; }
 bool use_tc(const qoc_ctx* c) { return c->opt.precision == QOC_PREC_TF32_SPLIT && c->path_kind == 1; }
 // BF16_SPLIT: the FP32 form with the large-d adjoint products on tcgen05 with exact accumulation
 bool use_oz(const qoc_ctx* c) { return c->opt.precision == QOC_PREC_BF16_SPLIT && c->path_kind == 1; }
+// ... and its Paterson-Stockmeyer forward products too, for kOzFwdMinD <= d <= kOzFwdMaxD (below,
+// the 128 x 64 tiles are mostly padding and the SIMT split products are faster; above, the exact
+// slice levels could overflow their accumulators)
+bool oz_fwd_on(const qoc_ctx* c) {
+    return use_oz(c) && c->ps && c->d >= kOzFwdMinD && c->d <= kOzFwdMaxD;
+}
 
 template <typename R>
 bool split_exp(const qoc_ctx* c) {
@@ -291,7 +298,7 @@ void plan_impl(qoc_ctx* c) {
         size_t per = 2 * ((size_t)c->ustride * cs + 3 * slice * cs);          // U, states, G, sources
         if (c->path_kind == 1) per += big_scratch_per_item(d, sizeof(R) == 8, c->ps);
         if (use_tc(c)) per += tc_scratch_floats(d, 1) * sizeof(float);
-        if (use_oz(c)) per += oz_scratch_bytes(d, 1);
+        if (use_oz(c)) per += std::max(oz_scratch_bytes(d, 1), oz_fwd_on(c) ? oz_fwd_scratch_bytes(d, 1) : 0);
         if (c->scan) per += dd0 * ks + (2 * (size_t)c->ustride * ks + seg - 1) / seg;
         if (c->path_kind == 0 && c->opt.gradient == QOC_GRAD_EXACT && c->opt.adjoint == QOC_ADJ_AUTO)
             per += 2 * (size_t)kZCap * ((dd0 + 31) / 32 * 32) * cs;
@@ -418,8 +425,11 @@ void plan_impl(qoc_ctx* c) {
     if (use_oz(c)) {
         // the tensor maps cover exactly d x d of every plane (reads past d fill zeros), so the
         // padding columns of the planes are never read and need no clearing
-        A(c->tc_planes, oz_scratch_bytes(d, E * W), "alloc tensor-core slices");
+        // the forward's and the adjoint's products run on one stream and share the plane array
+        A(c->tc_planes, std::max(oz_scratch_bytes(d, E * W), oz_fwd_on(c) ? oz_fwd_scratch_bytes(d, E * W) : 0),
+          "alloc tensor-core slices");
         check_cuda(c, oz_make_maps(c->tc_planes.p, d, E * W, &c->tc_maps), "tensor maps");
+        if (oz_fwd_on(c)) check_cuda(c, oz_fwd_make_maps(c->tc_planes.p, d, E * W, &c->tc_fwd_maps), "tensor maps");
     } else if (use_tc(c)) {
         A(c->tc_planes, tc_scratch_floats(d, E * W) * sizeof(float), "alloc tensor-core planes");
         check_cuda(c, cudaMemsetAsync(c->tc_planes.p, 0, c->tc_planes.bytes, st), "clear planes");
@@ -591,7 +601,8 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
         const int j0 = w * W, wlen = std::min(W, N - j0);
         if (big) {
             int n_l = 0;
-            cudaError_t e = launch_big_expm<R>(big_args(w), hp, split, st, &n_l, zbig(w));
+            OzFwd ozf{c->opt.fault_inject, prm, d, E * wlen, E * W, c->tc_planes.as<unsigned char>(), c->tc_fwd_maps};
+            cudaError_t e = launch_big_expm<R>(big_args(w), hp, split, st, &n_l, zbig(w), oz_fwd_on(c) ? &ozf : nullptr);
             extra += n_l - 1;
             return e;
         }

@@ -197,9 +197,11 @@ inline size_t big_scratch_per_item(int d, bool fp64, bool ps = false) {
 }
 // zst (or nullptr): store of the p - 1 + n product operands for the reverse-mode adjoint
 // (conjugate transposes, rounded, at zst + (item * (p - 1 + n) + r) * mstride)
+struct OzFwd;
+// ozf (FP32 forms with the Paterson-Stockmeyer form only): its products on the tensor cores
 template <typename R>
 cudaError_t launch_big_expm(const BigArgs<R>& a, const DevParams& hp, bool split, cudaStream_t st, int* launches,
-                            C_t<R>* zst = nullptr);
+                            C_t<R>* zst = nullptr, const OzFwd* ozf = nullptr);
 struct OzRev;
 // oz (FP32 form only, or nullptr): run the reverse-mode products on the tensor cores (BF16_SPLIT)
 template <typename R>
@@ -250,11 +252,15 @@ cudaError_t tc_make_maps(float* planes, int d, int items, TcMaps* maps);
 cudaError_t launch_tc_adj(const TcAdjArgs& a, cudaStream_t st, int* launches);
 
 // ---- tensor-core adjoint products with exact leading-level accumulation, BF16_SPLIT (k_oz.cu) ----
-constexpr int kOzSlices = 4;  // seven-bit slices per value
-constexpr int kOzMats = 5;    // sliced matrices per item: A1, B1, A2, B2 of a reverse step, X^dag
+constexpr int kOzSlices = 4;     // seven-bit slices per value (adjoint products: FP32-grade)
+constexpr int kOzFwdSlices = 6;  // seven-bit slices per value (forward products: split-grade)
+constexpr int kOzFwdMinD = 128;  // d range whose forward products BF16_SPLIT runs on the tensor cores
+constexpr int kOzFwdMaxD = 384;  // (the three exact slice levels stay exact up to here)
+constexpr int kOzMats = 5;       // sliced matrices per item: A1, B1, A2, B2 of a reverse step, X^dag
 inline int oz_ld(int d) { return (d + 7) / 8 * 8; }   // plane row stride (BF16): 16-byte rows for TMA
 struct OzSliceJob {
-    const float2* src;      // d x d row-major FP32 complex matrices, item i at src + i * stride
+    const void* src;        // d x d row-major complex matrices, item i at src + i * stride elements:
+                            // float2 (adjoint) or float4 value pairs (forward)
     size_t stride;
     int mat;                // plane matrix to write
     int col;                // 0: row layout (A operand), 1: column layout (B operand)
@@ -292,6 +298,25 @@ cudaError_t launch_oz_mm(const OzJobs& jobs, int njobs, int d, int items, int ca
 // O2 += A2 B2 / i; mode 1 (squaring) O1 = A1 B1 + A2 B2; ops = {A1, B1, A2, B2} with item strides
 cudaError_t oz_rev_step(const OzRev& z, const float2* const ops[4], const size_t strides[4], float2* O1, float2* O2,
                         size_t ms, int mode, int i, cudaStream_t st, int* launches);
+
+// The forward products of the Paterson-Stockmeyer form on the tensor cores (BF16_SPLIT, batched
+// path): six seven-bit slices of the value pairs, the leading two slice levels accumulated exactly
+// and the rest pre-weighted, so a product is as accurate as the split SIMT product it replaces.
+struct OzFwd {
+    int fault;              // qoc_options.fault_inject
+    DevParams* prm;
+    int d, items, cap;
+    unsigned char* scratch; // oz_fwd_scratch_bytes(d, cap): planes, then exponents
+    TcMaps maps;            // oz_fwd_make_maps over the planes
+};
+size_t oz_fwd_scratch_bytes(int d, int items);
+cudaError_t oz_fwd_make_maps(void* planes, int d, int items, TcMaps* maps);
+// out = A B (kind 1) or A B + c0 I + c1 X + c2 X^2 (kind 2, the chain product), written as value
+// pairs grid-split with `magic`; a_src / b_src (item stride ms) are sliced into matrices a_mat /
+// b_mat first, or null when that matrix already holds the operand's slices
+cudaError_t oz_fwd_product(const OzFwd& z, const float4* a_src, int a_mat, const float4* b_src, int b_mat,
+                           float4* out, size_t ms, int kind, float magic, const float4* X, const float4* X2, float2 c0,
+                           float2 c1, float2 c2, cudaStream_t st, int* launches);
 
 // ---- serial sweeps (k_serial.cu) ----
 // mode 0: forward propagation of one wave (grid z = 1) from checkpoint `seg0`, storing the

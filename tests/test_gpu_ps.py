@@ -58,6 +58,15 @@ def test_batched_forced_orders(precision, pn):
     assert info["kernel_path"] == 1 and info["adjoint_form"] == 0
 
 
+@pytest.mark.parametrize("pn", [(2, 1), (3, 0), (4, 2), (8, 1), (12, 0)])
+def test_batched_tensor_core_forward_forced_orders(pn):
+    """BF16_SPLIT from d = 128: the forward's products on the tensor cores (six seven-bit slices,
+    two exact levels), 130 = 128 + 2 rows and 2 x 64 + 2 columns of tiles: every tile edge ragged."""
+    prob = sy.random_problem(d=130, M=2, N=4, S=2, seed=410, nF=2, dt=0.03, u_scale=0.8)
+    info = against_truncated_series(prob, "bf16", *pn)
+    assert info["kernel_path"] == 1 and info["adjoint_form"] == 0
+
+
 @pytest.mark.parametrize("d", [9, 40, 70])
 def test_default_orders_match_oracle_and_horner(d):
     """Default (p, n) (theta_max 2): the oracle bar, and the Horner form of the same polynomial
