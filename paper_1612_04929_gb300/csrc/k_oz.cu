@@ -179,43 +179,89 @@ __host__ __device__ inline size_t oz_plane(int item, int mat, int part) {
 // ------------------------------------------------------------------------------------------
 // Row layout (A operand): plane row r = row r of M, exponent per row.  Column layout (B operand,
 // K-major): plane row c = column c of M, exponent per column (no conjugation is applied).
+// Eight consecutive elements of one plane row, as one 16-byte store (the plane rows are padded to
+// a multiple of eight elements and start on 16-byte boundaries)
+__device__ __forceinline__ void store8(__nv_bfloat16* dst, const float (&v)[8]) {
+    uint4 w;
+    __nv_bfloat162 h;
+    h = __floats2bfloat162_rn(v[0], v[1]);
+    w.x = *reinterpret_cast<uint32_t*>(&h);
+    h = __floats2bfloat162_rn(v[2], v[3]);
+    w.y = *reinterpret_cast<uint32_t*>(&h);
+    h = __floats2bfloat162_rn(v[4], v[5]);
+    w.z = *reinterpret_cast<uint32_t*>(&h);
+    h = __floats2bfloat162_rn(v[6], v[7]);
+    w.w = *reinterpret_cast<uint32_t*>(&h);
+    *reinterpret_cast<uint4*>(dst) = w;
+}
+
+// the slices of eight consecutive elements of one plane row (k0 .. k0 + 7; zero past d), written
+// as 16-byte stores into the row's 2 NS planes
+template <int NS>
+__device__ __forceinline__ void put8(__nv_bfloat16* __restrict__ planes, size_t pbase, size_t psz, size_t rowoff,
+                                     const float4 (&q)[8], int e, bool role_a) {
+    float sr[8][NS], si[8][NS];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        slices<NS>(q[i].x, q[i].y, e, role_a, sr[i]);
+        slices<NS>(q[i].z, q[i].w, e, role_a, si[i]);
+    }
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        float vr[8], vi[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            vr[i] = sr[i][s];
+            vi[i] = si[i][s];
+        }
+        store8(planes + (pbase + s) * psz + rowoff, vr);
+        store8(planes + (pbase + NS + s) * psz + rowoff, vi);
+    }
+}
+
 template <int NS, typename In>
 __global__ void __launch_bounds__(256)
 k_oz_slice(OzSliceJobs jobs, __nv_bfloat16* __restrict__ planes, int* __restrict__ exps, int d, int ldp) {
     constexpr int NPART = 2 * NS;
-    __shared__ float4 tile[32][33];
+    constexpr int KT = 64;                       // rows of M per staged tile (column layout)
+    __shared__ float4 tile[KT][33];
     __shared__ float cmax[8][32];
     __shared__ int cexp[32];
     const OzSliceJob jb = jobs.job[blockIdx.z];
     const int item = blockIdx.y, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const In* M = static_cast<const In*>(jb.src) + (size_t)item * jb.stride;
     const size_t psz = (size_t)d * ldp;
+    const size_t pbase = oz_plane<NPART>(item, jb.mat, 0);
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
     // the exponent comes from the rounded values |re|, |im| (a pair's sum rounded up to 2^e only
     // raises e: conservative)
     auto mag = [](float4 q) { return fmaxf(fabsf(q.x + q.y), fabsf(q.z + q.w)); };
-    auto put = [&](int plane_row, int k, float4 q, int e, bool role_a) {
-        float qr[NS], qi[NS];
-        slices<NS>(q.x, q.y, e, role_a, qr);
-        slices<NS>(q.z, q.w, e, role_a, qi);
-#pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            planes[oz_plane<NPART>(item, jb.mat, s) * psz + (size_t)plane_row * ldp + k] = __float2bfloat16_rn(qr[s]);
-            planes[oz_plane<NPART>(item, jb.mat, NS + s) * psz + (size_t)plane_row * ldp + k] =
-                __float2bfloat16_rn(qi[s]);
-        }
-    };
     if (!jb.col) {
+        // row layout: one warp per row, each lane eight consecutive columns per 256-column chunk
+        // (d <= 512: at most two chunks, held in registers between the maximum and the slicing)
         const int r = blockIdx.x * 8 + warp;
         if (r >= d) return;
+        float4 v[2][8];
         float m = 0.f;
-        for (int b = lane; b < d; b += 32) m = fmaxf(m, mag(as_pairs(M[(size_t)r * d + b])));
+#pragma unroll
+        for (int ch = 0; ch < 2; ++ch)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int b = ch * 256 + lane * 8 + i;
+                v[ch][i] = b < d ? as_pairs(M[(size_t)r * d + b]) : zero4;
+                m = fmaxf(m, mag(v[ch][i]));
+            }
         for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
         const int e = scale_exp(m);
         if (lane == 0) exps[((size_t)item * kOzMats + jb.mat) * d + r] = e;
-        for (int b = lane; b < d; b += 32) put(r, b, as_pairs(M[(size_t)r * d + b]), e, true);
+#pragma unroll
+        for (int ch = 0; ch < 2; ++ch) {
+            const int b0 = ch * 256 + lane * 8;
+            if (b0 < d) put8<NS>(planes, pbase, psz, (size_t)r * ldp + b0, v[ch], e, true);
+        }
         return;
     }
-    // column layout: 32 columns c0 .. c0 + 31 per CTA
+    // column layout: 32 columns c0 .. c0 + 31 per CTA; plane row c (a column of M) with k along it
     const int c0 = blockIdx.x * 32;
     if (c0 >= d) return;
     const int c = c0 + lane;
@@ -232,15 +278,21 @@ k_oz_slice(OzSliceJobs jobs, __nv_bfloat16* __restrict__ planes, int* __restrict
         if (c < d) exps[((size_t)item * kOzMats + jb.mat) * d + c] = e;
     }
     __syncthreads();
-    for (int k0 = 0; k0 < d; k0 += 32) {
-        for (int q = warp; q < 32; q += 8) {   // tile[k][c]: row k0 + q of M, columns c0 ..
+    // tiles of KT rows: staged with the lanes along the columns (coalesced reads), then thread t
+    // slices column t % 32 over the eight rows 8 (t / 32) .. + 7 of the tile
+    const int tc = tid & 31, tk = (tid >> 5) * 8;
+    for (int k0 = 0; k0 < d; k0 += KT) {
+        for (int q = warp; q < KT; q += 8) {
             const int k = k0 + q;
-            tile[q][lane] = (k < d && c < d) ? as_pairs(M[(size_t)k * d + c]) : make_float4(0.f, 0.f, 0.f, 0.f);
+            tile[q][lane] = (k < d && c < d) ? as_pairs(M[(size_t)k * d + c]) : zero4;
         }
         __syncthreads();
-        for (int q = warp; q < 32; q += 8) {   // plane row c0 + q (a column of M), k along lanes
-            const int cc = c0 + q, k = k0 + lane;
-            if (cc < d && k < d) put(cc, k, tile[lane][q], cexp[q], false);
+        const int cc = c0 + tc, kk = k0 + tk;
+        if (cc < d && kk < d) {
+            float4 q8[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) q8[i] = tile[tk + i][tc];
+            put8<NS>(planes, pbase, psz, (size_t)cc * ldp + kk, q8, cexp[tc], false);
         }
         __syncthreads();
     }
