@@ -156,6 +156,18 @@ typedef struct qoc_options {
                              (theta_max default 0.5 there).  The polynomial, its truncation and the
                              gradient's definition are the same; qoc_info.taylor_scheme reports the
                              form used. */
+    int autotune;         /* 0 (default): the built-in choices.  1: before the first evaluation of a
+                             context (unitary propagation only), time candidate configurations on
+                             the caller's own inputs and keep the fastest: the Taylor scheme (if
+                             taylor_scheme is auto), theta_max x {1/2, 1, 2} (if theta_max is
+                             left at 0) and the sweep form (if sweep is auto), one after another,
+                             each candidate one warm-up and two timed evaluations.  Every
+                             candidate computes the same cost and gradient to the form's tolerance.
+                             The choice is cached per process for the same form, dimensions and
+                             columns, so later contexts of that shape skip the timing.  The
+                             evaluation that triggers it synchronises the context stream and may
+                             not be captured into a graph (a qoc_options.graph context tunes
+                             before it captures). */
 } qoc_options;
 
 enum { QOC_SWEEP_AUTO = 0, QOC_SWEEP_SERIAL = 1, QOC_SWEEP_SCAN = 2 };
@@ -182,6 +194,8 @@ typedef struct qoc_info {
                              kept as d x r factors, r = 2^n S; small S, per-slice kernels), 4 the
                              state mode's reverse pass over its matrix-vector chain */
     int taylor_scheme;    /* 0 Horner, 1 Paterson-Stockmeyer (see qoc_options.taylor_scheme) */
+    int autotune_candidates; /* configurations timed by the autotuner for this context (0: none, or
+                             the choice came from the process cache) */
 } qoc_info;
 
 /* Per-kernel timings gathered while qoc_options.profile is set: for each kernel class the number

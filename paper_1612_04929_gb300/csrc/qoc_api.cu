@@ -23,6 +23,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -133,6 +135,9 @@ struct qoc_ctx {
 
     // plan
     bool planned = false;
+    bool tuned = false;                  // the autotuner has run (or found a cached choice)
+    int tune_candidates = 0;             // configurations it timed
+    bool theta_user = false;             // theta_max was set by the caller (not tuned)
     int W = 0, nw = 0, seg = 0, nseg_total = 0, path_kind = 0;
     int Spad = 0, cb = 0, ncb = 0, pstride = 0, S_eff = 0;
     bool scan = false;                   // segmented-scan form of the two recursions
@@ -467,9 +472,14 @@ void plan_impl(qoc_ctx* c) {
     A(c->gpart, (size_t)E * M * N * sizeof(double) + 8, "alloc gpart");
     A(c->prm, sizeof(DevParams), "alloc params");
     check_cuda(c, cudaMemsetAsync(c->prm.p, 0, sizeof(DevParams), st), "memset params");
-    A(c->u_h, (size_t)M * N * sizeof(double) + 8, "alloc u");
-    A(c->grad_h, (size_t)M * N * sizeof(double) + 8, "alloc grad");
-    A(c->out_h, 8 * sizeof(double), "alloc out");
+    // the host API's staging buffers survive a re-plan of the same shape (the autotuner re-plans
+    // while the caller's controls already sit in u_h)
+    auto keep = [&](DevBuf& b, size_t bytes, const char* what) {
+        if (!(b.p && b.bytes == bytes)) A(b, bytes, what);
+    };
+    keep(c->u_h, (size_t)M * N * sizeof(double) + 8, "alloc u");
+    keep(c->grad_h, (size_t)M * N * sizeof(double) + 8, "alloc grad");
+    keep(c->out_h, 8 * sizeof(double), "alloc out");
     check_cuda(c, cudaStreamSynchronize(st), "plan sync");
     c->planned = true;
 }
@@ -1041,8 +1051,11 @@ void evaluate_state_impl(qoc_ctx* c, const double* u, double* grad, double* out)
     c->launches = launches;
 }
 
+void autotune(qoc_ctx* c, const double* u, double* grad, double* out);
+
 void evaluate(qoc_ctx* c, const double* u, double* grad, double* out, const DevParams* known = nullptr) {
     if (!c->planned) plan(c);
+    if (c->opt.autotune && !c->tuned) autotune(c, u, grad, out);
     if (c->path_kind == 2) {
         if (is_fp64(c)) evaluate_state_impl<double>(c, u, grad, out);
         else evaluate_state_impl<float>(c, u, grad, out);
@@ -1050,6 +1063,90 @@ void evaluate(qoc_ctx* c, const double* u, double* grad, double* out, const DevP
     }
     if (is_fp64(c)) evaluate_impl<double>(c, u, grad, out, known);
     else evaluate_impl<float>(c, u, grad, out, known);
+}
+
+// ------------------------------------------------------------------------------------------
+// autotuner (qoc_options.autotune): coordinate descent over the Taylor scheme, theta_max and the
+// sweep form, each candidate timed by CUDA events on the context stream over two evaluations of
+// the caller's inputs after one warm-up; the choice is cached per process and shape
+// ------------------------------------------------------------------------------------------
+struct TuneChoice {
+    int taylor_scheme;
+    int sweep;
+    double theta_max;
+};
+std::mutex g_tune_mu;
+std::map<std::vector<long long>, TuneChoice> g_tune_cache;
+
+double time_evals(qoc_ctx* c, const double* u, double* grad, double* out) {
+    evaluate(c, u, grad, out);   // warm-up: first touches, the launch attributes
+    cudaEvent_t a = nullptr, b = nullptr;
+    check_cuda(c, cudaEventCreate(&a), "autotune event");
+    check_cuda(c, cudaEventCreate(&b), "autotune event");
+    cudaEventRecord(a, c->stream);
+    for (int k = 0; k < 2; ++k) evaluate(c, u, grad, out);
+    cudaEventRecord(b, c->stream);
+    const cudaError_t e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (e == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    check_cuda(c, e, "autotune timing");
+    return ms / 2.0;
+}
+
+void apply_choice(qoc_ctx* c, const TuneChoice& t) {
+    c->opt.taylor_scheme = t.taylor_scheme;
+    c->opt.sweep = t.sweep;
+    c->opt.theta_max = t.theta_max;
+    c->planned = false;
+    plan(c);
+}
+
+void autotune(qoc_ctx* c, const double* u, double* grad, double* out) {
+    c->tuned = true;   // set first: the timed evaluations below run the normal path
+    c->tune_candidates = 0;
+    if (c->path_kind == 2) return;   // state mode: nothing here to choose
+    const qoc_options& o = c->opt;
+    const std::vector<long long> key = {o.precision, c->d, c->N, c->M, c->S_eff, c->E, o.gradient, o.adjoint,
+                                        o.taylor_scheme, o.sweep, c->theta_user ? (long long)(o.theta_max * 1e9) : -1,
+                                        o.plain_fp32_exp, o.reversal};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            apply_choice(c, it->second);
+            return;
+        }
+    }
+    TuneChoice best{o.taylor_scheme, o.sweep, o.theta_max};
+    double best_ms = time_evals(c, u, grad, out);
+    c->tune_candidates = 1;
+    auto trial = [&](const TuneChoice& t) {
+        apply_choice(c, t);
+        const double ms = time_evals(c, u, grad, out);
+        ++c->tune_candidates;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = t;
+        }
+    };
+    if (best.taylor_scheme == QOC_TAYLOR_AUTO && c->ps) trial({QOC_TAYLOR_HORNER, best.sweep, best.theta_max});
+    if (!c->theta_user) {
+        apply_choice(c, best);
+        const double t0 = c->theta_max;   // the planner's default for the scheme chosen so far
+        const TuneChoice base = best;
+        trial({base.taylor_scheme, base.sweep, 0.5 * t0});
+        trial({base.taylor_scheme, base.sweep, 2.0 * t0});
+    }
+    if (best.sweep == QOC_SWEEP_AUTO) {
+        const TuneChoice base = best;
+        trial({base.taylor_scheme, QOC_SWEEP_SERIAL, base.theta_max});
+        trial({base.taylor_scheme, QOC_SWEEP_SCAN, base.theta_max});
+    }
+    apply_choice(c, best);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = best;
 }
 
 qoc_status device_error(qoc_ctx* c) {
@@ -1118,7 +1215,7 @@ qoc_status qoc_create(qoc_ctx** out, const qoc_options* opt) {
         o.fault_inject < 0 || o.fault_inject > 1 || o.adjoint < QOC_ADJ_AUTO || o.adjoint > QOC_ADJ_RECOMPUTE ||
         o.reversal < 0 || o.reversal > 1 || o.propagation < QOC_PROP_UNITARY || o.propagation > QOC_PROP_STATE ||
         o.exponential < QOC_EXP_TAYLOR || o.exponential > QOC_EXP_CHEBYSHEV || o.taylor_scheme < QOC_TAYLOR_AUTO ||
-        o.taylor_scheme > QOC_TAYLOR_HORNER)
+        o.taylor_scheme > QOC_TAYLOR_HORNER || o.autotune < 0 || o.autotune > 1)
         return QOC_ERR_ARG;
     if (o.exponential == QOC_EXP_CHEBYSHEV && o.propagation != QOC_PROP_STATE) return QOC_ERR_UNSUPPORTED;
     // reversal regenerates states through the stored propagators, whose FP32 rounding would
@@ -1126,10 +1223,12 @@ qoc_status qoc_create(qoc_ctx** out, const qoc_options* opt) {
     if (o.reversal && o.precision != QOC_PREC_FP64) return QOC_ERR_UNSUPPORTED;
     const bool f64 = o.precision == QOC_PREC_FP64;
     if (o.tol == 0.0) o.tol = f64 ? 1e-15 : 1e-8;
+    const bool theta_user = o.theta_max > 0.0;
     if (o.theta_max == 0.0 && f64) o.theta_max = 0.25;   // FP32 forms: resolved by the planner
     qoc_ctx* ctx = new (std::nothrow) qoc_ctx;
     if (!ctx) return QOC_ERR_OOM;
     ctx->opt = o;
+    ctx->theta_user = theta_user || f64;
     cudaError_t e = cudaSetDevice(o.device);
     if (e == cudaSuccess) {
         if (o.stream) {
@@ -1181,6 +1280,7 @@ qoc_status qoc_set_system(qoc_ctx* ctx, int d, int M, const double* H0, const do
     QOC_GUARD_BEGIN
     check_cuda(ctx, cudaSetDevice(ctx->opt.device), "set device");
     ctx->planned = false;
+    ctx->tuned = false;
     ctx->has_sys = ctx->has_tgt = false;
     ctx->d = d;
     ctx->M = M;
@@ -1235,6 +1335,7 @@ qoc_status qoc_set_targets(qoc_ctx* ctx, int S, const double* psi0, const double
     for (double x : w) wsum += x;
     if (!(wsum > 0.0)) return set_err(ctx, QOC_ERR_ARG, "column weights must have a positive sum");
     ctx->planned = false;
+    ctx->tuned = false;
     ctx->S = S;
     ctx->nF = nF;
     ctx->psi0.assign(psi0, psi0 + blk);
@@ -1267,6 +1368,7 @@ qoc_status qoc_set_ensemble(qoc_ctx* ctx, int E, const double* delta, const doub
     }
     QOC_GUARD_BEGIN
     ctx->planned = false;
+    ctx->tuned = false;
     ctx->E = E;
     ctx->delta.assign(delta, delta + E);
     if (Hdet) ctx->Hdet.assign(Hdet, Hdet + dd2);
@@ -1297,6 +1399,7 @@ qoc_status qoc_evaluate_device(qoc_ctx* ctx, const double* u_dev, double* grad_d
     QOC_GUARD_BEGIN
     check_cuda(ctx, cudaSetDevice(ctx->opt.device), "set device");
     if (!ctx->planned) plan(ctx);
+    if (ctx->opt.autotune && !ctx->tuned) autotune(ctx, u_dev, grad_dev, out_dev);   // never inside a capture
     if (ctx->opt.graph && !ctx->opt.profile && ctx->path_kind == 0) {
         const void* key[3] = {u_dev, grad_dev, out_dev};
         if (!(ctx->gexec && key[0] == ctx->gkey[0] && key[1] == ctx->gkey[1] && key[2] == ctx->gkey[2])) {
@@ -1391,6 +1494,7 @@ qoc_status qoc_get_info(qoc_ctx* ctx, qoc_info* info) {
         info->adjoint_form = adj_lowrank_applies(ctx->S_eff, info->n, ctx->d) ? 3 : 0;
     else info->adjoint_form = 1;
     info->taylor_scheme = ctx->planned && ctx->ps ? 1 : 0;
+    info->autotune_candidates = ctx->tune_candidates;
     if (ctx->planned && ctx->path_kind == 2 && ctx->opt.exponential == QOC_EXP_CHEBYSHEV) {
         info->p = ctx->cheb_host.K;       // the Chebyshev degree, no squaring
         info->n = 0;

@@ -52,7 +52,7 @@ class qoc_options(ct.Structure):
                 ("wave_slices", ct.c_int), ("plain_fp32_exp", ct.c_int), ("sweep", ct.c_int),
                 ("gradient", ct.c_int), ("adjoint", ct.c_int), ("graph", ct.c_int), ("fault_inject", ct.c_int),
                 ("reversal", ct.c_int), ("propagation", ct.c_int), ("exponential", ct.c_int),
-                ("taylor_scheme", ct.c_int)]
+                ("taylor_scheme", ct.c_int), ("autotune", ct.c_int)]
 
 
 PROFILE_SLOTS = 16
@@ -66,7 +66,8 @@ class qoc_profile(ct.Structure):
 class qoc_info(ct.Structure):
     _fields_ = [("p", ct.c_int), ("n", ct.c_int), ("theta", ct.c_double), ("ckpt_stride", ct.c_int),
                 ("wave_slices", ct.c_int), ("n_waves", ct.c_int), ("launches_per_eval", ct.c_int), ("kernel_path", ct.c_int),
-                ("device_bytes", ct.c_longlong), ("adjoint_form", ct.c_int), ("taylor_scheme", ct.c_int)]
+                ("device_bytes", ct.c_longlong), ("adjoint_form", ct.c_int), ("taylor_scheme", ct.c_int),
+                ("autotune_candidates", ct.c_int)]
 
 
 _lib = None
@@ -282,7 +283,8 @@ class Context:
                  p_override: int = 0, n_override: int = -1, profile: bool = False,
                  plain_fp32_exp: bool = False, sweep: str = "auto", gradient: str = "exact",
                  adjoint: str = "auto", graph: bool = False, fault_inject: int = 0, reversal: bool = False,
-                 propagation: str = "unitary", exponential: str = "taylor", taylor_scheme: str = "auto"):
+                 propagation: str = "unitary", exponential: str = "taylor", taylor_scheme: str = "auto",
+                 autotune: bool = False):
         opt = qoc_default_options()
         opt.precision = PRECISIONS[precision]
         opt.tol = tol
@@ -306,6 +308,7 @@ class Context:
         opt.propagation = PROPAGATIONS[propagation]
         opt.exponential = EXPONENTIALS[exponential]
         opt.taylor_scheme = TAYLOR_SCHEMES[taylor_scheme]
+        opt.autotune = 1 if autotune else 0
         self.precision = precision
         self._ctx = qoc_create(opt)
         self.M = self.N = 0

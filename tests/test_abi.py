@@ -123,7 +123,8 @@ def test_reversal_needs_the_fp64_form(lib):
                                          ("ckpt_stride", -2), ("wave_slices", -1), ("sweep", 3), ("gradient", 2),
                                          ("adjoint", 2), ("fault_inject", 2), ("reversal", 2),
                                          ("propagation", 2), ("propagation", -1), ("exponential", 2),
-                                         ("taylor_scheme", 2), ("taylor_scheme", -1)])
+                                         ("taylor_scheme", 2), ("taylor_scheme", -1), ("autotune", 2),
+                                         ("autotune", -1)])
 def test_invalid_options_are_rejected_before_the_device(lib, field, value):
     """qoc_create validates every option on the host before it touches a device: an out-of-range
     value is QOC_ERR_ARG (1) on any machine, and no context is returned."""

@@ -109,3 +109,38 @@ def test_scheme_reporting():
     assert info["kernel_path"] == 0 and info["taylor_scheme"] == 0
     big = sy.random_problem(d=70, M=1, N=3, S=1, seed=409, nF=1)
     assert run(big, "tf32")[3]["taylor_scheme"] == 0
+
+
+# ------------------------------------------------------------------ autotuner
+def test_autotune_chooses_a_configuration_and_caches_it():
+    """qoc_options.autotune: the candidates (Taylor scheme, theta_max x {1/2, 1, 2}, sweep form) are
+    timed on the caller's inputs; whichever wins, the result meets the oracle bar, and a second
+    context of the same shape takes the cached choice without timing and gives the same numbers."""
+    prob = sy.random_problem(d=12, M=2, N=40, S=2, seed=411, nF=2, path=True, E=2, dt=0.2, u_scale=0.8)
+    cost, grad, terms, info = check(prob, "fp32", autotune=True)
+    assert info["autotune_candidates"] == 6
+    c2, g2, _, info2 = run(prob, "fp32", autotune=True)
+    assert info2["autotune_candidates"] == 0
+    assert c2 == cost and np.array_equal(g2, grad)
+
+
+def test_autotune_batched_path_and_graph_replay():
+    """The batched path under BF16_SPLIT, and a graph-replayed per-slice context (tuned before the
+    capture)."""
+    big = sy.random_problem(d=70, M=2, N=8, S=2, seed=412, nF=2, dt=0.05, u_scale=0.8)
+    info = check(big, "bf16", autotune=True)[3]
+    assert info["kernel_path"] == 1 and info["autotune_candidates"] >= 4
+    from paper_1612_04929_gb300 import Context
+    import torch
+    small = sy.random_problem(d=8, M=2, N=30, S=1, seed=413, nF=1, dt=0.2)
+    c_ref, g_ref, _ = orc.cost_and_grad(small, small.u)
+    u = torch.tensor(small.u, dtype=torch.float64, device="cuda")
+    g = torch.empty_like(u)
+    out = torch.empty(6, dtype=torch.float64, device="cuda")
+    with Context("fp32", autotune=True, graph=True) as c:
+        c.set_problem(small)
+        for _ in range(2):
+            c.evaluate_device(u.data_ptr(), g.data_ptr(), out.data_ptr())
+        c.sync()
+        assert c.info()["autotune_candidates"] >= 1
+    assert abs(float(out[0]) - c_ref) <= TOL * abs(c_ref) and rel(g.cpu().numpy(), g_ref) <= TOL
