@@ -167,10 +167,10 @@ __device__ __forceinline__ void sweep_step_grid(const Mt* __restrict__ Mx, const
             a = grp / per_row;
             sl0 = (grp - a * per_row) * NCB;
             const Mt* Mr = Mx + (size_t)a * d;
-            for (int b = q; b < d; b += g) {
+            auto step = [&](const Mt m, int b) {
                 float4 u;
                 float2 uf;
-                gsplit_elem(Mr[b], mu, u, uf);
+                gsplit_elem(m, mu, u, uf);
                 const float4* xr = xg + b * cb + sl0;
 #pragma unroll
                 for (int c = 0; c < NCB; ++c) {
@@ -189,7 +189,18 @@ __device__ __forceinline__ void sweep_step_grid(const Mt* __restrict__ Mx, const
                     s[3] = fmaf(uf.x, x.w, s[3]);
                     s[3] = fmaf(uf.y, x.z, s[3]);
                 }
+            };
+            // the matrix elements come from L2 (the propagators do not fit shared memory at large
+            // d): four loads in flight before their products
+            int b = q;
+            for (; b + 3 * g < d; b += 4 * g) {
+                const Mt m0 = Mr[b], m1 = Mr[b + g], m2 = Mr[b + 2 * g], m3 = Mr[b + 3 * g];
+                step(m0, b);
+                step(m1, b + g);
+                step(m2, b + 2 * g);
+                step(m3, b + 3 * g);
             }
+            for (; b < d; b += g) step(Mr[b], b);
         }
         for (int off = g >> 1; off > 0; off >>= 1)
 #pragma unroll
