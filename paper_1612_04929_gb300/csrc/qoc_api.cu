@@ -272,15 +272,40 @@ void plan_impl(qoc_ctx* c) {
     int seg = rev ? 1 : (c->opt.ckpt_stride > 0 ? c->opt.ckpt_stride : (int)std::ceil(std::sqrt((double)N)));
     seg = std::max(1, std::min(seg, N));
     c->scan = !rev && (c->opt.sweep == QOC_SWEEP_SCAN || (c->opt.sweep == QOC_SWEEP_AUTO && seg >= 4));
+    int sms0 = 0;
+    cudaDeviceGetAttribute(&sms0, cudaDevAttrMultiProcessorCount, c->opt.device);
+    const long want_ctas = 2L * std::max(sms0, 1);
     // column panel width: a sweep CTA owns one panel of one member (and, in the segmented form,
     // one segment); wide panels read each U_j once for more columns, narrow ones spread the work
     // over more SMs: about two sweep CTAs per SM, up to 8 columns per panel.  The segments of a
     // (default, half-evolution) wave count towards the parallelism of the segmented form.
-    int sms0 = 0;
-    cudaDeviceGetAttribute(&sms0, cudaDevAttrMultiProcessorCount, c->opt.device);
-    const long want_ctas = 2L * std::max(sms0, 1);
+    auto panel_width = [&](long par) {
+        return (int)std::min<long>(S, std::max(1L, std::min<long>(8, ((long)S * E * par + want_ctas - 1) / want_ctas)));
+    };
+    if (c->scan && c->opt.ckpt_stride <= 0 && N >= 16) {
+        // Checkpoint stride of the segmented form from a cost model of one wave's sweeps: three
+        // passes of `seg` dependent steps over all segments at once (replay, the costate's two
+        // segment passes), each running in whole rounds of resident CTAs, and two scans of
+        // `nseg` steps (one CTA per panel); a CTA step costs in proportion to its panel width.
+        const long wave = ((long)N + 1) / 2;
+        double best = -1.0;
+        int best_seg = seg;
+        const int lo = std::max(4, (int)std::sqrt((double)N) / 2), hi = std::min(N, 2 * (int)std::ceil(std::sqrt((double)N)));
+        for (int sg = lo; sg <= hi; ++sg) {
+            const long nseg = (wave + sg - 1) / sg;
+            const int w = panel_width(nseg);
+            const long ctas = (long)((S + w - 1) / w) * E * nseg;
+            const long rounds = (ctas + want_ctas - 1) / want_ctas;
+            const double cost = (double)w * (3.0 * sg * rounds + 2.0 * nseg);
+            if (best < 0.0 || cost < best) {
+                best = cost;
+                best_seg = sg;
+            }
+        }
+        seg = best_seg;
+    }
     const long par = c->scan ? std::max(1L, ((long)(N + 1) / 2 + seg - 1) / seg) : 1L;
-    c->cb = (int)std::max(1L, std::min<long>(8, ((long)S * E * par + want_ctas - 1) / want_ctas));
+    c->cb = panel_width(par);
     c->cb = std::min(c->cb, S);
     c->ncb = (S + c->cb - 1) / c->cb;
     c->Spad = c->ncb * c->cb;

@@ -59,7 +59,7 @@ def test_zero_weight_columns_are_not_needed():
 def test_transmon4_fp32_full_size():
     prob = sy.transmon4()
     cost, grad, terms, info = check(prob, "fp32")
-    assert info["kernel_path"] == 1 and info["ckpt_stride"] == 32
+    assert info["kernel_path"] == 1 and 15 <= info["ckpt_stride"] <= 64   # around sqrt(N), by the cost model
 
 
 def test_gue256_fp32_reduced_N():
@@ -89,7 +89,7 @@ def test_gue256_full_size_sampled(gue256_ref, precision):
     cost, grad, terms, info = run(prob, precision)
     assert abs(cost - c_ref) <= 1e-5 * abs(c_ref)
     assert rel(grad[:, GUE256_COLS], g_ref[:, GUE256_COLS]) <= 1e-5
-    assert info["ckpt_stride"] == 45 and info["n_waves"] > 1
+    assert 22 <= info["ckpt_stride"] <= 90 and info["n_waves"] > 1   # around sqrt(N), by the cost model
     assert info["adjoint_form"] == 0          # reverse mode (tensor-core products in BF16_SPLIT)
 
 
