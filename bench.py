@@ -31,15 +31,16 @@ UNIT = "slice-steps/s"
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, averaged over the launches
 # of one evaluation) measured by ncu, keyed by (workload, precision, kernel, wave slices)
 MEASURED_TRAFFIC = {
-    # Paterson-Stockmeyer split exponential (k_expm_fwd_ps), one full ncu capture of the
-    # 1125-slice launch: 163,072 bytes read + 83,686,144 written (74.5 KB per slice), scaled by the
-    # slices to the average launch of the two waves (1125 and 875 slices)
-    ("transmon_cavity_d40", "fp32", "expm_fwd", 1125, 1): (163072.0 + 83686144.0) * 1000 / 1125,
+    # DRAM bytes per slice of the dominant kernel, keyed (workload, precision, kernel, Taylor scheme):
+    # the Paterson-Stockmeyer split exponential (k_expm_fwd_ps), one full ncu capture of a 1125-slice
+    # launch, 163,072 bytes read + 83,686,144 written; reported per launch as bytes per slice times
+    # the launch's average slices
+    ("transmon_cavity_d40", "fp32", "expm_fwd", 1): (163072.0 + 83686144.0) / 1125,
 }
 # executed side of the same kernel from that capture: FMA pipe and issue activity, % of peak over
 # active cycles
 MEASURED_PIPES = {
-    ("transmon_cavity_d40", "fp32", "expm_fwd", 1125, 1): {"fma_pipe_pct": 52.0, "issue_active_pct": 69.5},
+    ("transmon_cavity_d40", "fp32", "expm_fwd", 1): {"fma_pipe_pct": 52.0, "issue_active_pct": 69.5},
 }
 # FP32 FMA peak from unit counts (context only; the roofline uses the measured peak):
 # SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (the maximum SM clock)
@@ -370,12 +371,13 @@ def roofline_of(prob, precision, info, prof, K, peaks, traffic_key=None):
     else:
         peak, bound, src = peaks["fp32_tflops"], "alu", peaks["fp_source"] + ", FP32"
     # the counters belong to one kernel of one configuration: reported only when that kernel dominates
-    traffic = MEASURED_TRAFFIC.get(traffic_key) if traffic_key and traffic_key[2] == top_name else None
+    per_slice_bytes = MEASURED_TRAFFIC.get(traffic_key) if traffic_key and traffic_key[2] == top_name else None
+    traffic = per_slice_bytes * slices * prob.E * K / top_launches if per_slice_bytes else None
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": traffic, "kernel": top_name, "launches": top_launches, "avg_launch_ms": top_ms / top_launches,
             "peak_source": src + " (of measured)",
             "traffic_source": ("dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of this kernel at "
-                               "this workload") if traffic else None}
+                               "this workload, per slice, times this run's average slices per launch") if traffic else None}
     if tensor:
         roof["executed_mma_tflops"] = achieved * OZ_MMA_PER_COMPLEX_PRODUCT / 4.0
         roof["note"] = ("algorithmic flops count 8 d^3 per complex product; the exact-accumulation tensor-core "
@@ -745,11 +747,9 @@ def ours_arm(args):
     prof = cp.profile()
     cp.close()
     roof = roofline_of(prob, precision, info, prof, K, peaks,
-                       traffic_key=(prob.name, precision, "expm_fwd", info["wave_slices"],
-                                    info.get("taylor_scheme", 0)))
+                       traffic_key=(prob.name, precision, "expm_fwd", info.get("taylor_scheme", 0)))
     if roof is not None:
-        pipes = MEASURED_PIPES.get((prob.name, precision, roof["kernel"], info["wave_slices"],
-                                    info.get("taylor_scheme", 0)))
+        pipes = MEASURED_PIPES.get((prob.name, precision, roof["kernel"], info.get("taylor_scheme", 0)))
         if pipes:
             roof["executed"] = dict(pipes, source="ncu --set full, one launch of this kernel at this workload "
                                                   "(sm__pipe_fma_cycles_active, smsp__issue_active)")
