@@ -862,7 +862,7 @@ static cudaError_t big_expm_ps(const BigArgs<float>& a, const DevParams& hp, cud
     const int p = hp.p, n = hp.n, d = a.d, items = a.wlen * a.E;
     const size_t ms = a.mstride;
     const int eb = ew_blocks((size_t)d * d);
-    const int qt = ps_top(p), qs = (hp.m_split - 1) / 3, cap = ps_slots(p, n);
+    const int qt = ps_top(p), qs = (hp.m_split - 1) / 3, cap = ps_big_slots(p, n);
     if (!a.sH || qt >= kPsMaxBlocks) return cudaErrorInvalidValue;
     auto count = [&]() { if (launches) ++*launches; };
     float4* X = reinterpret_cast<float4*>(a.scratch);
@@ -886,6 +886,7 @@ static cudaError_t big_expm_ps(const BigArgs<float>& a, const DevParams& hp, cud
                                                           hp.eu);
     count();
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    if ((err = store(X, cap - 1)) != cudaSuccess) return err;   // X^dag for the reverse mode
     // With tensor-core products (ozf) every product is split-grade, so every chain matrix is written
     // grid-split on its own bound.  Sliced matrices: 0 / 1 the A / B operand of X^2 and of the
     // squarings (1 keeps X for X^3), 2 X^2, 3 X^3 (once for the whole chain), 4 the chain operand.
@@ -1182,20 +1183,18 @@ cudaError_t launch_big_adj_rev_ps(const BigArgs<R>& a, const SysView<R>& sys, co
         return cudaErrorInvalidValue;
     } else {
         using C = float2;
-        const int p = hp.p, n = hp.n, d = a.d, items = a.wlen * a.E, cap = ps_slots(p, n), qt = ps_top(p);
+        const int p = hp.p, n = hp.n, d = a.d, items = a.wlen * a.E, cap = ps_big_slots(p, n), qt = ps_top(p);
         const size_t dd = (size_t)d * d, ms = a.mstride, zs = (size_t)cap * ms;
         const int eb = ew_blocks(dd);
         auto count = [&]() { if (launches) ++*launches; };
-        C* XH = reinterpret_cast<C*>(a.scratch);
-        C* Za = XH + (size_t)items * ms;
+        // X^dag of every item: the forward stored it (the last slot, item stride zs)
+        const C* XH = zst + (size_t)(cap - 1) * ms;
+        C* Za = reinterpret_cast<C*>(a.scratch) + (size_t)items * ms;
         C* Zb = Za + (size_t)items * ms;
         C* Xb = Zb + (size_t)items * ms;
         C* X2b = Xb + (size_t)items * ms;
         C* Yb = X2b + (size_t)items * ms;
-        k_big_adj_init<R><<<dim3(eb, items), 256, 0, st>>>(a.prm, sys, a.j0, a.wlen, XH, static_cast<C*>(nullptr), ms);
-        count();
-        cudaError_t err = cudaGetLastError();
-        if (err != cudaSuccess) return err;
+        cudaError_t err;
         k_big_ubar_factors<C><<<dim3(eb, items), 256, 0, st>>>(d, sv, a.wlen, states, Gbuf, a.wmax, Zb, Xb, ms);
         count();
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
@@ -1206,9 +1205,9 @@ cudaError_t launch_big_adj_rev_ps(const BigArgs<R>& a, const SysView<R>& sys, co
         C *zb = Za, *zo = Zb;
         int xh_sliced = 0;
         OzRev tc{};
-        if (oz) {
+        if (oz) {   // the chain's A1 operand, Y^dag (slot 1), is sliced once for the wave
             tc = *oz;
-            tc.xh = XH;
+            tc.xh = zst + (size_t)1 * ms;
             tc.xh_sliced = &xh_sliced;
         }
         auto rev = [&](const RevOps<C>& ops, C* O2, int mode) {
@@ -1241,11 +1240,11 @@ cudaError_t launch_big_adj_rev_ps(const BigArgs<R>& a, const SysView<R>& sys, co
         }
         if ((err = acc(zb, hp.ch[3 * qt + 1], hp.ch[3 * qt + 2], hp.ch[3 * qt + 3])) != cudaSuccess) return err;
         if (p >= 3) {   // X2bar += Ybar X^dag, Xbar += X2^dag Ybar
-            if ((err = rev(RevOps<C>{{Yb, XH, slot(0), Yb}, {ms, ms, zs, ms}}, Xb, 0)) != cudaSuccess) return err;
+            if ((err = rev(RevOps<C>{{Yb, XH, slot(0), Yb}, {ms, zs, zs, ms}}, Xb, 0)) != cudaSuccess) return err;
             if ((err = acc(zb, 0.f, 1.f, 0.f)) != cudaSuccess) return err;
         }
         if (p >= 2) {   // Xbar += X2bar X^dag + X^dag X2bar
-            if ((err = rev(RevOps<C>{{X2b, XH, XH, X2b}, {ms, ms, ms, ms}}, nullptr, 1)) != cudaSuccess) return err;
+            if ((err = rev(RevOps<C>{{X2b, XH, XH, X2b}, {ms, zs, zs, ms}}, nullptr, 1)) != cudaSuccess) return err;
             if ((err = acc(zb, 1.f, 0.f, 0.f)) != cudaSuccess) return err;
         }
         if (sys.M > 0) {

@@ -604,7 +604,7 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
     bool big_rev = false;
     size_t zbig_set = 0;
     if (big && c->opt.gradient == QOC_GRAD_EXACT && c->opt.adjoint == QOC_ADJ_AUTO && !use_tc(c)) {
-        zbig_set = (size_t)E * W * (size_t)(c->ps ? ps_slots(hp.p, hp.n) : hp.p - 1 + hp.n) * c->mstride;
+        zbig_set = (size_t)E * W * (size_t)(c->ps ? ps_big_slots(hp.p, hp.n) : hp.p - 1 + hp.n) * c->mstride;
         const size_t need = 2 * zbig_set * sizeof(C);
         if (c->Zbig.bytes >= need) {
             big_rev = true;

@@ -113,6 +113,8 @@ constexpr int kZCap = 24;
 // squaring operand S_m.
 __host__ __device__ inline int ps_top(int p) { return (p % 3 == 0 && p >= 3) ? p / 3 - 1 : p / 3; }
 __host__ __device__ inline int ps_slots(int p, int n) { return ps_top(p) + 2 + n; }
+// the batched path also keeps X^dag of every item (the last slot) for its reverse mode
+inline int ps_big_slots(int p, int n) { return ps_slots(p, n) + 1; }
 // the forward stored the operands of this evaluation's (p, n) (the reverse mode applies)
 template <typename R>
 __host__ __device__ inline bool zs_fits(const ZStore<R>& zs, int p, int n) {
