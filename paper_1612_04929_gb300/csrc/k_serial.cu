@@ -143,52 +143,53 @@ __device__ __forceinline__ unsigned pair_maxbits(const float4 v) {
     return __float_as_uint(fmaxf(fabsf(v.x), fabsf(v.y)));
 }
 
-// One FP32 step y = Mx x (+ add) from the grid-split block xg.  A group of g lanes owns row a of
-// the output and NCB consecutive columns of the panel (NCB = cb when the panel has 8 columns,
-// else 1), so each element of Mx is read and split once for NCB outputs; the lanes sum the grid
-// parts (S, exact) and the cross terms (L) of b = q, q + g, ...; the shuffle reduction adds S and
-// L with plain adds (S stays exact); lane q = 0 forms each pair S + L without error, adds the
-// source, normalises, keeps it in y, hands it to `emit` and raises *ymax to the largest component.
-template <int NCB, typename Mt, typename S, typename Emit>
+// s += u x for one grid-split element u = (u1, u2) (full value uf) and one grid-split pair x:
+// s[0], s[1] the grid parts (exact), s[2], s[3] the cross terms
+__device__ __forceinline__ void mac_grid(float* s, const float4 u, const float2 uf, const float4 x) {
+    s[0] = fmaf(u.x, x.x, s[0]);
+    s[0] = fmaf(-u.y, x.y, s[0]);
+    s[1] = fmaf(u.x, x.y, s[1]);
+    s[1] = fmaf(u.y, x.x, s[1]);
+    s[2] = fmaf(u.z, x.x, s[2]);
+    s[2] = fmaf(-u.w, x.y, s[2]);
+    s[2] = fmaf(uf.x, x.z, s[2]);
+    s[2] = fmaf(-uf.y, x.w, s[2]);
+    s[3] = fmaf(u.z, x.y, s[3]);
+    s[3] = fmaf(u.w, x.x, s[3]);
+    s[3] = fmaf(uf.x, x.w, s[3]);
+    s[3] = fmaf(uf.y, x.z, s[3]);
+}
+// the output pair S + L of one grid step: S exact, so the pair is formed without error
+__device__ __forceinline__ float4 grid_out(const float* s) {
+    float4 v;
+    two_sum(s[0], s[2], v.x, v.z);
+    two_sum(s[1], s[3], v.y, v.w);
+    return v;
+}
+
+// One FP32 step y = Mx x (+ add) from the grid-split block xg (panels narrower than 8 columns).
+// A group of g lanes owns output (a, c); the lanes sum the grid parts (S, exact) and the cross
+// terms (L) of b = q, q + g, ...; the shuffle reduction adds S and L with plain adds (S stays
+// exact); lane q = 0 forms the pair S + L without error, adds the source, normalises, keeps it in
+// y, hands it to `emit` and raises *ymax to the largest component.
+template <typename Mt, typename S, typename Emit>
 __device__ __forceinline__ void sweep_step_grid(const Mt* __restrict__ Mx, const float4* __restrict__ xg,
                                                 float4* __restrict__ y, const S* __restrict__ add, int d, int cb,
                                                 int g, float mu, unsigned* ymax, Emit emit) {
-    const int per_row = cb / NCB;
-    const int groups = d * per_row;
+    const int O = d * cb;
     const int ngroups = blockDim.x / g;
     const int gi = threadIdx.x / g, q = threadIdx.x - gi * g;
-    for (int base = 0; base < groups; base += ngroups) {
-        const int grp = base + gi;
-        float acc[NCB][4];
-#pragma unroll
-        for (int c = 0; c < NCB; ++c) acc[c][0] = acc[c][1] = acc[c][2] = acc[c][3] = 0.f;
-        int a = 0, sl0 = 0;
-        if (grp < groups) {
-            a = grp / per_row;
-            sl0 = (grp - a * per_row) * NCB;
+    for (int base = 0; base < O; base += ngroups) {
+        const int o = base + gi;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        if (o < O) {
+            const int a = o / cb, c = o - a * cb;
             const Mt* Mr = Mx + (size_t)a * d;
             auto step = [&](const Mt m, int b) {
                 float4 u;
                 float2 uf;
                 gsplit_elem(m, mu, u, uf);
-                const float4* xr = xg + b * cb + sl0;
-#pragma unroll
-                for (int c = 0; c < NCB; ++c) {
-                    const float4 x = xr[c];
-                    float* s = acc[c];
-                    s[0] = fmaf(u.x, x.x, s[0]);
-                    s[0] = fmaf(-u.y, x.y, s[0]);
-                    s[1] = fmaf(u.x, x.y, s[1]);
-                    s[1] = fmaf(u.y, x.x, s[1]);
-                    s[2] = fmaf(u.z, x.x, s[2]);
-                    s[2] = fmaf(-u.w, x.y, s[2]);
-                    s[2] = fmaf(uf.x, x.z, s[2]);
-                    s[2] = fmaf(-uf.y, x.w, s[2]);
-                    s[3] = fmaf(u.z, x.y, s[3]);
-                    s[3] = fmaf(u.w, x.x, s[3]);
-                    s[3] = fmaf(uf.x, x.w, s[3]);
-                    s[3] = fmaf(uf.y, x.z, s[3]);
-                }
+                mac_grid(acc, u, uf, xg[b * cb + c]);
             };
             // the matrix elements come from L2 (the propagators do not fit shared memory at large
             // d): four loads in flight before their products
@@ -204,34 +205,150 @@ __device__ __forceinline__ void sweep_step_grid(const Mt* __restrict__ Mx, const
         }
         for (int off = g >> 1; off > 0; off >>= 1)
 #pragma unroll
-            for (int c = 0; c < NCB; ++c)
+            for (int i = 0; i < 4; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], off);
+        if (o < O && q == 0) {
+            float4 v = grid_out(acc);
+            if (add) kadd(v, kfrom(add[o]));
+            knorm(v);
+            y[o] = v;
+            emit(o, v);
+            atomicMax(ymax, pair_maxbits(v));
+        }
+    }
+}
+
+// The FP32 step on an 8-column panel.  A group of 8 lanes owns the row pair a, a + 1 and all 8
+// columns; lane q sums b = q, q + 8, ..., so each grid-split element of x read from shared memory
+// serves two rows (16 complex multiply-adds per 8 loads).  xg rows are padded to kGridRow float4,
+// which puts the rows b .. b + 7 that a group reads at once in distinct banks.  The elements of Mx
+// are software-pipelined: those of the next PF b's are in flight while the current ones compute.
+// A reduce-scatter over the group (three shuffle rounds on halves of the sums) leaves lane q with
+// row a + (q >> 2 & 1), columns 4 (q >> 1 & 1) + 2 (q & 1) + {0, 1}; the sums of grid parts stay
+// exact in any order, so each lane completes its two outputs like the one-row step.
+constexpr int kGridRow = 9;
+template <typename Mt, typename S, typename Emit>
+__device__ __forceinline__ void sweep_step_rows2(const Mt* __restrict__ Mx, const float4* __restrict__ xg,
+                                                 float4* __restrict__ y, const S* __restrict__ add, int d, float mu,
+                                                 unsigned* ymax, Emit emit) {
+    constexpr int G = 8, CB = 8;
+    constexpr int PF = sizeof(Mt) == 8 ? 2 : 1;   // b's per pipeline stage (registers: carried pairs are wider)
+    const int pairs = (d + 1) >> 1;
+    const int ngroups = blockDim.x / G;
+    const int gi = threadIdx.x / G, q = threadIdx.x & (G - 1);
+    // the loop bound is the same for every thread, so all lanes reach the shuffles
+    for (int base = 0; base < pairs; base += ngroups) {
+        const int a = 2 * (base + gi);
+        const bool on = a < d;
+        float acc[2][CB][4];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) acc[c][i] += __shfl_xor_sync(0xffffffffu, acc[c][i], off);
-        if (grp < groups && q == 0) {
-            unsigned mb = 0u;
+        for (int r = 0; r < 2; ++r)
 #pragma unroll
-            for (int c = 0; c < NCB; ++c) {
-                const int o = a * cb + sl0 + c;
-                float4 v;
-                two_sum(acc[c][0], acc[c][2], v.x, v.z);
-                two_sum(acc[c][1], acc[c][3], v.y, v.w);
+            for (int c = 0; c < CB; ++c) acc[r][c][0] = acc[r][c][1] = acc[r][c][2] = acc[r][c][3] = 0.f;
+        if (on) {
+            const Mt* M0 = Mx + (size_t)a * d;
+            const Mt* M1 = (a + 1 < d) ? M0 + d : M0;   // odd d: the last pair repeats its row, unused
+            auto step = [&](const Mt m0, const Mt m1, int b) {
+                float4 u0, u1;
+                float2 f0, f1;
+                gsplit_elem(m0, mu, u0, f0);
+                gsplit_elem(m1, mu, u1, f1);
+                const float4* xr = xg + b * kGridRow;
+#pragma unroll
+                for (int c = 0; c < CB; ++c) {
+                    const float4 x = xr[c];
+                    mac_grid(acc[0][c], u0, f0, x);
+                    mac_grid(acc[1][c], u1, f1, x);
+                }
+            };
+            Mt cur[2][PF], nxt[2][PF];
+#pragma unroll
+            for (int u = 0; u < PF; ++u) {
+                const int bb = q + u * G;
+                cur[0][u] = bb < d ? M0[bb] : Mt{};
+                cur[1][u] = bb < d ? M1[bb] : Mt{};
+            }
+            for (int b = q; b < d; b += PF * G) {
+#pragma unroll
+                for (int u = 0; u < PF; ++u) {
+                    const int bb = b + (PF + u) * G;
+                    nxt[0][u] = bb < d ? M0[bb] : Mt{};
+                    nxt[1][u] = bb < d ? M1[bb] : Mt{};
+                }
+#pragma unroll
+                for (int u = 0; u < PF; ++u)
+                    if (b + u * G < d) step(cur[0][u], cur[1][u], b + u * G);
+#pragma unroll
+                for (int u = 0; u < PF; ++u) {
+                    cur[0][u] = nxt[0][u];
+                    cur[1][u] = nxt[1][u];
+                }
+            }
+        }
+        // reduce-scatter: keep the half named by the lane's bit, send the other half to the partner
+        const bool h2 = q & 4, h1 = q & 2, h0 = q & 1;
+        float w1[CB][4];
+#pragma unroll
+        for (int c = 0; c < CB; ++c)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float keep = h2 ? acc[1][c][k] : acc[0][c][k];
+                const float send = h2 ? acc[0][c][k] : acc[1][c][k];
+                w1[c][k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+            }
+        float w2[4][4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float keep = h1 ? w1[4 + c][k] : w1[c][k];
+                const float send = h1 ? w1[c][k] : w1[4 + c][k];
+                w2[c][k] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+            }
+        float w3[2][4];
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float keep = h0 ? w2[2 + c][k] : w2[c][k];
+                const float send = h0 ? w2[c][k] : w2[2 + c][k];
+                w3[c][k] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
+            }
+        const int row = a + (h2 ? 1 : 0);
+        unsigned mb = 0u;
+        if (on && row < d) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int o = row * CB + (h1 ? 4 : 0) + (h0 ? 2 : 0) + c;
+                float4 v = grid_out(w3[c]);
                 if (add) kadd(v, kfrom(add[o]));
                 knorm(v);
                 y[o] = v;
                 mb = max(mb, pair_maxbits(v));
                 emit(o, v);
             }
-            atomicMax(ymax, mb);
         }
+        mb = __reduce_max_sync(0xffffffffu, mb);
+        if ((threadIdx.x & 31) == 0) atomicMax(ymax, mb);
     }
 }
 
-// lanes per output group and block size: minimise the issue time of one step on one SM
-// (passes x warps per scheduler x instructions per lane).  FP32 (grid step): a group is one row
-// and NCB columns (NCB = 8 for 8-column panels, else 1); FP64 (pair-free step): one output.
+// shared memory of the FP32 step's grid-split block (none in the FP64 form)
+template <typename R>
+static size_t grid_block_bytes(int d, int cb) {
+    return sizeof(R) == 4 ? sizeof(float4) * (size_t)d * (cb == 8 ? kGridRow : cb) : 0;
+}
+
+// lanes per output group and block size.  FP32 8-column panels (two-row step): groups of 8 lanes,
+// at most 8 warps (two CTAs per SM at 128 registers).  Otherwise a group is one output; minimise
+// the issue time of one step on one SM (passes x warps per scheduler x instructions per lane).
 static void pick_sweep_shape(int d, int cb, bool fp32, int& g, int& threads) {
-    const int ncb = (fp32 && cb == 8) ? 8 : 1;
-    const int O = d * (cb / ncb);
+    if (fp32 && cb == 8) {
+        g = 8;
+        const int t = ((((d + 1) / 2) * 8 + 31) / 32) * 32;
+        threads = t < 256 ? t : 256;
+        return;
+    }
+    const int O = d * cb;
     long best = -1;
     for (int gg = 1, lg = 0; gg <= 32; gg <<= 1, ++lg) {
         const int tmax = fp32 ? 512 : 1024;   // the kernels' launch bounds
@@ -240,11 +357,10 @@ static void pick_sweep_shape(int d, int cb, bool fp32, int& g, int& threads) {
         const int groups = thr / gg;
         const int passes = (O + groups - 1) / groups;
         const int wps = (thr / 32 + 3) / 4;
-        // instructions per lane: per b of the row, the reduction, the row-group epilogue
-        const long per_b = !fp32 ? 10 : (ncb == 1 ? 20 : 8 + 14L * ncb);
-        const long red = !fp32 ? 12L * lg : 8L * ncb * lg;
-        const long epi = (fp32 && ncb > 1) ? 30L * ncb : 0;
-        const long cost = (long)passes * wps * (((d + gg - 1) / gg) * per_b + red + epi);
+        // instructions per lane: per b of the row and the reduction
+        const long per_b = fp32 ? 20 : 10;
+        const long red = (fp32 ? 8L : 12L) * lg;
+        const long cost = (long)passes * wps * (((d + gg - 1) / gg) * per_b + red);
         if (best < 0 || cost < best) {
             best = cost;
             g = gg;
@@ -301,10 +417,14 @@ k_chain(int d, StateView<R> sv, int wlen, int seg, int mode, K_t<R>* __restrict_
         if constexpr (sizeof(R) == 4) {
             const float mx = block_magic(smax[k & 1], d);
             if (tid == 0) smax[(k + 1) & 1] = 0u;
-            for (int i = tid; i < (int)panel; i += blockDim.x) xg[i] = pair_to_grid(xa[i], mx);
+            for (int i = tid; i < (int)panel; i += blockDim.x)
+                xg[NCB == 8 ? i + (i >> 3) : i] = pair_to_grid(xa[i], mx);   // 8 columns: rows of kGridRow
             __syncthreads();
-            sweep_step_grid<NCB, Mt, C>(M, xg, xb, static_cast<const C*>(nullptr), d, cb, g, mu, &smax[(k + 1) & 1],
-                                        emit);
+            if constexpr (NCB == 8)
+                sweep_step_rows2<Mt, C>(M, xg, xb, static_cast<const C*>(nullptr), d, mu, &smax[(k + 1) & 1], emit);
+            else
+                sweep_step_grid<Mt, C>(M, xg, xb, static_cast<const C*>(nullptr), d, cb, g, mu, &smax[(k + 1) & 1],
+                                       emit);
         } else {
             sweep_step<Mt, K, C>(M, xa, xb, nullptr, d, cb, g, emit);
         }
@@ -374,7 +494,7 @@ static cudaError_t chain_ring_n(const ChainArgs<R>& a, const Mt* U, size_t smem,
     return cudaGetLastError();
 }
 
-// FP32: 8-column panels take the row-group step (NCB = 8)
+// FP32: 8-column panels take the two-row step (NCB = 8)
 template <typename R, int RING, typename Mt>
 static cudaError_t chain_ring(const ChainArgs<R>& a, const Mt* U, size_t smem, cudaStream_t st) {
     if (sizeof(R) == 4 && a.sv.cb == 8) return chain_ring_n<R, RING, Mt, (sizeof(R) == 4 ? 8 : 1)>(a, U, smem, st);
@@ -384,7 +504,7 @@ static cudaError_t chain_ring(const ChainArgs<R>& a, const Mt* U, size_t smem, c
 template <typename R, typename Mt>
 static cudaError_t chain_dispatch(const ChainArgs<R>& a, const Mt* U, cudaStream_t st) {
     const size_t ub = ring_bytes((size_t)a.d * a.d, sizeof(Mt));
-    const size_t xs = (2 * sizeof(K_t<R>) + (sizeof(R) == 4 ? sizeof(float4) : 0)) * (size_t)a.d * a.sv.cb;
+    const size_t xs = 2 * sizeof(K_t<R>) * (size_t)a.d * a.sv.cb + grid_block_bytes<R>(a.d, a.sv.cb);
     if (xs > kMaxDynSmem) return cudaErrorInvalidValue;
     for (int ring : {8, 4, 2, 1}) {
         const size_t smem = ring * ub + xs;
@@ -467,9 +587,13 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 1024) k_costate(Costate
         if constexpr (sizeof(R) == 4) {
             const float mx = block_magic(smax[k & 1], d);
             if (tid == 0) smax[(k + 1) & 1] = 0u;
-            for (int i = tid; i < (int)panel; i += blockDim.x) xg[i] = pair_to_grid(xa[i], mx);
+            for (int i = tid; i < (int)panel; i += blockDim.x)
+                xg[NCB == 8 ? i + (i >> 3) : i] = pair_to_grid(xa[i], mx);   // 8 columns: rows of kGridRow
             __syncthreads();
-            sweep_step_grid<NCB, Mt, S>(M, xg, xb, add, d, cb, g, mu, &smax[(k + 1) & 1], emit);
+            if constexpr (NCB == 8)
+                sweep_step_rows2<Mt, S>(M, xg, xb, add, d, mu, &smax[(k + 1) & 1], emit);
+            else
+                sweep_step_grid<Mt, S>(M, xg, xb, add, d, cb, g, mu, &smax[(k + 1) & 1], emit);
         } else {
             sweep_step<Mt, K, S>(M, xa, xb, add, d, cb, g, emit);
         }
@@ -555,7 +679,7 @@ static cudaError_t costate_dispatch(const CostateArgs<R>& a, cudaStream_t st) {
     const size_t panel = (size_t)a.d * a.sv.cb;
     const size_t ub = ring_bytes((size_t)a.d * a.d, sizeof(Mt));
     const size_t pb = (size_t)a.sv.pstride * sizeof(S);
-    const size_t fixed = (2 * sizeof(K_t<R>) + (sizeof(R) == 4 ? sizeof(float4) : 0)) * panel;
+    const size_t fixed = 2 * sizeof(K_t<R>) * panel + grid_block_bytes<R>(a.d, a.sv.cb);
     if (fixed > kMaxDynSmem) return cudaErrorInvalidValue;
     for (int ring : {8, 4, 2, 1}) {
         const size_t smem = ring * (ub + pb) + fixed;
