@@ -547,12 +547,13 @@ def measure_config(name, precision, peaks, stream, flush, K, warmup, fp64_N=0, e
 
 def measure_batch(count, ensemble, K, warmup, stream, flush, one_by_one=True, profile=False, err_problems=()):
     """The batched sweep: `count` problems of uneven d, N, M with `ensemble`-member detuning
-    ensembles, FP32 form, one qoc_evaluate_batch call per step; optionally compared with
-    evaluating the same contexts one after another, and checked against the oracle on the first
-    40 slices of the listed problems."""
+    ensembles, FP32 form, one launch of the batch captured into a CUDA graph per step (the
+    timed value; without per-kernel profiling), beside one qoc_evaluate_batch call per step
+    (streams fanned out from the host) and, optionally, the same contexts evaluated one after
+    another; checked against the oracle on the first 40 slices of the listed problems."""
     import torch
     import synthetic as sy
-    from paper_1612_04929_gb300 import Context, qoc_evaluate_batch
+    from paper_1612_04929_gb300 import Batch, Context, qoc_evaluate_batch
     probs = sy.batch_problems(count, ensemble=ensemble)
     ctxs = []
     for p in probs:
@@ -572,21 +573,35 @@ def measure_batch(count, ensemble, K, warmup, stream, flush, one_by_one=True, pr
             c.evaluate_device(u.data_ptr(), g.data_ptr(), o.data_ptr())
             c.sync()
 
+    def timed(step):
+        ts = []
+        for _ in range(K):
+            flush.zero_()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            e = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step()
+            e.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(e))
+        return sum(ts) / len(ts)
+
     for _ in range(max(warmup, 1)):
         batch()
     torch.cuda.synchronize()
-    ts = []
-    for _ in range(K):
-        flush.zero_()
-        torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        e = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        batch()
-        e.record(stream)
-        torch.cuda.synchronize()
-        ts.append(a.elapsed_time(e))
-    ms = sum(ts) / len(ts)
+    ms_fanout = timed(batch)
+    ms_graph = None
+    graph = None
+    if not profile:   # the captured batch: one graph launch per step
+        graph = Batch(ctxs, ptr(us), ptr(gs), ptr(outs), stream.cuda_stream)
+        for _ in range(max(warmup, 1)):
+            graph.launch(stream.cuda_stream)
+        graph.sync()
+        ms_graph = timed(lambda: graph.launch(stream.cuda_stream))
+        graph.sync()
+        graph.close()
+    ms = ms_graph if ms_graph is not None else ms_fanout
     by_d = {}
     if profile:     # per-kernel event time summed over the contexts (overlapping)
         for c, p in zip(ctxs, probs):
@@ -613,8 +628,11 @@ def measure_batch(count, ensemble, K, warmup, stream, flush, one_by_one=True, pr
                               adj_flops_per_slice(inf.get("adjoint_form", 1), p.d, inf["p"], inf["n"], p.S))
     row = {"workload": f"batch{count}_E{ensemble}", "problems": count, "members": ensemble, "precision": "fp32",
            "slice_steps_per_step": units, "ms_per_step": ms, "value": units / (ms / 1e3), "unit": UNIT, "steps": K,
+           "launch": "one CUDA-graph launch of the captured batch" if ms_graph is not None else "qoc_evaluate_batch",
+           "fanout_ms_per_step": ms_fanout,
            "d_counts": {str(d): sum(1 for p in probs if p.d == d) for d in sorted({p.d for p in probs})},
            "one_by_one_ms_per_step": ms_seq, "batch_speedup_vs_one_by_one": (ms_seq / ms) if ms_seq else None,
+           "graph_speedup_vs_fanout": (ms_fanout / ms_graph) if ms_graph else None,
            "step_algorithmic_tflops": flops / (ms / 1e3) / 1e12,
            "note": "step_algorithmic_tflops: the exponentials' and adjoints' algorithmic flops (8 d^3 per complex "
                    "product) of every problem over the batch's time (no single dominant kernel)"}
@@ -895,7 +913,9 @@ def batch_arm(args):
             "warmup": args.warmup, "ms_per_step": row["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded batched sweep)",
             "config": {"workload": row["workload"], "problems": args.count, "members": args.ensemble,
-                       "slice_steps_per_step": row["slice_steps_per_step"], "d_counts": row["d_counts"]},
+                       "slice_steps_per_step": row["slice_steps_per_step"], "d_counts": row["d_counts"],
+                       "launch": row["launch"]},
+            "fanout_ms_per_step": row["fanout_ms_per_step"], "graph_speedup_vs_fanout": row["graph_speedup_vs_fanout"],
             "one_by_one_ms_per_step": row["one_by_one_ms_per_step"],
             "batch_speedup_vs_one_by_one": row["batch_speedup_vs_one_by_one"],
             "kernel_ms_by_d": row.get("kernel_ms_by_d"), "clocks": clk.summary()}

@@ -49,7 +49,8 @@ typedef enum qoc_status {
     QOC_ERR_CUDA = 7,           /* a CUDA runtime call or kernel launch failed */
     QOC_ERR_TIMEOUT = 8,        /* a bounded device wait ran out (kernel returned early) */
     QOC_ERR_UNSUPPORTED = 9,    /* size / precision combination this build does not provide */
-    QOC_ERR_RANGE = 10          /* the (p, n) heuristic needs p above its maximum (huge |H dt|) */
+    QOC_ERR_RANGE = 10,         /* the (p, n) heuristic needs p above its maximum (huge |H dt|) */
+    QOC_ERR_STALE = 11          /* a captured batch's frozen (p, n) no longer cover the controls */
 } qoc_status;
 
 /* Arithmetic of the Taylor, squaring and propagation products.  Reductions of overlaps,
@@ -284,6 +285,38 @@ qoc_status qoc_evaluate_device(qoc_ctx* ctx, const double* u_dev, double* grad_d
  * context are reported through its qoc_last_error. */
 qoc_status qoc_evaluate_batch(int count, qoc_ctx* const* ctxs, const double* const* u_dev,
                               double* const* grad_dev, double* const* out_dev, void* stream);
+
+/* A batch captured into one CUDA graph (independent problems, Sec. II.A: every slice, problem and
+ * ensemble member is independent until the sweeps).  qoc_batch_create takes the arguments of
+ * qoc_evaluate_batch, runs one evaluation of the batch as that call does (planning, device
+ * allocations, qoc_options.autotune, the (p, n) of every problem; its results are in grad_dev and
+ * out_dev when the call returns, which synchronises `stream`), then freezes the Taylor orders and
+ * grid exponents of the problems on the batched large-d path at those of this evaluation and
+ * captures a second evaluation of every problem, fork and join included, into one graph on a
+ * stream of its own.  *out receives the batch.  qoc_batch_launch replays the graph on `stream`
+ * (NULL: the legacy default stream): every problem is evaluated on the device buffers given at
+ * creation (the caller rewrites u_dev[i] in place between launches), with no host work per
+ * problem.  A replay whose controls need a larger (p, n) or grid exponents than the frozen ones
+ * still runs, with the frozen orders, and is flagged: qoc_batch_sync (which waits for the last
+ * launch) then reports QOC_ERR_STALE for that problem; frozen orders that are larger than needed
+ * only cost time.  While a batch holds a context, the context's own evaluations use the frozen
+ * orders too, and qoc_set_system / qoc_set_targets / qoc_set_ensemble refuse with QOC_ERR_STATE;
+ * destroy every batch before its contexts.  Not in a batch (QOC_ERR_UNSUPPORTED): contexts in state
+ * mode (qoc_options.propagation), profiled contexts, contexts on different devices; contexts on
+ * the legacy default stream cannot be captured (QOC_ERR_CUDA from the capture).  Errors of
+ * one context are reported through its qoc_last_error (launch and graph errors through the first
+ * context's); count < 1 or a NULL out is QOC_ERR_ARG. */
+typedef struct qoc_batch qoc_batch;
+qoc_status qoc_batch_create(int count, qoc_ctx* const* ctxs, const double* const* u_dev,
+                            double* const* grad_dev, double* const* out_dev, void* stream,
+                            qoc_batch** out);
+qoc_status qoc_batch_launch(qoc_batch* batch, void* stream);
+/* Waits for the last launch and returns the first device-side error of the batch's problems
+ * (QOC_ERR_STALE, QOC_ERR_NONFINITE, QOC_ERR_TIMEOUT, QOC_ERR_RANGE), each also recorded in its
+ * context's qoc_last_error. */
+qoc_status qoc_batch_sync(qoc_batch* batch);
+/* Waits for the last launch, releases the graph and unfreezes the contexts it held. */
+void qoc_batch_destroy(qoc_batch* batch);
 
 /* Waits for the context stream and reports a device-side error of earlier evaluations. */
 qoc_status qoc_sync(qoc_ctx* ctx);

@@ -144,11 +144,25 @@ __device__ double pick_orders(double theta, double theta_max, double tol, int p_
     return ts;
 }
 
+// Frozen orders (an evaluation replayed from a captured graph, whose launches were sized for one
+// (p, n)): the orders and grid exponents of the capture, `frozen`, stay in force.  The series at
+// (p_f, n_f) still meets the tolerance when the minimal p at n_f squarings is at most p_f; the grid
+// exponents of the current controls at (p_f, n_f) must not exceed the captured ones (a larger grid
+// exponent keeps the grid sums exact and only coarsens the split), nor m_split the captured one.
+// Otherwise the evaluation is flagged kErrStale; the frozen values are written either way, so that
+// the kernels that read them from device memory agree with the captured launches.
+__device__ bool frozen_covers(const DevParams& cur, const DevParams& f) {
+    return cur.ex <= f.ex && cur.ez <= f.ez && cur.eu <= f.eu && cur.e2 <= f.e2 && cur.e3 <= f.e3 &&
+           cur.m_split <= f.m_split;
+}
+
 __global__ void k_theta(const double* __restrict__ u, int M, int N, const double* __restrict__ norms,
                         const double* __restrict__ delta, int E, double dt, double theta_max, double tol,
-                        int p_override, int n_override, DevParams* __restrict__ prm) {
+                        int p_override, int n_override, DevParams* __restrict__ prm,
+                        const DevParams* __restrict__ frozen) {
     __shared__ double red[32];
     __shared__ double sh_ts;
+    __shared__ int sh_stale;
     double best = 0.0;
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
         double s = 0.0;
@@ -165,7 +179,29 @@ __global__ void k_theta(const double* __restrict__ u, int M, int N, const double
         if (delta)
             for (int e = 0; e < E; ++e) dmax = fmax(dmax, fabs(delta[e]));
         const double theta = dt * (norms[0] + dmax * norms[M + 1] + best);
-        sh_ts = pick_orders(theta, theta_max, tol, p_override, n_override, prm, dt);
+        if (frozen) {
+            const int pf = frozen->p, nf = frozen->n;
+            double ts = pick_orders(theta, theta_max, tol, -1, nf, prm, dt);   // minimal p at n_f
+            int stale = ts >= 0.0 && (prm->p > pf || (prm->err & kErrRange));
+            if (ts >= 0.0) {
+                ts = pick_orders(theta, theta_max, tol, pf, nf, prm, dt);      // the fields at (p_f, n_f)
+                stale |= !frozen_covers(*prm, *frozen);
+            }
+            prm->p = pf;
+            prm->n = nf;
+            prm->s = ldexp(dt, -nf);
+            prm->ex = frozen->ex;
+            prm->ez = frozen->ez;
+            prm->eu = frozen->eu;
+            prm->e2 = frozen->e2;
+            prm->e3 = frozen->e3;
+            prm->m_split = frozen->m_split;
+            if (stale) prm->err |= kErrStale;
+            sh_stale = stale;
+            sh_ts = ts;
+        } else {
+            sh_ts = pick_orders(theta, theta_max, tol, p_override, n_override, prm, dt);
+        }
     }
     __syncthreads();
     // Paterson-Stockmeyer tables, one entry per thread: the coefficients 1/k! (k <= p, zero beyond)
@@ -188,14 +224,18 @@ __global__ void k_theta(const double* __restrict__ u, int M, int N, const double
             for (int k = p; k >= 3 * t; --k) b = fma(b, ts, kInvFact.v[k]);
             e = grid_exp(1.0625 * b);
         }
+        if (frozen) {
+            if (ok && e > frozen->ew[t] && !sh_stale) atomicOr(&prm->err, kErrStale);
+            e = frozen->ew[t];
+        }
         prm->ew[t] = e;
     }
 }
 
 cudaError_t launch_theta(const double* u, int M, int N, const double* norms, const double* delta, int E,
                          double dt, double theta_max, double tol, int p_override, int n_override,
-                         DevParams* prm, cudaStream_t st) {
-    k_theta<<<1, 1024, 0, st>>>(u, M, N, norms, delta, E, dt, theta_max, tol, p_override, n_override, prm);
+                         DevParams* prm, cudaStream_t st, const DevParams* frozen) {
+    k_theta<<<1, 1024, 0, st>>>(u, M, N, norms, delta, E, dt, theta_max, tol, p_override, n_override, prm, frozen);
     return cudaGetLastError();
 }
 

@@ -172,11 +172,19 @@ struct qoc_ctx {
     }
     TcMaps tc_maps{};
     TcMaps tc_fwd_maps{};                // the tensor-core forward products' maps over the same planes
+    // orders of a captured batch (qoc_batch_create): the batched path launches for the frozen
+    // (p, n) and grid exponents without reading them back, and k_theta checks that they still
+    // cover the controls
+    int batches = 0;                     // captured batches that hold this context
+    bool frozen = false;
+    DevParams hp_frozen{};
+    DevBuf frozen_d;
 
     size_t device_bytes() const {
         const DevBuf* all[] = {&H64, &HR, &dDelta, &norms, &psiTR, &pathR, &fmask, &colw, &ckpt, &Ubuf, &states,
                                &Gbuf, &src, &carry, &Oj, &C5j, &Ofin, &gpart, &prm, &u_h, &grad_h, &out_h, &scratch,
-                               &tc_planes, &Pbuf, &lv0, &lv1, &scanst, &hbuf, &Ybuf, &Zbuf, &Zbig, &sH, &chebd, &stscr};
+                               &tc_planes, &Pbuf, &lv0, &lv1, &scanst, &hbuf, &Ybuf, &Zbuf, &Zbig, &sH, &chebd, &stscr,
+                               &frozen_d};
         size_t s = 0;
         for (auto* b : all) s += b->bytes;
         return s;
@@ -570,7 +578,8 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
     if (!known) {
         B(st);
         L(launch_theta(u, M, N, c->norms.as<double>(), c->delta.empty() ? nullptr : c->dDelta.as<double>(), E, c->dt,
-                       c->theta_max, c->opt.tol, c->opt.p_override, c->opt.n_override, prm, st),
+                       c->theta_max, c->opt.tol, c->opt.p_override, c->opt.n_override, prm, st,
+                       c->frozen ? c->frozen_d.as<DevParams>() : nullptr),
           "theta", st);
     } else {
         ++launches;
@@ -590,6 +599,8 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
     if (big) {   // the batched path launches one kernel per product: read (p, n) back once
         if (known) {
             hp = *known;
+        } else if (c->frozen) {   // a captured batch's orders: no read-back (capture-safe)
+            hp = c->hp_frozen;
         } else {
             check_cuda(c, cudaMemcpyAsync(&hp, prm, sizeof(DevParams), cudaMemcpyDeviceToHost, st), "read (p, n)");
             check_cuda(c, cudaStreamSynchronize(st), "sync (p, n)");
@@ -608,7 +619,7 @@ void evaluate_impl(qoc_ctx* c, const double* u, double* grad, double* out, const
         const size_t need = 2 * zbig_set * sizeof(C);
         if (c->Zbig.bytes >= need) {
             big_rev = true;
-        } else {
+        } else if (!c->frozen) {   // frozen orders: the store of the first evaluation, no allocation
             c->Zbig.release();
             size_t free_b = 0, total_b = 0;
             if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && need <= free_b / 4 &&
@@ -1180,6 +1191,9 @@ qoc_status device_error(qoc_ctx* c) {
     check_cuda(c, cudaStreamSynchronize(c->stream), "sync");
     c->prof.harvest();
     if (h.err & kErrTimeout) return set_err(c, QOC_ERR_TIMEOUT, "a bounded device wait ran out");
+    if (h.err & kErrStale)   // first: results computed with too small orders may overflow
+        return set_err(c, QOC_ERR_STALE, "the controls need Taylor orders or grid exponents above those of the "
+                                         "captured batch (theta = " + std::to_string(h.theta) + "); re-create the batch");
     if (h.err & kErrNonfinite) return set_err(c, QOC_ERR_NONFINITE, "NaN or Inf in the controls or the results");
     if (h.err & kErrRange)
         return set_err(c, QOC_ERR_RANGE, "Taylor order above its maximum for theta = " + std::to_string(h.theta));
@@ -1193,7 +1207,104 @@ qoc_status device_error(qoc_ctx* c) {
     catch (const std::bad_alloc&) { return set_err(ctx, QOC_ERR_OOM, "host allocation failed"); } \
     catch (...) { return set_err(ctx, QOC_ERR_CUDA, "unexpected exception"); }
 
+// argument checks of a batch call (errors through the offending context's qoc_last_error)
+qoc_status check_batch(int count, qoc_ctx* const* ctxs, const double* const* u_dev, double* const* grad_dev,
+                       double* const* out_dev) {
+    if (count < 0 || (count > 0 && (!ctxs || !u_dev || !grad_dev || !out_dev))) return QOC_ERR_ARG;
+    for (int i = 0; i < count; ++i) {
+        qoc_ctx* c = ctxs[i];
+        if (!c) return QOC_ERR_ARG;
+        c->err.clear();
+        if (!c->has_sys || !c->has_tgt) return set_err(c, QOC_ERR_STATE, "set_system and set_targets must come first");
+        if (!u_dev[i] || !grad_dev[i] || !out_dev[i]) return set_err(c, QOC_ERR_ARG, "NULL device pointer");
+        for (int k = 0; k < i; ++k)
+            if (ctxs[k] == c) return set_err(c, QOC_ERR_ARG, "a context appears twice in the batch");
+    }
+    return QOC_OK;
+}
+
+// fork and join events of a batch, one pair per context (on the context's device)
+struct BatchEvents {
+    std::vector<cudaEvent_t> fork, join;
+    qoc_status create(int count, qoc_ctx* const* ctxs) {
+        fork.assign(count, nullptr);
+        join.assign(count, nullptr);
+        for (int i = 0; i < count; ++i) {
+            cudaSetDevice(ctxs[i]->opt.device);
+            if (cudaEventCreateWithFlags(&fork[i], cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming) != cudaSuccess)
+                return set_err(ctxs[i], QOC_ERR_CUDA, "create event");
+        }
+        return QOC_OK;
+    }
+    ~BatchEvents() {
+        for (auto e : fork)
+            if (e) cudaEventDestroy(e);
+        for (auto e : join)
+            if (e) cudaEventDestroy(e);
+    }
+};
+
+// Enqueues one evaluation of every context: the (p, n) of every batched-path context without
+// frozen orders are picked first and read back with one wait; then every evaluation runs on its
+// own context's streams, forked from `caller` (fork[i]) and joined into it (join[i]).  With frozen
+// orders and tuning done nothing here waits on the host, so the caller's stream may be capturing.
+qoc_status batch_body(int count, qoc_ctx* const* ctxs, const double* const* u_dev, double* const* grad_dev,
+                      double* const* out_dev, cudaStream_t caller, const cudaEvent_t* fork, const cudaEvent_t* join) {
+    qoc_ctx* cur = nullptr;
+    try {
+        std::vector<DevParams> hp(count);
+        std::vector<char> known(count, 0);
+        bool any = false;
+        for (int i = 0; i < count; ++i) {
+            qoc_ctx* c = cur = ctxs[i];
+            check_cuda(c, cudaSetDevice(c->opt.device), "set device");
+            if (!c->planned) plan(c);
+            check_cuda(c, cudaEventRecord(fork[i], caller), "fork");
+            check_cuda(c, cudaStreamWaitEvent(c->stream, fork[i], 0), "fork wait");
+            if (c->opt.autotune && !c->tuned) autotune(c, u_dev[i], grad_dev[i], out_dev[i]);
+            if (c->path_kind == 1 && !c->frozen) {
+                check_cuda(c, launch_theta(u_dev[i], c->M, c->N, c->norms.as<double>(),
+                                           c->delta.empty() ? nullptr : c->dDelta.as<double>(), c->E, c->dt,
+                                           c->theta_max, c->opt.tol, c->opt.p_override, c->opt.n_override,
+                                           c->prm.as<DevParams>(), c->stream),
+                           "theta");
+                check_cuda(c, cudaMemcpyAsync(&hp[i], c->prm.p, sizeof(DevParams), cudaMemcpyDeviceToHost, c->stream),
+                           "read (p, n)");
+                known[i] = 1;
+                any = true;
+            }
+        }
+        if (any)   // one wait for the (p, n) of the batched-path problems
+            for (int i = 0; i < count; ++i)
+                if (known[i]) check_cuda(cur = ctxs[i], cudaStreamSynchronize(ctxs[i]->stream), "sync (p, n)");
+        for (int i = 0; i < count; ++i) {   // every evaluation on its own streams
+            qoc_ctx* c = cur = ctxs[i];
+            evaluate(c, u_dev[i], grad_dev[i], out_dev[i], known[i] ? &hp[i] : nullptr);
+        }
+        for (int i = 0; i < count; ++i) {   // join into the caller's stream
+            qoc_ctx* c = cur = ctxs[i];
+            check_cuda(c, cudaEventRecord(join[i], c->stream), "join");
+            check_cuda(c, cudaStreamWaitEvent(caller, join[i], 0), "join wait");
+        }
+        return QOC_OK;
+    } catch (const Fail& f) {
+        return f.st;
+    } catch (...) {
+        return set_err(cur, QOC_ERR_CUDA, "unexpected exception");
+    }
+}
+
 }  // namespace
+
+// a captured batch (qoc_batch_create): the graph of one evaluation of every context
+struct qoc_batch {
+    std::vector<qoc_ctx*> ctxs;
+    cudaGraphExec_t exec = nullptr;
+    int device = 0;
+    cudaStream_t last = nullptr;   // stream of the last launch
+    bool launched = false;
+};
 
 extern "C" {
 
@@ -1224,6 +1335,7 @@ const char* qoc_status_string(qoc_status s) {
         case QOC_ERR_TIMEOUT: return "QOC_ERR_TIMEOUT";
         case QOC_ERR_UNSUPPORTED: return "QOC_ERR_UNSUPPORTED";
         case QOC_ERR_RANGE: return "QOC_ERR_RANGE";
+        case QOC_ERR_STALE: return "QOC_ERR_STALE";
     }
     return "QOC_ERR_UNKNOWN";
 }
@@ -1290,6 +1402,7 @@ const char* qoc_last_error(const qoc_ctx* ctx) { return ctx ? ctx->err.c_str() :
 qoc_status qoc_set_system(qoc_ctx* ctx, int d, int M, const double* H0, const double* Hk, double dt, int N) {
     if (!ctx) return QOC_ERR_ARG;
     ctx->err.clear();
+    if (ctx->batches > 0) return set_err(ctx, QOC_ERR_STATE, "the context belongs to a captured batch (qoc_batch_destroy first)");
     if (!H0 || (M > 0 && !Hk)) return set_err(ctx, QOC_ERR_ARG, "H0 or Hk is NULL");
     if (d < 1 || d > kMaxD) return set_err(ctx, QOC_ERR_SHAPE, "d must be in [1, 512]");
     if (M < 0 || M > kMaxControls) return set_err(ctx, QOC_ERR_SHAPE, "M must be in [0, 64]");
@@ -1337,6 +1450,7 @@ qoc_status qoc_set_targets(qoc_ctx* ctx, int S, const double* psi0, const double
                            const double* col_weight, const double* psiT_path, const double* alpha) {
     if (!ctx) return QOC_ERR_ARG;
     ctx->err.clear();
+    if (ctx->batches > 0) return set_err(ctx, QOC_ERR_STATE, "the context belongs to a captured batch (qoc_batch_destroy first)");
     if (!ctx->has_sys) return set_err(ctx, QOC_ERR_STATE, "qoc_set_system must come first");
     const int d = ctx->d, N = ctx->N;
     if (!psi0 || !psiT || !alpha || (nF > 0 && !forbidden)) return set_err(ctx, QOC_ERR_ARG, "NULL argument");
@@ -1378,6 +1492,7 @@ qoc_status qoc_set_targets(qoc_ctx* ctx, int S, const double* psi0, const double
 qoc_status qoc_set_ensemble(qoc_ctx* ctx, int E, const double* delta, const double* Hdet) {
     if (!ctx) return QOC_ERR_ARG;
     ctx->err.clear();
+    if (ctx->batches > 0) return set_err(ctx, QOC_ERR_STATE, "the context belongs to a captured batch (qoc_batch_destroy first)");
     if (!ctx->has_sys) return set_err(ctx, QOC_ERR_STATE, "qoc_set_system must come first");
     if (E < 1 || E > 65535) return set_err(ctx, QOC_ERR_SHAPE, "E must be in [1, 65535]");
     if (!delta) return set_err(ctx, QOC_ERR_ARG, "delta is NULL");
@@ -1530,74 +1645,146 @@ qoc_status qoc_get_info(qoc_ctx* ctx, qoc_info* info) {
 
 qoc_status qoc_evaluate_batch(int count, qoc_ctx* const* ctxs, const double* const* u_dev, double* const* grad_dev,
                               double* const* out_dev, void* stream) {
-    if (count < 0 || (count > 0 && (!ctxs || !u_dev || !grad_dev || !out_dev))) return QOC_ERR_ARG;
+    qoc_status st = check_batch(count, ctxs, u_dev, grad_dev, out_dev);
+    if (st != QOC_OK || count == 0) return st;
+    BatchEvents ev;
+    if ((st = ev.create(count, ctxs)) != QOC_OK) return st;
+    return batch_body(count, ctxs, u_dev, grad_dev, out_dev, reinterpret_cast<cudaStream_t>(stream), ev.fork.data(),
+                      ev.join.data());
+}
+
+qoc_status qoc_batch_create(int count, qoc_ctx* const* ctxs, const double* const* u_dev, double* const* grad_dev,
+                            double* const* out_dev, void* stream, qoc_batch** out) {
+    if (!out) return QOC_ERR_ARG;
+    *out = nullptr;
+    if (count < 1) return QOC_ERR_ARG;
+    qoc_status st = check_batch(count, ctxs, u_dev, grad_dev, out_dev);
+    if (st != QOC_OK) return st;
+    const int dev = ctxs[0]->opt.device;
     for (int i = 0; i < count; ++i) {
         qoc_ctx* c = ctxs[i];
-        if (!c) return QOC_ERR_ARG;
-        c->err.clear();
-        if (!c->has_sys || !c->has_tgt) return set_err(c, QOC_ERR_STATE, "set_system and set_targets must come first");
-        if (!u_dev[i] || !grad_dev[i] || !out_dev[i]) return set_err(c, QOC_ERR_ARG, "NULL device pointer");
-        for (int k = 0; k < i; ++k)
-            if (ctxs[k] == c) return set_err(c, QOC_ERR_ARG, "a context appears twice in the batch");
+        if (c->opt.device != dev) return set_err(c, QOC_ERR_UNSUPPORTED, "a captured batch runs on one device");
+        if (c->opt.profile) return set_err(c, QOC_ERR_UNSUPPORTED, "a captured batch takes no profiled context");
+        try {
+            check_cuda(c, cudaSetDevice(dev), "set device");
+            if (!c->planned) plan(c);
+        } catch (const Fail& f) {
+            return f.st;
+        } catch (...) {
+            return set_err(c, QOC_ERR_CUDA, "unexpected exception");
+        }
+        if (c->path_kind == 2)
+            return set_err(c, QOC_ERR_UNSUPPORTED, "state mode picks its orders on the host: not in a captured batch");
     }
     cudaStream_t caller = reinterpret_cast<cudaStream_t>(stream);
-    qoc_ctx* cur = nullptr;
-    try {
-        std::vector<cudaEvent_t> evs;
-        auto fresh = [&](qoc_ctx* c) {
-            cudaEvent_t e = nullptr;
-            check_cuda(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "create event");
-            evs.push_back(e);
-            return e;
-        };
-        struct Guard {
-            std::vector<cudaEvent_t>& v;
-            ~Guard() { for (auto e : v) cudaEventDestroy(e); }
-        } guard{evs};
-        // 1) plan every context, fork its stream from the caller's stream, pick (p, n)
-        std::vector<DevParams> hp(count);
-        std::vector<char> need(count, 0);
-        bool any_big = false;
-        for (int i = 0; i < count; ++i) {
-            qoc_ctx* c = cur = ctxs[i];
-            check_cuda(c, cudaSetDevice(c->opt.device), "set device");
-            if (!c->planned) plan(c);
-            cudaEvent_t f = fresh(c);
-            check_cuda(c, cudaEventRecord(f, caller), "fork");
-            check_cuda(c, cudaStreamWaitEvent(c->stream, f, 0), "fork wait");
-            check_cuda(c, launch_theta(u_dev[i], c->M, c->N, c->norms.as<double>(),
-                                       c->delta.empty() ? nullptr : c->dDelta.as<double>(), c->E, c->dt,
-                                       c->theta_max, c->opt.tol, c->opt.p_override, c->opt.n_override,
-                                       c->prm.as<DevParams>(), c->stream),
-                       "theta");
-            if (c->path_kind == 1) {
-                need[i] = 1;
-                any_big = true;
-                check_cuda(c, cudaMemcpyAsync(&hp[i], c->prm.p, sizeof(DevParams), cudaMemcpyDeviceToHost, c->stream),
-                           "read (p, n)");
-            }
+    BatchEvents ev;
+    if ((st = ev.create(count, ctxs)) != QOC_OK) return st;
+    // 1) one evaluation as qoc_evaluate_batch runs it: plans, allocations, tuning, and the orders
+    if ((st = batch_body(count, ctxs, u_dev, grad_dev, out_dev, caller, ev.fork.data(), ev.join.data())) != QOC_OK)
+        return st;
+    if (cudaStreamSynchronize(caller) != cudaSuccess) return set_err(ctxs[0], QOC_ERR_CUDA, "sync the caller stream");
+    for (int i = 0; i < count; ++i)
+        if ((st = device_error(ctxs[i])) != QOC_OK) return st;
+    // 2) freeze the batched-path contexts' orders at those of this evaluation
+    std::vector<qoc_ctx*> froze;
+    auto thaw = [&]() {
+        for (qoc_ctx* c : froze) c->frozen = false;
+    };
+    for (int i = 0; i < count; ++i) {
+        qoc_ctx* c = ctxs[i];
+        if (c->path_kind != 1 || c->frozen) continue;
+        DevParams h{};
+        cudaError_t e = cudaMemcpy(&h, c->prm.p, sizeof(DevParams), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && !c->frozen_d.p) e = c->frozen_d.alloc(sizeof(DevParams));
+        if (e == cudaSuccess) e = cudaMemcpy(c->frozen_d.p, &h, sizeof(DevParams), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            thaw();
+            return set_err(c, QOC_ERR_CUDA, std::string("freeze orders: ") + cudaGetErrorString(e));
         }
-        // 2) one wait for the (p, n) of the batched-path problems
-        if (any_big)
-            for (int i = 0; i < count; ++i)
-                if (need[i]) check_cuda(cur = ctxs[i], cudaStreamSynchronize(ctxs[i]->stream), "sync (p, n)");
-        // 3) every evaluation on its own streams, 4) join into the caller's stream
-        for (int i = 0; i < count; ++i) {
-            qoc_ctx* c = cur = ctxs[i];
-            evaluate(c, u_dev[i], grad_dev[i], out_dev[i], &hp[i]);   // (p, n) launched above
-        }
-        for (int i = 0; i < count; ++i) {
-            qoc_ctx* c = cur = ctxs[i];
-            cudaEvent_t j = fresh(c);
-            check_cuda(c, cudaEventRecord(j, c->stream), "join");
-            check_cuda(c, cudaStreamWaitEvent(caller, j, 0), "join wait");
-        }
-        return QOC_OK;
-    } catch (const Fail& f) {
-        return f.st;
-    } catch (...) {
-        return set_err(cur, QOC_ERR_CUDA, "unexpected exception");
+        c->hp_frozen = h;
+        c->frozen = true;
+        froze.push_back(c);
     }
+    // 3) capture a second evaluation on a private stream (the caller's may be the legacy stream)
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+        thaw();
+        return set_err(ctxs[0], QOC_ERR_CUDA, "create the capture stream");
+    }
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        st = batch_body(count, ctxs, u_dev, grad_dev, out_dev, cs, ev.fork.data(), ev.join.data());
+        cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+        if (st == QOC_OK && e2 != cudaSuccess) e = e2;
+    }
+    if (st == QOC_OK && e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (st == QOC_OK && e != cudaSuccess) st = set_err(ctxs[0], QOC_ERR_CUDA, std::string("capture the batch: ") + cudaGetErrorString(e));
+    if (st != QOC_OK) {
+        if (exec) cudaGraphExecDestroy(exec);
+        cudaGetLastError();
+        thaw();
+        return st;
+    }
+    qoc_batch* b = new (std::nothrow) qoc_batch;
+    if (!b) {
+        cudaGraphExecDestroy(exec);
+        thaw();
+        return set_err(ctxs[0], QOC_ERR_OOM, "host allocation failed");
+    }
+    b->ctxs.assign(ctxs, ctxs + count);
+    b->exec = exec;
+    b->device = dev;
+    for (qoc_ctx* c : b->ctxs) ++c->batches;
+    *out = b;
+    return QOC_OK;
+}
+
+qoc_status qoc_batch_launch(qoc_batch* b, void* stream) {
+    if (!b) return QOC_ERR_ARG;
+    qoc_ctx* c0 = b->ctxs[0];
+    c0->err.clear();
+    if (cudaSetDevice(b->device) != cudaSuccess) return set_err(c0, QOC_ERR_CUDA, "set device");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const cudaError_t e = cudaGraphLaunch(b->exec, st);
+    if (e != cudaSuccess) return set_err(c0, QOC_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+    b->last = st;
+    b->launched = true;
+    return QOC_OK;
+}
+
+qoc_status qoc_batch_sync(qoc_batch* b) {
+    if (!b) return QOC_ERR_ARG;
+    qoc_ctx* c0 = b->ctxs[0];
+    c0->err.clear();
+    if (cudaSetDevice(b->device) != cudaSuccess) return set_err(c0, QOC_ERR_CUDA, "set device");
+    if (b->launched && cudaStreamSynchronize(b->last) != cudaSuccess)
+        return set_err(c0, QOC_ERR_CUDA, "sync the launch stream");
+    qoc_status first = QOC_OK;
+    for (qoc_ctx* c : b->ctxs) {
+        c->err.clear();
+        qoc_status st = QOC_OK;
+        try {
+            st = device_error(c);
+        } catch (const Fail& f) {
+            st = f.st;
+        }
+        if (first == QOC_OK) first = st;
+    }
+    return first;
+}
+
+void qoc_batch_destroy(qoc_batch* b) {
+    if (!b) return;
+    cudaSetDevice(b->device);
+    if (b->launched) cudaStreamSynchronize(b->last);
+    cudaGraphExecDestroy(b->exec);
+    for (qoc_ctx* c : b->ctxs)
+        if (--c->batches == 0) c->frozen = false;
+    delete b;
 }
 
 qoc_status qoc_get_profile(qoc_ctx* ctx, qoc_profile* out) {

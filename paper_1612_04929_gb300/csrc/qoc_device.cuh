@@ -62,7 +62,7 @@ struct DevParams {
 };
 constexpr int kFinBlocks = 32;
 
-enum : int { kErrRange = 1, kErrTimeout = 2, kErrNonfinite = 4 };
+enum : int { kErrRange = 1, kErrTimeout = 2, kErrNonfinite = 4, kErrStale = 8 };
 
 // ------------------------------------------------------------------------------------------
 // Block-strided loop over a rows x cols array, f(idx, r, c) with r = idx / cols, c = idx % cols:

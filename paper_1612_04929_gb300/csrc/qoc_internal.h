@@ -60,7 +60,7 @@ struct CostView {
 cudaError_t launch_norms(const double2* mats, int count, int d, double* norms, cudaStream_t st);
 cudaError_t launch_theta(const double* u, int M, int N, const double* norms, const double* delta, int E,
                          double dt, double theta_max, double tol, int p_override, int n_override,
-                         DevParams* prm, cudaStream_t st);
+                         DevParams* prm, cudaStream_t st, const DevParams* frozen = nullptr);
 
 // ---- conversions ----
 template <typename R>

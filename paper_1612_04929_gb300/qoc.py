@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(_PKG, "_lib", "libqoc.so")
 QOC_OK = 0
 STATUS_NAMES = {0: "QOC_OK", 1: "QOC_ERR_ARG", 2: "QOC_ERR_SHAPE", 3: "QOC_ERR_NOT_HERMITIAN",
                 4: "QOC_ERR_NONFINITE", 5: "QOC_ERR_STATE", 6: "QOC_ERR_OOM", 7: "QOC_ERR_CUDA",
-                8: "QOC_ERR_TIMEOUT", 9: "QOC_ERR_UNSUPPORTED", 10: "QOC_ERR_RANGE"}
+                8: "QOC_ERR_TIMEOUT", 9: "QOC_ERR_UNSUPPORTED", 10: "QOC_ERR_RANGE", 11: "QOC_ERR_STALE"}
 PRECISIONS = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
 SWEEPS = {"auto": 0, "serial": 1, "scan": 2}
 GRADIENTS = {"exact": 0, "first_order": 1}
@@ -36,7 +36,8 @@ TAYLOR_SCHEMES = {"auto": 0, "horner": 1}
 ABI_SYMBOLS = ("qoc_default_options", "qoc_create", "qoc_destroy", "qoc_last_error", "qoc_status_string",
                "qoc_set_system", "qoc_set_targets", "qoc_set_ensemble", "qoc_evaluate_cost_and_grad",
                "qoc_evaluate_device", "qoc_sync", "qoc_get_info", "qoc_get_profile", "qoc_reset_profile",
-               "qoc_evaluate_static", "qoc_evaluate_batch", "qoc_measure_fma_peak")
+               "qoc_evaluate_static", "qoc_evaluate_batch", "qoc_batch_create", "qoc_batch_launch",
+               "qoc_batch_sync", "qoc_batch_destroy", "qoc_measure_fma_peak")
 
 
 class QocError(RuntimeError):
@@ -116,6 +117,14 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     PP = ct.POINTER(ct.c_void_p)
     lib.qoc_evaluate_batch.argtypes = [I, PP, PP, PP, PP, VP]
     lib.qoc_evaluate_batch.restype = I
+    lib.qoc_batch_create.argtypes = [I, PP, PP, PP, PP, VP, ct.POINTER(P)]
+    lib.qoc_batch_create.restype = I
+    lib.qoc_batch_launch.argtypes = [P, VP]
+    lib.qoc_batch_launch.restype = I
+    lib.qoc_batch_sync.argtypes = [P]
+    lib.qoc_batch_sync.restype = I
+    lib.qoc_batch_destroy.argtypes = [P]
+    lib.qoc_batch_destroy.restype = None
     lib.qoc_measure_fma_peak.argtypes = [I, I, DP, ct.POINTER(ct.c_int)]
     lib.qoc_measure_fma_peak.restype = I
     _lib = lib
@@ -263,6 +272,64 @@ def qoc_evaluate_batch(ctxs, u_dev, grad_dev, out_dev, stream: int = 0) -> None:
         raise QocError(st, "; ".join(m for m in msgs if m))
 
 
+def _batch_errors(ctxs):
+    return "; ".join(m for m in (load().qoc_last_error(c.handle if isinstance(c, Context) else c).decode()
+                                 for c in ctxs) if m)
+
+
+class Batch:
+    """A batch captured into one CUDA graph (qoc_batch_create, see include/qoc.h): ``ctxs`` are
+    Context objects or raw handles, the other lists raw device pointers, one per problem.
+    Creating it evaluates the batch once (synchronising ``stream``); ``launch`` replays the
+    graph, ``sync`` waits and raises on a device-side error (QOC_ERR_STALE when the controls
+    outgrew the frozen orders).  Close the batch before its contexts."""
+
+    def __init__(self, ctxs, u_dev, grad_dev, out_dev, stream: int = 0):
+        n = len(ctxs)
+        arr = lambda xs: (ct.c_void_p * n)(*[ct.c_void_p(int(x)) for x in xs])
+        handles = (ct.c_void_p * n)(*[(c.handle if isinstance(c, Context) else c) for c in ctxs])
+        self._ctxs = list(ctxs)
+        b = ct.c_void_p()
+        st = load().qoc_batch_create(n, handles, arr(u_dev), arr(grad_dev), arr(out_dev), stream or None,
+                                     ct.byref(b))
+        if st != QOC_OK:
+            raise QocError(st, _batch_errors(self._ctxs))
+        self._b = b.value
+        for c in self._ctxs:
+            if isinstance(c, Context):
+                c._batches += 1
+
+    def launch(self, stream: int = 0):
+        st = load().qoc_batch_launch(self._b, stream or None)
+        if st != QOC_OK:
+            raise QocError(st, _batch_errors(self._ctxs))
+
+    def sync(self):
+        st = load().qoc_batch_sync(self._b)
+        if st != QOC_OK:
+            raise QocError(st, _batch_errors(self._ctxs))
+
+    def close(self):
+        if getattr(self, "_b", None):
+            load().qoc_batch_destroy(self._b)
+            self._b = None
+            for c in self._ctxs:
+                if isinstance(c, Context):
+                    c._batches -= 1
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
 def qoc_measure_fma_peak(device: int = 0, fp64: bool = False):
     """Measured FP32 (or FP64) multiply-add throughput of the device in TFLOP/s and its SM count
     (see include/qoc.h)."""
@@ -310,11 +377,14 @@ class Context:
         opt.taylor_scheme = TAYLOR_SCHEMES[taylor_scheme]
         opt.autotune = 1 if autotune else 0
         self.precision = precision
+        self._batches = 0
         self._ctx = qoc_create(opt)
         self.M = self.N = 0
 
     def close(self):
         if getattr(self, "_ctx", None):
+            if self._batches:
+                raise QocError(5, "the context belongs to a captured batch: close the batch first")
             qoc_destroy(self._ctx)
             self._ctx = None
 
