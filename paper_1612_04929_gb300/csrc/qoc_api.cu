@@ -290,31 +290,39 @@ void plan_impl(qoc_ctx* c) {
     auto panel_width = [&](long par) {
         return (int)std::min<long>(S, std::max(1L, std::min<long>(8, ((long)S * E * par + want_ctas - 1) / want_ctas)));
     };
+    // The FP32 sweeps' 8-column step (two rows per lane group) costs about 0.62 of the narrower
+    // panels' one-output step per column (instructions per FMA, 1.14 against 1.83).
+    const bool wide8 = sizeof(R) == 4 && S >= 8;
+    auto col_cost = [&](int w) { return (wide8 && w == 8) ? 0.62 * w : (double)w; };
+    const long par = c->scan ? std::max(1L, ((long)(N + 1) / 2 + seg - 1) / seg) : 1L;
+    int cbw = panel_width(par);
+    if (wide8 && cbw >= 5) cbw = 8;
     if (c->scan && c->opt.ckpt_stride <= 0 && N >= 16) {
-        // Checkpoint stride of the segmented form from a cost model of one wave's sweeps: three
-        // passes of `seg` dependent steps over all segments at once (replay, the costate's two
-        // segment passes), each running in whole rounds of resident CTAs, and two scans of
-        // `nseg` steps (one CTA per panel); a CTA step costs in proportion to its panel width.
+        // Checkpoint stride and panel width of the segmented form from a cost model of one wave's
+        // sweeps: three passes of `seg` dependent steps over all segments at once (replay, the
+        // costate's two segment passes), each running in whole rounds of resident CTAs, and two
+        // scans of `nseg` steps (one CTA per panel); a CTA step costs col_cost(panel width).
         const long wave = ((long)N + 1) / 2;
         double best = -1.0;
         int best_seg = seg;
         const int lo = std::max(4, (int)std::sqrt((double)N) / 2), hi = std::min(N, 2 * (int)std::ceil(std::sqrt((double)N)));
         for (int sg = lo; sg <= hi; ++sg) {
             const long nseg = (wave + sg - 1) / sg;
-            const int w = panel_width(nseg);
-            const long ctas = (long)((S + w - 1) / w) * E * nseg;
-            const long rounds = (ctas + want_ctas - 1) / want_ctas;
-            const double cost = (double)w * (3.0 * sg * rounds + 2.0 * nseg);
-            if (best < 0.0 || cost < best) {
-                best = cost;
-                best_seg = sg;
+            for (int w : {panel_width(nseg), wide8 ? 8 : 0}) {
+                if (w < 1) continue;
+                const long ctas = (long)((S + w - 1) / w) * E * nseg;
+                const long rounds = (ctas + want_ctas - 1) / want_ctas;
+                const double cost = col_cost(w) * (3.0 * sg * rounds + 2.0 * nseg);
+                if (best < 0.0 || cost < best) {
+                    best = cost;
+                    best_seg = sg;
+                    cbw = w;
+                }
             }
         }
         seg = best_seg;
     }
-    const long par = c->scan ? std::max(1L, ((long)(N + 1) / 2 + seg - 1) / seg) : 1L;
-    c->cb = panel_width(par);
-    c->cb = std::min(c->cb, S);
+    c->cb = std::min(cbw, S);
     c->ncb = (S + c->cb - 1) / c->cb;
     c->Spad = c->ncb * c->cb;
     const int align_elems = (int)(16 / cs) > 0 ? (int)(16 / cs) : 1;
