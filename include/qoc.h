@@ -301,7 +301,7 @@ qoc_status qoc_evaluate_batch(int count, qoc_ctx* const* ctxs, const double* con
  * launch) then reports QOC_ERR_STALE for that problem; frozen orders that are larger than needed
  * only cost time.  While a batch holds a context, the context's own evaluations use the frozen
  * orders too, and qoc_set_system / qoc_set_targets / qoc_set_ensemble refuse with QOC_ERR_STATE;
- * destroy every batch before its contexts.  Not in a batch (QOC_ERR_UNSUPPORTED): contexts in state
+ * qoc_destroy of a held context is deferred until the last batch holding it is destroyed.  Not in a batch (QOC_ERR_UNSUPPORTED): contexts in state
  * mode (qoc_options.propagation), profiled contexts, contexts on different devices; contexts on
  * the legacy default stream cannot be captured (QOC_ERR_CUDA from the capture).  Errors of
  * one context are reported through its qoc_last_error (launch and graph errors through the first
@@ -315,7 +315,8 @@ qoc_status qoc_batch_launch(qoc_batch* batch, void* stream);
  * (QOC_ERR_STALE, QOC_ERR_NONFINITE, QOC_ERR_TIMEOUT, QOC_ERR_RANGE), each also recorded in its
  * context's qoc_last_error. */
 qoc_status qoc_batch_sync(qoc_batch* batch);
-/* Waits for the last launch, releases the graph and unfreezes the contexts it held. */
+/* Waits for the last launch, releases the graph, unfreezes the contexts it held and completes a
+ * qoc_destroy deferred while it held them. */
 void qoc_batch_destroy(qoc_batch* batch);
 
 /* Waits for the context stream and reports a device-side error of earlier evaluations. */

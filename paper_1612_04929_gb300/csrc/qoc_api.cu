@@ -176,6 +176,7 @@ struct qoc_ctx {
     // (p, n) and grid exponents without reading them back, and k_theta checks that they still
     // cover the controls
     int batches = 0;                     // captured batches that hold this context
+    bool destroy_pending = false;        // qoc_destroy called while a batch held it
     bool frozen = false;
     DevParams hp_frozen{};
     DevBuf frozen_d;
@@ -1393,6 +1394,10 @@ qoc_status qoc_create(qoc_ctx** out, const qoc_options* opt) {
 
 void qoc_destroy(qoc_ctx* ctx) {
     if (!ctx) return;
+    if (ctx->batches > 0) {   // a captured batch still refers to its buffers: the last batch frees it
+        ctx->destroy_pending = true;
+        return;
+    }
     cudaSetDevice(ctx->opt.device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     ctx->drop_graph();
@@ -1791,7 +1796,10 @@ void qoc_batch_destroy(qoc_batch* b) {
     if (b->launched) cudaStreamSynchronize(b->last);
     cudaGraphExecDestroy(b->exec);
     for (qoc_ctx* c : b->ctxs)
-        if (--c->batches == 0) c->frozen = false;
+        if (--c->batches == 0) {
+            c->frozen = false;
+            if (c->destroy_pending) qoc_destroy(c);
+        }
     delete b;
 }
 

@@ -140,3 +140,21 @@ def test_batch_holds_its_contexts():
             Batch([c], *[x[1:2] for x in s.ptrs()], s.stream)
         c.close()
     s.close()
+
+
+def test_destroying_a_held_context_is_deferred_to_the_batch():
+    from paper_1612_04929_gb300 import Batch, qoc_destroy
+    probs = _problems()[:3]
+    s = _Setup(probs)
+    b = Batch([c.handle for c in s.ctxs], *s.ptrs(), s.stream)
+    before = s.results()
+    h = s.ctxs[2].handle
+    qoc_destroy(h)                     # deferred: the batch's graph still uses the context's buffers
+    s.ctxs[2]._ctx = None
+    b.launch(s.stream)
+    b.sync()
+    after = s.results()
+    for (o0, g0), (o1, g1) in zip(before, after):
+        assert np.array_equal(o0, o1) and np.array_equal(g0, g1)
+    b.close()                          # frees the context
+    s.close()
