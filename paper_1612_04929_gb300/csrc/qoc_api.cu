@@ -503,7 +503,12 @@ void plan_impl(qoc_ctx* c) {
         for (DevBuf* b : {&c->Pbuf, &c->lv0, &c->lv1, &c->scanst, &c->hbuf, &c->Ybuf}) b->release();
     }
     // second stream and the dependency events between the two streams
-    if (!c->aux) check_cuda(c, cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking), "create stream");
+    if (!c->aux) {   // the serial sweeps' stream takes the highest priority: its few dependent CTAs are
+                     // the critical path, and the parallel kernels on the other stream fill the rest
+        int least = 0, greatest = 0;
+        check_cuda(c, cudaDeviceGetStreamPriorityRange(&least, &greatest), "stream priorities");
+        check_cuda(c, cudaStreamCreateWithPriority(&c->aux, cudaStreamNonBlocking, greatest), "create stream");
+    }
     for (auto e : c->events) cudaEventDestroy(e);
     c->events.assign(4 * c->nw + 3, nullptr);
     for (auto& e : c->events) check_cuda(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "create event");
@@ -1567,7 +1572,7 @@ qoc_status qoc_evaluate_device(qoc_ctx* ctx, const double* u_dev, double* grad_d
                 throw;
             }
             check_cuda(ctx, cudaStreamEndCapture(ctx->stream, &g), "end capture");
-            cudaError_t e = cudaGraphInstantiate(&ctx->gexec, g, 0);
+            cudaError_t e = cudaGraphInstantiate(&ctx->gexec, g, cudaGraphInstantiateFlagUseNodePriority);
             cudaGraphDestroy(g);
             check_cuda(ctx, e, "instantiate graph");
             for (int i = 0; i < 3; ++i) ctx->gkey[i] = key[i];
@@ -1732,7 +1737,7 @@ qoc_status qoc_batch_create(int count, qoc_ctx* const* ctxs, const double* const
         cudaError_t e2 = cudaStreamEndCapture(cs, &g);
         if (st == QOC_OK && e2 != cudaSuccess) e = e2;
     }
-    if (st == QOC_OK && e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+    if (st == QOC_OK && e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, cudaGraphInstantiateFlagUseNodePriority);
     if (g) cudaGraphDestroy(g);
     cudaStreamDestroy(cs);
     if (st == QOC_OK && e != cudaSuccess) st = set_err(ctxs[0], QOC_ERR_CUDA, std::string("capture the batch: ") + cudaGetErrorString(e));
