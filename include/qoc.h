@@ -116,7 +116,9 @@ typedef struct qoc_options {
                              of an evaluation is taken on the device, qoc_evaluate_device captures its
                              launches once into a CUDA graph (per (u_dev, grad_dev, out_dev) triple) and
                              replays it on later calls with the same pointers; a new triple or a new
-                             plan captures again.  Ignored with profile != 0 and on the batched path. */
+                             plan captures again.  qoc_evaluate_cost_and_grad replays the graph of its
+                             own device buffers between its copies.  Ignored with profile != 0 and on
+                             the batched path. */
     int fault_inject;     /* test of the failure path, 0 (default) off.  1: the tensor-core adjoint
                              kernels (TF32_SPLIT, BF16_SPLIT, d > 68) withhold their first operand
                              copy, so their bounded mbarrier wait (shortened to 4096 polls) runs

@@ -1221,6 +1221,38 @@ qoc_status device_error(qoc_ctx* c) {
     catch (const std::bad_alloc&) { return set_err(ctx, QOC_ERR_OOM, "host allocation failed"); } \
     catch (...) { return set_err(ctx, QOC_ERR_CUDA, "unexpected exception"); }
 
+// One evaluation from an entry point: tuned first when qoc_options.autotune asks (never inside a
+// capture), then replayed from the context's captured graph when qoc_options.graph applies (the
+// per-slice path, where every decision is taken on the device; one graph per (u, grad, out)
+// pointer triple, captured on first use), else launched directly.
+void evaluate_entry(qoc_ctx* ctx, const double* u, double* grad, double* out) {
+    if (ctx->opt.autotune && !ctx->tuned) autotune(ctx, u, grad, out);
+    if (ctx->opt.graph && !ctx->opt.profile && ctx->path_kind == 0) {
+        const void* key[3] = {u, grad, out};
+        if (!(ctx->gexec && key[0] == ctx->gkey[0] && key[1] == ctx->gkey[1] && key[2] == ctx->gkey[2])) {
+            ctx->drop_graph();
+            cudaGraph_t g = nullptr;
+            check_cuda(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+            try {
+                evaluate(ctx, u, grad, out);
+            } catch (...) {
+                cudaStreamEndCapture(ctx->stream, &g);   // leave the stream usable
+                if (g) cudaGraphDestroy(g);
+                throw;
+            }
+            check_cuda(ctx, cudaStreamEndCapture(ctx->stream, &g), "end capture");
+            // the serial sweeps' stream priority is recorded in its nodes; the graph keeps it
+            cudaError_t e = cudaGraphInstantiate(&ctx->gexec, g, cudaGraphInstantiateFlagUseNodePriority);
+            cudaGraphDestroy(g);
+            check_cuda(ctx, e, "instantiate graph");
+            for (int i = 0; i < 3; ++i) ctx->gkey[i] = key[i];
+        }
+        check_cuda(ctx, cudaGraphLaunch(ctx->gexec, ctx->stream), "graph launch");
+        return;
+    }
+    evaluate(ctx, u, grad, out);
+}
+
 // argument checks of a batch call (errors through the offending context's qoc_last_error)
 qoc_status check_batch(int count, qoc_ctx* const* ctxs, const double* const* u_dev, double* const* grad_dev,
                        double* const* out_dev) {
@@ -1557,30 +1589,7 @@ qoc_status qoc_evaluate_device(qoc_ctx* ctx, const double* u_dev, double* grad_d
     QOC_GUARD_BEGIN
     check_cuda(ctx, cudaSetDevice(ctx->opt.device), "set device");
     if (!ctx->planned) plan(ctx);
-    if (ctx->opt.autotune && !ctx->tuned) autotune(ctx, u_dev, grad_dev, out_dev);   // never inside a capture
-    if (ctx->opt.graph && !ctx->opt.profile && ctx->path_kind == 0) {
-        const void* key[3] = {u_dev, grad_dev, out_dev};
-        if (!(ctx->gexec && key[0] == ctx->gkey[0] && key[1] == ctx->gkey[1] && key[2] == ctx->gkey[2])) {
-            ctx->drop_graph();
-            cudaGraph_t g = nullptr;
-            check_cuda(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-            try {
-                evaluate(ctx, u_dev, grad_dev, out_dev);
-            } catch (...) {
-                cudaStreamEndCapture(ctx->stream, &g);   // leave the stream usable
-                if (g) cudaGraphDestroy(g);
-                throw;
-            }
-            check_cuda(ctx, cudaStreamEndCapture(ctx->stream, &g), "end capture");
-            cudaError_t e = cudaGraphInstantiate(&ctx->gexec, g, cudaGraphInstantiateFlagUseNodePriority);
-            cudaGraphDestroy(g);
-            check_cuda(ctx, e, "instantiate graph");
-            for (int i = 0; i < 3; ++i) ctx->gkey[i] = key[i];
-        }
-        check_cuda(ctx, cudaGraphLaunch(ctx->gexec, ctx->stream), "graph launch");
-        return QOC_OK;
-    }
-    evaluate(ctx, u_dev, grad_dev, out_dev);
+    evaluate_entry(ctx, u_dev, grad_dev, out_dev);
     return QOC_OK;
     QOC_GUARD_END
 }
@@ -1597,7 +1606,7 @@ qoc_status qoc_evaluate_cost_and_grad(qoc_ctx* ctx, const double* u, double* cos
     if (!ctx->planned) plan(ctx);
     cudaStream_t st = ctx->stream;
     if (mn) check_cuda(ctx, cudaMemcpyAsync(ctx->u_h.p, u, mn * sizeof(double), cudaMemcpyHostToDevice, st), "copy u");
-    evaluate(ctx, ctx->u_h.as<double>(), ctx->grad_h.as<double>(), ctx->out_h.as<double>());
+    evaluate_entry(ctx, ctx->u_h.as<double>(), ctx->grad_h.as<double>(), ctx->out_h.as<double>());
     double out[6];
     if (mn)
         check_cuda(ctx, cudaMemcpyAsync(grad, ctx->grad_h.p, mn * sizeof(double), cudaMemcpyDeviceToHost, st),

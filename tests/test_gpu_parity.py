@@ -379,6 +379,15 @@ def test_graph_replay_matches_plain_launches(precision):
         assert np.array_equal(o1, o2) and np.array_equal(g1, g2)
     c_ref, g_ref, _ = orc.cost_and_grad(prob, us[1])
     assert rel(outs[True][1][1], g_ref) <= TOL[precision]
+    # the host entry point replays the graph of its own device buffers between its copies
+    host = {}
+    for graph in (False, True):
+        with Context(precision, graph=graph) as c:
+            c.set_problem(prob)
+            host[graph] = [c.evaluate(us[t % 2]) for t in range(3)]
+    for (c1, g1, t1), (c2, g2, t2) in zip(host[False], host[True]):
+        assert c1 == c2 and np.array_equal(g1, g2) and np.array_equal(t1, t2)
+    assert np.array_equal(host[True][1][1], outs[True][1][1])
 
 
 # ------------------------------------------------------------------ torch autograd
