@@ -95,6 +95,9 @@ def parse():
     ap.add_argument("--no-fp64-form", action="store_true", help="skip timing the plain FP64 GPU form")
     ap.add_argument("--no-per-config", action="store_true",
                     help="skip the per-config lines (the other four configurations, a few seconds each)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="take the planner's choices instead of timing the candidates (qoc_options.autotune) "
+                         "during the warm-up")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch every kernel of each evaluation instead of replaying the evaluation from a "
                          "captured CUDA graph (per-slice path; the batched path always launches directly)")
@@ -719,6 +722,8 @@ def ours_arm(args):
     form = dict(propagation=args.propagation, exponential=args.exponential)
     if args.taylor_scheme != "auto":
         form["taylor_scheme"] = args.taylor_scheme
+    if not args.no_autotune:   # timed during the warm-up; the other contexts below take the cached choice
+        form["autotune"] = True
     ctx = Context(precision, device=local, stream=stream.cuda_stream, ckpt_stride=args.ckpt_stride,
                   gradient=args.gradient, graph=args.graph, **form)
     ctx.set_problem(prob)
@@ -877,6 +882,8 @@ def ours_arm(args):
                 "data": f"synthetic (seeded {prob.name} system, random controls)",
                 "config": config_of(prob, precision, info["ckpt_stride"],
                                     {"p": p_of(info), "n": info["n"], "wave_slices": info["wave_slices"],
+                                     "autotune": (None if args.no_autotune else
+                                                  {"candidates_timed": info.get("autotune_candidates")}),
                                      "n_waves": info["n_waves"], "gradient": args.gradient, "graph": graphed,
                                      "propagation": args.propagation, "exponential": args.exponential,
                                      "taylor_scheme": ["horner", "paterson-stockmeyer"][info.get("taylor_scheme", 0)],

@@ -1124,17 +1124,50 @@ struct TuneChoice {
     int taylor_scheme;
     int sweep;
     double theta_max;
+    int wave_slices;   // 0: the planner's
 };
 std::mutex g_tune_mu;
 std::map<std::vector<long long>, TuneChoice> g_tune_cache;
 
+// One evaluation, replayed from the context's captured graph when qoc_options.graph applies (the
+// per-slice path, where every decision is taken on the device; one graph per (u, grad, out)
+// pointer triple, captured on first use and dropped by a new plan), else launched directly.
+void run_eval(qoc_ctx* ctx, const double* u, double* grad, double* out) {
+    if (ctx->opt.graph && !ctx->opt.profile && ctx->path_kind == 0) {
+        const void* key[3] = {u, grad, out};
+        if (!(ctx->gexec && key[0] == ctx->gkey[0] && key[1] == ctx->gkey[1] && key[2] == ctx->gkey[2])) {
+            ctx->drop_graph();
+            cudaGraph_t g = nullptr;
+            check_cuda(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+            try {
+                evaluate(ctx, u, grad, out);
+            } catch (...) {
+                cudaStreamEndCapture(ctx->stream, &g);   // leave the stream usable
+                if (g) cudaGraphDestroy(g);
+                throw;
+            }
+            check_cuda(ctx, cudaStreamEndCapture(ctx->stream, &g), "end capture");
+            // the serial sweeps' stream priority is recorded in its nodes; the graph keeps it
+            cudaError_t e = cudaGraphInstantiate(&ctx->gexec, g, cudaGraphInstantiateFlagUseNodePriority);
+            cudaGraphDestroy(g);
+            check_cuda(ctx, e, "instantiate graph");
+            for (int i = 0; i < 3; ++i) ctx->gkey[i] = key[i];
+        }
+        check_cuda(ctx, cudaGraphLaunch(ctx->gexec, ctx->stream), "graph launch");
+        return;
+    }
+    evaluate(ctx, u, grad, out);
+}
+
+// mean device time of one evaluation as the context will run it (graph replay included)
 double time_evals(qoc_ctx* c, const double* u, double* grad, double* out) {
-    evaluate(c, u, grad, out);   // warm-up: first touches, the launch attributes
+    run_eval(c, u, grad, out);   // warm-up: first touches, the launch attributes, the capture
     cudaEvent_t a = nullptr, b = nullptr;
     check_cuda(c, cudaEventCreate(&a), "autotune event");
     check_cuda(c, cudaEventCreate(&b), "autotune event");
+    const int reps = c->path_kind == 0 ? 4 : 2;   // short per-slice evaluations: more of them
     cudaEventRecord(a, c->stream);
-    for (int k = 0; k < 2; ++k) evaluate(c, u, grad, out);
+    for (int k = 0; k < reps; ++k) run_eval(c, u, grad, out);
     cudaEventRecord(b, c->stream);
     const cudaError_t e = cudaEventSynchronize(b);
     float ms = 0.f;
@@ -1142,13 +1175,14 @@ double time_evals(qoc_ctx* c, const double* u, double* grad, double* out) {
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     check_cuda(c, e, "autotune timing");
-    return ms / 2.0;
+    return ms / reps;
 }
 
 void apply_choice(qoc_ctx* c, const TuneChoice& t) {
     c->opt.taylor_scheme = t.taylor_scheme;
     c->opt.sweep = t.sweep;
     c->opt.theta_max = t.theta_max;
+    c->opt.wave_slices = t.wave_slices;
     c->planned = false;
     plan(c);
 }
@@ -1158,9 +1192,10 @@ void autotune(qoc_ctx* c, const double* u, double* grad, double* out) {
     c->tune_candidates = 0;
     if (c->path_kind == 2) return;   // state mode: nothing here to choose
     const qoc_options& o = c->opt;
+    const int wave_user = o.wave_slices;
     const std::vector<long long> key = {o.precision, c->d, c->N, c->M, c->S_eff, c->E, o.gradient, o.adjoint,
                                         o.taylor_scheme, o.sweep, c->theta_user ? (long long)(o.theta_max * 1e9) : -1,
-                                        o.plain_fp32_exp, o.reversal};
+                                        o.plain_fp32_exp, o.reversal, wave_user, o.ckpt_stride};
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
@@ -1169,7 +1204,7 @@ void autotune(qoc_ctx* c, const double* u, double* grad, double* out) {
             return;
         }
     }
-    TuneChoice best{o.taylor_scheme, o.sweep, o.theta_max};
+    TuneChoice best{o.taylor_scheme, o.sweep, o.theta_max, wave_user};
     double best_ms = time_evals(c, u, grad, out);
     c->tune_candidates = 1;
     auto trial = [&](const TuneChoice& t) {
@@ -1181,18 +1216,34 @@ void autotune(qoc_ctx* c, const double* u, double* grad, double* out) {
             best = t;
         }
     };
-    if (best.taylor_scheme == QOC_TAYLOR_AUTO && c->ps) trial({QOC_TAYLOR_HORNER, best.sweep, best.theta_max});
+    if (best.taylor_scheme == QOC_TAYLOR_AUTO && c->ps) trial({QOC_TAYLOR_HORNER, best.sweep, best.theta_max, wave_user});
     if (!c->theta_user) {
         apply_choice(c, best);
         const double t0 = c->theta_max;   // the planner's default for the scheme chosen so far
         const TuneChoice base = best;
-        trial({base.taylor_scheme, base.sweep, 0.5 * t0});
-        trial({base.taylor_scheme, base.sweep, 2.0 * t0});
+        trial({base.taylor_scheme, base.sweep, 0.5 * t0, wave_user});
+        trial({base.taylor_scheme, base.sweep, 2.0 * t0, wave_user});
     }
     if (best.sweep == QOC_SWEEP_AUTO) {
         const TuneChoice base = best;
-        trial({base.taylor_scheme, QOC_SWEEP_SERIAL, base.theta_max});
-        trial({base.taylor_scheme, QOC_SWEEP_SCAN, base.theta_max});
+        trial({base.taylor_scheme, QOC_SWEEP_SERIAL, base.theta_max, wave_user});
+        trial({base.taylor_scheme, QOC_SWEEP_SCAN, base.theta_max, wave_user});
+    }
+    if (wave_user == 0 && c->path_kind == 0) {
+        // the split of the evolution into its two waves (per-slice path: the planner counts whole
+        // rounds of resident CTAs, which the other stream's kernels partly fill): up to three
+        // strides either way, keeping two waves
+        apply_choice(c, best);
+        const TuneChoice base = best;
+        const int W0 = c->W, sg = c->seg, N = c->N;
+        if (c->nw == 2)
+            for (int k : {-3, -2, -1, 1, 2, 3}) {
+                const int w = W0 + k * sg;
+                if (2 * w < N || w >= N) continue;
+                TuneChoice t = base;
+                t.wave_slices = w;
+                trial(t);
+            }
     }
     apply_choice(c, best);
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -1222,35 +1273,10 @@ qoc_status device_error(qoc_ctx* c) {
     catch (...) { return set_err(ctx, QOC_ERR_CUDA, "unexpected exception"); }
 
 // One evaluation from an entry point: tuned first when qoc_options.autotune asks (never inside a
-// capture), then replayed from the context's captured graph when qoc_options.graph applies (the
-// per-slice path, where every decision is taken on the device; one graph per (u, grad, out)
-// pointer triple, captured on first use), else launched directly.
+// capture), then run as run_eval runs it.
 void evaluate_entry(qoc_ctx* ctx, const double* u, double* grad, double* out) {
     if (ctx->opt.autotune && !ctx->tuned) autotune(ctx, u, grad, out);
-    if (ctx->opt.graph && !ctx->opt.profile && ctx->path_kind == 0) {
-        const void* key[3] = {u, grad, out};
-        if (!(ctx->gexec && key[0] == ctx->gkey[0] && key[1] == ctx->gkey[1] && key[2] == ctx->gkey[2])) {
-            ctx->drop_graph();
-            cudaGraph_t g = nullptr;
-            check_cuda(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-            try {
-                evaluate(ctx, u, grad, out);
-            } catch (...) {
-                cudaStreamEndCapture(ctx->stream, &g);   // leave the stream usable
-                if (g) cudaGraphDestroy(g);
-                throw;
-            }
-            check_cuda(ctx, cudaStreamEndCapture(ctx->stream, &g), "end capture");
-            // the serial sweeps' stream priority is recorded in its nodes; the graph keeps it
-            cudaError_t e = cudaGraphInstantiate(&ctx->gexec, g, cudaGraphInstantiateFlagUseNodePriority);
-            cudaGraphDestroy(g);
-            check_cuda(ctx, e, "instantiate graph");
-            for (int i = 0; i < 3; ++i) ctx->gkey[i] = key[i];
-        }
-        check_cuda(ctx, cudaGraphLaunch(ctx->gexec, ctx->stream), "graph launch");
-        return;
-    }
-    evaluate(ctx, u, grad, out);
+    run_eval(ctx, u, grad, out);
 }
 
 // argument checks of a batch call (errors through the offending context's qoc_last_error)

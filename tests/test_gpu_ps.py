@@ -113,12 +113,13 @@ def test_scheme_reporting():
 
 # ------------------------------------------------------------------ autotuner
 def test_autotune_chooses_a_configuration_and_caches_it():
-    """qoc_options.autotune: the candidates (Taylor scheme, theta_max x {1/2, 1, 2}, sweep form) are
-    timed on the caller's inputs; whichever wins, the result meets the oracle bar, and a second
-    context of the same shape takes the cached choice without timing and gives the same numbers."""
+    """qoc_options.autotune: the candidates (Taylor scheme, theta_max x {1/2, 1, 2}, sweep form, and
+    on the per-slice path the split into two waves) are timed on the caller's inputs; whichever wins,
+    the result meets the oracle bar, and a second context of the same shape takes the cached choice
+    without timing and gives the same numbers."""
     prob = sy.random_problem(d=12, M=2, N=40, S=2, seed=411, nF=2, path=True, E=2, dt=0.2, u_scale=0.8)
     cost, grad, terms, info = check(prob, "fp32", autotune=True)
-    assert info["autotune_candidates"] == 6
+    assert info["autotune_candidates"] >= 6
     c2, g2, _, info2 = run(prob, "fp32", autotune=True)
     assert info2["autotune_candidates"] == 0
     assert c2 == cost and np.array_equal(g2, grad)
