@@ -163,8 +163,11 @@ typedef struct qoc_options {
                              context (unitary propagation only), time candidate configurations on
                              the caller's own inputs and keep the fastest: the Taylor scheme (if
                              taylor_scheme is auto), theta_max x {1/2, 1, 2} (if theta_max is
-                             left at 0) and the sweep form (if sweep is auto), one after another,
-                             each candidate one warm-up and two timed evaluations.  Every
+                             left at 0), the sweep form (if sweep is auto) and, on the per-slice
+                             path with two waves, the wave size (up to three checkpoint strides
+                             either side of the planner's, if wave_slices is 0), one after another,
+                             each candidate run as the context runs it (graph replay included):
+                             one warm-up and four (per-slice path) or two timed evaluations.  Every
                              candidate computes the same cost and gradient to the form's tolerance.
                              The choice is cached per process for the same form, dimensions and
                              columns, so later contexts of that shape skip the timing.  The
