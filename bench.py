@@ -988,7 +988,9 @@ def dsweep_arm(args):
             N = 2000 if d <= 64 else 500
             prob = sy.dsweep_problem(d, N=N)
             u = torch.tensor(prob.u, dtype=torch.float64, device="cuda")
-            with Context("fp32", stream=stream.cuda_stream) as c:
+            # tuned during the warm-up and, on the per-slice path, replayed from a captured graph (as
+            # the headline; --no-autotune / --no-graph take the planner's choices / plain launches)
+            with Context("fp32", stream=stream.cuda_stream, graph=args.graph, autotune=not args.no_autotune) as c:
                 c.set_problem(prob)
                 ms, g, o = timed(c, u, args.steps)
                 info = c.info()
@@ -998,7 +1000,8 @@ def dsweep_arm(args):
                 ms64, _, _ = timed(c, u, max(1, min(args.steps, 3)))
             row = {"N": N, "ms_per_step": ms, "value": N / (ms / 1e3), "fp64_ms_per_step": ms64,
                    "speedup_vs_fp64_form": ms64 / ms, "p": info["p"], "n": info["n"],
-                   "kernel_path": info["kernel_path"]}
+                   "kernel_path": info["kernel_path"], "graph": bool(args.graph and info["kernel_path"] == 0),
+                   "wave_slices": info["wave_slices"]}
             if not args.no_cpu_baseline:
                 ref_n = N if d <= 64 else 100
                 try:
@@ -1025,7 +1028,7 @@ def dsweep_arm(args):
             "warmup": max(args.warmup, 3), "ms_per_step": tot_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded GUE-drift qubit registers)",
             "config": {"workload": "dsweep", "d": list(sy.DSWEEP_D), "precision": "fp32",
-                       "l2": "flushed before every timed evaluation"},
+                       "l2": "flushed before every timed evaluation", "autotune": not args.no_autotune},
             "per_d": per_d, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
 
